@@ -1,0 +1,222 @@
+/*
+ * libstereo: GB300 (sm_103a) implementation of the data-parallel hot path of
+ * the iterative, tunable stereo method of Pillai, Ramalingam and Leonard
+ * ("High-Performance and Tunable Stereo Reconstruction", Alg. 1-4).
+ *
+ * Two layers of entry points:
+ *   1. The request API (stereo_create / stereo_submit / stereo_poll /
+ *      stereo_release / stereo_destroy): the problem statement of Alg. 1 --
+ *      given a rectified grey-scale pair (I_l, I_r), return the semi-dense
+ *      disparity D_f and its cost C_f on the high-gradient pixels Omega_I.
+ *   2. Stage entry points (stereo_census ... stereo_resample_match): one call
+ *      per step of the method on caller-owned device buffers, for callers
+ *      that run their own pipeline and for step-by-step verification.
+ *
+ * Conventions for every call:
+ *   - Images are row-major uint8 with row stride W.  Pixel (u, v) is column
+ *     u, row v; linear index v*W + u ("raster order").
+ *   - Device pointers must be CUDA device (or managed) memory on the current
+ *     device; "host" pointers are ordinary or pinned host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Stage calls are asynchronous on that stream unless stated.
+ *   - Return value: STEREO_OK (0) or a negative STEREO_E_* code.  Argument
+ *     errors are detected on the host before anything is launched; CUDA
+ *     launch errors come back as STEREO_E_CUDA.
+ *   - The caller owns all buffers passed to stage calls.  Buffers handed out
+ *     by stereo_poll are owned by the library until stereo_release.
+ *   - Limits: 5 <= W, H <= 8192, W*H < 2^27, 1 <= dmax <= 256.
+ */
+#ifndef STEREO_H
+#define STEREO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STEREO_OK 0
+#define STEREO_E_INVAL (-1)     /* bad argument (size, pointer, threshold) */
+#define STEREO_E_NOMEM (-2)     /* request larger than the memory budget, or out of device memory */
+#define STEREO_E_BUSY (-3)      /* no free slot and the queue is full: retry later */
+#define STEREO_E_PENDING (-4)   /* poll timed out: result not ready yet */
+#define STEREO_E_TIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define STEREO_E_INTERNAL (-6)  /* host-step failure (e.g. triangulation) */
+#define STEREO_E_CUDA (-7)      /* a CUDA call failed */
+#define STEREO_E_NOTFOUND (-8)  /* unknown ticket */
+#define STEREO_E_CAP (-9)       /* a caller-provided output buffer is too small */
+
+/* Tunables of Table 1 (G-scope) plus the readings this library fixes where the
+ * paper gives no value.  Thresholds are census-bit counts in [0, 24]. */
+typedef struct {
+    int device;                /* CUDA device ordinal */
+    size_t mem_budget_bytes;   /* device memory for in-flight requests (0 = 4 GiB) */
+    void* arena;               /* optional caller-provided device arena of mem_budget_bytes
+                                  (e.g. from the PyTorch caching allocator); NULL = the
+                                  library calls cudaMalloc once at create time */
+    int max_slots;             /* requests in flight at once (1 = plain per-pair path) */
+    int max_queue;             /* submitted-but-not-admitted requests before STEREO_E_BUSY */
+    int t_lo, t_hi;            /* Alg. 3 validation thresholds, 0 <= t_lo <= t_hi < 24 */
+    int t_grad;                /* Omega_I: |dI/du| + |dI/dv| >= t_grad */
+    int t_fast;                /* FAST-9 intensity threshold */
+    int kp_per_bin;            /* keypoints kept per 12x10 bin, 1..32 */
+    int uniq_margin;           /* epipolar uniqueness margin in census bits */
+    int host_threads;          /* host triangulation workers (0 = 1) */
+    void* stream;              /* cudaStream_t for all work (NULL = library creates one) */
+} stereo_config;
+
+/* Fill *cfg with the defaults: t_lo 4, t_hi 8, t_grad 8, t_fast 20,
+ * kp_per_bin 4, uniq_margin 2, max_slots 1, max_queue 64, 4 GiB budget. */
+void stereo_default_config(stereo_config* cfg);
+
+typedef struct {
+    const float* disparity;    /* D_f, H*W device fp32; 0 where never validated */
+    const uint8_t* cost;       /* C_f, H*W device uint8 census bits; t_hi where never validated */
+    const uint8_t* mask;       /* H*W device uint8 of the last pass: bit0 in Omega_I,
+                                  bit1 evaluated (has a prior), bit2 C < t_lo, bit3 C > t_hi */
+    const int32_t* planeidx;   /* H*W device int32 plane index of the last pass (-1 = no triangle) */
+    int w, h;
+    int iters;
+    const int32_t* n_support;  /* host, iters entries: |S_it| for it = 1..iters */
+    const int32_t* n_tri;      /* host, iters entries: triangles of G(S_it) */
+    const float* support;      /* host, (u, v, d) triples of S_1 .. S_iters concatenated */
+    double latency_ms;         /* submit -> result ready, host clock */
+    double host_mesh_ms;       /* time spent in the host triangulation step */
+    int status;                /* STEREO_OK or the request's error */
+} stereo_result;
+
+typedef struct stereo_ctx stereo_ctx;
+
+/* Alg. 1 as a service.  stereo_create makes a context on cfg->device. */
+int stereo_create(const stereo_config* cfg, stereo_ctx** out);
+
+/* Submit one pair (I_l, I_r) with N_D = dmax, n_iters = iters and the initial
+ * occupancy-grid size sz_occ = cell (Alg. 1, Table 1).  left/right may be host
+ * or device pointers (detected); they are copied before the call returns, so
+ * the caller may reuse them at once.  *ticket_out identifies the request.
+ * Errors: STEREO_E_INVAL (sizes, thresholds, null pointers), STEREO_E_NOMEM
+ * (needs more than the whole budget), STEREO_E_BUSY (queue full). */
+int stereo_submit(stereo_ctx* ctx, int stream_id, const uint8_t* left, const uint8_t* right,
+                  int w, int h, int dmax, int iters, int cell, uint64_t* ticket_out);
+
+/* Wait up to timeout_us (<0 = forever, 0 = test only) for a ticket.  On
+ * STEREO_OK, *out describes the result; its buffers stay valid until
+ * stereo_release.  STEREO_E_PENDING = not ready yet.  A request that failed
+ * returns its error code (out->status holds it too). */
+int stereo_poll(stereo_ctx* ctx, uint64_t ticket, stereo_result* out, int timeout_us);
+
+/* Return a finished request's buffers to the pool. */
+int stereo_release(stereo_ctx* ctx, uint64_t ticket);
+
+/* Cancel queued work, wait for in-flight work, free everything. */
+void stereo_destroy(stereo_ctx* ctx);
+
+/* Counters of the context since creation: kernels launched, requests done,
+ * pairs per launch summed (for the mean batch size). */
+typedef struct {
+    long long kernel_launches;
+    long long requests_done;
+    long long batched_pairs;
+    long long gpu_rounds;
+    double host_mesh_ms;
+} stereo_stats;
+int stereo_get_stats(stereo_ctx* ctx, stereo_stats* out);
+
+/* ---------------------------------------------------------------------------
+ * Stage entry points.  All pointers device unless marked host.
+ * ------------------------------------------------------------------------- */
+
+/* Census 5x5 transform (Sec. III-C, "Census window-based matching on a 5x5
+ * patch") of both images, and the Omega_I bit map of the left image (Sec. III,
+ * high-gradient subset).  Census code bit b (b = 0..23) enumerates the
+ * non-centre offsets row by row (dy = -2..2, dx = -2..2, bit 0 at (-2,-2)) and
+ * is set when that neighbour is strictly darker than the centre; pixels within
+ * 2 of the border get code 0.  Omega_I: 2 <= u < W-2, 2 <= v < H-2 and
+ * |L(u+1,v) - L(u-1,v)| + |L(u,v+1) - L(u,v-1)| >= t_grad; stored as bit (u & 31)
+ * of word v*ceil(W/32) + u/32.  Outputs: cL, cR: W*H uint32; omega:
+ * H*ceil(W/32) uint32.  Any output pointer may be NULL to skip it. */
+int stereo_census(const uint8_t* left, const uint8_t* right, int w, int h, int t_grad,
+                  uint32_t* cL, uint32_t* cR, uint32_t* omega, void* stream);
+
+/* FAST keypoints sampled from 12x10 spatial bins (Sec. III-A, SparseStereo).
+ * FAST-9 on the radius-3 circle with threshold t_fast; score = max over the
+ * brighter and darker circle sets of the summed excess over t_fast; 3x3
+ * non-maximum suppression (equal scores go to the smaller raster index);
+ * per bin (bx = 12u/W, by = 10v/H) the K best by (score desc, raster index
+ * asc).  out_uv: 120*K slots of (u, v) int32 pairs in bin raster order then
+ * rank, (-1, -1) for empty slots.  scratch: W*H int16 score map. */
+int stereo_fast(const uint8_t* left, int w, int h, int t_fast, int K, int16_t* scratch,
+                int32_t* out_uv, void* stream);
+
+/* Epipolar matching along rows (Sec. III-A; Alg. 4 SparseEpipolarStereo).
+ * For query (u, v): d* = first argmin over d in [0, min(dmax-1, u-2)] of
+ * popcount(cL(u,v) ^ cR(u-d,v)); accepted when cost(d*) < t_lo and every d
+ * with |d - d*| >= 2 costs at least cost(d*) + margin.  q_uv: n (u, v) pairs
+ * (entries with u < 0 are skipped); out_d: n int32, d* or -1. */
+int stereo_epipolar_match(const uint32_t* cL, const uint32_t* cR, int w, int h,
+                          const int32_t* q_uv, int n, int dmax, int t_lo, int margin,
+                          int32_t* out_d, void* stream);
+
+/* Delaunay triangulation of support points (Sec. III-A, DelaunayTriangulation;
+ * host, synchronous).  uv: n (u, v) int32 pairs in canonical order (sorted by
+ * (v, u), no duplicates, 0 <= u, v <= 16383 so the exact int64 predicates
+ * cannot overflow).  Cocircular ties resolve by symbolic perturbation of
+ * the lifted coordinate u^2 + v^2 (smaller index = larger perturbation), which
+ * makes the triangulation unique.  tri (host): up to cap sorted index triples
+ * (i < j < k) in ascending order.  Returns the triangle count or a negative
+ * error (STEREO_E_CAP when cap is too small; 2n suffices). */
+int stereo_delaunay(const int32_t* uv, int n, int32_t* tri, int cap);
+
+/* Disparity plane d = a*u + b*v + c per triangle (Eq. 3, "solving a linear
+ * system"; host, synchronous): Cramer's rule in fp64 over the vertices in
+ * index order, rounded to fp32.  d: n fp32 support disparities; abc: 3*T. */
+int stereo_planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float* abc);
+
+/* Scratch bytes stereo_raster needs for the T triangles whose vertex
+ * coordinates tri_uv_host (host, T * 6 int32) holds, on a W x H image: the
+ * per-tile counts and offsets plus one entry per (triangle, 16x16 tile of its
+ * bounding box).  0 on invalid arguments. */
+size_t stereo_raster_scratch_bytes(const int32_t* tri_uv_host, int T, int w, int h);
+
+/* Pixel -> triangle lookup table (Sec. III-B).  A pixel (u, v), sampled at
+ * integer coordinates, belongs to a triangle when every edge function is
+ * positive or zero on a top or left edge; this partitions the hull.
+ * tri_uv: T * 6 int32 vertex coordinates (u0,v0,u1,v1,u2,v2) of triangle t;
+ * planeidx: W*H int32 output, triangle id or -1.  scratch: at least
+ * stereo_raster_scratch_bytes(tri_uv_host, T, w, h) bytes of device memory;
+ * STEREO_E_CAP when scratch_bytes cannot even hold the per-tile arrays. */
+int stereo_raster(const int32_t* tri_uv, int T, int w, int h, int32_t* planeidx,
+                  void* scratch, size_t scratch_bytes, void* stream);
+
+/* One pass of DisparityInterpolation + CostEvaluation (Alg. 2) +
+ * DisparityRefinement (Alg. 3) over Omega_I.  For a pixel in Omega_I with a
+ * triangle t: D = fma(a_t, u, fma(b_t, v, c_t)) in fp32, k = rint(D); it is
+ * evaluated when 2 <= u - k <= W - 3, with cost C = popcount(cL(u,v) ^
+ * cR(u-k,v)).  Then, as Alg. 3 in raster order: C < C_f => (D_f, C_f) <- (D, C);
+ * per sz x sz cell the least C below t_lo (first in raster order on ties) and
+ * the largest C above t_hi (first in raster order) are kept as keys:
+ *   cg_key[cell] = (C << 27) | (v*W + u),  cb_key[cell] = ((24 - C) << 27) | (v*W + u),
+ * 0xFFFFFFFF when empty; both arrays, ceil(H/sz)*ceil(W/sz) entries, must hold
+ * 0xFFFFFFFF on entry (atomic minimum).  first_pass = 1 treats D_f, C_f as
+ * their initial values (0, t_hi) without reading them.  mask may be NULL. */
+int stereo_validate(const uint32_t* cL, const uint32_t* cR, const uint32_t* omega,
+                    const int32_t* planeidx, const float* abc, int w, int h, int sz,
+                    int t_lo, int t_hi, int first_pass, float* D_f, uint8_t* C_f,
+                    uint8_t* mask, uint32_t* cg_key, uint32_t* cb_key, void* stream);
+
+/* SupportResampling (Alg. 4) per cell, fused with SparseEpipolarStereo on the
+ * invalid cells: for each cell with a cg key, cg_d = D_it at that pixel (the
+ * plane of planeidx there); for each cell with a cb key, x_d = the epipolar
+ * match of that pixel (as stereo_epipolar_match) or -1.  Cells without keys
+ * get cg_d = NaN and x_d = -1.  The caller merges them in cell raster order. */
+int stereo_resample_match(const uint32_t* cg_key, const uint32_t* cb_key, int ncells,
+                          const int32_t* planeidx, const float* abc,
+                          const uint32_t* cL, const uint32_t* cR, int w, int h, int dmax,
+                          int t_lo, int margin, float* cg_d, int32_t* x_d, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STEREO_H */

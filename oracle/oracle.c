@@ -296,7 +296,8 @@ static int tri_cmp(const void* a, const void* b) {
     return 0;
 }
 
-/* P: n points (u, v) in canonical order, no duplicates.  Writes triangles as
+/* P: n points (u, v) in canonical order, no duplicates, coordinates in
+ * [0, 16383] (the int64 in-circle determinant then cannot overflow).  Writes triangles as
  * sorted index triples (i < j < k), ascending; returns the count, or
  * OR_E_CAP. */
 int or_delaunay(const int32_t* P, int n, int32_t* tri, int cap) {

@@ -1,0 +1,997 @@
+// Host runtime of libstereo: the request API of include/stereo.h, a device
+// arena, the continuous-batching scheduler and the stage entry points.
+//
+// A request runs Alg. 1: SparseStereo (census, FAST bins, epipolar match on
+// the GPU), then per iteration the host mesh step (Delaunay + planes) and
+// the GPU pass (raster, fused validate, resample + match).  The scheduler
+// thread gathers every admitted request that is ready for a GPU stage and
+// launches each stage kind once for all of them (kernels take a PairBatch);
+// host mesh steps run on a worker pool meanwhile, so requests at different
+// iterations overlap.  max_slots = 1 gives the plain per-pair path.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+#include "../../include/stereo.h"
+
+using namespace stereo;
+
+namespace {
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ------------------------------------------------------------------ arena
+// First-fit sub-allocator over one device region (caller-provided, e.g. a
+// PyTorch tensor, or one cudaMalloc).  Not thread safe: the context mutex
+// guards it.
+class Arena {
+public:
+    void init(char* base, size_t size) {
+        base_ = base;
+        size_ = size;
+        free_.clear();
+        free_[0] = size;
+        used_.clear();
+        in_use_ = 0;
+    }
+    void* alloc(size_t bytes) {
+        bytes = align_up(bytes ? bytes : 1, 256);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                size_t off = it->first, rest = it->second - bytes;
+                free_.erase(it);
+                if (rest) free_[off + bytes] = rest;
+                used_[off] = bytes;
+                in_use_ += bytes;
+                return base_ + off;
+            }
+        }
+        return nullptr;
+    }
+    void release(void* p) {
+        if (!p) return;
+        size_t off = (size_t)((char*)p - base_);
+        auto u = used_.find(off);
+        if (u == used_.end()) return;
+        size_t bytes = u->second;
+        used_.erase(u);
+        in_use_ -= bytes;
+        auto nx = free_.lower_bound(off);
+        if (nx != free_.end() && off + bytes == nx->first) {
+            bytes += nx->second;
+            nx = free_.erase(nx);
+        }
+        if (nx != free_.begin()) {
+            auto pv = std::prev(nx);
+            if (pv->first + pv->second == off) {
+                pv->second += bytes;
+                return;
+            }
+        }
+        free_[off] = bytes;
+    }
+    size_t in_use() const { return in_use_; }
+    size_t size() const { return size_; }
+
+private:
+    char* base_ = nullptr;
+    size_t size_ = 0, in_use_ = 0;
+    std::map<size_t, size_t> free_, used_;
+};
+
+// ------------------------------------------------------------------ pinned host buffers
+struct Pinned {
+    void* p = nullptr;
+    size_t cap = 0;
+    bool ensure(size_t bytes) {
+        if (bytes <= cap) return true;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = align_up(bytes + bytes / 4, 4096);
+        if (cudaHostAlloc(&p, want, cudaHostAllocDefault) != cudaSuccess) {
+            p = nullptr;
+            return false;
+        }
+        cap = want;
+        return true;
+    }
+    void free() {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <class T> T* as() { return (T*)p; }
+};
+
+struct SupportPoint {
+    int32_t u, v;
+    float d;
+};
+
+enum State { Q_QUEUED, Q_SEED_READY, Q_RUNNING, Q_HOST, Q_ITER_READY, Q_DONE, Q_FAILED };
+
+struct Request {
+    uint64_t ticket = 0;
+    int stream_id = 0;
+    int W = 0, H = 0, dmax = 0, iters = 0, cell = 0;
+    int it = 0, sz = 0;
+    State state = Q_QUEUED;
+    int status = STEREO_OK;
+    double t_submit = 0, t_done = 0, mesh_ms = 0;
+    // inputs before admission
+    Pinned in_host;           // 2*W*H bytes when the caller gave host pointers
+    uint8_t* in_dev = nullptr;  // arena copy when the caller gave device pointers
+    // device block
+    void* block = nullptr;
+    PairDev dev{};
+    int ncell_max = 0, tiles = 0;
+    // triangle buffers (device) and their capacities
+    void* tri_block = nullptr;
+    size_t tri_block_bytes = 0;
+    // host state
+    std::vector<SupportPoint> S;
+    std::vector<int32_t> n_support, n_tri;
+    std::vector<float> trace;
+    int T = 0;
+    long long bin_entries = 0;
+    Pinned st_tri;            // tri_uv (6 ints) + abc (3 floats) per triangle
+    Pinned st_kp;             // kp_uv + kp_d
+    Pinned st_cells;          // cg_key, cg_d, cb_key, x_d
+    bool resample_now = false;
+};
+
+size_t block_bytes(const Request& r, int K) {
+    const size_t N = (size_t)r.W * r.H;
+    const size_t words = (size_t)r.H * ((r.W + 31) / 32);
+    size_t b = 0;
+    auto add = [&](size_t x) { b += align_up(x, 256); };
+    add(N); add(N);              // L, R
+    add(4 * N); add(4 * N);      // cL, cR
+    add(4 * words);              // omega
+    add(4 * N);                  // planeidx (FAST scores alias it)
+    add(4 * N); add(N); add(N);  // Df, Cf, mask
+    add((size_t)kFastBins * K * 8); add((size_t)kFastBins * K * 4);
+    for (int i = 0; i < 4; i++) add(4 * (size_t)r.ncell_max);
+    add(4 * (size_t)r.tiles); add(4 * (size_t)(r.tiles + 1));
+    return b;
+}
+
+void carve(Request& r, int K) {
+    char* p = (char*)r.block;
+    const size_t N = (size_t)r.W * r.H;
+    const size_t words = (size_t)r.H * ((r.W + 31) / 32);
+    auto take = [&](size_t x) { char* q = p; p += align_up(x, 256); return q; };
+    PairDev& d = r.dev;
+    d = PairDev{};
+    d.L = (const uint8_t*)take(N);
+    d.R = (const uint8_t*)take(N);
+    d.cL = (uint32_t*)take(4 * N);
+    d.cR = (uint32_t*)take(4 * N);
+    d.omega = (uint32_t*)take(4 * words);
+    d.planeidx = (int32_t*)take(4 * N);
+    d.fast_score = (int16_t*)d.planeidx;
+    d.Df = (float*)take(4 * N);
+    d.Cf = (uint8_t*)take(N);
+    d.mask = (uint8_t*)take(N);
+    d.kp_uv = (int32_t*)take((size_t)kFastBins * K * 8);
+    d.kp_d = (int32_t*)take((size_t)kFastBins * K * 4);
+    d.cg_key = (uint32_t*)take(4 * (size_t)r.ncell_max);
+    d.cb_key = (uint32_t*)take(4 * (size_t)r.ncell_max);
+    d.cg_d = (float*)take(4 * (size_t)r.ncell_max);
+    d.x_d = (int32_t*)take(4 * (size_t)r.ncell_max);
+    d.tile_cnt = (int32_t*)take(4 * (size_t)r.tiles);
+    d.tile_off = (int32_t*)take(4 * (size_t)(r.tiles + 1));
+    d.W = r.W;
+    d.H = r.H;
+    d.dmax = r.dmax;
+    d.K = K;
+    d.tiles_x = (r.W + kRasterTile - 1) / kRasterTile;
+    d.tiles_y = (r.H + kRasterTile - 1) / kRasterTile;
+}
+
+int cells_of(int W, int H, int sz) { return ((W + sz - 1) / sz) * ((H + sz - 1) / sz); }
+
+// ------------------------------------------------------------------ worker pool
+class Pool {
+public:
+    void start(int n) {
+        for (int i = 0; i < n; i++) th_.emplace_back([this] { loop(); });
+    }
+    void push(std::function<void()> f) {
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            q_.push_back(std::move(f));
+        }
+        cv_.notify_one();
+    }
+    void stop() {
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto& t : th_) t.join();
+        th_.clear();
+    }
+
+private:
+    void loop() {
+        for (;;) {
+            std::function<void()> f;
+            {
+                std::unique_lock<std::mutex> g(mu_);
+                cv_.wait(g, [this] { return stop_ || !q_.empty(); });
+                if (q_.empty()) return;
+                f = std::move(q_.front());
+                q_.pop_front();
+            }
+            f();
+        }
+    }
+    std::mutex mu_;
+    std::condition_variable cv_;
+    std::deque<std::function<void()>> q_;
+    std::vector<std::thread> th_;
+    bool stop_ = false;
+};
+
+}  // namespace
+
+struct stereo_ctx {
+    stereo_config cfg{};
+    Params prm{};
+    int K = 4;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    char* arena_base = nullptr;
+    bool own_arena = false;
+    Arena arena;
+    std::mutex mu;
+    std::condition_variable cv_sched, cv_done;
+    std::deque<Request*> queue;
+    std::vector<Request*> active;
+    std::unordered_map<uint64_t, Request*> reqs;
+    uint64_t next_ticket = 1;
+    std::thread sched;
+    bool stop = false;
+    int host_busy = 0;
+    Pool pool;
+    Pinned desc_host;
+    void* desc_dev = nullptr;
+    size_t desc_cap = 0;
+    cudaEvent_t ev = nullptr;
+    stereo_stats stats{};
+};
+
+namespace {
+
+bool valid_params(const stereo_config& c) {
+    return c.t_lo >= 0 && c.t_lo <= c.t_hi && c.t_hi < 24 && c.t_grad >= 0 && c.t_fast >= 0 &&
+           c.kp_per_bin >= 1 && c.kp_per_bin <= kMaxK && c.uniq_margin >= 0;
+}
+
+bool valid_size(int w, int h) {
+    return w >= 5 && h >= 5 && w <= 8192 && h <= 8192 && (long long)w * h < (1ll << 27);
+}
+
+// Support set -> triangles, planes and raster inputs in the request's pinned
+// staging buffer.  Runs on a pool thread.
+int mesh_step(Request& r) {
+    const double t0 = now_ms();
+    const int n = (int)r.S.size();
+    std::vector<int32_t> P((size_t)2 * n);
+    std::vector<float> D(n);
+    for (int i = 0; i < n; i++) {
+        P[2 * i] = r.S[i].u;
+        P[2 * i + 1] = r.S[i].v;
+        D[i] = r.S[i].d;
+    }
+    const int cap = 2 * n + 8;
+    std::vector<int32_t> tri((size_t)3 * cap);
+    int T = n >= 3 ? delaunay(P.data(), n, tri.data(), cap) : 0;
+    if (T < 0) return STEREO_E_INTERNAL;
+    if (!r.st_tri.ensure((size_t)T * 36 + 64)) return STEREO_E_NOMEM;
+    int32_t* tuv = r.st_tri.as<int32_t>();
+    float* abc = (float*)(tuv + (size_t)6 * T);
+    for (int t = 0; t < T; t++)
+        for (int k = 0; k < 3; k++) {
+            tuv[6 * t + 2 * k] = P[2 * tri[3 * t + k]];
+            tuv[6 * t + 2 * k + 1] = P[2 * tri[3 * t + k] + 1];
+        }
+    planes(P.data(), D.data(), tri.data(), T, abc);
+    r.T = T;
+    r.bin_entries = raster_bin_entries(tuv, T, r.W, r.H);
+    r.n_support.push_back(n);
+    r.n_tri.push_back(T);
+    for (const auto& s : r.S) {
+        r.trace.push_back((float)s.u);
+        r.trace.push_back((float)s.v);
+        r.trace.push_back(s.d);
+    }
+    r.mesh_ms += now_ms() - t0;
+    return STEREO_OK;
+}
+
+void sort_support(std::vector<SupportPoint>& S) {
+    std::sort(S.begin(), S.end(), [](const SupportPoint& a, const SupportPoint& b) {
+        return a.v != b.v ? a.v < b.v : a.u < b.u;
+    });
+}
+
+// Host work after the seeding stage: S_1 from the accepted keypoint matches.
+int host_after_seed(stereo_ctx* c, Request& r) {
+    const int nk = kFastBins * c->K;
+    const int32_t* uv = r.st_kp.as<int32_t>();
+    const int32_t* d = uv + 2 * nk;
+    r.S.clear();
+    for (int i = 0; i < nk; i++)
+        if (uv[2 * i] >= 0 && d[i] >= 0) r.S.push_back({uv[2 * i], uv[2 * i + 1], (float)d[i]});
+    sort_support(r.S);
+    r.S.erase(std::unique(r.S.begin(), r.S.end(), [](const SupportPoint& a, const SupportPoint& b) {
+                  return a.u == b.u && a.v == b.v;
+              }), r.S.end());
+    r.it = 1;
+    r.sz = r.cell;
+    return mesh_step(r);
+}
+
+// Host work after a resampling pass: S_{it+1} = S_it + C_g picks + matched X
+// (Alg. 4), in cell raster order, existing points first, then the next mesh.
+int host_after_iter(Request& r) {
+    const int nc = cells_of(r.W, r.H, r.sz);
+    const uint32_t* gk = r.st_cells.as<uint32_t>();
+    const float* gd = (const float*)(gk + r.ncell_max);
+    const uint32_t* bk = gk + 2 * (size_t)r.ncell_max;
+    const int32_t* xd = (const int32_t*)(gk + 3 * (size_t)r.ncell_max);
+    std::vector<uint8_t> occ((size_t)r.W * r.H, 0);
+    for (const auto& s : r.S) occ[(size_t)s.v * r.W + s.u] = 1;
+    for (int c = 0; c < nc; c++) {
+        if (gk[c] == kNoKey) continue;
+        const uint32_t p = gk[c] & kIdxMask;
+        if (occ[p]) continue;
+        occ[p] = 1;
+        r.S.push_back({(int32_t)(p % r.W), (int32_t)(p / r.W), gd[c]});
+    }
+    for (int c = 0; c < nc; c++) {
+        if (bk[c] == kNoKey || xd[c] < 0) continue;
+        const uint32_t p = bk[c] & kIdxMask;
+        if (occ[p]) continue;
+        occ[p] = 1;
+        r.S.push_back({(int32_t)(p % r.W), (int32_t)(p / r.W), (float)xd[c]});
+    }
+    sort_support(r.S);
+    r.it += 1;
+    r.sz = std::max(1, r.sz / 2);
+    return mesh_step(r);
+}
+
+void finish(stereo_ctx* c, Request& r, int status) {
+    r.status = status;
+    r.state = status == STEREO_OK ? Q_DONE : Q_FAILED;
+    r.t_done = now_ms();
+    c->stats.requests_done++;
+    c->stats.host_mesh_ms += r.mesh_ms;
+}
+
+// Admit queued requests while the arena has room.  Called with c->mu held.
+void admit(stereo_ctx* c) {
+    while (!c->queue.empty() && (int)c->active.size() < c->cfg.max_slots) {
+        Request* r = c->queue.front();
+        size_t need = block_bytes(*r, c->K);
+        void* blk = c->arena.alloc(need);
+        if (!blk) {
+            if (c->active.empty()) {  // cannot ever fit next to nothing
+                c->queue.pop_front();
+                finish(c, *r, STEREO_E_NOMEM);
+                c->cv_done.notify_all();
+                continue;
+            }
+            break;
+        }
+        c->queue.pop_front();
+        r->block = blk;
+        carve(*r, c->K);
+        const size_t N = (size_t)r->W * r->H;
+        if (r->in_dev) {
+            cudaMemcpyAsync((void*)r->dev.L, r->in_dev, N, cudaMemcpyDeviceToDevice, c->stream);
+            cudaMemcpyAsync((void*)r->dev.R, r->in_dev + N, N, cudaMemcpyDeviceToDevice, c->stream);
+        } else {
+            cudaMemcpyAsync((void*)r->dev.L, r->in_host.p, N, cudaMemcpyHostToDevice, c->stream);
+            cudaMemcpyAsync((void*)r->dev.R, (char*)r->in_host.p + N, N, cudaMemcpyHostToDevice, c->stream);
+        }
+        if (r->in_dev) {  // the copy above is ordered before any later use of this memory
+            c->arena.release(r->in_dev);
+            r->in_dev = nullptr;
+        }
+        r->state = Q_SEED_READY;
+        c->active.push_back(r);
+    }
+}
+
+// Descriptor upload for one group of pairs: PairDev[n] then per work kind
+// an offset array of n + 1 ints.  Returns device pointers via out params.
+struct Group {
+    std::vector<Request*> reqs;
+    const PairDev* pd = nullptr;
+    const int* off[WK_COUNT] = {};
+    int total[WK_COUNT] = {};
+};
+
+size_t group_bytes(const Group& g) {
+    return align_up(sizeof(PairDev) * g.reqs.size(), 256) + WK_COUNT * align_up(sizeof(int) * (g.reqs.size() + 1), 256);
+}
+
+void fill_group(Group& g, char* host, char* dev) {
+    const size_t n = g.reqs.size();
+    PairDev* hp = (PairDev*)host;
+    for (size_t i = 0; i < n; i++) {
+        hp[i] = g.reqs[i]->dev;
+        if (!g.reqs[i]->resample_now) {  // no cell records on a pass that does not resample
+            hp[i].cg_key = nullptr;
+            hp[i].cb_key = nullptr;
+            hp[i].Wc = hp[i].Hc = 0;
+        }
+    }
+    g.pd = (const PairDev*)dev;
+    size_t off = align_up(sizeof(PairDev) * n, 256);
+    for (int k = 0; k < WK_COUNT; k++) {
+        int* ho = (int*)(host + off);
+        int s = 0;
+        for (size_t i = 0; i < n; i++) {
+            ho[i] = s;
+            s += work_items((WorkKind)k, hp[i]);
+        }
+        ho[n] = s;
+        g.off[k] = (const int*)(dev + off);
+        g.total[k] = s;
+        off += align_up(sizeof(int) * (n + 1), 256);
+    }
+}
+
+PairBatch batch_of(const Group& g, WorkKind k) {
+    PairBatch b{};
+    b.pd = g.pd;
+    b.work_off = g.off[k];
+    b.npairs = (int)g.reqs.size();
+    b.total = g.total[k];
+    return b;
+}
+
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) return e_;       \
+    } while (0)
+
+// One GPU round for the seed group and the iteration group.
+cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter) {
+    cudaStream_t s = c->stream;
+    // iteration group: triangle buffers, uploads, cell resets
+    for (Request* r : iter.reqs) {
+        const size_t tri_bytes = align_up((size_t)r->T * 36 + 64, 256) + align_up((size_t)r->bin_entries * 4 + 4, 256);
+        if (tri_bytes > r->tri_block_bytes) {
+            std::lock_guard<std::mutex> g(c->mu);
+            c->arena.release(r->tri_block);
+            r->tri_block = c->arena.alloc(tri_bytes * 5 / 4);
+            r->tri_block_bytes = r->tri_block ? tri_bytes * 5 / 4 : 0;
+        }
+        if (!r->tri_block) return cudaErrorMemoryAllocation;
+        char* tb = (char*)r->tri_block;
+        r->dev.tri_uv = (const int32_t*)tb;
+        r->dev.abc = (const float*)(tb + (size_t)r->T * 24);
+        r->dev.tile_list = (int32_t*)(tb + align_up((size_t)r->T * 36 + 64, 256));
+        r->dev.tile_cap = (int)r->bin_entries;
+        r->dev.T = r->T;
+        r->dev.sz = r->sz;
+        r->dev.first_pass = r->it == 1;
+        r->resample_now = r->it < r->iters;
+        r->dev.Wc = r->resample_now ? (r->W + r->sz - 1) / r->sz : 0;
+        r->dev.Hc = r->resample_now ? (r->H + r->sz - 1) / r->sz : 0;
+        if (r->T > 0) CK(cudaMemcpyAsync((void*)r->dev.tri_uv, r->st_tri.p, (size_t)r->T * 36, cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(r->dev.tile_cnt, 0, sizeof(int32_t) * r->tiles, s));
+        if (r->resample_now) {
+            const int nc = r->dev.Wc * r->dev.Hc;
+            CK(launch_fill_u32(r->dev.cg_key, kNoKey, nc, s));
+            CK(launch_fill_u32(r->dev.cb_key, kNoKey, nc, s));
+            c->stats.kernel_launches += 2;
+        }
+    }
+    // descriptors
+    const size_t bs = group_bytes(seed), bi = group_bytes(iter);
+    if (bs + bi > c->desc_cap) {
+        if (c->desc_dev) cudaFree(c->desc_dev);
+        c->desc_cap = align_up((bs + bi) * 2, 4096);
+        CK(cudaMalloc(&c->desc_dev, c->desc_cap));
+        if (!c->desc_host.ensure(c->desc_cap)) return cudaErrorMemoryAllocation;
+    }
+    fill_group(seed, c->desc_host.as<char>(), (char*)c->desc_dev);
+    fill_group(iter, c->desc_host.as<char>() + bs, (char*)c->desc_dev + bs);
+    CK(cudaMemcpyAsync(c->desc_dev, c->desc_host.p, bs + bi, cudaMemcpyHostToDevice, s));
+    const Params& prm = c->prm;
+    int launches = 0;
+    if (!seed.reqs.empty()) {
+        CK(launch_census(batch_of(seed, WK_CENSUS), prm, s));
+        CK(launch_fast_score(batch_of(seed, WK_FAST_SCORE), prm, s));
+        CK(launch_fast_bins(batch_of(seed, WK_FAST_BINS), prm, s));
+        CK(launch_match_kp(batch_of(seed, WK_MATCH_KP), prm, s));
+        launches += 4;
+        c->stats.batched_pairs += 4 * (long long)seed.reqs.size();
+    }
+    if (!iter.reqs.empty()) {
+        CK(launch_raster_count(batch_of(iter, WK_TRI), s));
+        CK(launch_raster_scan(batch_of(iter, WK_SCAN), s));
+        CK(launch_raster_fill(batch_of(iter, WK_TRI), s));
+        CK(launch_raster_pixels(batch_of(iter, WK_RASTER), s));
+        CK(launch_validate(batch_of(iter, WK_VALIDATE), prm, s));
+        launches += 5;
+        c->stats.batched_pairs += 5 * (long long)iter.reqs.size();
+        if (batch_of(iter, WK_RESAMPLE).total > 0) {
+            CK(launch_resample(batch_of(iter, WK_RESAMPLE), prm, s));
+            launches += 1;
+        }
+    }
+    c->stats.kernel_launches += launches;
+    // results to pinned host memory
+    for (Request* r : seed.reqs) {
+        const int nk = kFastBins * c->K;
+        if (!r->st_kp.ensure((size_t)nk * 12)) return cudaErrorMemoryAllocation;
+        CK(cudaMemcpyAsync(r->st_kp.p, r->dev.kp_uv, (size_t)nk * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(r->st_kp.as<char>() + (size_t)nk * 8, r->dev.kp_d, (size_t)nk * 4, cudaMemcpyDeviceToHost, s));
+    }
+    for (Request* r : iter.reqs) {
+        if (!r->resample_now) continue;
+        const size_t nc = (size_t)r->dev.Wc * r->dev.Hc, m = r->ncell_max;
+        if (!r->st_cells.ensure(16 * m)) return cudaErrorMemoryAllocation;
+        char* h = r->st_cells.as<char>();
+        CK(cudaMemcpyAsync(h, r->dev.cg_key, 4 * nc, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h + 4 * m, r->dev.cg_d, 4 * nc, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h + 8 * m, r->dev.cb_key, 4 * nc, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h + 12 * m, r->dev.x_d, 4 * nc, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaEventRecord(c->ev, s));
+    CK(cudaEventSynchronize(c->ev));
+    c->stats.gpu_rounds++;
+    return cudaSuccess;
+}
+
+void scheduler(stereo_ctx* c) {
+    cudaSetDevice(c->cfg.device);
+    for (;;) {
+        Group seed, iter;
+        {
+            std::unique_lock<std::mutex> g(c->mu);
+            for (;;) {
+                admit(c);
+                for (Request* r : c->active) {
+                    if (r->state == Q_SEED_READY) seed.reqs.push_back(r);
+                    else if (r->state == Q_ITER_READY) iter.reqs.push_back(r);
+                }
+                if (!seed.reqs.empty() || !iter.reqs.empty()) break;
+                if (c->stop && c->queue.empty() && c->host_busy == 0) return;
+                c->cv_sched.wait(g);
+            }
+            for (Request* r : seed.reqs) r->state = Q_RUNNING;
+            for (Request* r : iter.reqs) r->state = Q_RUNNING;
+        }
+        cudaError_t e = gpu_round(c, seed, iter);
+        std::lock_guard<std::mutex> g(c->mu);
+        if (e != cudaSuccess) {
+            for (Request* r : seed.reqs) finish(c, *r, e == cudaErrorMemoryAllocation ? STEREO_E_NOMEM : STEREO_E_CUDA);
+            for (Request* r : iter.reqs) finish(c, *r, e == cudaErrorMemoryAllocation ? STEREO_E_NOMEM : STEREO_E_CUDA);
+            cudaGetLastError();
+            c->cv_done.notify_all();
+            continue;
+        }
+        for (Request* r : iter.reqs) {
+            if (!r->resample_now) finish(c, *r, STEREO_OK);
+        }
+        std::vector<Request*> host;
+        for (Request* r : seed.reqs) host.push_back(r);
+        for (Request* r : iter.reqs)
+            if (r->resample_now) host.push_back(r);
+        for (Request* r : host) {
+            r->state = Q_HOST;
+            c->host_busy++;
+            const bool is_seed = r->it == 0;
+            c->pool.push([c, r, is_seed] {
+                int rc = is_seed ? host_after_seed(c, *r) : host_after_iter(*r);
+                std::lock_guard<std::mutex> g2(c->mu);
+                c->host_busy--;
+                if (rc != STEREO_OK) finish(c, *r, rc);
+                else r->state = Q_ITER_READY;
+                c->cv_sched.notify_all();
+                c->cv_done.notify_all();
+            });
+        }
+        c->cv_done.notify_all();
+    }
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void stereo_default_config(stereo_config* cfg) {
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->device = 0;
+    cfg->mem_budget_bytes = (size_t)4 << 30;
+    cfg->max_slots = 1;
+    cfg->max_queue = 64;
+    cfg->t_lo = 4;
+    cfg->t_hi = 8;
+    cfg->t_grad = 8;
+    cfg->t_fast = 20;
+    cfg->kp_per_bin = 4;
+    cfg->uniq_margin = 2;
+    cfg->host_threads = 1;
+}
+
+int stereo_create(const stereo_config* cfg, stereo_ctx** out) {
+    if (!cfg || !out) return STEREO_E_INVAL;
+    if (!valid_params(*cfg) || cfg->max_slots < 1 || cfg->max_queue < 0) return STEREO_E_INVAL;
+    *out = nullptr;
+    if (cudaSetDevice(cfg->device) != cudaSuccess) return STEREO_E_CUDA;
+    stereo_ctx* c = new stereo_ctx();
+    c->cfg = *cfg;
+    if (c->cfg.mem_budget_bytes == 0) c->cfg.mem_budget_bytes = (size_t)4 << 30;
+    c->prm = Params{cfg->t_lo, cfg->t_hi, cfg->t_grad, cfg->t_fast, cfg->kp_per_bin, cfg->uniq_margin};
+    c->K = cfg->kp_per_bin;
+    if (cfg->stream) {
+        c->stream = (cudaStream_t)cfg->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return STEREO_E_CUDA;
+        }
+        c->own_stream = true;
+    }
+    if (cfg->arena) {
+        c->arena_base = (char*)cfg->arena;
+    } else {
+        if (cudaMalloc((void**)&c->arena_base, c->cfg.mem_budget_bytes) != cudaSuccess) {
+            if (c->own_stream) cudaStreamDestroy(c->stream);
+            delete c;
+            return STEREO_E_NOMEM;
+        }
+        c->own_arena = true;
+    }
+    c->arena.init(c->arena_base, c->cfg.mem_budget_bytes);
+    cudaEventCreateWithFlags(&c->ev, cudaEventBlockingSync | cudaEventDisableTiming);
+    c->pool.start(std::max(1, cfg->host_threads));
+    c->sched = std::thread(scheduler, c);
+    *out = c;
+    return STEREO_OK;
+}
+
+int stereo_submit(stereo_ctx* c, int stream_id, const uint8_t* left, const uint8_t* right, int w, int h,
+                  int dmax, int iters, int cell, uint64_t* ticket_out) {
+    if (!c || !left || !right || !ticket_out) return STEREO_E_INVAL;
+    if (!valid_size(w, h) || dmax < 1 || dmax > 256 || iters < 1 || cell < 1) return STEREO_E_INVAL;
+    Request* r = new Request();
+    r->stream_id = stream_id;
+    r->W = w;
+    r->H = h;
+    r->dmax = dmax;
+    r->iters = iters;
+    r->cell = cell;
+    int sz_min = iters >= 2 ? std::max(1, cell >> (iters - 2)) : 0;
+    r->ncell_max = iters >= 2 ? cells_of(w, h, sz_min) : 1;
+    r->tiles = ((w + kRasterTile - 1) / kRasterTile) * ((h + kRasterTile - 1) / kRasterTile);
+    const size_t need = block_bytes(*r, c->K);
+    if (need > c->cfg.mem_budget_bytes) {
+        delete r;
+        return STEREO_E_NOMEM;
+    }
+    const size_t N = (size_t)w * h;
+    cudaPointerAttributes at{};
+    bool dev_in = cudaPointerGetAttributes(&at, left) == cudaSuccess &&
+                  (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    std::unique_lock<std::mutex> g(c->mu);
+    if ((int)c->queue.size() >= c->cfg.max_queue && (int)c->active.size() >= c->cfg.max_slots) {
+        g.unlock();
+        delete r;
+        return STEREO_E_BUSY;
+    }
+    if (dev_in) {
+        r->in_dev = (uint8_t*)c->arena.alloc(2 * N);
+        if (!r->in_dev) {
+            g.unlock();
+            delete r;
+            return STEREO_E_BUSY;
+        }
+        g.unlock();
+        cudaMemcpyAsync(r->in_dev, left, N, cudaMemcpyDeviceToDevice, c->stream);
+        cudaMemcpyAsync(r->in_dev + N, right, N, cudaMemcpyDeviceToDevice, c->stream);
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            std::lock_guard<std::mutex> g2(c->mu);
+            c->arena.release(r->in_dev);
+            delete r;
+            return STEREO_E_CUDA;
+        }
+        g.lock();
+    } else {
+        g.unlock();
+        if (!r->in_host.ensure(2 * N)) {
+            delete r;
+            return STEREO_E_NOMEM;
+        }
+        std::memcpy(r->in_host.p, left, N);
+        std::memcpy((char*)r->in_host.p + N, right, N);
+        g.lock();
+    }
+    r->ticket = c->next_ticket++;
+    r->t_submit = now_ms();
+    c->reqs[r->ticket] = r;
+    c->queue.push_back(r);
+    *ticket_out = r->ticket;
+    g.unlock();
+    c->cv_sched.notify_all();
+    return STEREO_OK;
+}
+
+int stereo_poll(stereo_ctx* c, uint64_t ticket, stereo_result* out, int timeout_us) {
+    if (!c || !out) return STEREO_E_INVAL;
+    std::unique_lock<std::mutex> g(c->mu);
+    auto it = c->reqs.find(ticket);
+    if (it == c->reqs.end()) return STEREO_E_NOTFOUND;
+    Request* r = it->second;
+    auto ready = [r] { return r->state == Q_DONE || r->state == Q_FAILED; };
+    if (!ready()) {
+        if (timeout_us == 0) return STEREO_E_PENDING;
+        if (timeout_us < 0) c->cv_done.wait(g, ready);
+        else if (!c->cv_done.wait_for(g, std::chrono::microseconds(timeout_us), ready)) return STEREO_E_PENDING;
+    }
+    std::memset(out, 0, sizeof(*out));
+    out->status = r->status;
+    out->w = r->W;
+    out->h = r->H;
+    out->iters = r->iters;
+    out->latency_ms = r->t_done - r->t_submit;
+    out->host_mesh_ms = r->mesh_ms;
+    if (r->state == Q_DONE) {
+        out->disparity = r->dev.Df;
+        out->cost = r->dev.Cf;
+        out->mask = r->dev.mask;
+        out->planeidx = r->dev.planeidx;
+        out->n_support = r->n_support.data();
+        out->n_tri = r->n_tri.data();
+        out->support = r->trace.data();
+    }
+    return r->status;
+}
+
+int stereo_release(stereo_ctx* c, uint64_t ticket) {
+    if (!c) return STEREO_E_INVAL;
+    std::unique_lock<std::mutex> g(c->mu);
+    auto it = c->reqs.find(ticket);
+    if (it == c->reqs.end()) return STEREO_E_NOTFOUND;
+    Request* r = it->second;
+    if (r->state != Q_DONE && r->state != Q_FAILED) return STEREO_E_PENDING;
+    c->reqs.erase(it);
+    c->active.erase(std::remove(c->active.begin(), c->active.end(), r), c->active.end());
+    c->arena.release(r->block);
+    c->arena.release(r->tri_block);
+    c->arena.release(r->in_dev);
+    g.unlock();
+    r->in_host.free();
+    r->st_tri.free();
+    r->st_kp.free();
+    r->st_cells.free();
+    delete r;
+    c->cv_sched.notify_all();
+    return STEREO_OK;
+}
+
+int stereo_get_stats(stereo_ctx* c, stereo_stats* out) {
+    if (!c || !out) return STEREO_E_INVAL;
+    std::lock_guard<std::mutex> g(c->mu);
+    *out = c->stats;
+    return STEREO_OK;
+}
+
+void stereo_destroy(stereo_ctx* c) {
+    if (!c) return;
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        for (Request* r : c->queue) {
+            finish(c, *r, STEREO_E_INTERNAL);
+        }
+        c->queue.clear();
+        c->stop = true;
+    }
+    c->cv_sched.notify_all();
+    c->sched.join();
+    c->pool.stop();
+    cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->reqs) {
+        Request* r = kv.second;
+        r->in_host.free();
+        r->st_tri.free();
+        r->st_kp.free();
+        r->st_cells.free();
+        delete r;
+    }
+    c->reqs.clear();
+    c->desc_host.free();
+    if (c->desc_dev) cudaFree(c->desc_dev);
+    if (c->own_arena) cudaFree(c->arena_base);
+    if (c->ev) cudaEventDestroy(c->ev);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+// ---------------------------------------------------------------- stage entry points
+static int to_rc(cudaError_t e) { return e == cudaSuccess ? STEREO_OK : STEREO_E_CUDA; }
+
+static PairBatch single(const PairDev& p, WorkKind k) {
+    PairBatch b{};
+    b.pd = nullptr;
+    b.one = p;
+    b.npairs = 1;
+    b.total = work_items(k, p);
+    return b;
+}
+
+int stereo_census(const uint8_t* left, const uint8_t* right, int w, int h, int t_grad, uint32_t* cL,
+                  uint32_t* cR, uint32_t* omega, void* stream) {
+    if (!left || !valid_size(w, h) || t_grad < 0 || (cR && !right)) return STEREO_E_INVAL;
+    PairDev p{};
+    p.L = left;
+    p.R = right ? right : left;
+    p.cL = cL;
+    p.cR = cR;
+    p.omega = omega;
+    p.W = w;
+    p.H = h;
+    Params prm{0, 0, t_grad, 0, 1, 0};
+    return to_rc(launch_census(single(p, WK_CENSUS), prm, (cudaStream_t)stream));
+}
+
+int stereo_fast(const uint8_t* left, int w, int h, int t_fast, int K, int16_t* scratch, int32_t* out_uv,
+                void* stream) {
+    if (!left || !scratch || !out_uv || !valid_size(w, h) || t_fast < 0 || K < 1 || K > kMaxK) return STEREO_E_INVAL;
+    PairDev p{};
+    p.L = left;
+    p.fast_score = scratch;
+    p.kp_uv = out_uv;
+    p.W = w;
+    p.H = h;
+    p.K = K;
+    Params prm{0, 0, 0, t_fast, K, 0};
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_fast_score(single(p, WK_FAST_SCORE), prm, s);
+    if (e == cudaSuccess) e = launch_fast_bins(single(p, WK_FAST_BINS), prm, s);
+    return to_rc(e);
+}
+
+int stereo_epipolar_match(const uint32_t* cL, const uint32_t* cR, int w, int h, const int32_t* q_uv, int n,
+                          int dmax, int t_lo, int margin, int32_t* out_d, void* stream) {
+    if (!cL || !cR || (n > 0 && (!q_uv || !out_d)) || !valid_size(w, h) || n < 0 || dmax < 1 || dmax > 256 ||
+        t_lo < 0 || margin < 0)
+        return STEREO_E_INVAL;
+    Params prm{t_lo, 0, 0, 0, 1, margin};
+    return to_rc(launch_match_list(cL, cR, w, h, q_uv, n, dmax, prm, out_d, (cudaStream_t)stream));
+}
+
+int stereo_delaunay(const int32_t* uv, int n, int32_t* tri, int cap) {
+    if (n < 0 || (n > 0 && !uv) || cap < 0 || (cap > 0 && !tri)) return STEREO_E_INVAL;
+    for (int i = 0; i < n; i++) {
+        if (uv[2 * i] < 0 || uv[2 * i + 1] < 0 || uv[2 * i] > 16383 || uv[2 * i + 1] > 16383) return STEREO_E_INVAL;
+        if (i > 0) {
+            const int a = uv[2 * i - 1], b = uv[2 * i + 1];
+            if (b < a || (b == a && uv[2 * i] <= uv[2 * i - 2])) return STEREO_E_INVAL;  // not canonical
+        }
+    }
+    return delaunay(uv, n, tri, cap);
+}
+
+int stereo_planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float* abc) {
+    if (T < 0 || (T > 0 && (!uv || !d || !tri || !abc))) return STEREO_E_INVAL;
+    planes(uv, d, tri, T, abc);
+    return STEREO_OK;
+}
+
+size_t stereo_raster_scratch_bytes(const int32_t* tri_uv, int T, int w, int h) {
+    if (!valid_size(w, h) || T < 0) return 0;
+    const size_t tiles = (size_t)((w + kRasterTile - 1) / kRasterTile) * ((h + kRasterTile - 1) / kRasterTile);
+    const long long e = T > 0 && tri_uv ? raster_bin_entries(tri_uv, T, w, h) : 0;
+    return align_up(4 * tiles, 256) + align_up(4 * (tiles + 1), 256) + align_up(4 * (size_t)e + 4, 256);
+}
+
+int stereo_raster(const int32_t* tri_uv, int T, int w, int h, int32_t* planeidx, void* scratch,
+                  size_t scratch_bytes, void* stream) {
+    if (!valid_size(w, h) || T < 0 || (T > 0 && !tri_uv) || !planeidx || !scratch) return STEREO_E_INVAL;
+    PairDev p{};
+    p.W = w;
+    p.H = h;
+    p.T = T;
+    p.tri_uv = tri_uv;
+    p.planeidx = planeidx;
+    p.tiles_x = (w + kRasterTile - 1) / kRasterTile;
+    p.tiles_y = (h + kRasterTile - 1) / kRasterTile;
+    const size_t tiles = (size_t)p.tiles_x * p.tiles_y;
+    const size_t fixed = align_up(4 * tiles, 256) + align_up(4 * (tiles + 1), 256);
+    if (scratch_bytes < fixed + 4) return STEREO_E_CAP;
+    char* sp = (char*)scratch;
+    p.tile_cnt = (int32_t*)sp;
+    p.tile_off = (int32_t*)(sp + align_up(4 * tiles, 256));
+    p.tile_list = (int32_t*)(sp + fixed);
+    p.tile_cap = (int)std::min<size_t>((scratch_bytes - fixed) / 4, 0x7fffffff);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(p.tile_cnt, 0, 4 * tiles, s);
+    if (e == cudaSuccess) e = launch_raster_count(single(p, WK_TRI), s);
+    if (e == cudaSuccess) e = launch_raster_scan(single(p, WK_SCAN), s);
+    if (e == cudaSuccess) e = launch_raster_fill(single(p, WK_TRI), s);
+    if (e == cudaSuccess) e = launch_raster_pixels(single(p, WK_RASTER), s);
+    return to_rc(e);
+}
+
+int stereo_validate(const uint32_t* cL, const uint32_t* cR, const uint32_t* omega, const int32_t* planeidx,
+                    const float* abc, int w, int h, int sz, int t_lo, int t_hi, int first_pass, float* D_f,
+                    uint8_t* C_f, uint8_t* mask, uint32_t* cg_key, uint32_t* cb_key, void* stream) {
+    if (!cL || !cR || !omega || !planeidx || !abc || !D_f || !C_f || !valid_size(w, h) || sz < 1 ||
+        !(0 <= t_lo && t_lo <= t_hi && t_hi < 24) || ((cg_key == nullptr) != (cb_key == nullptr)))
+        return STEREO_E_INVAL;
+    PairDev p{};
+    p.cL = (uint32_t*)cL;
+    p.cR = (uint32_t*)cR;
+    p.omega = (uint32_t*)omega;
+    p.planeidx = (int32_t*)planeidx;
+    p.abc = abc;
+    p.W = w;
+    p.H = h;
+    p.sz = sz;
+    p.Wc = (w + sz - 1) / sz;
+    p.Hc = (h + sz - 1) / sz;
+    p.first_pass = first_pass ? 1 : 0;
+    p.Df = D_f;
+    p.Cf = C_f;
+    p.mask = mask;
+    p.cg_key = cg_key;
+    p.cb_key = cb_key;
+    Params prm{t_lo, t_hi, 0, 0, 1, 0};
+    return to_rc(launch_validate(single(p, WK_VALIDATE), prm, (cudaStream_t)stream));
+}
+
+int stereo_resample_match(const uint32_t* cg_key, const uint32_t* cb_key, int ncells, const int32_t* planeidx,
+                          const float* abc, const uint32_t* cL, const uint32_t* cR, int w, int h, int dmax,
+                          int t_lo, int margin, float* cg_d, int32_t* x_d, void* stream) {
+    if (!cg_key || !cb_key || ncells < 0 || !planeidx || !abc || !cL || !cR || !valid_size(w, h) || dmax < 1 ||
+        dmax > 256 || !cg_d || !x_d || t_lo < 0 || margin < 0)
+        return STEREO_E_INVAL;
+    PairDev p{};
+    p.cg_key = (uint32_t*)cg_key;
+    p.cb_key = (uint32_t*)cb_key;
+    p.planeidx = (int32_t*)planeidx;
+    p.abc = abc;
+    p.cL = (uint32_t*)cL;
+    p.cR = (uint32_t*)cR;
+    p.W = w;
+    p.H = h;
+    p.dmax = dmax;
+    p.Wc = ncells;
+    p.Hc = 1;
+    p.cg_d = cg_d;
+    p.x_d = x_d;
+    Params prm{t_lo, 0, 0, 0, 1, margin};
+    return to_rc(launch_resample(single(p, WK_RESAMPLE), prm, (cudaStream_t)stream));
+}
+
+}  // extern "C"

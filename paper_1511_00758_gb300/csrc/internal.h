@@ -1,0 +1,95 @@
+// Internal declarations shared by the kernels and the host engine of libstereo.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace stereo {
+
+constexpr int kFastBins = 120;          // 12 x 10 spatial bins (Sec. III-A)
+constexpr int kFastBinsX = 12;
+constexpr int kFastBinsY = 10;
+constexpr int kMaxK = 32;               // keypoints per bin, upper bound
+constexpr int kRasterTile = 16;         // raster bin edge in pixels
+constexpr uint32_t kNoKey = 0xFFFFFFFFu;
+constexpr uint32_t kIdxMask = (1u << 27) - 1;
+
+// Device buffers and sizes of one frame pair.  Every kernel reads its pair's
+// descriptor from a PairBatch, so one launch can cover many pairs.
+struct PairDev {
+    const uint8_t* L;
+    const uint8_t* R;
+    uint32_t* cL;
+    uint32_t* cR;
+    uint32_t* omega;          // H * ceil(W/32) bit words
+    int16_t* fast_score;      // W*H
+    int32_t* kp_uv;           // 120*K (u, v) slots
+    int32_t* kp_d;            // 120*K matches
+    const int32_t* tri_uv;    // T * 6
+    const float* abc;         // T * 3
+    int32_t* tile_cnt;        // tiles (count, then cursor)
+    int32_t* tile_off;        // tiles + 1
+    int32_t* tile_list;       // sum of bbox tiles
+    int tile_cap;             // entries tile_list can hold
+    int32_t* planeidx;        // W*H
+    float* Df;                // W*H
+    uint8_t* Cf;              // W*H
+    uint8_t* mask;            // W*H or null
+    uint32_t* cg_key;         // cells
+    uint32_t* cb_key;         // cells
+    float* cg_d;              // cells
+    int32_t* x_d;             // cells
+    int W, H, dmax;
+    int T;                    // triangles
+    int sz, Wc, Hc;           // current occupancy grid
+    int tiles_x, tiles_y;     // raster bins
+    int first_pass;
+    int K;                    // keypoints per bin
+};
+
+// One launch's pairs: either a single descriptor by value (pd == nullptr)
+// or a device array with a prefix of work items per pair.
+struct PairBatch {
+    const PairDev* pd;        // device array [npairs], or null
+    const int* work_off;      // device array [npairs + 1], or null
+    int npairs;
+    int total;                // work items in this launch
+    PairDev one;
+};
+
+struct Params {
+    int t_lo, t_hi, t_grad, t_fast, K, margin;
+};
+
+// Work items per pair for each kernel kind.
+enum WorkKind { WK_CENSUS = 0, WK_FAST_SCORE, WK_FAST_BINS, WK_MATCH_KP, WK_TRI, WK_SCAN,
+                WK_RASTER, WK_VALIDATE, WK_RESAMPLE, WK_COUNT };
+int work_items(WorkKind k, const PairDev& p);
+
+// Kernel launchers (async on stream).  grid_cap limits persistent grids.
+cudaError_t launch_census(const PairBatch& b, const Params& prm, cudaStream_t s);
+cudaError_t launch_fast_score(const PairBatch& b, const Params& prm, cudaStream_t s);
+cudaError_t launch_fast_bins(const PairBatch& b, const Params& prm, cudaStream_t s);
+cudaError_t launch_match_kp(const PairBatch& b, const Params& prm, cudaStream_t s);
+cudaError_t launch_raster_count(const PairBatch& b, cudaStream_t s);
+cudaError_t launch_raster_scan(const PairBatch& b, cudaStream_t s);
+cudaError_t launch_raster_fill(const PairBatch& b, cudaStream_t s);
+cudaError_t launch_raster_pixels(const PairBatch& b, cudaStream_t s);
+cudaError_t launch_validate(const PairBatch& b, const Params& prm, cudaStream_t s);
+cudaError_t launch_resample(const PairBatch& b, const Params& prm, cudaStream_t s);
+cudaError_t launch_fill_u32(uint32_t* p, uint32_t value, size_t n, cudaStream_t s);
+cudaError_t launch_match_list(const uint32_t* cL, const uint32_t* cR, int W, int H,
+                              const int32_t* q, int n, int dmax, const Params& prm,
+                              int32_t* out, cudaStream_t s);
+
+int sm_count();
+
+// Host mesh step (mesh.cpp).
+int delaunay(const int32_t* uv, int n, int32_t* tri, int cap);
+void planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float* abc);
+// Sum over triangles of the raster bins each triangle's bounding box touches.
+long long raster_bin_entries(const int32_t* tri_uv, int T, int W, int H);
+
+}  // namespace stereo

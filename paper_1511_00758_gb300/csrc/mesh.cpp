@@ -1,0 +1,250 @@
+// Host mesh step: Delaunay triangulation of the support points and the
+// disparity plane of every triangle (Sec. III-A DelaunayTriangulation,
+// Sec. III-B "solving a linear system", Eq. 3).
+//
+// Triangulation: Guibas-Stolfi divide and conquer on a quad-edge structure
+// (Guibas & Stolfi, ACM TOG 1985) with exact int64 predicates.  Cocircular
+// ties resolve by symbolic perturbation of the lifted coordinate u^2 + v^2
+// (Edelsbrunner & Muecke 1990): a point of smaller canonical index (support
+// points sorted by (v, u)) carries a larger perturbation.  The perturbed
+// point set is in general position, so its Delaunay triangulation is unique
+// and any correct algorithm returns it.
+//
+// Compiled with -ffp-contract=off: the plane coefficients are a fixed fp64
+// expression rounded to fp32, and contraction would change their bits.
+#include <algorithm>
+#include <cstdint>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+namespace stereo {
+namespace {
+
+struct Mesh {
+    const int32_t* P;            // (u, v) of canonical index i at P[2i], P[2i+1]
+    std::vector<int> nxt;        // onext of directed edge e (4 per quad edge)
+    std::vector<int> org;        // origin vertex of primal edges
+    std::vector<uint8_t> dead;   // per quad edge
+
+    static int rot(int e) { return (e & ~3) | ((e + 1) & 3); }
+    static int invrot(int e) { return (e & ~3) | ((e + 3) & 3); }
+    static int sym(int e) { return e ^ 2; }
+    int onext(int e) const { return nxt[e]; }
+    int oprev(int e) const { return rot(nxt[rot(e)]); }
+    int lnext(int e) const { return rot(nxt[invrot(e)]); }
+    int rprev(int e) const { return nxt[sym(e)]; }
+    int dest(int e) const { return org[sym(e)]; }
+
+    int64_t orient(int a, int b, int c) const {
+        const int64_t ax = P[2 * a], ay = P[2 * a + 1];
+        const int64_t bx = P[2 * b], by = P[2 * b + 1];
+        const int64_t cx = P[2 * c], cy = P[2 * c + 1];
+        return (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+    }
+    bool ccw(int a, int b, int c) const { return orient(a, b, c) > 0; }
+
+    // d strictly inside the circle of the positively oriented (a, b, c) in the
+    // perturbed configuration.  At an exact tie the sign is that of the
+    // cofactor of the smallest-index point's lifted entry in the 4x4
+    // determinant with rows (u, v, u^2 + v^2, 1).
+    bool incircle(int a, int b, int c, int d) const {
+        if (d == a || d == b || d == c) return false;
+        const int64_t dx = P[2 * d], dy = P[2 * d + 1];
+        const int64_t ax = P[2 * a] - dx, ay = P[2 * a + 1] - dy;
+        const int64_t bx = P[2 * b] - dx, by = P[2 * b + 1] - dy;
+        const int64_t cx = P[2 * c] - dx, cy = P[2 * c + 1] - dy;
+        const int64_t la = ax * ax + ay * ay, lb = bx * bx + by * by, lc = cx * cx + cy * cy;
+        const int64_t det = la * (bx * cy - by * cx) - lb * (ax * cy - ay * cx) + lc * (ax * by - ay * bx);
+        if (det != 0) return det > 0;
+        // cofactors of the lifted column for rows a, b, c, d
+        std::pair<int, int64_t> terms[4] = {{a, orient(b, c, d)}, {b, -orient(a, c, d)},
+                                            {c, orient(a, b, d)}, {d, -orient(a, b, c)}};
+        std::sort(terms, terms + 4, [](const std::pair<int, int64_t>& x, const std::pair<int, int64_t>& y) {
+            return x.first < y.first;
+        });
+        for (const auto& t : terms)
+            if (t.second != 0) return t.second > 0;
+        return false;
+    }
+
+    int make_edge(int a, int b) {
+        const int e = (int)nxt.size();
+        nxt.resize(e + 4);
+        org.resize(e + 4, -1);
+        dead.push_back(0);
+        nxt[e] = e;
+        nxt[e + 1] = e + 3;
+        nxt[e + 2] = e + 2;
+        nxt[e + 3] = e + 1;
+        org[e] = a;
+        org[e + 2] = b;
+        return e;
+    }
+    void splice(int a, int b) {
+        const int al = rot(nxt[a]), be = rot(nxt[b]);
+        std::swap(nxt[a], nxt[b]);
+        std::swap(nxt[al], nxt[be]);
+    }
+    int connect(int a, int b) {
+        const int e = make_edge(dest(a), org[b]);
+        splice(e, lnext(a));
+        splice(sym(e), b);
+        return e;
+    }
+    void remove(int e) {
+        splice(e, oprev(e));
+        splice(sym(e), oprev(sym(e)));
+        dead[e >> 2] = 1;
+    }
+    bool rightof(int x, int e) const { return ccw(x, dest(e), org[e]); }
+    bool leftof(int x, int e) const { return ccw(x, org[e], dest(e)); }
+
+    // s: vertex ids sorted lexicographically by (u, v).  Returns the
+    // counter-clockwise hull edge out of the leftmost vertex and the
+    // clockwise hull edge out of the rightmost one.
+    std::pair<int, int> build(const int* s, int n) {
+        if (n == 2) {
+            const int a = make_edge(s[0], s[1]);
+            return {a, sym(a)};
+        }
+        if (n == 3) {
+            const int a = make_edge(s[0], s[1]);
+            const int b = make_edge(s[1], s[2]);
+            splice(sym(a), b);
+            if (ccw(s[0], s[1], s[2])) {
+                connect(b, a);
+                return {a, sym(b)};
+            }
+            if (ccw(s[0], s[2], s[1])) {
+                const int c = connect(b, a);
+                return {sym(c), c};
+            }
+            return {a, sym(b)};
+        }
+        const int h = n / 2;
+        auto L = build(s, h);
+        auto R = build(s + h, n - h);
+        int ldo = L.first, ldi = L.second, rdi = R.first, rdo = R.second;
+        // lower common tangent
+        for (;;) {
+            if (leftof(org[rdi], ldi)) ldi = lnext(ldi);
+            else if (rightof(org[ldi], rdi)) rdi = rprev(rdi);
+            else break;
+        }
+        int basel = connect(sym(rdi), ldi);
+        if (org[ldi] == org[ldo]) ldo = sym(basel);
+        if (org[rdi] == org[rdo]) rdo = basel;
+        // merge upwards
+        for (;;) {
+            int lc = onext(sym(basel));
+            if (rightof(dest(lc), basel)) {
+                while (incircle(dest(basel), org[basel], dest(lc), dest(onext(lc)))) {
+                    const int t = onext(lc);
+                    remove(lc);
+                    lc = t;
+                }
+            }
+            int rc = oprev(basel);
+            if (rightof(dest(rc), basel)) {
+                while (incircle(dest(basel), org[basel], dest(rc), dest(oprev(rc)))) {
+                    const int t = oprev(rc);
+                    remove(rc);
+                    rc = t;
+                }
+            }
+            const bool lv = rightof(dest(lc), basel), rv = rightof(dest(rc), basel);
+            if (!lv && !rv) break;
+            if (!lv || (rv && incircle(dest(lc), org[lc], org[rc], dest(rc))))
+                basel = connect(rc, sym(basel));
+            else
+                basel = connect(sym(basel), sym(lc));
+        }
+        return {ldo, rdo};
+    }
+};
+
+}  // namespace
+
+int delaunay(const int32_t* uv, int n, int32_t* tri, int cap) {
+    if (n < 3) return 0;
+    Mesh m;
+    m.P = uv;
+    m.nxt.reserve((size_t)12 * n);
+    m.org.reserve((size_t)12 * n);
+    m.dead.reserve((size_t)3 * n);
+    std::vector<int> s(n);
+    for (int i = 0; i < n; i++) s[i] = i;
+    std::sort(s.begin(), s.end(), [uv](int a, int b) {
+        if (uv[2 * a] != uv[2 * b]) return uv[2 * a] < uv[2 * b];
+        return uv[2 * a + 1] < uv[2 * b + 1];
+    });
+    m.build(s.data(), n);
+    std::vector<int32_t> out;
+    out.reserve((size_t)6 * n);
+    const int ne = (int)m.nxt.size();
+    for (int e = 0; e < ne; e += 2) {
+        if (m.dead[e >> 2]) continue;
+        const int a = m.org[e], b = m.dest(e);
+        const int e2 = m.lnext(e);
+        const int c = m.dest(e2);
+        if (m.lnext(m.lnext(e2)) != e) continue;
+        if (!(a < b && a < c)) continue;
+        if (!m.ccw(a, b, c)) continue;
+        int t3[3] = {a, b, c};
+        std::sort(t3, t3 + 3);
+        out.insert(out.end(), t3, t3 + 3);
+    }
+    const int T = (int)(out.size() / 3);
+    if (T > cap) return -9;  // STEREO_E_CAP
+    std::vector<int> order(T);
+    for (int i = 0; i < T; i++) order[i] = i;
+    std::sort(order.begin(), order.end(), [&out](int x, int y) {
+        for (int k = 0; k < 3; k++)
+            if (out[3 * x + k] != out[3 * y + k]) return out[3 * x + k] < out[3 * y + k];
+        return false;
+    });
+    for (int i = 0; i < T; i++)
+        for (int k = 0; k < 3; k++) tri[3 * i + k] = out[3 * order[i] + k];
+    return T;
+}
+
+// Disparity plane d = a u + b v + c through the three vertices (Eq. 3), by
+// Cramer's rule in fp64 with the vertices in index order, rounded to fp32.
+void planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float* abc) {
+    for (int t = 0; t < T; t++) {
+        const int i0 = tri[3 * t], i1 = tri[3 * t + 1], i2 = tri[3 * t + 2];
+        const int64_t u0 = uv[2 * i0], v0 = uv[2 * i0 + 1];
+        const int64_t u1 = uv[2 * i1], v1 = uv[2 * i1 + 1];
+        const int64_t u2 = uv[2 * i2], v2 = uv[2 * i2 + 1];
+        const int64_t det = (u1 - u0) * (v2 - v0) - (u2 - u0) * (v1 - v0);
+        const double d0 = (double)d[i0];
+        const double e1 = (double)d[i1] - d0;
+        const double e2 = (double)d[i2] - d0;
+        const double na = e1 * (double)(v2 - v0) - e2 * (double)(v1 - v0);
+        const double nb = (double)(u1 - u0) * e2 - (double)(u2 - u0) * e1;
+        const double A = na / (double)det;
+        const double B = nb / (double)det;
+        const double C = d0 - A * (double)u0 - B * (double)v0;
+        abc[3 * t] = (float)A;
+        abc[3 * t + 1] = (float)B;
+        abc[3 * t + 2] = (float)C;
+    }
+}
+
+long long raster_bin_entries(const int32_t* q, int T, int W, int H) {
+    long long s = 0;
+    for (int t = 0; t < T; t++, q += 6) {
+        int x0 = std::min(q[0], std::min(q[2], q[4])), x1 = std::max(q[0], std::max(q[2], q[4]));
+        int y0 = std::min(q[1], std::min(q[3], q[5])), y1 = std::max(q[1], std::max(q[3], q[5]));
+        x0 = std::max(x0, 0);
+        y0 = std::max(y0, 0);
+        x1 = std::min(x1, W - 1);
+        y1 = std::min(y1, H - 1);
+        s += (long long)(x1 / kRasterTile - x0 / kRasterTile + 1) * (y1 / kRasterTile - y0 / kRasterTile + 1);
+    }
+    return s;
+}
+
+}  // namespace stereo

@@ -1,0 +1,309 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, stage by
+stage and end to end, on seeded synthetic pairs.  Integer outputs (census
+codes, Omega_I bits, keypoints, matches, plane-index maps, costs, masks, cell
+picks, support sets) must be bit-exact; interpolated fp32 disparities must
+agree within 1e-3 px (the design target, and what is observed, is equality)."""
+import numpy as np
+import pytest
+
+import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # collected on CPU machines, skipped there
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1511_00758_gb300 as S  # noqa: E402
+
+DEV = "cuda:0"
+TOL_D = 1e-3
+PRM = dict(t_lo=4, t_hi=8, t_grad=8, t_fast=20, kp_per_bin=4, uniq_margin=2)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    S.load()
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _sync():
+    torch.cuda.synchronize()
+
+
+def _gpu_census(L, R, t_grad=8):
+    H, W = L.shape
+    cL = torch.empty((H, W), dtype=torch.int32, device=DEV)
+    cR = torch.empty((H, W), dtype=torch.int32, device=DEV)
+    om = torch.empty((H, (W + 31) // 32), dtype=torch.int32, device=DEV)
+    S.census(_t(L), _t(R), W, H, t_grad, cL, cR, om)
+    _sync()
+    return cL, cR, om
+
+
+def _unpack_omega(om, W):
+    w = om.cpu().numpy().view(np.uint32)
+    bits = ((w[:, :, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(w.shape[0], -1)
+    return bits[:, :W].astype(np.uint8)
+
+
+SIZES = [(77, 45), (640, 480), (1242, 375), (33, 9), (5, 5)]
+
+
+@pytest.mark.parametrize("W,H", SIZES)
+def test_census_omega(oracle_mod, W, H):
+    rng = np.random.default_rng(W * 7 + H)
+    L = rng.integers(0, 256, (H, W), dtype=np.uint8)
+    R = np.clip(L.astype(int) + rng.integers(-20, 20, (H, W)), 0, 255).astype(np.uint8)
+    cL, cR, om = _gpu_census(L, R)
+    assert np.array_equal(cL.cpu().numpy().view(np.uint32), oracle_mod.census(L))
+    assert np.array_equal(cR.cpu().numpy().view(np.uint32), oracle_mod.census(R))
+    assert np.array_equal(_unpack_omega(om, W), oracle_mod.omega(L, 8))
+
+
+def _gpu_fast(L, t_fast=20, K=4):
+    H, W = L.shape
+    scratch = torch.empty((H, W), dtype=torch.int16, device=DEV)
+    out = torch.empty((120 * K, 2), dtype=torch.int32, device=DEV)
+    S.fast(_t(L), W, H, t_fast, K, scratch, out)
+    _sync()
+    o = out.cpu().numpy()
+    return o[o[:, 0] >= 0]
+
+
+@pytest.mark.parametrize("name", ["vga_polygons", "driving_1242x375"])
+def test_fast_bins_scene(oracle_mod, name):
+    p = scenes.config_pairs(name)[0]
+    assert np.array_equal(_gpu_fast(p.left), oracle_mod.fast_keypoints(p.left, 20, 4))
+
+
+@pytest.mark.parametrize("K,t_fast,W,H", [(1, 10, 200, 90), (7, 15, 333, 101), (32, 5, 96, 70), (4, 20, 12, 10)])
+def test_fast_bins_params(oracle_mod, K, t_fast, W, H):
+    rng = np.random.default_rng(K + W)
+    img = np.clip(scenes.value_noise(*np.meshgrid(np.arange(float(W)), np.arange(float(H))), 5 + K)
+                  + rng.normal(0, 8, (H, W)), 0, 255).astype(np.uint8)
+    assert np.array_equal(_gpu_fast(img, t_fast, K), oracle_mod.fast_keypoints(img, t_fast, K))
+
+
+@pytest.mark.parametrize("dmax,t_lo,margin", [(64, 4, 2), (128, 12, 1), (256, 24, 3), (1, 4, 2), (37, 6, 0)])
+def test_epipolar_match(oracle_mod, dmax, t_lo, margin):
+    p = scenes.config_pairs("driving_1242x375")[0]
+    H, W = p.left.shape
+    cL, cR, _ = _gpu_census(p.left, p.right)
+    rng = np.random.default_rng(dmax)
+    q = np.stack([rng.integers(-3, W + 3, 3000), rng.integers(-3, H + 3, 3000)], 1).astype(np.int32)
+    q[::50, 0] = -1
+    out = torch.empty(len(q), dtype=torch.int32, device=DEV)
+    S.epipolar_match(cL, cR, W, H, _t(q), len(q), dmax, t_lo, margin, out)
+    _sync()
+    want = oracle_mod.epipolar_match(oracle_mod.census(p.left), oracle_mod.census(p.right), q, dmax, t_lo, margin)
+    assert np.array_equal(out.cpu().numpy(), want)
+
+
+def _canon(P):
+    P = np.asarray(P, np.int64)
+    return np.ascontiguousarray(P[np.lexsort((P[:, 0], P[:, 1]))], dtype=np.int32)
+
+
+def _tri_uv(P, tri):
+    return np.ascontiguousarray(P[tri].reshape(-1, 6), dtype=np.int32)
+
+
+def _gpu_raster(P, tri, W, H):
+    tuv = _tri_uv(P, tri)
+    nbytes = S.raster_scratch_bytes(tuv, len(tri), W, H)
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=DEV)
+    pidx = torch.empty((H, W), dtype=torch.int32, device=DEV)
+    S.raster(_t(tuv) if len(tri) else None, len(tri), W, H, pidx, scratch, nbytes)
+    _sync()
+    return pidx.cpu().numpy()
+
+
+@pytest.mark.parametrize("seed,n,W,H", [(1, 40, 640, 480), (2, 2000, 300, 200), (3, 6000, 257, 131),
+                                        (4, 3, 50, 40), (5, 200, 1242, 375)])
+def test_raster(oracle_mod, seed, n, W, H):
+    rng = np.random.default_rng(seed)
+    P = _canon(np.unique(np.stack([rng.integers(0, W, n), rng.integers(0, H, n)], 1), axis=0))
+    tri = oracle_mod.delaunay(P)
+    assert np.array_equal(_gpu_raster(P, tri, W, H), oracle_mod.raster(P, tri, W, H))
+
+
+def test_raster_empty_and_lattice(oracle_mod):
+    W, H = 100, 60
+    assert (_gpu_raster(np.zeros((0, 2), np.int32), np.zeros((0, 3), np.int32), W, H) == -1).all()
+    P = _canon([(u, v) for v in range(0, H, 3) for u in range(0, W, 4)])
+    tri = oracle_mod.delaunay(P)
+    got = _gpu_raster(P, tri, W, H)
+    assert np.array_equal(got, oracle_mod.raster(P, tri, W, H))
+
+
+def _support_case(oracle_mod, p, n=400, seed=0):
+    """A realistic mesh: the oracle's first support set plus random extra points on the ground truth."""
+    H, W = p.left.shape
+    r = oracle_mod.run(p.left, p.right, p.dmax, 1, 16, **PRM)
+    S1 = r["support"][0]
+    rng = np.random.default_rng(seed)
+    extra = np.stack([rng.integers(0, W, n), rng.integers(0, H, n)], 1)
+    pts = {(int(u), int(v)): float(d) for u, v, d in S1}
+    for u, v in extra:
+        pts.setdefault((int(u), int(v)), float(np.float32(p.gt_disp[v, u] + rng.normal(0, 0.7))))
+    keys = sorted(pts, key=lambda t: (t[1], t[0]))
+    P = np.array(keys, np.int32)
+    D = np.array([pts[k] for k in keys], np.float32)
+    return P, D
+
+
+@pytest.mark.parametrize("name,sz,first", [("vga_polygons", 16, 1), ("driving_1242x375", 8, 0),
+                                           ("driving_1242x375", 1, 0), ("vga_polygons", 3, 0)])
+def test_validate(oracle_mod, name, sz, first):
+    p = scenes.config_pairs(name)[0]
+    H, W = p.left.shape
+    P, D = _support_case(oracle_mod, p)
+    tri = oracle_mod.delaunay(P)
+    abc = oracle_mod.planes(P, D, tri)
+    pidx = oracle_mod.raster(P, tri, W, H)
+    cL_o, cR_o, om_o = oracle_mod.census(p.left), oracle_mod.census(p.right), oracle_mod.omega(p.left)
+    rng = np.random.default_rng(sz)
+    Df0 = rng.uniform(0, 50, (H, W)).astype(np.float32)
+    Cf0 = rng.integers(0, 12, (H, W)).astype(np.uint8)
+    if first:
+        Df0[:] = 0
+        Cf0[:] = PRM["t_hi"]
+    Df_o, Cf_o = Df0.copy(), Cf0.copy()
+    ro = oracle_mod.validate(cL_o, cR_o, om_o, pidx, abc, sz, Df_o, Cf_o, PRM["t_lo"], PRM["t_hi"])
+
+    cL, cR, om = _gpu_census(p.left, p.right)
+    Df = _t(Df0 if not first else np.full((H, W), 7.0, np.float32))
+    Cf = _t(Cf0 if not first else np.full((H, W), 3, np.uint8))
+    mask = torch.empty((H, W), dtype=torch.uint8, device=DEV)
+    nc = ro["Wc"] * ro["Hc"]
+    cg = torch.full((nc,), -1, dtype=torch.int32, device=DEV)
+    cb = torch.full((nc,), -1, dtype=torch.int32, device=DEV)
+    S.validate(cL, cR, om, _t(pidx), _t(abc), W, H, sz, PRM["t_lo"], PRM["t_hi"], first, Df, Cf, mask, cg, cb)
+    _sync()
+    assert np.array_equal(mask.cpu().numpy(), ro["mask"])
+    assert np.array_equal(Cf.cpu().numpy(), Cf_o)
+    dd = Df.cpu().numpy()
+    assert np.abs(dd - Df_o).max() <= TOL_D
+    assert np.array_equal(dd.view(np.uint32), Df_o.view(np.uint32))
+    g = cg.cpu().numpy().view(np.uint32)
+    b = cb.cpu().numpy().view(np.uint32)
+    IDX = (1 << 27) - 1
+    assert np.array_equal(g != 0xFFFFFFFF, ro["cg_w"] == 1)
+    assert np.array_equal(b != 0xFFFFFFFF, ro["cb_w"] == 1)
+    wg = ro["cg_w"] == 1
+    assert np.array_equal((g[wg] & IDX) % W, ro["cg_uv"][wg, 0]) and np.array_equal((g[wg] & IDX) // W, ro["cg_uv"][wg, 1])
+    assert np.array_equal(g[wg] >> 27, ro["cg_cost"][wg])
+    wb = ro["cb_w"] == 1
+    assert np.array_equal((b[wb] & IDX) % W, ro["cb_uv"][wb, 0]) and np.array_equal((b[wb] & IDX) // W, ro["cb_uv"][wb, 1])
+    assert np.array_equal(24 - (b[wb] >> 27), ro["cb_cost"][wb])
+    assert wg.sum() > 10 and (wb.sum() > 10 or sz > 8)
+
+    # resample + match on the same cells
+    cgd = torch.empty(nc, dtype=torch.float32, device=DEV)
+    xd = torch.empty(nc, dtype=torch.int32, device=DEV)
+    dmax = p.dmax
+    S.resample_match(cg, cb, nc, _t(pidx), _t(abc), cL, cR, W, H, dmax, PRM["t_lo"], PRM["uniq_margin"], cgd, xd)
+    _sync()
+    cgd = cgd.cpu().numpy()
+    assert np.isnan(cgd[~wg]).all()
+    assert np.array_equal(cgd[wg].view(np.uint32), ro["cg_d"][wg].view(np.uint32))
+    want = np.full(nc, -1, np.int32)
+    if wb.any():
+        want[wb] = oracle_mod.epipolar_match(cL_o, cR_o, ro["cb_uv"][wb], dmax, PRM["t_lo"], PRM["uniq_margin"])
+    assert np.array_equal(xd.cpu().numpy(), want)
+
+
+def _run_ctx(pairs, max_slots=1, host_threads=1, budget=1 << 30):
+    with S.Context(mem_budget_bytes=budget, max_slots=max_slots, host_threads=host_threads, **PRM) as ctx:
+        tickets = [ctx.submit(_t(p.left), _t(p.right), p.left.shape[1], p.left.shape[0], p.dmax, p.iters, p.cell)
+                   for p in pairs]
+        outs = []
+        for t in tickets:
+            r = ctx.poll(t)
+            outs.append(ctx.result_tensors(r))
+            ctx.release(t)
+        return outs
+
+
+def _compare_run(oracle_mod, p, got):
+    want = oracle_mod.run(p.left, p.right, p.dmax, p.iters, p.cell, **PRM)
+    assert [len(s) for s in got["support"]] == [len(s) for s in want["support"]]
+    for a, b in zip(got["support"], want["support"]):
+        assert np.array_equal(a[:, :2], b[:, :2])
+        assert np.array_equal(a[:, 2].astype(np.float32).view(np.uint32), b[:, 2].astype(np.float32).view(np.uint32))
+    assert list(got["n_tri"]) == list(want["n_tri"])
+    assert np.array_equal(got["planeidx"].cpu().numpy(), want["planeidx"])
+    assert np.array_equal(got["mask"].cpu().numpy(), want["mask"])
+    assert np.array_equal(got["C_f"].cpu().numpy(), want["C_f"])
+    dd = got["D_f"].cpu().numpy()
+    assert np.abs(dd - want["D_f"]).max() <= TOL_D
+    return want
+
+
+def test_end_to_end_vga_one_iteration(oracle_mod):
+    p = scenes.config_pairs("vga_polygons")[0]
+    want = _compare_run(oracle_mod, p, _run_ctx([p])[0])
+    assert (want["C_f"] < 8).mean() > 0.2
+
+
+def test_end_to_end_driving_full_size(oracle_mod):
+    """The 1242x375 driving workload at full size, 3 iterations, 8x8 cells."""
+    p = scenes.config_pairs("driving_1242x375")[0]
+    want = _compare_run(oracle_mod, p, _run_ctx([p])[0])
+    assert len(want["support"][2]) > len(want["support"][1]) > len(want["support"][0])
+
+
+@pytest.mark.parametrize("W,H,dmax,iters,cell", [(321, 123, 48, 4, 16), (97, 61, 16, 3, 1), (200, 100, 1, 2, 4)])
+def test_end_to_end_ragged(oracle_mod, W, H, dmax, iters, cell):
+    pr = scenes.make_pair("polygon", W, H, 99 + W, min(dmax, 64), iters, cell, n_poly=6, sigma=2.0)
+    pr.dmax = dmax
+    _compare_run(oracle_mod, pr, _run_ctx([pr])[0])
+
+
+def test_end_to_end_degenerate(oracle_mod):
+    # flat images: no corners, no Omega_I, no mesh; D_f = 0 and C_f = t_hi everywhere
+    flat = scenes.StereoPair(np.full((40, 70), 100, np.uint8), np.full((40, 70), 100, np.uint8),
+                             np.zeros((40, 70), np.float32), np.zeros((40, 70), bool), 32, 3, 8)
+    got = _run_ctx([flat])[0]
+    _compare_run(oracle_mod, flat, got)
+    assert (got["C_f"].cpu().numpy() == 8).all() and (got["D_f"].cpu().numpy() == 0).all()
+    tiny = scenes.StereoPair(np.random.default_rng(1).integers(0, 256, (5, 5), dtype=np.uint8),
+                             np.random.default_rng(2).integers(0, 256, (5, 5), dtype=np.uint8),
+                             np.zeros((5, 5), np.float32), np.zeros((5, 5), bool), 4, 2, 1)
+    _compare_run(oracle_mod, tiny, _run_ctx([tiny])[0])
+
+
+def test_batched_serving_matches_solo(oracle_mod):
+    """Continuous batching: results in a mixed batch equal solo results bit for bit."""
+    pairs = [scenes.make_pair("polygon", 320, 240, 500 + i, 64, 3, 16, n_poly=10) for i in range(3)]
+    pairs += [scenes.make_pair("driving", 400, 150, 600 + i, 96, 2, 8, n_box=10) for i in range(3)]
+    solo = [_run_ctx([p])[0] for p in pairs]
+    mixed = _run_ctx(pairs, max_slots=4, host_threads=3)
+    for a, b in zip(solo, mixed):
+        for k in ("D_f", "C_f", "mask", "planeidx"):
+            assert torch.equal(a[k], b[k]), k
+        for x, y in zip(a["support"], b["support"]):
+            assert np.array_equal(x, y)
+
+
+def test_host_input_pointers(oracle_mod):
+    p = scenes.config_pairs("vga_polygons")[0]
+    with S.Context(mem_budget_bytes=1 << 28, **PRM) as ctx:
+        t = ctx.submit(p.left, p.right, 640, 480, p.dmax, p.iters, p.cell)
+        got = ctx.result_tensors(ctx.poll(t))
+        ctx.release(t)
+    _compare_run(oracle_mod, p, got)
+
+
+def test_budget_errors():
+    with S.Context(mem_budget_bytes=1 << 22, **PRM) as ctx:
+        img = np.zeros((480, 640), np.uint8)
+        with pytest.raises(S.StereoError) as e:
+            ctx.submit(img, img, 640, 480, 64, 1, 16)
+        assert e.value.code == -2
+        with pytest.raises(S.StereoError) as e:
+            ctx.submit(img, img, 640, 480, 300, 1, 16)
+        assert e.value.code == -1
