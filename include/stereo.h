@@ -64,6 +64,8 @@ typedef struct {
     int uniq_margin;           /* epipolar uniqueness margin in census bits */
     int host_threads;          /* host triangulation workers (0 = 1) */
     void* stream;              /* cudaStream_t for all work (NULL = library creates one) */
+    int profile;               /* 1 = time every kernel launch with CUDA events on `stream`
+                                  and accumulate per-kind durations in stereo_stats */
 } stereo_config;
 
 /* Fill *cfg with the defaults: t_lo 4, t_hi 8, t_grad 8, t_fast 20,
@@ -112,14 +114,34 @@ int stereo_release(stereo_ctx* ctx, uint64_t ticket);
 /* Cancel queued work, wait for in-flight work, free everything. */
 void stereo_destroy(stereo_ctx* ctx);
 
-/* Counters of the context since creation: kernels launched, requests done,
- * pairs per launch summed (for the mean batch size). */
+/* Kernel kinds of the per-kind counters in stereo_stats. */
+#define STEREO_K_CENSUS 0        /* census + Omega_I */
+#define STEREO_K_FAST_SCORE 1    /* FAST-9 scores */
+#define STEREO_K_FAST_BINS 2     /* non-maximum suppression + per-bin top-K */
+#define STEREO_K_MATCH_KP 3      /* epipolar match of the keypoints */
+#define STEREO_K_RASTER_BIN 4    /* triangle-to-tile binning (count, scan, fill) */
+#define STEREO_K_RASTER 5        /* per-pixel triangle lookup */
+#define STEREO_K_VALIDATE 6      /* fused interpolate + cost + refine */
+#define STEREO_K_RESAMPLE 7      /* per-cell resample + epipolar match */
+#define STEREO_K_FILL 8          /* cell-record resets */
+#define STEREO_K_KINDS 9
+
+/* Counters of the context since creation.  kernel_launches counts every
+ * kernel the library launched; batched_pairs sums the pairs each launch
+ * covered (batched_pairs / kernel_launches = mean pairs per launch).  With
+ * profile = 1, kind_ms[k] holds the summed CUDA-event durations of kind k and
+ * kind_bytes[k] the algorithmic bytes those launches had to move (census:
+ * 2 B/px read + 8.125 B/px written; raster: 4 B/px written; validate:
+ * 13.125 B/px read (12.125 on a first pass) + 6 B/px written). */
 typedef struct {
     long long kernel_launches;
     long long requests_done;
     long long batched_pairs;
     long long gpu_rounds;
     double host_mesh_ms;
+    long long kind_launches[STEREO_K_KINDS];
+    double kind_ms[STEREO_K_KINDS];
+    double kind_bytes[STEREO_K_KINDS];
 } stereo_stats;
 int stereo_get_stats(stereo_ctx* ctx, stereo_stats* out);
 

@@ -34,7 +34,7 @@ class Config(ctypes.Structure):
                 ("max_slots", ctypes.c_int), ("max_queue", ctypes.c_int), ("t_lo", ctypes.c_int),
                 ("t_hi", ctypes.c_int), ("t_grad", ctypes.c_int), ("t_fast", ctypes.c_int),
                 ("kp_per_bin", ctypes.c_int), ("uniq_margin", ctypes.c_int), ("host_threads", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("profile", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -48,7 +48,11 @@ class Result(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_longlong), ("requests_done", ctypes.c_longlong),
                 ("batched_pairs", ctypes.c_longlong), ("gpu_rounds", ctypes.c_longlong),
-                ("host_mesh_ms", ctypes.c_double)]
+                ("host_mesh_ms", ctypes.c_double), ("kind_launches", ctypes.c_longlong * 9),
+                ("kind_ms", ctypes.c_double * 9), ("kind_bytes", ctypes.c_double * 9)]
+
+
+KINDS = ("census", "fast_score", "fast_bins", "match_kp", "raster_bin", "raster", "validate", "resample", "fill")
 
 
 _lib = None

@@ -34,6 +34,12 @@ double now_ms() {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) return e_;       \
+    } while (0)
+
 // ------------------------------------------------------------------ arena
 // First-fit sub-allocator over one device region (caller-provided, e.g. a
 // PyTorch tensor, or one cudaMalloc).  Not thread safe: the context mutex
@@ -275,6 +281,7 @@ struct stereo_ctx {
     void* desc_dev = nullptr;
     size_t desc_cap = 0;
     cudaEvent_t ev = nullptr;
+    std::vector<cudaEvent_t> ev_pool;  // timing events of profiled launches
     stereo_stats stats{};
 };
 
@@ -472,15 +479,76 @@ PairBatch batch_of(const Group& g, WorkKind k) {
     return b;
 }
 
-#define CK(x)                                   \
-    do {                                        \
-        cudaError_t e_ = (x);                   \
-        if (e_ != cudaSuccess) return e_;       \
-    } while (0)
+
+// Launch bookkeeping of one round: counters, algorithmic bytes and (when
+// profiling) CUDA events recorded on the launching stream around each launch.
+struct Launcher {
+    stereo_ctx* c;
+    cudaStream_t s;
+    stereo_stats delta{};
+    struct Timed {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Timed> timed;
+
+    cudaEvent_t event() {
+        if (!c->ev_pool.empty()) {
+            cudaEvent_t e = c->ev_pool.back();
+            c->ev_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    template <class F>
+    cudaError_t run(int kind, int npairs, double bytes, F&& f) {
+        cudaEvent_t a = nullptr;
+        if (c->cfg.profile) {
+            a = event();
+            CK(cudaEventRecord(a, s));
+        }
+        CK(f());
+        if (c->cfg.profile) {
+            cudaEvent_t b = event();
+            CK(cudaEventRecord(b, s));
+            timed.push_back({kind, a, b});
+        }
+        delta.kernel_launches++;
+        delta.kind_launches[kind]++;
+        delta.kind_bytes[kind] += bytes;
+        delta.batched_pairs += npairs;
+        return cudaSuccess;
+    }
+    // after the round's synchronisation
+    void collect() {
+        for (auto& t : timed) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) delta.kind_ms[t.kind] += ms;
+            c->ev_pool.push_back(t.a);
+            c->ev_pool.push_back(t.b);
+        }
+        timed.clear();
+    }
+};
+
+void add_stats(stereo_stats& to, const stereo_stats& d) {
+    to.kernel_launches += d.kernel_launches;
+    to.batched_pairs += d.batched_pairs;
+    to.gpu_rounds += d.gpu_rounds;
+    for (int k = 0; k < STEREO_K_KINDS; k++) {
+        to.kind_launches[k] += d.kind_launches[k];
+        to.kind_ms[k] += d.kind_ms[k];
+        to.kind_bytes[k] += d.kind_bytes[k];
+    }
+}
 
 // One GPU round for the seed group and the iteration group.
-cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter) {
+cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
     cudaStream_t s = c->stream;
+    double seed_px = 0, iter_px = 0, validate_bytes = 0;
+    for (Request* r : seed.reqs) seed_px += (double)r->W * r->H;
     // iteration group: triangle buffers, uploads, cell resets
     for (Request* r : iter.reqs) {
         const size_t tri_bytes = align_up((size_t)r->T * 36 + 64, 256) + align_up((size_t)r->bin_entries * 4 + 4, 256);
@@ -502,13 +570,15 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter) {
         r->resample_now = r->it < r->iters;
         r->dev.Wc = r->resample_now ? (r->W + r->sz - 1) / r->sz : 0;
         r->dev.Hc = r->resample_now ? (r->H + r->sz - 1) / r->sz : 0;
+        const double px = (double)r->W * r->H;
+        iter_px += px;
+        validate_bytes += px * (r->dev.first_pass ? 18.125 : 19.125);
         if (r->T > 0) CK(cudaMemcpyAsync((void*)r->dev.tri_uv, r->st_tri.p, (size_t)r->T * 36, cudaMemcpyHostToDevice, s));
         CK(cudaMemsetAsync(r->dev.tile_cnt, 0, sizeof(int32_t) * r->tiles, s));
         if (r->resample_now) {
             const int nc = r->dev.Wc * r->dev.Hc;
-            CK(launch_fill_u32(r->dev.cg_key, kNoKey, nc, s));
-            CK(launch_fill_u32(r->dev.cb_key, kNoKey, nc, s));
-            c->stats.kernel_launches += 2;
+            CK(Lr.run(STEREO_K_FILL, 1, 8.0 * nc, [&] { return launch_fill_u32(r->dev.cg_key, kNoKey, nc, s); }));
+            CK(Lr.run(STEREO_K_FILL, 1, 8.0 * nc, [&] { return launch_fill_u32(r->dev.cb_key, kNoKey, nc, s); }));
         }
     }
     // descriptors
@@ -523,29 +593,22 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter) {
     fill_group(iter, c->desc_host.as<char>() + bs, (char*)c->desc_dev + bs);
     CK(cudaMemcpyAsync(c->desc_dev, c->desc_host.p, bs + bi, cudaMemcpyHostToDevice, s));
     const Params& prm = c->prm;
-    int launches = 0;
-    if (!seed.reqs.empty()) {
-        CK(launch_census(batch_of(seed, WK_CENSUS), prm, s));
-        CK(launch_fast_score(batch_of(seed, WK_FAST_SCORE), prm, s));
-        CK(launch_fast_bins(batch_of(seed, WK_FAST_BINS), prm, s));
-        CK(launch_match_kp(batch_of(seed, WK_MATCH_KP), prm, s));
-        launches += 4;
-        c->stats.batched_pairs += 4 * (long long)seed.reqs.size();
+    const int ns = (int)seed.reqs.size(), ni = (int)iter.reqs.size();
+    if (ns) {
+        CK(Lr.run(STEREO_K_CENSUS, ns, seed_px * 10.125, [&] { return launch_census(batch_of(seed, WK_CENSUS), prm, s); }));
+        CK(Lr.run(STEREO_K_FAST_SCORE, ns, seed_px * 3.0, [&] { return launch_fast_score(batch_of(seed, WK_FAST_SCORE), prm, s); }));
+        CK(Lr.run(STEREO_K_FAST_BINS, ns, 0.0, [&] { return launch_fast_bins(batch_of(seed, WK_FAST_BINS), prm, s); }));
+        CK(Lr.run(STEREO_K_MATCH_KP, ns, 0.0, [&] { return launch_match_kp(batch_of(seed, WK_MATCH_KP), prm, s); }));
     }
-    if (!iter.reqs.empty()) {
-        CK(launch_raster_count(batch_of(iter, WK_TRI), s));
-        CK(launch_raster_scan(batch_of(iter, WK_SCAN), s));
-        CK(launch_raster_fill(batch_of(iter, WK_TRI), s));
-        CK(launch_raster_pixels(batch_of(iter, WK_RASTER), s));
-        CK(launch_validate(batch_of(iter, WK_VALIDATE), prm, s));
-        launches += 5;
-        c->stats.batched_pairs += 5 * (long long)iter.reqs.size();
-        if (batch_of(iter, WK_RESAMPLE).total > 0) {
-            CK(launch_resample(batch_of(iter, WK_RESAMPLE), prm, s));
-            launches += 1;
-        }
+    if (ni) {
+        CK(Lr.run(STEREO_K_RASTER_BIN, ni, 0.0, [&] { return launch_raster_count(batch_of(iter, WK_TRI), s); }));
+        CK(Lr.run(STEREO_K_RASTER_BIN, ni, 0.0, [&] { return launch_raster_scan(batch_of(iter, WK_SCAN), s); }));
+        CK(Lr.run(STEREO_K_RASTER_BIN, ni, 0.0, [&] { return launch_raster_fill(batch_of(iter, WK_TRI), s); }));
+        CK(Lr.run(STEREO_K_RASTER, ni, iter_px * 4.0, [&] { return launch_raster_pixels(batch_of(iter, WK_RASTER), s); }));
+        CK(Lr.run(STEREO_K_VALIDATE, ni, validate_bytes, [&] { return launch_validate(batch_of(iter, WK_VALIDATE), prm, s); }));
+        PairBatch rb = batch_of(iter, WK_RESAMPLE);
+        if (rb.total > 0) CK(Lr.run(STEREO_K_RESAMPLE, ni, 0.0, [&] { return launch_resample(rb, prm, s); }));
     }
-    c->stats.kernel_launches += launches;
     // results to pinned host memory
     for (Request* r : seed.reqs) {
         const int nk = kFastBins * c->K;
@@ -565,7 +628,8 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter) {
     }
     CK(cudaEventRecord(c->ev, s));
     CK(cudaEventSynchronize(c->ev));
-    c->stats.gpu_rounds++;
+    Lr.collect();
+    Lr.delta.gpu_rounds++;
     return cudaSuccess;
 }
 
@@ -588,8 +652,14 @@ void scheduler(stereo_ctx* c) {
             for (Request* r : seed.reqs) r->state = Q_RUNNING;
             for (Request* r : iter.reqs) r->state = Q_RUNNING;
         }
-        cudaError_t e = gpu_round(c, seed, iter);
+        Launcher Lr{c, c->stream};
+        cudaError_t e = gpu_round(c, seed, iter, Lr);
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(c->stream);
+            Lr.collect();
+        }
         std::lock_guard<std::mutex> g(c->mu);
+        add_stats(c->stats, Lr.delta);
         if (e != cudaSuccess) {
             for (Request* r : seed.reqs) finish(c, *r, e == cudaErrorMemoryAllocation ? STEREO_E_NOMEM : STEREO_E_CUDA);
             for (Request* r : iter.reqs) finish(c, *r, e == cudaErrorMemoryAllocation ? STEREO_E_NOMEM : STEREO_E_CUDA);
@@ -833,6 +903,7 @@ void stereo_destroy(stereo_ctx* c) {
     if (c->desc_dev) cudaFree(c->desc_dev);
     if (c->own_arena) cudaFree(c->arena_base);
     if (c->ev) cudaEventDestroy(c->ev);
+    for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
