@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 stereo path.  Prints ONE JSON line (rank 0).
+
+Workload: 1242x375 driving-shaped synthetic pairs (ground plane + 40 boxes,
+noise sigma 3, 5% unmatched pixels), N_D = 128, 3 refine+resample iterations,
+8x8 initial cells.  One step = one batch of distinct pairs through the whole
+method (census, FAST bins, epipolar match, host Delaunay, raster, fused
+validate, resample + match) via the request API with continuous batching.
+Inputs are resident in HBM when a step starts; L2 is flushed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain restatement of the method)
+on the same workload, one pair per step, on the host cores.  With N > 1 the
+pairs shard across ranks (independent replicas, no collective on the data
+path); the timed region is bracketed by barriers and the max over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+os.environ.setdefault("STEREO_SCENE_CACHE", os.path.join(tempfile.gettempdir(), "stereo_scenes"))
+
+WORKLOAD = "driving_1242x375"
+PRM = dict(t_lo=4, t_hi=8, t_grad=8, t_fast=20, kp_per_bin=4, uniq_margin=2)
+METRIC = "Mpix/s"
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def _workload_config(batch, W, H, p):
+    return {"workload": f"{W}x{H} driving-shaped synthetic pairs, dmax {p.dmax}, {p.iters} iterations, "
+                        f"{p.cell}x{p.cell} initial cells, " + (f"{batch} distinct pairs per step" if batch > 1 else "1 pair per step"),
+            "pairs_per_step": batch, "W": W, "H": H, "dmax": p.dmax, "iters": p.iters, "cell": p.cell,
+            "l2": "flushed between steps (256 MiB write), flush outside the timed spans",
+            "parallelism": "replicas: pairs sharded across ranks, no data-path collective"}
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        self.idx = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    import oracle
+    import scenes
+    oracle.build()
+    pairs = scenes.config_pairs(WORKLOAD, n=1)
+    p = pairs[0]
+    H, W = p.left.shape
+    for _ in range(args.warmup):
+        oracle.run(p.left, p.right, p.dmax, p.iters, p.cell, **PRM)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run(p.left, p.right, p.dmax, p.iters, p.cell, **PRM)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    v = W * H * args.steps / tot / 1e6
+    cfg = _workload_config(1, W, H, p)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpix/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/f32",
+           "data": "synthetic", "config": cfg,
+           "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                            "sample": f"one {W}x{H} pair per step, whole method, single thread"},
+           "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def _source_hash():
+    h = hashlib.sha256()
+    for f in ("paper_1511_00758_gb300/csrc/kernels.cu", "paper_1511_00758_gb300/csrc/internal.h"):
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel):
+    """ncu DRAM bytes per launch of the kernel, if the committed capture is of the current source."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+        e = d[kernel]
+        if e.get("source_hash") != _source_hash():
+            return None
+        return e["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1511_00758_gb300 as S
+    import scenes
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    S.load()
+    B = args.batch
+    pairs = scenes.config_pairs(WORKLOAD, n=B, first=rank * B)
+    H, W = pairs[0].left.shape
+    p0 = pairs[0]
+    px_step = W * H * B
+    dev_in = [(torch.from_numpy(p.left).cuda(), torch.from_numpy(p.right).cuda()) for p in pairs]
+    host_in = []
+    for p in pairs:
+        l = torch.from_numpy(p.left).pin_memory()
+        r = torch.from_numpy(p.right).pin_memory()
+        host_in.append((l, r))
+    host_out = [(torch.empty((H, W), dtype=torch.float32).pin_memory(),
+                 torch.empty((H, W), dtype=torch.uint8).pin_memory()) for _ in pairs]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ncpu = os.cpu_count() or 1
+    threads = max(1, min(B, ncpu // max(1, world)))
+    budget = int(0.5 * 2**30) + B * (40 * W * H + (64 << 20))
+    ctx = S.Context(device=local, mem_budget_bytes=budget, max_slots=B, max_queue=4 * B, host_threads=threads,
+                    profile=1, **PRM)
+    stream = ctx.stream
+
+    def one_step(host=False):
+        lat = []
+        ins = host_in if host else dev_in
+        tickets = [ctx.submit(l, r, W, H, p.dmax, p.iters, p.cell) for (l, r), p in zip(ins, pairs)]
+        for i, t in enumerate(tickets):
+            r = ctx.poll(t)
+            if r.status != 0:
+                raise RuntimeError(f"request failed: {r.status}")
+            lat.append(r.latency_ms)
+            if host:
+                with torch.cuda.stream(stream):
+                    host_out[i][0].copy_(S.device_view(r.disparity, (H, W), "<f4"), non_blocking=True)
+                    host_out[i][1].copy_(S.device_view(r.cost, (H, W), "|u1"), non_blocking=True)
+                stream.synchronize()
+            ctx.release(t)
+        return lat
+
+    def timed(nsteps, host=False):
+        spans, lats = [], []
+        for _ in range(nsteps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lats += one_step(host)
+            e1.record(stream)
+            e1.synchronize()
+            spans.append(e0.elapsed_time(e1))
+        return spans, lats
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    s0 = ctx.stats()
+    clocks = Clocks(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]
+                    if os.environ.get("CUDA_VISIBLE_DEVICES") else local)
+    clocks.start()
+    spans, lats = timed(args.steps)
+    clk = clocks.stop()
+    s1 = ctx.stats()
+    my_ms = sum(spans)
+    t = torch.tensor([my_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = world * px_step * args.steps / (max_ms / 1e3) / 1e6
+
+    # validate-kernel roofline from the events recorded inside the timed region
+    k = S.KINDS.index("validate")
+    nl = s1.kind_launches[k] - s0.kind_launches[k]
+    kms = s1.kind_ms[k] - s0.kind_ms[k]
+    kbytes = s1.kind_bytes[k] - s0.kind_bytes[k]
+    peaks = _peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = (kbytes / nl) / (kms / nl * 1e-3) / 1e9 if nl and kms > 0 else None
+    roofline = {"kernel": "k_validate (fused interpolate + census cost + refine)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None,
+                "peak_source": "measured" if peaks else "fallback",
+                "traffic": _traffic("k_validate"),
+                "launches": nl, "avg_launch_us": 1e3 * kms / nl if nl else None,
+                "algorithmic_bytes_per_launch": kbytes / nl if nl else None,
+                "pairs_per_launch_mean": None}
+    kinds = {S.KINDS[i]: {"launches": s1.kind_launches[i] - s0.kind_launches[i],
+                          "ms": round(s1.kind_ms[i] - s0.kind_ms[i], 4)} for i in range(len(S.KINDS))}
+    launches = s1.kernel_launches - s0.kernel_launches
+    if launches:
+        roofline["pairs_per_launch_mean"] = (s1.batched_pairs - s0.batched_pairs) / launches
+
+    # end to end through the public API with host buffers, copies inside the span
+    e2e_spans, _ = timed(max(1, min(args.steps, 3)), host=True)
+    e2e = {"value": px_step * len(e2e_spans) / (sum(e2e_spans) / 1e3) / 1e6, "unit": "Mpix/s",
+           "h2d_bytes_per_step": 2 * px_step, "d2h_bytes_per_step": 5 * px_step}
+    mesh_ms = (s1.host_mesh_ms - s0.host_mesh_ms) / max(1, (s1.requests_done - s0.requests_done))
+    ctx.close()
+
+    # plain per-pair path: one request in flight, one host thread
+    plain = None
+    if not args.no_plain:
+        pctx = S.Context(device=local, mem_budget_bytes=budget, max_slots=1, max_queue=4 * B, host_threads=1, **PRM)
+        ctx_plain = pctx
+        nplain = min(B, 4)
+
+        def plain_step():
+            for (l, r), p in list(zip(dev_in, pairs))[:nplain]:
+                tk = ctx_plain.submit(l, r, W, H, p.dmax, p.iters, p.cell)
+                ctx_plain.poll(tk)
+                ctx_plain.release(tk)
+        plain_step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(pctx.stream)
+        plain_step()
+        e1.record(pctx.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        plain = {"value": W * H * nplain / (ms / 1e3) / 1e6, "unit": "Mpix/s",
+                 "pairs_per_s": nplain / (ms / 1e3), "pairs_timed": nplain}
+        pctx.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        n = 0
+        while True:
+            oracle.run(p0.left, p0.right, p0.dmax, p0.iters, p0.cell, **PRM)
+            n += 1
+            if time.perf_counter() - t0 > 8.0 or n >= 3:
+                break
+        dt = time.perf_counter() - t0
+        cpu = {"value": W * H * n / dt / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n} x the first {W}x{H} pair of the workload, whole method, single thread"}
+
+    if rank == 0:
+        lats.sort()
+        out = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "u8/f32", "data": "synthetic",
+               "config": _workload_config(B, W, H, p0),
+               "pairs_per_s": world * B * args.steps / (max_ms / 1e3),
+               "latency_ms": {"p50": lats[len(lats) // 2], "p99": lats[min(len(lats) - 1, int(0.99 * len(lats)))]},
+               "host_mesh_ms_per_pair": mesh_ms, "host_threads": threads,
+               "plain": plain, "roofline": roofline, "kernels": kinds, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

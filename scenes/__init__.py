@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import os
 
 import numpy as np
 
@@ -117,26 +118,46 @@ def render(scene: Scene):
     # left view: front-most surface at each pixel
     best_d = np.full((H, W), -np.inf)
     best_s = np.full((H, W), -1, dtype=np.int64)
+
+    def window(s, right):
+        """Row/column slices that can contain the surface (the whole image without a polygon)."""
+        if s.poly is None:
+            return slice(0, H), slice(0, W)
+        u0, u1 = s.poly[:, 0].min(), s.poly[:, 0].max()
+        v0, v1 = s.poly[:, 1].min(), s.poly[:, 1].max()
+        if right:  # x = u - d(u, v); d is linear, so its extremes sit at the vertices
+            dv = s.a * s.poly[:, 0] + s.b * s.poly[:, 1] + s.c
+            u0, u1 = u0 - dv.max(), u1 - dv.min()
+        r = slice(int(np.clip(np.floor(v0) - 1, 0, H)), int(np.clip(np.ceil(v1) + 2, 0, H)))
+        c = slice(int(np.clip(np.floor(u0) - 1, 0, W)), int(np.clip(np.ceil(u1) + 2, 0, W)))
+        return r, c
+
     for si, s in enumerate(scene.surfaces):
-        d = s.a * uu + s.b * vv + s.c
-        m = d > best_d
+        r, c = window(s, False)
+        U, V = uu[r, c], vv[r, c]
+        d = s.a * U + s.b * V + s.c
+        bd = best_d[r, c]
+        m = d > bd
         if s.poly is not None:
-            m &= _inside_convex(s.poly, uu, vv)
-        best_d[m] = d[m]
-        best_s[m] = si
+            m &= _inside_convex(s.poly, U, V)
+        bd[m] = d[m]
+        best_s[r, c][m] = si
     # right view: for right pixel x, source column u solves u - d(u, v) = x
     rbest_d = np.full((H, W), -np.inf)
     rbest_s = np.full((H, W), -1, dtype=np.int64)
     rsrc_u = np.zeros((H, W))
     for si, s in enumerate(scene.surfaces):
-        u_src = (uu + s.b * vv + s.c) / (1.0 - s.a)
-        d = u_src - uu
-        m = d > rbest_d
+        r, c = window(s, True)
+        X, V = uu[r, c], vv[r, c]
+        u_src = (X + s.b * V + s.c) / (1.0 - s.a)
+        d = u_src - X
+        bd = rbest_d[r, c]
+        m = d > bd
         if s.poly is not None:
-            m &= _inside_convex(s.poly, u_src, vv)
-        rbest_d[m] = d[m]
-        rbest_s[m] = si
-        rsrc_u[m] = u_src[m]
+            m &= _inside_convex(s.poly, u_src, V)
+        bd[m] = d[m]
+        rbest_s[r, c][m] = si
+        rsrc_u[r, c][m] = u_src[m]
     assert (best_s >= 0).all() and (rbest_s >= 0).all(), "scene must cover the image (background surface)"
     left_f = np.zeros((H, W))
     right_f = np.zeros((H, W))
@@ -270,13 +291,29 @@ CONFIGS = {
 }
 
 
-def config_pairs(name, n=None, first=0):
-    """Pairs of one named workload, pair i seeded SEED_BASE + idx*1000 + i."""
+def config_pairs(name, n=None, first=0, cache_dir=None):
+    """Pairs of one named workload, pair i seeded SEED_BASE + idx*1000 + i.
+    With cache_dir (or $STEREO_SCENE_CACHE) rendered pairs are kept as .npz files."""
     cfg = CONFIGS[name]
     count = cfg["n"] if n is None else n
-    return [make_pair(cfg["kind"], cfg["W"], cfg["H"], SEED_BASE + cfg["idx"] * 1000 + i,
-                      cfg["dmax"], cfg["iters"], cfg["cell"], **cfg["kw"])
-            for i in range(first, first + count)]
+    cache_dir = cache_dir or os.environ.get("STEREO_SCENE_CACHE")
+    out = []
+    for i in range(first, first + count):
+        seed = SEED_BASE + cfg["idx"] * 1000 + i
+        path = os.path.join(cache_dir, f"{name}_{seed}.npz") if cache_dir else None
+        if path and os.path.exists(path):
+            z = np.load(path)
+            out.append(StereoPair(z["left"], z["right"], z["gt_disp"], z["gt_occ"], cfg["dmax"], cfg["iters"],
+                                  cfg["cell"]))
+            continue
+        p = make_pair(cfg["kind"], cfg["W"], cfg["H"], seed, cfg["dmax"], cfg["iters"], cfg["cell"], **cfg["kw"])
+        if path:
+            os.makedirs(cache_dir, exist_ok=True)
+            tmp = path + f".{os.getpid()}.npz"
+            np.savez(tmp, left=p.left, right=p.right, gt_disp=p.gt_disp, gt_occ=p.gt_occ)
+            os.replace(tmp, path)
+        out.append(p)
+    return out
 
 
 def integer_shift_pair(W, H, shift, seed=1, dmax=None, texture="noise", flat_left=0):
