@@ -45,10 +45,10 @@ def _env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def _workload_config(batch, W, H, p):
+def _workload_config(batch, W, H, p, window=0):
     return {"workload": f"{W}x{H} driving-shaped synthetic pairs, dmax {p.dmax}, {p.iters} iterations, "
                         f"{p.cell}x{p.cell} initial cells, " + (f"{batch} distinct pairs per step" if batch > 1 else "1 pair per step"),
-            "pairs_per_step": batch, "W": W, "H": H, "dmax": p.dmax, "iters": p.iters, "cell": p.cell,
+            "pairs_per_step": batch, "batch_window_us": window, "W": W, "H": H, "dmax": p.dmax, "iters": p.iters, "cell": p.cell,
             "l2": "flushed between steps (256 MiB write), flush outside the timed spans",
             "parallelism": "replicas: pairs sharded across ranks, no data-path collective"}
 
@@ -181,7 +181,7 @@ def run_ours(args):
     threads = max(1, min(B, ncpu // max(1, world)))
     budget = int(0.5 * 2**30) + B * (40 * W * H + (64 << 20))
     ctx = S.Context(device=local, mem_budget_bytes=budget, max_slots=B, max_queue=4 * B, host_threads=threads,
-                    profile=1, **PRM)
+                    profile=1, batch_window_us=args.window_us, **PRM)
     stream = ctx.stream
 
     def one_step(host=False):
@@ -308,7 +308,7 @@ def run_ours(args):
         out = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "u8/f32", "data": "synthetic",
-               "config": _workload_config(B, W, H, p0),
+               "config": _workload_config(B, W, H, p0, args.window_us),
                "pairs_per_s": world * B * args.steps / (max_ms / 1e3),
                "latency_ms": {"p50": lats[len(lats) // 2], "p99": lats[min(len(lats) - 1, int(0.99 * len(lats)))]},
                "host_mesh_ms_per_pair": mesh_ms, "host_threads": threads,
@@ -328,6 +328,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--window-us", type=int, default=3000, help="batching window of the request scheduler")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

@@ -66,6 +66,9 @@ typedef struct {
     void* stream;              /* cudaStream_t for all work (NULL = library creates one) */
     int profile;               /* 1 = time every kernel launch with CUDA events on `stream`
                                   and accumulate per-kind durations in stereo_stats */
+    int batch_window_us;       /* continuous batching: when some requests are ready for a GPU
+                                  stage while others are still in their host step, wait up to
+                                  this long for more of them before launching (0 = launch at once) */
 } stereo_config;
 
 /* Fill *cfg with the defaults: t_lo 4, t_hi 8, t_grad 8, t_fast 20,
@@ -119,8 +122,8 @@ void stereo_destroy(stereo_ctx* ctx);
 #define STEREO_K_FAST_SCORE 1    /* FAST-9 scores */
 #define STEREO_K_FAST_BINS 2     /* non-maximum suppression + per-bin top-K */
 #define STEREO_K_MATCH_KP 3      /* epipolar match of the keypoints */
-#define STEREO_K_RASTER_BIN 4    /* triangle-to-tile binning (count, scan, fill) */
-#define STEREO_K_RASTER 5        /* per-pixel triangle lookup */
+#define STEREO_K_RASTER_CLEAR 4  /* plane-index map reset to -1 */
+#define STEREO_K_RASTER 5        /* scan conversion of the triangles */
 #define STEREO_K_VALIDATE 6      /* fused interpolate + cost + refine */
 #define STEREO_K_RESAMPLE 7      /* per-cell resample + epipolar match */
 #define STEREO_K_FILL 8          /* cell-record resets */
@@ -131,7 +134,7 @@ void stereo_destroy(stereo_ctx* ctx);
  * covered (batched_pairs / kernel_launches = mean pairs per launch).  With
  * profile = 1, kind_ms[k] holds the summed CUDA-event durations of kind k and
  * kind_bytes[k] the algorithmic bytes those launches had to move (census:
- * 2 B/px read + 8.125 B/px written; raster: 4 B/px written; validate:
+ * 2 B/px read + 8.125 B/px written; raster clear and raster: 4 B/px written each; validate:
  * 13.125 B/px read (12.125 on a first pass) + 6 B/px written). */
 typedef struct {
     long long kernel_launches;
@@ -195,19 +198,19 @@ int stereo_delaunay(const int32_t* uv, int n, int32_t* tri, int cap);
  * index order, rounded to fp32.  d: n fp32 support disparities; abc: 3*T. */
 int stereo_planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float* abc);
 
-/* Scratch bytes stereo_raster needs for the T triangles whose vertex
- * coordinates tri_uv_host (host, T * 6 int32) holds, on a W x H image: the
- * per-tile counts and offsets plus one entry per (triangle, 16x16 tile of its
- * bounding box).  0 on invalid arguments. */
-size_t stereo_raster_scratch_bytes(const int32_t* tri_uv_host, int T, int w, int h);
+/* Scratch bytes stereo_raster needs for T triangles: T + 1 int32 row-chunk
+ * offsets (rounded up to 256 bytes). */
+size_t stereo_raster_scratch_bytes(int T);
 
 /* Pixel -> triangle lookup table (Sec. III-B).  A pixel (u, v), sampled at
  * integer coordinates, belongs to a triangle when every edge function is
- * positive or zero on a top or left edge; this partitions the hull.
+ * positive or zero on a top or left edge; this partitions the hull, and
+ * pixels outside it get -1.  The table is built by exact scan conversion
+ * (per row, integer floor/ceil bounds of the three edge half-planes).
  * tri_uv: T * 6 int32 vertex coordinates (u0,v0,u1,v1,u2,v2) of triangle t;
- * planeidx: W*H int32 output, triangle id or -1.  scratch: at least
- * stereo_raster_scratch_bytes(tri_uv_host, T, w, h) bytes of device memory;
- * STEREO_E_CAP when scratch_bytes cannot even hold the per-tile arrays. */
+ * planeidx: W*H int32 output (16-byte aligned), triangle id or -1.  scratch:
+ * at least stereo_raster_scratch_bytes(T) bytes of device memory (the
+ * per-triangle row-chunk offsets, written here). */
 int stereo_raster(const int32_t* tri_uv, int T, int w, int h, int32_t* planeidx,
                   void* scratch, size_t scratch_bytes, void* stream);
 

@@ -34,7 +34,7 @@ class Config(ctypes.Structure):
                 ("max_slots", ctypes.c_int), ("max_queue", ctypes.c_int), ("t_lo", ctypes.c_int),
                 ("t_hi", ctypes.c_int), ("t_grad", ctypes.c_int), ("t_fast", ctypes.c_int),
                 ("kp_per_bin", ctypes.c_int), ("uniq_margin", ctypes.c_int), ("host_threads", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("profile", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("profile", ctypes.c_int), ("batch_window_us", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -52,7 +52,7 @@ class Stats(ctypes.Structure):
                 ("kind_ms", ctypes.c_double * 9), ("kind_bytes", ctypes.c_double * 9)]
 
 
-KINDS = ("census", "fast_score", "fast_bins", "match_kp", "raster_bin", "raster", "validate", "resample", "fill")
+KINDS = ("census", "fast_score", "fast_bins", "match_kp", "raster_clear", "raster", "validate", "resample", "fill")
 
 
 _lib = None
@@ -71,7 +71,7 @@ _SIGS = {
     "stereo_epipolar_match": (_I, [_P, _P, _I, _I, _P, _I, _I, _I, _I, _P, _P]),
     "stereo_delaunay": (_I, [_P, _I, _P, _I]),
     "stereo_planes": (_I, [_P, _P, _P, _I, _P]),
-    "stereo_raster_scratch_bytes": (ctypes.c_size_t, [_P, _I, _I, _I]),
+    "stereo_raster_scratch_bytes": (ctypes.c_size_t, [_I]),
     "stereo_raster": (_I, [_P, _I, _I, _I, _P, _P, ctypes.c_size_t, _P]),
     "stereo_validate": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P]),
     "stereo_resample_match": (_I, [_P, _P, _I, _P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
@@ -153,8 +153,8 @@ def planes(uv, d, tri, T, abc):
     return _check(lib().stereo_planes(_ptr(uv), _ptr(d), _ptr(tri), T, _ptr(abc)), "planes")
 
 
-def raster_scratch_bytes(tri_uv_host, T, w, h):
-    return int(lib().stereo_raster_scratch_bytes(_ptr(tri_uv_host), T, w, h))
+def raster_scratch_bytes(T):
+    return int(lib().stereo_raster_scratch_bytes(T))
 
 
 def raster(tri_uv, T, w, h, planeidx, scratch, scratch_bytes, stream=None):

@@ -145,7 +145,7 @@ struct Request {
     // device block
     void* block = nullptr;
     PairDev dev{};
-    int ncell_max = 0, tiles = 0;
+    int ncell_max = 0;
     // triangle buffers (device) and their capacities
     void* tri_block = nullptr;
     size_t tri_block_bytes = 0;
@@ -154,8 +154,8 @@ struct Request {
     std::vector<int32_t> n_support, n_tri;
     std::vector<float> trace;
     int T = 0;
-    long long bin_entries = 0;
-    Pinned st_tri;            // tri_uv (6 ints) + abc (3 floats) per triangle
+    int raster_items = 0;
+    Pinned st_tri;            // tri_uv (6 ints) + abc (3 floats) per triangle, then T + 1 chunk offsets
     Pinned st_kp;             // kp_uv + kp_d
     Pinned st_cells;          // cg_key, cg_d, cb_key, x_d
     bool resample_now = false;
@@ -173,7 +173,6 @@ size_t block_bytes(const Request& r, int K) {
     add(4 * N); add(N); add(N);  // Df, Cf, mask
     add((size_t)kFastBins * K * 8); add((size_t)kFastBins * K * 4);
     for (int i = 0; i < 4; i++) add(4 * (size_t)r.ncell_max);
-    add(4 * (size_t)r.tiles); add(4 * (size_t)(r.tiles + 1));
     return b;
 }
 
@@ -200,14 +199,10 @@ void carve(Request& r, int K) {
     d.cb_key = (uint32_t*)take(4 * (size_t)r.ncell_max);
     d.cg_d = (float*)take(4 * (size_t)r.ncell_max);
     d.x_d = (int32_t*)take(4 * (size_t)r.ncell_max);
-    d.tile_cnt = (int32_t*)take(4 * (size_t)r.tiles);
-    d.tile_off = (int32_t*)take(4 * (size_t)(r.tiles + 1));
     d.W = r.W;
     d.H = r.H;
     d.dmax = r.dmax;
     d.K = K;
-    d.tiles_x = (r.W + kRasterTile - 1) / kRasterTile;
-    d.tiles_y = (r.H + kRasterTile - 1) / kRasterTile;
 }
 
 int cells_of(int W, int H, int sz) { return ((W + sz - 1) / sz) * ((H + sz - 1) / sz); }
@@ -312,9 +307,10 @@ int mesh_step(Request& r) {
     std::vector<int32_t> tri((size_t)3 * cap);
     int T = n >= 3 ? delaunay(P.data(), n, tri.data(), cap) : 0;
     if (T < 0) return STEREO_E_INTERNAL;
-    if (!r.st_tri.ensure((size_t)T * 36 + 64)) return STEREO_E_NOMEM;
+    if (!r.st_tri.ensure((size_t)T * 40 + 64)) return STEREO_E_NOMEM;
     int32_t* tuv = r.st_tri.as<int32_t>();
     float* abc = (float*)(tuv + (size_t)6 * T);
+    int32_t* rows = (int32_t*)(abc + (size_t)3 * T);
     for (int t = 0; t < T; t++)
         for (int k = 0; k < 3; k++) {
             tuv[6 * t + 2 * k] = P[2 * tri[3 * t + k]];
@@ -322,7 +318,7 @@ int mesh_step(Request& r) {
         }
     planes(P.data(), D.data(), tri.data(), T, abc);
     r.T = T;
-    r.bin_entries = raster_bin_entries(tuv, T, r.W, r.H);
+    r.raster_items = raster_row_chunks(tuv, T, r.H, rows);
     r.n_support.push_back(n);
     r.n_tri.push_back(T);
     for (const auto& s : r.S) {
@@ -547,11 +543,11 @@ void add_stats(stereo_stats& to, const stereo_stats& d) {
 // One GPU round for the seed group and the iteration group.
 cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
     cudaStream_t s = c->stream;
-    double seed_px = 0, iter_px = 0, validate_bytes = 0;
+    double seed_px = 0, iter_px = 0, validate_bytes = 0, cells_bytes = 0;
     for (Request* r : seed.reqs) seed_px += (double)r->W * r->H;
     // iteration group: triangle buffers, uploads, cell resets
     for (Request* r : iter.reqs) {
-        const size_t tri_bytes = align_up((size_t)r->T * 36 + 64, 256) + align_up((size_t)r->bin_entries * 4 + 4, 256);
+        const size_t tri_bytes = align_up((size_t)r->T * 40 + 64, 256);
         if (tri_bytes > r->tri_block_bytes) {
             std::lock_guard<std::mutex> g(c->mu);
             c->arena.release(r->tri_block);
@@ -562,10 +558,10 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         char* tb = (char*)r->tri_block;
         r->dev.tri_uv = (const int32_t*)tb;
         r->dev.abc = (const float*)(tb + (size_t)r->T * 24);
-        r->dev.tile_list = (int32_t*)(tb + align_up((size_t)r->T * 36 + 64, 256));
-        r->dev.tile_cap = (int)r->bin_entries;
+        r->dev.tri_rows = (int32_t*)(tb + (size_t)r->T * 36);
+        r->dev.raster_items = r->raster_items;
         r->dev.T = r->T;
-        r->dev.sz = r->sz;
+        set_cell_size(r->dev, r->sz);
         r->dev.first_pass = r->it == 1;
         r->resample_now = r->it < r->iters;
         r->dev.Wc = r->resample_now ? (r->W + r->sz - 1) / r->sz : 0;
@@ -573,13 +569,8 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         const double px = (double)r->W * r->H;
         iter_px += px;
         validate_bytes += px * (r->dev.first_pass ? 18.125 : 19.125);
-        if (r->T > 0) CK(cudaMemcpyAsync((void*)r->dev.tri_uv, r->st_tri.p, (size_t)r->T * 36, cudaMemcpyHostToDevice, s));
-        CK(cudaMemsetAsync(r->dev.tile_cnt, 0, sizeof(int32_t) * r->tiles, s));
-        if (r->resample_now) {
-            const int nc = r->dev.Wc * r->dev.Hc;
-            CK(Lr.run(STEREO_K_FILL, 1, 8.0 * nc, [&] { return launch_fill_u32(r->dev.cg_key, kNoKey, nc, s); }));
-            CK(Lr.run(STEREO_K_FILL, 1, 8.0 * nc, [&] { return launch_fill_u32(r->dev.cb_key, kNoKey, nc, s); }));
-        }
+        if (r->T > 0) CK(cudaMemcpyAsync((void*)r->dev.tri_uv, r->st_tri.p, (size_t)r->T * 40 + 4, cudaMemcpyHostToDevice, s));
+        if (r->resample_now) cells_bytes += 8.0 * r->dev.Wc * r->dev.Hc;
     }
     // descriptors
     const size_t bs = group_bytes(seed), bi = group_bytes(iter);
@@ -601,10 +592,10 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         CK(Lr.run(STEREO_K_MATCH_KP, ns, 0.0, [&] { return launch_match_kp(batch_of(seed, WK_MATCH_KP), prm, s); }));
     }
     if (ni) {
-        CK(Lr.run(STEREO_K_RASTER_BIN, ni, 0.0, [&] { return launch_raster_count(batch_of(iter, WK_TRI), s); }));
-        CK(Lr.run(STEREO_K_RASTER_BIN, ni, 0.0, [&] { return launch_raster_scan(batch_of(iter, WK_SCAN), s); }));
-        CK(Lr.run(STEREO_K_RASTER_BIN, ni, 0.0, [&] { return launch_raster_fill(batch_of(iter, WK_TRI), s); }));
-        CK(Lr.run(STEREO_K_RASTER, ni, iter_px * 4.0, [&] { return launch_raster_pixels(batch_of(iter, WK_RASTER), s); }));
+        PairBatch fb = batch_of(iter, WK_FILL);
+        if (fb.total > 0) CK(Lr.run(STEREO_K_FILL, ni, cells_bytes, [&] { return launch_fill_cells(fb, s); }));
+        CK(Lr.run(STEREO_K_RASTER_CLEAR, ni, iter_px * 4.0, [&] { return launch_raster_clear(batch_of(iter, WK_CLEAR), s); }));
+        CK(Lr.run(STEREO_K_RASTER, ni, iter_px * 4.0, [&] { return launch_raster_spans(batch_of(iter, WK_RASTER), s); }));
         CK(Lr.run(STEREO_K_VALIDATE, ni, validate_bytes, [&] { return launch_validate(batch_of(iter, WK_VALIDATE), prm, s); }));
         PairBatch rb = batch_of(iter, WK_RESAMPLE);
         if (rb.total > 0) CK(Lr.run(STEREO_K_RESAMPLE, ni, 0.0, [&] { return launch_resample(rb, prm, s); }));
@@ -639,13 +630,32 @@ void scheduler(stereo_ctx* c) {
         Group seed, iter;
         {
             std::unique_lock<std::mutex> g(c->mu);
+            bool waiting = false;
+            std::chrono::steady_clock::time_point deadline;
             for (;;) {
                 admit(c);
+                seed.reqs.clear();
+                iter.reqs.clear();
                 for (Request* r : c->active) {
                     if (r->state == Q_SEED_READY) seed.reqs.push_back(r);
                     else if (r->state == Q_ITER_READY) iter.reqs.push_back(r);
                 }
-                if (!seed.reqs.empty() || !iter.reqs.empty()) break;
+                const size_t ready = seed.reqs.size() + iter.reqs.size();
+                if (ready > 0) {
+                    // batching window: others are still in their host step
+                    if (c->cfg.batch_window_us > 0 && c->host_busy > 0 && !c->stop) {
+                        if (!waiting) {
+                            waiting = true;
+                            deadline = std::chrono::steady_clock::now() +
+                                       std::chrono::microseconds(c->cfg.batch_window_us);
+                        }
+                        if (std::chrono::steady_clock::now() < deadline) {
+                            c->cv_sched.wait_until(g, deadline);
+                            continue;
+                        }
+                    }
+                    break;
+                }
                 if (c->stop && c->queue.empty() && c->host_busy == 0) return;
                 c->cv_sched.wait(g);
             }
@@ -762,7 +772,6 @@ int stereo_submit(stereo_ctx* c, int stream_id, const uint8_t* left, const uint8
     r->cell = cell;
     int sz_min = iters >= 2 ? std::max(1, cell >> (iters - 2)) : 0;
     r->ncell_max = iters >= 2 ? cells_of(w, h, sz_min) : 1;
-    r->tiles = ((w + kRasterTile - 1) / kRasterTile) * ((h + kRasterTile - 1) / kRasterTile);
     const size_t need = block_bytes(*r, c->K);
     if (need > c->cfg.mem_budget_bytes) {
         delete r;
@@ -979,38 +988,27 @@ int stereo_planes(const int32_t* uv, const float* d, const int32_t* tri, int T, 
     return STEREO_OK;
 }
 
-size_t stereo_raster_scratch_bytes(const int32_t* tri_uv, int T, int w, int h) {
-    if (!valid_size(w, h) || T < 0) return 0;
-    const size_t tiles = (size_t)((w + kRasterTile - 1) / kRasterTile) * ((h + kRasterTile - 1) / kRasterTile);
-    const long long e = T > 0 && tri_uv ? raster_bin_entries(tri_uv, T, w, h) : 0;
-    return align_up(4 * tiles, 256) + align_up(4 * (tiles + 1), 256) + align_up(4 * (size_t)e + 4, 256);
+size_t stereo_raster_scratch_bytes(int T) {
+    if (T < 0) return 0;
+    return align_up(4 * ((size_t)T + 1), 256);
 }
 
 int stereo_raster(const int32_t* tri_uv, int T, int w, int h, int32_t* planeidx, void* scratch,
                   size_t scratch_bytes, void* stream) {
-    if (!valid_size(w, h) || T < 0 || (T > 0 && !tri_uv) || !planeidx || !scratch) return STEREO_E_INVAL;
+    if (!valid_size(w, h) || T < 0 || (T > 0 && (!tri_uv || !scratch)) || !planeidx ||
+        ((uintptr_t)planeidx & 15) != 0)
+        return STEREO_E_INVAL;
+    if (T > 0 && scratch_bytes < 4 * ((size_t)T + 1)) return STEREO_E_CAP;
     PairDev p{};
     p.W = w;
     p.H = h;
     p.T = T;
     p.tri_uv = tri_uv;
+    p.tri_rows = (int32_t*)scratch;
     p.planeidx = planeidx;
-    p.tiles_x = (w + kRasterTile - 1) / kRasterTile;
-    p.tiles_y = (h + kRasterTile - 1) / kRasterTile;
-    const size_t tiles = (size_t)p.tiles_x * p.tiles_y;
-    const size_t fixed = align_up(4 * tiles, 256) + align_up(4 * (tiles + 1), 256);
-    if (scratch_bytes < fixed + 4) return STEREO_E_CAP;
-    char* sp = (char*)scratch;
-    p.tile_cnt = (int32_t*)sp;
-    p.tile_off = (int32_t*)(sp + align_up(4 * tiles, 256));
-    p.tile_list = (int32_t*)(sp + fixed);
-    p.tile_cap = (int)std::min<size_t>((scratch_bytes - fixed) / 4, 0x7fffffff);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(p.tile_cnt, 0, 4 * tiles, s);
-    if (e == cudaSuccess) e = launch_raster_count(single(p, WK_TRI), s);
-    if (e == cudaSuccess) e = launch_raster_scan(single(p, WK_SCAN), s);
-    if (e == cudaSuccess) e = launch_raster_fill(single(p, WK_TRI), s);
-    if (e == cudaSuccess) e = launch_raster_pixels(single(p, WK_RASTER), s);
+    cudaError_t e = launch_raster_clear(single(p, WK_CLEAR), s);
+    if (e == cudaSuccess) e = launch_raster_device_prefix(p, s);
     return to_rc(e);
 }
 
@@ -1028,7 +1026,7 @@ int stereo_validate(const uint32_t* cL, const uint32_t* cR, const uint32_t* omeg
     p.abc = abc;
     p.W = w;
     p.H = h;
-    p.sz = sz;
+    set_cell_size(p, sz);
     p.Wc = (w + sz - 1) / sz;
     p.Hc = (h + sz - 1) / sz;
     p.first_pass = first_pass ? 1 : 0;

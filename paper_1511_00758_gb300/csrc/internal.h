@@ -12,7 +12,7 @@ constexpr int kFastBins = 120;          // 12 x 10 spatial bins (Sec. III-A)
 constexpr int kFastBinsX = 12;
 constexpr int kFastBinsY = 10;
 constexpr int kMaxK = 32;               // keypoints per bin, upper bound
-constexpr int kRasterTile = 16;         // raster bin edge in pixels
+constexpr int kRasterRows = 8;          // triangle rows per raster work item
 constexpr uint32_t kNoKey = 0xFFFFFFFFu;
 constexpr uint32_t kIdxMask = (1u << 27) - 1;
 
@@ -29,10 +29,7 @@ struct PairDev {
     int32_t* kp_d;            // 120*K matches
     const int32_t* tri_uv;    // T * 6
     const float* abc;         // T * 3
-    int32_t* tile_cnt;        // tiles (count, then cursor)
-    int32_t* tile_off;        // tiles + 1
-    int32_t* tile_list;       // sum of bbox tiles
-    int tile_cap;             // entries tile_list can hold
+    int32_t* tri_rows;        // T + 1: exclusive prefix of 8-row chunks per triangle
     int32_t* planeidx;        // W*H
     float* Df;                // W*H
     uint8_t* Cf;              // W*H
@@ -44,7 +41,9 @@ struct PairDev {
     int W, H, dmax;
     int T;                    // triangles
     int sz, Wc, Hc;           // current occupancy grid
-    int tiles_x, tiles_y;     // raster bins
+    int sz_shift;             // log2(sz) when sz is a power of two, else -1
+    uint32_t sz_magic;        // floor(2^32 / sz) + 1: x / sz == umulhi(x, magic) for x < 2^18
+    int raster_items;         // tri_rows[T] when known on the host
     int first_pass;
     int K;                    // keypoints per bin
 };
@@ -64,21 +63,24 @@ struct Params {
 };
 
 // Work items per pair for each kernel kind.
-enum WorkKind { WK_CENSUS = 0, WK_FAST_SCORE, WK_FAST_BINS, WK_MATCH_KP, WK_TRI, WK_SCAN,
-                WK_RASTER, WK_VALIDATE, WK_RESAMPLE, WK_COUNT };
+enum WorkKind { WK_CENSUS = 0, WK_FAST_SCORE, WK_FAST_BINS, WK_MATCH_KP, WK_CLEAR,
+                WK_RASTER, WK_VALIDATE, WK_RESAMPLE, WK_FILL, WK_COUNT };
 int work_items(WorkKind k, const PairDev& p);
+// Sets sz and its division helpers.
+void set_cell_size(PairDev& p, int sz);
 
 // Kernel launchers (async on stream).  grid_cap limits persistent grids.
 cudaError_t launch_census(const PairBatch& b, const Params& prm, cudaStream_t s);
 cudaError_t launch_fast_score(const PairBatch& b, const Params& prm, cudaStream_t s);
 cudaError_t launch_fast_bins(const PairBatch& b, const Params& prm, cudaStream_t s);
 cudaError_t launch_match_kp(const PairBatch& b, const Params& prm, cudaStream_t s);
-cudaError_t launch_raster_count(const PairBatch& b, cudaStream_t s);
-cudaError_t launch_raster_scan(const PairBatch& b, cudaStream_t s);
-cudaError_t launch_raster_fill(const PairBatch& b, cudaStream_t s);
-cudaError_t launch_raster_pixels(const PairBatch& b, cudaStream_t s);
+cudaError_t launch_raster_clear(const PairBatch& b, cudaStream_t s);
+cudaError_t launch_raster_spans(const PairBatch& b, cudaStream_t s);
+// single pair whose chunk prefix is built on the device (stage entry point)
+cudaError_t launch_raster_device_prefix(const PairDev& p, cudaStream_t s);
 cudaError_t launch_validate(const PairBatch& b, const Params& prm, cudaStream_t s);
 cudaError_t launch_resample(const PairBatch& b, const Params& prm, cudaStream_t s);
+cudaError_t launch_fill_cells(const PairBatch& b, cudaStream_t s);
 cudaError_t launch_fill_u32(uint32_t* p, uint32_t value, size_t n, cudaStream_t s);
 cudaError_t launch_match_list(const uint32_t* cL, const uint32_t* cR, int W, int H,
                               const int32_t* q, int n, int dmax, const Params& prm,
@@ -89,7 +91,8 @@ int sm_count();
 // Host mesh step (mesh.cpp).
 int delaunay(const int32_t* uv, int n, int32_t* tri, int cap);
 void planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float* abc);
-// Sum over triangles of the raster bins each triangle's bounding box touches.
-long long raster_bin_entries(const int32_t* tri_uv, int T, int W, int H);
+// Exclusive prefix of 8-row chunks of each triangle's clipped row range
+// (rows[T + 1]); returns the total.
+int raster_row_chunks(const int32_t* tri_uv, int T, int H, int32_t* rows);
 
 }  // namespace stereo

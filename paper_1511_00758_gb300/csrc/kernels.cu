@@ -27,16 +27,24 @@ constexpr int kTileH = 8;
 int work_items(WorkKind k, const PairDev& p) {
     switch (k) {
         case WK_CENSUS:
-        case WK_FAST_SCORE:
-        case WK_VALIDATE: return cdiv(p.W, kTileW) * cdiv(p.H, kTileH);
+        case WK_FAST_SCORE: return cdiv(p.W, kTileW) * cdiv(p.H, kTileH);
+        case WK_VALIDATE: return cdiv(p.W, 128) * cdiv(p.H, 8);
         case WK_FAST_BINS: return kFastBins;
         case WK_MATCH_KP: return cdiv((long long)kFastBins * p.K, 8);
-        case WK_TRI: return cdiv(p.T, 256);
-        case WK_SCAN: return 1;
-        case WK_RASTER: return p.tiles_x * p.tiles_y;
+        case WK_CLEAR: return cdiv((long long)p.W * p.H, 4096);
+        case WK_FILL: return p.cg_key ? cdiv((long long)p.Wc * p.Hc, 4096) : 0;
+        case WK_RASTER: return cdiv(p.raster_items, 8);
         case WK_RESAMPLE: return cdiv((long long)p.Wc * p.Hc, 8);
         default: return 0;
     }
+}
+
+void set_cell_size(PairDev& p, int sz) {
+    p.sz = sz;
+    p.sz_shift = -1;
+    for (int s = 0; s < 31; s++)
+        if ((1 << s) == sz) p.sz_shift = s;
+    p.sz_magic = (uint32_t)(0xFFFFFFFFull / (unsigned)sz + 1ull);
 }
 
 __device__ __forceinline__ int find_pair(const int* off, int n, int item) {
@@ -334,40 +342,108 @@ __global__ void __launch_bounds__(256) k_match_list(const uint32_t* cL, const ui
 }
 
 // ---------------------------------------------------------------- raster (Sec. III-B)
-// Triangles are binned to 16x16 tiles by bounding box (count, scan, fill);
-// then each tile's pixels test the tile's triangles with exact integer edge
-// functions and the top-left rule.  The rule partitions the hull, so the
-// order of a tile's list does not matter.
-__device__ __forceinline__ void tri_tiles(const int32_t* t6, int W, int H, int& tx0, int& tx1, int& ty0, int& ty1) {
-    int x0 = min(t6[0], min(t6[2], t6[4])), x1 = max(t6[0], max(t6[2], t6[4]));
-    int y0 = min(t6[1], min(t6[3], t6[5])), y1 = max(t6[1], max(t6[3], t6[5]));
-    x0 = max(x0, 0); y0 = max(y0, 0); x1 = min(x1, W - 1); y1 = min(y1, H - 1);
-    tx0 = x0 / kRasterTile; tx1 = x1 / kRasterTile; ty0 = y0 / kRasterTile; ty1 = y1 / kRasterTile;
+// Pixel -> triangle lookup table by exact scan conversion.  A pixel (u, v)
+// belongs to the positively oriented triangle when every edge function
+// E(u, v) = A u + B v + C is > 0, or == 0 on a top or left edge; for one row
+// v each edge bounds u from one side, so the covered pixels are the integer
+// range [lo, hi] obtained by exact floor/ceil division.  The rule partitions
+// the hull: every pixel is written by exactly one triangle, in any order.
+// One warp per chunk of 8 rows of one triangle; lanes stride the columns.
+__device__ __forceinline__ long long floordiv_pos(long long a, long long b) {  // b > 0
+    return a >= 0 ? a / b : -((-a + b - 1) / b);
 }
 
-__device__ __forceinline__ void raster_count_body(const PairDev& P, int local) {
-    const int t = local * 256 + threadIdx.x;
-    if (t >= P.T) return;
-    int tx0, tx1, ty0, ty1;
-    tri_tiles(P.tri_uv + 6 * (size_t)t, P.W, P.H, tx0, tx1, ty0, ty1);
-    for (int ty = ty0; ty <= ty1; ty++)
-        for (int tx = tx0; tx <= tx1; tx++) atomicAdd(P.tile_cnt + ty * P.tiles_x + tx, 1);
+__device__ __forceinline__ void raster_clear_body(const PairDev& P, int local) {
+    const size_t n = (size_t)P.W * P.H;
+    const size_t base = (size_t)local * 4096;
+    int4* q = reinterpret_cast<int4*>(P.planeidx);
+    const int4 m1 = make_int4(-1, -1, -1, -1);
+    for (size_t i = base + 4 * threadIdx.x; i < base + 4096 && i < n; i += 4 * blockDim.x) {
+        if (i + 4 <= n) q[i / 4] = m1;
+        else for (size_t j = i; j < n; j++) P.planeidx[j] = -1;
+    }
 }
 
-__global__ void __launch_bounds__(256) k_raster_count(PairBatch b) {
-#define BODY(P, l) raster_count_body(P, l)
+__global__ void __launch_bounds__(256) k_raster_clear(PairBatch b) {
+#define BODY(P, l) raster_clear_body(P, l)
     FOR_EACH_ITEM(b, BODY)
 #undef BODY
 }
 
-__device__ __forceinline__ void raster_scan_body(const PairDev& P, int) {
+__device__ __forceinline__ void raster_chunk(const int32_t* __restrict__ tri_uv, const int32_t* __restrict__ rows,
+                                             int T, int W, int H, int32_t* __restrict__ planeidx, int item) {
+    const int lane = threadIdx.x & 31;
+    // triangle of this chunk: the last t with rows[t] <= item
+    int lo = 0, hi = T - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(rows + mid) <= item) lo = mid; else hi = mid - 1;
+    }
+    const int t = lo;
+    const int c = item - __ldg(rows + t);
+    const int32_t* q = tri_uv + 6 * (size_t)t;
+    int x[3] = {__ldg(q), __ldg(q + 2), __ldg(q + 4)};
+    int y[3] = {__ldg(q + 1), __ldg(q + 3), __ldg(q + 5)};
+    const long long o = (long long)(x[1] - x[0]) * (y[2] - y[0]) - (long long)(y[1] - y[0]) * (x[2] - x[0]);
+    if (o < 0) {  // positive orientation
+        int s = x[1]; x[1] = x[2]; x[2] = s;
+        s = y[1]; y[1] = y[2]; y[2] = s;
+    }
+    long long A[3], B[3], C[3];
+    int bias[3];
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+        const int ax = x[e], ay = y[e], bx = x[(e + 1) % 3], by = y[(e + 1) % 3];
+        const int dx = bx - ax, dy = by - ay;
+        A[e] = -dy;
+        B[e] = dx;
+        C[e] = (long long)dy * ax - (long long)dx * ay;
+        bias[e] = ((dy == 0 && dx > 0) || dy < 0) ? 0 : 1;  // top or left edges keep E == 0
+    }
+    const int ymin = max(0, min(y[0], min(y[1], y[2])));
+    const int ymax = min(H - 1, max(y[0], max(y[1], y[2])));
+    const int v0 = ymin + c * kRasterRows, v1 = min(ymax, v0 + kRasterRows - 1);
+    for (int v = v0; v <= v1; v++) {
+        long long ulo = 0, uhi = W - 1;
+#pragma unroll
+        for (int e = 0; e < 3; e++) {
+            const long long R = bias[e] - B[e] * v - C[e];  // need A u >= R
+            if (A[e] > 0) ulo = max(ulo, -floordiv_pos(-R, A[e]));
+            else if (A[e] < 0) uhi = min(uhi, floordiv_pos(-R, -A[e]));
+            else if (R > 0) uhi = -1;
+        }
+        int32_t* row = planeidx + (size_t)v * W;
+        for (long long u = ulo + lane; u <= uhi; u += 32) row[u] = t;
+    }
+}
+
+__device__ __forceinline__ void raster_spans_body(const PairDev& P, int local) {
+    const int item = local * 8 + (threadIdx.x >> 5);
+    if (item >= P.raster_items) return;
+    raster_chunk(P.tri_uv, P.tri_rows, P.T, P.W, P.H, P.planeidx, item);
+}
+
+__global__ void __launch_bounds__(256) k_raster_spans(PairBatch b) {
+#define BODY(P, l) raster_spans_body(P, l)
+    FOR_EACH_ITEM(b, BODY)
+#undef BODY
+}
+
+// Chunk prefix on the device (one block), for callers without a host copy of
+// the triangles.
+__global__ void __launch_bounds__(1024) k_raster_prefix(const int32_t* __restrict__ tri_uv, int T, int H,
+                                                        int32_t* __restrict__ rows) {
     __shared__ int warp_sums[32];
-    const int n = P.tiles_x * P.tiles_y;
-    const int chunk = (n + blockDim.x - 1) / blockDim.x;
-    const int a = min(n, (int)threadIdx.x * chunk), e = min(n, a + chunk);
+    const int chunk = (T + blockDim.x - 1) / blockDim.x;
+    const int a = min(T, (int)threadIdx.x * chunk), e = min(T, a + chunk);
+    auto count = [&](int t) {
+        const int32_t* q = tri_uv + 6 * (size_t)t;
+        const int y0 = max(0, min(q[1], min(q[3], q[5])));
+        const int y1 = min(H - 1, max(q[1], max(q[3], q[5])));
+        return y1 >= y0 ? (y1 - y0) / kRasterRows + 1 : 0;
+    };
     int s = 0;
-    for (int i = a; i < e; i++) s += P.tile_cnt[i];
-    // exclusive scan of s across the block
+    for (int t = a; t < e; t++) s += count(t);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int x = s;
 #pragma unroll
@@ -388,100 +464,21 @@ __device__ __forceinline__ void raster_scan_body(const PairDev& P, int) {
     }
     __syncthreads();
     int run = x - s + (w > 0 ? warp_sums[w - 1] : 0);
-    for (int i = a; i < e; i++) {
-        P.tile_off[i] = run;
-        run += P.tile_cnt[i];
-        P.tile_cnt[i] = 0;
+    for (int t = a; t < e; t++) {
+        rows[t] = run;
+        run += count(t);
     }
-    if (threadIdx.x == blockDim.x - 1) P.tile_off[n] = run;
-    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) rows[T] = run;
 }
 
-__global__ void __launch_bounds__(1024) k_raster_scan(PairBatch b) {
-#define BODY(P, l) raster_scan_body(P, l)
-    FOR_EACH_ITEM(b, BODY)
-#undef BODY
-}
-
-__device__ __forceinline__ void raster_fill_body(const PairDev& P, int local) {
-    const int t = local * 256 + threadIdx.x;
-    if (t >= P.T) return;
-    int tx0, tx1, ty0, ty1;
-    tri_tiles(P.tri_uv + 6 * (size_t)t, P.W, P.H, tx0, tx1, ty0, ty1);
-    for (int ty = ty0; ty <= ty1; ty++)
-        for (int tx = tx0; tx <= tx1; tx++) {
-            const int tile = ty * P.tiles_x + tx;
-            const int pos = atomicAdd(P.tile_cnt + tile, 1);
-            const int at = P.tile_off[tile] + pos;
-            if (at < P.tile_cap) P.tile_list[at] = t;
-        }
-}
-
-__global__ void __launch_bounds__(256) k_raster_fill(PairBatch b) {
-#define BODY(P, l) raster_fill_body(P, l)
-    FOR_EACH_ITEM(b, BODY)
-#undef BODY
-}
-
-struct EdgeSet {  // three edge functions A*u + B*v + C >= bias, and the id
-    int A[3], B[3], C[3];
-    int bias;     // bit e set: edge e needs E >= 1 (not a top or left edge)
-    int id;
-};
-
-__device__ __forceinline__ void raster_pixels_body(const PairDev& P, int local) {
-    __shared__ EdgeSet s[256];
-    const int tile = local;
-    const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
-    const int u = tx * kRasterTile + (threadIdx.x % kRasterTile);
-    const int v = ty * kRasterTile + (threadIdx.x / kRasterTile);
-    const int beg = min(P.tile_off[tile], P.tile_cap), end = min(P.tile_off[tile + 1], P.tile_cap);
-    int hit = -1;
-    for (int base = beg; base < end; base += 256) {
-        const int i = base + threadIdx.x;
-        if (i < end) {
-            const int t = P.tile_list[i];
-            const int32_t* q = P.tri_uv + 6 * (size_t)t;
-            int x[3] = {q[0], q[2], q[4]}, y[3] = {q[1], q[3], q[5]};
-            const long long o = (long long)(x[1] - x[0]) * (y[2] - y[0]) - (long long)(y[1] - y[0]) * (x[2] - x[0]);
-            if (o < 0) {  // make the orientation positive
-                int tx_ = x[1]; x[1] = x[2]; x[2] = tx_;
-                int ty_ = y[1]; y[1] = y[2]; y[2] = ty_;
-            }
-            EdgeSet e;
-            e.bias = 0;
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                const int ax = x[k], ay = y[k], bx = x[(k + 1) % 3], by = y[(k + 1) % 3];
-                const int dx = bx - ax, dy = by - ay;
-                // E(u, v) = dx * (v - ay) - dy * (u - ax)
-                e.A[k] = -dy;
-                e.B[k] = dx;
-                e.C[k] = dy * ax - dx * ay;
-                const bool tl = (dy == 0 && dx > 0) || dy < 0;
-                if (!tl) e.bias |= 1 << k;
-            }
-            e.id = t;
-            s[threadIdx.x] = e;
-        }
-        __syncthreads();
-        const int m = min(256, end - base);
-        for (int j = 0; j < m; j++) {
-            const EdgeSet& e = s[j];
-            const int e0 = e.A[0] * u + e.B[0] * v + e.C[0];
-            const int e1 = e.A[1] * u + e.B[1] * v + e.C[1];
-            const int e2 = e.A[2] * u + e.B[2] * v + e.C[2];
-            if (e0 >= (e.bias & 1) && e1 >= ((e.bias >> 1) & 1) && e2 >= ((e.bias >> 2) & 1)) hit = e.id;
-        }
-        __syncthreads();
-    }
-    if (u < P.W && v < P.H) P.planeidx[(size_t)v * P.W + u] = hit;
-}
-
-__global__ void __launch_bounds__(256) k_raster_pixels(PairBatch b) {
-#define BODY(P, l) raster_pixels_body(P, l)
-    FOR_EACH_ITEM(b, BODY)
-#undef BODY
+// Persistent spans kernel whose item count is read from the device prefix.
+__global__ void __launch_bounds__(256) k_raster_spans_dev(const int32_t* __restrict__ tri_uv,
+                                                          const int32_t* __restrict__ rows, int T, int W, int H,
+                                                          int32_t* __restrict__ planeidx) {
+    const int total = __ldg(rows + T);
+    const int nw = gridDim.x * 8;
+    for (int item = blockIdx.x * 8 + (threadIdx.x >> 5); item < total; item += nw)
+        raster_chunk(tri_uv, rows, T, W, H, planeidx, item);
 }
 
 // ---------------------------------------------------------------- fused validate (Alg. 2 + Alg. 3)
@@ -489,69 +486,127 @@ __global__ void __launch_bounds__(256) k_raster_pixels(PairBatch b) {
 // Hamming cost at the rounded disparity, the strict-< update of (D_f, C_f),
 // the validation mask, and the per-cell C_g / C_b keys reduced in shared
 // memory before one global atomicMin per cell and tile.
-constexpr int kMaxLocalCells = 256;
+// Tile: 128 x 8 pixels, one warp per row, lane l handles u0 + l + 32 j for
+// j = 0..3, so every warp access is 128 contiguous bytes (no alignment
+// assumption on W) and each thread keeps four independent load chains.
+constexpr int kVW = 128, kVH = 8, kVJ = kVW / 32;
+constexpr int kMaxLocalCells = kVW * kVH;
+
+__device__ __forceinline__ uint32_t cell_div(uint32_t x, int shift, uint32_t magic) {
+    return shift >= 0 ? (x >> shift) : __umulhi(x, magic);
+}
 
 __device__ __forceinline__ void validate_body(const PairDev& P, int local, const Params& prm) {
     __shared__ uint32_t s_g[kMaxLocalCells], s_b[kMaxLocalCells];
-    const int W = P.W, H = P.H;
-    const int tx_n = (W + kTileW - 1) / kTileW;
-    const int u0 = (local % tx_n) * kTileW, v0 = (local / tx_n) * kTileH;
-    const int lx = threadIdx.x % kTileW, ly = threadIdx.x / kTileW;
-    const int u = u0 + lx, v = v0 + ly;
-    const bool cells = P.cg_key != nullptr;
-    const int sz = P.sz;
-    const int cx0 = u0 / sz, cy0 = v0 / sz;
-    const int ncx = min(u0 + kTileW - 1, W - 1) / sz - cx0 + 1;
-    const int ncy = min(v0 + kTileH - 1, H - 1) / sz - cy0 + 1;
+    // descriptor fields in registers: later stores cannot alias them
+    const int W = P.W, H = P.H, sz = P.sz, Wc = P.Wc, first = P.first_pass;
+    const int shift = P.sz_shift;
+    const uint32_t magic = P.sz_magic;
+    const uint32_t* __restrict__ omega = P.omega;
+    const int32_t* __restrict__ pidx = P.planeidx;
+    const float* __restrict__ abc = P.abc;
+    const uint32_t* __restrict__ cLp = P.cL;
+    const uint32_t* __restrict__ cRp = P.cR;
+    float* __restrict__ Df = P.Df;
+    uint8_t* __restrict__ Cf = P.Cf;
+    uint8_t* __restrict__ mask = P.mask;
+    uint32_t* __restrict__ cg = P.cg_key;
+    uint32_t* __restrict__ cb = P.cb_key;
+    const int t_lo = prm.t_lo, t_hi = prm.t_hi;
+    const bool cells = cg != nullptr;
+
+    const int tx_n = (W + kVW - 1) / kVW;
+    const int u0 = (local % tx_n) * kVW, v0 = (local / tx_n) * kVH;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int v = v0 + w;
+    const int cx0 = cell_div(u0, shift, magic), cy0 = cell_div(v0, shift, magic);
+    const int ncx = cell_div(min(u0 + kVW - 1, W - 1), shift, magic) - cx0 + 1;
+    const int ncy = cell_div(min(v0 + kVH - 1, H - 1), shift, magic) - cy0 + 1;
     if (cells) {
         for (int i = threadIdx.x; i < ncx * ncy; i += blockDim.x) { s_g[i] = kNoKey; s_b[i] = kNoKey; }
         __syncthreads();
     }
-    if (u < W && v < H) {
-        const size_t p = (size_t)v * W + u;
-        const bool om = (__ldg(P.omega + (size_t)v * ((W + 31) >> 5) + (u >> 5)) >> (u & 31)) & 1u;
-        uint8_t m = om ? 1 : 0;
-        int cost = -1;
-        float d = 0.0f;
-        if (om) {
-            const int t = __ldg(P.planeidx + p);
-            if (t >= 0) {
-                const float a = __ldg(P.abc + 3 * t), bb = __ldg(P.abc + 3 * t + 1), c = __ldg(P.abc + 3 * t + 2);
-                d = __fmaf_rn(a, (float)u, __fmaf_rn(bb, (float)v, c));
-                const float kf = rintf(d);
+    if (v < H) {
+        const size_t row = (size_t)v * W;
+        const size_t wrow = (size_t)v * ((W + 31) >> 5) + (u0 >> 5);
+        int t[kVJ];
+        uint32_t cl[kVJ];
+        int cf[kVJ];
+        bool om[kVJ];
+#pragma unroll
+        for (int j = 0; j < kVJ; j++) {  // independent loads first
+            const int u = u0 + lane + 32 * j;
+            const bool in = u < W;
+            om[j] = in && ((__ldg(omega + wrow + j) >> lane) & 1u);
+            t[j] = om[j] ? __ldg(pidx + row + u) : -1;
+            cl[j] = om[j] ? __ldg(cLp + row + u) : 0u;
+            cf[j] = (!first && om[j]) ? (int)Cf[row + u] : t_hi;
+        }
+        float d[kVJ];
+        int cost[kVJ];
+#pragma unroll
+        for (int j = 0; j < kVJ; j++) {
+            const int u = u0 + lane + 32 * j;
+            d[j] = 0.0f;
+            cost[j] = -1;
+            if (t[j] >= 0) {
+                const float a = __ldg(abc + 3 * t[j]), b = __ldg(abc + 3 * t[j] + 1), c = __ldg(abc + 3 * t[j] + 2);
+                d[j] = __fmaf_rn(a, (float)u, __fmaf_rn(b, (float)v, c));
+                const float kf = rintf(d[j]);
                 const float col = (float)u - kf;
-                if (col >= 2.0f && col <= (float)(W - 3)) {
-                    const int k = (int)kf;
-                    cost = __popc(__ldg(P.cL + p) ^ __ldg(P.cR + p - k));
-                    m |= 2;
-                    if (cost < prm.t_lo) m |= 4;
-                    if (cost > prm.t_hi) m |= 8;
+                if (col >= 2.0f && col <= (float)(W - 3)) cost[j] = __popc(cl[j] ^ __ldg(cRp + row + (int)col));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kVJ; j++) {
+            const int u = u0 + lane + 32 * j;
+            if (u >= W) continue;
+            const size_t p = row + u;
+            const int cj = cost[j];
+            uint8_t m = om[j] ? 1 : 0;
+            if (cj >= 0) m |= 2 | (cj < t_lo ? 4 : 0) | (cj > t_hi ? 8 : 0);
+            if (first) {
+                const bool upd = cj >= 0 && cj < t_hi;
+                Df[p] = upd ? d[j] : 0.0f;
+                Cf[p] = (uint8_t)(upd ? cj : t_hi);
+            } else if (cj >= 0 && cj < cf[j]) {
+                Df[p] = d[j];
+                Cf[p] = (uint8_t)cj;
+            }
+            if (mask) mask[p] = m;
+        }
+        if (cells) {
+            const int ly = cell_div(v, shift, magic) - cy0;
+            const bool warp_cell = sz >= 32 && (sz & 31) == 0;  // a warp's 32 pixels share one cell
+#pragma unroll
+            for (int j = 0; j < kVJ; j++) {
+                const int u = u0 + lane + 32 * j;
+                const int cj = cost[j];
+                const uint32_t p = (uint32_t)(row + u);
+                uint32_t kg = (cj >= 0 && cj < t_lo) ? (((uint32_t)cj << 27) | p) : kNoKey;
+                uint32_t kb = (cj > t_hi) ? (((uint32_t)(24 - cj) << 27) | p) : kNoKey;
+                const int lc = ly * ncx + ((int)cell_div(min(u, W - 1), shift, magic) - cx0);
+                if (warp_cell) {
+                    kg = __reduce_min_sync(0xffffffffu, kg);
+                    kb = __reduce_min_sync(0xffffffffu, kb);
+                    if (lane == 0) {
+                        if (kg != kNoKey) atomicMin(s_g + lc, kg);
+                        if (kb != kNoKey) atomicMin(s_b + lc, kb);
+                    }
+                } else {
+                    if (kg != kNoKey) atomicMin(s_g + lc, kg);
+                    if (kb != kNoKey) atomicMin(s_b + lc, kb);
                 }
             }
-        }
-        if (P.first_pass) {
-            const bool upd = cost >= 0 && cost < prm.t_hi;
-            P.Df[p] = upd ? d : 0.0f;
-            P.Cf[p] = (uint8_t)(upd ? cost : prm.t_hi);
-        } else if (cost >= 0) {
-            if (cost < (int)P.Cf[p]) {
-                P.Df[p] = d;
-                P.Cf[p] = (uint8_t)cost;
-            }
-        }
-        if (P.mask) P.mask[p] = m;
-        if (cells && (m & 12)) {
-            const int lc = (v / sz - cy0) * ncx + (u / sz - cx0);
-            if (m & 4) atomicMin(s_g + lc, ((uint32_t)cost << 27) | (uint32_t)p);
-            if (m & 8) atomicMin(s_b + lc, ((uint32_t)(24 - cost) << 27) | (uint32_t)p);
         }
     }
     if (cells) {
         __syncthreads();
         for (int i = threadIdx.x; i < ncx * ncy; i += blockDim.x) {
-            const size_t cell = (size_t)(cy0 + i / ncx) * P.Wc + (cx0 + i % ncx);
-            if (s_g[i] != kNoKey) atomicMin(P.cg_key + cell, s_g[i]);
-            if (s_b[i] != kNoKey) atomicMin(P.cb_key + cell, s_b[i]);
+            const int iy = i / ncx, ix = i - iy * ncx;
+            const size_t cell = (size_t)(cy0 + iy) * Wc + (cx0 + ix);
+            if (s_g[i] != kNoKey) atomicMin(cg + cell, s_g[i]);
+            if (s_b[i] != kNoKey) atomicMin(cb + cell, s_b[i]);
         }
         __syncthreads();
     }
@@ -596,6 +651,21 @@ __global__ void __launch_bounds__(256) k_resample(PairBatch b, Params prm) {
 #undef BODY
 }
 
+// Cell records of a pass start empty (0xFFFFFFFF) for the atomic minimum.
+__device__ __forceinline__ void fill_cells_body(const PairDev& P, int local) {
+    const size_t n = (size_t)P.Wc * P.Hc;
+    for (size_t i = (size_t)local * 4096 + threadIdx.x; i < n && i < (size_t)(local + 1) * 4096; i += blockDim.x) {
+        P.cg_key[i] = kNoKey;
+        P.cb_key[i] = kNoKey;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_fill_cells(PairBatch b) {
+#define BODY(P, l) fill_cells_body(P, l)
+    FOR_EACH_ITEM(b, BODY)
+#undef BODY
+}
+
 __global__ void k_fill_u32(uint32_t* p, uint32_t value, size_t n) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = value;
 }
@@ -621,24 +691,22 @@ cudaError_t launch_match_kp(const PairBatch& b, const Params& prm, cudaStream_t 
     k_match_kp<<<grid_for(b.total, 8), 256, 0, s>>>(b, prm);
     return cudaGetLastError();
 }
-cudaError_t launch_raster_count(const PairBatch& b, cudaStream_t s) {
+cudaError_t launch_raster_clear(const PairBatch& b, cudaStream_t s) {
     if (b.total <= 0) return cudaSuccess;
-    k_raster_count<<<grid_for(b.total, 8), 256, 0, s>>>(b);
+    k_raster_clear<<<grid_for(b.total, 8), 256, 0, s>>>(b);
     return cudaGetLastError();
 }
-cudaError_t launch_raster_scan(const PairBatch& b, cudaStream_t s) {
+cudaError_t launch_raster_spans(const PairBatch& b, cudaStream_t s) {
     if (b.total <= 0) return cudaSuccess;
-    k_raster_scan<<<grid_for(b.total, 2), 1024, 0, s>>>(b);
+    k_raster_spans<<<grid_for(b.total, 8), 256, 0, s>>>(b);
     return cudaGetLastError();
 }
-cudaError_t launch_raster_fill(const PairBatch& b, cudaStream_t s) {
-    if (b.total <= 0) return cudaSuccess;
-    k_raster_fill<<<grid_for(b.total, 8), 256, 0, s>>>(b);
-    return cudaGetLastError();
-}
-cudaError_t launch_raster_pixels(const PairBatch& b, cudaStream_t s) {
-    if (b.total <= 0) return cudaSuccess;
-    k_raster_pixels<<<grid_for(b.total, 8), 256, 0, s>>>(b);
+cudaError_t launch_raster_device_prefix(const PairDev& p, cudaStream_t s) {
+    if (p.T <= 0) return cudaSuccess;
+    k_raster_prefix<<<1, 1024, 0, s>>>(p.tri_uv, p.T, p.H, p.tri_rows);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_raster_spans_dev<<<sm_count() * 8, 256, 0, s>>>(p.tri_uv, p.tri_rows, p.T, p.W, p.H, p.planeidx);
     return cudaGetLastError();
 }
 cudaError_t launch_validate(const PairBatch& b, const Params& prm, cudaStream_t s) {
@@ -649,6 +717,11 @@ cudaError_t launch_validate(const PairBatch& b, const Params& prm, cudaStream_t 
 cudaError_t launch_resample(const PairBatch& b, const Params& prm, cudaStream_t s) {
     if (b.total <= 0) return cudaSuccess;
     k_resample<<<grid_for(b.total, 8), 256, 0, s>>>(b, prm);
+    return cudaGetLastError();
+}
+cudaError_t launch_fill_cells(const PairBatch& b, cudaStream_t s) {
+    if (b.total <= 0) return cudaSuccess;
+    k_fill_cells<<<grid_for(b.total, 8), 256, 0, s>>>(b);
     return cudaGetLastError();
 }
 cudaError_t launch_fill_u32(uint32_t* p, uint32_t value, size_t n, cudaStream_t s) {

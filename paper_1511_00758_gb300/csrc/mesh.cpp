@@ -233,17 +233,15 @@ void planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float*
     }
 }
 
-long long raster_bin_entries(const int32_t* q, int T, int W, int H) {
-    long long s = 0;
+int raster_row_chunks(const int32_t* q, int T, int H, int32_t* rows) {
+    int s = 0;
     for (int t = 0; t < T; t++, q += 6) {
-        int x0 = std::min(q[0], std::min(q[2], q[4])), x1 = std::max(q[0], std::max(q[2], q[4]));
-        int y0 = std::min(q[1], std::min(q[3], q[5])), y1 = std::max(q[1], std::max(q[3], q[5]));
-        x0 = std::max(x0, 0);
-        y0 = std::max(y0, 0);
-        x1 = std::min(x1, W - 1);
-        y1 = std::min(y1, H - 1);
-        s += (long long)(x1 / kRasterTile - x0 / kRasterTile + 1) * (y1 / kRasterTile - y0 / kRasterTile + 1);
+        rows[t] = s;
+        const int y0 = std::max(0, std::min(q[1], std::min(q[3], q[5])));
+        const int y1 = std::min(H - 1, std::max(q[1], std::max(q[3], q[5])));
+        if (y1 >= y0) s += (y1 - y0) / kRasterRows + 1;
     }
+    rows[T] = s;
     return s;
 }
 

@@ -113,8 +113,8 @@ def _tri_uv(P, tri):
 
 def _gpu_raster(P, tri, W, H):
     tuv = _tri_uv(P, tri)
-    nbytes = S.raster_scratch_bytes(tuv, len(tri), W, H)
-    scratch = torch.empty(nbytes, dtype=torch.uint8, device=DEV)
+    nbytes = S.raster_scratch_bytes(len(tri))
+    scratch = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=DEV)
     pidx = torch.empty((H, W), dtype=torch.int32, device=DEV)
     S.raster(_t(tuv) if len(tri) else None, len(tri), W, H, pidx, scratch, nbytes)
     _sync()
@@ -216,8 +216,9 @@ def test_validate(oracle_mod, name, sz, first):
     assert np.array_equal(xd.cpu().numpy(), want)
 
 
-def _run_ctx(pairs, max_slots=1, host_threads=1, budget=1 << 30):
-    with S.Context(mem_budget_bytes=budget, max_slots=max_slots, host_threads=host_threads, **PRM) as ctx:
+def _run_ctx(pairs, max_slots=1, host_threads=1, budget=1 << 30, window_us=0):
+    with S.Context(mem_budget_bytes=budget, max_slots=max_slots, host_threads=host_threads,
+                   batch_window_us=window_us, **PRM) as ctx:
         tickets = [ctx.submit(_t(p.left), _t(p.right), p.left.shape[1], p.left.shape[0], p.dmax, p.iters, p.cell)
                    for p in pairs]
         outs = []
@@ -281,12 +282,13 @@ def test_batched_serving_matches_solo(oracle_mod):
     pairs = [scenes.make_pair("polygon", 320, 240, 500 + i, 64, 3, 16, n_poly=10) for i in range(3)]
     pairs += [scenes.make_pair("driving", 400, 150, 600 + i, 96, 2, 8, n_box=10) for i in range(3)]
     solo = [_run_ctx([p])[0] for p in pairs]
-    mixed = _run_ctx(pairs, max_slots=4, host_threads=3)
-    for a, b in zip(solo, mixed):
-        for k in ("D_f", "C_f", "mask", "planeidx"):
-            assert torch.equal(a[k], b[k]), k
-        for x, y in zip(a["support"], b["support"]):
-            assert np.array_equal(x, y)
+    for slots, threads, window in ((4, 3, 0), (6, 2, 2000)):
+        mixed = _run_ctx(pairs, max_slots=slots, host_threads=threads, window_us=window)
+        for a, b in zip(solo, mixed):
+            for k in ("D_f", "C_f", "mask", "planeidx"):
+                assert torch.equal(a[k], b[k]), k
+            for x, y in zip(a["support"], b["support"]):
+                assert np.array_equal(x, y)
 
 
 def test_host_input_pointers(oracle_mod):
