@@ -291,6 +291,10 @@ bool valid_size(int w, int h) {
     return w >= 5 && h >= 5 && w <= 8192 && h <= 8192 && (long long)w * h < (1ll << 27);
 }
 
+// Staging layout of one mesh: tri_uv (6 int32), abc (3 fp32) per triangle,
+// T + 1 chunk offsets, then the triangle of every raster chunk.
+size_t tri_stage_bytes(int T, int items) { return (size_t)T * 40 + 4 + (size_t)items * 4; }
+
 // Support set -> triangles, planes and raster inputs in the request's pinned
 // staging buffer.  Runs on a pool thread.
 int mesh_step(Request& r) {
@@ -307,18 +311,24 @@ int mesh_step(Request& r) {
     std::vector<int32_t> tri((size_t)3 * cap);
     int T = n >= 3 ? delaunay(P.data(), n, tri.data(), cap) : 0;
     if (T < 0) return STEREO_E_INTERNAL;
-    if (!r.st_tri.ensure((size_t)T * 40 + 64)) return STEREO_E_NOMEM;
+    std::vector<int32_t> tuv_v((size_t)6 * T), rows_v((size_t)T + 1);
+    for (int t = 0; t < T; t++)
+        for (int k = 0; k < 3; k++) {
+            tuv_v[6 * t + 2 * k] = P[2 * tri[3 * t + k]];
+            tuv_v[6 * t + 2 * k + 1] = P[2 * tri[3 * t + k] + 1];
+        }
+    const int items = raster_row_chunks(tuv_v.data(), T, r.H, rows_v.data());
+    if (!r.st_tri.ensure(tri_stage_bytes(T, items))) return STEREO_E_NOMEM;
     int32_t* tuv = r.st_tri.as<int32_t>();
     float* abc = (float*)(tuv + (size_t)6 * T);
     int32_t* rows = (int32_t*)(abc + (size_t)3 * T);
-    for (int t = 0; t < T; t++)
-        for (int k = 0; k < 3; k++) {
-            tuv[6 * t + 2 * k] = P[2 * tri[3 * t + k]];
-            tuv[6 * t + 2 * k + 1] = P[2 * tri[3 * t + k] + 1];
-        }
+    int32_t* item_tri = rows + T + 1;
+    std::memcpy(tuv, tuv_v.data(), sizeof(int32_t) * 6 * (size_t)T);
+    std::memcpy(rows, rows_v.data(), sizeof(int32_t) * ((size_t)T + 1));
+    raster_item_tri(rows, T, item_tri);
     planes(P.data(), D.data(), tri.data(), T, abc);
     r.T = T;
-    r.raster_items = raster_row_chunks(tuv, T, r.H, rows);
+    r.raster_items = items;
     r.n_support.push_back(n);
     r.n_tri.push_back(T);
     for (const auto& s : r.S) {
@@ -547,7 +557,7 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
     for (Request* r : seed.reqs) seed_px += (double)r->W * r->H;
     // iteration group: triangle buffers, uploads, cell resets
     for (Request* r : iter.reqs) {
-        const size_t tri_bytes = align_up((size_t)r->T * 40 + 64, 256);
+        const size_t tri_bytes = align_up(tri_stage_bytes(r->T, r->raster_items) + 64, 256);
         if (tri_bytes > r->tri_block_bytes) {
             std::lock_guard<std::mutex> g(c->mu);
             c->arena.release(r->tri_block);
@@ -559,6 +569,7 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         r->dev.tri_uv = (const int32_t*)tb;
         r->dev.abc = (const float*)(tb + (size_t)r->T * 24);
         r->dev.tri_rows = (int32_t*)(tb + (size_t)r->T * 36);
+        r->dev.item_tri = r->dev.tri_rows + r->T + 1;
         r->dev.raster_items = r->raster_items;
         r->dev.T = r->T;
         set_cell_size(r->dev, r->sz);
@@ -569,7 +580,9 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         const double px = (double)r->W * r->H;
         iter_px += px;
         validate_bytes += px * (r->dev.first_pass ? 18.125 : 19.125);
-        if (r->T > 0) CK(cudaMemcpyAsync((void*)r->dev.tri_uv, r->st_tri.p, (size_t)r->T * 40 + 4, cudaMemcpyHostToDevice, s));
+        if (r->T > 0)
+            CK(cudaMemcpyAsync((void*)r->dev.tri_uv, r->st_tri.p, tri_stage_bytes(r->T, r->raster_items),
+                               cudaMemcpyHostToDevice, s));
         if (r->resample_now) cells_bytes += 8.0 * r->dev.Wc * r->dev.Hc;
     }
     // descriptors

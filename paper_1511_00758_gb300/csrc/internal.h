@@ -30,6 +30,7 @@ struct PairDev {
     const int32_t* tri_uv;    // T * 6
     const float* abc;         // T * 3
     int32_t* tri_rows;        // T + 1: exclusive prefix of 8-row chunks per triangle
+    const int32_t* item_tri;  // raster_items: triangle of each chunk
     int32_t* planeidx;        // W*H
     float* Df;                // W*H
     uint8_t* Cf;              // W*H
@@ -94,5 +95,7 @@ void planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float*
 // Exclusive prefix of 8-row chunks of each triangle's clipped row range
 // (rows[T + 1]); returns the total.
 int raster_row_chunks(const int32_t* tri_uv, int T, int H, int32_t* rows);
+// Triangle of every chunk (items = rows[T] entries).
+void raster_item_tri(const int32_t* rows, int T, int32_t* item_tri);
 
 }  // namespace stereo

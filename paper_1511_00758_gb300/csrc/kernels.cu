@@ -370,17 +370,16 @@ __global__ void __launch_bounds__(256) k_raster_clear(PairBatch b) {
 #undef BODY
 }
 
-__device__ __forceinline__ void raster_chunk(const int32_t* __restrict__ tri_uv, const int32_t* __restrict__ rows,
-                                             int T, int W, int H, int32_t* __restrict__ planeidx, int item) {
+__device__ __forceinline__ int floordiv32(int a, int b) {  // b > 0
+    return a >= 0 ? a / b : -((-a + b - 1) / b);
+}
+
+// Chunk c (8 rows) of triangle t.  Lanes 0..7 bound one row each in exact
+// int32 arithmetic (|R| < 2^28 for coordinates below 8192); the warp then
+// writes the rows with lanes striding the columns.
+__device__ __forceinline__ void raster_chunk_tc(const int32_t* __restrict__ tri_uv, int t, int c, int W, int H,
+                                                int32_t* __restrict__ planeidx) {
     const int lane = threadIdx.x & 31;
-    // triangle of this chunk: the last t with rows[t] <= item
-    int lo = 0, hi = T - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(rows + mid) <= item) lo = mid; else hi = mid - 1;
-    }
-    const int t = lo;
-    const int c = item - __ldg(rows + t);
     const int32_t* q = tri_uv + 6 * (size_t)t;
     int x[3] = {__ldg(q), __ldg(q + 2), __ldg(q + 4)};
     int y[3] = {__ldg(q + 1), __ldg(q + 3), __ldg(q + 5)};
@@ -389,38 +388,46 @@ __device__ __forceinline__ void raster_chunk(const int32_t* __restrict__ tri_uv,
         int s = x[1]; x[1] = x[2]; x[2] = s;
         s = y[1]; y[1] = y[2]; y[2] = s;
     }
-    long long A[3], B[3], C[3];
-    int bias[3];
+    const int ymin = max(0, min(y[0], min(y[1], y[2])));
+    const int ymax = min(H - 1, max(y[0], max(y[1], y[2])));
+    const int v0 = ymin + c * kRasterRows;
+    const int vr = v0 + (lane & (kRasterRows - 1));
+    int lo = 0, hi = W - 1;
 #pragma unroll
     for (int e = 0; e < 3; e++) {
         const int ax = x[e], ay = y[e], bx = x[(e + 1) % 3], by = y[(e + 1) % 3];
         const int dx = bx - ax, dy = by - ay;
-        A[e] = -dy;
-        B[e] = dx;
-        C[e] = (long long)dy * ax - (long long)dx * ay;
-        bias[e] = ((dy == 0 && dx > 0) || dy < 0) ? 0 : 1;  // top or left edges keep E == 0
+        // E(u, v) = -dy u + dx (v - ay) + dy ax >= bias  <=>  -dy u >= R
+        const int bias = ((dy == 0 && dx > 0) || dy < 0) ? 0 : 1;  // top or left edges keep E == 0
+        const int R = bias - dx * (vr - ay) - dy * ax;
+        if (dy < 0) lo = max(lo, -floordiv32(-R, -dy));      // u >= ceil(R / -dy)
+        else if (dy > 0) hi = min(hi, floordiv32(-R, dy));   // u <= floor(-R / dy)
+        else if (R > 0) hi = -1;
     }
-    const int ymin = max(0, min(y[0], min(y[1], y[2])));
-    const int ymax = min(H - 1, max(y[0], max(y[1], y[2])));
-    const int v0 = ymin + c * kRasterRows, v1 = min(ymax, v0 + kRasterRows - 1);
-    for (int v = v0; v <= v1; v++) {
-        long long ulo = 0, uhi = W - 1;
-#pragma unroll
-        for (int e = 0; e < 3; e++) {
-            const long long R = bias[e] - B[e] * v - C[e];  // need A u >= R
-            if (A[e] > 0) ulo = max(ulo, -floordiv_pos(-R, A[e]));
-            else if (A[e] < 0) uhi = min(uhi, floordiv_pos(-R, -A[e]));
-            else if (R > 0) uhi = -1;
-        }
-        int32_t* row = planeidx + (size_t)v * W;
-        for (long long u = ulo + lane; u <= uhi; u += 32) row[u] = t;
+    const int nrows = min(kRasterRows, ymax - v0 + 1);
+    for (int r = 0; r < nrows; r++) {
+        const int a = __shfl_sync(0xffffffffu, lo, r), b = __shfl_sync(0xffffffffu, hi, r);
+        int32_t* row = planeidx + (size_t)(v0 + r) * W;
+        for (int u = a + lane; u <= b; u += 32) row[u] = t;
     }
+}
+
+__device__ __forceinline__ void raster_chunk(const int32_t* __restrict__ tri_uv, const int32_t* __restrict__ rows,
+                                             int T, int W, int H, int32_t* __restrict__ planeidx, int item) {
+    // triangle of this chunk: the last t with rows[t] <= item
+    int lo = 0, hi = T - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(rows + mid) <= item) lo = mid; else hi = mid - 1;
+    }
+    raster_chunk_tc(tri_uv, lo, item - __ldg(rows + lo), W, H, planeidx);
 }
 
 __device__ __forceinline__ void raster_spans_body(const PairDev& P, int local) {
     const int item = local * 8 + (threadIdx.x >> 5);
     if (item >= P.raster_items) return;
-    raster_chunk(P.tri_uv, P.tri_rows, P.T, P.W, P.H, P.planeidx, item);
+    const int t = __ldg(P.item_tri + item);
+    raster_chunk_tc(P.tri_uv, t, item - __ldg(P.tri_rows + t), P.W, P.H, P.planeidx);
 }
 
 __global__ void __launch_bounds__(256) k_raster_spans(PairBatch b) {
@@ -537,10 +544,13 @@ __device__ __forceinline__ void validate_body(const PairDev& P, int local, const
         for (int j = 0; j < kVJ; j++) {  // independent loads first
             const int u = u0 + lane + 32 * j;
             const bool in = u < W;
-            om[j] = in && ((__ldg(omega + wrow + j) >> lane) & 1u);
-            t[j] = om[j] ? __ldg(pidx + row + u) : -1;
-            cl[j] = om[j] ? __ldg(cLp + row + u) : 0u;
-            cf[j] = (!first && om[j]) ? (int)Cf[row + u] : t_hi;
+            // all first-level loads issue together: one memory round trip
+            const uint32_t ow = __ldg(omega + wrow + j);
+            const int tj = in ? __ldg(pidx + row + u) : -1;
+            cl[j] = in ? __ldg(cLp + row + u) : 0u;
+            cf[j] = (!first && in) ? (int)Cf[row + u] : t_hi;
+            om[j] = in && ((ow >> lane) & 1u);
+            t[j] = om[j] ? tj : -1;
         }
         float d[kVJ];
         int cost[kVJ];

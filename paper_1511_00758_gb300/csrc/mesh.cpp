@@ -58,22 +58,37 @@ struct Mesh {
         const int64_t la = ax * ax + ay * ay, lb = bx * bx + by * by, lc = cx * cx + cy * cy;
         const int64_t det = la * (bx * cy - by * cx) - lb * (ax * cy - ay * cx) + lc * (ax * by - ay * bx);
         if (det != 0) return det > 0;
-        // cofactors of the lifted column for rows a, b, c, d
-        std::pair<int, int64_t> terms[4] = {{a, orient(b, c, d)}, {b, -orient(a, c, d)},
-                                            {c, orient(a, b, d)}, {d, -orient(a, b, c)}};
-        std::sort(terms, terms + 4, [](const std::pair<int, int64_t>& x, const std::pair<int, int64_t>& y) {
-            return x.first < y.first;
-        });
-        for (const auto& t : terms)
-            if (t.second != 0) return t.second > 0;
+        // cofactors of the lifted column for rows a, b, c, d, taken in
+        // increasing index order until one is non-zero
+        int id[4] = {a, b, c, d};
+        for (int r = 0; r < 4; r++) {
+            int k = 0;
+            for (int q = 1; q < 4; q++)
+                if (id[q] < id[k]) k = q;
+            int64_t cof;
+            switch (k) {
+                case 0: cof = orient(b, c, d); break;
+                case 1: cof = -orient(a, c, d); break;
+                case 2: cof = orient(a, b, d); break;
+                default: cof = -orient(a, b, c); break;
+            }
+            if (cof != 0) return cof > 0;
+            id[k] = 0x7fffffff;
+        }
         return false;
     }
 
+    int ne = 0;  // directed edges in use (4 per quad edge)
+
     int make_edge(int a, int b) {
-        const int e = (int)nxt.size();
-        nxt.resize(e + 4);
-        org.resize(e + 4, -1);
-        dead.push_back(0);
+        const int e = ne;
+        ne += 4;
+        if ((size_t)ne > nxt.size()) {
+            nxt.resize(std::max<size_t>(2 * nxt.size(), 64));
+            org.resize(nxt.size(), -1);
+            dead.resize(nxt.size() / 4, 0);
+        }
+        dead[e >> 2] = 0;
         nxt[e] = e;
         nxt[e + 1] = e + 3;
         nxt[e + 2] = e + 2;
@@ -171,42 +186,54 @@ int delaunay(const int32_t* uv, int n, int32_t* tri, int cap) {
     if (n < 3) return 0;
     Mesh m;
     m.P = uv;
-    m.nxt.reserve((size_t)12 * n);
-    m.org.reserve((size_t)12 * n);
-    m.dead.reserve((size_t)3 * n);
-    std::vector<int> s(n);
-    for (int i = 0; i < n; i++) s[i] = i;
-    std::sort(s.begin(), s.end(), [uv](int a, int b) {
-        if (uv[2 * a] != uv[2 * b]) return uv[2 * a] < uv[2 * b];
-        return uv[2 * a + 1] < uv[2 * b + 1];
-    });
+    m.nxt.resize((size_t)24 * n);
+    m.org.resize((size_t)24 * n, -1);
+    m.dead.resize((size_t)6 * n, 0);
+    // (u, v) order for the divide and conquer: the input is sorted by (v, u),
+    // so a stable counting sort on u gives it in linear time
+    int umax = 0;
+    for (int i = 0; i < n; i++) umax = std::max(umax, uv[2 * i]);
+    std::vector<int> cnt((size_t)umax + 2, 0), s(n);
+    for (int i = 0; i < n; i++) cnt[uv[2 * i] + 1]++;
+    for (int u = 0; u <= umax; u++) cnt[u + 1] += cnt[u];
+    for (int i = 0; i < n; i++) s[cnt[uv[2 * i]]++] = i;
     m.build(s.data(), n);
-    std::vector<int32_t> out;
-    out.reserve((size_t)6 * n);
-    const int ne = (int)m.nxt.size();
+    // faces: each triangle once, from its directed edge leaving the smallest
+    // vertex; bucketed by that vertex, so the output order is lexicographic
+    // after sorting the (at most a few) triangles of each bucket
+    std::vector<int> first(n + 1, 0);
+    std::vector<int32_t> jk;
+    std::vector<int> owner;
+    jk.reserve((size_t)4 * n);
+    owner.reserve((size_t)2 * n);
+    const int ne = m.ne;
     for (int e = 0; e < ne; e += 2) {
         if (m.dead[e >> 2]) continue;
         const int a = m.org[e], b = m.dest(e);
+        if (!(a < b)) continue;
         const int e2 = m.lnext(e);
         const int c = m.dest(e2);
-        if (m.lnext(m.lnext(e2)) != e) continue;
-        if (!(a < b && a < c)) continue;
+        if (!(a < c) || m.lnext(m.lnext(e2)) != e) continue;
         if (!m.ccw(a, b, c)) continue;
-        int t3[3] = {a, b, c};
-        std::sort(t3, t3 + 3);
-        out.insert(out.end(), t3, t3 + 3);
+        owner.push_back(a);
+        jk.push_back(std::min(b, c));
+        jk.push_back(std::max(b, c));
+        first[a + 1]++;
     }
-    const int T = (int)(out.size() / 3);
+    const int T = (int)owner.size();
     if (T > cap) return -9;  // STEREO_E_CAP
-    std::vector<int> order(T);
-    for (int i = 0; i < T; i++) order[i] = i;
-    std::sort(order.begin(), order.end(), [&out](int x, int y) {
-        for (int k = 0; k < 3; k++)
-            if (out[3 * x + k] != out[3 * y + k]) return out[3 * x + k] < out[3 * y + k];
-        return false;
-    });
-    for (int i = 0; i < T; i++)
-        for (int k = 0; k < 3; k++) tri[3 * i + k] = out[3 * order[i] + k];
+    for (int i = 0; i < n; i++) first[i + 1] += first[i];
+    std::vector<int> pos(first.begin(), first.end() - 1);
+    std::vector<uint64_t> key(T);
+    for (int t = 0; t < T; t++) key[pos[owner[t]]++] = ((uint64_t)(uint32_t)jk[2 * t] << 32) | (uint32_t)jk[2 * t + 1];
+    for (int a = 0; a < n; a++) {
+        std::sort(key.begin() + first[a], key.begin() + first[a + 1]);
+        for (int t = first[a]; t < first[a + 1]; t++) {
+            tri[3 * t] = a;
+            tri[3 * t + 1] = (int32_t)(key[t] >> 32);
+            tri[3 * t + 2] = (int32_t)(key[t] & 0xFFFFFFFFu);
+        }
+    }
     return T;
 }
 
@@ -243,6 +270,11 @@ int raster_row_chunks(const int32_t* q, int T, int H, int32_t* rows) {
     }
     rows[T] = s;
     return s;
+}
+
+void raster_item_tri(const int32_t* rows, int T, int32_t* item_tri) {
+    for (int t = 0; t < T; t++)
+        for (int i = rows[t]; i < rows[t + 1]; i++) item_tri[i] = t;
 }
 
 }  // namespace stereo
