@@ -198,45 +198,45 @@ int stereo_delaunay(const int32_t* uv, int n, int32_t* tri, int cap);
  * index order, rounded to fp32.  d: n fp32 support disparities; abc: 3*T. */
 int stereo_planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float* abc);
 
-/* Scratch bytes stereo_raster needs for T triangles: T + 1 int32 row-chunk
- * offsets (rounded up to 256 bytes). */
+/* Scratch bytes stereo_raster needs for T triangles: 2 * (T + 1) int32 of
+ * work lists (rounded up to 256 bytes). */
 size_t stereo_raster_scratch_bytes(int T);
 
-/* Pixel -> triangle lookup table (Sec. III-B).  A pixel (u, v), sampled at
- * integer coordinates, belongs to a triangle when every edge function is
- * positive or zero on a top or left edge; this partitions the hull, and
- * pixels outside it get -1.  The table is built by exact scan conversion
- * (per row, integer floor/ceil bounds of the three edge half-planes).
- * tri_uv: T * 6 int32 vertex coordinates (u0,v0,u1,v1,u2,v2) of triangle t;
- * planeidx: W*H int32 output (16-byte aligned), triangle id or -1.  scratch:
- * at least stereo_raster_scratch_bytes(T) bytes of device memory (the
- * per-triangle row-chunk offsets, written here). */
-int stereo_raster(const int32_t* tri_uv, int T, int w, int h, int32_t* planeidx,
-                  void* scratch, size_t scratch_bytes, void* stream);
+/* Pixel -> triangle lookup table (Sec. III-B) and DisparityInterpolation
+ * (Alg. 1, Eq. 3) in one pass.  A pixel (u, v), sampled at integer
+ * coordinates, belongs to a triangle when every edge function is positive or
+ * zero on a top or left edge; this partitions the hull.  The table is built
+ * by exact scan conversion.  Per covered pixel: planeidx = t and
+ * D_it = fma(a_t, u, fma(b_t, v, c_t)) in fp32; outside the hull -1 and NaN.
+ * tri_uv: T * 6 int32 vertex coordinates (u0,v0,u1,v1,u2,v2); abc: T * 3 fp32
+ * plane coefficients (needed when D_it is given).  planeidx (int32) and D_it
+ * (fp32), W*H each, 16-byte aligned; either may be NULL, not both.  scratch:
+ * at least stereo_raster_scratch_bytes(T) bytes of device memory. */
+int stereo_raster(const int32_t* tri_uv, const float* abc, int T, int w, int h, int32_t* planeidx,
+                  float* D_it, void* scratch, size_t scratch_bytes, void* stream);
 
-/* One pass of DisparityInterpolation + CostEvaluation (Alg. 2) +
- * DisparityRefinement (Alg. 3) over Omega_I.  For a pixel in Omega_I with a
- * triangle t: D = fma(a_t, u, fma(b_t, v, c_t)) in fp32, k = rint(D); it is
- * evaluated when 2 <= u - k <= W - 3, with cost C = popcount(cL(u,v) ^
- * cR(u-k,v)).  Then, as Alg. 3 in raster order: C < C_f => (D_f, C_f) <- (D, C);
- * per sz x sz cell the least C below t_lo (first in raster order on ties) and
- * the largest C above t_hi (first in raster order) are kept as keys:
+/* One pass of CostEvaluation (Alg. 2) + DisparityRefinement (Alg. 3) over
+ * Omega_I on the interpolated prior D_it (NaN = no triangle).  A pixel in
+ * Omega_I is evaluated when k = rint(D_it) keeps the right window inside the
+ * image (2 <= u - k <= W - 3); its cost is C = popcount(cL(u,v) ^ cR(u-k,v)).
+ * Then, as Alg. 3 in raster order: C < C_f => (D_f, C_f) <- (D_it, C); per
+ * sz x sz cell the least C below t_lo (first in raster order on ties) and the
+ * largest C above t_hi (first in raster order) are kept as keys:
  *   cg_key[cell] = (C << 27) | (v*W + u),  cb_key[cell] = ((24 - C) << 27) | (v*W + u),
  * 0xFFFFFFFF when empty; both arrays, ceil(H/sz)*ceil(W/sz) entries, must hold
- * 0xFFFFFFFF on entry (atomic minimum).  first_pass = 1 treats D_f, C_f as
- * their initial values (0, t_hi) without reading them.  mask may be NULL. */
-int stereo_validate(const uint32_t* cL, const uint32_t* cR, const uint32_t* omega,
-                    const int32_t* planeidx, const float* abc, int w, int h, int sz,
-                    int t_lo, int t_hi, int first_pass, float* D_f, uint8_t* C_f,
-                    uint8_t* mask, uint32_t* cg_key, uint32_t* cb_key, void* stream);
+ * 0xFFFFFFFF on entry (atomic minimum), or both be NULL to skip the cells.
+ * first_pass = 1 treats D_f, C_f as their initial values (0, t_hi) without
+ * reading them, and writes every pixel.  mask may be NULL. */
+int stereo_validate(const uint32_t* cL, const uint32_t* cR, const uint32_t* omega, const float* D_it,
+                    int w, int h, int sz, int t_lo, int t_hi, int first_pass, float* D_f,
+                    uint8_t* C_f, uint8_t* mask, uint32_t* cg_key, uint32_t* cb_key, void* stream);
 
 /* SupportResampling (Alg. 4) per cell, fused with SparseEpipolarStereo on the
- * invalid cells: for each cell with a cg key, cg_d = D_it at that pixel (the
- * plane of planeidx there); for each cell with a cb key, x_d = the epipolar
- * match of that pixel (as stereo_epipolar_match) or -1.  Cells without keys
- * get cg_d = NaN and x_d = -1.  The caller merges them in cell raster order. */
-int stereo_resample_match(const uint32_t* cg_key, const uint32_t* cb_key, int ncells,
-                          const int32_t* planeidx, const float* abc,
+ * invalid cells: for each cell with a cg key, cg_d = D_it at that pixel; for
+ * each cell with a cb key, x_d = the epipolar match of that pixel (as
+ * stereo_epipolar_match) or -1.  Cells without keys get cg_d = NaN and
+ * x_d = -1.  The caller merges them in cell raster order. */
+int stereo_resample_match(const uint32_t* cg_key, const uint32_t* cb_key, int ncells, const float* D_it,
                           const uint32_t* cL, const uint32_t* cR, int w, int h, int dmax,
                           int t_lo, int margin, float* cg_d, int32_t* x_d, void* stream);
 

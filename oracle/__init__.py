@@ -130,6 +130,15 @@ def raster(P, tri, W, H):
     return out
 
 
+def interp_map(planeidx, abc):
+    """DisparityInterpolation: D_it over the lookup table (NaN without a triangle)."""
+    planeidx = np.ascontiguousarray(planeidx, dtype=np.int32)
+    H, W = planeidx.shape
+    out = np.zeros((H, W), np.float32)
+    lib().or_interp_map(_p(planeidx), _p(np.ascontiguousarray(abc, dtype=np.float32)), W, H, _p(out))
+    return out
+
+
 def validate(cL, cR, om, planeidx, abc, sz, Df, Cf, t_lo=DEFAULT_PARAMS["t_lo"], t_hi=DEFAULT_PARAMS["t_hi"]):
     """One CostEvaluation + DisparityRefinement pass.  Df, Cf are updated in place.
     Returns mask and the cell records as a dict."""

@@ -440,6 +440,16 @@ float or_interp(const float* abc, int t, int u, int v) {
     return fmaf(abc[3 * t], (float)u, fmaf(abc[3 * t + 1], (float)v, abc[3 * t + 2]));
 }
 
+/* DisparityInterpolation (Alg. 1): the dense map D_it over the lookup table,
+ * NaN where a pixel has no triangle. */
+void or_interp_map(const int32_t* planeidx, const float* abc, int W, int H, float* out) {
+    for (int v = 0; v < H; v++)
+        for (int u = 0; u < W; u++) {
+            int t = planeidx[v * W + u];
+            out[v * W + u] = t >= 0 ? or_interp(abc, t, u, v) : NAN;
+        }
+}
+
 /* ---------------------------------------------------------------------- */
 /* One pass of DisparityInterpolation + CostEvaluation (Alg. 2) +           */
 /* DisparityRefinement (Alg. 3) in raster order over Omega_I.               */

@@ -72,9 +72,9 @@ _SIGS = {
     "stereo_delaunay": (_I, [_P, _I, _P, _I]),
     "stereo_planes": (_I, [_P, _P, _P, _I, _P]),
     "stereo_raster_scratch_bytes": (ctypes.c_size_t, [_I]),
-    "stereo_raster": (_I, [_P, _I, _I, _I, _P, _P, ctypes.c_size_t, _P]),
-    "stereo_validate": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P]),
-    "stereo_resample_match": (_I, [_P, _P, _I, _P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
+    "stereo_raster": (_I, [_P, _P, _I, _I, _I, _P, _P, _P, ctypes.c_size_t, _P]),
+    "stereo_validate": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P]),
+    "stereo_resample_match": (_I, [_P, _P, _I, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
 }
 SYMBOLS = tuple(_SIGS)
 
@@ -157,23 +157,21 @@ def raster_scratch_bytes(T):
     return int(lib().stereo_raster_scratch_bytes(T))
 
 
-def raster(tri_uv, T, w, h, planeidx, scratch, scratch_bytes, stream=None):
-    return _check(lib().stereo_raster(_ptr(tri_uv), T, w, h, _ptr(planeidx), _ptr(scratch), scratch_bytes,
-                                      _stream(stream)), "raster")
+def raster(tri_uv, abc, T, w, h, planeidx, D_it, scratch, scratch_bytes, stream=None):
+    return _check(lib().stereo_raster(_ptr(tri_uv), _ptr(abc), T, w, h, _ptr(planeidx), _ptr(D_it), _ptr(scratch),
+                                      scratch_bytes, _stream(stream)), "raster")
 
 
-def validate(cL, cR, omega, planeidx, abc, w, h, sz, t_lo, t_hi, first_pass, D_f, C_f, mask, cg_key, cb_key,
-             stream=None):
-    return _check(lib().stereo_validate(_ptr(cL), _ptr(cR), _ptr(omega), _ptr(planeidx), _ptr(abc), w, h, sz,
-                                        t_lo, t_hi, int(first_pass), _ptr(D_f), _ptr(C_f), _ptr(mask),
-                                        _ptr(cg_key), _ptr(cb_key), _stream(stream)), "validate")
+def validate(cL, cR, omega, D_it, w, h, sz, t_lo, t_hi, first_pass, D_f, C_f, mask, cg_key, cb_key, stream=None):
+    return _check(lib().stereo_validate(_ptr(cL), _ptr(cR), _ptr(omega), _ptr(D_it), w, h, sz, t_lo, t_hi,
+                                        int(first_pass), _ptr(D_f), _ptr(C_f), _ptr(mask), _ptr(cg_key),
+                                        _ptr(cb_key), _stream(stream)), "validate")
 
 
-def resample_match(cg_key, cb_key, ncells, planeidx, abc, cL, cR, w, h, dmax, t_lo, margin, cg_d, x_d,
-                   stream=None):
-    return _check(lib().stereo_resample_match(_ptr(cg_key), _ptr(cb_key), ncells, _ptr(planeidx), _ptr(abc),
-                                              _ptr(cL), _ptr(cR), w, h, dmax, t_lo, margin, _ptr(cg_d), _ptr(x_d),
-                                              _stream(stream)), "resample_match")
+def resample_match(cg_key, cb_key, ncells, D_it, cL, cR, w, h, dmax, t_lo, margin, cg_d, x_d, stream=None):
+    return _check(lib().stereo_resample_match(_ptr(cg_key), _ptr(cb_key), ncells, _ptr(D_it), _ptr(cL), _ptr(cR),
+                                              w, h, dmax, t_lo, margin, _ptr(cg_d), _ptr(x_d), _stream(stream)),
+                  "resample_match")
 
 
 # ---------------------------------------------------------------- request API

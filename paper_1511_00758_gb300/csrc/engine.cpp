@@ -146,6 +146,7 @@ struct Request {
     void* block = nullptr;
     PairDev dev{};
     int ncell_max = 0;
+    int32_t* pidx_buf = nullptr;  // plane-index map, written on the last pass
     // triangle buffers (device) and their capacities
     void* tri_block = nullptr;
     size_t tri_block_bytes = 0;
@@ -154,8 +155,8 @@ struct Request {
     std::vector<int32_t> n_support, n_tri;
     std::vector<float> trace;
     int T = 0;
-    int raster_items = 0;
-    Pinned st_tri;            // tri_uv (6 ints) + abc (3 floats) per triangle, then T + 1 chunk offsets
+    int raster_items = 0, n_small = 0;
+    Pinned st_tri;            // one mesh, laid out as tri_stage_bytes() describes
     Pinned st_kp;             // kp_uv + kp_d
     Pinned st_cells;          // cg_key, cg_d, cb_key, x_d
     bool resample_now = false;
@@ -170,6 +171,7 @@ size_t block_bytes(const Request& r, int K) {
     add(4 * N); add(4 * N);      // cL, cR
     add(4 * words);              // omega
     add(4 * N);                  // planeidx (FAST scores alias it)
+    add(4 * N);                  // D_it
     add(4 * N); add(N); add(N);  // Df, Cf, mask
     add((size_t)kFastBins * K * 8); add((size_t)kFastBins * K * 4);
     for (int i = 0; i < 4; i++) add(4 * (size_t)r.ncell_max);
@@ -189,7 +191,9 @@ void carve(Request& r, int K) {
     d.cR = (uint32_t*)take(4 * N);
     d.omega = (uint32_t*)take(4 * words);
     d.planeidx = (int32_t*)take(4 * N);
+    r.pidx_buf = d.planeidx;
     d.fast_score = (int16_t*)d.planeidx;
+    d.Dit = (float*)take(4 * N);
     d.Df = (float*)take(4 * N);
     d.Cf = (uint8_t*)take(N);
     d.mask = (uint8_t*)take(N);
@@ -291,9 +295,12 @@ bool valid_size(int w, int h) {
     return w >= 5 && h >= 5 && w <= 8192 && h <= 8192 && (long long)w * h < (1ll << 27);
 }
 
-// Staging layout of one mesh: tri_uv (6 int32), abc (3 fp32) per triangle,
-// T + 1 chunk offsets, then the triangle of every raster chunk.
-size_t tri_stage_bytes(int T, int items) { return (size_t)T * 40 + 4 + (size_t)items * 4; }
+// Staging layout of one mesh: tri_uv (6 int32) and abc (3 fp32) per
+// triangle, T + 1 chunk offsets, the triangle of every raster chunk, then the
+// small triangles.
+size_t tri_stage_bytes(int T, int items, int n_small) {
+    return (size_t)T * 40 + 4 + (size_t)items * 4 + (size_t)n_small * 4;
+}
 
 // Support set -> triangles, planes and raster inputs in the request's pinned
 // staging buffer.  Runs on a pool thread.
@@ -311,14 +318,15 @@ int mesh_step(Request& r) {
     std::vector<int32_t> tri((size_t)3 * cap);
     int T = n >= 3 ? delaunay(P.data(), n, tri.data(), cap) : 0;
     if (T < 0) return STEREO_E_INTERNAL;
-    std::vector<int32_t> tuv_v((size_t)6 * T), rows_v((size_t)T + 1);
+    std::vector<int32_t> tuv_v((size_t)6 * T), rows_v((size_t)T + 1), small_v((size_t)T + 1);
     for (int t = 0; t < T; t++)
         for (int k = 0; k < 3; k++) {
             tuv_v[6 * t + 2 * k] = P[2 * tri[3 * t + k]];
             tuv_v[6 * t + 2 * k + 1] = P[2 * tri[3 * t + k] + 1];
         }
-    const int items = raster_row_chunks(tuv_v.data(), T, r.H, rows_v.data());
-    if (!r.st_tri.ensure(tri_stage_bytes(T, items))) return STEREO_E_NOMEM;
+    int n_small = 0;
+    const int items = raster_lists(tuv_v.data(), T, r.W, r.H, rows_v.data(), small_v.data(), &n_small);
+    if (!r.st_tri.ensure(tri_stage_bytes(T, items, n_small))) return STEREO_E_NOMEM;
     int32_t* tuv = r.st_tri.as<int32_t>();
     float* abc = (float*)(tuv + (size_t)6 * T);
     int32_t* rows = (int32_t*)(abc + (size_t)3 * T);
@@ -326,9 +334,11 @@ int mesh_step(Request& r) {
     std::memcpy(tuv, tuv_v.data(), sizeof(int32_t) * 6 * (size_t)T);
     std::memcpy(rows, rows_v.data(), sizeof(int32_t) * ((size_t)T + 1));
     raster_item_tri(rows, T, item_tri);
+    std::memcpy(item_tri + items, small_v.data(), sizeof(int32_t) * (size_t)n_small);
     planes(P.data(), D.data(), tri.data(), T, abc);
     r.T = T;
     r.raster_items = items;
+    r.n_small = n_small;
     r.n_support.push_back(n);
     r.n_tri.push_back(T);
     for (const auto& s : r.S) {
@@ -553,11 +563,12 @@ void add_stats(stereo_stats& to, const stereo_stats& d) {
 // One GPU round for the seed group and the iteration group.
 cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
     cudaStream_t s = c->stream;
-    double seed_px = 0, iter_px = 0, validate_bytes = 0, cells_bytes = 0;
+    double seed_px = 0, iter_px = 0, validate_bytes = 0, cells_bytes = 0, raster_bytes = 0;
     for (Request* r : seed.reqs) seed_px += (double)r->W * r->H;
     // iteration group: triangle buffers, uploads, cell resets
     for (Request* r : iter.reqs) {
-        const size_t tri_bytes = align_up(tri_stage_bytes(r->T, r->raster_items) + 64, 256);
+        const size_t stage = tri_stage_bytes(r->T, r->raster_items, r->n_small);
+        const size_t tri_bytes = align_up(stage + 64, 256);
         if (tri_bytes > r->tri_block_bytes) {
             std::lock_guard<std::mutex> g(c->mu);
             c->arena.release(r->tri_block);
@@ -570,7 +581,10 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         r->dev.abc = (const float*)(tb + (size_t)r->T * 24);
         r->dev.tri_rows = (int32_t*)(tb + (size_t)r->T * 36);
         r->dev.item_tri = r->dev.tri_rows + r->T + 1;
+        r->dev.small_tri = r->dev.tri_rows + r->T + 1 + r->raster_items;
         r->dev.raster_items = r->raster_items;
+        r->dev.n_small = r->n_small;
+        r->dev.planeidx = r->it == r->iters ? r->pidx_buf : nullptr;  // the LUT is an output of the last pass
         r->dev.T = r->T;
         set_cell_size(r->dev, r->sz);
         r->dev.first_pass = r->it == 1;
@@ -579,10 +593,10 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         r->dev.Hc = r->resample_now ? (r->H + r->sz - 1) / r->sz : 0;
         const double px = (double)r->W * r->H;
         iter_px += px;
+        raster_bytes += px * (r->dev.planeidx ? 8.0 : 4.0);
         validate_bytes += px * (r->dev.first_pass ? 18.125 : 19.125);
         if (r->T > 0)
-            CK(cudaMemcpyAsync((void*)r->dev.tri_uv, r->st_tri.p, tri_stage_bytes(r->T, r->raster_items),
-                               cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync((void*)r->dev.tri_uv, r->st_tri.p, stage, cudaMemcpyHostToDevice, s));
         if (r->resample_now) cells_bytes += 8.0 * r->dev.Wc * r->dev.Hc;
     }
     // descriptors
@@ -607,8 +621,8 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
     if (ni) {
         PairBatch fb = batch_of(iter, WK_FILL);
         if (fb.total > 0) CK(Lr.run(STEREO_K_FILL, ni, cells_bytes, [&] { return launch_fill_cells(fb, s); }));
-        CK(Lr.run(STEREO_K_RASTER_CLEAR, ni, iter_px * 4.0, [&] { return launch_raster_clear(batch_of(iter, WK_CLEAR), s); }));
-        CK(Lr.run(STEREO_K_RASTER, ni, iter_px * 4.0, [&] { return launch_raster_spans(batch_of(iter, WK_RASTER), s); }));
+        CK(Lr.run(STEREO_K_RASTER_CLEAR, ni, raster_bytes, [&] { return launch_raster_clear(batch_of(iter, WK_CLEAR), s); }));
+        CK(Lr.run(STEREO_K_RASTER, ni, raster_bytes, [&] { return launch_raster(batch_of(iter, WK_RASTER), s); }));
         CK(Lr.run(STEREO_K_VALIDATE, ni, validate_bytes, [&] { return launch_validate(batch_of(iter, WK_VALIDATE), prm, s); }));
         PairBatch rb = batch_of(iter, WK_RESAMPLE);
         if (rb.total > 0) CK(Lr.run(STEREO_K_RESAMPLE, ni, 0.0, [&] { return launch_resample(rb, prm, s); }));
@@ -861,7 +875,7 @@ int stereo_poll(stereo_ctx* c, uint64_t ticket, stereo_result* out, int timeout_
         out->disparity = r->dev.Df;
         out->cost = r->dev.Cf;
         out->mask = r->dev.mask;
-        out->planeidx = r->dev.planeidx;
+        out->planeidx = r->pidx_buf;
         out->n_support = r->n_support.data();
         out->n_tri = r->n_tri.data();
         out->support = r->trace.data();
@@ -1003,40 +1017,42 @@ int stereo_planes(const int32_t* uv, const float* d, const int32_t* tri, int T, 
 
 size_t stereo_raster_scratch_bytes(int T) {
     if (T < 0) return 0;
-    return align_up(4 * ((size_t)T + 1), 256);
+    return align_up(8 * ((size_t)T + 1), 256);
 }
 
-int stereo_raster(const int32_t* tri_uv, int T, int w, int h, int32_t* planeidx, void* scratch,
-                  size_t scratch_bytes, void* stream) {
-    if (!valid_size(w, h) || T < 0 || (T > 0 && (!tri_uv || !scratch)) || !planeidx ||
-        ((uintptr_t)planeidx & 15) != 0)
+int stereo_raster(const int32_t* tri_uv, const float* abc, int T, int w, int h, int32_t* planeidx, float* D_it,
+                  void* scratch, size_t scratch_bytes, void* stream) {
+    if (!valid_size(w, h) || T < 0 || (T > 0 && (!tri_uv || !scratch)) || (!planeidx && !D_it) ||
+        (D_it && T > 0 && !abc) || ((uintptr_t)planeidx & 15) != 0 || ((uintptr_t)D_it & 15) != 0)
         return STEREO_E_INVAL;
-    if (T > 0 && scratch_bytes < 4 * ((size_t)T + 1)) return STEREO_E_CAP;
+    if (T > 0 && scratch_bytes < 8 * ((size_t)T + 1)) return STEREO_E_CAP;
     PairDev p{};
     p.W = w;
     p.H = h;
     p.T = T;
     p.tri_uv = tri_uv;
+    p.abc = abc;
     p.tri_rows = (int32_t*)scratch;
+    p.small_tri = (int32_t*)scratch + T + 1;
     p.planeidx = planeidx;
+    p.Dit = D_it;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = launch_raster_clear(single(p, WK_CLEAR), s);
-    if (e == cudaSuccess) e = launch_raster_device_prefix(p, s);
+    if (e == cudaSuccess) e = launch_raster_device_lists(p, s);
     return to_rc(e);
 }
 
-int stereo_validate(const uint32_t* cL, const uint32_t* cR, const uint32_t* omega, const int32_t* planeidx,
-                    const float* abc, int w, int h, int sz, int t_lo, int t_hi, int first_pass, float* D_f,
-                    uint8_t* C_f, uint8_t* mask, uint32_t* cg_key, uint32_t* cb_key, void* stream) {
-    if (!cL || !cR || !omega || !planeidx || !abc || !D_f || !C_f || !valid_size(w, h) || sz < 1 ||
+int stereo_validate(const uint32_t* cL, const uint32_t* cR, const uint32_t* omega, const float* D_it, int w, int h,
+                    int sz, int t_lo, int t_hi, int first_pass, float* D_f, uint8_t* C_f, uint8_t* mask,
+                    uint32_t* cg_key, uint32_t* cb_key, void* stream) {
+    if (!cL || !cR || !omega || !D_it || !D_f || !C_f || !valid_size(w, h) || sz < 1 ||
         !(0 <= t_lo && t_lo <= t_hi && t_hi < 24) || ((cg_key == nullptr) != (cb_key == nullptr)))
         return STEREO_E_INVAL;
     PairDev p{};
     p.cL = (uint32_t*)cL;
     p.cR = (uint32_t*)cR;
     p.omega = (uint32_t*)omega;
-    p.planeidx = (int32_t*)planeidx;
-    p.abc = abc;
+    p.Dit = (float*)D_it;
     p.W = w;
     p.H = h;
     set_cell_size(p, sz);
@@ -1052,17 +1068,16 @@ int stereo_validate(const uint32_t* cL, const uint32_t* cR, const uint32_t* omeg
     return to_rc(launch_validate(single(p, WK_VALIDATE), prm, (cudaStream_t)stream));
 }
 
-int stereo_resample_match(const uint32_t* cg_key, const uint32_t* cb_key, int ncells, const int32_t* planeidx,
-                          const float* abc, const uint32_t* cL, const uint32_t* cR, int w, int h, int dmax,
-                          int t_lo, int margin, float* cg_d, int32_t* x_d, void* stream) {
-    if (!cg_key || !cb_key || ncells < 0 || !planeidx || !abc || !cL || !cR || !valid_size(w, h) || dmax < 1 ||
-        dmax > 256 || !cg_d || !x_d || t_lo < 0 || margin < 0)
+int stereo_resample_match(const uint32_t* cg_key, const uint32_t* cb_key, int ncells, const float* D_it,
+                          const uint32_t* cL, const uint32_t* cR, int w, int h, int dmax, int t_lo, int margin,
+                          float* cg_d, int32_t* x_d, void* stream) {
+    if (!cg_key || !cb_key || ncells < 0 || !D_it || !cL || !cR || !valid_size(w, h) || dmax < 1 || dmax > 256 ||
+        !cg_d || !x_d || t_lo < 0 || margin < 0)
         return STEREO_E_INVAL;
     PairDev p{};
     p.cg_key = (uint32_t*)cg_key;
     p.cb_key = (uint32_t*)cb_key;
-    p.planeidx = (int32_t*)planeidx;
-    p.abc = abc;
+    p.Dit = (float*)D_it;
     p.cL = (uint32_t*)cL;
     p.cR = (uint32_t*)cR;
     p.W = w;

@@ -13,6 +13,7 @@ constexpr int kFastBinsX = 12;
 constexpr int kFastBinsY = 10;
 constexpr int kMaxK = 32;               // keypoints per bin, upper bound
 constexpr int kRasterRows = 8;          // triangle rows per raster work item
+constexpr int kSmallArea = 48;          // bounding-box pixels of a thread-rasterised triangle
 constexpr uint32_t kNoKey = 0xFFFFFFFFu;
 constexpr uint32_t kIdxMask = (1u << 27) - 1;
 
@@ -29,9 +30,12 @@ struct PairDev {
     int32_t* kp_d;            // 120*K matches
     const int32_t* tri_uv;    // T * 6
     const float* abc;         // T * 3
-    int32_t* tri_rows;        // T + 1: exclusive prefix of 8-row chunks per triangle
+    int32_t* tri_rows;        // T + 1: exclusive prefix of 8-row chunks per large triangle
     const int32_t* item_tri;  // raster_items: triangle of each chunk
-    int32_t* planeidx;        // W*H
+    int32_t* small_tri;       // n_small triangles rasterised by one thread each
+    int n_small;
+    int32_t* planeidx;        // W*H plane-index map, or null (not needed this pass)
+    float* Dit;               // W*H interpolated prior D_it (NaN outside the mesh)
     float* Df;                // W*H
     uint8_t* Cf;              // W*H
     uint8_t* mask;            // W*H or null
@@ -76,9 +80,10 @@ cudaError_t launch_fast_score(const PairBatch& b, const Params& prm, cudaStream_
 cudaError_t launch_fast_bins(const PairBatch& b, const Params& prm, cudaStream_t s);
 cudaError_t launch_match_kp(const PairBatch& b, const Params& prm, cudaStream_t s);
 cudaError_t launch_raster_clear(const PairBatch& b, cudaStream_t s);
-cudaError_t launch_raster_spans(const PairBatch& b, cudaStream_t s);
-// single pair whose chunk prefix is built on the device (stage entry point)
-cudaError_t launch_raster_device_prefix(const PairDev& p, cudaStream_t s);
+cudaError_t launch_raster(const PairBatch& b, cudaStream_t s);
+// single pair whose work lists are built on the device (stage entry point):
+// tri_rows needs T + 1 and small_tri T + 1 entries
+cudaError_t launch_raster_device_lists(const PairDev& p, cudaStream_t s);
 cudaError_t launch_validate(const PairBatch& b, const Params& prm, cudaStream_t s);
 cudaError_t launch_resample(const PairBatch& b, const Params& prm, cudaStream_t s);
 cudaError_t launch_fill_cells(const PairBatch& b, cudaStream_t s);
@@ -92,9 +97,10 @@ int sm_count();
 // Host mesh step (mesh.cpp).
 int delaunay(const int32_t* uv, int n, int32_t* tri, int cap);
 void planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float* abc);
-// Exclusive prefix of 8-row chunks of each triangle's clipped row range
-// (rows[T + 1]); returns the total.
-int raster_row_chunks(const int32_t* tri_uv, int T, int H, int32_t* rows);
+// Raster work lists of a mesh: small[] the triangles whose clipped bounding
+// box has at most 48 pixels (returns their count in *n_small); rows[T + 1]
+// the exclusive prefix of 8-row chunks of the others (returns the total).
+int raster_lists(const int32_t* tri_uv, int T, int W, int H, int32_t* rows, int32_t* small, int* n_small);
 // Triangle of every chunk (items = rows[T] entries).
 void raster_item_tri(const int32_t* rows, int T, int32_t* item_tri);
 

@@ -33,7 +33,7 @@ int work_items(WorkKind k, const PairDev& p) {
         case WK_MATCH_KP: return cdiv((long long)kFastBins * p.K, 8);
         case WK_CLEAR: return cdiv((long long)p.W * p.H, 4096);
         case WK_FILL: return p.cg_key ? cdiv((long long)p.Wc * p.Hc, 4096) : 0;
-        case WK_RASTER: return cdiv(p.raster_items, 8);
+        case WK_RASTER: return cdiv(p.n_small, 256) + cdiv(p.raster_items, 8);
         case WK_RESAMPLE: return cdiv((long long)p.Wc * p.Hc, 8);
         default: return 0;
     }
@@ -341,26 +341,132 @@ __global__ void __launch_bounds__(256) k_match_list(const uint32_t* cL, const ui
     }
 }
 
-// ---------------------------------------------------------------- raster (Sec. III-B)
-// Pixel -> triangle lookup table by exact scan conversion.  A pixel (u, v)
-// belongs to the positively oriented triangle when every edge function
-// E(u, v) = A u + B v + C is > 0, or == 0 on a top or left edge; for one row
-// v each edge bounds u from one side, so the covered pixels are the integer
-// range [lo, hi] obtained by exact floor/ceil division.  The rule partitions
-// the hull: every pixel is written by exactly one triangle, in any order.
-// One warp per chunk of 8 rows of one triangle; lanes stride the columns.
-__device__ __forceinline__ long long floordiv_pos(long long a, long long b) {  // b > 0
+// ---------------------------------------------------------------- raster + interpolation (Sec. III-B)
+// Pixel -> triangle lookup table and the interpolated prior D_it (Eq. 3) by
+// exact scan conversion.  A pixel (u, v) belongs to the positively oriented
+// triangle when every edge function E(u, v) = A u + B v + C is > 0, or == 0
+// on a top or left edge.  The rule partitions the hull: every pixel is
+// written by exactly one triangle, in any order; pixels outside keep the
+// cleared values (-1, NaN).  D_it = fma(a, u, fma(b, v, c)) in fp32.
+// Small triangles (bounding box of at most kSmallArea pixels): one thread
+// walks the box with incremental edge values.  Larger ones: one warp per
+// chunk of 8 rows, lanes 0..7 bound one row each by exact int32 floor/ceil
+// division, then lanes stride the columns.
+struct TriEdges {
+    int x[3], y[3];
+    int A[3], B[3], C[3], bias[3];
+};
+
+__device__ __forceinline__ void tri_setup(const int32_t* __restrict__ tri_uv, int t, TriEdges& e) {
+    const int32_t* q = tri_uv + 6 * (size_t)t;
+    int x[3] = {__ldg(q), __ldg(q + 2), __ldg(q + 4)};
+    int y[3] = {__ldg(q + 1), __ldg(q + 3), __ldg(q + 5)};
+    const long long o = (long long)(x[1] - x[0]) * (y[2] - y[0]) - (long long)(y[1] - y[0]) * (x[2] - x[0]);
+    if (o < 0) {  // positive orientation
+        int s = x[1]; x[1] = x[2]; x[2] = s;
+        s = y[1]; y[1] = y[2]; y[2] = s;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        e.x[k] = x[k];
+        e.y[k] = y[k];
+        const int ax = x[k], ay = y[k], bx = x[(k + 1) % 3], by = y[(k + 1) % 3];
+        const int dx = bx - ax, dy = by - ay;
+        e.A[k] = -dy;
+        e.B[k] = dx;
+        e.C[k] = dy * ax - dx * ay;
+        e.bias[k] = ((dy == 0 && dx > 0) || dy < 0) ? 0 : 1;  // top or left edges keep E == 0
+    }
+}
+
+__device__ __forceinline__ bool tri_is_small(const int32_t* __restrict__ q, int W, int H) {
+    const int x0 = max(0, min(q[0], min(q[2], q[4]))), x1 = min(W - 1, max(q[0], max(q[2], q[4])));
+    const int y0 = max(0, min(q[1], min(q[3], q[5]))), y1 = min(H - 1, max(q[1], max(q[3], q[5])));
+    return x1 < x0 || y1 < y0 || (x1 - x0 + 1) * (y1 - y0 + 1) <= kSmallArea;
+}
+
+__device__ __forceinline__ int tri_chunks(const int32_t* __restrict__ q, int W, int H) {
+    if (tri_is_small(q, W, H)) return 0;
+    const int y0 = max(0, min(q[1], min(q[3], q[5])));
+    const int y1 = min(H - 1, max(q[1], max(q[3], q[5])));
+    return (y1 - y0) / kRasterRows + 1;
+}
+
+__device__ __forceinline__ void put(int32_t* __restrict__ pidx, float* __restrict__ dit, size_t p, int t, float a,
+                                    float b, float c, int u, int v) {
+    if (pidx) pidx[p] = t;
+    if (dit) dit[p] = __fmaf_rn(a, (float)u, __fmaf_rn(b, (float)v, c));
+}
+
+__device__ __forceinline__ void raster_small(const int32_t* __restrict__ tri_uv, const float* __restrict__ abc,
+                                             int t, int W, int H, int32_t* __restrict__ pidx,
+                                             float* __restrict__ dit) {
+    TriEdges e;
+    tri_setup(tri_uv, t, e);
+    const float a = __ldg(abc + 3 * t), b = __ldg(abc + 3 * t + 1), c = __ldg(abc + 3 * t + 2);
+    const int x0 = max(0, min(e.x[0], min(e.x[1], e.x[2]))), x1 = min(W - 1, max(e.x[0], max(e.x[1], e.x[2])));
+    const int y0 = max(0, min(e.y[0], min(e.y[1], e.y[2]))), y1 = min(H - 1, max(e.y[0], max(e.y[1], e.y[2])));
+    for (int v = y0; v <= y1; v++) {
+        int e0 = e.A[0] * x0 + e.B[0] * v + e.C[0];
+        int e1 = e.A[1] * x0 + e.B[1] * v + e.C[1];
+        int e2 = e.A[2] * x0 + e.B[2] * v + e.C[2];
+        for (int u = x0; u <= x1; u++) {
+            if (e0 >= e.bias[0] && e1 >= e.bias[1] && e2 >= e.bias[2]) put(pidx, dit, (size_t)v * W + u, t, a, b, c, u, v);
+            e0 += e.A[0];
+            e1 += e.A[1];
+            e2 += e.A[2];
+        }
+    }
+}
+
+__device__ __forceinline__ int floordiv32(int a, int b) {  // b > 0
     return a >= 0 ? a / b : -((-a + b - 1) / b);
+}
+
+__device__ __forceinline__ void raster_chunk_tc(const int32_t* __restrict__ tri_uv, const float* __restrict__ abc,
+                                                int t, int c, int W, int H, int32_t* __restrict__ pidx,
+                                                float* __restrict__ dit) {
+    const int lane = threadIdx.x & 31;
+    TriEdges e;
+    tri_setup(tri_uv, t, e);
+    const float pa = __ldg(abc + 3 * t), pb = __ldg(abc + 3 * t + 1), pc = __ldg(abc + 3 * t + 2);
+    const int ymin = max(0, min(e.y[0], min(e.y[1], e.y[2])));
+    const int ymax = min(H - 1, max(e.y[0], max(e.y[1], e.y[2])));
+    const int v0 = ymin + c * kRasterRows;
+    const int vr = v0 + (lane & (kRasterRows - 1));
+    int lo = 0, hi = W - 1;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        // A u + B v + C >= bias  <=>  A u >= R
+        const int R = e.bias[k] - e.B[k] * vr - e.C[k];
+        if (e.A[k] > 0) lo = max(lo, -floordiv32(-R, e.A[k]));       // u >= ceil(R / A)
+        else if (e.A[k] < 0) hi = min(hi, floordiv32(-R, -e.A[k]));  // u <= floor(R / A)
+        else if (R > 0) hi = -1;
+    }
+    const int nrows = min(kRasterRows, ymax - v0 + 1);
+    for (int r = 0; r < nrows; r++) {
+        const int a = __shfl_sync(0xffffffffu, lo, r), b = __shfl_sync(0xffffffffu, hi, r);
+        const int v = v0 + r;
+        for (int u = a + lane; u <= b; u += 32) put(pidx, dit, (size_t)v * W + u, t, pa, pb, pc, u, v);
+    }
 }
 
 __device__ __forceinline__ void raster_clear_body(const PairDev& P, int local) {
     const size_t n = (size_t)P.W * P.H;
     const size_t base = (size_t)local * 4096;
-    int4* q = reinterpret_cast<int4*>(P.planeidx);
-    const int4 m1 = make_int4(-1, -1, -1, -1);
+    int32_t* pidx = P.planeidx;
+    float* dit = P.Dit;
+    const float qnan = __int_as_float(0x7fc00000);
     for (size_t i = base + 4 * threadIdx.x; i < base + 4096 && i < n; i += 4 * blockDim.x) {
-        if (i + 4 <= n) q[i / 4] = m1;
-        else for (size_t j = i; j < n; j++) P.planeidx[j] = -1;
+        if (i + 4 <= n) {
+            if (pidx) reinterpret_cast<int4*>(pidx)[i / 4] = make_int4(-1, -1, -1, -1);
+            if (dit) reinterpret_cast<float4*>(dit)[i / 4] = make_float4(qnan, qnan, qnan, qnan);
+        } else {
+            for (size_t j = i; j < n; j++) {
+                if (pidx) pidx[j] = -1;
+                if (dit) dit[j] = qnan;
+            }
+        }
     }
 }
 
@@ -370,122 +476,93 @@ __global__ void __launch_bounds__(256) k_raster_clear(PairBatch b) {
 #undef BODY
 }
 
-__device__ __forceinline__ int floordiv32(int a, int b) {  // b > 0
-    return a >= 0 ? a / b : -((-a + b - 1) / b);
-}
-
-// Chunk c (8 rows) of triangle t.  Lanes 0..7 bound one row each in exact
-// int32 arithmetic (|R| < 2^28 for coordinates below 8192); the warp then
-// writes the rows with lanes striding the columns.
-__device__ __forceinline__ void raster_chunk_tc(const int32_t* __restrict__ tri_uv, int t, int c, int W, int H,
-                                                int32_t* __restrict__ planeidx) {
-    const int lane = threadIdx.x & 31;
-    const int32_t* q = tri_uv + 6 * (size_t)t;
-    int x[3] = {__ldg(q), __ldg(q + 2), __ldg(q + 4)};
-    int y[3] = {__ldg(q + 1), __ldg(q + 3), __ldg(q + 5)};
-    const long long o = (long long)(x[1] - x[0]) * (y[2] - y[0]) - (long long)(y[1] - y[0]) * (x[2] - x[0]);
-    if (o < 0) {  // positive orientation
-        int s = x[1]; x[1] = x[2]; x[2] = s;
-        s = y[1]; y[1] = y[2]; y[2] = s;
+// Work of one pair: ceil(n_small / 256) thread blocks, then ceil(items / 8)
+// warp blocks (host-built small list, chunk prefix and chunk -> triangle table).
+__device__ __forceinline__ void raster_body(const PairDev& P, int local) {
+    const int nsb = (P.n_small + 255) / 256;
+    if (local < nsb) {
+        const int i = local * 256 + threadIdx.x;
+        if (i < P.n_small) raster_small(P.tri_uv, P.abc, __ldg(P.small_tri + i), P.W, P.H, P.planeidx, P.Dit);
+        return;
     }
-    const int ymin = max(0, min(y[0], min(y[1], y[2])));
-    const int ymax = min(H - 1, max(y[0], max(y[1], y[2])));
-    const int v0 = ymin + c * kRasterRows;
-    const int vr = v0 + (lane & (kRasterRows - 1));
-    int lo = 0, hi = W - 1;
-#pragma unroll
-    for (int e = 0; e < 3; e++) {
-        const int ax = x[e], ay = y[e], bx = x[(e + 1) % 3], by = y[(e + 1) % 3];
-        const int dx = bx - ax, dy = by - ay;
-        // E(u, v) = -dy u + dx (v - ay) + dy ax >= bias  <=>  -dy u >= R
-        const int bias = ((dy == 0 && dx > 0) || dy < 0) ? 0 : 1;  // top or left edges keep E == 0
-        const int R = bias - dx * (vr - ay) - dy * ax;
-        if (dy < 0) lo = max(lo, -floordiv32(-R, -dy));      // u >= ceil(R / -dy)
-        else if (dy > 0) hi = min(hi, floordiv32(-R, dy));   // u <= floor(-R / dy)
-        else if (R > 0) hi = -1;
-    }
-    const int nrows = min(kRasterRows, ymax - v0 + 1);
-    for (int r = 0; r < nrows; r++) {
-        const int a = __shfl_sync(0xffffffffu, lo, r), b = __shfl_sync(0xffffffffu, hi, r);
-        int32_t* row = planeidx + (size_t)(v0 + r) * W;
-        for (int u = a + lane; u <= b; u += 32) row[u] = t;
-    }
-}
-
-__device__ __forceinline__ void raster_chunk(const int32_t* __restrict__ tri_uv, const int32_t* __restrict__ rows,
-                                             int T, int W, int H, int32_t* __restrict__ planeidx, int item) {
-    // triangle of this chunk: the last t with rows[t] <= item
-    int lo = 0, hi = T - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(rows + mid) <= item) lo = mid; else hi = mid - 1;
-    }
-    raster_chunk_tc(tri_uv, lo, item - __ldg(rows + lo), W, H, planeidx);
-}
-
-__device__ __forceinline__ void raster_spans_body(const PairDev& P, int local) {
-    const int item = local * 8 + (threadIdx.x >> 5);
+    const int item = (local - nsb) * 8 + (threadIdx.x >> 5);
     if (item >= P.raster_items) return;
     const int t = __ldg(P.item_tri + item);
-    raster_chunk_tc(P.tri_uv, t, item - __ldg(P.tri_rows + t), P.W, P.H, P.planeidx);
+    raster_chunk_tc(P.tri_uv, P.abc, t, item - __ldg(P.tri_rows + t), P.W, P.H, P.planeidx, P.Dit);
 }
 
-__global__ void __launch_bounds__(256) k_raster_spans(PairBatch b) {
-#define BODY(P, l) raster_spans_body(P, l)
+__global__ void __launch_bounds__(256) k_raster(PairBatch b) {
+#define BODY(P, l) raster_body(P, l)
     FOR_EACH_ITEM(b, BODY)
 #undef BODY
 }
 
-// Chunk prefix on the device (one block), for callers without a host copy of
-// the triangles.
-__global__ void __launch_bounds__(1024) k_raster_prefix(const int32_t* __restrict__ tri_uv, int T, int H,
-                                                        int32_t* __restrict__ rows) {
-    __shared__ int warp_sums[32];
+// Device-built work lists for callers without a host copy of the triangles
+// (one block): rows[T + 1] chunk prefix of the large triangles, small[0..] the
+// small ones, small[T] their count.
+__global__ void __launch_bounds__(1024) k_raster_prefix(const int32_t* __restrict__ tri_uv, int T, int W, int H,
+                                                        int32_t* __restrict__ rows, int32_t* __restrict__ small) {
+    __shared__ int warp_sums[2][32];
     const int chunk = (T + blockDim.x - 1) / blockDim.x;
     const int a = min(T, (int)threadIdx.x * chunk), e = min(T, a + chunk);
-    auto count = [&](int t) {
+    int s = 0, ns = 0;
+    for (int t = a; t < e; t++) {
         const int32_t* q = tri_uv + 6 * (size_t)t;
-        const int y0 = max(0, min(q[1], min(q[3], q[5])));
-        const int y1 = min(H - 1, max(q[1], max(q[3], q[5])));
-        return y1 >= y0 ? (y1 - y0) / kRasterRows + 1 : 0;
-    };
-    int s = 0;
-    for (int t = a; t < e; t++) s += count(t);
+        s += tri_chunks(q, W, H);
+        ns += tri_is_small(q, W, H) ? 1 : 0;
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int x = s;
+    int x = s, y = ns;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+        const int xs = __shfl_up_sync(0xffffffffu, x, o), ys = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) { x += xs; y += ys; }
     }
-    if (lane == 31) warp_sums[w] = x;
+    if (lane == 31) { warp_sums[0][w] = x; warp_sums[1][w] = y; }
     __syncthreads();
     if (w == 0) {
-        int ws = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+        int ws = lane < (int)(blockDim.x >> 5) ? warp_sums[0][lane] : 0;
+        int wn = lane < (int)(blockDim.x >> 5) ? warp_sums[1][lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, ws, o);
-            if (lane >= o) ws += y;
+            const int xs = __shfl_up_sync(0xffffffffu, ws, o), ys = __shfl_up_sync(0xffffffffu, wn, o);
+            if (lane >= o) { ws += xs; wn += ys; }
         }
-        warp_sums[lane] = ws;
+        warp_sums[0][lane] = ws;
+        warp_sums[1][lane] = wn;
     }
     __syncthreads();
-    int run = x - s + (w > 0 ? warp_sums[w - 1] : 0);
+    int run = x - s + (w > 0 ? warp_sums[0][w - 1] : 0);
+    int runs = y - ns + (w > 0 ? warp_sums[1][w - 1] : 0);
     for (int t = a; t < e; t++) {
+        const int32_t* q = tri_uv + 6 * (size_t)t;
         rows[t] = run;
-        run += count(t);
+        run += tri_chunks(q, W, H);
+        if (tri_is_small(q, W, H)) small[runs++] = t;
     }
-    if (threadIdx.x == blockDim.x - 1) rows[T] = run;
+    if (threadIdx.x == blockDim.x - 1) {
+        rows[T] = run;
+        small[T] = runs;
+    }
 }
 
-// Persistent spans kernel whose item count is read from the device prefix.
-__global__ void __launch_bounds__(256) k_raster_spans_dev(const int32_t* __restrict__ tri_uv,
-                                                          const int32_t* __restrict__ rows, int T, int W, int H,
-                                                          int32_t* __restrict__ planeidx) {
+__global__ void __launch_bounds__(256) k_raster_dev(const int32_t* __restrict__ tri_uv, const float* __restrict__ abc,
+                                                    const int32_t* __restrict__ rows,
+                                                    const int32_t* __restrict__ small, int T, int W, int H,
+                                                    int32_t* __restrict__ pidx, float* __restrict__ dit) {
+    const int nsmall = __ldg(small + T);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsmall; i += gridDim.x * blockDim.x)
+        raster_small(tri_uv, abc, __ldg(small + i), W, H, pidx, dit);
     const int total = __ldg(rows + T);
     const int nw = gridDim.x * 8;
-    for (int item = blockIdx.x * 8 + (threadIdx.x >> 5); item < total; item += nw)
-        raster_chunk(tri_uv, rows, T, W, H, planeidx, item);
+    for (int item = blockIdx.x * 8 + (threadIdx.x >> 5); item < total; item += nw) {
+        int lo = 0, hi = T - 1;  // the last t with rows[t] <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(rows + mid) <= item) lo = mid; else hi = mid - 1;
+        }
+        raster_chunk_tc(tri_uv, abc, lo, item - __ldg(rows + lo), W, H, pidx, dit);
+    }
 }
 
 // ---------------------------------------------------------------- fused validate (Alg. 2 + Alg. 3)
@@ -510,8 +587,7 @@ __device__ __forceinline__ void validate_body(const PairDev& P, int local, const
     const int shift = P.sz_shift;
     const uint32_t magic = P.sz_magic;
     const uint32_t* __restrict__ omega = P.omega;
-    const int32_t* __restrict__ pidx = P.planeidx;
-    const float* __restrict__ abc = P.abc;
+    const float* __restrict__ dit = P.Dit;
     const uint32_t* __restrict__ cLp = P.cL;
     const uint32_t* __restrict__ cRp = P.cR;
     float* __restrict__ Df = P.Df;
@@ -536,36 +612,27 @@ __device__ __forceinline__ void validate_body(const PairDev& P, int local, const
     if (v < H) {
         const size_t row = (size_t)v * W;
         const size_t wrow = (size_t)v * ((W + 31) >> 5) + (u0 >> 5);
-        int t[kVJ];
+        float d[kVJ];
         uint32_t cl[kVJ];
         int cf[kVJ];
         bool om[kVJ];
 #pragma unroll
-        for (int j = 0; j < kVJ; j++) {  // independent loads first
+        for (int j = 0; j < kVJ; j++) {  // all first-level loads issue together
             const int u = u0 + lane + 32 * j;
             const bool in = u < W;
-            // all first-level loads issue together: one memory round trip
             const uint32_t ow = __ldg(omega + wrow + j);
-            const int tj = in ? __ldg(pidx + row + u) : -1;
+            d[j] = in ? __ldg(dit + row + u) : __int_as_float(0x7fc00000);
             cl[j] = in ? __ldg(cLp + row + u) : 0u;
             cf[j] = (!first && in) ? (int)Cf[row + u] : t_hi;
             om[j] = in && ((ow >> lane) & 1u);
-            t[j] = om[j] ? tj : -1;
         }
-        float d[kVJ];
         int cost[kVJ];
 #pragma unroll
-        for (int j = 0; j < kVJ; j++) {
+        for (int j = 0; j < kVJ; j++) {  // second level: the right census at u - rint(D_it)
             const int u = u0 + lane + 32 * j;
-            d[j] = 0.0f;
+            const float col = (float)u - rintf(d[j]);  // NaN outside the mesh: not evaluated
             cost[j] = -1;
-            if (t[j] >= 0) {
-                const float a = __ldg(abc + 3 * t[j]), b = __ldg(abc + 3 * t[j] + 1), c = __ldg(abc + 3 * t[j] + 2);
-                d[j] = __fmaf_rn(a, (float)u, __fmaf_rn(b, (float)v, c));
-                const float kf = rintf(d[j]);
-                const float col = (float)u - kf;
-                if (col >= 2.0f && col <= (float)(W - 3)) cost[j] = __popc(cl[j] ^ __ldg(cRp + row + (int)col));
-            }
+            if (om[j] && col >= 2.0f && col <= (float)(W - 3)) cost[j] = __popc(cl[j] ^ __ldg(cRp + row + (int)col));
         }
 #pragma unroll
         for (int j = 0; j < kVJ; j++) {
@@ -639,10 +706,7 @@ __device__ __forceinline__ void resample_body(const PairDev& P, int local, const
     if (lane == 0) {
         float d = __int_as_float(0x7fc00000);
         if (gk != kNoKey) {
-            const uint32_t p = gk & kIdxMask;
-            const int u = (int)(p % (uint32_t)P.W), v = (int)(p / (uint32_t)P.W);
-            const int t = P.planeidx[p];
-            d = __fmaf_rn(P.abc[3 * t], (float)u, __fmaf_rn(P.abc[3 * t + 1], (float)v, P.abc[3 * t + 2]));
+            d = P.Dit[gk & kIdxMask];
         }
         P.cg_d[cell] = d;
     }
@@ -706,17 +770,18 @@ cudaError_t launch_raster_clear(const PairBatch& b, cudaStream_t s) {
     k_raster_clear<<<grid_for(b.total, 8), 256, 0, s>>>(b);
     return cudaGetLastError();
 }
-cudaError_t launch_raster_spans(const PairBatch& b, cudaStream_t s) {
+cudaError_t launch_raster(const PairBatch& b, cudaStream_t s) {
     if (b.total <= 0) return cudaSuccess;
-    k_raster_spans<<<grid_for(b.total, 8), 256, 0, s>>>(b);
+    k_raster<<<grid_for(b.total, 8), 256, 0, s>>>(b);
     return cudaGetLastError();
 }
-cudaError_t launch_raster_device_prefix(const PairDev& p, cudaStream_t s) {
+cudaError_t launch_raster_device_lists(const PairDev& p, cudaStream_t s) {
     if (p.T <= 0) return cudaSuccess;
-    k_raster_prefix<<<1, 1024, 0, s>>>(p.tri_uv, p.T, p.H, p.tri_rows);
+    k_raster_prefix<<<1, 1024, 0, s>>>(p.tri_uv, p.T, p.W, p.H, p.tri_rows, p.small_tri);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_raster_spans_dev<<<sm_count() * 8, 256, 0, s>>>(p.tri_uv, p.tri_rows, p.T, p.W, p.H, p.planeidx);
+    k_raster_dev<<<sm_count() * 8, 256, 0, s>>>(p.tri_uv, p.abc, p.tri_rows, p.small_tri, p.T, p.W, p.H,
+                                               p.planeidx, p.Dit);
     return cudaGetLastError();
 }
 cudaError_t launch_validate(const PairBatch& b, const Params& prm, cudaStream_t s) {

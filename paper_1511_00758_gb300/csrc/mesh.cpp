@@ -260,15 +260,19 @@ void planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float*
     }
 }
 
-int raster_row_chunks(const int32_t* q, int T, int H, int32_t* rows) {
-    int s = 0;
+int raster_lists(const int32_t* q, int T, int W, int H, int32_t* rows, int32_t* small, int* n_small) {
+    int s = 0, ns = 0;
     for (int t = 0; t < T; t++, q += 6) {
         rows[t] = s;
+        const int x0 = std::max(0, std::min(q[0], std::min(q[2], q[4])));
+        const int x1 = std::min(W - 1, std::max(q[0], std::max(q[2], q[4])));
         const int y0 = std::max(0, std::min(q[1], std::min(q[3], q[5])));
         const int y1 = std::min(H - 1, std::max(q[1], std::max(q[3], q[5])));
-        if (y1 >= y0) s += (y1 - y0) / kRasterRows + 1;
+        if (x1 < x0 || y1 < y0 || (x1 - x0 + 1) * (y1 - y0 + 1) <= kSmallArea) small[ns++] = t;
+        else s += (y1 - y0) / kRasterRows + 1;
     }
     rows[T] = s;
+    *n_small = ns;
     return s;
 }
 

@@ -111,31 +111,44 @@ def _tri_uv(P, tri):
     return np.ascontiguousarray(P[tri].reshape(-1, 6), dtype=np.int32)
 
 
-def _gpu_raster(P, tri, W, H):
+def _gpu_raster(P, tri, W, H, abc=None):
     tuv = _tri_uv(P, tri)
     nbytes = S.raster_scratch_bytes(len(tri))
     scratch = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=DEV)
     pidx = torch.empty((H, W), dtype=torch.int32, device=DEV)
-    S.raster(_t(tuv) if len(tri) else None, len(tri), W, H, pidx, scratch, nbytes)
+    dit = torch.empty((H, W), dtype=torch.float32, device=DEV) if abc is not None else None
+    S.raster(_t(tuv) if len(tri) else None, _t(abc) if abc is not None and len(tri) else None, len(tri), W, H,
+             pidx, dit, scratch, nbytes)
     _sync()
-    return pidx.cpu().numpy()
+    return pidx.cpu().numpy(), (dit.cpu().numpy() if dit is not None else None)
+
+
+def _same_f32(a, b):
+    """Bit-identical fp32 maps (NaN where both are NaN)."""
+    return np.array_equal(np.isnan(a), np.isnan(b)) and np.array_equal(a[~np.isnan(a)].view(np.uint32),
+                                                                        b[~np.isnan(b)].view(np.uint32))
 
 
 @pytest.mark.parametrize("seed,n,W,H", [(1, 40, 640, 480), (2, 2000, 300, 200), (3, 6000, 257, 131),
-                                        (4, 3, 50, 40), (5, 200, 1242, 375)])
+                                        (4, 3, 50, 40), (5, 200, 1242, 375), (6, 30000, 1242, 375)])
 def test_raster(oracle_mod, seed, n, W, H):
     rng = np.random.default_rng(seed)
     P = _canon(np.unique(np.stack([rng.integers(0, W, n), rng.integers(0, H, n)], 1), axis=0))
+    D = rng.uniform(0, 100, len(P)).astype(np.float32)
     tri = oracle_mod.delaunay(P)
-    assert np.array_equal(_gpu_raster(P, tri, W, H), oracle_mod.raster(P, tri, W, H))
+    abc = oracle_mod.planes(P, D, tri)
+    want = oracle_mod.raster(P, tri, W, H)
+    pidx, dit = _gpu_raster(P, tri, W, H, abc)
+    assert np.array_equal(pidx, want)
+    assert _same_f32(dit, oracle_mod.interp_map(want, abc))
 
 
 def test_raster_empty_and_lattice(oracle_mod):
     W, H = 100, 60
-    assert (_gpu_raster(np.zeros((0, 2), np.int32), np.zeros((0, 3), np.int32), W, H) == -1).all()
+    assert (_gpu_raster(np.zeros((0, 2), np.int32), np.zeros((0, 3), np.int32), W, H)[0] == -1).all()
     P = _canon([(u, v) for v in range(0, H, 3) for u in range(0, W, 4)])
     tri = oracle_mod.delaunay(P)
-    got = _gpu_raster(P, tri, W, H)
+    got, _ = _gpu_raster(P, tri, W, H)
     assert np.array_equal(got, oracle_mod.raster(P, tri, W, H))
 
 
@@ -175,13 +188,14 @@ def test_validate(oracle_mod, name, sz, first):
     ro = oracle_mod.validate(cL_o, cR_o, om_o, pidx, abc, sz, Df_o, Cf_o, PRM["t_lo"], PRM["t_hi"])
 
     cL, cR, om = _gpu_census(p.left, p.right)
+    dit = _t(oracle_mod.interp_map(pidx, abc))
     Df = _t(Df0 if not first else np.full((H, W), 7.0, np.float32))
     Cf = _t(Cf0 if not first else np.full((H, W), 3, np.uint8))
     mask = torch.empty((H, W), dtype=torch.uint8, device=DEV)
     nc = ro["Wc"] * ro["Hc"]
     cg = torch.full((nc,), -1, dtype=torch.int32, device=DEV)
     cb = torch.full((nc,), -1, dtype=torch.int32, device=DEV)
-    S.validate(cL, cR, om, _t(pidx), _t(abc), W, H, sz, PRM["t_lo"], PRM["t_hi"], first, Df, Cf, mask, cg, cb)
+    S.validate(cL, cR, om, dit, W, H, sz, PRM["t_lo"], PRM["t_hi"], first, Df, Cf, mask, cg, cb)
     _sync()
     assert np.array_equal(mask.cpu().numpy(), ro["mask"])
     assert np.array_equal(Cf.cpu().numpy(), Cf_o)
@@ -205,7 +219,7 @@ def test_validate(oracle_mod, name, sz, first):
     cgd = torch.empty(nc, dtype=torch.float32, device=DEV)
     xd = torch.empty(nc, dtype=torch.int32, device=DEV)
     dmax = p.dmax
-    S.resample_match(cg, cb, nc, _t(pidx), _t(abc), cL, cR, W, H, dmax, PRM["t_lo"], PRM["uniq_margin"], cgd, xd)
+    S.resample_match(cg, cb, nc, dit, cL, cR, W, H, dmax, PRM["t_lo"], PRM["uniq_margin"], cgd, xd)
     _sync()
     cgd = cgd.cpu().numpy()
     assert np.isnan(cgd[~wg]).all()

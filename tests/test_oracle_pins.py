@@ -346,6 +346,10 @@ def test_planes_reproduce_dyadic_plane(oracle_mod):
     abc = oracle_mod.planes(P, D, tri)
     assert (abc == np.float32([a, b, c])).all()
     pidx = oracle_mod.raster(P, tri, 64, 64)
+    dmap = oracle_mod.interp_map(pidx, abc)
+    uu, vv = np.meshgrid(np.arange(64), np.arange(64))
+    assert np.isnan(dmap[pidx < 0]).all()
+    assert (dmap[pidx >= 0] == (a * uu + b * vv + c)[pidx >= 0]).all()
     for v in range(64):
         for u in range(64):
             t = pidx[v, u]
