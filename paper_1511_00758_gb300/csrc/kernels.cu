@@ -403,7 +403,12 @@ __device__ __forceinline__ void raster_small(const int32_t* __restrict__ tri_uv,
                                              float* __restrict__ dit) {
     TriEdges e;
     tri_setup(tri_uv, t, e);
-    const float a = __ldg(abc + 3 * t), b = __ldg(abc + 3 * t + 1), c = __ldg(abc + 3 * t + 2);
+    float a = 0.0f, b = 0.0f, c = 0.0f;
+    if (dit) {  // planes are only read when D_it is written (abc may be null otherwise)
+        a = __ldg(abc + 3 * t);
+        b = __ldg(abc + 3 * t + 1);
+        c = __ldg(abc + 3 * t + 2);
+    }
     const int x0 = max(0, min(e.x[0], min(e.x[1], e.x[2]))), x1 = min(W - 1, max(e.x[0], max(e.x[1], e.x[2])));
     const int y0 = max(0, min(e.y[0], min(e.y[1], e.y[2]))), y1 = min(H - 1, max(e.y[0], max(e.y[1], e.y[2])));
     for (int v = y0; v <= y1; v++) {
@@ -429,7 +434,12 @@ __device__ __forceinline__ void raster_chunk_tc(const int32_t* __restrict__ tri_
     const int lane = threadIdx.x & 31;
     TriEdges e;
     tri_setup(tri_uv, t, e);
-    const float pa = __ldg(abc + 3 * t), pb = __ldg(abc + 3 * t + 1), pc = __ldg(abc + 3 * t + 2);
+    float pa = 0.0f, pb = 0.0f, pc = 0.0f;
+    if (dit) {  // planes are only read when D_it is written (abc may be null otherwise)
+        pa = __ldg(abc + 3 * t);
+        pb = __ldg(abc + 3 * t + 1);
+        pc = __ldg(abc + 3 * t + 2);
+    }
     const int ymin = max(0, min(e.y[0], min(e.y[1], e.y[2])));
     const int ymax = min(H - 1, max(e.y[0], max(e.y[1], e.y[2])));
     const int v0 = ymin + c * kRasterRows;
