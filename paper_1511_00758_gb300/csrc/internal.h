@@ -13,7 +13,7 @@ constexpr int kFastBinsX = 12;
 constexpr int kFastBinsY = 10;
 constexpr int kMaxK = 32;               // keypoints per bin, upper bound
 constexpr int kRasterRows = 8;          // triangle rows per raster work item
-constexpr int kSmallArea = 48;          // bounding-box pixels of a thread-rasterised triangle
+constexpr int kSmallArea = 256;         // bounding-box pixels of a thread-rasterised triangle
 constexpr uint32_t kNoKey = 0xFFFFFFFFu;
 constexpr uint32_t kIdxMask = (1u << 27) - 1;
 
@@ -98,7 +98,7 @@ int sm_count();
 int delaunay(const int32_t* uv, int n, int32_t* tri, int cap);
 void planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float* abc);
 // Raster work lists of a mesh: small[] the triangles whose clipped bounding
-// box has at most 48 pixels (returns their count in *n_small); rows[T + 1]
+// box has at most kSmallArea pixels (returns their count in *n_small); rows[T + 1]
 // the exclusive prefix of 8-row chunks of the others (returns the total).
 int raster_lists(const int32_t* tri_uv, int T, int W, int H, int32_t* rows, int32_t* small, int* n_small);
 // Triangle of every chunk (items = rows[T] entries).
