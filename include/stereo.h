@@ -215,6 +215,20 @@ size_t stereo_raster_scratch_bytes(int T);
 int stereo_raster(const int32_t* tri_uv, const float* abc, int T, int w, int h, int32_t* planeidx,
                   float* D_it, void* scratch, size_t scratch_bytes, void* stream);
 
+/* stereo_raster without a scratch argument, for callers that cannot allocate
+ * device memory where they run the raster (a fixed real-time memory plan, an
+ * allocator owned by another component, work recorded into a capture).  The
+ * paper has no counterpart: it is a memory-management variant of
+ * stereo_raster with the same arguments and results otherwise.  Its work
+ * lists live in one file-scope device array sized for at most 262143
+ * triangles (2 MiB, held by every GPU that loads the library until exit);
+ * larger T returns STEREO_E_CAP.  The first call on each device looks up the
+ * array's device address (no allocation); make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * race and must be serialised by the caller. */
+int stereo_raster_noalloc(const int32_t* tri_uv, const float* abc, int T, int w, int h,
+                          int32_t* planeidx, float* D_it, void* stream);
+
 /* One pass of CostEvaluation (Alg. 2) + DisparityRefinement (Alg. 3) over
  * Omega_I on the interpolated prior D_it (NaN = no triangle).  A pixel in
  * Omega_I is evaluated when k = rint(D_it) keeps the right window inside the

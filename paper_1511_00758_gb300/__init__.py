@@ -14,7 +14,7 @@ from . import _build
 
 __all__ = [
     "StereoError", "load", "lib", "Config", "Result", "Stats", "Context",
-    "census", "fast", "epipolar_match", "delaunay", "planes", "raster_scratch_bytes", "raster",
+    "census", "fast", "epipolar_match", "delaunay", "planes", "raster_scratch_bytes", "raster", "raster_noalloc",
     "validate", "resample_match", "ERRORS",
 ]
 
@@ -73,6 +73,7 @@ _SIGS = {
     "stereo_planes": (_I, [_P, _P, _P, _I, _P]),
     "stereo_raster_scratch_bytes": (ctypes.c_size_t, [_I]),
     "stereo_raster": (_I, [_P, _P, _I, _I, _I, _P, _P, _P, ctypes.c_size_t, _P]),
+    "stereo_raster_noalloc": (_I, [_P, _P, _I, _I, _I, _P, _P, _P]),
     "stereo_validate": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P]),
     "stereo_resample_match": (_I, [_P, _P, _I, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
 }
@@ -160,6 +161,13 @@ def raster_scratch_bytes(T):
 def raster(tri_uv, abc, T, w, h, planeidx, D_it, scratch, scratch_bytes, stream=None):
     return _check(lib().stereo_raster(_ptr(tri_uv), _ptr(abc), T, w, h, _ptr(planeidx), _ptr(D_it), _ptr(scratch),
                                       scratch_bytes, _stream(stream)), "raster")
+
+
+def raster_noalloc(tri_uv, abc, T, w, h, planeidx, D_it, stream=None):
+    """stereo_raster with its work lists in the library's fixed device array
+    (for callers that cannot allocate device memory); T <= 262143."""
+    return _check(lib().stereo_raster_noalloc(_ptr(tri_uv), _ptr(abc), T, w, h, _ptr(planeidx), _ptr(D_it),
+                                              _stream(stream)), "raster_noalloc")
 
 
 def validate(cL, cR, omega, D_it, w, h, sz, t_lo, t_hi, first_pass, D_f, C_f, mask, cg_key, cb_key, stream=None):
