@@ -280,6 +280,8 @@ struct stereo_ctx {
     void* desc_dev = nullptr;
     size_t desc_cap = 0;
     cudaEvent_t ev = nullptr;
+    cudaStream_t copy_stream = nullptr;      // submit-time device copies (never captured)
+    cudaGraphExec_t graph_exec = nullptr;    // the last round's executable graph
     std::vector<cudaEvent_t> ev_pool;  // timing events of profiled launches
     stereo_stats stats{};
 };
@@ -521,14 +523,14 @@ struct Launcher {
     template <class F>
     cudaError_t run(int kind, int npairs, double bytes, F&& f) {
         cudaEvent_t a = nullptr;
-        if (c->cfg.profile) {
+        if (c->cfg.profile) {  // event nodes of the round's graph: timed on the GPU, after it
             a = event();
-            CK(cudaEventRecord(a, s));
+            CK(cudaEventRecordWithFlags(a, s, cudaEventRecordExternal));
         }
         CK(f());
         if (c->cfg.profile) {
             cudaEvent_t b = event();
-            CK(cudaEventRecord(b, s));
+            CK(cudaEventRecordWithFlags(b, s, cudaEventRecordExternal));
             timed.push_back({kind, a, b});
         }
         delta.kernel_launches++;
@@ -560,15 +562,62 @@ void add_stats(stereo_stats& to, const stereo_stats& d) {
     }
 }
 
-// One GPU round for the seed group and the iteration group.
+// Copies and launches of one round, issued on stream s (captured into a graph).
+cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, cudaStream_t s, size_t desc_bytes,
+                         double seed_px, double cells_bytes, double raster_bytes, double validate_bytes) {
+    for (Request* r : iter.reqs)
+        if (r->T > 0)
+            CK(cudaMemcpyAsync((void*)r->dev.tri_uv, r->st_tri.p, tri_stage_bytes(r->T, r->raster_items, r->n_small),
+                               cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->desc_dev, c->desc_host.p, desc_bytes, cudaMemcpyHostToDevice, s));
+    const Params& prm = c->prm;
+    const int ns = (int)seed.reqs.size(), ni = (int)iter.reqs.size();
+    if (ns) {
+        CK(Lr.run(STEREO_K_CENSUS, ns, seed_px * 10.125, [&] { return launch_census(batch_of(seed, WK_CENSUS), prm, s); }));
+        CK(Lr.run(STEREO_K_FAST_SCORE, ns, seed_px * 3.0, [&] { return launch_fast_score(batch_of(seed, WK_FAST_SCORE), prm, s); }));
+        CK(Lr.run(STEREO_K_FAST_BINS, ns, 0.0, [&] { return launch_fast_bins(batch_of(seed, WK_FAST_BINS), prm, s); }));
+        CK(Lr.run(STEREO_K_MATCH_KP, ns, 0.0, [&] { return launch_match_kp(batch_of(seed, WK_MATCH_KP), prm, s); }));
+    }
+    if (ni) {
+        PairBatch fb = batch_of(iter, WK_FILL);
+        if (fb.total > 0) CK(Lr.run(STEREO_K_FILL, ni, cells_bytes, [&] { return launch_fill_cells(fb, s); }));
+        CK(Lr.run(STEREO_K_RASTER_CLEAR, ni, raster_bytes, [&] { return launch_raster_clear(batch_of(iter, WK_CLEAR), s); }));
+        CK(Lr.run(STEREO_K_RASTER, ni, raster_bytes, [&] { return launch_raster(batch_of(iter, WK_RASTER), s); }));
+        CK(Lr.run(STEREO_K_VALIDATE, ni, validate_bytes, [&] { return launch_validate(batch_of(iter, WK_VALIDATE), prm, s); }));
+        PairBatch rb = batch_of(iter, WK_RESAMPLE);
+        if (rb.total > 0) CK(Lr.run(STEREO_K_RESAMPLE, ni, 0.0, [&] { return launch_resample(rb, prm, s); }));
+    }
+    // results to pinned host memory
+    for (Request* r : seed.reqs) {
+        const int nk = kFastBins * c->K;
+        CK(cudaMemcpyAsync(r->st_kp.p, r->dev.kp_uv, (size_t)nk * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(r->st_kp.as<char>() + (size_t)nk * 8, r->dev.kp_d, (size_t)nk * 4, cudaMemcpyDeviceToHost, s));
+    }
+    for (Request* r : iter.reqs) {
+        if (!r->resample_now) continue;
+        const size_t nc = (size_t)r->dev.Wc * r->dev.Hc, m = r->ncell_max;
+        char* h = r->st_cells.as<char>();
+        CK(cudaMemcpyAsync(h, r->dev.cg_key, 4 * nc, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h + 4 * m, r->dev.cg_d, 4 * nc, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h + 8 * m, r->dev.cb_key, 4 * nc, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h + 12 * m, r->dev.x_d, 4 * nc, cudaMemcpyDeviceToHost, s));
+    }
+    return cudaSuccess;
+}
+
+// One GPU round for the seed group and the iteration group: host-side
+// preparation (buffers, descriptors), then every copy and launch of the round
+// captured as one CUDA graph and replayed (the previous executable graph is
+// updated in place when the topology matches), then one synchronisation.
 cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
     cudaStream_t s = c->stream;
-    double seed_px = 0, iter_px = 0, validate_bytes = 0, cells_bytes = 0, raster_bytes = 0;
-    for (Request* r : seed.reqs) seed_px += (double)r->W * r->H;
-    // iteration group: triangle buffers, uploads, cell resets
+    double seed_px = 0, validate_bytes = 0, cells_bytes = 0, raster_bytes = 0;
+    for (Request* r : seed.reqs) {
+        seed_px += (double)r->W * r->H;
+        if (!r->st_kp.ensure((size_t)kFastBins * c->K * 12)) return cudaErrorMemoryAllocation;
+    }
     for (Request* r : iter.reqs) {
-        const size_t stage = tri_stage_bytes(r->T, r->raster_items, r->n_small);
-        const size_t tri_bytes = align_up(stage + 64, 256);
+        const size_t tri_bytes = align_up(tri_stage_bytes(r->T, r->raster_items, r->n_small) + 64, 256);
         if (tri_bytes > r->tri_block_bytes) {
             std::lock_guard<std::mutex> g(c->mu);
             c->arena.release(r->tri_block);
@@ -592,58 +641,52 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         r->dev.Wc = r->resample_now ? (r->W + r->sz - 1) / r->sz : 0;
         r->dev.Hc = r->resample_now ? (r->H + r->sz - 1) / r->sz : 0;
         const double px = (double)r->W * r->H;
-        iter_px += px;
         raster_bytes += px * (r->dev.planeidx ? 8.0 : 4.0);
         validate_bytes += px * (r->dev.first_pass ? 18.125 : 19.125);
-        if (r->T > 0)
-            CK(cudaMemcpyAsync((void*)r->dev.tri_uv, r->st_tri.p, stage, cudaMemcpyHostToDevice, s));
-        if (r->resample_now) cells_bytes += 8.0 * r->dev.Wc * r->dev.Hc;
+        if (r->resample_now) {
+            cells_bytes += 8.0 * r->dev.Wc * r->dev.Hc;
+            if (!r->st_cells.ensure(16 * (size_t)r->ncell_max)) return cudaErrorMemoryAllocation;
+        }
     }
-    // descriptors
     const size_t bs = group_bytes(seed), bi = group_bytes(iter);
     if (bs + bi > c->desc_cap) {
         if (c->desc_dev) cudaFree(c->desc_dev);
+        c->desc_dev = nullptr;
         c->desc_cap = align_up((bs + bi) * 2, 4096);
         CK(cudaMalloc(&c->desc_dev, c->desc_cap));
         if (!c->desc_host.ensure(c->desc_cap)) return cudaErrorMemoryAllocation;
     }
     fill_group(seed, c->desc_host.as<char>(), (char*)c->desc_dev);
     fill_group(iter, c->desc_host.as<char>() + bs, (char*)c->desc_dev + bs);
-    CK(cudaMemcpyAsync(c->desc_dev, c->desc_host.p, bs + bi, cudaMemcpyHostToDevice, s));
-    const Params& prm = c->prm;
-    const int ns = (int)seed.reqs.size(), ni = (int)iter.reqs.size();
-    if (ns) {
-        CK(Lr.run(STEREO_K_CENSUS, ns, seed_px * 10.125, [&] { return launch_census(batch_of(seed, WK_CENSUS), prm, s); }));
-        CK(Lr.run(STEREO_K_FAST_SCORE, ns, seed_px * 3.0, [&] { return launch_fast_score(batch_of(seed, WK_FAST_SCORE), prm, s); }));
-        CK(Lr.run(STEREO_K_FAST_BINS, ns, 0.0, [&] { return launch_fast_bins(batch_of(seed, WK_FAST_BINS), prm, s); }));
-        CK(Lr.run(STEREO_K_MATCH_KP, ns, 0.0, [&] { return launch_match_kp(batch_of(seed, WK_MATCH_KP), prm, s); }));
+
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = record_round(c, seed, iter, Lr, s, bs + bi, seed_px, cells_bytes, raster_bytes, validate_bytes);
+    cudaGraph_t graph = nullptr;
+    cudaError_t end = cudaStreamEndCapture(s, &graph);
+    if (err == cudaSuccess) err = end;
+    if (err != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        Lr.timed.clear();
+        return err;
     }
-    if (ni) {
-        PairBatch fb = batch_of(iter, WK_FILL);
-        if (fb.total > 0) CK(Lr.run(STEREO_K_FILL, ni, cells_bytes, [&] { return launch_fill_cells(fb, s); }));
-        CK(Lr.run(STEREO_K_RASTER_CLEAR, ni, raster_bytes, [&] { return launch_raster_clear(batch_of(iter, WK_CLEAR), s); }));
-        CK(Lr.run(STEREO_K_RASTER, ni, raster_bytes, [&] { return launch_raster(batch_of(iter, WK_RASTER), s); }));
-        CK(Lr.run(STEREO_K_VALIDATE, ni, validate_bytes, [&] { return launch_validate(batch_of(iter, WK_VALIDATE), prm, s); }));
-        PairBatch rb = batch_of(iter, WK_RESAMPLE);
-        if (rb.total > 0) CK(Lr.run(STEREO_K_RESAMPLE, ni, 0.0, [&] { return launch_resample(rb, prm, s); }));
+    bool updated = false;
+    if (c->graph_exec) {
+        cudaGraphExecUpdateResultInfo info{};
+        updated = cudaGraphExecUpdate(c->graph_exec, graph, &info) == cudaSuccess;
+        if (!updated) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(c->graph_exec);
+            c->graph_exec = nullptr;
+        }
     }
-    // results to pinned host memory
-    for (Request* r : seed.reqs) {
-        const int nk = kFastBins * c->K;
-        if (!r->st_kp.ensure((size_t)nk * 12)) return cudaErrorMemoryAllocation;
-        CK(cudaMemcpyAsync(r->st_kp.p, r->dev.kp_uv, (size_t)nk * 8, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(r->st_kp.as<char>() + (size_t)nk * 8, r->dev.kp_d, (size_t)nk * 4, cudaMemcpyDeviceToHost, s));
+    if (!updated) err = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (err != cudaSuccess) {
+        c->graph_exec = nullptr;
+        Lr.timed.clear();
+        return err;
     }
-    for (Request* r : iter.reqs) {
-        if (!r->resample_now) continue;
-        const size_t nc = (size_t)r->dev.Wc * r->dev.Hc, m = r->ncell_max;
-        if (!r->st_cells.ensure(16 * m)) return cudaErrorMemoryAllocation;
-        char* h = r->st_cells.as<char>();
-        CK(cudaMemcpyAsync(h, r->dev.cg_key, 4 * nc, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(h + 4 * m, r->dev.cg_d, 4 * nc, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(h + 8 * m, r->dev.cb_key, 4 * nc, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(h + 12 * m, r->dev.x_d, 4 * nc, cudaMemcpyDeviceToHost, s));
-    }
+    CK(cudaGraphLaunch(c->graph_exec, s));
     CK(cudaEventRecord(c->ev, s));
     CK(cudaEventSynchronize(c->ev));
     Lr.collect();
@@ -780,6 +823,7 @@ int stereo_create(const stereo_config* cfg, stereo_ctx** out) {
     }
     c->arena.init(c->arena_base, c->cfg.mem_budget_bytes);
     cudaEventCreateWithFlags(&c->ev, cudaEventBlockingSync | cudaEventDisableTiming);
+    cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
     c->pool.start(std::max(1, cfg->host_threads));
     c->sched = std::thread(scheduler, c);
     *out = c;
@@ -823,9 +867,9 @@ int stereo_submit(stereo_ctx* c, int stream_id, const uint8_t* left, const uint8
             return STEREO_E_BUSY;
         }
         g.unlock();
-        cudaMemcpyAsync(r->in_dev, left, N, cudaMemcpyDeviceToDevice, c->stream);
-        cudaMemcpyAsync(r->in_dev + N, right, N, cudaMemcpyDeviceToDevice, c->stream);
-        if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaMemcpyAsync(r->in_dev, left, N, cudaMemcpyDeviceToDevice, c->copy_stream);
+        cudaMemcpyAsync(r->in_dev + N, right, N, cudaMemcpyDeviceToDevice, c->copy_stream);
+        if (cudaStreamSynchronize(c->copy_stream) != cudaSuccess) {
             std::lock_guard<std::mutex> g2(c->mu);
             c->arena.release(r->in_dev);
             delete r;
@@ -938,6 +982,8 @@ void stereo_destroy(stereo_ctx* c) {
     c->desc_host.free();
     if (c->desc_dev) cudaFree(c->desc_dev);
     if (c->own_arena) cudaFree(c->arena_base);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->ev) cudaEventDestroy(c->ev);
     for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
     if (c->own_stream) cudaStreamDestroy(c->stream);

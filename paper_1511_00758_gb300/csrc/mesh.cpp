@@ -261,18 +261,30 @@ void planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float*
 }
 
 int raster_lists(const int32_t* q, int T, int W, int H, int32_t* rows, int32_t* small, int* n_small) {
-    int s = 0, ns = 0;
+    // small triangles are listed by increasing bounding-box area (a counting
+    // sort), so the 32 threads of a warp walk boxes of similar size
+    std::vector<int> area_of(T, -1);
+    int cnt[kSmallArea + 2] = {0};
+    int s = 0;
     for (int t = 0; t < T; t++, q += 6) {
         rows[t] = s;
         const int x0 = std::max(0, std::min(q[0], std::min(q[2], q[4])));
         const int x1 = std::min(W - 1, std::max(q[0], std::max(q[2], q[4])));
         const int y0 = std::max(0, std::min(q[1], std::min(q[3], q[5])));
         const int y1 = std::min(H - 1, std::max(q[1], std::max(q[3], q[5])));
-        if (x1 < x0 || y1 < y0 || (x1 - x0 + 1) * (y1 - y0 + 1) <= kSmallArea) small[ns++] = t;
-        else s += (y1 - y0) / kRasterRows + 1;
+        const int area = (x1 < x0 || y1 < y0) ? 0 : (x1 - x0 + 1) * (y1 - y0 + 1);
+        if (area <= kSmallArea) {
+            area_of[t] = area;
+            cnt[area + 1]++;
+        } else {
+            s += (y1 - y0) / kRasterRows + 1;
+        }
     }
     rows[T] = s;
-    *n_small = ns;
+    for (int a = 0; a <= kSmallArea; a++) cnt[a + 1] += cnt[a];
+    for (int t = 0; t < T; t++)
+        if (area_of[t] >= 0) small[cnt[area_of[t]]++] = t;
+    *n_small = cnt[kSmallArea];
     return s;
 }
 
