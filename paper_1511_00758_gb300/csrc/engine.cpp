@@ -281,6 +281,7 @@ struct stereo_ctx {
     size_t desc_cap = 0;
     cudaEvent_t ev = nullptr;
     cudaStream_t copy_stream = nullptr;      // submit-time device copies (never captured)
+    cudaStream_t capture_stream = nullptr;   // private stream the rounds are captured on
     cudaGraphExec_t graph_exec = nullptr;    // the last round's executable graph
     std::vector<cudaEvent_t> ev_pool;  // timing events of profiled launches
     stereo_stats stats{};
@@ -659,10 +660,12 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
     fill_group(seed, c->desc_host.as<char>(), (char*)c->desc_dev);
     fill_group(iter, c->desc_host.as<char>() + bs, (char*)c->desc_dev + bs);
 
-    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    cudaError_t err = record_round(c, seed, iter, Lr, s, bs + bi, seed_px, cells_bytes, raster_bytes, validate_bytes);
+    // capture on a private stream nobody else uses, launch on the context's stream
+    cudaStream_t cs = c->capture_stream;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = record_round(c, seed, iter, Lr, cs, bs + bi, seed_px, cells_bytes, raster_bytes, validate_bytes);
     cudaGraph_t graph = nullptr;
-    cudaError_t end = cudaStreamEndCapture(s, &graph);
+    cudaError_t end = cudaStreamEndCapture(cs, &graph);
     if (err == cudaSuccess) err = end;
     if (err != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
@@ -824,6 +827,7 @@ int stereo_create(const stereo_config* cfg, stereo_ctx** out) {
     c->arena.init(c->arena_base, c->cfg.mem_budget_bytes);
     cudaEventCreateWithFlags(&c->ev, cudaEventBlockingSync | cudaEventDisableTiming);
     cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+    cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
     c->pool.start(std::max(1, cfg->host_threads));
     c->sched = std::thread(scheduler, c);
     *out = c;
@@ -984,6 +988,7 @@ void stereo_destroy(stereo_ctx* c) {
     if (c->own_arena) cudaFree(c->arena_base);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     if (c->ev) cudaEventDestroy(c->ev);
     for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
     if (c->own_stream) cudaStreamDestroy(c->stream);
