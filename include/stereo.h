@@ -117,6 +117,11 @@ int stereo_release(stereo_ctx* ctx, uint64_t ticket);
 /* Cancel queued work, wait for in-flight work, free everything. */
 void stereo_destroy(stereo_ctx* ctx);
 
+/* Text of the last failing CUDA call inside the library (error name, code,
+ * source line, call), or "" when none failed.  The string is a thread-local
+ * copy, valid until the next call from the same thread. */
+const char* stereo_last_error(void);
+
 /* Kernel kinds of the per-kind counters in stereo_stats. */
 #define STEREO_K_CENSUS 0        /* census + Omega_I */
 #define STEREO_K_FAST_SCORE 1    /* FAST-9 scores */

@@ -66,6 +66,7 @@ _SIGS = {
     "stereo_release": (_I, [_P, ctypes.c_uint64]),
     "stereo_destroy": (None, [_P]),
     "stereo_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
+    "stereo_last_error": (ctypes.c_char_p, []),
     "stereo_census": (_I, [_P, _P, _I, _I, _I, _P, _P, _P, _P]),
     "stereo_fast": (_I, [_P, _I, _I, _I, _I, _P, _P, _P]),
     "stereo_epipolar_match": (_I, [_P, _P, _I, _I, _P, _I, _I, _I, _I, _P, _P]),
@@ -125,6 +126,8 @@ def _stream(s):
 
 def _check(rc, what):
     if rc < 0:
+        if rc == -7 and _lib is not None:
+            what = f"{what} [{_lib.stereo_last_error().decode()}]"
         raise StereoError(rc, what)
     return rc
 

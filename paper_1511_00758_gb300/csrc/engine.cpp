@@ -34,10 +34,21 @@ double now_ms() {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-#define CK(x)                                   \
-    do {                                        \
-        cudaError_t e_ = (x);                   \
-        if (e_ != cudaSuccess) return e_;       \
+// Last failing CUDA call of this process (for stereo_last_error).
+static std::mutex g_err_mu;
+static char g_err[256] = "";
+static void note_error(cudaError_t e, const char* what, int line) {
+    std::lock_guard<std::mutex> g(g_err_mu);
+    std::snprintf(g_err, sizeof(g_err), "%s (%d) at engine.cpp:%d: %s", cudaGetErrorName(e), (int)e, line, what);
+}
+
+#define CK(x)                                            \
+    do {                                                 \
+        cudaError_t e_ = (x);                            \
+        if (e_ != cudaSuccess) {                         \
+            note_error(e_, #x, __LINE__);                \
+            return e_;                                   \
+        }                                                \
     } while (0)
 
 // ------------------------------------------------------------------ arena
@@ -668,6 +679,7 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
     cudaError_t end = cudaStreamEndCapture(cs, &graph);
     if (err == cudaSuccess) err = end;
     if (err != cudaSuccess) {
+        note_error(err, "round capture", __LINE__);
         if (graph) cudaGraphDestroy(graph);
         Lr.timed.clear();
         return err;
@@ -685,6 +697,7 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
     if (!updated) err = cudaGraphInstantiate(&c->graph_exec, graph, 0);
     cudaGraphDestroy(graph);
     if (err != cudaSuccess) {
+        note_error(err, "cudaGraphInstantiate", __LINE__);
         c->graph_exec = nullptr;
         Lr.timed.clear();
         return err;
@@ -951,6 +964,13 @@ int stereo_release(stereo_ctx* c, uint64_t ticket) {
     delete r;
     c->cv_sched.notify_all();
     return STEREO_OK;
+}
+
+const char* stereo_last_error(void) {
+    std::lock_guard<std::mutex> g(g_err_mu);
+    static thread_local char copy[256];
+    std::memcpy(copy, g_err, sizeof(copy));
+    return copy;
 }
 
 int stereo_get_stats(stereo_ctx* c, stereo_stats* out) {
