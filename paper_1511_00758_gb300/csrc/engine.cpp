@@ -42,6 +42,12 @@ static void note_error(cudaError_t e, const char* what, int line) {
     std::snprintf(g_err, sizeof(g_err), "%s (%d) at engine.cpp:%d: %s", cudaGetErrorName(e), (int)e, line, what);
 }
 
+#define CKQ(x)                                    \
+    do {                                          \
+        cudaError_t e_ = (x);                     \
+        if (e_ != cudaSuccess) return e_;         \
+    } while (0)
+
 #define CK(x)                                            \
     do {                                                 \
         cudaError_t e_ = (x);                            \
@@ -294,7 +300,8 @@ struct stereo_ctx {
     cudaStream_t copy_stream = nullptr;      // submit-time device copies (never captured)
     cudaStream_t capture_stream = nullptr;   // private stream the rounds are captured on
     cudaGraphExec_t graph_exec = nullptr;    // the last round's executable graph
-    std::vector<cudaEvent_t> ev_pool;  // timing events of profiled launches
+    std::vector<cudaEvent_t> ev_pool;     // timing events of profiled launches
+    std::vector<cudaEvent_t> ev_retired;  // events of the last round (still in its graph)
     stereo_stats stats{};
 };
 
@@ -522,27 +529,32 @@ struct Launcher {
     };
     std::vector<Timed> timed;
 
-    cudaEvent_t event() {
-        if (!c->ev_pool.empty()) {
-            cudaEvent_t e = c->ev_pool.back();
-            c->ev_pool.pop_back();
-            return e;
-        }
-        cudaEvent_t e = nullptr;
-        cudaEventCreate(&e);
+    cudaEvent_t event() {  // the pool is filled before each capture (at most 24 per round)
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
         return e;
     }
     template <class F>
     cudaError_t run(int kind, int npairs, double bytes, F&& f) {
         cudaEvent_t a = nullptr;
+        cudaError_t e;
         if (c->cfg.profile) {  // event nodes of the round's graph: timed on the GPU, after it
             a = event();
-            CK(cudaEventRecordWithFlags(a, s, cudaEventRecordExternal));
+            if ((e = cudaEventRecordWithFlags(a, s, cudaEventRecordExternal)) != cudaSuccess) {
+                note_error(e, "event record before a launch", __LINE__);
+                return e;
+            }
         }
-        CK(f());
+        if ((e = f()) != cudaSuccess) {
+            note_error(e, "kernel launch", __LINE__);
+            return e;
+        }
         if (c->cfg.profile) {
             cudaEvent_t b = event();
-            CK(cudaEventRecordWithFlags(b, s, cudaEventRecordExternal));
+            if ((e = cudaEventRecordWithFlags(b, s, cudaEventRecordExternal)) != cudaSuccess) {
+                note_error(e, "event record after a launch", __LINE__);
+                return e;
+            }
             timed.push_back({kind, a, b});
         }
         delta.kernel_launches++;
@@ -551,13 +563,14 @@ struct Launcher {
         delta.batched_pairs += npairs;
         return cudaSuccess;
     }
-    // after the round's synchronisation
+    // after the round's synchronisation.  The round's events stay owned by
+    // the executable graph; they return to the pool when it is destroyed.
     void collect() {
         for (auto& t : timed) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) delta.kind_ms[t.kind] += ms;
-            c->ev_pool.push_back(t.a);
-            c->ev_pool.push_back(t.b);
+            c->ev_retired.push_back(t.a);
+            c->ev_retired.push_back(t.b);
         }
         timed.clear();
     }
@@ -585,19 +598,19 @@ cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, 
     const Params& prm = c->prm;
     const int ns = (int)seed.reqs.size(), ni = (int)iter.reqs.size();
     if (ns) {
-        CK(Lr.run(STEREO_K_CENSUS, ns, seed_px * 10.125, [&] { return launch_census(batch_of(seed, WK_CENSUS), prm, s); }));
-        CK(Lr.run(STEREO_K_FAST_SCORE, ns, seed_px * 3.0, [&] { return launch_fast_score(batch_of(seed, WK_FAST_SCORE), prm, s); }));
-        CK(Lr.run(STEREO_K_FAST_BINS, ns, 0.0, [&] { return launch_fast_bins(batch_of(seed, WK_FAST_BINS), prm, s); }));
-        CK(Lr.run(STEREO_K_MATCH_KP, ns, 0.0, [&] { return launch_match_kp(batch_of(seed, WK_MATCH_KP), prm, s); }));
+        CKQ(Lr.run(STEREO_K_CENSUS, ns, seed_px * 10.125, [&] { return launch_census(batch_of(seed, WK_CENSUS), prm, s); }));
+        CKQ(Lr.run(STEREO_K_FAST_SCORE, ns, seed_px * 3.0, [&] { return launch_fast_score(batch_of(seed, WK_FAST_SCORE), prm, s); }));
+        CKQ(Lr.run(STEREO_K_FAST_BINS, ns, 0.0, [&] { return launch_fast_bins(batch_of(seed, WK_FAST_BINS), prm, s); }));
+        CKQ(Lr.run(STEREO_K_MATCH_KP, ns, 0.0, [&] { return launch_match_kp(batch_of(seed, WK_MATCH_KP), prm, s); }));
     }
     if (ni) {
         PairBatch fb = batch_of(iter, WK_FILL);
-        if (fb.total > 0) CK(Lr.run(STEREO_K_FILL, ni, cells_bytes, [&] { return launch_fill_cells(fb, s); }));
-        CK(Lr.run(STEREO_K_RASTER_CLEAR, ni, raster_bytes, [&] { return launch_raster_clear(batch_of(iter, WK_CLEAR), s); }));
-        CK(Lr.run(STEREO_K_RASTER, ni, raster_bytes, [&] { return launch_raster(batch_of(iter, WK_RASTER), s); }));
-        CK(Lr.run(STEREO_K_VALIDATE, ni, validate_bytes, [&] { return launch_validate(batch_of(iter, WK_VALIDATE), prm, s); }));
+        if (fb.total > 0) CKQ(Lr.run(STEREO_K_FILL, ni, cells_bytes, [&] { return launch_fill_cells(fb, s); }));
+        CKQ(Lr.run(STEREO_K_RASTER_CLEAR, ni, raster_bytes, [&] { return launch_raster_clear(batch_of(iter, WK_CLEAR), s); }));
+        CKQ(Lr.run(STEREO_K_RASTER, ni, raster_bytes, [&] { return launch_raster(batch_of(iter, WK_RASTER), s); }));
+        CKQ(Lr.run(STEREO_K_VALIDATE, ni, validate_bytes, [&] { return launch_validate(batch_of(iter, WK_VALIDATE), prm, s); }));
         PairBatch rb = batch_of(iter, WK_RESAMPLE);
-        if (rb.total > 0) CK(Lr.run(STEREO_K_RESAMPLE, ni, 0.0, [&] { return launch_resample(rb, prm, s); }));
+        if (rb.total > 0) CKQ(Lr.run(STEREO_K_RESAMPLE, ni, 0.0, [&] { return launch_resample(rb, prm, s); }));
     }
     // results to pinned host memory
     for (Request* r : seed.reqs) {
@@ -671,16 +684,41 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
     fill_group(seed, c->desc_host.as<char>(), (char*)c->desc_dev);
     fill_group(iter, c->desc_host.as<char>() + bs, (char*)c->desc_dev + bs);
 
+    // Profiling: an event recorded by an external event node stays owned by
+    // the executable graph, so the previous executable is destroyed (and its
+    // events recycled) before the next capture, and each round instantiates
+    // afresh.  Timing events must exist before the capture that records them.
+    if (c->cfg.profile) {
+        if (c->graph_exec) {
+            cudaGraphExecDestroy(c->graph_exec);
+            c->graph_exec = nullptr;
+        }
+        for (cudaEvent_t ev : c->ev_retired) c->ev_pool.push_back(ev);
+        c->ev_retired.clear();
+    }
+    if (c->cfg.profile)
+        while (c->ev_pool.size() < 32) {
+            cudaEvent_t ev = nullptr;
+            CK(cudaEventCreate(&ev));
+            c->ev_pool.push_back(ev);
+        }
     // capture on a private stream nobody else uses, launch on the context's stream
     cudaStream_t cs = c->capture_stream;
+    Lr.s = cs;  // event records belong to the captured stream too
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     cudaError_t err = record_round(c, seed, iter, Lr, cs, bs + bi, seed_px, cells_bytes, raster_bytes, validate_bytes);
     cudaGraph_t graph = nullptr;
     cudaError_t end = cudaStreamEndCapture(cs, &graph);
-    if (err == cudaSuccess) err = end;
+    if (err == cudaSuccess && end != cudaSuccess) {
+        err = end;
+        note_error(err, "cudaStreamEndCapture", __LINE__);
+    }
     if (err != cudaSuccess) {
-        note_error(err, "round capture", __LINE__);
         if (graph) cudaGraphDestroy(graph);
+        for (auto& t : Lr.timed) {
+            c->ev_retired.push_back(t.a);
+            c->ev_retired.push_back(t.b);
+        }
         Lr.timed.clear();
         return err;
     }
@@ -1011,6 +1049,7 @@ void stereo_destroy(stereo_ctx* c) {
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     if (c->ev) cudaEventDestroy(c->ev);
     for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : c->ev_retired) cudaEventDestroy(ev);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
