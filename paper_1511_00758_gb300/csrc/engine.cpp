@@ -164,6 +164,7 @@ struct Request {
     PairDev dev{};
     int ncell_max = 0;
     int32_t* pidx_buf = nullptr;  // plane-index map, written on the last pass
+    uint32_t* cells_dev = nullptr;  // 4 * ncell_max words of cell records
     // triangle buffers (device) and their capacities
     void* tri_block = nullptr;
     size_t tri_block_bytes = 0;
@@ -190,8 +191,8 @@ size_t block_bytes(const Request& r, int K) {
     add(4 * N);                  // planeidx (FAST scores alias it)
     add(4 * N);                  // D_it
     add(4 * N); add(N); add(N);  // Df, Cf, mask
-    add((size_t)kFastBins * K * 8); add((size_t)kFastBins * K * 4);
-    for (int i = 0; i < 4; i++) add(4 * (size_t)r.ncell_max);
+    add((size_t)kFastBins * K * 12);
+    add(16 * (size_t)r.ncell_max);
     return b;
 }
 
@@ -214,12 +215,11 @@ void carve(Request& r, int K) {
     d.Df = (float*)take(4 * N);
     d.Cf = (uint8_t*)take(N);
     d.mask = (uint8_t*)take(N);
-    d.kp_uv = (int32_t*)take((size_t)kFastBins * K * 8);
-    d.kp_d = (int32_t*)take((size_t)kFastBins * K * 4);
-    d.cg_key = (uint32_t*)take(4 * (size_t)r.ncell_max);
-    d.cb_key = (uint32_t*)take(4 * (size_t)r.ncell_max);
-    d.cg_d = (float*)take(4 * (size_t)r.ncell_max);
-    d.x_d = (int32_t*)take(4 * (size_t)r.ncell_max);
+    d.kp_uv = (int32_t*)take((size_t)kFastBins * K * 12);  // (u, v) slots, then the matches
+    d.kp_d = d.kp_uv + (size_t)kFastBins * K * 2;
+    // cell records: four arrays laid out at the current pass's cell count, so
+    // one copy moves them (set per pass by set_cells)
+    r.cells_dev = (uint32_t*)take(16 * (size_t)r.ncell_max);
     d.W = r.W;
     d.H = r.H;
     d.dmax = r.dmax;
@@ -398,10 +398,10 @@ int host_after_seed(stereo_ctx* c, Request& r) {
 // (Alg. 4), in cell raster order, existing points first, then the next mesh.
 int host_after_iter(Request& r) {
     const int nc = cells_of(r.W, r.H, r.sz);
-    const uint32_t* gk = r.st_cells.as<uint32_t>();
-    const float* gd = (const float*)(gk + r.ncell_max);
-    const uint32_t* bk = gk + 2 * (size_t)r.ncell_max;
-    const int32_t* xd = (const int32_t*)(gk + 3 * (size_t)r.ncell_max);
+    const uint32_t* gk = r.st_cells.as<uint32_t>();  // cg_key, cg_d, cb_key, x_d at stride nc
+    const float* gd = (const float*)(gk + nc);
+    const uint32_t* bk = gk + 2 * (size_t)nc;
+    const int32_t* xd = (const int32_t*)(gk + 3 * (size_t)nc);
     std::vector<uint8_t> occ((size_t)r.W * r.H, 0);
     for (const auto& s : r.S) occ[(size_t)s.v * r.W + s.u] = 1;
     for (int c = 0; c < nc; c++) {
@@ -563,9 +563,11 @@ struct Launcher {
         delta.batched_pairs += npairs;
         return cudaSuccess;
     }
-    // after the round's synchronisation.  The round's events stay owned by
-    // the executable graph; they return to the pool when it is destroyed.
+    // after the round's synchronisation: read this round's durations; the
+    // previous round's events are no longer in any graph and return to the pool.
     void collect() {
+        for (cudaEvent_t ev : c->ev_retired) c->ev_pool.push_back(ev);
+        c->ev_retired.clear();
         for (auto& t : timed) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) delta.kind_ms[t.kind] += ms;
@@ -613,19 +615,12 @@ cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, 
         if (rb.total > 0) CKQ(Lr.run(STEREO_K_RESAMPLE, ni, 0.0, [&] { return launch_resample(rb, prm, s); }));
     }
     // results to pinned host memory
-    for (Request* r : seed.reqs) {
-        const int nk = kFastBins * c->K;
-        CK(cudaMemcpyAsync(r->st_kp.p, r->dev.kp_uv, (size_t)nk * 8, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(r->st_kp.as<char>() + (size_t)nk * 8, r->dev.kp_d, (size_t)nk * 4, cudaMemcpyDeviceToHost, s));
-    }
-    for (Request* r : iter.reqs) {
+    for (Request* r : seed.reqs)  // keypoint slots and their matches, one copy
+        CK(cudaMemcpyAsync(r->st_kp.p, r->dev.kp_uv, (size_t)kFastBins * c->K * 12, cudaMemcpyDeviceToHost, s));
+    for (Request* r : iter.reqs) {  // the four cell arrays of this pass, one copy
         if (!r->resample_now) continue;
-        const size_t nc = (size_t)r->dev.Wc * r->dev.Hc, m = r->ncell_max;
-        char* h = r->st_cells.as<char>();
-        CK(cudaMemcpyAsync(h, r->dev.cg_key, 4 * nc, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(h + 4 * m, r->dev.cg_d, 4 * nc, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(h + 8 * m, r->dev.cb_key, 4 * nc, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(h + 12 * m, r->dev.x_d, 4 * nc, cudaMemcpyDeviceToHost, s));
+        const size_t nc = (size_t)r->dev.Wc * r->dev.Hc;
+        CK(cudaMemcpyAsync(r->st_cells.p, r->cells_dev, 16 * nc, cudaMemcpyDeviceToHost, s));
     }
     return cudaSuccess;
 }
@@ -665,6 +660,13 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         r->resample_now = r->it < r->iters;
         r->dev.Wc = r->resample_now ? (r->W + r->sz - 1) / r->sz : 0;
         r->dev.Hc = r->resample_now ? (r->H + r->sz - 1) / r->sz : 0;
+        {
+            const size_t nc = (size_t)r->dev.Wc * r->dev.Hc;
+            r->dev.cg_key = r->cells_dev;
+            r->dev.cg_d = (float*)(r->cells_dev + nc);
+            r->dev.cb_key = r->cells_dev + 2 * nc;
+            r->dev.x_d = (int32_t*)(r->cells_dev + 3 * nc);
+        }
         const double px = (double)r->W * r->H;
         raster_bytes += px * (r->dev.planeidx ? 8.0 : 4.0);
         validate_bytes += px * (r->dev.first_pass ? 18.125 : 19.125);
@@ -684,18 +686,9 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
     fill_group(seed, c->desc_host.as<char>(), (char*)c->desc_dev);
     fill_group(iter, c->desc_host.as<char>() + bs, (char*)c->desc_dev + bs);
 
-    // Profiling: an event recorded by an external event node stays owned by
-    // the executable graph, so the previous executable is destroyed (and its
-    // events recycled) before the next capture, and each round instantiates
-    // afresh.  Timing events must exist before the capture that records them.
-    if (c->cfg.profile) {
-        if (c->graph_exec) {
-            cudaGraphExecDestroy(c->graph_exec);
-            c->graph_exec = nullptr;
-        }
-        for (cudaEvent_t ev : c->ev_retired) c->ev_pool.push_back(ev);
-        c->ev_retired.clear();
-    }
+    // Timing events must exist before the capture that records them.  The
+    // last round's events are still referenced by the executable graph until
+    // this round's update replaces them, so they are recycled a round later.
     if (c->cfg.profile)
         while (c->ev_pool.size() < 32) {
             cudaEvent_t ev = nullptr;
