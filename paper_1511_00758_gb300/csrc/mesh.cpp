@@ -3,7 +3,9 @@
 // Sec. III-B "solving a linear system", Eq. 3).
 //
 // Triangulation: Guibas-Stolfi divide and conquer on a quad-edge structure
-// (Guibas & Stolfi, ACM TOG 1985) with exact int64 predicates.  Cocircular
+// (Guibas & Stolfi, ACM TOG 1985) with exact int64 predicates, cutting
+// alternately along u and v (Dwyer's alternating cuts) so subproblems stay
+// near square on wide images.  Cocircular
 // ties resolve by symbolic perturbation of the lifted coordinate u^2 + v^2
 // (Edelsbrunner & Muecke 1990): a point of smaller canonical index (support
 // points sorted by (v, u)) carries a larger perturbation.  The perturbed
@@ -116,15 +118,51 @@ struct Mesh {
     bool rightof(int x, int e) const { return ccw(x, dest(e), org[e]); }
     bool leftof(int x, int e) const { return ccw(x, org[e], dest(e)); }
 
-    // s: vertex ids sorted lexicographically by (u, v).  Returns the
-    // counter-clockwise hull edge out of the leftmost vertex and the
-    // clockwise hull edge out of the rightmost one.
-    std::pair<int, int> build(const int* s, int n) {
-        if (n == 2) {
-            const int a = make_edge(s[0], s[1]);
-            return {a, sym(a)};
+    // Order of frame f: frame 0 is (u, v) lexicographic; frame 1 is the
+    // frame rotated by -90 degrees, (v, -u) lexicographic.  A rotation keeps
+    // the orientation and in-circle signs, so the merge logic is the same in
+    // both frames; only "leftmost" and "rightmost" change.
+    bool less_f(int a, int b, int f) const {
+        const int au = P[2 * a], av = P[2 * a + 1], bu = P[2 * b], bv = P[2 * b + 1];
+        if (f == 0) return au != bu ? au < bu : av < bv;
+        return av != bv ? av < bv : au > bu;
+    }
+
+    // Walk the hull from the clockwise hull edge e (outer face on its left)
+    // and return, for frame f, the counter-clockwise hull edge out of the
+    // minimum vertex and the clockwise hull edge out of the maximum vertex.
+    std::pair<int, int> reroot(int e, int f) const {
+        int emin = e, emax = e;   // clockwise edges out of the extreme vertices
+        int pmin = e;             // clockwise edge into the minimum vertex
+        int prev = e, cur = lnext(e);
+        // one full turn around the outer face
+        for (;;) {
+            const int v = org[cur];
+            if (less_f(v, org[emin], f)) { emin = cur; pmin = prev; }
+            if (less_f(org[emax], v, f)) emax = cur;
+            if (cur == e) break;
+            prev = cur;
+            cur = lnext(cur);
         }
-        if (n == 3) {
+        if (emin == e) {  // find the edge that enters org[e]
+            int q = e;
+            while (lnext(q) != e) q = lnext(q);
+            pmin = q;
+        }
+        return {sym(pmin), emax};
+    }
+
+    // s: n vertex ids (reordered in place).  Returns, in frame f, the
+    // counter-clockwise hull edge out of the minimum vertex and the clockwise
+    // hull edge out of the maximum vertex.  Cuts alternate between the two
+    // frames so the subproblems stay close to square.
+    std::pair<int, int> build(int* s, int n, int f) {
+        if (n <= 3) {
+            std::sort(s, s + n, [this, f](int a, int b) { return less_f(a, b, f); });
+            if (n == 2) {
+                const int a = make_edge(s[0], s[1]);
+                return {a, sym(a)};
+            }
             const int a = make_edge(s[0], s[1]);
             const int b = make_edge(s[1], s[2]);
             splice(sym(a), b);
@@ -139,9 +177,14 @@ struct Mesh {
             return {a, sym(b)};
         }
         const int h = n / 2;
-        auto L = build(s, h);
-        auto R = build(s + h, n - h);
-        int ldo = L.first, ldi = L.second, rdi = R.first, rdo = R.second;
+        std::nth_element(s, s + h, s + n, [this, f](int a, int b) { return less_f(a, b, f); });
+        const int g = 1 - f;
+        auto L = build(s, h, g);
+        auto R = build(s + h, n - h, g);
+        // hull handles of the children in this frame
+        auto Lf = reroot(L.second, f);
+        auto Rf = reroot(R.second, f);
+        int ldo = Lf.first, ldi = Lf.second, rdi = Rf.first, rdo = Rf.second;
         // lower common tangent
         for (;;) {
             if (leftof(org[rdi], ldi)) ldi = lnext(ldi);
@@ -189,15 +232,9 @@ int delaunay(const int32_t* uv, int n, int32_t* tri, int cap) {
     m.nxt.resize((size_t)24 * n);
     m.org.resize((size_t)24 * n, -1);
     m.dead.resize((size_t)6 * n, 0);
-    // (u, v) order for the divide and conquer: the input is sorted by (v, u),
-    // so a stable counting sort on u gives it in linear time
-    int umax = 0;
-    for (int i = 0; i < n; i++) umax = std::max(umax, uv[2 * i]);
-    std::vector<int> cnt((size_t)umax + 2, 0), s(n);
-    for (int i = 0; i < n; i++) cnt[uv[2 * i] + 1]++;
-    for (int u = 0; u <= umax; u++) cnt[u + 1] += cnt[u];
-    for (int i = 0; i < n; i++) s[cnt[uv[2 * i]]++] = i;
-    m.build(s.data(), n);
+    std::vector<int> s(n);
+    for (int i = 0; i < n; i++) s[i] = i;
+    m.build(s.data(), n, 0);
     // faces: each triangle once, from its directed edge leaving the smallest
     // vertex; bucketed by that vertex, so the output order is lexicographic
     // after sorting the (at most a few) triangles of each bucket
