@@ -130,6 +130,27 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ replicas across ranks
+def rank_shard(rank, batch):
+    """First pair index and count of a rank: every rank runs its own distinct pairs (no shared data)."""
+    return rank * batch, batch
+
+
+def max_over_ranks(value, world, dist=None, device="cpu"):
+    """The step time that counts is the slowest rank's (all ranks start after a barrier)."""
+    if world <= 1 or dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mpix_s(px_per_rank_step, steps, world, max_ms):
+    """Pixels all ranks processed divided by the slowest rank's time."""
+    return world * px_per_rank_step * steps / (max_ms / 1e3) / 1e6
+
+
 # ------------------------------------------------------------------ our arm
 def _source_hash():
     h = hashlib.sha256()
@@ -164,7 +185,8 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     S.load()
     B = args.batch
-    pairs = scenes.config_pairs(WORKLOAD, n=B, first=rank * B)
+    first, count = rank_shard(rank, B)
+    pairs = scenes.config_pairs(WORKLOAD, n=count, first=first)
     H, W = pairs[0].left.shape
     p0 = pairs[0]
     px_step = W * H * B
@@ -227,12 +249,8 @@ def run_ours(args):
     spans, lats = timed(args.steps)
     clk = clocks.stop()
     s1 = ctx.stats()
-    my_ms = sum(spans)
-    t = torch.tensor([my_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
-    value = world * px_step * args.steps / (max_ms / 1e3) / 1e6
+    max_ms = max_over_ranks(sum(spans), world, dist if world > 1 else None, device="cuda")
+    value = whole_job_mpix_s(px_step, args.steps, world, max_ms)
 
     # validate-kernel roofline from the events recorded inside the timed region
     k = S.KINDS.index("validate")
@@ -321,19 +339,179 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------ other workloads
+def _make_ctx(S, local, pairs, slots, threads, window_us=0, profile=1):
+    need = sum(80 * p.left.size + (96 << 20) for p in pairs[:slots])
+    return S.Context(device=local, mem_budget_bytes=int(0.5 * 2**30) + need, max_slots=slots, max_queue=4096,
+                     host_threads=threads, profile=profile, batch_window_us=window_us, **PRM)
+
+
+def run_batch_workload(args, name):
+    """One step = every pair of the workload through the batched engine."""
+    import torch
+
+    import paper_1511_00758_gb300 as S
+    import scenes
+    S.load()
+    torch.cuda.set_device(0)
+    pairs = scenes.mixed_pairs(64) if name == "mixed" else (scenes.large_pairs(16) if name == "large"
+                                                            else scenes.burst_pairs(32))
+    dev = [(torch.from_numpy(p.left).cuda(), torch.from_numpy(p.right).cuda()) for p in pairs]
+    threads = os.cpu_count() or 1
+    ctx = _make_ctx(S, 0, pairs, len(pairs), threads, args.window_us)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        lat = []
+        ts = [ctx.submit(l, r, p.left.shape[1], p.left.shape[0], p.dmax, p.iters, p.cell) for (l, r), p in zip(dev, pairs)]
+        for t in ts:
+            res = ctx.poll(t)
+            if res.status != 0:
+                raise RuntimeError(f"request failed: {res.status}")
+            lat.append(res.latency_ms)
+            ctx.release(t)
+        return lat
+    for _ in range(args.warmup):
+        step()
+    s0 = ctx.stats()
+    spans, lats = [], []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        lats += step()
+        e1.record(ctx.stream)
+        e1.synchronize()
+        spans.append(e0.elapsed_time(e1))
+    s1 = ctx.stats()
+    ctx.close()
+    px = sum(p.left.size for p in pairs)
+    tot = sum(spans) / 1e3
+    lats.sort()
+    k = 6  # validate
+    nl = s1.kind_launches[k] - s0.kind_launches[k]
+    kms = s1.kind_ms[k] - s0.kind_ms[k]
+    kb = s1.kind_bytes[k] - s0.kind_bytes[k]
+    desc = {"mixed": "64 uneven pairs (16 each of 320x240, 640x480, 1242x375 driving, 1280x720), dmax 64-128, "
+                     "3 iterations, 16x16 cells, one batch per step",
+            "large": "16 pairs of 2048x1536, 30-plane scenes, dmax 256, 5 iterations, 4x4 initial cells",
+            "burst": "32 concurrent 1920x1080 streams arriving together, dmax 128, 2 iterations, 16x16 cells"}[name]
+    out = {"metric": METRIC, "value": px * args.steps / tot / 1e6, "unit": "Mpix/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+           "higher_is_better": True, "data": "synthetic", "config": {"workload": desc, "pairs_per_step": len(pairs)},
+           "pairs_per_s": len(pairs) * args.steps / tot,
+           "latency_ms": {"p50": lats[len(lats) // 2], "p99": lats[min(len(lats) - 1, int(0.99 * len(lats)))]},
+           "host_mesh_ms_per_pair": (s1.host_mesh_ms - s0.host_mesh_ms) / max(1, s1.requests_done - s0.requests_done),
+           "validate_gbs": (kb / (kms * 1e-3) / 1e9) if kms > 0 else None,
+           "validate_pairs_per_launch": (s1.batched_pairs - s0.batched_pairs) / max(1, s1.kernel_launches - s0.kernel_launches),
+           "gpu_launches": s1.kernel_launches - s0.kernel_launches}
+    print(json.dumps(out))
+    return 0
+
+
+def run_serving(args):
+    """Eight camera streams with Poisson arrivals at 120 Hz each; requests are admitted as slots and
+    memory free up; latency is submit -> result ready."""
+    import queue
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_1511_00758_gb300 as S
+    import scenes
+    S.load()
+    torch.cuda.set_device(0)
+    streams = scenes.serving_streams()
+    host = [(torch.from_numpy(p.left).pin_memory(), torch.from_numpy(p.right).pin_memory()) for p in streams]
+    threads = os.cpu_count() or 1
+    ctx = _make_ctx(S, 0, streams * 2, 16, threads, window_us=0, profile=0)
+    rng = np.random.default_rng(0x5EED0004)
+    arrivals = []
+    for sid in range(len(streams)):
+        t = 0.0
+        while True:
+            t += rng.exponential(1.0 / args.rate_hz)
+            if t >= args.duration_s:
+                break
+            arrivals.append((t, sid))
+    arrivals.sort()
+    done_q = queue.Queue()
+    lat, errors = [], []
+
+    def poller():
+        while True:
+            item = done_q.get()
+            if item is None:
+                return
+            ticket = item
+            res = ctx.poll(ticket)
+            if res.status != 0:
+                errors.append(res.status)
+            lat.append(res.latency_ms)
+            ctx.release(ticket)
+    th = threading.Thread(target=poller)
+    th.start()
+    busy = 0
+    t0 = time.perf_counter()
+    for at, sid in arrivals:
+        now = time.perf_counter() - t0
+        if at > now:
+            time.sleep(at - now)
+        p = streams[sid]
+        l, r = host[sid]
+        while True:
+            try:
+                tk = ctx.submit(l, r, p.left.shape[1], p.left.shape[0], p.dmax, p.iters, p.cell, stream_id=sid)
+                break
+            except S.StereoError as e:
+                if e.code != -3:
+                    raise
+                busy += 1
+                time.sleep(0.0005)
+        done_q.put(tk)
+    done_q.put(None)
+    th.join()
+    wall = time.perf_counter() - t0
+    st = ctx.stats()
+    ctx.close()
+    lat.sort()
+    px = sum(streams[sid].left.size for _, sid in arrivals)
+    out = {"metric": "p50/p99 latency and throughput under Poisson arrivals", "unit": "ms",
+           "config": {"workload": f"8 streams (4 x 640x480 dmax 64, 4 x 1280x720 dmax 128), Poisson "
+                                  f"{args.rate_hz} Hz per stream for {args.duration_s} s, 2 iterations, 16x16 cells, "
+                                  "host input buffers, 16 slots"},
+           "requests": len(arrivals), "failed": len(errors), "busy_retries": busy,
+           "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                          "max": lat[-1]},
+           "throughput_pairs_per_s": len(arrivals) / wall, "throughput_mpix_s": px / wall / 1e6,
+           "offered_pairs_per_s": len(arrivals) / args.duration_s,
+           "mean_pairs_per_launch": st.batched_pairs / max(1, st.kernel_launches), "gpu_rounds": st.gpu_rounds}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--window-us", type=int, default=3000, help="batching window of the request scheduler")
+    ap.add_argument("--window-us", type=int, default=0, help="batching window of the request scheduler")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", choices=("driving", "mixed", "serving", "large", "burst"), default="driving")
+    ap.add_argument("--rate-hz", type=float, default=120.0)
+    ap.add_argument("--duration-s", type=float, default=10.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
+    if args.workload in ("mixed", "large", "burst"):
+        return run_batch_workload(args, args.workload)
     return run_ours(args)
 
 

@@ -66,6 +66,8 @@ typedef struct {
     void* stream;              /* cudaStream_t for all work (NULL = library creates one) */
     int profile;               /* 1 = time every kernel launch with CUDA events on `stream`
                                   and accumulate per-kind durations in stereo_stats */
+    int inject_mesh_failure;   /* testing: the n-th host mesh step of the context (1-based) fails
+                                  as if the triangulation had failed (STEREO_E_INTERNAL); 0 = off */
     int batch_window_us;       /* continuous batching: when some requests are ready for a GPU
                                   stage while others are still in their host step, wait up to
                                   this long for more of them before launching (0 = launch at once) */

@@ -34,7 +34,8 @@ class Config(ctypes.Structure):
                 ("max_slots", ctypes.c_int), ("max_queue", ctypes.c_int), ("t_lo", ctypes.c_int),
                 ("t_hi", ctypes.c_int), ("t_grad", ctypes.c_int), ("t_fast", ctypes.c_int),
                 ("kp_per_bin", ctypes.c_int), ("uniq_margin", ctypes.c_int), ("host_threads", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("profile", ctypes.c_int), ("batch_window_us", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("profile", ctypes.c_int), ("inject_mesh_failure", ctypes.c_int),
+                ("batch_window_us", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):

@@ -9,6 +9,7 @@
 // host mesh steps run on a worker pool meanwhile, so requests at different
 // iterations overlap.  max_slots = 1 gives the plain per-pair path.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
@@ -292,6 +293,7 @@ struct stereo_ctx {
     std::thread sched;
     bool stop = false;
     int host_busy = 0;
+    std::atomic<int> mesh_steps{0};  // host mesh steps run (for the failure-injection hook)
     Pool pool;
     Pinned desc_host;
     void* desc_dev = nullptr;
@@ -807,6 +809,8 @@ void scheduler(stereo_ctx* c) {
             const bool is_seed = r->it == 0;
             c->pool.push([c, r, is_seed] {
                 int rc = is_seed ? host_after_seed(c, *r) : host_after_iter(*r);
+                if (c->cfg.inject_mesh_failure > 0 && ++c->mesh_steps == c->cfg.inject_mesh_failure)
+                    rc = STEREO_E_INTERNAL;  // test hook: this host step reports a failure
                 std::lock_guard<std::mutex> g2(c->mu);
                 c->host_busy--;
                 if (rc != STEREO_OK) finish(c, *r, rc);

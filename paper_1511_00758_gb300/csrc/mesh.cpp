@@ -229,9 +229,9 @@ int delaunay(const int32_t* uv, int n, int32_t* tri, int cap) {
     if (n < 3) return 0;
     Mesh m;
     m.P = uv;
-    m.nxt.resize((size_t)24 * n);
-    m.org.resize((size_t)24 * n, -1);
-    m.dead.resize((size_t)6 * n, 0);
+    m.nxt.resize((size_t)16 * n);  // about 3n quad edges survive; make_edge grows on demand
+    m.org.resize((size_t)16 * n, -1);
+    m.dead.resize((size_t)4 * n, 0);
     std::vector<int> s(n);
     for (int i = 0; i < n; i++) s[i] = i;
     m.build(s.data(), n, 0);

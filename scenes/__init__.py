@@ -23,7 +23,8 @@ import numpy as np
 
 __all__ = [
     "Surface", "Scene", "StereoPair", "polygon_scene", "driving_scene",
-    "render", "make_pair", "CONFIGS", "config_pairs", "integer_shift_pair",
+    "render", "make_pair", "CONFIGS", "config_pairs", "integer_shift_pair", "mixed_pairs", "serving_streams",
+    "large_pairs", "burst_pairs",
 ]
 
 _OCT_SPACING = (16.0, 8.0, 4.0, 2.0)
@@ -289,6 +290,67 @@ CONFIGS = {
     "driving_1242x375": dict(kind="driving", W=1242, H=375, dmax=128, iters=3, cell=8, n=1, idx=1,
                              kw=dict(n_box=40, sigma=3.0, unmatched=0.05)),
 }
+
+
+def _mixed_spec(i):
+    """Pair i of the uneven batch: 16 each of 320x240, 640x480, 1242x375 (driving), 1280x720;
+    dmax drawn from 64..128 per pair; 3 iterations, 16x16 cells."""
+    sizes = [(320, 240, "polygon"), (640, 480, "polygon"), (1242, 375, "driving"), (1280, 720, "polygon")]
+    W, H, kind = sizes[i % 4]
+    dmax = int(_rng(SEED_BASE + 2000 + 7919 * i).integers(64, 129))
+    return kind, W, H, dmax
+
+
+def mixed_pairs(n=64, cache_dir=None):
+    """The uneven batch (64 pairs of four sizes, mixed dmax)."""
+    out = []
+    for i in range(n):
+        kind, W, H, dmax = _mixed_spec(i)
+        kw = dict(n_box=40, sigma=3.0, unmatched=0.05) if kind == "driving" else dict(n_poly=20, sigma=2.0)
+        out.append(_cached(f"mixed_{i}", cache_dir, lambda: make_pair(kind, W, H, SEED_BASE + 2000 + i, dmax, 3, 16, **kw),
+                           dmax, 3, 16))
+    return out
+
+
+def serving_streams(cache_dir=None):
+    """Eight camera streams: four 640x480 (dmax 64) and four 1280x720 (dmax 128); one rendered pair
+    per stream (frames of a stream are the same seeded scene); 2 iterations, 16x16 cells."""
+    out = []
+    for i in range(8):
+        W, H, dmax = (640, 480, 64) if i < 4 else (1280, 720, 128)
+        out.append(_cached(f"serving_{i}", cache_dir,
+                           lambda: make_pair("polygon", W, H, SEED_BASE + 3000 + i, dmax, 2, 16, n_poly=20, sigma=2.0),
+                           dmax, 2, 16))
+    return out
+
+
+def large_pairs(n=16, cache_dir=None):
+    """2048x1536 pairs, 30-plane scenes, dmax 256, 5 iterations, 4x4 initial cells."""
+    return [_cached(f"large_{i}", cache_dir,
+                    lambda: make_pair("polygon", 2048, 1536, SEED_BASE + 4000 + i, 256, 5, 4, n_poly=30, sigma=2.0),
+                    256, 5, 4) for i in range(n)]
+
+
+def burst_pairs(n=32, cache_dir=None):
+    """1920x1080 pairs for a burst of concurrent streams, dmax 128, 2 iterations, 16x16 cells."""
+    return [_cached(f"burst_{i}", cache_dir,
+                    lambda: make_pair("polygon", 1920, 1080, SEED_BASE + 5000 + i, 128, 2, 16, n_poly=20, sigma=2.0),
+                    128, 2, 16) for i in range(n)]
+
+
+def _cached(key, cache_dir, make, dmax, iters, cell):
+    cache_dir = cache_dir or os.environ.get("STEREO_SCENE_CACHE")
+    path = os.path.join(cache_dir, f"{key}.npz") if cache_dir else None
+    if path and os.path.exists(path):
+        z = np.load(path)
+        return StereoPair(z["left"], z["right"], z["gt_disp"], z["gt_occ"], dmax, iters, cell)
+    p = make()
+    if path:
+        os.makedirs(cache_dir, exist_ok=True)
+        tmp = path + f".{os.getpid()}.npz"
+        np.savez(tmp, left=p.left, right=p.right, gt_disp=p.gt_disp, gt_occ=p.gt_occ)
+        os.replace(tmp, path)
+    return p
 
 
 def config_pairs(name, n=None, first=0, cache_dir=None):

@@ -1,0 +1,88 @@
+"""Request API behaviour under load and failure, with the failures made on the
+host: a host mesh step that reports an error, a full queue, a context
+destroyed with work in flight.  No GPU fault is involved."""
+import numpy as np
+import pytest
+
+import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1511_00758_gb300 as S  # noqa: E402
+
+PRM = dict(t_lo=4, t_hi=8, t_grad=8, t_fast=20, kp_per_bin=4, uniq_margin=2)
+
+
+def _pairs(n, W=320, H=240, iters=3):
+    return [scenes.make_pair("polygon", W, H, 900 + i, 48, iters, 16, n_poly=8) for i in range(n)]
+
+
+def _solo(p):
+    with S.Context(mem_budget_bytes=1 << 28, **PRM) as ctx:
+        t = ctx.submit(p.left, p.right, p.left.shape[1], p.left.shape[0], p.dmax, p.iters, p.cell)
+        out = ctx.result_tensors(ctx.poll(t))
+        ctx.release(t)
+    return out
+
+
+def test_injected_host_failure_is_reported_and_isolated():
+    pairs = _pairs(5)
+    with S.Context(mem_budget_bytes=1 << 29, max_slots=5, host_threads=2, inject_mesh_failure=4, **PRM) as ctx:
+        ts = [ctx.submit(p.left, p.right, p.left.shape[1], p.left.shape[0], p.dmax, p.iters, p.cell) for p in pairs]
+        status, outs = [], []
+        for t in ts:
+            try:
+                outs.append(ctx.result_tensors(ctx.poll(t)))
+                status.append(0)
+            except S.StereoError as e:
+                status.append(e.code)
+                outs.append(None)
+            ctx.release(t)
+    assert status.count(-6) == 1 and status.count(0) == 4
+    for p, o in zip(pairs, outs):
+        if o is not None:
+            want = _solo(p)
+            for k in ("D_f", "C_f", "mask", "planeidx"):
+                assert torch.equal(o[k], want[k])
+
+
+def test_queue_full_returns_busy_then_drains():
+    pairs = _pairs(8, 1242, 375)
+    got_busy = 0
+    with S.Context(mem_budget_bytes=1 << 29, max_slots=1, max_queue=1, **PRM) as ctx:
+        ts = []
+        for p in pairs:
+            try:
+                ts.append(ctx.submit(p.left, p.right, p.left.shape[1], p.left.shape[0], p.dmax, p.iters, p.cell))
+            except S.StereoError as e:
+                assert e.code == -3
+                got_busy += 1
+        for t in ts:
+            assert ctx.poll(t).status == 0
+            ctx.release(t)
+        assert ctx.stats().requests_done == len(ts)
+    assert got_busy >= 1 and len(ts) >= 1
+
+
+def test_destroy_with_work_in_flight():
+    pairs = _pairs(6)
+    ctx = S.Context(mem_budget_bytes=1 << 29, max_slots=3, host_threads=2, **PRM)
+    for p in pairs:
+        ctx.submit(p.left, p.right, p.left.shape[1], p.left.shape[0], p.dmax, p.iters, p.cell)
+    ctx.close()  # queued work is cancelled, in-flight work finishes, nothing leaks or hangs
+
+
+def test_poll_timeout_and_unknown_ticket():
+    p = _pairs(1, 1242, 375)[0]
+    with S.Context(mem_budget_bytes=1 << 28, **PRM) as ctx:
+        t = ctx.submit(p.left, p.right, 1242, 375, p.dmax, p.iters, p.cell)
+        r = ctx.poll(t, timeout_us=0)  # almost surely still running: None, or done
+        assert r is None or r.status == 0
+        assert ctx.poll(t).status == 0
+        with pytest.raises(S.StereoError) as e:
+            ctx.release(t + 1000)
+        assert e.value.code == -8
+        ctx.release(t)
