@@ -410,6 +410,83 @@ def run_batch_workload(args, name):
     return 0
 
 
+def run_kernel(args, which):
+    """One kernel alone on a 4096x4096 frame (inputs larger than L2) through the stage entry points:
+    random images, their census, and a smooth slanted D_it field; CUDA events on the launching stream."""
+    import torch
+
+    import paper_1511_00758_gb300 as S
+    S.load()
+    torch.cuda.set_device(0)
+    W = H = args.kernel_size
+    g = torch.Generator(device="cuda").manual_seed(0x5EED0006)
+    L = torch.randint(0, 256, (H, W), dtype=torch.uint8, device="cuda", generator=g)
+    R = torch.roll(L, shifts=-5, dims=1).contiguous()
+    cL = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    cR = torch.empty_like(cL)
+    om = torch.empty((H, (W + 31) // 32), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    S.census(L, R, W, H, PRM["t_grad"], cL, cR, om, stream)
+    vv, uu = torch.meshgrid(torch.arange(H, device="cuda", dtype=torch.float32),
+                            torch.arange(W, device="cuda", dtype=torch.float32), indexing="ij")
+    Dit = (5.0 + 0.001 * uu + 0.002 * vv).contiguous()
+    Df = torch.zeros((H, W), dtype=torch.float32, device="cuda")
+    Cf = torch.full((H, W), PRM["t_hi"], dtype=torch.uint8, device="cuda")
+    mask = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+    sz = 8
+    nc = -(-W // sz) * -(-H // sz)
+    cg = torch.empty(nc, dtype=torch.int32, device="cuda")
+    cb = torch.empty(nc, dtype=torch.int32, device="cuda")
+    # a mesh for the raster: a jittered lattice of support points, triangulated on the host
+    import numpy as np
+    rng = np.random.default_rng(6)
+    step = 6
+    P = np.array([(min(W - 1, u + int(rng.integers(0, step))), min(H - 1, v + int(rng.integers(0, step))))
+                  for v in range(0, H, step) for u in range(0, W, step)], np.int32)
+    P = np.unique(P, axis=0)
+    P = np.ascontiguousarray(P[np.lexsort((P[:, 0], P[:, 1]))])
+    tri = np.zeros((2 * len(P) + 8, 3), np.int32)
+    T = S.delaunay(P, len(P), tri, len(tri))
+    D = (5.0 + 0.001 * P[:, 0] + 0.002 * P[:, 1]).astype(np.float32)
+    abc = np.zeros((T, 3), np.float32)
+    S.planes(P, D, tri[:T], T, abc)
+    tuv = torch.from_numpy(np.ascontiguousarray(P[tri[:T]].reshape(-1, 6))).cuda()
+    tabc = torch.from_numpy(abc).cuda()
+    nbytes = S.raster_scratch_bytes(T)
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    Dit2 = torch.empty_like(Dit)
+
+    def once():
+        if which == "validate":
+            cg.fill_(-1)
+            cb.fill_(-1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            S.validate(cL, cR, om, Dit, W, H, sz, PRM["t_lo"], PRM["t_hi"], 0, Df, Cf, mask, cg, cb, stream)
+            e1.record(stream)
+        else:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            S.raster(tuv, tabc, T, W, H, None, Dit2, scratch, nbytes, stream)
+            e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+    for _ in range(args.warmup):
+        once()
+    ms = [once() for _ in range(args.steps)]
+    avg = sum(ms) / len(ms)
+    px = W * H
+    algo = px * (19.125 if which == "validate" else 8.0)  # raster: clear + write of D_it
+    peaks = _peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    out = {"kernel": "k_validate" if which == "validate" else "k_raster_clear + k_raster (D_it only)",
+           "frame": f"{W}x{H}", "pixels": px, "triangles": T if which == "raster" else None,
+           "algorithmic_bytes": algo, "avg_us": 1e3 * avg, "gbs": algo / (avg * 1e-3) / 1e9,
+           "frac": algo / (avg * 1e-3) / 1e9 / peak, "peak": peak, "steps": args.steps, "warmup": args.warmup}
+    print(json.dumps(out))
+    return 0
+
+
 def run_serving(args):
     """Eight camera streams with Poisson arrivals at 120 Hz each; requests are admitted as slots and
     memory free up; latency is submit -> result ready."""
@@ -502,7 +579,9 @@ def main():
     ap.add_argument("--window-us", type=int, default=0, help="batching window of the request scheduler")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", choices=("driving", "mixed", "serving", "large", "burst"), default="driving")
+    ap.add_argument("--workload", choices=("driving", "mixed", "serving", "large", "burst", "kernel-validate",
+                                           "kernel-raster"), default="driving")
+    ap.add_argument("--kernel-size", type=int, default=4096)
     ap.add_argument("--rate-hz", type=float, default=120.0)
     ap.add_argument("--duration-s", type=float, default=10.0)
     args = ap.parse_args()
@@ -510,6 +589,8 @@ def main():
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload.startswith("kernel-"):
+        return run_kernel(args, args.workload.split("-", 1)[1])
     if args.workload in ("mixed", "large", "burst"):
         return run_batch_workload(args, args.workload)
     return run_ours(args)
