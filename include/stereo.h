@@ -205,8 +205,8 @@ int stereo_delaunay(const int32_t* uv, int n, int32_t* tri, int cap);
  * index order, rounded to fp32.  d: n fp32 support disparities; abc: 3*T. */
 int stereo_planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float* abc);
 
-/* Scratch bytes stereo_raster needs for T triangles: 2 * (T + 1) int32 of
- * work lists (rounded up to 256 bytes). */
+/* Scratch bytes stereo_raster needs for T triangles: 2 * (T + 1) +
+ * 2 * ceil(T / 1024) int32 of work lists (rounded up to 256 bytes). */
 size_t stereo_raster_scratch_bytes(int T);
 
 /* Pixel -> triangle lookup table (Sec. III-B) and DisparityInterpolation
@@ -228,7 +228,7 @@ int stereo_raster(const int32_t* tri_uv, const float* abc, int T, int w, int h, 
  * paper has no counterpart: it is a memory-management variant of
  * stereo_raster with the same arguments and results otherwise.  Its work
  * lists live in one file-scope device array sized for at most 262143
- * triangles (2 MiB, held by every GPU that loads the library until exit);
+ * triangles (just over 2 MiB, held by every GPU that loads the library until exit);
  * larger T returns STEREO_E_CAP.  The first call on each device looks up the
  * array's device address (no allocation); make that first call before any
  * stream capture.  All calls share the array: calls that overlap on the GPU

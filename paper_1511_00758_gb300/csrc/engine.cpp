@@ -1124,7 +1124,7 @@ int stereo_planes(const int32_t* uv, const float* d, const int32_t* tri, int T, 
 
 size_t stereo_raster_scratch_bytes(int T) {
     if (T < 0) return 0;
-    return align_up(8 * ((size_t)T + 1), 256);
+    return align_up(4 * raster_list_words(T), 256);
 }
 
 int stereo_raster(const int32_t* tri_uv, const float* abc, int T, int w, int h, int32_t* planeidx, float* D_it,
@@ -1132,7 +1132,7 @@ int stereo_raster(const int32_t* tri_uv, const float* abc, int T, int w, int h, 
     if (!valid_size(w, h) || T < 0 || (T > 0 && (!tri_uv || !scratch)) || (!planeidx && !D_it) ||
         (D_it && T > 0 && !abc) || ((uintptr_t)planeidx & 15) != 0 || ((uintptr_t)D_it & 15) != 0)
         return STEREO_E_INVAL;
-    if (T > 0 && scratch_bytes < 8 * ((size_t)T + 1)) return STEREO_E_CAP;
+    if (T > 0 && scratch_bytes < 4 * raster_list_words(T)) return STEREO_E_CAP;
     PairDev p{};
     p.W = w;
     p.H = h;

@@ -82,8 +82,10 @@ cudaError_t launch_match_kp(const PairBatch& b, const Params& prm, cudaStream_t 
 cudaError_t launch_raster_clear(const PairBatch& b, cudaStream_t s);
 cudaError_t launch_raster(const PairBatch& b, cudaStream_t s);
 // single pair whose work lists are built on the device (stage entry point):
-// tri_rows needs T + 1 and small_tri T + 1 entries
+// tri_rows needs T + 1 entries; small_tri T + 1 entries followed by
+// 2 * ceil(T / 1024) entries of block offsets
 cudaError_t launch_raster_device_lists(const PairDev& p, cudaStream_t s);
+inline size_t raster_list_words(int T) { return 2 * ((size_t)T + 1) + 2 * (((size_t)T + 1023) / 1024); }
 cudaError_t launch_validate(const PairBatch& b, const Params& prm, cudaStream_t s);
 cudaError_t launch_resample(const PairBatch& b, const Params& prm, cudaStream_t s);
 cudaError_t launch_fill_cells(const PairBatch& b, cudaStream_t s);

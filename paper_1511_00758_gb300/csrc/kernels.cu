@@ -507,52 +507,98 @@ __global__ void __launch_bounds__(256) k_raster(PairBatch b) {
 #undef BODY
 }
 
-// Device-built work lists for callers without a host copy of the triangles
-// (one block): rows[T + 1] chunk prefix of the large triangles, small[0..] the
-// small ones, small[T] their count.
-__global__ void __launch_bounds__(1024) k_raster_prefix(const int32_t* __restrict__ tri_uv, int T, int W, int H,
-                                                        int32_t* __restrict__ rows, int32_t* __restrict__ small) {
-    __shared__ int warp_sums[2][32];
-    const int chunk = (T + blockDim.x - 1) / blockDim.x;
-    const int a = min(T, (int)threadIdx.x * chunk), e = min(T, a + chunk);
-    int s = 0, ns = 0;
-    for (int t = a; t < e; t++) {
+// Device-built work lists for callers without a host copy of the triangles,
+// in three launches over blocks of 1024 triangles: per-block totals, a scan
+// of the block totals, then each block's exclusive scan written out.
+// rows[T + 1]: chunk prefix of the large triangles; small[0..n): the small
+// triangles in index order, small[T] = n; blk[2 * nblk]: block offsets.
+constexpr int kListBlock = 1024;
+
+__device__ __forceinline__ void tri_kind(const int32_t* __restrict__ tri_uv, int T, int W, int H, int t, int& chunks,
+                                         int& small) {
+    chunks = 0;
+    small = 0;
+    if (t < T) {
         const int32_t* q = tri_uv + 6 * (size_t)t;
-        s += tri_chunks(q, W, H);
-        ns += tri_is_small(q, W, H) ? 1 : 0;
+        chunks = tri_chunks(q, W, H);
+        small = tri_is_small(q, W, H) ? 1 : 0;
     }
+}
+
+// Block-wide inclusive scan of two counters (1024 threads).
+__device__ __forceinline__ void block_scan2(int& a, int& b, int (*ws)[32]) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int x = s, y = ns;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int xs = __shfl_up_sync(0xffffffffu, x, o), ys = __shfl_up_sync(0xffffffffu, y, o);
-        if (lane >= o) { x += xs; y += ys; }
+        const int xa = __shfl_up_sync(0xffffffffu, a, o), xb = __shfl_up_sync(0xffffffffu, b, o);
+        if (lane >= o) { a += xa; b += xb; }
     }
-    if (lane == 31) { warp_sums[0][w] = x; warp_sums[1][w] = y; }
+    if (lane == 31) { ws[0][w] = a; ws[1][w] = b; }
     __syncthreads();
     if (w == 0) {
-        int ws = lane < (int)(blockDim.x >> 5) ? warp_sums[0][lane] : 0;
-        int wn = lane < (int)(blockDim.x >> 5) ? warp_sums[1][lane] : 0;
+        int sa = ws[0][lane], sb = ws[1][lane];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int xs = __shfl_up_sync(0xffffffffu, ws, o), ys = __shfl_up_sync(0xffffffffu, wn, o);
-            if (lane >= o) { ws += xs; wn += ys; }
+            const int xa = __shfl_up_sync(0xffffffffu, sa, o), xb = __shfl_up_sync(0xffffffffu, sb, o);
+            if (lane >= o) { sa += xa; sb += xb; }
         }
-        warp_sums[0][lane] = ws;
-        warp_sums[1][lane] = wn;
+        ws[0][lane] = sa;
+        ws[1][lane] = sb;
     }
     __syncthreads();
-    int run = x - s + (w > 0 ? warp_sums[0][w - 1] : 0);
-    int runs = y - ns + (w > 0 ? warp_sums[1][w - 1] : 0);
-    for (int t = a; t < e; t++) {
-        const int32_t* q = tri_uv + 6 * (size_t)t;
-        rows[t] = run;
-        run += tri_chunks(q, W, H);
-        if (tri_is_small(q, W, H)) small[runs++] = t;
+    if (w > 0) { a += ws[0][w - 1]; b += ws[1][w - 1]; }
+}
+
+__global__ void __launch_bounds__(kListBlock) k_lists_count(const int32_t* __restrict__ tri_uv, int T, int W, int H,
+                                                            int32_t* __restrict__ blk) {
+    __shared__ int ws[2][32];
+    int c, s;
+    tri_kind(tri_uv, T, W, H, blockIdx.x * kListBlock + threadIdx.x, c, s);
+    block_scan2(c, s, ws);
+    if (threadIdx.x == kListBlock - 1) {
+        blk[2 * blockIdx.x] = c;
+        blk[2 * blockIdx.x + 1] = s;
     }
-    if (threadIdx.x == blockDim.x - 1) {
-        rows[T] = run;
-        small[T] = runs;
+}
+
+__global__ void __launch_bounds__(kListBlock) k_lists_scan(int32_t* __restrict__ blk, int nblk, int T,
+                                                           int32_t* __restrict__ rows, int32_t* __restrict__ small) {
+    __shared__ int ws[2][32];
+    int carry_c = 0, carry_s = 0;
+    for (int base = 0; base < nblk; base += kListBlock) {  // exclusive scan of the block totals
+        const int i = base + threadIdx.x;
+        int c = i < nblk ? blk[2 * i] : 0, s = i < nblk ? blk[2 * i + 1] : 0;
+        const int c0 = c, s0 = s;
+        block_scan2(c, s, ws);
+        if (i < nblk) {
+            blk[2 * i] = carry_c + c - c0;
+            blk[2 * i + 1] = carry_s + s - s0;
+        }
+        __syncthreads();  // every thread is done reading ws inside the scan
+        if (threadIdx.x == kListBlock - 1) { ws[0][0] = c; ws[1][0] = s; }
+        __syncthreads();
+        carry_c += ws[0][0];
+        carry_s += ws[1][0];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        rows[T] = carry_c;
+        small[T] = carry_s;
+    }
+}
+
+__global__ void __launch_bounds__(kListBlock) k_lists_write(const int32_t* __restrict__ tri_uv, int T, int W, int H,
+                                                            const int32_t* __restrict__ blk, int32_t* __restrict__ rows,
+                                                            int32_t* __restrict__ small) {
+    __shared__ int ws[2][32];
+    const int t = blockIdx.x * kListBlock + threadIdx.x;
+    int c, s;
+    tri_kind(tri_uv, T, W, H, t, c, s);
+    const int c0 = c, s0 = s;
+    block_scan2(c, s, ws);
+    if (t < T) {
+        rows[t] = blk[2 * blockIdx.x] + c - c0;
+        if (s0) small[blk[2 * blockIdx.x + 1] + s - 1] = t;
     }
 }
 
@@ -787,7 +833,11 @@ cudaError_t launch_raster(const PairBatch& b, cudaStream_t s) {
 }
 cudaError_t launch_raster_device_lists(const PairDev& p, cudaStream_t s) {
     if (p.T <= 0) return cudaSuccess;
-    k_raster_prefix<<<1, 1024, 0, s>>>(p.tri_uv, p.T, p.W, p.H, p.tri_rows, p.small_tri);
+    const int nblk = (p.T + kListBlock - 1) / kListBlock;
+    int32_t* blk = p.small_tri + p.T + 1;  // after the small list: 2 * nblk entries
+    k_lists_count<<<nblk, kListBlock, 0, s>>>(p.tri_uv, p.T, p.W, p.H, blk);
+    k_lists_scan<<<1, kListBlock, 0, s>>>(blk, nblk, p.T, p.tri_rows, p.small_tri);
+    k_lists_write<<<nblk, kListBlock, 0, s>>>(p.tri_uv, p.T, p.W, p.H, blk, p.tri_rows, p.small_tri);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_raster_dev<<<sm_count() * 8, 256, 0, s>>>(p.tri_uv, p.abc, p.tri_rows, p.small_tri, p.T, p.W, p.H,

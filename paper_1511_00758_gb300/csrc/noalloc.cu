@@ -10,7 +10,7 @@
 // inputs and outputs.
 //
 // The array holds the work lists of up to kNoAllocMaxTriangles triangles
-// (2 * (T + 1) int32 = 2 MiB).  Every GPU that loads the library keeps it
+// (2 * (T + 1) + 2 * ceil(T / 1024) int32, just over 2 MiB).  Every GPU that loads the library keeps it
 // until the process exits.  All calls share it: two calls whose work
 // overlaps on the GPU (different streams, or different threads without
 // ordering) race on it and must be serialised by the caller.  Nothing in it
@@ -25,8 +25,10 @@ namespace {
 constexpr int kNoAllocMaxTriangles = 262143;
 constexpr int kMaxDevices = 64;
 
-// Work lists: row-chunk offsets (T + 1) then the small-triangle list (T + 1).
-static __device__ __align__(256) int32_t g_raster_lists[2 * (kNoAllocMaxTriangles + 1)];
+// Work lists: row-chunk offsets (T + 1), the small-triangle list (T + 1),
+// then per-block offsets of the list builder.
+static __device__ __align__(256) int32_t
+    g_raster_lists[2 * (kNoAllocMaxTriangles + 1) + 2 * ((kNoAllocMaxTriangles + 1023) / 1024)];
 
 std::mutex g_mu;
 int32_t* g_addr[kMaxDevices] = {};
