@@ -455,6 +455,7 @@ def run_kernel(args, which):
     nbytes = S.raster_scratch_bytes(T)
     scratch = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     Dit2 = torch.empty_like(Dit)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
 
     def once():
         if which == "validate":
@@ -462,7 +463,11 @@ def run_kernel(args, which):
             cb.fill_(-1)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            S.validate(cL, cR, om, Dit, W, H, sz, PRM["t_lo"], PRM["t_hi"], 0, Df, Cf, mask, cg, cb, stream)
+            if args.plain_kernel:
+                S.validate(cL, cR, om, Dit, W, H, sz, PRM["t_lo"], PRM["t_hi"], 0, Df, Cf, mask, cg, cb, stream)
+            else:
+                S.validate_bulk(cL, cR, om, Dit, W, H, sz, PRM["t_lo"], PRM["t_hi"], 0, Df, Cf, mask, cg, cb, err,
+                                stream)
             e1.record(stream)
         else:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -479,7 +484,10 @@ def run_kernel(args, which):
     algo = px * (19.125 if which == "validate" else 8.0)  # raster: clear + write of D_it
     peaks = _peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    out = {"kernel": "k_validate" if which == "validate" else "k_raster_clear + k_raster (D_it only)",
+    if which == "validate" and not args.plain_kernel and int(err.item()) != 0:
+        raise RuntimeError("a bounded wait of the bulk validate kernel gave up")
+    out = {"kernel": ("k_validate" if args.plain_kernel else "k_validate_bulk") if which == "validate"
+           else "k_raster_clear + k_raster (D_it only)",
            "frame": f"{W}x{H}", "pixels": px, "triangles": T if which == "raster" else None,
            "algorithmic_bytes": algo, "avg_us": 1e3 * avg, "gbs": algo / (avg * 1e-3) / 1e9,
            "frac": algo / (avg * 1e-3) / 1e9 / peak, "peak": peak, "steps": args.steps, "warmup": args.warmup}
@@ -582,6 +590,7 @@ def main():
     ap.add_argument("--workload", choices=("driving", "mixed", "serving", "large", "burst", "kernel-validate",
                                            "kernel-raster"), default="driving")
     ap.add_argument("--kernel-size", type=int, default=4096)
+    ap.add_argument("--plain-kernel", action="store_true", help="kernel-validate: the single-pass kernel")
     ap.add_argument("--rate-hz", type=float, default=120.0)
     ap.add_argument("--duration-s", type=float, default=10.0)
     args = ap.parse_args()

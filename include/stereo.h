@@ -252,6 +252,19 @@ int stereo_validate(const uint32_t* cL, const uint32_t* cR, const uint32_t* omeg
                     int w, int h, int sz, int t_lo, int t_hi, int first_pass, float* D_f,
                     uint8_t* C_f, uint8_t* mask, uint32_t* cg_key, uint32_t* cb_key, void* stream);
 
+/* stereo_validate as a pipelined kernel: one producer warp per block stages
+ * each 128x8 tile's inputs into shared memory with asynchronous bulk copies
+ * (cp.async.bulk, completion on mbarriers) while eight consumer warps evaluate
+ * earlier tiles; the right-census columns a tile row needs are staged too.
+ * Same results as stereo_validate.  cL, cR, omega, D_it and C_f must be
+ * 16-byte aligned.  err_flag: device int the kernel sets to 1 if one of its
+ * bounded waits gave up (the outputs are then incomplete); the caller clears
+ * it and reads it after the stream synchronises. */
+int stereo_validate_bulk(const uint32_t* cL, const uint32_t* cR, const uint32_t* omega, const float* D_it,
+                         int w, int h, int sz, int t_lo, int t_hi, int first_pass, float* D_f,
+                         uint8_t* C_f, uint8_t* mask, uint32_t* cg_key, uint32_t* cb_key, int* err_flag,
+                         void* stream);
+
 /* SupportResampling (Alg. 4) per cell, fused with SparseEpipolarStereo on the
  * invalid cells: for each cell with a cg key, cg_d = D_it at that pixel; for
  * each cell with a cb key, x_d = the epipolar match of that pixel (as

@@ -14,7 +14,7 @@ from . import _build
 
 __all__ = [
     "StereoError", "load", "lib", "Config", "Result", "Stats", "Context",
-    "census", "fast", "epipolar_match", "delaunay", "planes", "raster_scratch_bytes", "raster", "raster_noalloc",
+    "census", "fast", "epipolar_match", "delaunay", "planes", "raster_scratch_bytes", "raster", "raster_noalloc", "validate_bulk",
     "validate", "resample_match", "ERRORS",
 ]
 
@@ -77,6 +77,7 @@ _SIGS = {
     "stereo_raster": (_I, [_P, _P, _I, _I, _I, _P, _P, _P, ctypes.c_size_t, _P]),
     "stereo_raster_noalloc": (_I, [_P, _P, _I, _I, _I, _P, _P, _P]),
     "stereo_validate": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P]),
+    "stereo_validate_bulk": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P]),
     "stereo_resample_match": (_I, [_P, _P, _I, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
 }
 SYMBOLS = tuple(_SIGS)
@@ -178,6 +179,13 @@ def validate(cL, cR, omega, D_it, w, h, sz, t_lo, t_hi, first_pass, D_f, C_f, ma
     return _check(lib().stereo_validate(_ptr(cL), _ptr(cR), _ptr(omega), _ptr(D_it), w, h, sz, t_lo, t_hi,
                                         int(first_pass), _ptr(D_f), _ptr(C_f), _ptr(mask), _ptr(cg_key),
                                         _ptr(cb_key), _stream(stream)), "validate")
+
+
+def validate_bulk(cL, cR, omega, D_it, w, h, sz, t_lo, t_hi, first_pass, D_f, C_f, mask, cg_key, cb_key, err_flag,
+                  stream=None):
+    return _check(lib().stereo_validate_bulk(_ptr(cL), _ptr(cR), _ptr(omega), _ptr(D_it), w, h, sz, t_lo, t_hi,
+                                             int(first_pass), _ptr(D_f), _ptr(C_f), _ptr(mask), _ptr(cg_key),
+                                             _ptr(cb_key), _ptr(err_flag), _stream(stream)), "validate_bulk")
 
 
 def resample_match(cg_key, cb_key, ncells, D_it, cL, cR, w, h, dmax, t_lo, margin, cg_d, x_d, stream=None):

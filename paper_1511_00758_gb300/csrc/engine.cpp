@@ -13,6 +13,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <functional>
@@ -302,6 +303,9 @@ struct stereo_ctx {
     cudaStream_t copy_stream = nullptr;      // submit-time device copies (never captured)
     cudaStream_t capture_stream = nullptr;   // private stream the rounds are captured on
     cudaGraphExec_t graph_exec = nullptr;    // the last round's executable graph
+    int* err_dev = nullptr;                  // set by a device-side wait that gave up
+    Pinned err_host;
+    bool bulk_validate = true;               // the bulk-copy validate kernel (else the plain one)
     std::vector<cudaEvent_t> ev_pool;     // timing events of profiled launches
     std::vector<cudaEvent_t> ev_retired;  // events of the last round (still in its graph)
     stereo_stats stats{};
@@ -599,7 +603,9 @@ cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, 
             CK(cudaMemcpyAsync((void*)r->dev.tri_uv, r->st_tri.p, tri_stage_bytes(r->T, r->raster_items, r->n_small),
                                cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->desc_dev, c->desc_host.p, desc_bytes, cudaMemcpyHostToDevice, s));
-    const Params& prm = c->prm;
+    CK(cudaMemsetAsync(c->err_dev, 0, sizeof(int), s));
+    Params prm = c->prm;
+    prm.err = c->err_dev;
     const int ns = (int)seed.reqs.size(), ni = (int)iter.reqs.size();
     if (ns) {
         CKQ(Lr.run(STEREO_K_CENSUS, ns, seed_px * 10.125, [&] { return launch_census(batch_of(seed, WK_CENSUS), prm, s); }));
@@ -612,11 +618,15 @@ cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, 
         if (fb.total > 0) CKQ(Lr.run(STEREO_K_FILL, ni, cells_bytes, [&] { return launch_fill_cells(fb, s); }));
         CKQ(Lr.run(STEREO_K_RASTER_CLEAR, ni, raster_bytes, [&] { return launch_raster_clear(batch_of(iter, WK_CLEAR), s); }));
         CKQ(Lr.run(STEREO_K_RASTER, ni, raster_bytes, [&] { return launch_raster(batch_of(iter, WK_RASTER), s); }));
-        CKQ(Lr.run(STEREO_K_VALIDATE, ni, validate_bytes, [&] { return launch_validate(batch_of(iter, WK_VALIDATE), prm, s); }));
+        CKQ(Lr.run(STEREO_K_VALIDATE, ni, validate_bytes, [&] {
+            return c->bulk_validate ? launch_validate_bulk(batch_of(iter, WK_VALIDATE), prm, s)
+                                    : launch_validate(batch_of(iter, WK_VALIDATE), prm, s);
+        }));
         PairBatch rb = batch_of(iter, WK_RESAMPLE);
         if (rb.total > 0) CKQ(Lr.run(STEREO_K_RESAMPLE, ni, 0.0, [&] { return launch_resample(rb, prm, s); }));
     }
     // results to pinned host memory
+    CK(cudaMemcpyAsync(c->err_host.p, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
     for (Request* r : seed.reqs)  // keypoint slots and their matches, one copy
         CK(cudaMemcpyAsync(r->st_kp.p, r->dev.kp_uv, (size_t)kFastBins * c->K * 12, cudaMemcpyDeviceToHost, s));
     for (Request* r : iter.reqs) {  // the four cell arrays of this pass, one copy
@@ -740,6 +750,10 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
     CK(cudaEventSynchronize(c->ev));
     Lr.collect();
     Lr.delta.gpu_rounds++;
+    if (*c->err_host.as<int>() != 0) {
+        note_error(cudaErrorTimeout, "a bounded device-side wait gave up", __LINE__);
+        return cudaErrorTimeout;
+    }
     return cudaSuccess;
 }
 
@@ -790,8 +804,11 @@ void scheduler(stereo_ctx* c) {
         std::lock_guard<std::mutex> g(c->mu);
         add_stats(c->stats, Lr.delta);
         if (e != cudaSuccess) {
-            for (Request* r : seed.reqs) finish(c, *r, e == cudaErrorMemoryAllocation ? STEREO_E_NOMEM : STEREO_E_CUDA);
-            for (Request* r : iter.reqs) finish(c, *r, e == cudaErrorMemoryAllocation ? STEREO_E_NOMEM : STEREO_E_CUDA);
+            const int rc = e == cudaErrorMemoryAllocation ? STEREO_E_NOMEM
+                           : e == cudaErrorTimeout           ? STEREO_E_TIMEOUT
+                                                             : STEREO_E_CUDA;
+            for (Request* r : seed.reqs) finish(c, *r, rc);
+            for (Request* r : iter.reqs) finish(c, *r, rc);
             cudaGetLastError();
             c->cv_done.notify_all();
             continue;
@@ -876,6 +893,13 @@ int stereo_create(const stereo_config* cfg, stereo_ctx** out) {
     cudaEventCreateWithFlags(&c->ev, cudaEventBlockingSync | cudaEventDisableTiming);
     cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
     cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
+    if (cudaMalloc((void**)&c->err_dev, 256) != cudaSuccess || !c->err_host.ensure(sizeof(int))) {
+        stereo_destroy(c);
+        return STEREO_E_NOMEM;
+    }
+    *c->err_host.as<int>() = 0;
+    if (const char* v = std::getenv("STEREO_VALIDATE")) c->bulk_validate = std::strcmp(v, "plain") != 0;
+    if (prepare_kernels() != cudaSuccess) c->bulk_validate = false;
     c->pool.start(std::max(1, cfg->host_threads));
     c->sched = std::thread(scheduler, c);
     *out = c;
@@ -1026,7 +1050,7 @@ void stereo_destroy(stereo_ctx* c) {
         c->stop = true;
     }
     c->cv_sched.notify_all();
-    c->sched.join();
+    if (c->sched.joinable()) c->sched.join();
     c->pool.stop();
     cudaStreamSynchronize(c->stream);
     for (auto& kv : c->reqs) {
@@ -1042,6 +1066,8 @@ void stereo_destroy(stereo_ctx* c) {
     if (c->desc_dev) cudaFree(c->desc_dev);
     if (c->own_arena) cudaFree(c->arena_base);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->err_dev) cudaFree(c->err_dev);
+    c->err_host.free();
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     if (c->ev) cudaEventDestroy(c->ev);
@@ -1173,6 +1199,41 @@ int stereo_validate(const uint32_t* cL, const uint32_t* cR, const uint32_t* omeg
     p.cb_key = cb_key;
     Params prm{t_lo, t_hi, 0, 0, 1, 0};
     return to_rc(launch_validate(single(p, WK_VALIDATE), prm, (cudaStream_t)stream));
+}
+
+int stereo_validate_bulk(const uint32_t* cL, const uint32_t* cR, const uint32_t* omega, const float* D_it, int w,
+                         int h, int sz, int t_lo, int t_hi, int first_pass, float* D_f, uint8_t* C_f, uint8_t* mask,
+                         uint32_t* cg_key, uint32_t* cb_key, int* err_flag, void* stream) {
+    if (!cL || !cR || !omega || !D_it || !D_f || !C_f || !err_flag || !valid_size(w, h) || sz < 1 ||
+        !(0 <= t_lo && t_lo <= t_hi && t_hi < 24) || ((cg_key == nullptr) != (cb_key == nullptr)))
+        return STEREO_E_INVAL;
+    if ((((uintptr_t)cL | (uintptr_t)cR | (uintptr_t)omega | (uintptr_t)D_it | (uintptr_t)C_f) & 15) != 0)
+        return STEREO_E_INVAL;
+    static int prepared_device = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (prepared_device != dev) {
+        if (prepare_kernels() != cudaSuccess) return STEREO_E_CUDA;
+        prepared_device = dev;
+    }
+    PairDev p{};
+    p.cL = (uint32_t*)cL;
+    p.cR = (uint32_t*)cR;
+    p.omega = (uint32_t*)omega;
+    p.Dit = (float*)D_it;
+    p.W = w;
+    p.H = h;
+    set_cell_size(p, sz);
+    p.Wc = (w + sz - 1) / sz;
+    p.Hc = (h + sz - 1) / sz;
+    p.first_pass = first_pass ? 1 : 0;
+    p.Df = D_f;
+    p.Cf = C_f;
+    p.mask = mask;
+    p.cg_key = cg_key;
+    p.cb_key = cb_key;
+    Params prm{t_lo, t_hi, 0, 0, 1, 0, err_flag};
+    return to_rc(launch_validate_bulk(single(p, WK_VALIDATE), prm, (cudaStream_t)stream));
 }
 
 int stereo_resample_match(const uint32_t* cg_key, const uint32_t* cb_key, int ncells, const float* D_it,

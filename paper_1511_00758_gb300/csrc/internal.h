@@ -65,6 +65,7 @@ struct PairBatch {
 
 struct Params {
     int t_lo, t_hi, t_grad, t_fast, K, margin;
+    int* err;  // device flag set when a bounded device-side wait gave up (may be null)
 };
 
 // Work items per pair for each kernel kind.
@@ -87,6 +88,11 @@ cudaError_t launch_raster(const PairBatch& b, cudaStream_t s);
 cudaError_t launch_raster_device_lists(const PairDev& p, cudaStream_t s);
 inline size_t raster_list_words(int T) { return 2 * ((size_t)T + 1) + 2 * (((size_t)T + 1023) / 1024); }
 cudaError_t launch_validate(const PairBatch& b, const Params& prm, cudaStream_t s);
+// Bulk-copy pipelined validate (same results).  Needs 16-byte aligned D_it,
+// cL, cR, C_f and Omega_I buffers; sets *prm.err if a bounded wait gave up.
+cudaError_t launch_validate_bulk(const PairBatch& b, const Params& prm, cudaStream_t s);
+size_t validate_bulk_smem_bytes();
+cudaError_t prepare_kernels();  // kernel attributes; call with the device current, outside capture
 cudaError_t launch_resample(const PairBatch& b, const Params& prm, cudaStream_t s);
 cudaError_t launch_fill_cells(const PairBatch& b, cudaStream_t s);
 cudaError_t launch_fill_u32(uint32_t* p, uint32_t value, size_t n, cudaStream_t s);

@@ -751,6 +751,359 @@ __global__ void __launch_bounds__(256) k_validate(PairBatch b, Params prm) {
 #undef BODY
 }
 
+// ---------------------------------------------------------------- fused validate: bulk-copy pipeline
+// The same computation as k_validate, organised for Blackwell's asynchronous
+// bulk copies.  Persistent blocks of one producer warp and eight consumer
+// warps (one per tile row) share a ring of kBS shared-memory stages guarded
+// by mbarriers.  Per tile the producer bulk-copies (cp.async.bulk) each row's
+// D_it, left census, C_f and Omega_I words into a stage; when they land it
+// takes the row's range of right-census columns u - rint(D_it) over the
+// evaluable pixels and bulk-copies that window of the right census too.  The
+// consumers then read every input from shared memory; a row whose column
+// range is wider than the window, and the last bytes of a buffer (copies stop
+// at the last 16-byte boundary inside it), fall back to global loads.
+// Every mbarrier wait is bounded: on timeout the thread sets *prm.err and
+// leaves, and the producer first waits (bounded) for its own copies.
+constexpr int kBS = 4;                       // ring stages
+constexpr int kBRowD = 136;                  // 4-byte words per staged D_it / cL row
+constexpr int kBRowF = 160;                  // bytes per staged C_f row
+constexpr int kBRowO = 8;                    // words per staged Omega_I row
+constexpr int kBRowR = 264;                  // words per staged right-census window row
+constexpr int kBWinMax = kBRowR - 8;         // widest column range staged
+constexpr unsigned kSpinLimit = 1u << 24;    // about a second with the back-off below
+
+// Pair descriptor and local work index of a batch item.
+__device__ __forceinline__ const PairDev& item_pair(const PairBatch& b, int item, int& local) {
+    if (b.pd) {
+        const int pi = find_pair(b.work_off, b.npairs, item);
+        local = item - __ldg(b.work_off + pi);
+        return b.pd[pi];
+    }
+    local = item;
+    return b.one;
+}
+
+struct BulkRowMeta {
+    int d_off, d_cnt;   // staged D_it / cL: element of pixel u0, elements present
+    int f_off, f_cnt;   // staged C_f bytes
+    int o_off, o_cnt;   // staged Omega_I words
+    int r_base, r_cnt;  // right census: global column of element 0 (-1: no window), elements present
+};
+
+struct __align__(16) BulkStage {
+    float d[kVH][kBRowD];
+    uint32_t cl[kVH][kBRowD];
+    uint32_t cr[kVH][kBRowR];
+    uint8_t cf[kVH][kBRowF];
+    uint32_t om[kVH][kBRowO];
+    BulkRowMeta meta[kVH];
+};
+
+struct __align__(16) BulkSmem {
+    BulkStage st[kBS];
+    uint32_t g[2][kMaxLocalCells], b[2][kMaxLocalCells];
+    unsigned long long full1[kBS], full2[kBS], empty[kBS];
+    unsigned long long cdone[2];  // consumer warps finished their cell minima (per cell buffer)
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the completion of the phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    for (unsigned i = 0; i < kSpinLimit; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 32) __nanosleep(64);
+    }
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+struct BulkCopy {
+    const void* src;
+    void* dst;
+    unsigned bytes;
+};
+
+// Plan the copy of elements [e0, e0 + n) of a buffer of ntot elements of es
+// bytes (16-byte aligned base) into dst: the 16-byte aligned span around them,
+// never past the last 16-byte boundary inside the buffer.
+__device__ __forceinline__ void plan_row(const void* base, size_t ntot, int es, size_t e0, int n, void* dst, int& off,
+                                         int& cnt, BulkCopy* cps, int& ncp) {
+    const uintptr_t b = (uintptr_t)base;
+    const uintptr_t s = b + e0 * es, e = b + (e0 + n) * es;
+    const uintptr_t as = s & ~(uintptr_t)15;
+    uintptr_t ae = (e + 15) & ~(uintptr_t)15;
+    const uintptr_t lim = (b + ntot * es) & ~(uintptr_t)15;
+    if (ae > lim) ae = lim;
+    off = (int)((s - as) / es);
+    cnt = 0;
+    if (n <= 0 || ae <= as) return;
+    cnt = (int)((ae - as) / es);
+    cps[ncp].src = (const void*)as;
+    cps[ncp].dst = dst;
+    cps[ncp].bytes = (unsigned)(ae - as);
+    ncp++;
+}
+
+__device__ __forceinline__ void bulk_producer(const PairBatch& b, const Params& prm, BulkSmem& sm) {
+    const int lane = threadIdx.x & 31;
+    int k = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < b.total; item += gridDim.x, k++) {
+        const int s = k % kBS;
+        const unsigned use = (unsigned)(k / kBS);
+        if (!mbar_wait(&sm.empty[s], (use & 1u) ^ 1u)) { ok = false; break; }
+        int local;
+        const PairDev& P = item_pair(b, item, local);
+        const int W = P.W, H = P.H;
+        const size_t N = (size_t)W * H;
+        const int words = (W + 31) >> 5;
+        const int tx_n = (W + kVW - 1) / kVW;
+        const int u0 = (local % tx_n) * kVW, v0 = (local / tx_n) * kVH;
+        BulkStage& st = sm.st[s];
+        // phase A: lane r < 8 plans row r's first-level copies
+        BulkCopy cps[4];
+        int ncp = 0;
+        unsigned bytes = 0;
+        if (lane < kVH) {
+            const int r = lane, v = v0 + r;
+            BulkRowMeta m{};
+            if (v < H) {
+                const int n = min(kVW, W - u0);
+                const size_t e0 = (size_t)v * W + u0;
+                plan_row(P.Dit, N, 4, e0, n, st.d[r], m.d_off, m.d_cnt, cps, ncp);
+                int o2, c2;
+                plan_row(P.cL, N, 4, e0, n, st.cl[r], o2, c2, cps, ncp);
+                m.d_cnt = min(m.d_cnt, c2);  // the two planned spans coincide in position
+                if (!P.first_pass) plan_row(P.Cf, N, 1, e0, n, st.cf[r], m.f_off, m.f_cnt, cps, ncp);
+                plan_row(P.omega, (size_t)H * words, 4, (size_t)v * words + (u0 >> 5), min(kVJ, words - (u0 >> 5)),
+                         st.om[r], m.o_off, m.o_cnt, cps, ncp);
+            }
+            st.meta[r] = m;
+            for (int i = 0; i < ncp; i++) bytes += cps[i].bytes;
+        }
+        const unsigned total = __reduce_add_sync(0xffffffffu, bytes);
+        if (lane == 0) mbar_arrive_expect_tx(&sm.full1[s], total);
+        __syncwarp();
+        for (int i = 0; i < ncp; i++) bulk_g2s(cps[i].dst, cps[i].src, cps[i].bytes, &sm.full1[s]);
+        // phase B: once the first-level rows landed, stage each row's right-census window
+        if (!mbar_wait(&sm.full1[s], use & 1u)) { ok = false; break; }
+        int my_lo = 0x7fffffff, my_hi = -1;
+        for (int r = 0; r < kVH; r++) {
+            const int v = v0 + r;
+            int lo = 0x7fffffff, hi = -1;
+            if (v < H) {
+                const BulkRowMeta& m = st.meta[r];
+#pragma unroll
+                for (int j = 0; j < kVJ; j++) {
+                    const int u = u0 + lane + 32 * j;
+                    if (u >= W) continue;
+                    const int oi = m.o_off + j;
+                    const uint32_t ow = oi < m.o_cnt ? st.om[r][oi] : __ldg(P.omega + (size_t)v * words + (u0 >> 5) + j);
+                    if (!((ow >> lane) & 1u)) continue;
+                    const int di = m.d_off + lane + 32 * j;
+                    const float d = di < m.d_cnt ? st.d[r][di] : __ldg(P.Dit + (size_t)v * W + u);
+                    const float col = (float)u - rintf(d);
+                    if (col >= 2.0f && col <= (float)(W - 3)) {
+                        lo = min(lo, (int)col);
+                        hi = max(hi, (int)col);
+                    }
+                }
+            }
+            lo = __reduce_min_sync(0xffffffffu, lo);
+            hi = __reduce_max_sync(0xffffffffu, hi);
+            if (lane == r) { my_lo = lo; my_hi = hi; }
+        }
+        ncp = 0;
+        bytes = 0;
+        if (lane < kVH) {
+            const int r = lane, v = v0 + r;
+            BulkRowMeta& m = st.meta[r];
+            m.r_base = -1;
+            m.r_cnt = 0;
+            if (v < H && my_hi >= my_lo && my_hi - my_lo + 1 <= kBWinMax) {
+                int off;
+                plan_row(P.cR, N, 4, (size_t)v * W + my_lo, my_hi - my_lo + 1, st.cr[r], off, m.r_cnt, cps, ncp);
+                m.r_base = my_lo - off;
+            }
+            for (int i = 0; i < ncp; i++) bytes += cps[i].bytes;
+        }
+        __syncwarp();  // row metadata written before the release below
+        const unsigned total2 = __reduce_add_sync(0xffffffffu, bytes);
+        if (lane == 0) mbar_arrive_expect_tx(&sm.full2[s], total2);
+        __syncwarp();
+        for (int i = 0; i < ncp; i++) bulk_g2s(cps[i].dst, cps[i].src, cps[i].bytes, &sm.full2[s]);
+    }
+    // drain: the copies this warp issued for the last stages land before it leaves
+    for (int j = max(0, k - kBS); j < k; j++) {
+        const int s = j % kBS;
+        const unsigned use = (unsigned)(j / kBS);
+        mbar_wait(&sm.full1[s], use & 1u);
+        mbar_wait(&sm.full2[s], use & 1u);
+    }
+    if (!ok && lane == 0 && prm.err) atomicExch(prm.err, 1);
+}
+
+__device__ __forceinline__ void bulk_consumer(const PairBatch& b, const Params& prm, BulkSmem& sm, int r) {
+    const int lane = threadIdx.x & 31;
+    const int ct = threadIdx.x - 32;  // consumer thread index, 0..255
+    const int t_lo = prm.t_lo, t_hi = prm.t_hi;
+    int k = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < b.total; item += gridDim.x, k++) {
+        const int s = k % kBS;
+        const unsigned use = (unsigned)(k / kBS);
+        if (!mbar_wait(&sm.full2[s], use & 1u)) { ok = false; break; }
+        int local;
+        const PairDev& P = item_pair(b, item, local);
+        const int W = P.W, H = P.H, Wc = P.Wc, first = P.first_pass, sz = P.sz, shift = P.sz_shift;
+        const uint32_t magic = P.sz_magic;
+        const int words = (W + 31) >> 5;
+        const int tx_n = (W + kVW - 1) / kVW;
+        const int u0 = (local % tx_n) * kVW, v0 = (local / tx_n) * kVH;
+        const int v = v0 + r;
+        const bool cells = P.cg_key != nullptr;
+        const int cb = k & 1;
+        const int cx0 = cell_div(u0, shift, magic), cy0 = cell_div(v0, shift, magic);
+        const int ncx = cell_div(min(u0 + kVW - 1, W - 1), shift, magic) - cx0 + 1;
+        const int ncy = cell_div(min(v0 + kVH - 1, H - 1), shift, magic) - cy0 + 1;
+        const BulkStage& st = sm.st[s];
+        if (v < H) {
+            const BulkRowMeta m = st.meta[r];
+            const size_t row = (size_t)v * W;
+            float* __restrict__ Df = P.Df;
+            uint8_t* __restrict__ Cf = P.Cf;
+            uint8_t* __restrict__ mask = P.mask;
+            int cost[kVJ];
+#pragma unroll
+            for (int j = 0; j < kVJ; j++) {
+                const int u = u0 + lane + 32 * j;
+                cost[j] = -1;
+                if (u >= W) continue;
+                const int oi = m.o_off + j;
+                const uint32_t ow = oi < m.o_cnt ? st.om[r][oi] : __ldg(P.omega + (size_t)v * words + (u0 >> 5) + j);
+                const bool om = (ow >> lane) & 1u;
+                const int di = m.d_off + lane + 32 * j;
+                const float d = di < m.d_cnt ? st.d[r][di] : __ldg(P.Dit + row + u);
+                const float col = (float)u - rintf(d);
+                uint8_t mk = om ? 1 : 0;
+                if (om && col >= 2.0f && col <= (float)(W - 3)) {
+                    const int c = (int)col;
+                    const uint32_t cl = di < m.d_cnt ? st.cl[r][di] : __ldg(P.cL + row + u);
+                    const int ri = c - m.r_base;
+                    const uint32_t cr = (m.r_base >= 0 && ri >= 0 && ri < m.r_cnt) ? st.cr[r][ri] : __ldg(P.cR + row + c);
+                    cost[j] = __popc(cl ^ cr);
+                    mk |= 2 | (cost[j] < t_lo ? 4 : 0) | (cost[j] > t_hi ? 8 : 0);
+                }
+                if (mask) mask[row + u] = mk;
+                const int cj = cost[j];
+                if (first) {
+                    const bool upd = cj >= 0 && cj < t_hi;
+                    Df[row + u] = upd ? d : 0.0f;
+                    Cf[row + u] = (uint8_t)(upd ? cj : t_hi);
+                } else if (cj >= 0) {
+                    const int fi = m.f_off + lane + 32 * j;
+                    const int cf = fi < m.f_cnt ? (int)st.cf[r][fi] : (int)Cf[row + u];
+                    if (cj < cf) {
+                        Df[row + u] = d;
+                        Cf[row + u] = (uint8_t)cj;
+                    }
+                }
+            }
+            if (cells) {
+                const int ly = cell_div(v, shift, magic) - cy0;
+                const bool warp_cell = sz >= 32 && (sz & 31) == 0;
+#pragma unroll
+                for (int j = 0; j < kVJ; j++) {
+                    const int u = u0 + lane + 32 * j;
+                    const int cj = cost[j];
+                    const uint32_t p = (uint32_t)(row + u);
+                    uint32_t kg = (cj >= 0 && cj < t_lo) ? (((uint32_t)cj << 27) | p) : kNoKey;
+                    uint32_t kb = (cj > t_hi) ? (((uint32_t)(24 - cj) << 27) | p) : kNoKey;
+                    const int lc = ly * ncx + ((int)cell_div(min(u, W - 1), shift, magic) - cx0);
+                    if (warp_cell) {
+                        kg = __reduce_min_sync(0xffffffffu, kg);
+                        kb = __reduce_min_sync(0xffffffffu, kb);
+                        if (lane == 0) {
+                            if (kg != kNoKey) atomicMin(&sm.g[cb][lc], kg);
+                            if (kb != kNoKey) atomicMin(&sm.b[cb][lc], kb);
+                        }
+                    } else {
+                        if (kg != kNoKey) atomicMin(&sm.g[cb][lc], kg);
+                        if (kb != kNoKey) atomicMin(&sm.b[cb][lc], kb);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive(&sm.empty[s]);     // this warp is done with the stage
+            mbar_arrive(&sm.cdone[cb]);    // and with its cell minima
+        }
+        // all eight consumer warps' minima are in before the flush (a bounded wait)
+        if (!mbar_wait(&sm.cdone[cb], (unsigned)(k >> 1) & 1u)) { ok = false; break; }
+        if (cells) {
+            for (int i = ct; i < ncx * ncy; i += 256) {
+                const int iy = i / ncx, ix = i - iy * ncx;
+                const size_t cell = (size_t)(cy0 + iy) * Wc + (cx0 + ix);
+                const uint32_t g = sm.g[cb][i], bb = sm.b[cb][i];
+                if (g != kNoKey) atomicMin(P.cg_key + cell, g);
+                if (bb != kNoKey) atomicMin(P.cb_key + cell, bb);
+                sm.g[cb][i] = kNoKey;
+                sm.b[cb][i] = kNoKey;
+            }
+        }
+    }
+    if (!ok && lane == 0 && prm.err) atomicExch(prm.err, 1);
+}
+
+__global__ void __launch_bounds__(288, 2) k_validate_bulk(PairBatch b, Params prm) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    BulkSmem& sm = *reinterpret_cast<BulkSmem*>(smraw);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kBS; s++) {
+            mbar_init(&sm.full1[s], 1);
+            mbar_init(&sm.full2[s], 1);
+            mbar_init(&sm.empty[s], kVH);
+        }
+        mbar_init(&sm.cdone[0], kVH);
+        mbar_init(&sm.cdone[1], kVH);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = threadIdx.x; i < 2 * kMaxLocalCells; i += blockDim.x) {
+        (&sm.g[0][0])[i] = kNoKey;
+        (&sm.b[0][0])[i] = kNoKey;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) bulk_producer(b, prm, sm);
+    else bulk_consumer(b, prm, sm, (threadIdx.x >> 5) - 1);
+}
+
 // ---------------------------------------------------------------- resample + match (Alg. 4)
 // One warp per cell: a C_g key becomes the interpolated disparity at its
 // pixel; a C_b key is matched along its row by the same warp search.
@@ -847,6 +1200,15 @@ cudaError_t launch_raster_device_lists(const PairDev& p, cudaStream_t s) {
 cudaError_t launch_validate(const PairBatch& b, const Params& prm, cudaStream_t s) {
     if (b.total <= 0) return cudaSuccess;
     k_validate<<<grid_for(b.total, 8), 256, 0, s>>>(b, prm);
+    return cudaGetLastError();
+}
+size_t validate_bulk_smem_bytes() { return sizeof(BulkSmem); }
+cudaError_t prepare_kernels() {  // once per device, outside any stream capture
+    return cudaFuncSetAttribute(k_validate_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BulkSmem));
+}
+cudaError_t launch_validate_bulk(const PairBatch& b, const Params& prm, cudaStream_t s) {
+    if (b.total <= 0) return cudaSuccess;
+    k_validate_bulk<<<grid_for(b.total, 2), 288, sizeof(BulkSmem), s>>>(b, prm);
     return cudaGetLastError();
 }
 cudaError_t launch_resample(const PairBatch& b, const Params& prm, cudaStream_t s) {

@@ -168,9 +168,11 @@ def _support_case(oracle_mod, p, n=400, seed=0):
     return P, D
 
 
+@pytest.mark.parametrize("bulk", [0, 1])
 @pytest.mark.parametrize("name,sz,first", [("vga_polygons", 16, 1), ("driving_1242x375", 8, 0),
-                                           ("driving_1242x375", 1, 0), ("vga_polygons", 3, 0)])
-def test_validate(oracle_mod, name, sz, first):
+                                           ("driving_1242x375", 1, 0), ("vga_polygons", 3, 0),
+                                           ("driving_1242x375", 64, 1)])
+def test_validate(oracle_mod, name, sz, first, bulk):
     p = scenes.config_pairs(name)[0]
     H, W = p.left.shape
     P, D = _support_case(oracle_mod, p)
@@ -195,7 +197,13 @@ def test_validate(oracle_mod, name, sz, first):
     nc = ro["Wc"] * ro["Hc"]
     cg = torch.full((nc,), -1, dtype=torch.int32, device=DEV)
     cb = torch.full((nc,), -1, dtype=torch.int32, device=DEV)
-    S.validate(cL, cR, om, dit, W, H, sz, PRM["t_lo"], PRM["t_hi"], first, Df, Cf, mask, cg, cb)
+    if bulk:
+        err = torch.zeros(1, dtype=torch.int32, device=DEV)
+        S.validate_bulk(cL, cR, om, dit, W, H, sz, PRM["t_lo"], PRM["t_hi"], first, Df, Cf, mask, cg, cb, err)
+        _sync()
+        assert int(err.item()) == 0
+    else:
+        S.validate(cL, cR, om, dit, W, H, sz, PRM["t_lo"], PRM["t_hi"], first, Df, Cf, mask, cg, cb)
     _sync()
     assert np.array_equal(mask.cpu().numpy(), ro["mask"])
     assert np.array_equal(Cf.cpu().numpy(), Cf_o)
