@@ -305,7 +305,7 @@ struct stereo_ctx {
     cudaGraphExec_t graph_exec = nullptr;    // the last round's executable graph
     int* err_dev = nullptr;                  // set by a device-side wait that gave up
     Pinned err_host;
-    bool bulk_validate = true;               // the bulk-copy validate kernel (else the plain one)
+    bool bulk_validate = false;              // the bulk-copy validate kernel (else the plain one)
     std::vector<cudaEvent_t> ev_pool;     // timing events of profiled launches
     std::vector<cudaEvent_t> ev_retired;  // events of the last round (still in its graph)
     stereo_stats stats{};
@@ -898,7 +898,7 @@ int stereo_create(const stereo_config* cfg, stereo_ctx** out) {
         return STEREO_E_NOMEM;
     }
     *c->err_host.as<int>() = 0;
-    if (const char* v = std::getenv("STEREO_VALIDATE")) c->bulk_validate = std::strcmp(v, "plain") != 0;
+    if (const char* v = std::getenv("STEREO_VALIDATE")) c->bulk_validate = std::strcmp(v, "bulk") == 0;
     if (prepare_kernels() != cudaSuccess) c->bulk_validate = false;
     c->pool.start(std::max(1, cfg->host_threads));
     c->sched = std::thread(scheduler, c);

@@ -299,6 +299,13 @@ def test_end_to_end_degenerate(oracle_mod):
     _compare_run(oracle_mod, tiny, _run_ctx([tiny])[0])
 
 
+def test_end_to_end_bulk_validate(oracle_mod, monkeypatch):
+    """The engine with the bulk-copy validate kernel gives the same results."""
+    monkeypatch.setenv("STEREO_VALIDATE", "bulk")
+    p = scenes.config_pairs("driving_1242x375")[0]
+    _compare_run(oracle_mod, p, _run_ctx([p])[0])
+
+
 def test_batched_serving_matches_solo(oracle_mod):
     """Continuous batching: results in a mixed batch equal solo results bit for bit."""
     pairs = [scenes.make_pair("polygon", 320, 240, 500 + i, 64, 3, 16, n_poly=10) for i in range(3)]
