@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(256) k_match_list(const uint32_t* cL, const ui
 // cleared values (-1, NaN).  D_it = fma(a, u, fma(b, v, c)) in fp32.
 // Small triangles (bounding box of at most kSmallArea pixels): one thread
 // walks the box with incremental edge values.  Larger ones: one warp per
-// chunk of 8 rows, lanes 0..7 bound one row each by exact int32 floor/ceil
+// chunk of kRasterRows rows, one lane per row bounds it by exact int32 floor/ceil
 // division, then lanes stride the columns.
 struct TriEdges {
     int x[3], y[3];
@@ -392,11 +392,6 @@ __device__ __forceinline__ int tri_chunks(const int32_t* __restrict__ q, int W, 
     return (y1 - y0) / kRasterRows + 1;
 }
 
-__device__ __forceinline__ void put(int32_t* __restrict__ pidx, float* __restrict__ dit, size_t p, int t, float a,
-                                    float b, float c, int u, int v) {
-    if (pidx) pidx[p] = t;
-    if (dit) dit[p] = __fmaf_rn(a, (float)u, __fmaf_rn(b, (float)v, c));
-}
 
 __device__ __forceinline__ void raster_small(const int32_t* __restrict__ tri_uv, const float* __restrict__ abc,
                                              int t, int W, int H, int32_t* __restrict__ pidx,
@@ -415,8 +410,19 @@ __device__ __forceinline__ void raster_small(const int32_t* __restrict__ tri_uv,
         int e0 = e.A[0] * x0 + e.B[0] * v + e.C[0];
         int e1 = e.A[1] * x0 + e.B[1] * v + e.C[1];
         int e2 = e.A[2] * x0 + e.B[2] * v + e.C[2];
+        const float rowterm = __fmaf_rn(b, (float)v, c);  // D_it = fma(a, u, fma(b, v, c))
+        int32_t* prow = pidx ? pidx + (size_t)v * W : nullptr;
+        float* drow = dit ? dit + (size_t)v * W : nullptr;
+        bool seen = false;
         for (int u = x0; u <= x1; u++) {
-            if (e0 >= e.bias[0] && e1 >= e.bias[1] && e2 >= e.bias[2]) put(pidx, dit, (size_t)v * W + u, t, a, b, c, u, v);
+            const bool in = e0 >= e.bias[0] && e1 >= e.bias[1] && e2 >= e.bias[2];
+            if (in) {
+                if (prow) prow[u] = t;
+                if (drow) drow[u] = __fmaf_rn(a, (float)u, rowterm);
+            } else if (seen) {
+                break;  // a row of a convex triangle is one run
+            }
+            seen |= in;
             e0 += e.A[0];
             e1 += e.A[1];
             e2 += e.A[2];
@@ -457,7 +463,13 @@ __device__ __forceinline__ void raster_chunk_tc(const int32_t* __restrict__ tri_
     for (int r = 0; r < nrows; r++) {
         const int a = __shfl_sync(0xffffffffu, lo, r), b = __shfl_sync(0xffffffffu, hi, r);
         const int v = v0 + r;
-        for (int u = a + lane; u <= b; u += 32) put(pidx, dit, (size_t)v * W + u, t, pa, pb, pc, u, v);
+        const float rowterm = __fmaf_rn(pb, (float)v, pc);  // D_it = fma(a, u, fma(b, v, c))
+        int32_t* prow = pidx ? pidx + (size_t)v * W : nullptr;
+        float* drow = dit ? dit + (size_t)v * W : nullptr;
+        for (int u = a + lane; u <= b; u += 32) {
+            if (prow) prow[u] = t;
+            if (drow) drow[u] = __fmaf_rn(pa, (float)u, rowterm);
+        }
     }
 }
 
