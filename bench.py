@@ -440,7 +440,7 @@ def run_kernel(args, which):
     # a mesh for the raster: a jittered lattice of support points, triangulated on the host
     import numpy as np
     rng = np.random.default_rng(6)
-    step = 6
+    step = args.mesh_step
     P = np.array([(min(W - 1, u + int(rng.integers(0, step))), min(H - 1, v + int(rng.integers(0, step))))
                   for v in range(0, H, step) for u in range(0, W, step)], np.int32)
     P = np.unique(P, axis=0)
@@ -591,6 +591,7 @@ def main():
                                            "kernel-raster"), default="driving")
     ap.add_argument("--kernel-size", type=int, default=4096)
     ap.add_argument("--plain-kernel", action="store_true", help="kernel-validate: the single-pass kernel")
+    ap.add_argument("--mesh-step", type=int, default=6, help="kernel-raster: support-point spacing in pixels")
     ap.add_argument("--rate-hz", type=float, default=120.0)
     ap.add_argument("--duration-s", type=float, default=10.0)
     args = ap.parse_args()

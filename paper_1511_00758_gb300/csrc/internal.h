@@ -12,7 +12,7 @@ constexpr int kFastBins = 120;          // 12 x 10 spatial bins (Sec. III-A)
 constexpr int kFastBinsX = 12;
 constexpr int kFastBinsY = 10;
 constexpr int kMaxK = 32;               // keypoints per bin, upper bound
-constexpr int kRasterRows = 2;          // triangle rows per raster work item (large triangles)
+constexpr int kRasterRows = 8;          // triangle rows per raster work item (large triangles)
 constexpr int kSmallArea = 256;         // bounding-box pixels of a thread-rasterised triangle
 constexpr uint32_t kNoKey = 0xFFFFFFFFu;
 constexpr uint32_t kIdxMask = (1u << 27) - 1;
