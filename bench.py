@@ -159,14 +159,16 @@ def _source_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel):
-    """ncu DRAM bytes per launch of the kernel, if the committed capture is of the current source."""
+def _traffic(kind, algo_bytes_per_launch):
+    """DRAM bytes per launch from the committed ncu capture of this kernel kind, scaled from the
+    captured launch to this run's average launch by algorithmic bytes (traffic grows in proportion);
+    None when there is no capture or the kernel source changed since it was taken."""
     try:
         d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
-        e = d[kernel]
-        if e.get("source_hash") != _source_hash():
+        e = d[kind]
+        if e.get("source_hash") != _source_hash() or not algo_bytes_per_launch:
             return None
-        return e["dram_bytes_per_launch"]
+        return e["dram_bytes"] * algo_bytes_per_launch / e["algorithmic_bytes"]
     except Exception:
         return None
 
@@ -273,7 +275,7 @@ def run_ours(args):
     roofline = {"kernel": names.get(rk, rk), "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None,
                 "peak_source": "measured" if peaks else "fallback",
-                "traffic": _traffic(rk), "launches": nl, "avg_launch_us": 1e3 * kms / nl if nl else None,
+                "traffic": _traffic(rk, kbytes / nl if nl else None), "launches": nl, "avg_launch_us": 1e3 * kms / nl if nl else None,
                 "algorithmic_bytes_per_launch": kbytes / nl if nl else None,
                 "share_of_kernel_time": kms / max(1e-9, sum(v[1] for v in per.values())),
                 "dominant_kernel": dominant, "pairs_per_launch_mean": None}
