@@ -261,7 +261,7 @@ def run_ours(args):
     for i, name in enumerate(S.KINDS):
         nl = s1.kind_launches[i] - s0.kind_launches[i]
         per[name] = (nl, s1.kind_ms[i] - s0.kind_ms[i], s1.kind_bytes[i] - s0.kind_bytes[i])
-    # the raster pass is two launches (clear, scan conversion) over the same map
+    # a separate clear launch (if any) belongs to the raster pass over the same map
     rc, rr = per.pop("raster_clear"), per.pop("raster")
     per["raster"] = (rr[0], rc[1] + rr[1], rc[2] + rr[2])
     dominant = max(per, key=lambda n: per[n][1])
@@ -270,7 +270,7 @@ def run_ours(args):
     nl, kms, kbytes = per[rk]
     achieved = (kbytes / nl) / (kms / nl * 1e-3) / 1e9 if nl and kms > 0 else None
     names = {"validate": "k_validate (cost evaluation + refinement, fused)",
-             "raster": "k_raster_clear + k_raster (lookup table + interpolation)",
+             "raster": "k_raster (lookup table + interpolation, hull-interval clear fused)",
              "census": "k_census", "fast_score": "k_fast_score", "fill": "k_fill_cells"}
     roofline = {"kernel": names.get(rk, rk), "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None,

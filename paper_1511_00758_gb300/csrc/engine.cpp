@@ -175,7 +175,7 @@ struct Request {
     std::vector<int32_t> n_support, n_tri;
     std::vector<float> trace;
     int T = 0;
-    int raster_items = 0, n_small = 0;
+    int raster_items = 0, n_small = 0, n_hull = 0;
     Pinned st_tri;            // one mesh, laid out as tri_stage_bytes() describes
     Pinned st_kp;             // kp_uv + kp_d
     Pinned st_cells;          // cg_key, cg_d, cb_key, x_d
@@ -322,11 +322,12 @@ bool valid_size(int w, int h) {
     return w >= 5 && h >= 5 && w <= 8192 && h <= 8192 && (long long)w * h < (1ll << 27);
 }
 
-// Staging layout of one mesh: tri_uv (6 int32) and abc (3 fp32) per
-// triangle, T + 1 chunk offsets, the triangle of every raster chunk, then the
+// Staging layout of one mesh: the hull edges (4 int32 each, first so they
+// stay 16-byte aligned), tri_uv (6 int32) and abc (3 fp32) per triangle,
+// T + 1 work item offsets, the triangle of every raster work item, then the
 // small triangles.
-size_t tri_stage_bytes(int T, int items, int n_small) {
-    return (size_t)T * 40 + 4 + (size_t)items * 4 + (size_t)n_small * 4;
+size_t tri_stage_bytes(int T, int items, int n_small, int n_hull) {
+    return (size_t)n_hull * 16 + (size_t)T * 40 + 4 + (size_t)items * 4 + (size_t)n_small * 4;
 }
 
 // Support set -> triangles, planes and raster inputs in the request's pinned
@@ -343,7 +344,9 @@ int mesh_step(Request& r) {
     }
     const int cap = 2 * n + 8;
     std::vector<int32_t> tri((size_t)3 * cap);
-    int T = n >= 3 ? delaunay(P.data(), n, tri.data(), cap) : 0;
+    std::vector<int32_t> hull_v((size_t)4 * n + 4);
+    int n_hull = 0;
+    int T = n >= 3 ? delaunay(P.data(), n, tri.data(), cap, hull_v.data(), &n_hull) : 0;
     if (T < 0) return STEREO_E_INTERNAL;
     std::vector<int32_t> tuv_v((size_t)6 * T), rows_v((size_t)T + 1), small_v((size_t)T + 1);
     for (int t = 0; t < T; t++)
@@ -353,8 +356,16 @@ int mesh_step(Request& r) {
         }
     int n_small = 0;
     const int items = raster_lists(tuv_v.data(), T, r.W, r.H, rows_v.data(), small_v.data(), &n_small);
-    if (!r.st_tri.ensure(tri_stage_bytes(T, items, n_small))) return STEREO_E_NOMEM;
-    int32_t* tuv = r.st_tri.as<int32_t>();
+    if (!r.st_tri.ensure(tri_stage_bytes(T, items, n_small, n_hull))) return STEREO_E_NOMEM;
+    int32_t* hull = r.st_tri.as<int32_t>();
+    for (int j = 0; j < n_hull; j++) {
+        const int a = hull_v[2 * j], b = hull_v[2 * j + 1];
+        hull[4 * j] = P[2 * a];
+        hull[4 * j + 1] = P[2 * a + 1];
+        hull[4 * j + 2] = P[2 * b];
+        hull[4 * j + 3] = P[2 * b + 1];
+    }
+    int32_t* tuv = hull + (size_t)4 * n_hull;
     float* abc = (float*)(tuv + (size_t)6 * T);
     int32_t* rows = (int32_t*)(abc + (size_t)3 * T);
     int32_t* item_tri = rows + T + 1;
@@ -366,6 +377,7 @@ int mesh_step(Request& r) {
     r.T = T;
     r.raster_items = items;
     r.n_small = n_small;
+    r.n_hull = n_hull;
     r.n_support.push_back(n);
     r.n_tri.push_back(T);
     for (const auto& s : r.S) {
@@ -600,7 +612,7 @@ cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, 
                          double seed_px, double cells_bytes, double raster_bytes, double validate_bytes) {
     for (Request* r : iter.reqs)
         if (r->T > 0)
-            CK(cudaMemcpyAsync((void*)r->dev.tri_uv, r->st_tri.p, tri_stage_bytes(r->T, r->raster_items, r->n_small),
+            CK(cudaMemcpyAsync((void*)r->dev.hull, r->st_tri.p, tri_stage_bytes(r->T, r->raster_items, r->n_small, r->n_hull),
                                cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->desc_dev, c->desc_host.p, desc_bytes, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(c->err_dev, 0, sizeof(int), s));
@@ -616,7 +628,6 @@ cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, 
     if (ni) {
         PairBatch fb = batch_of(iter, WK_FILL);
         if (fb.total > 0) CKQ(Lr.run(STEREO_K_FILL, ni, cells_bytes, [&] { return launch_fill_cells(fb, s); }));
-        CKQ(Lr.run(STEREO_K_RASTER_CLEAR, ni, raster_bytes, [&] { return launch_raster_clear(batch_of(iter, WK_CLEAR), s); }));
         CKQ(Lr.run(STEREO_K_RASTER, ni, raster_bytes, [&] { return launch_raster(batch_of(iter, WK_RASTER), s); }));
         CKQ(Lr.run(STEREO_K_VALIDATE, ni, validate_bytes, [&] {
             return c->bulk_validate ? launch_validate_bulk(batch_of(iter, WK_VALIDATE), prm, s)
@@ -649,7 +660,7 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         if (!r->st_kp.ensure((size_t)kFastBins * c->K * 12)) return cudaErrorMemoryAllocation;
     }
     for (Request* r : iter.reqs) {
-        const size_t tri_bytes = align_up(tri_stage_bytes(r->T, r->raster_items, r->n_small) + 64, 256);
+        const size_t tri_bytes = align_up(tri_stage_bytes(r->T, r->raster_items, r->n_small, r->n_hull) + 64, 256);
         if (tri_bytes > r->tri_block_bytes) {
             std::lock_guard<std::mutex> g(c->mu);
             c->arena.release(r->tri_block);
@@ -658,6 +669,9 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         }
         if (!r->tri_block) return cudaErrorMemoryAllocation;
         char* tb = (char*)r->tri_block;
+        r->dev.hull = (const int32_t*)tb;
+        r->dev.n_hull = r->n_hull;
+        tb += (size_t)r->n_hull * 16;
         r->dev.tri_uv = (const int32_t*)tb;
         r->dev.abc = (const float*)(tb + (size_t)r->T * 24);
         r->dev.tri_rows = (int32_t*)(tb + (size_t)r->T * 36);
@@ -680,7 +694,7 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
             r->dev.x_d = (int32_t*)(r->cells_dev + 3 * nc);
         }
         const double px = (double)r->W * r->H;
-        raster_bytes += px * (r->dev.planeidx ? 8.0 : 4.0);
+        raster_bytes += px * (r->dev.planeidx ? 8.0 : 4.0) + (double)r->T * 36.0;  // each pixel written once; tri_uv + abc read
         validate_bytes += px * (r->dev.first_pass ? 18.125 : 19.125);
         if (r->resample_now) {
             cells_bytes += 8.0 * r->dev.Wc * r->dev.Hc;
@@ -1167,6 +1181,7 @@ int stereo_raster(const int32_t* tri_uv, const float* abc, int T, int w, int h, 
     p.abc = abc;
     p.tri_rows = (int32_t*)scratch;
     p.small_tri = (int32_t*)scratch + T + 1;
+    p.n_hull = -1;  // no hull: the frame is cleared first
     p.planeidx = planeidx;
     p.Dit = D_it;
     cudaStream_t s = (cudaStream_t)stream;

@@ -12,7 +12,8 @@ constexpr int kFastBins = 120;          // 12 x 10 spatial bins (Sec. III-A)
 constexpr int kFastBinsX = 12;
 constexpr int kFastBinsY = 10;
 constexpr int kMaxK = 32;               // keypoints per bin, upper bound
-constexpr int kRasterRows = 8;          // triangle rows per raster work item (large triangles)
+constexpr int kRasterRows = 8;          // rows of a raster work item of a large triangle
+constexpr int kRasterCols = 128;        // columns of a raster work item of a large triangle
 constexpr int kSmallArea = 256;         // bounding-box pixels of a thread-rasterised triangle
 constexpr uint32_t kNoKey = 0xFFFFFFFFu;
 constexpr uint32_t kIdxMask = (1u << 27) - 1;
@@ -30,9 +31,11 @@ struct PairDev {
     int32_t* kp_d;            // 120*K matches
     const int32_t* tri_uv;    // T * 6
     const float* abc;         // T * 3
-    int32_t* tri_rows;        // T + 1: exclusive prefix of 8-row chunks per large triangle
+    int32_t* tri_rows;        // T + 1: exclusive prefix of work items (8x128 blocks) per large triangle
     const int32_t* item_tri;  // raster_items: triangle of each chunk
-    int32_t* small_tri;       // n_small triangles rasterised by one thread each
+    int32_t* small_tri;       // n_small small triangles (32 per warp)
+    const int32_t* hull;      // n_hull directed hull edges (ax, ay, bx, by), interior on the positive side
+    int n_hull;               // -1: no hull; the caller clears the frame before the raster
     int n_small;
     int32_t* planeidx;        // W*H plane-index map, or null (not needed this pass)
     float* Dit;               // W*H interpolated prior D_it (NaN outside the mesh)
@@ -104,10 +107,14 @@ int sm_count();
 
 // Host mesh step (mesh.cpp).
 int delaunay(const int32_t* uv, int n, int32_t* tri, int cap);
+// Also returns the directed hull edges (org, dest vertex index pairs, the
+// triangles on the left as in a positively oriented triangle) in hull[2 * n]
+// and their count in *n_hull (0 when there is no triangle).
+int delaunay(const int32_t* uv, int n, int32_t* tri, int cap, int32_t* hull, int* n_hull);
 void planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float* abc);
 // Raster work lists of a mesh: small[] the triangles whose clipped bounding
 // box has at most kSmallArea pixels (returns their count in *n_small); rows[T + 1]
-// the exclusive prefix of 8-row chunks of the others (returns the total).
+// the exclusive prefix of the 8x128 work items of the others (returns the total).
 int raster_lists(const int32_t* tri_uv, int T, int W, int H, int32_t* rows, int32_t* small, int* n_small);
 // Triangle of every chunk (items = rows[T] entries).
 void raster_item_tri(const int32_t* rows, int T, int32_t* item_tri);

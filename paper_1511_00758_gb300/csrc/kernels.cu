@@ -33,7 +33,7 @@ int work_items(WorkKind k, const PairDev& p) {
         case WK_MATCH_KP: return cdiv((long long)kFastBins * p.K, 8);
         case WK_CLEAR: return cdiv((long long)p.W * p.H, 4096);
         case WK_FILL: return p.cg_key ? cdiv((long long)p.Wc * p.Hc, 4096) : 0;
-        case WK_RASTER: return cdiv(p.n_small, 256) + cdiv(p.raster_items, 8);
+        case WK_RASTER: return cdiv(p.n_small, 256) + cdiv(p.raster_items, 8) + (p.n_hull >= 0 ? cdiv(p.H, 8) : 0);
         case WK_RESAMPLE: return cdiv((long long)p.Wc * p.Hc, 8);
         default: return 0;
     }
@@ -348,14 +348,27 @@ __global__ void __launch_bounds__(256) k_match_list(const uint32_t* cL, const ui
 // on a top or left edge.  The rule partitions the hull: every pixel is
 // written by exactly one triangle, in any order; pixels outside keep the
 // cleared values (-1, NaN).  D_it = fma(a, u, fma(b, v, c)) in fp32.
-// Small triangles (bounding box of at most kSmallArea pixels): one thread
-// walks the box with incremental edge values.  Larger ones: one warp per
-// chunk of kRasterRows rows, one lane per row bounds it by exact int32 floor/ceil
-// division, then lanes stride the columns.
+// Small triangles (bounding box of at most kSmallArea pixels): a warp takes
+// 32 of them and covers each box in turn with its 32 lanes.  Larger ones: one
+// warp per work item of kRasterRows rows by kRasterCols columns of the box;
+// one lane per row bounds the row by exact int32 floor/ceil division, then
+// the lanes stride the columns of the item.
 struct TriEdges {
     int x[3], y[3];
     int A[3], B[3], C[3], bias[3];
 };
+
+// Edge function of the directed edge a -> b (interior on its positive side)
+// and the fill-rule bias: a pixel on the edge (E == 0) is kept only on a top
+// or left edge.  Triangles and the hull use this one definition, so a hull
+// edge decides every pixel exactly as the triangle behind it does.
+__device__ __forceinline__ void edge_fn(int ax, int ay, int bx, int by, int& A, int& B, int& C, int& bias) {
+    const int dx = bx - ax, dy = by - ay;
+    A = -dy;
+    B = dx;
+    C = dy * ax - dx * ay;
+    bias = ((dy == 0 && dx > 0) || dy < 0) ? 0 : 1;
+}
 
 __device__ __forceinline__ void tri_setup(const int32_t* __restrict__ tri_uv, int t, TriEdges& e) {
     const int32_t* q = tri_uv + 6 * (size_t)t;
@@ -370,12 +383,7 @@ __device__ __forceinline__ void tri_setup(const int32_t* __restrict__ tri_uv, in
     for (int k = 0; k < 3; k++) {
         e.x[k] = x[k];
         e.y[k] = y[k];
-        const int ax = x[k], ay = y[k], bx = x[(k + 1) % 3], by = y[(k + 1) % 3];
-        const int dx = bx - ax, dy = by - ay;
-        e.A[k] = -dy;
-        e.B[k] = dx;
-        e.C[k] = dy * ax - dx * ay;
-        e.bias[k] = ((dy == 0 && dx > 0) || dy < 0) ? 0 : 1;  // top or left edges keep E == 0
+        edge_fn(x[k], y[k], x[(k + 1) % 3], y[(k + 1) % 3], e.A[k], e.B[k], e.C[k], e.bias[k]);
     }
 }
 
@@ -385,49 +393,98 @@ __device__ __forceinline__ bool tri_is_small(const int32_t* __restrict__ q, int 
     return x1 < x0 || y1 < y0 || (x1 - x0 + 1) * (y1 - y0 + 1) <= kSmallArea;
 }
 
+// Work items of a large triangle: 8-row by 128-column blocks of its clipped box.
+__device__ __forceinline__ int tri_col_chunks(const int32_t* __restrict__ q, int W) {
+    const int x0 = max(0, min(q[0], min(q[2], q[4]))), x1 = min(W - 1, max(q[0], max(q[2], q[4])));
+    return (x1 - x0) / kRasterCols + 1;
+}
 __device__ __forceinline__ int tri_chunks(const int32_t* __restrict__ q, int W, int H) {
     if (tri_is_small(q, W, H)) return 0;
     const int y0 = max(0, min(q[1], min(q[3], q[5])));
     const int y1 = min(H - 1, max(q[1], max(q[3], q[5])));
-    return (y1 - y0) / kRasterRows + 1;
+    return ((y1 - y0) / kRasterRows + 1) * tri_col_chunks(q, W);
 }
 
 
-__device__ __forceinline__ void raster_small(const int32_t* __restrict__ tri_uv, const float* __restrict__ abc,
-                                             int t, int W, int H, int32_t* __restrict__ pidx,
-                                             float* __restrict__ dit) {
-    TriEdges e;
-    tri_setup(tri_uv, t, e);
-    float a = 0.0f, b = 0.0f, c = 0.0f;
-    if (dit) {  // planes are only read when D_it is written (abc may be null otherwise)
-        a = __ldg(abc + 3 * t);
-        b = __ldg(abc + 3 * t + 1);
-        c = __ldg(abc + 3 * t + 2);
+// Small triangles, 32 to a warp: lane i sets triangle i up in shared memory;
+// then the warp splits into groups of G lanes (G = the widest box of the 32,
+// rounded up to a power of two, at most 32) and each group walks one box
+// down its columns, G adjacent pixels per row, so the stores of a row are
+// contiguous.  The bias is folded into C: a pixel is inside when the three
+// edge values are all >= 0.
+struct SmallTri {
+    int A[3], B[3], C[3];
+    int x0, y0, bw, bh;
+    float a, b, c;
+    int t;
+};
+
+__device__ __forceinline__ void raster_small_warp(const int32_t* __restrict__ tri_uv, const float* __restrict__ abc,
+                                                  const int32_t* __restrict__ list, int n, int W, int H,
+                                                  int32_t* __restrict__ pidx, float* __restrict__ dit,
+                                                  SmallTri* __restrict__ s) {
+    const int lane = threadIdx.x & 31;
+    int bw = 0;
+    if (lane < n) {
+        const int t = __ldg(list + lane);
+        TriEdges e;
+        tri_setup(tri_uv, t, e);
+        SmallTri q;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            q.A[k] = e.A[k];
+            q.B[k] = e.B[k];
+            q.C[k] = e.C[k] - e.bias[k];
+        }
+        const int x0 = max(0, min(e.x[0], min(e.x[1], e.x[2]))), x1 = min(W - 1, max(e.x[0], max(e.x[1], e.x[2])));
+        const int y0 = max(0, min(e.y[0], min(e.y[1], e.y[2]))), y1 = min(H - 1, max(e.y[0], max(e.y[1], e.y[2])));
+        q.x0 = x0;
+        q.y0 = y0;
+        q.bw = max(0, x1 - x0 + 1);
+        q.bh = max(0, y1 - y0 + 1);
+        q.a = q.b = q.c = 0.0f;
+        if (dit) {  // planes are only read when D_it is written (abc may be null otherwise)
+            q.a = __ldg(abc + 3 * t);
+            q.b = __ldg(abc + 3 * t + 1);
+            q.c = __ldg(abc + 3 * t + 2);
+        }
+        q.t = t;
+        s[lane] = q;
+        bw = q.bw;
     }
-    const int x0 = max(0, min(e.x[0], min(e.x[1], e.x[2]))), x1 = min(W - 1, max(e.x[0], max(e.x[1], e.x[2])));
-    const int y0 = max(0, min(e.y[0], min(e.y[1], e.y[2]))), y1 = min(H - 1, max(e.y[0], max(e.y[1], e.y[2])));
-    for (int v = y0; v <= y1; v++) {
-        int e0 = e.A[0] * x0 + e.B[0] * v + e.C[0];
-        int e1 = e.A[1] * x0 + e.B[1] * v + e.C[1];
-        int e2 = e.A[2] * x0 + e.B[2] * v + e.C[2];
-        const float rowterm = __fmaf_rn(b, (float)v, c);  // D_it = fma(a, u, fma(b, v, c))
-        int32_t* prow = pidx ? pidx + (size_t)v * W : nullptr;
-        float* drow = dit ? dit + (size_t)v * W : nullptr;
-        bool seen = false;
-        for (int u = x0; u <= x1; u++) {
-            const bool in = e0 >= e.bias[0] && e1 >= e.bias[1] && e2 >= e.bias[2];
-            if (in) {
-                if (prow) prow[u] = t;
-                if (drow) drow[u] = __fmaf_rn(a, (float)u, rowterm);
-            } else if (seen) {
-                break;  // a row of a convex triangle is one run
+#pragma unroll
+    for (int o = 16; o; o >>= 1) bw = max(bw, __shfl_xor_sync(0xffffffffu, bw, o));
+    __syncwarp();
+    const int lg = bw > 16 ? 5 : bw > 8 ? 4 : bw > 4 ? 3 : bw > 2 ? 2 : bw > 1 ? 1 : 0;
+    const int G = 1 << lg, ng = 32 >> lg, lx = lane & (G - 1);
+    for (int i = lane >> lg; i < n; i += ng) {
+        const int A0 = s[i].A[0], A1 = s[i].A[1], A2 = s[i].A[2];
+        const int B0 = s[i].B[0], B1 = s[i].B[1], B2 = s[i].B[2];
+        const int C0 = s[i].C[0], C1 = s[i].C[1], C2 = s[i].C[2];
+        const int x0 = s[i].x0, y0 = s[i].y0, tw = s[i].bw, th = s[i].bh, t = s[i].t;
+        const float pa = s[i].a, pb = s[i].b, pc = s[i].c;
+        for (int cx = lx; cx < tw; cx += G) {
+            const int u = x0 + cx;
+            int e0 = A0 * u + B0 * y0 + C0;
+            int e1 = A1 * u + B1 * y0 + C1;
+            int e2 = A2 * u + B2 * y0 + C2;
+            const float uf = (float)u;
+            float vf = (float)y0;
+            size_t p = (size_t)y0 * W + u;
+            for (int r = 0; r < th; r++) {
+                if ((e0 | e1 | e2) >= 0) {
+                    if (pidx) pidx[p] = t;
+                    if (dit) dit[p] = __fmaf_rn(pa, uf, __fmaf_rn(pb, vf, pc));  // D_it = fma(a, u, fma(b, v, c))
+                }
+                e0 += B0;
+                e1 += B1;
+                e2 += B2;
+                vf += 1.0f;
+                p += W;
             }
-            seen |= in;
-            e0 += e.A[0];
-            e1 += e.A[1];
-            e2 += e.A[2];
         }
     }
+    __syncwarp();
 }
 
 __device__ __forceinline__ int floordiv32(int a, int b) {  // b > 0
@@ -435,9 +492,12 @@ __device__ __forceinline__ int floordiv32(int a, int b) {  // b > 0
 }
 
 __device__ __forceinline__ void raster_chunk_tc(const int32_t* __restrict__ tri_uv, const float* __restrict__ abc,
-                                                int t, int c, int W, int H, int32_t* __restrict__ pidx,
+                                                int t, int item, int W, int H, int32_t* __restrict__ pidx,
                                                 float* __restrict__ dit) {
     const int lane = threadIdx.x & 31;
+    // item -> (row block, column block) of the triangle's clipped box
+    const int ncol = tri_col_chunks(tri_uv + 6 * (size_t)t, W);
+    const int c = item / ncol, cc = item - c * ncol;
     TriEdges e;
     tri_setup(tri_uv, t, e);
     float pa = 0.0f, pb = 0.0f, pc = 0.0f;
@@ -450,7 +510,8 @@ __device__ __forceinline__ void raster_chunk_tc(const int32_t* __restrict__ tri_
     const int ymax = min(H - 1, max(e.y[0], max(e.y[1], e.y[2])));
     const int v0 = ymin + c * kRasterRows;
     const int vr = v0 + (lane & (kRasterRows - 1));
-    int lo = 0, hi = W - 1;
+    const int bx0 = max(0, min(e.x[0], min(e.x[1], e.x[2]))) + cc * kRasterCols;
+    int lo = bx0, hi = min(W - 1, bx0 + kRasterCols - 1);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         // A u + B v + C >= bias  <=>  A u >= R
@@ -498,23 +559,72 @@ __global__ void __launch_bounds__(256) k_raster_clear(PairBatch b) {
 #undef BODY
 }
 
-// Work of one pair: ceil(n_small / 256) thread blocks, then ceil(items / 8)
-// warp blocks (host-built small list, chunk prefix and chunk -> triangle table).
-__device__ __forceinline__ void raster_body(const PairDev& P, int local) {
+// Pixels outside the convex hull of the support points, one warp per row.
+// The hull is the union of the triangles, and with the fill rule a pixel is
+// inside the hull exactly when it passes every hull edge, so on row v the
+// covered pixels are the interval [lo, hi] cut by the hull edges; the pixels
+// outside it get the cleared values (-1, NaN) and the triangles write the
+// rest: every pixel is written once.
+__device__ __forceinline__ void hull_row_clear(const int32_t* __restrict__ hull, int nh, int v, int W,
+                                               int32_t* __restrict__ pidx, float* __restrict__ dit) {
+    const int lane = threadIdx.x & 31;
+    int lo = nh > 0 ? 0 : W, hi = W - 1;
+    for (int j = lane; j < nh; j += 32) {
+        const int4 h = __ldg(reinterpret_cast<const int4*>(hull) + j);
+        int A, B, C, bias;
+        edge_fn(h.x, h.y, h.z, h.w, A, B, C, bias);
+        const int R = bias - B * v - C;  // A u + B v + C >= bias  <=>  A u >= R
+        if (A > 0) lo = max(lo, -floordiv32(-R, A));
+        else if (A < 0) hi = min(hi, floordiv32(-R, -A));
+        else if (R > 0) lo = W;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        lo = max(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = min(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    lo = min(lo, W);
+    const float qnan = __int_as_float(0x7fc00000);
+    int32_t* prow = pidx ? pidx + (size_t)v * W : nullptr;
+    float* drow = dit ? dit + (size_t)v * W : nullptr;
+    for (int u = lane; u < lo; u += 32) {
+        if (prow) prow[u] = -1;
+        if (drow) drow[u] = qnan;
+    }
+    for (int u = max(hi + 1, lo) + lane; u < W; u += 32) {
+        if (prow) prow[u] = -1;
+        if (drow) drow[u] = qnan;
+    }
+}
+
+// Work of one pair: ceil(n_small / 256) blocks of small triangles (32 per
+// warp), ceil(items / 8) blocks of large-triangle work items (one per warp),
+// then, when the hull is given, ceil(H / 8) blocks of hull row clears.
+__device__ __forceinline__ void raster_body(const PairDev& P, int local, SmallTri* s) {
     const int nsb = (P.n_small + 255) / 256;
+    const int ncb = (P.raster_items + 7) / 8;
+    const int w = threadIdx.x >> 5;
     if (local < nsb) {
-        const int i = local * 256 + threadIdx.x;
-        if (i < P.n_small) raster_small(P.tri_uv, P.abc, __ldg(P.small_tri + i), P.W, P.H, P.planeidx, P.Dit);
+        const int i0 = local * 256 + w * 32;
+        if (i0 < P.n_small)
+            raster_small_warp(P.tri_uv, P.abc, P.small_tri + i0, min(32, P.n_small - i0), P.W, P.H, P.planeidx,
+                              P.Dit, s + w * 32);
         return;
     }
-    const int item = (local - nsb) * 8 + (threadIdx.x >> 5);
-    if (item >= P.raster_items) return;
-    const int t = __ldg(P.item_tri + item);
-    raster_chunk_tc(P.tri_uv, P.abc, t, item - __ldg(P.tri_rows + t), P.W, P.H, P.planeidx, P.Dit);
+    if (local < nsb + ncb) {
+        const int item = (local - nsb) * 8 + w;
+        if (item >= P.raster_items) return;
+        const int t = __ldg(P.item_tri + item);
+        raster_chunk_tc(P.tri_uv, P.abc, t, item - __ldg(P.tri_rows + t), P.W, P.H, P.planeidx, P.Dit);
+        return;
+    }
+    const int v = (local - nsb - ncb) * 8 + w;
+    if (v < P.H) hull_row_clear(P.hull, P.n_hull, v, P.W, P.planeidx, P.Dit);
 }
 
 __global__ void __launch_bounds__(256) k_raster(PairBatch b) {
-#define BODY(P, l) raster_body(P, l)
+    __shared__ SmallTri s[256];
+#define BODY(P, l) raster_body(P, l, s)
     FOR_EACH_ITEM(b, BODY)
 #undef BODY
 }
@@ -618,9 +728,11 @@ __global__ void __launch_bounds__(256) k_raster_dev(const int32_t* __restrict__ 
                                                     const int32_t* __restrict__ rows,
                                                     const int32_t* __restrict__ small, int T, int W, int H,
                                                     int32_t* __restrict__ pidx, float* __restrict__ dit) {
+    __shared__ SmallTri s[256];
     const int nsmall = __ldg(small + T);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsmall; i += gridDim.x * blockDim.x)
-        raster_small(tri_uv, abc, __ldg(small + i), W, H, pidx, dit);
+    const int w = threadIdx.x >> 5;
+    for (int i0 = (blockIdx.x * 8 + w) * 32; i0 < nsmall; i0 += gridDim.x * 8 * 32)
+        raster_small_warp(tri_uv, abc, small + i0, min(32, nsmall - i0), W, H, pidx, dit, s + w * 32);
     const int total = __ldg(rows + T);
     const int nw = gridDim.x * 8;
     for (int item = blockIdx.x * 8 + (threadIdx.x >> 5); item < total; item += nw) {

@@ -225,7 +225,10 @@ struct Mesh {
 
 }  // namespace
 
-int delaunay(const int32_t* uv, int n, int32_t* tri, int cap) {
+int delaunay(const int32_t* uv, int n, int32_t* tri, int cap) { return delaunay(uv, n, tri, cap, nullptr, nullptr); }
+
+int delaunay(const int32_t* uv, int n, int32_t* tri, int cap, int32_t* hull, int* n_hull) {
+    if (n_hull) *n_hull = 0;
     if (n < 3) return 0;
     Mesh m;
     m.P = uv;
@@ -244,14 +247,23 @@ int delaunay(const int32_t* uv, int n, int32_t* tri, int cap) {
     jk.reserve((size_t)4 * n);
     owner.reserve((size_t)2 * n);
     const int ne = m.ne;
+    int nh = 0;
     for (int e = 0; e < ne; e += 2) {
         if (m.dead[e >> 2]) continue;
         const int a = m.org[e], b = m.dest(e);
-        if (!(a < b)) continue;
         const int e2 = m.lnext(e);
         const int c = m.dest(e2);
-        if (!(a < c) || m.lnext(m.lnext(e2)) != e) continue;
-        if (!m.ccw(a, b, c)) continue;
+        if (m.lnext(m.lnext(e2)) != e || !m.ccw(a, b, c)) {
+            // the left face is the outside: b -> a is a hull edge with its
+            // triangle on the left
+            if (hull && nh < 2 * n) {
+                hull[2 * nh] = b;
+                hull[2 * nh + 1] = a;
+            }
+            nh++;
+            continue;
+        }
+        if (!(a < b) || !(a < c)) continue;
         owner.push_back(a);
         jk.push_back(std::min(b, c));
         jk.push_back(std::max(b, c));
@@ -259,6 +271,7 @@ int delaunay(const int32_t* uv, int n, int32_t* tri, int cap) {
     }
     const int T = (int)owner.size();
     if (T > cap) return -9;  // STEREO_E_CAP
+    if (n_hull) *n_hull = (T > 0 && nh <= 2 * n) ? nh : 0;
     for (int i = 0; i < n; i++) first[i + 1] += first[i];
     std::vector<int> pos(first.begin(), first.end() - 1);
     std::vector<uint64_t> key(T);
@@ -298,10 +311,13 @@ void planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float*
 }
 
 int raster_lists(const int32_t* q, int T, int W, int H, int32_t* rows, int32_t* small, int* n_small) {
-    // small triangles are listed by increasing bounding-box area (a counting
-    // sort), so the 32 threads of a warp walk boxes of similar size
+    // small triangles are listed by box width class, then by box area (a
+    // counting sort), so the 32 triangles of a warp have boxes of similar
+    // width and size
     std::vector<int> area_of(T, -1);
-    int cnt[kSmallArea + 2] = {0};
+    constexpr int kClasses = 7;  // box width 1, 2, <=4, <=8, <=16, <=32, wider
+    constexpr int kKeys = kClasses * (kSmallArea + 1);
+    std::vector<int> cnt(kKeys + 1, 0);
     int s = 0;
     for (int t = 0; t < T; t++, q += 6) {
         rows[t] = s;
@@ -311,17 +327,20 @@ int raster_lists(const int32_t* q, int T, int W, int H, int32_t* rows, int32_t* 
         const int y1 = std::min(H - 1, std::max(q[1], std::max(q[3], q[5])));
         const int area = (x1 < x0 || y1 < y0) ? 0 : (x1 - x0 + 1) * (y1 - y0 + 1);
         if (area <= kSmallArea) {
-            area_of[t] = area;
-            cnt[area + 1]++;
+            const int bw = x1 - x0 + 1;
+            int cls = 0;
+            while (cls < kClasses - 1 && (1 << cls) < bw) cls++;
+            area_of[t] = cls * (kSmallArea + 1) + area;
+            cnt[area_of[t] + 1]++;
         } else {
-            s += (y1 - y0) / kRasterRows + 1;
+            s += ((y1 - y0) / kRasterRows + 1) * ((x1 - x0) / kRasterCols + 1);
         }
     }
     rows[T] = s;
-    for (int a = 0; a <= kSmallArea; a++) cnt[a + 1] += cnt[a];
+    for (int a = 0; a < kKeys; a++) cnt[a + 1] += cnt[a];
     for (int t = 0; t < T; t++)
         if (area_of[t] >= 0) small[cnt[area_of[t]]++] = t;
-    *n_small = cnt[kSmallArea];
+    *n_small = cnt[kKeys - 1];
     return s;
 }
 

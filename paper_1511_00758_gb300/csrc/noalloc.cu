@@ -72,6 +72,7 @@ extern "C" int stereo_raster_noalloc(const int32_t* tri_uv, const float* abc, in
     p.abc = abc;
     p.tri_rows = lists;
     p.small_tri = lists + T + 1;
+    p.n_hull = -1;  // no hull: the frame is cleared first
     p.planeidx = planeidx;
     p.Dit = D_it;
     stereo::PairBatch b{};
