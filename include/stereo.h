@@ -247,7 +247,8 @@ int stereo_raster_noalloc(const int32_t* tri_uv, const float* abc, int T, int w,
  * 0xFFFFFFFF when empty; both arrays, ceil(H/sz)*ceil(W/sz) entries, must hold
  * 0xFFFFFFFF on entry (atomic minimum), or both be NULL to skip the cells.
  * first_pass = 1 treats D_f, C_f as their initial values (0, t_hi) without
- * reading them, and writes every pixel.  mask may be NULL. */
+ * reading them, and writes every pixel.  mask (W*H bytes) is required;
+ * NULL returns STEREO_E_INVAL. */
 int stereo_validate(const uint32_t* cL, const uint32_t* cR, const uint32_t* omega, const float* D_it,
                     int w, int h, int sz, int t_lo, int t_hi, int first_pass, float* D_f,
                     uint8_t* C_f, uint8_t* mask, uint32_t* cg_key, uint32_t* cb_key, void* stream);

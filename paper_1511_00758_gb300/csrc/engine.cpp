@@ -306,6 +306,7 @@ struct stereo_ctx {
     int* err_dev = nullptr;                  // set by a device-side wait that gave up
     Pinned err_host;
     bool bulk_validate = false;              // the bulk-copy validate kernel (else the plain one)
+    bool mixed_validate = true;              // plain validate: one launch for every cell class (else one per class)
     std::vector<cudaEvent_t> ev_pool;     // timing events of profiled launches
     std::vector<cudaEvent_t> ev_retired;  // events of the last round (still in its graph)
     stereo_stats stats{};
@@ -490,6 +491,7 @@ void admit(stereo_ctx* c) {
 struct Group {
     std::vector<Request*> reqs;
     const PairDev* pd = nullptr;
+    const PairDev* hpd = nullptr;  // host copies of the descriptors (as uploaded)
     const int* off[WK_COUNT] = {};
     int total[WK_COUNT] = {};
 };
@@ -510,6 +512,7 @@ void fill_group(Group& g, char* host, char* dev) {
         }
     }
     g.pd = (const PairDev*)dev;
+    g.hpd = hp;
     size_t off = align_up(sizeof(PairDev) * n, 256);
     for (int k = 0; k < WK_COUNT; k++) {
         int* ho = (int*)(host + off);
@@ -546,6 +549,7 @@ struct Launcher {
         cudaEvent_t a, b;
     };
     std::vector<Timed> timed;
+    int launched = 1;  // kernels issued by the current run() body (a body may set it)
 
     cudaEvent_t event() {  // the pool is filled before each capture (at most 24 per round)
         cudaEvent_t e = c->ev_pool.back();
@@ -575,8 +579,9 @@ struct Launcher {
             }
             timed.push_back({kind, a, b});
         }
-        delta.kernel_launches++;
-        delta.kind_launches[kind]++;
+        delta.kernel_launches += launched;
+        delta.kind_launches[kind] += launched;
+        launched = 1;
         delta.kind_bytes[kind] += bytes;
         delta.batched_pairs += npairs;
         return cudaSuccess;
@@ -630,8 +635,20 @@ cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, 
         if (fb.total > 0) CKQ(Lr.run(STEREO_K_FILL, ni, cells_bytes, [&] { return launch_fill_cells(fb, s); }));
         CKQ(Lr.run(STEREO_K_RASTER, ni, raster_bytes, [&] { return launch_raster(batch_of(iter, WK_RASTER), s); }));
         CKQ(Lr.run(STEREO_K_VALIDATE, ni, validate_bytes, [&] {
-            return c->bulk_validate ? launch_validate_bulk(batch_of(iter, WK_VALIDATE), prm, s)
-                                    : launch_validate(batch_of(iter, WK_VALIDATE), prm, s);
+            if (c->bulk_validate) return launch_validate_bulk(batch_of(iter, WK_VALIDATE_BULK), prm, s);
+            int n = 0, nk = 0;
+            if (c->mixed_validate) {
+                const cudaError_t ev = launch_validate(iter.hpd, ni, WK_VALIDATE_MIXED, prm, s, &n);
+                if (ev != cudaSuccess) return ev;
+            } else {  // one launch per cell-side class present in the group
+                for (WorkKind k : kValidateKinds) {
+                    const cudaError_t ev = launch_validate(iter.hpd, ni, k, prm, s, &nk);
+                    if (ev != cudaSuccess) return ev;
+                    n += nk;
+                }
+            }
+            Lr.launched = n;
+            return cudaSuccess;
         }));
         PairBatch rb = batch_of(iter, WK_RESAMPLE);
         if (rb.total > 0) CKQ(Lr.run(STEREO_K_RESAMPLE, ni, 0.0, [&] { return launch_resample(rb, prm, s); }));
@@ -912,7 +929,10 @@ int stereo_create(const stereo_config* cfg, stereo_ctx** out) {
         return STEREO_E_NOMEM;
     }
     *c->err_host.as<int>() = 0;
-    if (const char* v = std::getenv("STEREO_VALIDATE")) c->bulk_validate = std::strcmp(v, "bulk") == 0;
+    if (const char* v = std::getenv("STEREO_VALIDATE")) {
+        c->bulk_validate = std::strcmp(v, "bulk") == 0;
+        c->mixed_validate = std::strcmp(v, "classes") != 0;
+    }
     if (prepare_kernels() != cudaSuccess) c->bulk_validate = false;
     c->pool.start(std::max(1, cfg->host_threads));
     c->sched = std::thread(scheduler, c);
@@ -1193,7 +1213,7 @@ int stereo_raster(const int32_t* tri_uv, const float* abc, int T, int w, int h, 
 int stereo_validate(const uint32_t* cL, const uint32_t* cR, const uint32_t* omega, const float* D_it, int w, int h,
                     int sz, int t_lo, int t_hi, int first_pass, float* D_f, uint8_t* C_f, uint8_t* mask,
                     uint32_t* cg_key, uint32_t* cb_key, void* stream) {
-    if (!cL || !cR || !omega || !D_it || !D_f || !C_f || !valid_size(w, h) || sz < 1 ||
+    if (!cL || !cR || !omega || !D_it || !D_f || !C_f || !mask || !valid_size(w, h) || sz < 1 ||
         !(0 <= t_lo && t_lo <= t_hi && t_hi < 24) || ((cg_key == nullptr) != (cb_key == nullptr)))
         return STEREO_E_INVAL;
     PairDev p{};
@@ -1213,7 +1233,8 @@ int stereo_validate(const uint32_t* cL, const uint32_t* cR, const uint32_t* omeg
     p.cg_key = cg_key;
     p.cb_key = cb_key;
     Params prm{t_lo, t_hi, 0, 0, 1, 0};
-    return to_rc(launch_validate(single(p, WK_VALIDATE), prm, (cudaStream_t)stream));
+    const WorkKind k = validate_kind(p);
+    return to_rc(launch_validate(&p, 1, k, prm, (cudaStream_t)stream, nullptr));
 }
 
 int stereo_validate_bulk(const uint32_t* cL, const uint32_t* cR, const uint32_t* omega, const float* D_it, int w,
@@ -1248,7 +1269,7 @@ int stereo_validate_bulk(const uint32_t* cL, const uint32_t* cR, const uint32_t*
     p.cg_key = cg_key;
     p.cb_key = cb_key;
     Params prm{t_lo, t_hi, 0, 0, 1, 0, err_flag};
-    return to_rc(launch_validate_bulk(single(p, WK_VALIDATE), prm, (cudaStream_t)stream));
+    return to_rc(launch_validate_bulk(single(p, WK_VALIDATE_BULK), prm, (cudaStream_t)stream));
 }
 
 int stereo_resample_match(const uint32_t* cg_key, const uint32_t* cb_key, int ncells, const float* D_it,

@@ -73,7 +73,8 @@ struct Params {
 
 // Work items per pair for each kernel kind.
 enum WorkKind { WK_CENSUS = 0, WK_FAST_SCORE, WK_FAST_BINS, WK_MATCH_KP, WK_CLEAR,
-                WK_RASTER, WK_VALIDATE, WK_RESAMPLE, WK_FILL, WK_COUNT };
+                WK_RASTER, WK_VALIDATE, WK_VALIDATE_UNIT, WK_VALIDATE_C4, WK_VALIDATE_C2,
+                WK_VALIDATE_ANY, WK_VALIDATE_MIXED, WK_VALIDATE_BULK, WK_RESAMPLE, WK_FILL, WK_COUNT };
 int work_items(WorkKind k, const PairDev& p);
 // Sets sz and its division helpers.
 void set_cell_size(PairDev& p, int sz);
@@ -90,7 +91,19 @@ cudaError_t launch_raster(const PairBatch& b, cudaStream_t s);
 // 2 * ceil(T / 1024) entries of block offsets
 cudaError_t launch_raster_device_lists(const PairDev& p, cudaStream_t s);
 inline size_t raster_list_words(int T) { return 2 * ((size_t)T + 1) + 2 * (((size_t)T + 1023) / 1024); }
-cudaError_t launch_validate(const PairBatch& b, const Params& prm, cudaStream_t s);
+// Fused validate: one kernel variant per cell-side class; a pair has work
+// only under its own class, validate_kind(p): WK_VALIDATE (no cells, or
+// 8 | sz), WK_VALIDATE_UNIT (sz 1), WK_VALIDATE_C4 (sz 4), WK_VALIDATE_C2
+// (sz 2), WK_VALIDATE_ANY (other sides).  Launch every class with work, or
+// WK_VALIDATE_MIXED: one launch in which every pair takes its own class.
+constexpr WorkKind kValidateKinds[] = {WK_VALIDATE, WK_VALIDATE_UNIT, WK_VALIDATE_C4, WK_VALIDATE_C2,
+                                       WK_VALIDATE_ANY};
+WorkKind validate_kind(const PairDev& p);
+// Launches class k over pairs[0..n) (pairs without work under k are skipped),
+// kVBatch pairs per launch, their descriptors passed in the kernel
+// parameters; *launches (may be null) receives the launch count.
+cudaError_t launch_validate(const PairDev* pairs, int n, WorkKind k, const Params& prm, cudaStream_t s,
+                            int* launches);
 // Bulk-copy pipelined validate (same results).  Needs 16-byte aligned D_it,
 // cL, cR, C_f and Omega_I buffers; sets *prm.err if a bounded wait gave up.
 cudaError_t launch_validate_bulk(const PairBatch& b, const Params& prm, cudaStream_t s);

@@ -171,7 +171,10 @@ def _support_case(oracle_mod, p, n=400, seed=0):
 @pytest.mark.parametrize("bulk", [0, 1])
 @pytest.mark.parametrize("name,sz,first", [("vga_polygons", 16, 1), ("driving_1242x375", 8, 0),
                                            ("driving_1242x375", 1, 0), ("vga_polygons", 3, 0),
-                                           ("driving_1242x375", 64, 1)])
+                                           ("driving_1242x375", 64, 1), ("driving_1242x375", 4, 0),
+                                           ("vga_polygons", 2, 1), ("driving_1242x375", 6, 0),
+                                           ("vga_polygons", 12, 0), ("driving_1242x375", 5, 0),
+                                           ("vga_polygons", 40, 0), ("driving_1242x375", 7, 1)])
 def test_validate(oracle_mod, name, sz, first, bulk):
     p = scenes.config_pairs(name)[0]
     H, W = p.left.shape

@@ -89,6 +89,7 @@ def test_host_argument_errors(L):
     assert L.stereo_census(1, 1, 3, 64, 8, None, None, None, None) == -1
     assert L.stereo_epipolar_match(1, 1, 64, 64, 1, 4, 300, 4, 2, 1, None) == -1
     assert L.stereo_validate(1, 1, 1, 1, 1, 64, 64, 4, 9, 8, 1, 1, 1, None, 1, None, None) == -1
+    assert L.stereo_validate(1, 1, 1, 1, 64, 64, 8, 4, 8, 0, 1, 1, None, None, None, None) == -1  # mask required
     assert L.stereo_submit(None, 0, None, None, 64, 64, 64, 1, 16, ctypes.byref(ctypes.c_uint64())) == -1
     cfg = S.Config()
     L.stereo_default_config(ctypes.byref(cfg))
