@@ -230,40 +230,50 @@ int delaunay(const int32_t* uv, int n, int32_t* tri, int cap) { return delaunay(
 int delaunay(const int32_t* uv, int n, int32_t* tri, int cap, int32_t* hull, int* n_hull) {
     if (n_hull) *n_hull = 0;
     if (n < 3) return 0;
-    Mesh m;
+    // per-thread storage, reused across calls: make_edge initialises every
+    // entry an edge reads, so nothing needs clearing
+    thread_local Mesh m;
+    thread_local std::vector<int> s, first, owner, pos;
+    thread_local std::vector<int32_t> jk;
+    thread_local std::vector<uint64_t> key;
+    thread_local std::vector<uint8_t> outer;
     m.P = uv;
-    m.nxt.resize((size_t)16 * n);  // about 3n quad edges survive; make_edge grows on demand
-    m.org.resize((size_t)16 * n, -1);
-    m.dead.resize((size_t)4 * n, 0);
-    std::vector<int> s(n);
+    m.ne = 0;
+    if (m.nxt.size() < (size_t)16 * n) {  // about 3n quad edges survive; make_edge grows on demand
+        m.nxt.resize((size_t)16 * n);
+        m.org.resize((size_t)16 * n);
+        m.dead.resize((size_t)4 * n);
+    }
+    s.resize(n);
     for (int i = 0; i < n; i++) s[i] = i;
-    m.build(s.data(), n, 0);
+    const int cw = m.build(s.data(), n, 0).second;  // clockwise hull edge: the outer face on its left
+    const int ne = m.ne;
+    // the outer face, walked once; its edges reversed are the hull edges,
+    // every other live directed edge bounds a triangle
+    outer.assign((size_t)ne / 2, 0);
+    int nh = 0;
+    for (int e = cw;;) {
+        outer[e >> 1] = 1;
+        if (hull && nh < 2 * n) {
+            hull[2 * nh] = m.dest(e);
+            hull[2 * nh + 1] = m.org[e];
+        }
+        nh++;
+        e = m.lnext(e);
+        if (e == cw) break;
+    }
     // faces: each triangle once, from its directed edge leaving the smallest
     // vertex; bucketed by that vertex, so the output order is lexicographic
     // after sorting the (at most a few) triangles of each bucket
-    std::vector<int> first(n + 1, 0);
-    std::vector<int32_t> jk;
-    std::vector<int> owner;
-    jk.reserve((size_t)4 * n);
-    owner.reserve((size_t)2 * n);
-    const int ne = m.ne;
-    int nh = 0;
+    first.assign((size_t)n + 1, 0);
+    owner.clear();
+    jk.clear();
     for (int e = 0; e < ne; e += 2) {
-        if (m.dead[e >> 2]) continue;
+        if (m.dead[e >> 2] || outer[e >> 1]) continue;
         const int a = m.org[e], b = m.dest(e);
-        const int e2 = m.lnext(e);
-        const int c = m.dest(e2);
-        if (m.lnext(m.lnext(e2)) != e || !m.ccw(a, b, c)) {
-            // the left face is the outside: b -> a is a hull edge with its
-            // triangle on the left
-            if (hull && nh < 2 * n) {
-                hull[2 * nh] = b;
-                hull[2 * nh + 1] = a;
-            }
-            nh++;
-            continue;
-        }
-        if (!(a < b) || !(a < c)) continue;
+        if (!(a < b)) continue;
+        const int c = m.dest(m.lnext(e));
+        if (!(a < c)) continue;
         owner.push_back(a);
         jk.push_back(std::min(b, c));
         jk.push_back(std::max(b, c));
@@ -273,11 +283,11 @@ int delaunay(const int32_t* uv, int n, int32_t* tri, int cap, int32_t* hull, int
     if (T > cap) return -9;  // STEREO_E_CAP
     if (n_hull) *n_hull = (T > 0 && nh <= 2 * n) ? nh : 0;
     for (int i = 0; i < n; i++) first[i + 1] += first[i];
-    std::vector<int> pos(first.begin(), first.end() - 1);
-    std::vector<uint64_t> key(T);
+    pos.assign(first.begin(), first.end() - 1);
+    key.resize(T);
     for (int t = 0; t < T; t++) key[pos[owner[t]]++] = ((uint64_t)(uint32_t)jk[2 * t] << 32) | (uint32_t)jk[2 * t + 1];
     for (int a = 0; a < n; a++) {
-        std::sort(key.begin() + first[a], key.begin() + first[a + 1]);
+        if (first[a + 1] - first[a] > 1) std::sort(key.begin() + first[a], key.begin() + first[a + 1]);
         for (int t = first[a]; t < first[a + 1]; t++) {
             tri[3 * t] = a;
             tri[3 * t + 1] = (int32_t)(key[t] >> 32);
