@@ -50,6 +50,7 @@ def _workload_config(batch, W, H, p, window=0):
                         f"{p.cell}x{p.cell} initial cells, " + (f"{batch} distinct pairs per step" if batch > 1 else "1 pair per step"),
             "pairs_per_step": batch, "batch_window_us": window, "W": W, "H": H, "dmax": p.dmax, "iters": p.iters, "cell": p.cell,
             "l2": "flushed between steps (256 MiB write), flush outside the timed spans",
+            "omega": "dense (t_grad 0)" if PRM["t_grad"] == 0 else f"semi-dense (t_grad {PRM['t_grad']})",
             "parallelism": "replicas: pairs sharded across ranks, no data-path collective"}
 
 
@@ -597,6 +598,80 @@ def run_serving(args):
     return 0
 
 
+def accuracy(D_f, C_f, mask, gt, occ, t_hi):
+    """Error-rate protocol of the paper's accuracy table, on synthetic ground
+    truth: over the valid (C_f < t_hi), non-occluded pixels of Omega_I (mask
+    bit 0), the share within tau px of the truth, tau = 2..5; and the density,
+    the share of non-occluded Omega_I pixels that are valid."""
+    import numpy as np
+    sel = ((mask & 1) != 0) & ~occ
+    ok = (C_f < t_hi) & sel
+    nv = max(1, int(ok.sum()))
+    err = np.abs(D_f - gt)
+    out = {f"lt{t}px": float(((err < t) & ok).sum() / nv) for t in (2, 3, 4, 5)}
+    out["density"] = float(ok.sum() / max(1, int(sel.sum())))
+    return out
+
+
+def run_sweep(args):
+    """The paper's runtime table as a workload: 320x240 .. 1920x1080, 1 / 2 / 4
+    iterations, 4 pairs per point through the batched engine; per point the time
+    per pair and the error rates of the accuracy protocol on synthetic truth."""
+    import numpy as np
+    import torch
+
+    import paper_1511_00758_gb300 as S
+    import scenes
+    S.load()
+    torch.cuda.set_device(0)
+    threads = os.cpu_count() or 1
+    rows = []
+    for W, H, dmax in scenes.SWEEP_SIZES:
+        pairs = scenes.sweep_pairs(W, H, dmax, 4)
+        dev = [(torch.from_numpy(p.left).cuda(), torch.from_numpy(p.right).cuda()) for p in pairs]
+        ctx = _make_ctx(S, 0, pairs, len(pairs), threads, args.window_us)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        for iters in (1, 2, 4):
+            def step(keep=False):
+                ts = [ctx.submit(l, r, W, H, dmax, iters, p.cell) for (l, r), p in zip(dev, pairs)]
+                res = []
+                for t in ts:
+                    r = ctx.poll(t)
+                    if r.status != 0:
+                        raise RuntimeError(f"request failed: {r.status}")
+                    if keep:
+                        o = ctx.result_tensors(r)
+                        res.append({k: o[k].cpu().numpy() for k in ("D_f", "C_f", "mask")})
+                    ctx.release(t)
+                return res
+            step()
+            spans = []
+            for _ in range(max(1, args.steps)):
+                flush.fill_(1)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(ctx.stream)
+                step()
+                e1.record(ctx.stream)
+                e1.synchronize()
+                spans.append(e0.elapsed_time(e1))
+            res = step(keep=True)  # results for the accuracy protocol, outside the timed steps
+            acc = [accuracy(o["D_f"], o["C_f"], o["mask"], p.gt_disp, p.gt_occ, PRM["t_hi"]) for o, p in zip(res, pairs)]
+            ms = sum(spans) / len(spans) / len(pairs)
+            rows.append({"W": W, "H": H, "dmax": dmax, "iters": iters, "pairs": len(pairs), "ms_per_pair": ms,
+                         "mpix_s": W * H / (ms * 1e-3) / 1e6,
+                         **{k: float(np.mean([a[k] for a in acc])) for k in acc[0]}})
+        ctx.close()
+    out = {"metric": "ms per pair and error rates (sweep of the paper's runtime table)", "workload": "sweep",
+           "unit": "ms/pair", "higher_is_better": False, "data": "synthetic",
+           "config": {"workload": "polygon scenes (20 planes, noise sigma 2), 16x16 initial cells, 4 pairs per point "
+                                  "submitted together; L2 flushed between steps",
+                      "omega": "dense (t_grad 0)" if PRM["t_grad"] == 0 else f"semi-dense (t_grad {PRM['t_grad']})"},
+           "rows": rows}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -607,14 +682,19 @@ def main():
     ap.add_argument("--window-us", type=int, default=0, help="batching window of the request scheduler")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", choices=("driving", "mixed", "serving", "large", "burst", "kernel-validate",
+    ap.add_argument("--workload", choices=("driving", "mixed", "serving", "large", "burst", "sweep", "kernel-validate",
                                            "kernel-raster"), default="driving")
+    ap.add_argument("--dense", action="store_true", help="the dense variant: t_grad 0, every pixel evaluated")
     ap.add_argument("--kernel-size", type=int, default=4096)
     ap.add_argument("--plain-kernel", action="store_true", help="kernel-validate: the single-pass kernel")
     ap.add_argument("--mesh-step", type=int, default=6, help="kernel-raster: support-point spacing in pixels")
     ap.add_argument("--rate-hz", type=float, default=120.0)
     ap.add_argument("--duration-s", type=float, default=10.0)
     args = ap.parse_args()
+    if args.dense:
+        PRM["t_grad"] = 0
+    if args.workload == "sweep":
+        return run_sweep(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serving":

@@ -58,7 +58,8 @@ typedef struct {
     int max_slots;             /* requests in flight at once (1 = plain per-pair path) */
     int max_queue;             /* submitted-but-not-admitted requests before STEREO_E_BUSY */
     int t_lo, t_hi;            /* Alg. 3 validation thresholds, 0 <= t_lo <= t_hi < 24 */
-    int t_grad;                /* Omega_I: |dI/du| + |dI/dv| >= t_grad */
+    int t_grad;                /* Omega_I: |dI/du| + |dI/dv| >= t_grad; 0 = the dense
+                                  variant (every pixel inside the 2-pixel border evaluated) */
     int t_fast;                /* FAST-9 intensity threshold */
     int kp_per_bin;            /* keypoints kept per 12x10 bin, 1..32 */
     int uniq_margin;           /* epipolar uniqueness margin in census bits */

@@ -24,7 +24,7 @@ import numpy as np
 __all__ = [
     "Surface", "Scene", "StereoPair", "polygon_scene", "driving_scene",
     "render", "make_pair", "CONFIGS", "config_pairs", "integer_shift_pair", "mixed_pairs", "serving_streams",
-    "large_pairs", "burst_pairs",
+    "large_pairs", "burst_pairs", "sweep_pairs", "SWEEP_SIZES",
 ]
 
 _OCT_SPACING = (16.0, 8.0, 4.0, 2.0)
@@ -336,6 +336,19 @@ def burst_pairs(n=32, cache_dir=None):
     return [_cached(f"burst_{i}", cache_dir,
                     lambda: make_pair("polygon", 1920, 1080, SEED_BASE + 5000 + i, 128, 2, 16, n_poly=20, sigma=2.0),
                     128, 2, 16) for i in range(n)]
+
+
+# Sizes of the iteration and resolution sweep (the paper's runtime table),
+# with the disparity range used at each.
+SWEEP_SIZES = [(320, 240, 64), (640, 480, 64), (800, 600, 64), (1280, 720, 128), (1920, 1080, 128)]
+
+
+def sweep_pairs(W, H, dmax, n=4, cache_dir=None):
+    """n polygon-scene pairs of one sweep size (20 planes, noise sigma 2, 16x16
+    initial cells); the iteration count is chosen at submit time."""
+    return [_cached(f"sweep_{W}x{H}_{i}", cache_dir,
+                    lambda: make_pair("polygon", W, H, SEED_BASE + 6000 + 97 * i + W, dmax, 1, 16, n_poly=20, sigma=2.0),
+                    dmax, 1, 16) for i in range(n)]
 
 
 def _cached(key, cache_dir, make, dmax, iters, cell):

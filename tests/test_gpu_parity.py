@@ -241,9 +241,9 @@ def test_validate(oracle_mod, name, sz, first, bulk):
     assert np.array_equal(xd.cpu().numpy(), want)
 
 
-def _run_ctx(pairs, max_slots=1, host_threads=1, budget=1 << 30, window_us=0):
+def _run_ctx(pairs, max_slots=1, host_threads=1, budget=1 << 30, window_us=0, prm=PRM):
     with S.Context(mem_budget_bytes=budget, max_slots=max_slots, host_threads=host_threads,
-                   batch_window_us=window_us, **PRM) as ctx:
+                   batch_window_us=window_us, **prm) as ctx:
         tickets = [ctx.submit(_t(p.left), _t(p.right), p.left.shape[1], p.left.shape[0], p.dmax, p.iters, p.cell)
                    for p in pairs]
         outs = []
@@ -254,8 +254,8 @@ def _run_ctx(pairs, max_slots=1, host_threads=1, budget=1 << 30, window_us=0):
         return outs
 
 
-def _compare_run(oracle_mod, p, got):
-    want = oracle_mod.run(p.left, p.right, p.dmax, p.iters, p.cell, **PRM)
+def _compare_run(oracle_mod, p, got, prm=PRM):
+    want = oracle_mod.run(p.left, p.right, p.dmax, p.iters, p.cell, **prm)
     assert [len(s) for s in got["support"]] == [len(s) for s in want["support"]]
     for a, b in zip(got["support"], want["support"]):
         assert np.array_equal(a[:, :2], b[:, :2])
@@ -267,6 +267,17 @@ def _compare_run(oracle_mod, p, got):
     dd = got["D_f"].cpu().numpy()
     assert np.abs(dd - want["D_f"]).max() <= TOL_D
     return want
+
+
+@pytest.mark.parametrize("name", ["vga_polygons", "driving_1242x375"])
+def test_end_to_end_dense(oracle_mod, name):
+    """The dense variant (t_grad = 0: every pixel inside the 2-pixel border is
+    evaluated) through the engine, against the oracle run with the same setting."""
+    prm = dict(PRM, t_grad=0)
+    p = scenes.config_pairs(name)[0]
+    want = _compare_run(oracle_mod, p, _run_ctx([p], prm=prm)[0], prm=prm)
+    H, W = p.left.shape
+    assert (want["mask"][2:H - 2, 2:W - 2] & 1).all()  # all of the interior is in Omega
 
 
 def test_end_to_end_vga_one_iteration(oracle_mod):

@@ -492,3 +492,16 @@ def test_accuracy_sanity_band(oracle_mod):
     m = valid & ~p.gt_occ
     acc = (np.abs(r["D_f"] - p.gt_disp)[m] < 3).mean()
     assert valid.mean() > 0.2 and acc > 0.6
+
+
+def test_omega_dense_is_the_interior(oracle_mod):
+    """t_grad = 0 (the dense variant): Omega_I is every pixel at least 2 pixels
+    from the border, and nothing else, whatever the image (the gradient sum is
+    never negative)."""
+    rng = np.random.default_rng(21)
+    for W, H in [(5, 5), (9, 7), (40, 23)]:
+        img = rng.integers(0, 256, (H, W), dtype=np.uint8)
+        om = oracle_mod.omega(img, t_grad=0)
+        want = np.zeros((H, W), bool)
+        want[2:H - 2, 2:W - 2] = True
+        assert np.array_equal(om.astype(bool), want)
