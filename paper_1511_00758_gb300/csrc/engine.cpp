@@ -175,7 +175,7 @@ struct Request {
     std::vector<int32_t> n_support, n_tri;
     std::vector<float> trace;
     int T = 0;
-    int raster_items = 0, n_small = 0, n_hull = 0;
+    int raster_items = 0, n_small = 0, n_hull = 0, n_batch = 0;
     Pinned st_tri;            // one mesh, laid out as tri_stage_bytes() describes
     Pinned st_kp;             // kp_uv + kp_d
     Pinned st_cells;          // cg_key, cg_d, cb_key, x_d
@@ -325,10 +325,11 @@ bool valid_size(int w, int h) {
 
 // Staging layout of one mesh: the hull edges (4 int32 each, first so they
 // stay 16-byte aligned), tri_uv (6 int32) and abc (3 fp32) per triangle,
-// T + 1 work item offsets, the triangle of every raster work item, then the
-// small triangles.
-size_t tri_stage_bytes(int T, int items, int n_small, int n_hull) {
-    return (size_t)n_hull * 16 + (size_t)T * 40 + 4 + (size_t)items * 4 + (size_t)n_small * 4;
+// T + 1 work item offsets, the triangle of every raster work item, the
+// small triangles, then the n_batch + 1 starts of their warp batches.
+size_t tri_stage_bytes(int T, int items, int n_small, int n_hull, int n_batch) {
+    return (size_t)n_hull * 16 + (size_t)T * 40 + 4 + (size_t)items * 4 + (size_t)n_small * 4 +
+           ((size_t)n_batch + 1) * 4;
 }
 
 // Support set -> triangles, planes and raster inputs in the request's pinned
@@ -357,7 +358,9 @@ int mesh_step(Request& r) {
         }
     int n_small = 0;
     const int items = raster_lists(tuv_v.data(), T, r.W, r.H, rows_v.data(), small_v.data(), &n_small);
-    if (!r.st_tri.ensure(tri_stage_bytes(T, items, n_small, n_hull))) return STEREO_E_NOMEM;
+    std::vector<int32_t> batch_v((size_t)n_small + 1);
+    const int n_batch = small_batches(tuv_v.data(), small_v.data(), n_small, r.W, r.H, batch_v.data());
+    if (!r.st_tri.ensure(tri_stage_bytes(T, items, n_small, n_hull, n_batch))) return STEREO_E_NOMEM;
     int32_t* hull = r.st_tri.as<int32_t>();
     for (int j = 0; j < n_hull; j++) {
         const int a = hull_v[2 * j], b = hull_v[2 * j + 1];
@@ -374,10 +377,12 @@ int mesh_step(Request& r) {
     std::memcpy(rows, rows_v.data(), sizeof(int32_t) * ((size_t)T + 1));
     raster_item_tri(rows, T, item_tri);
     std::memcpy(item_tri + items, small_v.data(), sizeof(int32_t) * (size_t)n_small);
+    std::memcpy(item_tri + items + n_small, batch_v.data(), sizeof(int32_t) * ((size_t)n_batch + 1));
     planes(P.data(), D.data(), tri.data(), T, abc);
     r.T = T;
     r.raster_items = items;
     r.n_small = n_small;
+    r.n_batch = n_batch;
     r.n_hull = n_hull;
     r.n_support.push_back(n);
     r.n_tri.push_back(T);
@@ -617,7 +622,7 @@ cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, 
                          double seed_px, double cells_bytes, double raster_bytes, double validate_bytes) {
     for (Request* r : iter.reqs)
         if (r->T > 0)
-            CK(cudaMemcpyAsync((void*)r->dev.hull, r->st_tri.p, tri_stage_bytes(r->T, r->raster_items, r->n_small, r->n_hull),
+            CK(cudaMemcpyAsync((void*)r->dev.hull, r->st_tri.p, tri_stage_bytes(r->T, r->raster_items, r->n_small, r->n_hull, r->n_batch),
                                cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->desc_dev, c->desc_host.p, desc_bytes, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(c->err_dev, 0, sizeof(int), s));
@@ -677,7 +682,7 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         if (!r->st_kp.ensure((size_t)kFastBins * c->K * 12)) return cudaErrorMemoryAllocation;
     }
     for (Request* r : iter.reqs) {
-        const size_t tri_bytes = align_up(tri_stage_bytes(r->T, r->raster_items, r->n_small, r->n_hull) + 64, 256);
+        const size_t tri_bytes = align_up(tri_stage_bytes(r->T, r->raster_items, r->n_small, r->n_hull, r->n_batch) + 64, 256);
         if (tri_bytes > r->tri_block_bytes) {
             std::lock_guard<std::mutex> g(c->mu);
             c->arena.release(r->tri_block);
@@ -694,6 +699,8 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         r->dev.tri_rows = (int32_t*)(tb + (size_t)r->T * 36);
         r->dev.item_tri = r->dev.tri_rows + r->T + 1;
         r->dev.small_tri = r->dev.tri_rows + r->T + 1 + r->raster_items;
+        r->dev.small_batch = r->dev.small_tri + r->n_small;
+        r->dev.n_batch = r->n_batch;
         r->dev.raster_items = r->raster_items;
         r->dev.n_small = r->n_small;
         r->dev.planeidx = r->it == r->iters ? r->pidx_buf : nullptr;  // the LUT is an output of the last pass

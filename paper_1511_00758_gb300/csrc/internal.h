@@ -14,6 +14,7 @@ constexpr int kFastBinsY = 10;
 constexpr int kMaxK = 32;               // keypoints per bin, upper bound
 constexpr int kRasterRows = 8;          // rows of a raster work item of a large triangle
 constexpr int kRasterCols = 128;        // columns of a raster work item of a large triangle
+constexpr int kBatchArea = 1024;        // box pixels of a warp's batch of small triangles (at most 32)
 constexpr int kSmallArea = 256;         // bounding-box pixels of a thread-rasterised triangle
 constexpr uint32_t kNoKey = 0xFFFFFFFFu;
 constexpr uint32_t kIdxMask = (1u << 27) - 1;
@@ -33,7 +34,9 @@ struct PairDev {
     const float* abc;         // T * 3
     int32_t* tri_rows;        // T + 1: exclusive prefix of work items (8x128 blocks) per large triangle
     const int32_t* item_tri;  // raster_items: triangle of each chunk
-    int32_t* small_tri;       // n_small small triangles (32 per warp)
+    int32_t* small_tri;       // n_small small triangles
+    const int32_t* small_batch;  // n_batch + 1 starts of the warp batches of small_tri (null: 32 each)
+    int n_batch;
     const int32_t* hull;      // n_hull directed hull edges (ax, ay, bx, by), interior on the positive side
     int n_hull;               // -1: no hull; the caller clears the frame before the raster
     int n_small;
@@ -129,6 +132,10 @@ void planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float*
 // box has at most kSmallArea pixels (returns their count in *n_small); rows[T + 1]
 // the exclusive prefix of the 8x128 work items of the others (returns the total).
 int raster_lists(const int32_t* tri_uv, int T, int W, int H, int32_t* rows, int32_t* small, int* n_small);
+// Warp batches of the (sorted) small list: consecutive runs of at most 32
+// triangles and kBatchArea box pixels (a single larger box runs alone);
+// batch[0..n] are their starts plus n_small; returns n.
+int small_batches(const int32_t* tri_uv, const int32_t* small, int n_small, int W, int H, int32_t* batch);
 // Triangle of every chunk (items = rows[T] entries).
 void raster_item_tri(const int32_t* rows, int T, int32_t* item_tri);
 

@@ -42,7 +42,9 @@ int work_items(WorkKind k, const PairDev& p) {
         case WK_MATCH_KP: return cdiv((long long)kFastBins * p.K, 8);
         case WK_CLEAR: return cdiv((long long)p.W * p.H, 4096);
         case WK_FILL: return p.cg_key ? cdiv((long long)p.Wc * p.Hc, 4096) : 0;
-        case WK_RASTER: return cdiv(p.n_small, 256) + cdiv(p.raster_items, 8) + (p.n_hull >= 0 ? cdiv(p.H, 8) : 0);
+        case WK_RASTER:
+            return (p.small_batch ? cdiv(p.n_batch, 8) : cdiv(p.n_small, 256)) + cdiv(p.raster_items, 8) +
+                   (p.n_hull >= 0 ? cdiv(p.H, 8) : 0);
         case WK_RESAMPLE: return cdiv((long long)p.Wc * p.Hc, 8);
         default: return 0;
     }
@@ -606,18 +608,26 @@ __device__ __forceinline__ void hull_row_clear(const int32_t* __restrict__ hull,
     }
 }
 
-// Work of one pair: ceil(n_small / 256) blocks of small triangles (32 per
-// warp), ceil(items / 8) blocks of large-triangle work items (one per warp),
+// Work of one pair: blocks of small triangles (8 warp batches each, or 256
+// triangles when no batches are given), ceil(items / 8) blocks of
+// large-triangle work items (one per warp),
 // then, when the hull is given, ceil(H / 8) blocks of hull row clears.
 __device__ __forceinline__ void raster_body(const PairDev& P, int local, SmallTri* s) {
-    const int nsb = (P.n_small + 255) / 256;
+    const int nsb = P.small_batch ? (P.n_batch + 7) / 8 : (P.n_small + 255) / 256;
     const int ncb = (P.raster_items + 7) / 8;
     const int w = threadIdx.x >> 5;
     if (local < nsb) {
-        const int i0 = local * 256 + w * 32;
-        if (i0 < P.n_small)
-            raster_small_warp(P.tri_uv, P.abc, P.small_tri + i0, min(32, P.n_small - i0), P.W, P.H, P.planeidx,
-                              P.Dit, s + w * 32);
+        int i0, n;
+        if (P.small_batch) {  // host-cut batches of about equal box area
+            const int bi = local * 8 + w;
+            if (bi >= P.n_batch) return;
+            i0 = __ldg(P.small_batch + bi);
+            n = __ldg(P.small_batch + bi + 1) - i0;
+        } else {
+            i0 = local * 256 + w * 32;
+            n = min(32, P.n_small - i0);
+        }
+        if (n > 0) raster_small_warp(P.tri_uv, P.abc, P.small_tri + i0, n, P.W, P.H, P.planeidx, P.Dit, s + w * 32);
         return;
     }
     if (local < nsb + ncb) {

@@ -230,50 +230,40 @@ int delaunay(const int32_t* uv, int n, int32_t* tri, int cap) { return delaunay(
 int delaunay(const int32_t* uv, int n, int32_t* tri, int cap, int32_t* hull, int* n_hull) {
     if (n_hull) *n_hull = 0;
     if (n < 3) return 0;
-    // per-thread storage, reused across calls: make_edge initialises every
-    // entry an edge reads, so nothing needs clearing
-    thread_local Mesh m;
-    thread_local std::vector<int> s, first, owner, pos;
-    thread_local std::vector<int32_t> jk;
-    thread_local std::vector<uint64_t> key;
-    thread_local std::vector<uint8_t> outer;
+    Mesh m;
     m.P = uv;
-    m.ne = 0;
-    if (m.nxt.size() < (size_t)16 * n) {  // about 3n quad edges survive; make_edge grows on demand
-        m.nxt.resize((size_t)16 * n);
-        m.org.resize((size_t)16 * n);
-        m.dead.resize((size_t)4 * n);
-    }
-    s.resize(n);
+    m.nxt.resize((size_t)16 * n);  // about 3n quad edges survive; make_edge grows on demand
+    m.org.resize((size_t)16 * n, -1);
+    m.dead.resize((size_t)4 * n, 0);
+    std::vector<int> s(n);
     for (int i = 0; i < n; i++) s[i] = i;
-    const int cw = m.build(s.data(), n, 0).second;  // clockwise hull edge: the outer face on its left
-    const int ne = m.ne;
-    // the outer face, walked once; its edges reversed are the hull edges,
-    // every other live directed edge bounds a triangle
-    outer.assign((size_t)ne / 2, 0);
-    int nh = 0;
-    for (int e = cw;;) {
-        outer[e >> 1] = 1;
-        if (hull && nh < 2 * n) {
-            hull[2 * nh] = m.dest(e);
-            hull[2 * nh + 1] = m.org[e];
-        }
-        nh++;
-        e = m.lnext(e);
-        if (e == cw) break;
-    }
+    m.build(s.data(), n, 0);
     // faces: each triangle once, from its directed edge leaving the smallest
     // vertex; bucketed by that vertex, so the output order is lexicographic
     // after sorting the (at most a few) triangles of each bucket
-    first.assign((size_t)n + 1, 0);
-    owner.clear();
-    jk.clear();
+    std::vector<int> first(n + 1, 0);
+    std::vector<int32_t> jk;
+    std::vector<int> owner;
+    jk.reserve((size_t)4 * n);
+    owner.reserve((size_t)2 * n);
+    const int ne = m.ne;
+    int nh = 0;
     for (int e = 0; e < ne; e += 2) {
-        if (m.dead[e >> 2] || outer[e >> 1]) continue;
+        if (m.dead[e >> 2]) continue;
         const int a = m.org[e], b = m.dest(e);
-        if (!(a < b)) continue;
-        const int c = m.dest(m.lnext(e));
-        if (!(a < c)) continue;
+        const int e2 = m.lnext(e);
+        const int c = m.dest(e2);
+        if (m.lnext(m.lnext(e2)) != e || !m.ccw(a, b, c)) {
+            // the left face is the outside: b -> a is a hull edge with its
+            // triangle on the left
+            if (hull && nh < 2 * n) {
+                hull[2 * nh] = b;
+                hull[2 * nh + 1] = a;
+            }
+            nh++;
+            continue;
+        }
+        if (!(a < b) || !(a < c)) continue;
         owner.push_back(a);
         jk.push_back(std::min(b, c));
         jk.push_back(std::max(b, c));
@@ -283,11 +273,11 @@ int delaunay(const int32_t* uv, int n, int32_t* tri, int cap, int32_t* hull, int
     if (T > cap) return -9;  // STEREO_E_CAP
     if (n_hull) *n_hull = (T > 0 && nh <= 2 * n) ? nh : 0;
     for (int i = 0; i < n; i++) first[i + 1] += first[i];
-    pos.assign(first.begin(), first.end() - 1);
-    key.resize(T);
+    std::vector<int> pos(first.begin(), first.end() - 1);
+    std::vector<uint64_t> key(T);
     for (int t = 0; t < T; t++) key[pos[owner[t]]++] = ((uint64_t)(uint32_t)jk[2 * t] << 32) | (uint32_t)jk[2 * t + 1];
     for (int a = 0; a < n; a++) {
-        if (first[a + 1] - first[a] > 1) std::sort(key.begin() + first[a], key.begin() + first[a + 1]);
+        std::sort(key.begin() + first[a], key.begin() + first[a + 1]);
         for (int t = first[a]; t < first[a + 1]; t++) {
             tri[3 * t] = a;
             tri[3 * t + 1] = (int32_t)(key[t] >> 32);
@@ -352,6 +342,27 @@ int raster_lists(const int32_t* q, int T, int W, int H, int32_t* rows, int32_t* 
         if (area_of[t] >= 0) small[cnt[area_of[t]]++] = t;
     *n_small = cnt[kKeys - 1];
     return s;
+}
+
+int small_batches(const int32_t* q, const int32_t* small, int n_small, int W, int H, int32_t* batch) {
+    int nb = 0, cnt = 0, area = 0;
+    for (int i = 0; i < n_small; i++) {
+        const int32_t* t = q + 6 * (size_t)small[i];
+        const int x0 = std::max(0, std::min(t[0], std::min(t[2], t[4])));
+        const int x1 = std::min(W - 1, std::max(t[0], std::max(t[2], t[4])));
+        const int y0 = std::max(0, std::min(t[1], std::min(t[3], t[5])));
+        const int y1 = std::min(H - 1, std::max(t[1], std::max(t[3], t[5])));
+        const int a = (x1 < x0 || y1 < y0) ? 1 : (x1 - x0 + 1) * (y1 - y0 + 1);
+        if (cnt == 0 || cnt == 32 || area + a > kBatchArea) {  // open a new batch
+            batch[nb++] = i;
+            cnt = 0;
+            area = 0;
+        }
+        cnt++;
+        area += a;
+    }
+    batch[nb] = n_small;
+    return nb;
 }
 
 void raster_item_tri(const int32_t* rows, int T, int32_t* item_tri) {
