@@ -291,6 +291,13 @@ def run_ours(args):
     roofline["other_kernels"] = other
     kinds = {S.KINDS[i]: {"launches": s1.kind_launches[i] - s0.kind_launches[i],
                           "ms": round(s1.kind_ms[i] - s0.kind_ms[i], 4)} for i in range(len(S.KINDS))}
+    rounds = s1.gpu_rounds - s0.gpu_rounds
+    round_stats = {"rounds_per_step": rounds / args.steps,
+                   "round_wall_ms": (s1.round_ms - s0.round_ms) / max(1, rounds),
+                   "graph_ms": (s1.graph_ms - s0.graph_ms) / max(1, rounds),
+                   "exec_ms": (s1.exec_ms - s0.exec_ms) / max(1, rounds),
+                   "instantiations_per_step": (s1.graph_instantiations - s0.graph_instantiations) / args.steps,
+                   "scheduler_busy": (s1.round_ms - s0.round_ms) / max(1e-9, sum(spans))}
     launches = s1.kernel_launches - s0.kernel_launches
     if launches:
         roofline["pairs_per_launch_mean"] = (s1.batched_pairs - s0.batched_pairs) / launches
@@ -351,7 +358,7 @@ def run_ours(args):
                "pairs_per_s": world * B * args.steps / (max_ms / 1e3),
                "latency_ms": {"p50": lats[len(lats) // 2], "p99": lats[min(len(lats) - 1, int(0.99 * len(lats)))]},
                "host_mesh_ms_per_pair": mesh_ms, "host_threads": threads,
-               "plain": plain, "roofline": roofline, "kernels": kinds, "cpu_baseline": cpu, "e2e": e2e,
+               "plain": plain, "roofline": roofline, "kernels": kinds, "rounds": round_stats, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": clk}
         print(json.dumps(out))
     if world > 1:

@@ -153,6 +153,10 @@ typedef struct {
     long long kind_launches[STEREO_K_KINDS];
     double kind_ms[STEREO_K_KINDS];
     double kind_bytes[STEREO_K_KINDS];
+    double round_ms;              /* wall time inside GPU rounds (host preparation to synchronisation) */
+    double graph_ms;              /* of which capturing and updating / instantiating the round's graph */
+    double exec_ms;               /* of which from the graph launch to the round's synchronisation */
+    long long graph_instantiations; /* rounds whose graph could not be updated in place */
 } stereo_stats;
 int stereo_get_stats(stereo_ctx* ctx, stereo_stats* out);
 

@@ -50,7 +50,9 @@ class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_longlong), ("requests_done", ctypes.c_longlong),
                 ("batched_pairs", ctypes.c_longlong), ("gpu_rounds", ctypes.c_longlong),
                 ("host_mesh_ms", ctypes.c_double), ("kind_launches", ctypes.c_longlong * 9),
-                ("kind_ms", ctypes.c_double * 9), ("kind_bytes", ctypes.c_double * 9)]
+                ("kind_ms", ctypes.c_double * 9), ("kind_bytes", ctypes.c_double * 9),
+                ("round_ms", ctypes.c_double), ("graph_ms", ctypes.c_double), ("exec_ms", ctypes.c_double),
+                ("graph_instantiations", ctypes.c_longlong)]
 
 
 KINDS = ("census", "fast_score", "fast_bins", "match_kp", "raster_clear", "raster", "validate", "resample", "fill")

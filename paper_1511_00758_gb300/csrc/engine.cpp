@@ -610,6 +610,10 @@ void add_stats(stereo_stats& to, const stereo_stats& d) {
     to.kernel_launches += d.kernel_launches;
     to.batched_pairs += d.batched_pairs;
     to.gpu_rounds += d.gpu_rounds;
+    to.round_ms += d.round_ms;
+    to.graph_ms += d.graph_ms;
+    to.exec_ms += d.exec_ms;
+    to.graph_instantiations += d.graph_instantiations;
     for (int k = 0; k < STEREO_K_KINDS; k++) {
         to.kind_launches[k] += d.kind_launches[k];
         to.kind_ms[k] += d.kind_ms[k];
@@ -617,49 +621,19 @@ void add_stats(stereo_stats& to, const stereo_stats& d) {
     }
 }
 
-// Copies and launches of one round, issued on stream s (captured into a graph).
-cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, cudaStream_t s, size_t desc_bytes,
-                         double seed_px, double cells_bytes, double raster_bytes, double validate_bytes) {
+// Per-request copies of a round, issued directly on the round's stream
+// before and after the graph launch, so that the graph's nodes do not
+// depend on how many requests the round holds.
+cudaError_t issue_inputs(Group& iter, cudaStream_t s) {
     for (Request* r : iter.reqs)
         if (r->T > 0)
-            CK(cudaMemcpyAsync((void*)r->dev.hull, r->st_tri.p, tri_stage_bytes(r->T, r->raster_items, r->n_small, r->n_hull, r->n_batch),
+            CK(cudaMemcpyAsync((void*)r->dev.hull, r->st_tri.p,
+                               tri_stage_bytes(r->T, r->raster_items, r->n_small, r->n_hull, r->n_batch),
                                cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->desc_dev, c->desc_host.p, desc_bytes, cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(c->err_dev, 0, sizeof(int), s));
-    Params prm = c->prm;
-    prm.err = c->err_dev;
-    const int ns = (int)seed.reqs.size(), ni = (int)iter.reqs.size();
-    if (ns) {
-        CKQ(Lr.run(STEREO_K_CENSUS, ns, seed_px * 10.125, [&] { return launch_census(batch_of(seed, WK_CENSUS), prm, s); }));
-        CKQ(Lr.run(STEREO_K_FAST_SCORE, ns, seed_px * 3.0, [&] { return launch_fast_score(batch_of(seed, WK_FAST_SCORE), prm, s); }));
-        CKQ(Lr.run(STEREO_K_FAST_BINS, ns, 0.0, [&] { return launch_fast_bins(batch_of(seed, WK_FAST_BINS), prm, s); }));
-        CKQ(Lr.run(STEREO_K_MATCH_KP, ns, 0.0, [&] { return launch_match_kp(batch_of(seed, WK_MATCH_KP), prm, s); }));
-    }
-    if (ni) {
-        PairBatch fb = batch_of(iter, WK_FILL);
-        if (fb.total > 0) CKQ(Lr.run(STEREO_K_FILL, ni, cells_bytes, [&] { return launch_fill_cells(fb, s); }));
-        CKQ(Lr.run(STEREO_K_RASTER, ni, raster_bytes, [&] { return launch_raster(batch_of(iter, WK_RASTER), s); }));
-        CKQ(Lr.run(STEREO_K_VALIDATE, ni, validate_bytes, [&] {
-            if (c->bulk_validate) return launch_validate_bulk(batch_of(iter, WK_VALIDATE_BULK), prm, s);
-            int n = 0, nk = 0;
-            if (c->mixed_validate) {
-                const cudaError_t ev = launch_validate(iter.hpd, ni, WK_VALIDATE_MIXED, prm, s, &n);
-                if (ev != cudaSuccess) return ev;
-            } else {  // one launch per cell-side class present in the group
-                for (WorkKind k : kValidateKinds) {
-                    const cudaError_t ev = launch_validate(iter.hpd, ni, k, prm, s, &nk);
-                    if (ev != cudaSuccess) return ev;
-                    n += nk;
-                }
-            }
-            Lr.launched = n;
-            return cudaSuccess;
-        }));
-        PairBatch rb = batch_of(iter, WK_RESAMPLE);
-        if (rb.total > 0) CKQ(Lr.run(STEREO_K_RESAMPLE, ni, 0.0, [&] { return launch_resample(rb, prm, s); }));
-    }
-    // results to pinned host memory
-    CK(cudaMemcpyAsync(c->err_host.p, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    return cudaSuccess;
+}
+
+cudaError_t issue_outputs(stereo_ctx* c, Group& seed, Group& iter, cudaStream_t s) {
     for (Request* r : seed.reqs)  // keypoint slots and their matches, one copy
         CK(cudaMemcpyAsync(r->st_kp.p, r->dev.kp_uv, (size_t)kFastBins * c->K * 12, cudaMemcpyDeviceToHost, s));
     for (Request* r : iter.reqs) {  // the four cell arrays of this pass, one copy
@@ -667,6 +641,45 @@ cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, 
         const size_t nc = (size_t)r->dev.Wc * r->dev.Hc;
         CK(cudaMemcpyAsync(r->st_cells.p, r->cells_dev, 16 * nc, cudaMemcpyDeviceToHost, s));
     }
+    return cudaSuccess;
+}
+
+// The kernels of one round, issued on stream s (captured into a graph).  The
+// same nodes every round: every kernel is launched, with one idle block when
+// its group has no work, and the fused validate a fixed number of times, so
+// the previous executable graph can always be updated in place.
+cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, cudaStream_t s, size_t desc_bytes,
+                         double seed_px, double cells_bytes, double raster_bytes, double validate_bytes) {
+    CK(cudaMemcpyAsync(c->desc_dev, c->desc_host.p, desc_bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(c->err_dev, 0, sizeof(int), s));
+    Params prm = c->prm;
+    prm.err = c->err_dev;
+    const int ns = (int)seed.reqs.size(), ni = (int)iter.reqs.size();
+    CKQ(Lr.run(STEREO_K_CENSUS, ns, seed_px * 10.125, [&] { return launch_census(batch_of(seed, WK_CENSUS), prm, s); }));
+    CKQ(Lr.run(STEREO_K_FAST_SCORE, ns, seed_px * 3.0, [&] { return launch_fast_score(batch_of(seed, WK_FAST_SCORE), prm, s); }));
+    CKQ(Lr.run(STEREO_K_FAST_BINS, ns, 0.0, [&] { return launch_fast_bins(batch_of(seed, WK_FAST_BINS), prm, s); }));
+    CKQ(Lr.run(STEREO_K_MATCH_KP, ns, 0.0, [&] { return launch_match_kp(batch_of(seed, WK_MATCH_KP), prm, s); }));
+    CKQ(Lr.run(STEREO_K_FILL, ni, cells_bytes, [&] { return launch_fill_cells(batch_of(iter, WK_FILL), s); }));
+    CKQ(Lr.run(STEREO_K_RASTER, ni, raster_bytes, [&] { return launch_raster(batch_of(iter, WK_RASTER), s); }));
+    CKQ(Lr.run(STEREO_K_VALIDATE, ni, validate_bytes, [&] {
+        if (c->bulk_validate) return launch_validate_bulk(batch_of(iter, WK_VALIDATE_BULK), prm, s);
+        const int fixed = (std::max(1, c->cfg.max_slots) + kVBatch - 1) / kVBatch;
+        int n = 0, nk = 0;
+        if (c->mixed_validate) {
+            const cudaError_t ev = launch_validate(iter.hpd, ni, WK_VALIDATE_MIXED, prm, s, &n, fixed);
+            if (ev != cudaSuccess) return ev;
+        } else {  // one launch per cell-side class
+            for (WorkKind k : kValidateKinds) {
+                const cudaError_t ev = launch_validate(iter.hpd, ni, k, prm, s, &nk, fixed);
+                if (ev != cudaSuccess) return ev;
+                n += nk;
+            }
+        }
+        Lr.launched = n;
+        return cudaSuccess;
+    }));
+    CKQ(Lr.run(STEREO_K_RESAMPLE, ni, 0.0, [&] { return launch_resample(batch_of(iter, WK_RESAMPLE), prm, s); }));
+    CK(cudaMemcpyAsync(c->err_host.p, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
     return cudaSuccess;
 }
 
@@ -748,6 +761,7 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
     // capture on a private stream nobody else uses, launch on the context's stream
     cudaStream_t cs = c->capture_stream;
     Lr.s = cs;  // event records belong to the captured stream too
+    const double tg0 = now_ms();
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     cudaError_t err = record_round(c, seed, iter, Lr, cs, bs + bi, seed_px, cells_bytes, raster_bytes, validate_bytes);
     cudaGraph_t graph = nullptr;
@@ -775,7 +789,10 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
             c->graph_exec = nullptr;
         }
     }
-    if (!updated) err = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+    if (!updated) {
+        err = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+        Lr.delta.graph_instantiations++;
+    }
     cudaGraphDestroy(graph);
     if (err != cudaSuccess) {
         note_error(err, "cudaGraphInstantiate", __LINE__);
@@ -783,9 +800,14 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         Lr.timed.clear();
         return err;
     }
+    const double tx0 = now_ms();
+    Lr.delta.graph_ms += tx0 - tg0;
+    CK(issue_inputs(iter, s));
     CK(cudaGraphLaunch(c->graph_exec, s));
+    CK(issue_outputs(c, seed, iter, s));
     CK(cudaEventRecord(c->ev, s));
     CK(cudaEventSynchronize(c->ev));
+    Lr.delta.exec_ms += now_ms() - tx0;
     Lr.collect();
     Lr.delta.gpu_rounds++;
     if (*c->err_host.as<int>() != 0) {
@@ -834,7 +856,9 @@ void scheduler(stereo_ctx* c) {
             for (Request* r : iter.reqs) r->state = Q_RUNNING;
         }
         Launcher Lr{c, c->stream};
+        const double tr0 = now_ms();
         cudaError_t e = gpu_round(c, seed, iter, Lr);
+        Lr.delta.round_ms += now_ms() - tr0;
         if (e != cudaSuccess) {
             cudaStreamSynchronize(c->stream);
             Lr.collect();

@@ -14,6 +14,7 @@ constexpr int kFastBinsY = 10;
 constexpr int kMaxK = 32;               // keypoints per bin, upper bound
 constexpr int kRasterRows = 8;          // rows of a raster work item of a large triangle
 constexpr int kRasterCols = 128;        // columns of a raster work item of a large triangle
+constexpr int kVBatch = 32;            // pair descriptors per fused-validate launch (kernel parameters)
 constexpr int kBatchArea = 1024;        // box pixels of a warp's batch of small triangles (at most 32)
 constexpr int kSmallArea = 256;         // bounding-box pixels of a thread-rasterised triangle
 constexpr uint32_t kNoKey = 0xFFFFFFFFu;
@@ -104,9 +105,10 @@ constexpr WorkKind kValidateKinds[] = {WK_VALIDATE, WK_VALIDATE_UNIT, WK_VALIDAT
 WorkKind validate_kind(const PairDev& p);
 // Launches class k over pairs[0..n) (pairs without work under k are skipped),
 // kVBatch pairs per launch, their descriptors passed in the kernel
-// parameters; *launches (may be null) receives the launch count.
+// parameters, and at least min_launches launches (empty ones idle);
+// *launches (may be null) receives the launch count.
 cudaError_t launch_validate(const PairDev* pairs, int n, WorkKind k, const Params& prm, cudaStream_t s,
-                            int* launches);
+                            int* launches, int min_launches = 0);
 // Bulk-copy pipelined validate (same results).  Needs 16-byte aligned D_it,
 // cL, cR, C_f and Omega_I buffers; sets *prm.err if a bounded wait gave up.
 cudaError_t launch_validate_bulk(const PairBatch& b, const Params& prm, cudaStream_t s);

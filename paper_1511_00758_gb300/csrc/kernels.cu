@@ -81,9 +81,11 @@ __device__ __forceinline__ int find_pair(const int* off, int n, int item) {
         }                                                                       \
     }
 
+// At least one block: a launch with no work still runs (one idle block), so
+// a round's graph keeps the same nodes whatever its groups hold.
 static int grid_for(int total, int per_sm) {
     int cap = sm_count() * per_sm;
-    return total < cap ? total : cap;
+    return total < 1 ? 1 : (total < cap ? total : cap);
 }
 
 // ---------------------------------------------------------------- census + Omega_I
@@ -882,7 +884,6 @@ struct VDesc {
     uint32_t magic;
 };
 
-constexpr int kVBatch = 32;
 struct VBatch {
     VDesc d[kVBatch];
     int off[kVBatch + 1];  // exclusive prefix of the pairs' strips
@@ -1483,22 +1484,18 @@ __global__ void k_fill_u32(uint32_t* p, uint32_t value, size_t n) {
 
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_census(const PairBatch& b, const Params& prm, cudaStream_t s) {
-    if (b.total <= 0) return cudaSuccess;
     k_census<<<grid_for(b.total, 8), 256, 0, s>>>(b, prm);
     return cudaGetLastError();
 }
 cudaError_t launch_fast_score(const PairBatch& b, const Params& prm, cudaStream_t s) {
-    if (b.total <= 0) return cudaSuccess;
     k_fast_score<<<grid_for(b.total, 8), 256, 0, s>>>(b, prm);
     return cudaGetLastError();
 }
 cudaError_t launch_fast_bins(const PairBatch& b, const Params& prm, cudaStream_t s) {
-    if (b.total <= 0) return cudaSuccess;
     k_fast_bins<<<grid_for(b.total, 8), 256, 0, s>>>(b, prm);
     return cudaGetLastError();
 }
 cudaError_t launch_match_kp(const PairBatch& b, const Params& prm, cudaStream_t s) {
-    if (b.total <= 0) return cudaSuccess;
     k_match_kp<<<grid_for(b.total, 8), 256, 0, s>>>(b, prm);
     return cudaGetLastError();
 }
@@ -1508,7 +1505,6 @@ cudaError_t launch_raster_clear(const PairBatch& b, cudaStream_t s) {
     return cudaGetLastError();
 }
 cudaError_t launch_raster(const PairBatch& b, cudaStream_t s) {
-    if (b.total <= 0) return cudaSuccess;
     k_raster<<<grid_for(b.total, 8), 256, 0, s>>>(b);
     return cudaGetLastError();
 }
@@ -1555,11 +1551,11 @@ static cudaError_t launch_vbatch(const VBatch& vb, const Params& prm, cudaStream
 }
 
 cudaError_t launch_validate(const PairDev* pairs, int n, WorkKind k, const Params& prm, cudaStream_t s,
-                            int* launches) {
+                            int* launches, int min_launches) {
     int nl = 0;
     VBatch vb;
     int i = 0;
-    while (i < n) {  // up to kVBatch pairs with work per launch
+    while (i < n || nl < min_launches) {  // up to kVBatch pairs with work per launch
         vb.npairs = 0;
         vb.total = 0;
         for (; i < n && vb.npairs < kVBatch; i++) {
@@ -1569,7 +1565,7 @@ cudaError_t launch_validate(const PairDev* pairs, int n, WorkKind k, const Param
             vb.off[vb.npairs++] = vb.total;
             vb.total += items;
         }
-        if (vb.npairs == 0) break;
+        if (vb.npairs == 0 && nl >= min_launches) break;
         vb.off[vb.npairs] = vb.total;
         cudaError_t e;
         switch (k) {
@@ -1597,12 +1593,10 @@ cudaError_t launch_validate_bulk(const PairBatch& b, const Params& prm, cudaStre
     return cudaGetLastError();
 }
 cudaError_t launch_resample(const PairBatch& b, const Params& prm, cudaStream_t s) {
-    if (b.total <= 0) return cudaSuccess;
     k_resample<<<grid_for(b.total, 8), 256, 0, s>>>(b, prm);
     return cudaGetLastError();
 }
 cudaError_t launch_fill_cells(const PairBatch& b, cudaStream_t s) {
-    if (b.total <= 0) return cudaSuccess;
     k_fill_cells<<<grid_for(b.total, 8), 256, 0, s>>>(b);
     return cudaGetLastError();
 }
