@@ -307,6 +307,7 @@ struct stereo_ctx {
     Pinned err_host;
     bool bulk_validate = false;              // the bulk-copy validate kernel (else the plain one)
     bool mixed_validate = true;              // plain validate: one launch for every cell class (else one per class)
+    FILE* launch_log = nullptr;              // per-launch kind and algorithmic bytes, in launch order (diagnostics)
     std::vector<cudaEvent_t> ev_pool;     // timing events of profiled launches
     std::vector<cudaEvent_t> ev_retired;  // events of the last round (still in its graph)
     stereo_stats stats{};
@@ -584,6 +585,9 @@ struct Launcher {
             }
             timed.push_back({kind, a, b});
         }
+        if (c->launch_log)  // one line per launch; a run() body's bytes split evenly over its launches
+            for (int i = 0; i < launched; i++)
+                std::fprintf(c->launch_log, "%d %d %.0f\n", kind, npairs, launched ? bytes / launched : 0.0);
         delta.kernel_launches += launched;
         delta.kind_launches[kind] += launched;
         launched = 1;
@@ -960,6 +964,7 @@ int stereo_create(const stereo_config* cfg, stereo_ctx** out) {
         return STEREO_E_NOMEM;
     }
     *c->err_host.as<int>() = 0;
+    if (const char* v = std::getenv("STEREO_LAUNCH_LOG")) c->launch_log = std::fopen(v, "a");
     if (const char* v = std::getenv("STEREO_VALIDATE")) {
         c->bulk_validate = std::strcmp(v, "bulk") == 0;
         c->mixed_validate = std::strcmp(v, "classes") != 0;
@@ -1127,6 +1132,7 @@ void stereo_destroy(stereo_ctx* c) {
         delete r;
     }
     c->reqs.clear();
+    if (c->launch_log) std::fclose(c->launch_log);
     c->desc_host.free();
     if (c->desc_dev) cudaFree(c->desc_dev);
     if (c->own_arena) cudaFree(c->arena_base);
