@@ -14,7 +14,7 @@ constexpr int kFastBinsY = 10;
 constexpr int kMaxK = 32;               // keypoints per bin, upper bound
 constexpr int kRasterRows = 8;          // rows of a raster work item of a large triangle
 constexpr int kRasterCols = 128;        // columns of a raster work item of a large triangle
-constexpr int kVBatch = 32;            // pair descriptors per fused-validate launch (kernel parameters)
+constexpr int kVBatch = 64;            // pair descriptors per fused-validate launch (about 7 KB of kernel parameters)
 constexpr int kBatchArea = 1024;        // box pixels of a warp's batch of small triangles (at most 32)
 constexpr int kSmallArea = 256;         // bounding-box pixels of a thread-rasterised triangle
 constexpr uint32_t kNoKey = 0xFFFFFFFFu;
