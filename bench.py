@@ -46,7 +46,8 @@ def _env_rank():
 
 
 def _workload_config(batch, W, H, p, window=0):
-    return {"workload": f"{W}x{H} driving-shaped synthetic pairs, dmax {p.dmax}, {p.iters} iterations, "
+    kind = "driving-shaped" if WORKLOAD.startswith("driving") else "polygon-scene"
+    return {"workload": f"{W}x{H} {kind} synthetic pairs, dmax {p.dmax}, {p.iters} iterations, "
                         f"{p.cell}x{p.cell} initial cells, " + (f"{batch} distinct pairs per step" if batch > 1 else "1 pair per step"),
             "pairs_per_step": batch, "batch_window_us": window, "W": W, "H": H, "dmax": p.dmax, "iters": p.iters, "cell": p.cell,
             "l2": "flushed between steps (256 MiB write), flush outside the timed spans",
@@ -208,22 +209,34 @@ def run_ours(args):
     ctx = S.Context(device=local, mem_budget_bytes=budget, max_slots=B, max_queue=4 * B, host_threads=threads,
                     profile=1, batch_window_us=args.window_us, **PRM)
     stream = ctx.stream
+    copy_stream = torch.cuda.Stream()
 
     def one_step(host=False):
         lat = []
         ins = host_in if host else dev_in
         tickets = [ctx.submit(l, r, W, H, p.dmax, p.iters, p.cell) for (l, r), p in zip(ins, pairs)]
+        pending = []  # (ticket, copy-done event): results go to pinned host buffers on a copy stream
         for i, t in enumerate(tickets):
             r = ctx.poll(t)
             if r.status != 0:
                 raise RuntimeError(f"request failed: {r.status}")
             lat.append(r.latency_ms)
-            if host:
-                with torch.cuda.stream(stream):
-                    host_out[i][0].copy_(S.device_view(r.disparity, (H, W), "<f4"), non_blocking=True)
-                    host_out[i][1].copy_(S.device_view(r.cost, (H, W), "|u1"), non_blocking=True)
-                stream.synchronize()
+            if not host:
+                ctx.release(t)
+                continue
+            with torch.cuda.stream(copy_stream):
+                host_out[i][0].copy_(S.device_view(r.disparity, (H, W), "<f4"), non_blocking=True)
+                host_out[i][1].copy_(S.device_view(r.cost, (H, W), "|u1"), non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(copy_stream)
+            pending.append((t, ev))
+            while pending and pending[0][1].query():  # release what has landed
+                ctx.release(pending.pop(0)[0])
+        for t, ev in pending:
+            ev.synchronize()
             ctx.release(t)
+        if host:
+            stream.wait_stream(copy_stream)  # the step's span ends after the copies
         return lat
 
     def timed(nsteps, host=False):
@@ -692,12 +705,16 @@ def main():
     ap.add_argument("--workload", choices=("driving", "mixed", "serving", "large", "burst", "sweep", "kernel-validate",
                                            "kernel-raster"), default="driving")
     ap.add_argument("--dense", action="store_true", help="the dense variant: t_grad 0, every pixel evaluated")
+    ap.add_argument("--config", choices=("driving_1242x375", "vga_polygons"), default="driving_1242x375",
+                    help="scene configuration of the main workload (and of --impl reference)")
     ap.add_argument("--kernel-size", type=int, default=4096)
     ap.add_argument("--plain-kernel", action="store_true", help="kernel-validate: the single-pass kernel")
     ap.add_argument("--mesh-step", type=int, default=6, help="kernel-raster: support-point spacing in pixels")
     ap.add_argument("--rate-hz", type=float, default=120.0)
     ap.add_argument("--duration-s", type=float, default=10.0)
     args = ap.parse_args()
+    global WORKLOAD
+    WORKLOAD = args.config
     if args.dense:
         PRM["t_grad"] = 0
     if args.workload == "sweep":
