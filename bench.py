@@ -204,7 +204,8 @@ def run_ours(args):
                  torch.empty((H, W), dtype=torch.uint8).pin_memory()) for _ in pairs]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     ncpu = os.cpu_count() or 1
-    threads = max(1, min(B, ncpu // max(1, world)))
+    # one core stays free for the scheduler thread and this client thread (measured faster)
+    threads = args.host_threads or max(1, min(B, ncpu // max(1, world) - 1))
     budget = int(0.5 * 2**30) + B * (40 * W * H + (64 << 20))
     ctx = S.Context(device=local, mem_budget_bytes=budget, max_slots=B, max_queue=4 * B, host_threads=threads,
                     profile=1, batch_window_us=args.window_us, **PRM)
@@ -398,7 +399,7 @@ def run_batch_workload(args, name):
     pairs = scenes.mixed_pairs(64) if name == "mixed" else (scenes.large_pairs(16) if name == "large"
                                                             else scenes.burst_pairs(32))
     dev = [(torch.from_numpy(p.left).cuda(), torch.from_numpy(p.right).cuda()) for p in pairs]
-    threads = os.cpu_count() or 1
+    threads = max(1, (os.cpu_count() or 1) - 1)  # one core for the scheduler and this thread
     ctx = _make_ctx(S, 0, pairs, len(pairs), threads, args.window_us)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -551,7 +552,7 @@ def run_serving(args):
     torch.cuda.set_device(0)
     streams = scenes.serving_streams()
     host = [(torch.from_numpy(p.left).pin_memory(), torch.from_numpy(p.right).pin_memory()) for p in streams]
-    threads = os.cpu_count() or 1
+    threads = max(1, (os.cpu_count() or 1) - 1)  # one core for the scheduler and this thread
     ctx = _make_ctx(S, 0, streams * 2, 16, threads, window_us=0, profile=0)
     rng = np.random.default_rng(0x5EED0004)
     arrivals = []
@@ -644,7 +645,7 @@ def run_sweep(args):
     import scenes
     S.load()
     torch.cuda.set_device(0)
-    threads = os.cpu_count() or 1
+    threads = max(1, (os.cpu_count() or 1) - 1)  # one core for the scheduler and this thread
     rows = []
     for W, H, dmax in scenes.SWEEP_SIZES:
         pairs = scenes.sweep_pairs(W, H, dmax, 4)
@@ -705,6 +706,7 @@ def main():
     ap.add_argument("--workload", choices=("driving", "mixed", "serving", "large", "burst", "sweep", "kernel-validate",
                                            "kernel-raster"), default="driving")
     ap.add_argument("--dense", action="store_true", help="the dense variant: t_grad 0, every pixel evaluated")
+    ap.add_argument("--host-threads", type=int, default=0, help="host triangulation workers (0: the core count)")
     ap.add_argument("--config", choices=("driving_1242x375", "vga_polygons"), default="driving_1242x375",
                     help="scene configuration of the main workload (and of --impl reference)")
     ap.add_argument("--kernel-size", type=int, default=4096)
