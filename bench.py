@@ -208,7 +208,8 @@ def run_ours(args):
     threads = args.host_threads or max(1, min(B, ncpu // max(1, world) - 1))
     budget = int(0.5 * 2**30) + B * (40 * W * H + (64 << 20))
     ctx = S.Context(device=local, mem_budget_bytes=budget, max_slots=B, max_queue=4 * B, host_threads=threads,
-                    profile=1, batch_window_us=args.window_us, **PRM)
+                    profile=1, batch_window_us=args.window_us, autotune=0 if args.no_autotune else 1,
+                    tune_w=W, tune_h=H, **PRM)
     stream = ctx.stream
     copy_stream = torch.cuda.Stream()
 
@@ -305,6 +306,7 @@ def run_ours(args):
     roofline["other_kernels"] = other
     kinds = {S.KINDS[i]: {"launches": s1.kind_launches[i] - s0.kind_launches[i],
                           "ms": round(s1.kind_ms[i] - s0.kind_ms[i], 4)} for i in range(len(S.KINDS))}
+    tuning = ctx.tuning()
     rounds = s1.gpu_rounds - s0.gpu_rounds
     round_stats = {"rounds_per_step": rounds / args.steps,
                    "round_wall_ms": (s1.round_ms - s0.round_ms) / max(1, rounds),
@@ -326,7 +328,8 @@ def run_ours(args):
     # plain per-pair path: one request in flight, one host thread
     plain = None
     if not args.no_plain:
-        pctx = S.Context(device=local, mem_budget_bytes=budget, max_slots=1, max_queue=4 * B, host_threads=1, **PRM)
+        pctx = S.Context(device=local, mem_budget_bytes=budget, max_slots=1, max_queue=4 * B, host_threads=1,
+                         autotune=0 if args.no_autotune else 1, tune_w=W, tune_h=H, **PRM)
         ctx_plain = pctx
         nplain = min(B, 4)
 
@@ -372,7 +375,8 @@ def run_ours(args):
                "pairs_per_s": world * B * args.steps / (max_ms / 1e3),
                "latency_ms": {"p50": lats[len(lats) // 2], "p99": lats[min(len(lats) - 1, int(0.99 * len(lats)))]},
                "host_mesh_ms_per_pair": mesh_ms, "host_threads": threads,
-               "plain": plain, "roofline": roofline, "kernels": kinds, "rounds": round_stats, "cpu_baseline": cpu, "e2e": e2e,
+               "plain": plain, "roofline": roofline, "kernels": kinds, "rounds": round_stats, "tuning": tuning,
+               "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": clk}
         print(json.dumps(out))
     if world > 1:
@@ -384,8 +388,10 @@ def run_ours(args):
 # ------------------------------------------------------------------ other workloads
 def _make_ctx(S, local, pairs, slots, threads, window_us=0, profile=1):
     need = sum(80 * p.left.size + (96 << 20) for p in pairs[:slots])
+    big = max(pairs, key=lambda p: p.left.size)  # the tuning round uses the largest frame
     return S.Context(device=local, mem_budget_bytes=int(0.5 * 2**30) + need, max_slots=slots, max_queue=4096,
-                     host_threads=threads, profile=profile, batch_window_us=window_us, **PRM)
+                     host_threads=threads, profile=profile, batch_window_us=window_us, autotune=1,
+                     tune_w=big.left.shape[1], tune_h=big.left.shape[0], **PRM)
 
 
 def run_batch_workload(args, name):
@@ -707,6 +713,7 @@ def main():
                                            "kernel-raster"), default="driving")
     ap.add_argument("--dense", action="store_true", help="the dense variant: t_grad 0, every pixel evaluated")
     ap.add_argument("--host-threads", type=int, default=0, help="host triangulation workers (0: the core count)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel work shapes")
     ap.add_argument("--config", choices=("driving_1242x375", "vga_polygons"), default="driving_1242x375",
                     help="scene configuration of the main workload (and of --impl reference)")
     ap.add_argument("--kernel-size", type=int, default=4096)

@@ -72,6 +72,10 @@ typedef struct {
     int batch_window_us;       /* continuous batching: when some requests are ready for a GPU
                                   stage while others are still in their host step, wait up to
                                   this long for more of them before launching (0 = launch at once) */
+    int autotune;              /* 1 = at create, time the kernels' work-shape candidates on a
+                                  synthetic round of tune_w x tune_h pairs and keep the fastest
+                                  (results do not depend on it; see stereo_get_tuning) */
+    int tune_w, tune_h;        /* frame of the synthetic tuning round (0 = 1242 x 375) */
 } stereo_config;
 
 /* Fill *cfg with the defaults: t_lo 4, t_hi 8, t_grad 8, t_fast 20,
@@ -159,6 +163,20 @@ typedef struct {
     long long graph_instantiations; /* rounds whose graph could not be updated in place */
 } stereo_stats;
 int stereo_get_stats(stereo_ctx* ctx, stereo_stats* out);
+
+/* The kernels' work shapes in use: the raster's small-triangle threshold
+ * (bounding-box pixels; smaller boxes go to warp batches), the box pixels of
+ * a warp batch, the column width of a large-triangle work item, and the
+ * fused validate's blocks per SM and launch mode (1 = one launch for every
+ * cell-side class).  With autotune, also the measured best times of the
+ * synthetic round.  None of these change any result. */
+typedef struct {
+    int small_area, batch_area, raster_cols;
+    int validate_blocks_per_sm, validate_mixed;
+    int autotuned;
+    double raster_us, validate_us;  /* best candidate's time (autotune), else 0 */
+} stereo_tuning;
+int stereo_get_tuning(stereo_ctx* ctx, stereo_tuning* out);
 
 /* ---------------------------------------------------------------------------
  * Stage entry points.  All pointers device unless marked host.

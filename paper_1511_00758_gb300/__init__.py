@@ -13,7 +13,7 @@ import os
 from . import _build
 
 __all__ = [
-    "StereoError", "load", "lib", "Config", "Result", "Stats", "Context",
+    "StereoError", "load", "lib", "Config", "Result", "Stats", "Tuning", "Context",
     "census", "fast", "epipolar_match", "delaunay", "planes", "raster_scratch_bytes", "raster", "raster_noalloc", "validate_bulk",
     "validate", "resample_match", "ERRORS",
 ]
@@ -35,7 +35,8 @@ class Config(ctypes.Structure):
                 ("t_hi", ctypes.c_int), ("t_grad", ctypes.c_int), ("t_fast", ctypes.c_int),
                 ("kp_per_bin", ctypes.c_int), ("uniq_margin", ctypes.c_int), ("host_threads", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("profile", ctypes.c_int), ("inject_mesh_failure", ctypes.c_int),
-                ("batch_window_us", ctypes.c_int)]
+                ("batch_window_us", ctypes.c_int), ("autotune", ctypes.c_int), ("tune_w", ctypes.c_int),
+                ("tune_h", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -55,6 +56,12 @@ class Stats(ctypes.Structure):
                 ("graph_instantiations", ctypes.c_longlong)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("small_area", ctypes.c_int), ("batch_area", ctypes.c_int), ("raster_cols", ctypes.c_int),
+                ("validate_blocks_per_sm", ctypes.c_int), ("validate_mixed", ctypes.c_int), ("autotuned", ctypes.c_int),
+                ("raster_us", ctypes.c_double), ("validate_us", ctypes.c_double)]
+
+
 KINDS = ("census", "fast_score", "fast_bins", "match_kp", "raster_clear", "raster", "validate", "resample", "fill")
 
 
@@ -69,6 +76,7 @@ _SIGS = {
     "stereo_release": (_I, [_P, ctypes.c_uint64]),
     "stereo_destroy": (None, [_P]),
     "stereo_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
+    "stereo_get_tuning": (_I, [_P, ctypes.POINTER(Tuning)]),
     "stereo_last_error": (ctypes.c_char_p, []),
     "stereo_census": (_I, [_P, _P, _I, _I, _I, _P, _P, _P, _P]),
     "stereo_fast": (_I, [_P, _I, _I, _I, _I, _P, _P, _P]),
@@ -247,6 +255,12 @@ class Context:
         s = Stats()
         _check(lib().stereo_get_stats(self.h, ctypes.byref(s)), "stats")
         return s
+
+    def tuning(self):
+        """The kernels' work shapes in use, as a dict (see stereo_get_tuning)."""
+        t = Tuning()
+        _check(lib().stereo_get_tuning(self.h, ctypes.byref(t)), "tuning")
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
 
     def close(self):
         if getattr(self, "h", None):

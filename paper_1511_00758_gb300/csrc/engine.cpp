@@ -150,11 +150,23 @@ struct SupportPoint {
 
 enum State { Q_QUEUED, Q_SEED_READY, Q_RUNNING, Q_HOST, Q_ITER_READY, Q_DONE, Q_FAILED };
 
+// Work shapes of the kernels that a context may tune (results do not depend
+// on them): the raster's small-triangle threshold, warp batch area and
+// large-triangle item width, the fused validate's blocks per SM and launch mode.
+struct Tuning {
+    int small_area = kSmallArea;
+    int batch_area = kBatchArea;
+    int raster_cols = kRasterCols;
+    int validate_bps = 8;
+    int validate_mixed = 1;
+};
+
 struct Request {
     uint64_t ticket = 0;
     int stream_id = 0;
     int W = 0, H = 0, dmax = 0, iters = 0, cell = 0;
     int it = 0, sz = 0;
+    Tuning tune;              // the context's work shapes when admitted
     State state = Q_QUEUED;
     int status = STEREO_OK;
     double t_submit = 0, t_done = 0, mesh_ms = 0;
@@ -306,7 +318,9 @@ struct stereo_ctx {
     int* err_dev = nullptr;                  // set by a device-side wait that gave up
     Pinned err_host;
     bool bulk_validate = false;              // the bulk-copy validate kernel (else the plain one)
-    bool mixed_validate = true;              // plain validate: one launch for every cell class (else one per class)
+    Tuning tune;                             // kernel work shapes (defaults, or chosen by the autotuner)
+    bool tuned = false;                      // tune chosen by the autotuner
+    double tune_raster_us = 0, tune_validate_us = 0;
     FILE* launch_log = nullptr;              // per-launch kind and algorithmic bytes, in launch order (diagnostics)
     std::vector<cudaEvent_t> ev_pool;     // timing events of profiled launches
     std::vector<cudaEvent_t> ev_retired;  // events of the last round (still in its graph)
@@ -358,9 +372,10 @@ int mesh_step(Request& r) {
             tuv_v[6 * t + 2 * k + 1] = P[2 * tri[3 * t + k] + 1];
         }
     int n_small = 0;
-    const int items = raster_lists(tuv_v.data(), T, r.W, r.H, rows_v.data(), small_v.data(), &n_small);
+    const int items = raster_lists(tuv_v.data(), T, r.W, r.H, rows_v.data(), small_v.data(), &n_small,
+                                   r.tune.small_area, r.tune.raster_cols);
     std::vector<int32_t> batch_v((size_t)n_small + 1);
-    const int n_batch = small_batches(tuv_v.data(), small_v.data(), n_small, r.W, r.H, batch_v.data());
+    const int n_batch = small_batches(tuv_v.data(), small_v.data(), n_small, r.W, r.H, batch_v.data(), r.tune.batch_area);
     if (!r.st_tri.ensure(tri_stage_bytes(T, items, n_small, n_hull, n_batch))) return STEREO_E_NOMEM;
     int32_t* hull = r.st_tri.as<int32_t>();
     for (int j = 0; j < n_hull; j++) {
@@ -474,6 +489,7 @@ void admit(stereo_ctx* c) {
         }
         c->queue.pop_front();
         r->block = blk;
+        r->tune = c->tune;
         carve(*r, c->K);
         const size_t N = (size_t)r->W * r->H;
         if (r->in_dev) {
@@ -669,12 +685,12 @@ cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, 
         if (c->bulk_validate) return launch_validate_bulk(batch_of(iter, WK_VALIDATE_BULK), prm, s);
         const int fixed = (std::max(1, c->cfg.max_slots) + kVBatch - 1) / kVBatch;
         int n = 0, nk = 0;
-        if (c->mixed_validate) {
-            const cudaError_t ev = launch_validate(iter.hpd, ni, WK_VALIDATE_MIXED, prm, s, &n, fixed);
+        if (c->tune.validate_mixed) {
+            const cudaError_t ev = launch_validate(iter.hpd, ni, WK_VALIDATE_MIXED, prm, s, &n, fixed, c->tune.validate_bps);
             if (ev != cudaSuccess) return ev;
         } else {  // one launch per cell-side class
             for (WorkKind k : kValidateKinds) {
-                const cudaError_t ev = launch_validate(iter.hpd, ni, k, prm, s, &nk, fixed);
+                const cudaError_t ev = launch_validate(iter.hpd, ni, k, prm, s, &nk, fixed, c->tune.validate_bps);
                 if (ev != cudaSuccess) return ev;
                 n += nk;
             }
@@ -718,6 +734,7 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         r->dev.small_tri = r->dev.tri_rows + r->T + 1 + r->raster_items;
         r->dev.small_batch = r->dev.small_tri + r->n_small;
         r->dev.n_batch = r->n_batch;
+        r->dev.raster_cols = r->tune.raster_cols;
         r->dev.raster_items = r->raster_items;
         r->dev.n_small = r->n_small;
         r->dev.planeidx = r->it == r->iters ? r->pidx_buf : nullptr;  // the LUT is an output of the last pass
@@ -909,7 +926,296 @@ void scheduler(stereo_ctx* c) {
 }  // namespace
 
 // ====================================================================== C ABI
+// ------------------------------------------------------------------ autotuner
+// Times the kernels' work-shape candidates on a synthetic round and keeps the
+// fastest.  None of the shapes changes a result, so the choice only moves
+// time.  The round: 8 pairs of tune_w x tune_h sharing one jittered-lattice
+// mesh as dense as a late pass (one point per 6x6 pixels), each with its own
+// outputs; for the validate, random census codes with the right image a few
+// pixels shifted (so cells get C_g and C_b keys), random Omega_I bits and two
+// cell-side classes (8 and 4) in the batch.  Buffers are allocated for the
+// tuning only and freed before create returns.
+namespace {
+
+struct TuneBuf {
+    std::vector<void*> ptrs;
+    ~TuneBuf() {
+        for (void* p : ptrs) cudaFree(p);
+    }
+    template <class T>
+    T* alloc(size_t n) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(n * sizeof(T), 256)) != cudaSuccess) return nullptr;
+        ptrs.push_back(p);
+        return (T*)p;
+    }
+};
+
+// Minimum over reps timed runs of f (after one untimed run), in microseconds;
+// negative on a CUDA error.
+template <class F>
+double time_runs(cudaStream_t s, cudaEvent_t a, cudaEvent_t b, int reps, F&& f) {
+    if (f() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return -1.0;
+    double best = 1e30;
+    for (int i = 0; i < reps; i++) {
+        cudaEventRecord(a, s);
+        if (f() != cudaSuccess) return -1.0;
+        cudaEventRecord(b, s);
+        if (cudaEventSynchronize(b) != cudaSuccess) return -1.0;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, a, b);
+        best = std::min(best, 1e3 * (double)ms);
+    }
+    return best;
+}
+
+}  // namespace
+
+cudaError_t autotune(stereo_ctx* c) {
+    const int W = c->cfg.tune_w > 0 ? c->cfg.tune_w : 1242, H = c->cfg.tune_h > 0 ? c->cfg.tune_h : 375;
+    if (!valid_size(W, H)) return cudaErrorInvalidValue;
+    const size_t N = (size_t)W * H;
+    const int NP = (int)std::max<size_t>(1, std::min<size_t>(8, ((size_t)512 << 20) / (N * 32)));
+    cudaStream_t s = c->stream;
+    // the mesh: canonical (v, u) order, no duplicates
+    std::vector<int32_t> P;
+    std::vector<float> D;
+    uint32_t seed = 0x5EEDu;
+    auto rnd = [&]() {
+        seed = seed * 1664525u + 1013904223u;
+        return seed >> 8;
+    };
+    std::vector<std::pair<int, int>> pts;
+    for (int v = 0; v < H; v += 6)
+        for (int u = 0; u < W; u += 6)
+            pts.push_back({std::min(H - 1, v + (int)(rnd() % 6)), std::min(W - 1, u + (int)(rnd() % 6))});
+    std::sort(pts.begin(), pts.end());
+    pts.erase(std::unique(pts.begin(), pts.end()), pts.end());
+    const int n = (int)pts.size();
+    for (auto& q : pts) {
+        P.push_back(q.second);
+        P.push_back(q.first);
+        D.push_back(20.0f + 0.01f * q.second + 0.02f * q.first + 0.001f * (float)(rnd() % 1000));
+    }
+    const int cap = 2 * n + 8;
+    std::vector<int32_t> tri((size_t)3 * cap), hull_v((size_t)4 * n + 4);
+    int n_hull = 0;
+    const int T = delaunay(P.data(), n, tri.data(), cap, hull_v.data(), &n_hull);
+    if (T <= 0) return cudaErrorInvalidValue;
+    std::vector<int32_t> tuv((size_t)6 * T);
+    for (int t = 0; t < T; t++)
+        for (int k = 0; k < 3; k++) {
+            tuv[6 * t + 2 * k] = P[2 * tri[3 * t + k]];
+            tuv[6 * t + 2 * k + 1] = P[2 * tri[3 * t + k] + 1];
+        }
+    std::vector<float> abc((size_t)3 * T);
+    planes(P.data(), D.data(), tri.data(), T, abc.data());
+    std::vector<int32_t> hull((size_t)4 * n_hull);
+    for (int j = 0; j < n_hull; j++) {
+        const int a = hull_v[2 * j], b = hull_v[2 * j + 1];
+        hull[4 * j] = P[2 * a];
+        hull[4 * j + 1] = P[2 * a + 1];
+        hull[4 * j + 2] = P[2 * b];
+        hull[4 * j + 3] = P[2 * b + 1];
+    }
+    TuneBuf buf;
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (cudaEventCreate(&ea) != cudaSuccess || cudaEventCreate(&eb) != cudaSuccess) return cudaErrorUnknown;
+    struct Events {
+        cudaEvent_t a, b;
+        ~Events() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } evs{ea, eb};
+    float* dit = buf.alloc<float>(N * NP);
+    int32_t* pidx = buf.alloc<int32_t>(N * NP);
+    PairDev* desc = buf.alloc<PairDev>(NP);
+    int* off = buf.alloc<int>(NP + 1);
+    if (!dit || !pidx || !desc || !off) return cudaErrorMemoryAllocation;
+
+    // raster: every (small-triangle threshold, batch area, item width)
+    const int kSmall[] = {128, 256, 512}, kBatch[] = {512, 1024, 2048}, kCols[] = {64, 128, 256};
+    std::vector<int32_t> rows((size_t)T + 1), small((size_t)T + 1), batch((size_t)T + 2);
+    std::vector<char> blob;
+    char* blob_dev = nullptr;
+    size_t blob_cap = 0;
+    std::vector<PairDev> pd(NP);
+    auto stage = [&](int sa, int ba, int cols) -> cudaError_t {  // host lists + upload + descriptors
+        int n_small = 0;
+        const int items = raster_lists(tuv.data(), T, W, H, rows.data(), small.data(), &n_small, sa, cols);
+        const int n_batch = small_batches(tuv.data(), small.data(), n_small, W, H, batch.data(), ba);
+        const size_t bytes = tri_stage_bytes(T, items, n_small, n_hull, n_batch);
+        blob.assign(bytes, 0);
+        char* q = blob.data();
+        std::memcpy(q, hull.data(), (size_t)16 * n_hull);
+        int32_t* t_uv = (int32_t*)(q + (size_t)16 * n_hull);
+        float* t_abc = (float*)(t_uv + (size_t)6 * T);
+        int32_t* t_rows = (int32_t*)(t_abc + (size_t)3 * T);
+        int32_t* t_item = t_rows + T + 1;
+        std::memcpy(t_uv, tuv.data(), (size_t)24 * T);
+        std::memcpy(t_abc, abc.data(), (size_t)12 * T);
+        std::memcpy(t_rows, rows.data(), (size_t)4 * (T + 1));
+        raster_item_tri(t_rows, T, t_item);
+        std::memcpy(t_item + items, small.data(), (size_t)4 * n_small);
+        std::memcpy(t_item + items + n_small, batch.data(), (size_t)4 * (n_batch + 1));
+        if (bytes > blob_cap) {
+            blob_dev = buf.alloc<char>(bytes * 2);
+            blob_cap = blob_dev ? bytes * 2 : 0;
+            if (!blob_dev) return cudaErrorMemoryAllocation;
+        }
+        cudaError_t e = cudaMemcpy(blob_dev, blob.data(), bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+        std::vector<int> o(NP + 1, 0);
+        for (int i = 0; i < NP; i++) {
+            PairDev p{};
+            p.W = W;
+            p.H = H;
+            p.T = T;
+            p.hull = (const int32_t*)blob_dev;
+            p.n_hull = n_hull;
+            p.tri_uv = (const int32_t*)(blob_dev + (size_t)16 * n_hull);
+            p.abc = (const float*)(p.tri_uv + (size_t)6 * T);
+            p.tri_rows = (int32_t*)(p.abc + (size_t)3 * T);
+            p.item_tri = p.tri_rows + T + 1;
+            p.small_tri = p.tri_rows + T + 1 + items;
+            p.small_batch = p.small_tri + n_small;
+            p.n_small = n_small;
+            p.n_batch = n_batch;
+            p.raster_items = items;
+            p.raster_cols = cols;
+            p.planeidx = pidx + N * i;
+            p.Dit = dit + N * i;
+            pd[i] = p;
+            o[i + 1] = o[i] + work_items(WK_RASTER, p);
+        }
+        if ((e = cudaMemcpy(desc, pd.data(), sizeof(PairDev) * NP, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+        return cudaMemcpy(off, o.data(), sizeof(int) * (NP + 1), cudaMemcpyHostToDevice);
+    };
+    auto raster_batch = [&]() {
+        PairBatch b{};
+        b.pd = desc;
+        b.work_off = off;
+        b.npairs = NP;
+        int o = 0;
+        for (int i = 0; i < NP; i++) o += work_items(WK_RASTER, pd[i]);
+        b.total = o;
+        return b;
+    };
+    Tuning best = c->tune;
+    double best_r = 1e30;
+    for (int sa : kSmall)
+        for (int ba : kBatch)
+            for (int cols : kCols) {
+                cudaError_t e = stage(sa, ba, cols);
+                if (e != cudaSuccess) return e;
+                const PairBatch b = raster_batch();
+                const double us = time_runs(s, ea, eb, 3, [&] { return launch_raster(b, s); });
+                if (us < 0) return cudaErrorUnknown;
+                if (us < best_r) {
+                    best_r = us;
+                    best.small_area = sa;
+                    best.batch_area = ba;
+                    best.raster_cols = cols;
+                }
+            }
+    cudaError_t e = stage(best.small_area, best.batch_area, best.raster_cols);  // D_it for the validate
+    if (e != cudaSuccess) return e;
+    {
+        const PairBatch b = raster_batch();
+        if ((e = launch_raster(b, s)) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    }
+    // validate: blocks per SM and launch mode, on two cell-side classes
+    const int words = (W + 31) / 32;
+    const int Wc4 = (W + 3) / 4, Hc4 = (H + 3) / 4;
+    uint32_t* cL = buf.alloc<uint32_t>(N * NP);
+    uint32_t* cR = buf.alloc<uint32_t>(N * NP);
+    uint32_t* om = buf.alloc<uint32_t>((size_t)words * H * NP);
+    float* Df = buf.alloc<float>(N * NP);
+    uint8_t* Cf = buf.alloc<uint8_t>(N * NP);
+    uint8_t* mask = buf.alloc<uint8_t>(N * NP);
+    uint32_t* cells = buf.alloc<uint32_t>((size_t)2 * Wc4 * Hc4 * NP);
+    if (!cL || !cR || !om || !Df || !Cf || !mask || !cells) return cudaErrorMemoryAllocation;
+    {
+        std::vector<uint32_t> hl(N), hr(N), ho((size_t)words * H);
+        for (size_t i = 0; i < N; i++) hl[i] = rnd() & 0xFFFFFFu;
+        for (size_t i = 0; i < N; i++) {  // the right image: a few pixels of shift, some noise
+            const size_t u = i % W;
+            hr[i] = (u + 3 < (size_t)W && rnd() % 8) ? hl[i + 3] : (rnd() & 0xFFFFFFu);
+        }
+        for (auto& w : ho) w = rnd() | rnd();
+        for (int i = 0; i < NP; i++) {
+            if ((e = cudaMemcpy(cL + N * i, hl.data(), 4 * N, cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (e = cudaMemcpy(cR + N * i, hr.data(), 4 * N, cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (e = cudaMemcpy(om + (size_t)words * H * i, ho.data(), 4 * ho.size(), cudaMemcpyHostToDevice)) !=
+                    cudaSuccess)
+                return e;
+        }
+        if ((e = cudaMemset(Df, 0, 4 * N * NP)) != cudaSuccess || (e = cudaMemset(Cf, 12, N * NP)) != cudaSuccess ||
+            (e = cudaMemset(cells, 0xFF, (size_t)8 * Wc4 * Hc4 * NP)) != cudaSuccess)
+            return e;
+    }
+    std::vector<PairDev> pv(NP);
+    for (int i = 0; i < NP; i++) {
+        PairDev p{};
+        p.W = W;
+        p.H = H;
+        p.cL = cL + N * i;
+        p.cR = cR + N * i;
+        p.omega = om + (size_t)words * H * i;
+        p.Dit = dit + N * i;
+        p.Df = Df + N * i;
+        p.Cf = Cf + N * i;
+        p.mask = mask + N * i;
+        const int sz = i % 2 ? 4 : 8;
+        set_cell_size(p, sz);
+        p.Wc = (W + sz - 1) / sz;
+        p.Hc = (H + sz - 1) / sz;
+        p.cg_key = cells + (size_t)2 * Wc4 * Hc4 * i;
+        p.cb_key = p.cg_key + (size_t)Wc4 * Hc4;
+        pv[i] = p;
+    }
+    Params prm = c->prm;
+    prm.err = c->err_dev;
+    double best_v = 1e30;
+    for (int mixed = 1; mixed >= 0; mixed--)
+        for (int bps : {4, 8, 16}) {
+            const double us = time_runs(s, ea, eb, 3, [&]() -> cudaError_t {
+                if (mixed) return launch_validate(pv.data(), NP, WK_VALIDATE_MIXED, prm, s, nullptr, 0, bps);
+                for (WorkKind k : kValidateKinds) {
+                    const cudaError_t ev = launch_validate(pv.data(), NP, k, prm, s, nullptr, 0, bps);
+                    if (ev != cudaSuccess) return ev;
+                }
+                return cudaSuccess;
+            });
+            if (us < 0) return cudaErrorUnknown;
+            if (us < best_v) {
+                best_v = us;
+                best.validate_mixed = mixed;
+                best.validate_bps = bps;
+            }
+        }
+    c->tune = best;
+    c->tuned = true;
+    c->tune_raster_us = best_r;
+    c->tune_validate_us = best_v;
+    return cudaSuccess;
+}
+
 extern "C" {
+
+int stereo_get_tuning(stereo_ctx* c, stereo_tuning* out) {
+    if (!c || !out) return STEREO_E_INVAL;
+    out->small_area = c->tune.small_area;
+    out->batch_area = c->tune.batch_area;
+    out->raster_cols = c->tune.raster_cols;
+    out->validate_blocks_per_sm = c->tune.validate_bps;
+    out->validate_mixed = c->tune.validate_mixed;
+    out->autotuned = c->tuned ? 1 : 0;
+    out->raster_us = c->tuned ? c->tune_raster_us : 0.0;
+    out->validate_us = c->tuned ? c->tune_validate_us : 0.0;
+    return STEREO_OK;
+}
 
 void stereo_default_config(stereo_config* cfg) {
     std::memset(cfg, 0, sizeof(*cfg));
@@ -967,9 +1273,17 @@ int stereo_create(const stereo_config* cfg, stereo_ctx** out) {
     if (const char* v = std::getenv("STEREO_LAUNCH_LOG")) c->launch_log = std::fopen(v, "a");
     if (const char* v = std::getenv("STEREO_VALIDATE")) {
         c->bulk_validate = std::strcmp(v, "bulk") == 0;
-        c->mixed_validate = std::strcmp(v, "classes") != 0;
+        c->tune.validate_mixed = std::strcmp(v, "classes") != 0;
     }
     if (prepare_kernels() != cudaSuccess) c->bulk_validate = false;
+    if (cfg->autotune) {  // before the scheduler starts: the tuning round owns the stream
+        const Tuning keep = c->tune;
+        if (autotune(c) != cudaSuccess) {
+            note_error(cudaGetLastError(), "autotune (defaults kept)", __LINE__);
+            c->tune = keep;
+            c->tuned = false;
+        }
+    }
     c->pool.start(std::max(1, cfg->host_threads));
     c->sched = std::thread(scheduler, c);
     *out = c;

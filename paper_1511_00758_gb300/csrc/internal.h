@@ -38,6 +38,7 @@ struct PairDev {
     int32_t* small_tri;       // n_small small triangles
     const int32_t* small_batch;  // n_batch + 1 starts of the warp batches of small_tri (null: 32 each)
     int n_batch;
+    int raster_cols;              // columns of a large-triangle work item (0: kRasterCols)
     const int32_t* hull;      // n_hull directed hull edges (ax, ay, bx, by), interior on the positive side
     int n_hull;               // -1: no hull; the caller clears the frame before the raster
     int n_small;
@@ -108,7 +109,7 @@ WorkKind validate_kind(const PairDev& p);
 // parameters, and at least min_launches launches (empty ones idle);
 // *launches (may be null) receives the launch count.
 cudaError_t launch_validate(const PairDev* pairs, int n, WorkKind k, const Params& prm, cudaStream_t s,
-                            int* launches, int min_launches = 0);
+                            int* launches, int min_launches = 0, int blocks_per_sm = 8);
 // Bulk-copy pipelined validate (same results).  Needs 16-byte aligned D_it,
 // cL, cR, C_f and Omega_I buffers; sets *prm.err if a bounded wait gave up.
 cudaError_t launch_validate_bulk(const PairBatch& b, const Params& prm, cudaStream_t s);
@@ -133,11 +134,13 @@ void planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float*
 // Raster work lists of a mesh: small[] the triangles whose clipped bounding
 // box has at most kSmallArea pixels (returns their count in *n_small); rows[T + 1]
 // the exclusive prefix of the 8x128 work items of the others (returns the total).
-int raster_lists(const int32_t* tri_uv, int T, int W, int H, int32_t* rows, int32_t* small, int* n_small);
+int raster_lists(const int32_t* tri_uv, int T, int W, int H, int32_t* rows, int32_t* small, int* n_small,
+                 int small_area = kSmallArea, int cols = kRasterCols);
 // Warp batches of the (sorted) small list: consecutive runs of at most 32
 // triangles and kBatchArea box pixels (a single larger box runs alone);
 // batch[0..n] are their starts plus n_small; returns n.
-int small_batches(const int32_t* tri_uv, const int32_t* small, int n_small, int W, int H, int32_t* batch);
+int small_batches(const int32_t* tri_uv, const int32_t* small, int n_small, int W, int H, int32_t* batch,
+                  int batch_area = kBatchArea);
 // Triangle of every chunk (items = rows[T] entries).
 void raster_item_tri(const int32_t* rows, int T, int32_t* item_tri);
 

@@ -406,10 +406,10 @@ __device__ __forceinline__ bool tri_is_small(const int32_t* __restrict__ q, int 
     return x1 < x0 || y1 < y0 || (x1 - x0 + 1) * (y1 - y0 + 1) <= kSmallArea;
 }
 
-// Work items of a large triangle: 8-row by 128-column blocks of its clipped box.
-__device__ __forceinline__ int tri_col_chunks(const int32_t* __restrict__ q, int W) {
+// Work items of a large triangle: 8-row by cols-column blocks of its clipped box.
+__device__ __forceinline__ int tri_col_chunks(const int32_t* __restrict__ q, int W, int cols = kRasterCols) {
     const int x0 = max(0, min(q[0], min(q[2], q[4]))), x1 = min(W - 1, max(q[0], max(q[2], q[4])));
-    return (x1 - x0) / kRasterCols + 1;
+    return (x1 - x0) / cols + 1;
 }
 __device__ __forceinline__ int tri_chunks(const int32_t* __restrict__ q, int W, int H) {
     if (tri_is_small(q, W, H)) return 0;
@@ -506,10 +506,10 @@ __device__ __forceinline__ int floordiv32(int a, int b) {  // b > 0
 
 __device__ __forceinline__ void raster_chunk_tc(const int32_t* __restrict__ tri_uv, const float* __restrict__ abc,
                                                 int t, int item, int W, int H, int32_t* __restrict__ pidx,
-                                                float* __restrict__ dit) {
+                                                float* __restrict__ dit, int cols) {
     const int lane = threadIdx.x & 31;
     // item -> (row block, column block) of the triangle's clipped box
-    const int ncol = tri_col_chunks(tri_uv + 6 * (size_t)t, W);
+    const int ncol = tri_col_chunks(tri_uv + 6 * (size_t)t, W, cols);
     const int c = item / ncol, cc = item - c * ncol;
     TriEdges e;
     tri_setup(tri_uv, t, e);
@@ -523,8 +523,8 @@ __device__ __forceinline__ void raster_chunk_tc(const int32_t* __restrict__ tri_
     const int ymax = min(H - 1, max(e.y[0], max(e.y[1], e.y[2])));
     const int v0 = ymin + c * kRasterRows;
     const int vr = v0 + (lane & (kRasterRows - 1));
-    const int bx0 = max(0, min(e.x[0], min(e.x[1], e.x[2]))) + cc * kRasterCols;
-    int lo = bx0, hi = min(W - 1, bx0 + kRasterCols - 1);
+    const int bx0 = max(0, min(e.x[0], min(e.x[1], e.x[2]))) + cc * cols;
+    int lo = bx0, hi = min(W - 1, bx0 + cols - 1);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         // A u + B v + C >= bias  <=>  A u >= R
@@ -636,7 +636,8 @@ __device__ __forceinline__ void raster_body(const PairDev& P, int local, SmallTr
         const int item = (local - nsb) * 8 + w;
         if (item >= P.raster_items) return;
         const int t = __ldg(P.item_tri + item);
-        raster_chunk_tc(P.tri_uv, P.abc, t, item - __ldg(P.tri_rows + t), P.W, P.H, P.planeidx, P.Dit);
+        raster_chunk_tc(P.tri_uv, P.abc, t, item - __ldg(P.tri_rows + t), P.W, P.H, P.planeidx, P.Dit,
+                        P.raster_cols > 0 ? P.raster_cols : kRasterCols);
         return;
     }
     const int v = (local - nsb - ncb) * 8 + w;
@@ -762,7 +763,7 @@ __global__ void __launch_bounds__(256) k_raster_dev(const int32_t* __restrict__ 
             const int mid = (lo + hi + 1) >> 1;
             if (__ldg(rows + mid) <= item) lo = mid; else hi = mid - 1;
         }
-        raster_chunk_tc(tri_uv, abc, lo, item - __ldg(rows + lo), W, H, pidx, dit);
+        raster_chunk_tc(tri_uv, abc, lo, item - __ldg(rows + lo), W, H, pidx, dit, kRasterCols);
     }
 }
 
@@ -1545,13 +1546,14 @@ static VDesc vdesc_of(const PairDev& p) {
 }
 
 template <int KIND>
-static cudaError_t launch_vbatch(const VBatch& vb, const Params& prm, cudaStream_t s) {
-    k_validate<KIND><<<grid_for(cdiv(vb.total, 8), 8), 256, 0, s>>>(vb, prm);  // 8 strips (warps) per block
+static cudaError_t launch_vbatch(const VBatch& vb, const Params& prm, cudaStream_t s, int bps) {
+    k_validate<KIND><<<grid_for(cdiv(vb.total, 8), bps), 256, 0, s>>>(vb, prm);  // 8 strips (warps) per block
     return cudaGetLastError();
 }
 
 cudaError_t launch_validate(const PairDev* pairs, int n, WorkKind k, const Params& prm, cudaStream_t s,
-                            int* launches, int min_launches) {
+                            int* launches, int min_launches, int blocks_per_sm) {
+    const int bps = blocks_per_sm > 0 ? blocks_per_sm : 8;
     int nl = 0;
     VBatch vb;
     int i = 0;
@@ -1569,12 +1571,12 @@ cudaError_t launch_validate(const PairDev* pairs, int n, WorkKind k, const Param
         vb.off[vb.npairs] = vb.total;
         cudaError_t e;
         switch (k) {
-            case WK_VALIDATE: e = launch_vbatch<WK_VALIDATE>(vb, prm, s); break;
-            case WK_VALIDATE_UNIT: e = launch_vbatch<WK_VALIDATE_UNIT>(vb, prm, s); break;
-            case WK_VALIDATE_C4: e = launch_vbatch<WK_VALIDATE_C4>(vb, prm, s); break;
-            case WK_VALIDATE_C2: e = launch_vbatch<WK_VALIDATE_C2>(vb, prm, s); break;
-            case WK_VALIDATE_ANY: e = launch_vbatch<WK_VALIDATE_ANY>(vb, prm, s); break;
-            case WK_VALIDATE_MIXED: e = launch_vbatch<WK_VALIDATE_MIXED>(vb, prm, s); break;
+            case WK_VALIDATE: e = launch_vbatch<WK_VALIDATE>(vb, prm, s, bps); break;
+            case WK_VALIDATE_UNIT: e = launch_vbatch<WK_VALIDATE_UNIT>(vb, prm, s, bps); break;
+            case WK_VALIDATE_C4: e = launch_vbatch<WK_VALIDATE_C4>(vb, prm, s, bps); break;
+            case WK_VALIDATE_C2: e = launch_vbatch<WK_VALIDATE_C2>(vb, prm, s, bps); break;
+            case WK_VALIDATE_ANY: e = launch_vbatch<WK_VALIDATE_ANY>(vb, prm, s, bps); break;
+            case WK_VALIDATE_MIXED: e = launch_vbatch<WK_VALIDATE_MIXED>(vb, prm, s, bps); break;
             default: e = cudaErrorInvalidValue;
         }
         if (e != cudaSuccess) return e;

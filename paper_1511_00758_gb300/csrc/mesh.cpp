@@ -310,13 +310,14 @@ void planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float*
     }
 }
 
-int raster_lists(const int32_t* q, int T, int W, int H, int32_t* rows, int32_t* small, int* n_small) {
+int raster_lists(const int32_t* q, int T, int W, int H, int32_t* rows, int32_t* small, int* n_small, int small_area,
+                 int cols) {
     // small triangles are listed by box width class, then by box area (a
     // counting sort), so the 32 triangles of a warp have boxes of similar
     // width and size
     std::vector<int> area_of(T, -1);
     constexpr int kClasses = 7;  // box width 1, 2, <=4, <=8, <=16, <=32, wider
-    constexpr int kKeys = kClasses * (kSmallArea + 1);
+    const int kKeys = kClasses * (small_area + 1);
     std::vector<int> cnt(kKeys + 1, 0);
     int s = 0;
     for (int t = 0; t < T; t++, q += 6) {
@@ -326,14 +327,14 @@ int raster_lists(const int32_t* q, int T, int W, int H, int32_t* rows, int32_t* 
         const int y0 = std::max(0, std::min(q[1], std::min(q[3], q[5])));
         const int y1 = std::min(H - 1, std::max(q[1], std::max(q[3], q[5])));
         const int area = (x1 < x0 || y1 < y0) ? 0 : (x1 - x0 + 1) * (y1 - y0 + 1);
-        if (area <= kSmallArea) {
+        if (area <= small_area) {
             const int bw = x1 - x0 + 1;
             int cls = 0;
             while (cls < kClasses - 1 && (1 << cls) < bw) cls++;
-            area_of[t] = cls * (kSmallArea + 1) + area;
+            area_of[t] = cls * (small_area + 1) + area;
             cnt[area_of[t] + 1]++;
         } else {
-            s += ((y1 - y0) / kRasterRows + 1) * ((x1 - x0) / kRasterCols + 1);
+            s += ((y1 - y0) / kRasterRows + 1) * ((x1 - x0) / cols + 1);
         }
     }
     rows[T] = s;
@@ -344,7 +345,7 @@ int raster_lists(const int32_t* q, int T, int W, int H, int32_t* rows, int32_t* 
     return s;
 }
 
-int small_batches(const int32_t* q, const int32_t* small, int n_small, int W, int H, int32_t* batch) {
+int small_batches(const int32_t* q, const int32_t* small, int n_small, int W, int H, int32_t* batch, int batch_area) {
     int nb = 0, cnt = 0, area = 0;
     for (int i = 0; i < n_small; i++) {
         const int32_t* t = q + 6 * (size_t)small[i];
@@ -353,7 +354,7 @@ int small_batches(const int32_t* q, const int32_t* small, int n_small, int W, in
         const int y0 = std::max(0, std::min(t[1], std::min(t[3], t[5])));
         const int y1 = std::min(H - 1, std::max(t[1], std::max(t[3], t[5])));
         const int a = (x1 < x0 || y1 < y0) ? 1 : (x1 - x0 + 1) * (y1 - y0 + 1);
-        if (cnt == 0 || cnt == 32 || area + a > kBatchArea) {  // open a new batch
+        if (cnt == 0 || cnt == 32 || area + a > batch_area) {  // open a new batch
             batch[nb++] = i;
             cnt = 0;
             area = 0;

@@ -280,6 +280,23 @@ def test_end_to_end_dense(oracle_mod, name):
     assert (want["mask"][2:H - 2, 2:W - 2] & 1).all()  # all of the interior is in Omega
 
 
+def test_end_to_end_autotuned(oracle_mod):
+    """A context that tunes its kernels' work shapes at create gives the same
+    results (the shapes only move time)."""
+    p = scenes.config_pairs("driving_1242x375")[0]
+    H, W = p.left.shape
+    with S.Context(mem_budget_bytes=1 << 30, max_slots=1, host_threads=1, autotune=1, tune_w=W, tune_h=H,
+                   **PRM) as ctx:
+        tu = ctx.tuning()
+        assert tu["autotuned"] == 1 and tu["raster_us"] > 0 and tu["validate_us"] > 0
+        assert tu["small_area"] in (128, 256, 512) and tu["batch_area"] in (512, 1024, 2048)
+        assert tu["raster_cols"] in (64, 128, 256) and tu["validate_blocks_per_sm"] in (4, 8, 16)
+        t = ctx.submit(_t(p.left), _t(p.right), W, H, p.dmax, p.iters, p.cell)
+        got = ctx.result_tensors(ctx.poll(t))
+        ctx.release(t)
+    _compare_run(oracle_mod, p, got)
+
+
 def test_end_to_end_vga_one_iteration(oracle_mod):
     p = scenes.config_pairs("vga_polygons")[0]
     want = _compare_run(oracle_mod, p, _run_ctx([p])[0])
