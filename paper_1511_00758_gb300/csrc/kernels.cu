@@ -1068,6 +1068,11 @@ __device__ __forceinline__ void validate_dispatch(const VDesc& a, int s, const P
 template <int KIND>
 __global__ void __launch_bounds__(256, 4) k_validate(const __grid_constant__ VBatch b, Params prm) {
     const int nw = gridDim.x * (blockDim.x >> 5);
+    if (b.npairs == 1) {  // one pair: its fields are fixed constant-bank operands
+        for (int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < b.total; s += nw)
+            validate_dispatch<KIND>(b.d[0], s, prm);
+        return;
+    }
     for (int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < b.total; s += nw) {
         int lo = 0, hi = b.npairs - 1;  // the last pair whose first strip is <= s
         while (lo < hi) {
