@@ -34,7 +34,7 @@ struct PairDev {
     const int32_t* tri_uv;    // T * 6
     const float* abc;         // T * 3
     int32_t* tri_rows;        // T + 1: exclusive prefix of work items (8x128 blocks) per large triangle
-    const int32_t* item_tri;  // raster_items: triangle of each chunk
+    const int32_t* item_tri;  // raster_items: triangle of each large-triangle work item
     int32_t* small_tri;       // n_small small triangles
     const int32_t* small_batch;  // n_batch + 1 starts of the warp batches of small_tri (null: 32 each)
     int n_batch;
@@ -141,7 +141,7 @@ int raster_lists(const int32_t* tri_uv, int T, int W, int H, int32_t* rows, int3
 // batch[0..n] are their starts plus n_small; returns n.
 int small_batches(const int32_t* tri_uv, const int32_t* small, int n_small, int W, int H, int32_t* batch,
                   int batch_area = kBatchArea);
-// Triangle of every chunk (items = rows[T] entries).
+// Triangle of every large-triangle work item (items = rows[T] entries).
 void raster_item_tri(const int32_t* rows, int T, int32_t* item_tri);
 
 }  // namespace stereo

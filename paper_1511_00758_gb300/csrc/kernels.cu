@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(256) k_raster(PairBatch b) {
 // Device-built work lists for callers without a host copy of the triangles,
 // in three launches over blocks of 1024 triangles: per-block totals, a scan
 // of the block totals, then each block's exclusive scan written out.
-// rows[T + 1]: chunk prefix of the large triangles; small[0..n): the small
+// rows[T + 1]: work-item prefix of the large triangles; small[0..n): the small
 // triangles in index order, small[T] = n; blk[2 * nblk]: block offsets.
 constexpr int kListBlock = 1024;
 

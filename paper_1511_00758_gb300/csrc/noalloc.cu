@@ -25,7 +25,7 @@ namespace {
 constexpr int kNoAllocMaxTriangles = 262143;
 constexpr int kMaxDevices = 64;
 
-// Work lists: row-chunk offsets (T + 1), the small-triangle list (T + 1),
+// Work lists: work-item offsets of the large triangles (T + 1), the small-triangle list (T + 1),
 // then per-block offsets of the list builder.
 static __device__ __align__(256) int32_t
     g_raster_lists[2 * (kNoAllocMaxTriangles + 1) + 2 * ((kNoAllocMaxTriangles + 1023) / 1024)];
