@@ -351,6 +351,20 @@ def test_batched_serving_matches_solo(oracle_mod):
                 assert np.array_equal(x, y)
 
 
+def test_batched_mixed_cell_classes(oracle_mod):
+    """One batch whose pairs fall in every fused-validate class over their passes
+    (cell sides 5, 12, 2 and 3 halve to 6, 2, 1, 1 ...): batched equals solo bit
+    for bit, and one pair equals the oracle."""
+    pairs = [scenes.make_pair("polygon", 200, 120, 700 + i, 48, 3, cell, n_poly=8)
+             for i, cell in enumerate((5, 12, 2, 3))]
+    solo = [_run_ctx([p])[0] for p in pairs]
+    mixed = _run_ctx(pairs, max_slots=4, host_threads=2)
+    for a, b in zip(solo, mixed):
+        for k in ("D_f", "C_f", "mask", "planeidx"):
+            assert torch.equal(a[k], b[k]), k
+    _compare_run(oracle_mod, pairs[1], mixed[1])
+
+
 def test_host_input_pointers(oracle_mod):
     p = scenes.config_pairs("vga_polygons")[0]
     with S.Context(mem_budget_bytes=1 << 28, **PRM) as ctx:
