@@ -24,13 +24,13 @@ static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b)
 
 static int validate_items(WorkKind k, const PairDev& p);
 
-constexpr int kTileW = 32;   // census / FAST score tile: one warp per row
-constexpr int kTileH = 8;
+constexpr int kTileW = 32;     // census / FAST score tile: 32 columns (a warp's lanes)
+constexpr int kSeedRows = 32;  // by 32 rows
 
 int work_items(WorkKind k, const PairDev& p) {
     switch (k) {
         case WK_CENSUS:
-        case WK_FAST_SCORE: return cdiv(p.W, kTileW) * cdiv(p.H, kTileH);
+        case WK_FAST_SCORE: return cdiv(p.W, kTileW) * cdiv(p.H, kSeedRows);
         case WK_VALIDATE:
         case WK_VALIDATE_UNIT:
         case WK_VALIDATE_C4:
@@ -90,7 +90,22 @@ static int grid_for(int total, int per_sm) {
 
 // ---------------------------------------------------------------- census + Omega_I
 // Census 5x5 (Sec. III-C) of L and R and the Omega_I bit map of L.  One
-// 32x8 tile per block; rows are staged with a 2-pixel halo in shared memory.
+// 32x32 tile per block of 256 threads; lane l of warp w computes column l of
+// rows w, w + 8, w + 16, w + 24.  Rows are staged with a 2-pixel halo in
+// shared memory (borders clamped), loaded by row and column loops without
+// divisions.
+
+template <int HALO>
+__device__ __forceinline__ void stage_tile(uint8_t (*s)[kTileW + 2 * HALO], const uint8_t* __restrict__ img, int W,
+                                           int H, int u0, int v0) {
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    for (int r = ly; r < kSeedRows + 2 * HALO; r += 8) {
+        const size_t row = (size_t)min(max(v0 + r - HALO, 0), H - 1) * W;
+        s[r][lx] = __ldg(img + row + min(max(u0 + lx - HALO, 0), W - 1));
+        if (lx < 2 * HALO) s[r][kTileW + lx] = __ldg(img + row + min(max(u0 + kTileW + lx - HALO, 0), W - 1));
+    }
+}
+
 __device__ __forceinline__ uint32_t census_at(const uint8_t (*s)[kTileW + 4], int r, int c) {
     const int p = s[r][c];
     uint32_t code = 0;
@@ -108,38 +123,38 @@ __device__ __forceinline__ uint32_t census_at(const uint8_t (*s)[kTileW + 4], in
 }
 
 __device__ __forceinline__ void census_body(const PairDev& P, int local, const Params& prm) {
-    __shared__ uint8_t sL[kTileH + 4][kTileW + 4];
-    __shared__ uint8_t sR[kTileH + 4][kTileW + 4];
+    __shared__ uint8_t sL[kSeedRows + 4][kTileW + 4];
+    __shared__ uint8_t sR[kSeedRows + 4][kTileW + 4];
     const int W = P.W, H = P.H;
     const int tx_n = (W + kTileW - 1) / kTileW;
-    const int u0 = (local % tx_n) * kTileW, v0 = (local / tx_n) * kTileH;
-    for (int i = threadIdx.x; i < (kTileH + 4) * (kTileW + 4); i += blockDim.x) {
-        int r = i / (kTileW + 4), c = i % (kTileW + 4);
-        int v = min(max(v0 + r - 2, 0), H - 1), u = min(max(u0 + c - 2, 0), W - 1);
-        sL[r][c] = P.L[(size_t)v * W + u];
-        sR[r][c] = P.R[(size_t)v * W + u];
-    }
+    const int u0 = (local % tx_n) * kTileW, v0 = (local / tx_n) * kSeedRows;
+    stage_tile<2>(sL, P.L, W, H, u0, v0);
+    if (P.cR) stage_tile<2>(sR, P.R, W, H, u0, v0);
     __syncthreads();
-    const int lx = threadIdx.x % kTileW, ly = threadIdx.x / kTileW;
-    const int u = u0 + lx, v = v0 + ly;
-    const bool inimg = u < W && v < H;
-    const bool interior = u >= 2 && u < W - 2 && v >= 2 && v < H - 2;
-    uint32_t cl = 0, cr = 0;
-    bool om = false;
-    if (interior) {
-        cl = census_at(sL, ly + 2, lx + 2);
-        cr = census_at(sR, ly + 2, lx + 2);
-        int gx = abs((int)sL[ly + 2][lx + 3] - (int)sL[ly + 2][lx + 1]);
-        int gy = abs((int)sL[ly + 3][lx + 2] - (int)sL[ly + 1][lx + 2]);
-        om = gx + gy >= prm.t_grad;
+    const int lx = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int u = u0 + lx;
+    const int words = (W + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < kSeedRows / 8; k++) {
+        const int ly = w + 8 * k, v = v0 + ly;
+        const bool interior = u >= 2 && u < W - 2 && v >= 2 && v < H - 2;
+        uint32_t cl = 0, cr = 0;
+        bool om = false;
+        if (interior) {
+            cl = census_at(sL, ly + 2, lx + 2);
+            if (P.cR) cr = census_at(sR, ly + 2, lx + 2);
+            const int gx = abs((int)sL[ly + 2][lx + 3] - (int)sL[ly + 2][lx + 1]);
+            const int gy = abs((int)sL[ly + 3][lx + 2] - (int)sL[ly + 1][lx + 2]);
+            om = gx + gy >= prm.t_grad;
+        }
+        if (u < W && v < H) {
+            const size_t p = (size_t)v * W + u;
+            if (P.cL) P.cL[p] = cl;
+            if (P.cR) P.cR[p] = cr;
+        }
+        const unsigned bits = __ballot_sync(0xffffffffu, om);
+        if (lx == 0 && v < H && P.omega) P.omega[(size_t)v * words + (u0 >> 5)] = bits;
     }
-    if (inimg) {
-        size_t p = (size_t)v * W + u;
-        if (P.cL) P.cL[p] = cl;
-        if (P.cR) P.cR[p] = cr;
-    }
-    unsigned bits = __ballot_sync(0xffffffffu, om);
-    if (lx == 0 && v < H && P.omega) P.omega[(size_t)v * ((W + 31) / 32) + (u0 >> 5)] = bits;
     __syncthreads();
 }
 
@@ -150,9 +165,14 @@ __global__ void __launch_bounds__(256) k_census(PairBatch b, Params prm) {
 }
 
 // ---------------------------------------------------------------- FAST score
-// FAST-9 on the radius-3 Bresenham circle (Sec. III-A, [rosten2006machine]).
-__constant__ int8_t c_fast_dx[16] = {0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1};
-__constant__ int8_t c_fast_dy[16] = {-3, -3, -2, -1, 0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3};
+// FAST-9 on the radius-3 Bresenham circle (Sec. III-A, [rosten2006machine]),
+// same tiling as the census with a 3-pixel halo.
+// Circle offsets, folded to constants once the loop over i is unrolled.
+__device__ constexpr int fast_dx(int i) {
+    return i == 0 || i == 8 ? 0 : i == 1 || i == 7 ? 1 : i == 2 || i == 6 ? 2 : i >= 3 && i <= 5 ? 3
+         : i == 9 || i == 15 ? -1 : i == 10 || i == 14 ? -2 : -3;
+}
+__device__ constexpr int fast_dy(int i) { return fast_dx((i + 12) & 15); }  // the same circle a quarter turn on
 
 __device__ __forceinline__ bool has_run9(uint32_t m16) {
     uint32_t x = m16 | (m16 << 16);
@@ -163,30 +183,34 @@ __device__ __forceinline__ bool has_run9(uint32_t m16) {
 }
 
 __device__ __forceinline__ void fast_score_body(const PairDev& P, int local, const Params& prm) {
-    __shared__ uint8_t s[kTileH + 6][kTileW + 6];
+    __shared__ uint8_t s[kSeedRows + 6][kTileW + 6];
     const int W = P.W, H = P.H;
     const int tx_n = (W + kTileW - 1) / kTileW;
-    const int u0 = (local % tx_n) * kTileW, v0 = (local / tx_n) * kTileH;
-    for (int i = threadIdx.x; i < (kTileH + 6) * (kTileW + 6); i += blockDim.x) {
-        int r = i / (kTileW + 6), c = i % (kTileW + 6);
-        int v = min(max(v0 + r - 3, 0), H - 1), u = min(max(u0 + c - 3, 0), W - 1);
-        s[r][c] = P.L[(size_t)v * W + u];
-    }
+    const int u0 = (local % tx_n) * kTileW, v0 = (local / tx_n) * kSeedRows;
+    stage_tile<3>(s, P.L, W, H, u0, v0);
     __syncthreads();
-    const int lx = threadIdx.x % kTileW, ly = threadIdx.x / kTileW;
-    const int u = u0 + lx, v = v0 + ly;
-    if (u < W && v < H) {
+    const int lx = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int u = u0 + lx;
+    const int t = prm.t_fast;
+#pragma unroll
+    for (int k = 0; k < kSeedRows / 8; k++) {
+        const int ly = w + 8 * k, v = v0 + ly;
+        if (u >= W || v >= H) continue;
         int score = 0;
         if (u >= 3 && u < W - 3 && v >= 3 && v < H - 3) {
             const int p = s[ly + 3][lx + 3];
-            const int t = prm.t_fast;
             uint32_t mb = 0, md = 0;
             int sb = 0, sd = 0;
 #pragma unroll
             for (int i = 0; i < 16; i++) {
-                int q = s[ly + 3 + c_fast_dy[i]][lx + 3 + c_fast_dx[i]];
-                if (q > p + t) { mb |= 1u << i; sb += q - p - t; }
-                else if (q < p - t) { md |= 1u << i; sd += p - q - t; }
+                const int q = s[ly + 3 + fast_dy(i)][lx + 3 + fast_dx(i)];
+                if (q > p + t) {
+                    mb |= 1u << i;
+                    sb += q - p - t;
+                } else if (q < p - t) {
+                    md |= 1u << i;
+                    sd += p - q - t;
+                }
             }
             if (has_run9(mb) || has_run9(md)) score = sb > sd ? sb : sd;
         }
