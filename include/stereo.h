@@ -164,12 +164,14 @@ typedef struct {
 } stereo_stats;
 int stereo_get_stats(stereo_ctx* ctx, stereo_stats* out);
 
-/* The kernels' work shapes in use: the raster's small-triangle threshold
+/* No counterpart in the paper (the paper has one CPU thread and no kernels).
+ * The kernels' work shapes in use: the raster's small-triangle threshold
  * (bounding-box pixels; smaller boxes go to warp batches), the box pixels of
  * a warp batch, the column width of a large-triangle work item, and the
  * fused validate's blocks per SM and launch mode (1 = one launch for every
  * cell-side class).  With autotune, also the measured best times of the
- * synthetic round.  None of these change any result. */
+ * synthetic round.  None of these change any result.  Returns STEREO_OK, or
+ * STEREO_E_INVAL for a null argument; *out is caller-owned memory the call fills. */
 typedef struct {
     int small_area, batch_area, raster_cols;
     int validate_blocks_per_sm, validate_mixed;
