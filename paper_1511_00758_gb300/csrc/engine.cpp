@@ -119,14 +119,65 @@ private:
 };
 
 // ------------------------------------------------------------------ pinned host buffers
+// Pinned host buffers of finished requests, kept for the next ones: page-
+// locking memory is slow and freeing it can wait for the device, so requests
+// take their staging buffers from here (sizes rounded up to powers of two)
+// and give them back at release.  At most kKeep bytes stay idle.
+class PinnedPool {
+public:
+    static constexpr size_t kKeep = (size_t)2 << 30;
+    void* get(size_t bytes, size_t* cap) {
+        size_t want = 1 << 16;
+        while (want < bytes) want <<= 1;
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            auto it = free_.find(want);
+            if (it != free_.end()) {
+                void* p = it->second;
+                free_.erase(it);
+                idle_ -= want;
+                *cap = want;
+                return p;
+            }
+        }
+        void* p = nullptr;
+        if (cudaHostAlloc(&p, want, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        *cap = want;
+        return p;
+    }
+    void put(void* p, size_t cap) {
+        std::lock_guard<std::mutex> g(mu_);
+        if (idle_ + cap > kKeep) {
+            cudaFreeHost(p);
+            return;
+        }
+        free_.emplace(cap, p);
+        idle_ += cap;
+    }
+    ~PinnedPool() {
+        for (auto& kv : free_) cudaFreeHost(kv.second);
+    }
+
+private:
+    std::mutex mu_;
+    std::multimap<size_t, void*> free_;
+    size_t idle_ = 0;
+};
+
 struct Pinned {
     void* p = nullptr;
     size_t cap = 0;
+    PinnedPool* pool = nullptr;  // null: allocated and freed directly
     bool ensure(size_t bytes) {
         if (bytes <= cap) return true;
-        if (p) cudaFreeHost(p);
-        p = nullptr;
-        cap = 0;
+        free();
+        if (pool) {
+            p = pool->get(bytes, &cap);
+            return p != nullptr;
+        }
         size_t want = align_up(bytes + bytes / 4, 4096);
         if (cudaHostAlloc(&p, want, cudaHostAllocDefault) != cudaSuccess) {
             p = nullptr;
@@ -136,7 +187,10 @@ struct Pinned {
         return true;
     }
     void free() {
-        if (p) cudaFreeHost(p);
+        if (p) {
+            if (pool) pool->put(p, cap);
+            else cudaFreeHost(p);
+        }
         p = nullptr;
         cap = 0;
     }
@@ -289,6 +343,7 @@ private:
 }  // namespace
 
 struct stereo_ctx {
+    PinnedPool pinned;  // first member, destroyed last (after every request's buffers came back)
     stereo_config cfg{};
     Params prm{};
     int K = 4;
@@ -1295,6 +1350,7 @@ int stereo_submit(stereo_ctx* c, int stream_id, const uint8_t* left, const uint8
     if (!c || !left || !right || !ticket_out) return STEREO_E_INVAL;
     if (!valid_size(w, h) || dmax < 1 || dmax > 256 || iters < 1 || cell < 1) return STEREO_E_INVAL;
     Request* r = new Request();
+    r->in_host.pool = r->st_tri.pool = r->st_kp.pool = r->st_cells.pool = &c->pinned;
     r->stream_id = stream_id;
     r->W = w;
     r->H = h;
@@ -1309,17 +1365,21 @@ int stereo_submit(stereo_ctx* c, int stream_id, const uint8_t* left, const uint8
         return STEREO_E_NOMEM;
     }
     const size_t N = (size_t)w * h;
-    cudaPointerAttributes at{};
-    bool dev_in = cudaPointerGetAttributes(&at, left) == cudaSuccess &&
-                  (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+    cudaPointerAttributes at{}, at_r{};
+    const bool known = cudaPointerGetAttributes(&at, left) == cudaSuccess &&
+                       cudaPointerGetAttributes(&at_r, right) == cudaSuccess;
     cudaGetLastError();
+    const bool dev_in = known && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+    // page-locked host inputs are copied straight to the device (one DMA each),
+    // pageable ones through a pinned staging buffer
+    const bool pinned_in = known && !dev_in && at.type == cudaMemoryTypeHost && at_r.type == cudaMemoryTypeHost;
     std::unique_lock<std::mutex> g(c->mu);
     if ((int)c->queue.size() >= c->cfg.max_queue && (int)c->active.size() >= c->cfg.max_slots) {
         g.unlock();
         delete r;
         return STEREO_E_BUSY;
     }
-    if (dev_in) {
+    if (dev_in || pinned_in) {
         r->in_dev = (uint8_t*)c->arena.alloc(2 * N);
         if (!r->in_dev) {
             g.unlock();
@@ -1327,8 +1387,9 @@ int stereo_submit(stereo_ctx* c, int stream_id, const uint8_t* left, const uint8
             return STEREO_E_BUSY;
         }
         g.unlock();
-        cudaMemcpyAsync(r->in_dev, left, N, cudaMemcpyDeviceToDevice, c->copy_stream);
-        cudaMemcpyAsync(r->in_dev + N, right, N, cudaMemcpyDeviceToDevice, c->copy_stream);
+        const cudaMemcpyKind kind = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        cudaMemcpyAsync(r->in_dev, left, N, kind, c->copy_stream);
+        cudaMemcpyAsync(r->in_dev + N, right, N, kind, c->copy_stream);
         if (cudaStreamSynchronize(c->copy_stream) != cudaSuccess) {
             std::lock_guard<std::mutex> g2(c->mu);
             c->arena.release(r->in_dev);

@@ -374,6 +374,21 @@ def test_host_input_pointers(oracle_mod):
     _compare_run(oracle_mod, p, got)
 
 
+def test_pinned_host_input_pointers(oracle_mod):
+    """Page-locked host inputs take the direct-copy path; the caller may reuse
+    them as soon as submit returns."""
+    p = scenes.config_pairs("vga_polygons")[0]
+    left = torch.from_numpy(p.left.copy()).pin_memory()
+    right = torch.from_numpy(p.right.copy()).pin_memory()
+    with S.Context(mem_budget_bytes=1 << 28, **PRM) as ctx:
+        t = ctx.submit(left, right, 640, 480, p.dmax, p.iters, p.cell)
+        left.zero_()
+        right.zero_()  # overwritten right after submit: the request already holds its copy
+        got = ctx.result_tensors(ctx.poll(t))
+        ctx.release(t)
+    _compare_run(oracle_mod, p, got)
+
+
 def test_budget_errors():
     with S.Context(mem_budget_bytes=1 << 22, **PRM) as ctx:
         img = np.zeros((480, 640), np.uint8)
