@@ -18,6 +18,7 @@
 #include <deque>
 #include <functional>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -415,22 +416,24 @@ int mesh_step(Request& r) {
         D[i] = r.S[i].d;
     }
     const int cap = 2 * n + 8;
-    std::vector<int32_t> tri((size_t)3 * cap);
-    std::vector<int32_t> hull_v((size_t)4 * n + 4);
+    // scratch left uninitialised: every entry read below is written first
+    std::unique_ptr<int32_t[]> tri(new int32_t[(size_t)3 * cap]);
+    std::unique_ptr<int32_t[]> hull_v(new int32_t[(size_t)4 * n + 4]);
     int n_hull = 0;
-    int T = n >= 3 ? delaunay(P.data(), n, tri.data(), cap, hull_v.data(), &n_hull) : 0;
+    int T = n >= 3 ? delaunay(P.data(), n, tri.get(), cap, hull_v.get(), &n_hull) : 0;
     if (T < 0) return STEREO_E_INTERNAL;
-    std::vector<int32_t> tuv_v((size_t)6 * T), rows_v((size_t)T + 1), small_v((size_t)T + 1);
+    std::unique_ptr<int32_t[]> tuv_v(new int32_t[(size_t)6 * T + 1]), rows_v(new int32_t[(size_t)T + 1]),
+        small_v(new int32_t[(size_t)T + 1]);
     for (int t = 0; t < T; t++)
         for (int k = 0; k < 3; k++) {
             tuv_v[6 * t + 2 * k] = P[2 * tri[3 * t + k]];
             tuv_v[6 * t + 2 * k + 1] = P[2 * tri[3 * t + k] + 1];
         }
     int n_small = 0;
-    const int items = raster_lists(tuv_v.data(), T, r.W, r.H, rows_v.data(), small_v.data(), &n_small,
+    const int items = raster_lists(tuv_v.get(), T, r.W, r.H, rows_v.get(), small_v.get(), &n_small,
                                    r.tune.small_area, r.tune.raster_cols);
-    std::vector<int32_t> batch_v((size_t)n_small + 1);
-    const int n_batch = small_batches(tuv_v.data(), small_v.data(), n_small, r.W, r.H, batch_v.data(), r.tune.batch_area);
+    std::unique_ptr<int32_t[]> batch_v(new int32_t[(size_t)n_small + 1]);
+    const int n_batch = small_batches(tuv_v.get(), small_v.get(), n_small, r.W, r.H, batch_v.get(), r.tune.batch_area);
     if (!r.st_tri.ensure(tri_stage_bytes(T, items, n_small, n_hull, n_batch))) return STEREO_E_NOMEM;
     int32_t* hull = r.st_tri.as<int32_t>();
     for (int j = 0; j < n_hull; j++) {
@@ -444,12 +447,12 @@ int mesh_step(Request& r) {
     float* abc = (float*)(tuv + (size_t)6 * T);
     int32_t* rows = (int32_t*)(abc + (size_t)3 * T);
     int32_t* item_tri = rows + T + 1;
-    std::memcpy(tuv, tuv_v.data(), sizeof(int32_t) * 6 * (size_t)T);
-    std::memcpy(rows, rows_v.data(), sizeof(int32_t) * ((size_t)T + 1));
+    std::memcpy(tuv, tuv_v.get(), sizeof(int32_t) * 6 * (size_t)T);
+    std::memcpy(rows, rows_v.get(), sizeof(int32_t) * ((size_t)T + 1));
     raster_item_tri(rows, T, item_tri);
-    std::memcpy(item_tri + items, small_v.data(), sizeof(int32_t) * (size_t)n_small);
-    std::memcpy(item_tri + items + n_small, batch_v.data(), sizeof(int32_t) * ((size_t)n_batch + 1));
-    planes(P.data(), D.data(), tri.data(), T, abc);
+    std::memcpy(item_tri + items, small_v.get(), sizeof(int32_t) * (size_t)n_small);
+    std::memcpy(item_tri + items + n_small, batch_v.get(), sizeof(int32_t) * ((size_t)n_batch + 1));
+    planes(P.data(), D.data(), tri.get(), T, abc);
     r.T = T;
     r.raster_items = items;
     r.n_small = n_small;
@@ -497,6 +500,7 @@ int host_after_iter(Request& r) {
     const float* gd = (const float*)(gk + nc);
     const uint32_t* bk = gk + 2 * (size_t)nc;
     const int32_t* xd = (const int32_t*)(gk + 3 * (size_t)nc);
+    const size_t n_old = r.S.size();  // sorted by (v, u) since the previous pass
     std::vector<uint8_t> occ((size_t)r.W * r.H, 0);
     for (const auto& s : r.S) occ[(size_t)s.v * r.W + s.u] = 1;
     for (int c = 0; c < nc; c++) {
@@ -513,7 +517,10 @@ int host_after_iter(Request& r) {
         occ[p] = 1;
         r.S.push_back({(int32_t)(p % r.W), (int32_t)(p / r.W), (float)xd[c]});
     }
-    sort_support(r.S);
+    // the new points sorted, then merged into the sorted old ones (pixels are unique)
+    auto by_vu = [](const SupportPoint& a, const SupportPoint& b) { return a.v != b.v ? a.v < b.v : a.u < b.u; };
+    std::sort(r.S.begin() + n_old, r.S.end(), by_vu);
+    std::inplace_merge(r.S.begin(), r.S.begin() + n_old, r.S.end(), by_vu);
     r.it += 1;
     r.sz = std::max(1, r.sz / 2);
     return mesh_step(r);
