@@ -51,9 +51,9 @@ def build(force=False, verbose=False):
         "noalloc.o": [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", *inc,
                       "-c", os.path.join(CSRC, "noalloc.cu")],
         # the plane solve is a fixed fp64 expression: no contraction into FMAs
-        "mesh.o": ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", *inc,
+        "mesh.o": ["g++", "-O3", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", *inc,
                    "-c", os.path.join(CSRC, "mesh.cpp")],
-        "engine.o": ["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", *inc, "-c", os.path.join(CSRC, "engine.cpp")],
+        "engine.o": ["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", *inc, "-c", os.path.join(CSRC, "engine.cpp")],
     }
     procs = {}
     for obj, cmd in jobs.items():

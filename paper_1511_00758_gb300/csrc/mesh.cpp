@@ -5,7 +5,10 @@
 // Triangulation: Guibas-Stolfi divide and conquer on a quad-edge structure
 // (Guibas & Stolfi, ACM TOG 1985) with exact int64 predicates, cutting
 // alternately along u and v (Dwyer's alternating cuts) so subproblems stay
-// near square on wide images.  Cocircular
+// near square on wide images.  The points are sorted once in each cut's
+// order and every split partitions both lists stably, so no level sorts or
+// selects; quad edges live in 32-byte records and removed ones are reused,
+// which keeps the structure compact in cache.  Cocircular
 // ties resolve by symbolic perturbation of the lifted coordinate u^2 + v^2
 // (Edelsbrunner & Muecke 1990): a point of smaller canonical index (support
 // points sorted by (v, u)) carries a larger perturbation.  The perturbed
@@ -16,6 +19,8 @@
 // expression rounded to fp32, and contraction would change their bits.
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
+#include <memory>
 #include <utility>
 #include <vector>
 
@@ -24,20 +29,35 @@
 namespace stereo {
 namespace {
 
+// One quad edge: the onext links of its four directed edges (e = 4q + r;
+// r = 0, 2 primal, 1, 3 dual), the origins of the two primal ones, a
+// liveness flag and, once the mesh is built, which of the two primal
+// directions has the outer face on its left (bit r / 2); 32 bytes, so an
+// edge's whole record shares a cache line.
+struct alignas(32) Quad {
+    int32_t nx[4];
+    int32_t org[2];
+    int32_t dead;
+    int32_t outer;
+};
+
 struct Mesh {
-    const int32_t* P;            // (u, v) of canonical index i at P[2i], P[2i+1]
-    std::vector<int> nxt;        // onext of directed edge e (4 per quad edge)
-    std::vector<int> org;        // origin vertex of primal edges
-    std::vector<uint8_t> dead;   // per quad edge
+    const int32_t* P;  // (u, v) of canonical index i at P[2i], P[2i+1]
+    const uint32_t* key[2];  // per-frame order keys of the points (see reroot)
+    std::unique_ptr<Quad[]> q;
+    int nq = 0, cap = 0;
+    std::vector<int> freed;  // quad edges removed by a merge, reused first
 
     static int rot(int e) { return (e & ~3) | ((e + 1) & 3); }
     static int invrot(int e) { return (e & ~3) | ((e + 3) & 3); }
     static int sym(int e) { return e ^ 2; }
-    int onext(int e) const { return nxt[e]; }
-    int oprev(int e) const { return rot(nxt[rot(e)]); }
-    int lnext(int e) const { return rot(nxt[invrot(e)]); }
-    int rprev(int e) const { return nxt[sym(e)]; }
-    int dest(int e) const { return org[sym(e)]; }
+    int onext(int e) const { return q[e >> 2].nx[e & 3]; }
+    int& nref(int e) { return q[e >> 2].nx[e & 3]; }
+    int org(int e) const { return q[e >> 2].org[(e >> 1) & 1]; }
+    int dest(int e) const { return q[e >> 2].org[((e >> 1) & 1) ^ 1]; }
+    int oprev(int e) const { return rot(onext(rot(e))); }
+    int lnext(int e) const { return rot(onext(invrot(e))); }
+    int rprev(int e) const { return onext(sym(e)); }
 
     int64_t orient(int a, int b, int c) const {
         const int64_t ax = P[2 * a], ay = P[2 * a + 1];
@@ -65,8 +85,8 @@ struct Mesh {
         int id[4] = {a, b, c, d};
         for (int r = 0; r < 4; r++) {
             int k = 0;
-            for (int q = 1; q < 4; q++)
-                if (id[q] < id[k]) k = q;
+            for (int j = 1; j < 4; j++)
+                if (id[j] < id[k]) k = j;
             int64_t cof;
             switch (k) {
                 case 0: cof = orient(b, c, d); break;
@@ -80,32 +100,39 @@ struct Mesh {
         return false;
     }
 
-    int ne = 0;  // directed edges in use (4 per quad edge)
-
     int make_edge(int a, int b) {
-        const int e = ne;
-        ne += 4;
-        if ((size_t)ne > nxt.size()) {
-            nxt.resize(std::max<size_t>(2 * nxt.size(), 64));
-            org.resize(nxt.size(), -1);
-            dead.resize(nxt.size() / 4, 0);
+        int k;
+        if (!freed.empty()) {
+            k = freed.back();
+            freed.pop_back();
+        } else {
+            if (nq == cap) {
+                const int nc = std::max(2 * cap, 64);
+                std::unique_ptr<Quad[]> g(new Quad[nc]);
+                if (nq) std::memcpy(g.get(), q.get(), sizeof(Quad) * (size_t)nq);
+                q.swap(g);
+                cap = nc;
+            }
+            k = nq++;
         }
-        dead[e >> 2] = 0;
-        nxt[e] = e;
-        nxt[e + 1] = e + 3;
-        nxt[e + 2] = e + 2;
-        nxt[e + 3] = e + 1;
-        org[e] = a;
-        org[e + 2] = b;
+        Quad& Q = q[k];
+        const int e = 4 * k;
+        Q.nx[0] = e;
+        Q.nx[1] = e + 3;
+        Q.nx[2] = e + 2;
+        Q.nx[3] = e + 1;
+        Q.org[0] = a;
+        Q.org[1] = b;
+        Q.dead = 0;
         return e;
     }
     void splice(int a, int b) {
-        const int al = rot(nxt[a]), be = rot(nxt[b]);
-        std::swap(nxt[a], nxt[b]);
-        std::swap(nxt[al], nxt[be]);
+        const int al = rot(onext(a)), be = rot(onext(b));
+        std::swap(nref(a), nref(b));
+        std::swap(nref(al), nref(be));
     }
     int connect(int a, int b) {
-        const int e = make_edge(dest(a), org[b]);
+        const int e = make_edge(dest(a), org(b));
         splice(e, lnext(a));
         splice(sym(e), b);
         return e;
@@ -113,108 +140,131 @@ struct Mesh {
     void remove(int e) {
         splice(e, oprev(e));
         splice(sym(e), oprev(sym(e)));
-        dead[e >> 2] = 1;
+        q[e >> 2].dead = 1;
+        freed.push_back(e >> 2);
     }
-    bool rightof(int x, int e) const { return ccw(x, dest(e), org[e]); }
-    bool leftof(int x, int e) const { return ccw(x, org[e], dest(e)); }
+    bool rightof(int x, int e) const { return ccw(x, dest(e), org(e)); }
+    bool leftof(int x, int e) const { return ccw(x, org(e), dest(e)); }
 
-    // Order of frame f: frame 0 is (u, v) lexicographic; frame 1 is the
-    // frame rotated by -90 degrees, (v, -u) lexicographic.  A rotation keeps
-    // the orientation and in-circle signs, so the merge logic is the same in
-    // both frames; only "leftmost" and "rightmost" change.
-    bool less_f(int a, int b, int f) const {
-        const int au = P[2 * a], av = P[2 * a + 1], bu = P[2 * b], bv = P[2 * b + 1];
-        if (f == 0) return au != bu ? au < bu : av < bv;
-        return av != bv ? av < bv : au > bu;
-    }
-
+    // Frame 0 orders points by (u, v) lexicographically; frame 1 is the frame
+    // rotated by -90 degrees, (v, -u) lexicographic, as the key
+    // (v << 16) | (65535 - u).  A rotation keeps the orientation and
+    // in-circle signs, so the merge logic is the same in both frames; only
+    // "leftmost" and "rightmost" change.
+    //
     // Walk the hull from the clockwise hull edge e (outer face on its left)
     // and return, for frame f, the counter-clockwise hull edge out of the
     // minimum vertex and the clockwise hull edge out of the maximum vertex.
     std::pair<int, int> reroot(int e, int f) const {
-        int emin = e, emax = e;   // clockwise edges out of the extreme vertices
-        int pmin = e;             // clockwise edge into the minimum vertex
+        const uint32_t* K = key[f];
+        int emin = e, emax = e;
+        int pmin = e;
+        uint32_t kmin = K[org(e)], kmax = kmin;
         int prev = e, cur = lnext(e);
-        // one full turn around the outer face
         for (;;) {
-            const int v = org[cur];
-            if (less_f(v, org[emin], f)) { emin = cur; pmin = prev; }
-            if (less_f(org[emax], v, f)) emax = cur;
+            const uint32_t kv = K[org(cur)];
+            if (kv < kmin) {
+                kmin = kv;
+                emin = cur;
+                pmin = prev;
+            }
+            if (kv > kmax) {
+                kmax = kv;
+                emax = cur;
+            }
             if (cur == e) break;
             prev = cur;
             cur = lnext(cur);
         }
-        if (emin == e) {  // find the edge that enters org[e]
-            int q = e;
-            while (lnext(q) != e) q = lnext(q);
-            pmin = q;
+        if (emin == e) {  // find the edge that enters org(e)
+            int t = e;
+            while (lnext(t) != e) t = lnext(t);
+            pmin = t;
         }
         return {sym(pmin), emax};
     }
 
-    // s: n vertex ids (reordered in place).  Returns, in frame f, the
-    // counter-clockwise hull edge out of the minimum vertex and the clockwise
-    // hull edge out of the maximum vertex.  Cuts alternate between the two
-    // frames so the subproblems stay close to square.
-    std::pair<int, int> build(int* s, int n, int f) {
+    // s0, s1: the n vertex ids of this subproblem sorted in frame 0 and in
+    // frame 1; both are reordered in place so that the first child's ids
+    // come first, each part still sorted in both frames.  tmp: scratch for n
+    // ids; side: a per-vertex mark.  Returns, in frame f, the
+    // counter-clockwise hull edge out of the minimum vertex and the
+    // clockwise hull edge out of the maximum vertex.  Cuts alternate between
+    // the two frames so the subproblems stay close to square.
+    std::pair<int, int> build(int* s0, int* s1, int n, int f, int* tmp, uint8_t* side) {
+        int* sf = f == 0 ? s0 : s1;  // sorted in the cut frame
         if (n <= 3) {
-            std::sort(s, s + n, [this, f](int a, int b) { return less_f(a, b, f); });
             if (n == 2) {
-                const int a = make_edge(s[0], s[1]);
+                const int a = make_edge(sf[0], sf[1]);
                 return {a, sym(a)};
             }
-            const int a = make_edge(s[0], s[1]);
-            const int b = make_edge(s[1], s[2]);
+            const int a = make_edge(sf[0], sf[1]);
+            const int b = make_edge(sf[1], sf[2]);
             splice(sym(a), b);
-            if (ccw(s[0], s[1], s[2])) {
+            if (ccw(sf[0], sf[1], sf[2])) {
                 connect(b, a);
                 return {a, sym(b)};
             }
-            if (ccw(s[0], s[2], s[1])) {
+            if (ccw(sf[0], sf[2], sf[1])) {
                 const int c = connect(b, a);
                 return {sym(c), c};
             }
             return {a, sym(b)};
         }
         const int h = n / 2;
-        std::nth_element(s, s + h, s + n, [this, f](int a, int b) { return less_f(a, b, f); });
+        int* so = f == 0 ? s1 : s0;  // sorted in the other frame: split stably
+        for (int i = 0; i < h; i++) side[sf[i]] = 0;
+        for (int i = h; i < n; i++) side[sf[i]] = 1;
+        int nl = 0, nr = h;
+        for (int i = 0; i < n; i++) {
+            const int v = so[i];
+            if (side[v]) tmp[nr++] = v;
+            else tmp[nl++] = v;
+        }
+        std::memcpy(so, tmp, sizeof(int) * (size_t)n);
         const int g = 1 - f;
-        auto L = build(s, h, g);
-        auto R = build(s + h, n - h, g);
+        auto L = build(s0, s1, h, g, tmp, side);
+        auto R = build(s0 + h, s1 + h, n - h, g, tmp, side);
         // hull handles of the children in this frame
         auto Lf = reroot(L.second, f);
         auto Rf = reroot(R.second, f);
         int ldo = Lf.first, ldi = Lf.second, rdi = Rf.first, rdo = Rf.second;
         // lower common tangent
         for (;;) {
-            if (leftof(org[rdi], ldi)) ldi = lnext(ldi);
-            else if (rightof(org[ldi], rdi)) rdi = rprev(rdi);
+            if (leftof(org(rdi), ldi)) ldi = lnext(ldi);
+            else if (rightof(org(ldi), rdi)) rdi = rprev(rdi);
             else break;
         }
         int basel = connect(sym(rdi), ldi);
-        if (org[ldi] == org[ldo]) ldo = sym(basel);
-        if (org[rdi] == org[rdo]) rdo = basel;
+        if (org(ldi) == org(ldo)) ldo = sym(basel);
+        if (org(rdi) == org(rdo)) rdo = basel;
         // merge upwards
         for (;;) {
+            const int bo = org(basel), bd = dest(basel);
             int lc = onext(sym(basel));
-            if (rightof(dest(lc), basel)) {
-                while (incircle(dest(basel), org[basel], dest(lc), dest(onext(lc)))) {
-                    const int t = onext(lc);
+            bool lv = ccw(dest(lc), bd, bo);
+            if (lv) {
+                int lcn = onext(lc);
+                while (incircle(bd, bo, dest(lc), dest(lcn))) {
                     remove(lc);
-                    lc = t;
+                    lc = lcn;
+                    lcn = onext(lc);
                 }
+                lv = ccw(dest(lc), bd, bo);
             }
             int rc = oprev(basel);
-            if (rightof(dest(rc), basel)) {
-                while (incircle(dest(basel), org[basel], dest(rc), dest(oprev(rc)))) {
-                    const int t = oprev(rc);
+            bool rv = ccw(dest(rc), bd, bo);
+            if (rv) {
+                int rcp = oprev(rc);
+                while (incircle(bd, bo, dest(rc), dest(rcp))) {
                     remove(rc);
-                    rc = t;
+                    rc = rcp;
+                    rcp = oprev(rc);
                 }
+                rv = ccw(dest(rc), bd, bo);
             }
-            const bool lv = rightof(dest(lc), basel), rv = rightof(dest(rc), basel);
             if (!lv && !rv) break;
-            if (!lv || (rv && incircle(dest(lc), org[lc], org[rc], dest(rc))))
+            if (!lv || (rv && incircle(dest(lc), org(lc), org(rc), dest(rc))))
                 basel = connect(rc, sym(basel));
             else
                 basel = connect(sym(basel), sym(lc));
@@ -230,62 +280,106 @@ int delaunay(const int32_t* uv, int n, int32_t* tri, int cap) { return delaunay(
 int delaunay(const int32_t* uv, int n, int32_t* tri, int cap, int32_t* hull, int* n_hull) {
     if (n_hull) *n_hull = 0;
     if (n < 3) return 0;
+    std::unique_ptr<uint32_t[]> keys(new uint32_t[(size_t)2 * n]);
+    for (int i = 0; i < n; i++) {
+        const uint32_t u = (uint32_t)uv[2 * i], v = (uint32_t)uv[2 * i + 1];
+        keys[i] = (u << 16) | v;
+        keys[n + i] = (v << 16) | (0xFFFFu - u);
+    }
     Mesh m;
     m.P = uv;
-    m.nxt.resize((size_t)16 * n);  // about 3n quad edges survive; make_edge grows on demand
-    m.org.resize((size_t)16 * n, -1);
-    m.dead.resize((size_t)4 * n, 0);
-    std::vector<int> s(n);
-    for (int i = 0; i < n; i++) s[i] = i;
-    m.build(s.data(), n, 0);
-    // faces: each triangle once, from its directed edge leaving the smallest
-    // vertex; bucketed by that vertex, so the output order is lexicographic
-    // after sorting the (at most a few) triangles of each bucket
-    std::vector<int> first(n + 1, 0);
-    std::vector<int32_t> jk;
-    std::vector<int> owner;
-    jk.reserve((size_t)4 * n);
-    owner.reserve((size_t)2 * n);
-    const int ne = m.ne;
+    m.key[0] = keys.get();
+    m.key[1] = keys.get() + n;
+    m.cap = 3 * n + 16;
+    m.q.reset(new Quad[m.cap]);
+    m.freed.reserve(n);
+    // the vertex ids in both frames' orders: the input is in (v, u) order, so
+    // frame 1 (v ascending, u descending) reverses each row's run, and frame
+    // 0 (u, then v) is a stable counting sort of the input by u
+    std::unique_ptr<int[]> s0(new int[n]), s1(new int[n]), tmp(new int[n]);
+    std::unique_ptr<uint8_t[]> side(new uint8_t[n]);
+    for (int i = 0; i < n;) {
+        int j = i;
+        while (j < n && uv[2 * j + 1] == uv[2 * i + 1]) j++;
+        for (int k = i; k < j; k++) s1[k] = i + j - 1 - k;
+        i = j;
+    }
+    {
+        int umax = 0;
+        for (int i = 0; i < n; i++) umax = std::max(umax, (int)uv[2 * i]);
+        std::vector<int> cnt((size_t)umax + 2, 0);
+        for (int i = 0; i < n; i++) cnt[uv[2 * i] + 1]++;
+        for (int u = 0; u <= umax; u++) cnt[u + 1] += cnt[u];
+        for (int i = 0; i < n; i++) s0[cnt[uv[2 * i]]++] = i;
+    }
+    const int ldo = m.build(s0.get(), s1.get(), n, 0, tmp.get(), side.get()).first;
+    // the outer face, walked from the reverse of a hull edge: its edges are
+    // the hull edges (reported tail-first in the interior's orientation)
+    for (int k = 0; k < m.nq; k++) m.q[k].outer = 0;
     int nh = 0;
-    for (int e = 0; e < ne; e += 2) {
-        if (m.dead[e >> 2]) continue;
-        const int a = m.org[e], b = m.dest(e);
-        const int e2 = m.lnext(e);
-        const int c = m.dest(e2);
-        if (m.lnext(m.lnext(e2)) != e || !m.ccw(a, b, c)) {
-            // the left face is the outside: b -> a is a hull edge with its
-            // triangle on the left
+    {
+        const int e0 = Mesh::sym(ldo);
+        int e = e0;
+        do {
             if (hull && nh < 2 * n) {
-                hull[2 * nh] = b;
-                hull[2 * nh + 1] = a;
+                hull[2 * nh] = m.dest(e);
+                hull[2 * nh + 1] = m.org(e);
             }
             nh++;
-            continue;
-        }
-        if (!(a < b) || !(a < c)) continue;
-        owner.push_back(a);
-        jk.push_back(std::min(b, c));
-        jk.push_back(std::max(b, c));
-        first[a + 1]++;
+            m.q[e >> 2].outer |= 1 << ((e >> 1) & 1);
+            e = m.lnext(e);
+        } while (e != e0 && nh <= 4 * n);
     }
-    const int T = (int)owner.size();
+    // every other face is a triangle, found once from its directed edge
+    // leaving its smallest vertex (edges in memory order, so the loads of
+    // the third vertex are independent), then bucketed by that vertex and
+    // listed with the other two in increasing order: lexicographic output
+    std::unique_ptr<int[]> first(new int[(size_t)n + 1]);
+    std::fill(first.get(), first.get() + n + 1, 0);
+    std::vector<int32_t> own;
+    std::vector<uint64_t> bc;
+    own.reserve((size_t)2 * n + 8);
+    bc.reserve((size_t)2 * n + 8);
+    for (int k = 0; k < m.nq; k++) {
+        const Quad& Q = m.q[k];
+        if (Q.dead) continue;
+        for (int r = 0; r < 2; r++) {
+            if ((Q.outer >> r) & 1) continue;
+            const int a = Q.org[r], b = Q.org[r ^ 1];
+            if (b < a) continue;
+            const int c = m.dest(m.lnext(4 * k + 2 * r));
+            if (c < a) continue;
+            own.push_back(a);
+            bc.push_back(((uint64_t)(uint32_t)std::min(b, c) << 32) | (uint32_t)std::max(b, c));
+            first[a + 1]++;
+        }
+    }
+    const int T = (int)own.size();
     if (T > cap) return -9;  // STEREO_E_CAP
-    if (n_hull) *n_hull = (T > 0 && nh <= 2 * n) ? nh : 0;
     for (int i = 0; i < n; i++) first[i + 1] += first[i];
-    std::vector<int> pos(first.begin(), first.end() - 1);
-    std::vector<uint64_t> key(T);
-    for (int t = 0; t < T; t++) key[pos[owner[t]]++] = ((uint64_t)(uint32_t)jk[2 * t] << 32) | (uint32_t)jk[2 * t + 1];
+    std::unique_ptr<uint64_t[]> key(new uint64_t[(size_t)T + 1]);
+    {
+        std::unique_ptr<int[]> pos(new int[n]);
+        std::memcpy(pos.get(), first.get(), sizeof(int) * (size_t)n);
+        for (int t = 0; t < T; t++) key[pos[own[t]]++] = bc[t];
+    }
     for (int a = 0; a < n; a++) {
-        std::sort(key.begin() + first[a], key.begin() + first[a + 1]);
+        for (int i = first[a] + 1; i < first[a + 1]; i++) {  // insertion sort: a vertex owns few triangles
+            const uint64_t kk = key[i];
+            int j = i;
+            for (; j > first[a] && key[j - 1] > kk; j--) key[j] = key[j - 1];
+            key[j] = kk;
+        }
         for (int t = first[a]; t < first[a + 1]; t++) {
             tri[3 * t] = a;
             tri[3 * t + 1] = (int32_t)(key[t] >> 32);
             tri[3 * t + 2] = (int32_t)(key[t] & 0xFFFFFFFFu);
         }
     }
+    if (n_hull) *n_hull = (T > 0 && nh <= 2 * n) ? nh : 0;
     return T;
 }
+
 
 // Disparity plane d = a u + b v + c through the three vertices (Eq. 3), by
 // Cramer's rule in fp64 with the vertices in index order, rounded to fp32.
