@@ -94,7 +94,8 @@ typedef struct {
     const int32_t* n_tri;      /* host, iters entries: triangles of G(S_it) */
     const float* support;      /* host, (u, v, d) triples of S_1 .. S_iters concatenated */
     double latency_ms;         /* submit -> result ready, host clock */
-    double host_mesh_ms;       /* time spent in the host triangulation step */
+    double host_mesh_ms;       /* time spent in the host steps (support-set merge, triangulation,
+                                  planes, raster lists), summed over passes */
     int status;                /* STEREO_OK or the request's error */
 } stereo_result;
 
