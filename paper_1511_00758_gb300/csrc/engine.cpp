@@ -370,7 +370,9 @@ struct stereo_ctx {
     cudaEvent_t ev = nullptr;
     cudaStream_t copy_stream = nullptr;      // submit-time device copies (never captured)
     cudaStream_t capture_stream = nullptr;   // private stream the rounds are captured on
-    cudaGraphExec_t graph_exec = nullptr;    // the last round's executable graph
+    // executable graphs by round shape (bit 0: seed stage, bit 1: iteration
+    // stage), each updated in place by the next round of its shape
+    cudaGraphExec_t graph_exec[4] = {nullptr, nullptr, nullptr, nullptr};
     int* err_dev = nullptr;                  // set by a device-side wait that gave up
     Pinned err_host;
     bool bulk_validate = false;              // the bulk-copy validate kernel (else the plain one)
@@ -758,10 +760,11 @@ cudaError_t issue_outputs(stereo_ctx* c, Group& seed, Group& iter, cudaStream_t 
     return cudaSuccess;
 }
 
-// The kernels of one round, issued on stream s (captured into a graph).  The
-// same nodes every round: every kernel is launched, with one idle block when
-// its group has no work, and the fused validate a fixed number of times, so
-// the previous executable graph can always be updated in place.
+// The kernels of one round, issued on stream s (captured into a graph): the
+// seed stage's kernels when the seed group has requests, the iteration
+// stage's when the iteration group has.  For a given shape the nodes are the
+// same every round (the fused validate is launched a fixed number of times),
+// so the previous executable graph of that shape can be updated in place.
 cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, cudaStream_t s, size_t desc_bytes,
                          double seed_px, double cells_bytes, double raster_bytes, double validate_bytes) {
     CK(cudaMemcpyAsync(c->desc_dev, c->desc_host.p, desc_bytes, cudaMemcpyHostToDevice, s));
@@ -769,10 +772,16 @@ cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, 
     Params prm = c->prm;
     prm.err = c->err_dev;
     const int ns = (int)seed.reqs.size(), ni = (int)iter.reqs.size();
-    CKQ(Lr.run(STEREO_K_CENSUS, ns, seed_px * 10.125, [&] { return launch_census(batch_of(seed, WK_CENSUS), prm, s); }));
-    CKQ(Lr.run(STEREO_K_FAST_SCORE, ns, seed_px * 3.0, [&] { return launch_fast_score(batch_of(seed, WK_FAST_SCORE), prm, s); }));
-    CKQ(Lr.run(STEREO_K_FAST_BINS, ns, 0.0, [&] { return launch_fast_bins(batch_of(seed, WK_FAST_BINS), prm, s); }));
-    CKQ(Lr.run(STEREO_K_MATCH_KP, ns, 0.0, [&] { return launch_match_kp(batch_of(seed, WK_MATCH_KP), prm, s); }));
+    if (ns > 0) {
+        CKQ(Lr.run(STEREO_K_CENSUS, ns, seed_px * 10.125, [&] { return launch_census(batch_of(seed, WK_CENSUS), prm, s); }));
+        CKQ(Lr.run(STEREO_K_FAST_SCORE, ns, seed_px * 3.0, [&] { return launch_fast_score(batch_of(seed, WK_FAST_SCORE), prm, s); }));
+        CKQ(Lr.run(STEREO_K_FAST_BINS, ns, 0.0, [&] { return launch_fast_bins(batch_of(seed, WK_FAST_BINS), prm, s); }));
+        CKQ(Lr.run(STEREO_K_MATCH_KP, ns, 0.0, [&] { return launch_match_kp(batch_of(seed, WK_MATCH_KP), prm, s); }));
+    }
+    if (ni == 0) {
+        CK(cudaMemcpyAsync(c->err_host.p, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+        return cudaSuccess;
+    }
     CKQ(Lr.run(STEREO_K_FILL, ni, cells_bytes, [&] { return launch_fill_cells(batch_of(iter, WK_FILL), s); }));
     CKQ(Lr.run(STEREO_K_RASTER, ni, raster_bytes, [&] { return launch_raster(batch_of(iter, WK_RASTER), s); }));
     CKQ(Lr.run(STEREO_K_VALIDATE, ni, validate_bytes, [&] {
@@ -865,8 +874,10 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
     fill_group(iter, c->desc_host.as<char>() + bs, (char*)c->desc_dev + bs);
 
     // Timing events must exist before the capture that records them.  The
-    // last round's events are still referenced by the executable graph until
-    // this round's update replaces them, so they are recycled a round later.
+    // last round's events are still referenced by its executable graph until
+    // that graph has run, so they are recycled a round later; events are
+    // never destroyed while the context lives, and an executable graph is
+    // always updated with fresh events before it is launched again.
     if (c->cfg.profile)
         while (c->ev_pool.size() < 32) {
             cudaEvent_t ev = nullptr;
@@ -894,31 +905,32 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         Lr.timed.clear();
         return err;
     }
+    cudaGraphExec_t& exec = c->graph_exec[(seed.reqs.empty() ? 0 : 1) | (iter.reqs.empty() ? 0 : 2)];
     bool updated = false;
-    if (c->graph_exec) {
+    if (exec) {
         cudaGraphExecUpdateResultInfo info{};
-        updated = cudaGraphExecUpdate(c->graph_exec, graph, &info) == cudaSuccess;
+        updated = cudaGraphExecUpdate(exec, graph, &info) == cudaSuccess;
         if (!updated) {
             cudaGetLastError();
-            cudaGraphExecDestroy(c->graph_exec);
-            c->graph_exec = nullptr;
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
         }
     }
     if (!updated) {
-        err = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+        err = cudaGraphInstantiate(&exec, graph, 0);
         Lr.delta.graph_instantiations++;
     }
     cudaGraphDestroy(graph);
     if (err != cudaSuccess) {
         note_error(err, "cudaGraphInstantiate", __LINE__);
-        c->graph_exec = nullptr;
+        exec = nullptr;
         Lr.timed.clear();
         return err;
     }
     const double tx0 = now_ms();
     Lr.delta.graph_ms += tx0 - tg0;
     CK(issue_inputs(iter, s));
-    CK(cudaGraphLaunch(c->graph_exec, s));
+    CK(cudaGraphLaunch(exec, s));
     CK(issue_outputs(c, seed, iter, s));
     CK(cudaEventRecord(c->ev, s));
     CK(cudaEventSynchronize(c->ev));
@@ -1555,7 +1567,8 @@ void stereo_destroy(stereo_ctx* c) {
     c->desc_host.free();
     if (c->desc_dev) cudaFree(c->desc_dev);
     if (c->own_arena) cudaFree(c->arena_base);
-    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    for (cudaGraphExec_t g : c->graph_exec)
+        if (g) cudaGraphExecDestroy(g);
     if (c->err_dev) cudaFree(c->err_dev);
     c->err_host.free();
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
