@@ -226,6 +226,14 @@ int stereo_epipolar_match(const uint32_t* cL, const uint32_t* cR, int w, int h,
  * error (STEREO_E_CAP when cap is too small; 2n suffices). */
 int stereo_delaunay(const int32_t* uv, int n, int32_t* tri, int cap);
 
+/* stereo_delaunay with the top levels of the divide and conquer on up to
+ * `threads` host threads (1, 2, 4 or 8; other counts round down; the halves
+ * of a split below 2048 points stay on one thread).  Same arguments, result
+ * and errors as stereo_delaunay: the splits and merges are the same, only
+ * their threads differ.  The engine uses the same routine with its idle host
+ * workers at the end of a burst. */
+int stereo_delaunay_parallel(const int32_t* uv, int n, int32_t* tri, int cap, int threads);
+
 /* Disparity plane d = a*u + b*v + c per triangle (Eq. 3, "solving a linear
  * system"; host, synchronous): Cramer's rule in fp64 over the vertices in
  * index order, rounded to fp32.  d: n fp32 support disparities; abc: 3*T. */

@@ -14,7 +14,7 @@ from . import _build
 
 __all__ = [
     "StereoError", "load", "lib", "Config", "Result", "Stats", "Tuning", "Context",
-    "census", "fast", "epipolar_match", "delaunay", "planes", "raster_scratch_bytes", "raster", "raster_noalloc", "validate_bulk",
+    "census", "fast", "epipolar_match", "delaunay", "delaunay_parallel", "planes", "raster_scratch_bytes", "raster", "raster_noalloc", "validate_bulk",
     "validate", "resample_match", "ERRORS",
 ]
 
@@ -82,6 +82,7 @@ _SIGS = {
     "stereo_fast": (_I, [_P, _I, _I, _I, _I, _P, _P, _P]),
     "stereo_epipolar_match": (_I, [_P, _P, _I, _I, _P, _I, _I, _I, _I, _P, _P]),
     "stereo_delaunay": (_I, [_P, _I, _P, _I]),
+    "stereo_delaunay_parallel": (_I, [_P, _I, _P, _I, _I]),
     "stereo_planes": (_I, [_P, _P, _P, _I, _P]),
     "stereo_raster_scratch_bytes": (ctypes.c_size_t, [_I]),
     "stereo_raster": (_I, [_P, _P, _I, _I, _I, _P, _P, _P, ctypes.c_size_t, _P]),
@@ -163,6 +164,11 @@ def epipolar_match(cL, cR, w, h, q_uv, n, dmax, t_lo, margin, out_d, stream=None
 def delaunay(uv, n, tri, cap):
     """Host call: uv, tri are host (numpy) buffers.  Returns the triangle count."""
     return _check(lib().stereo_delaunay(_ptr(uv), n, _ptr(tri), cap), "delaunay")
+
+
+def delaunay_parallel(uv, n, tri, cap, threads):
+    """Host call, as delaunay, with the top splits on up to `threads` host threads."""
+    return _check(lib().stereo_delaunay_parallel(_ptr(uv), n, _ptr(tri), cap, threads), "delaunay_parallel")
 
 
 def planes(uv, d, tri, T, abc):

@@ -247,6 +247,7 @@ struct Request {
     Pinned st_kp;             // kp_uv + kp_d
     Pinned st_cells;          // cg_key, cg_d, cb_key, x_d
     bool resample_now = false;
+    class Pool* pool = nullptr;  // the context's host workers (idle ones help triangulate)
 };
 
 size_t block_bytes(const Request& r, int K) {
@@ -310,6 +311,8 @@ public:
         }
         cv_.notify_one();
     }
+    // Workers waiting for a task (a hint: it may change at once).
+    int idle() const { return idle_.load(std::memory_order_relaxed); }
     void stop() {
         {
             std::lock_guard<std::mutex> g(mu_);
@@ -326,7 +329,9 @@ private:
             std::function<void()> f;
             {
                 std::unique_lock<std::mutex> g(mu_);
+                idle_++;
                 cv_.wait(g, [this] { return stop_ || !q_.empty(); });
+                idle_--;
                 if (q_.empty()) return;
                 f = std::move(q_.front());
                 q_.pop_front();
@@ -338,6 +343,7 @@ private:
     std::condition_variable cv_;
     std::deque<std::function<void()>> q_;
     std::vector<std::thread> th_;
+    std::atomic<int> idle_{0};
     bool stop_ = false;
 };
 
@@ -421,10 +427,16 @@ int mesh_step(Request& r) {
     std::unique_ptr<int32_t[]> tri(new int32_t[(size_t)3 * cap]);
     std::unique_ptr<int32_t[]> hull_v(new int32_t[(size_t)4 * n + 4]);
     int n_hull = 0;
-    int T = n >= 3 ? delaunay(P.data(), n, tri.get(), cap, hull_v.get(), &n_hull) : 0;
+    // workers with nothing to do (the end of a burst) take halves of a large
+    // triangulation: one idle worker, the top split; three or more, the top two
+    const int idle = r.pool ? r.pool->idle() : 0;
+    const int depth = n < 4096 || idle == 0 ? 0 : idle >= 3 ? 2 : 1;
+    Pool* pool = r.pool;
+    const Spawn spawn = [pool](std::function<void()> f) { pool->push(std::move(f)); };
+    int T = n >= 3 ? delaunay(P.data(), n, tri.get(), cap, hull_v.get(), &n_hull, depth, depth ? &spawn : nullptr) : 0;
     if (T < 0) return STEREO_E_INTERNAL;
     std::unique_ptr<int32_t[]> tuv_v(new int32_t[(size_t)6 * T + 1]), rows_v(new int32_t[(size_t)T + 1]),
-        small_v(new int32_t[(size_t)T + 1]);
+        small_v(new int32_t[(size_t)T + 1]), box_v(new int32_t[(size_t)T + 1]);
     for (int t = 0; t < T; t++)
         for (int k = 0; k < 3; k++) {
             tuv_v[6 * t + 2 * k] = P[2 * tri[3 * t + k]];
@@ -432,9 +444,9 @@ int mesh_step(Request& r) {
         }
     int n_small = 0;
     const int items = raster_lists(tuv_v.get(), T, r.W, r.H, rows_v.get(), small_v.get(), &n_small,
-                                   r.tune.small_area, r.tune.raster_cols);
+                                   r.tune.small_area, r.tune.raster_cols, box_v.get());
     std::unique_ptr<int32_t[]> batch_v(new int32_t[(size_t)n_small + 1]);
-    const int n_batch = small_batches(tuv_v.get(), small_v.get(), n_small, r.W, r.H, batch_v.get(), r.tune.batch_area);
+    const int n_batch = small_batches(box_v.get(), n_small, batch_v.get(), r.tune.batch_area);
     if (!r.st_tri.ensure(tri_stage_bytes(T, items, n_small, n_hull, n_batch))) return STEREO_E_NOMEM;
     int32_t* hull = r.st_tri.as<int32_t>();
     for (int j = 0; j < n_hull; j++) {
@@ -1144,15 +1156,15 @@ cudaError_t autotune(stereo_ctx* c) {
 
     // raster: every (small-triangle threshold, batch area, item width)
     const int kSmall[] = {128, 256, 512}, kBatch[] = {512, 1024, 2048}, kCols[] = {64, 128, 256};
-    std::vector<int32_t> rows((size_t)T + 1), small((size_t)T + 1), batch((size_t)T + 2);
+    std::vector<int32_t> rows((size_t)T + 1), small((size_t)T + 1), box((size_t)T + 1), batch((size_t)T + 2);
     std::vector<char> blob;
     char* blob_dev = nullptr;
     size_t blob_cap = 0;
     std::vector<PairDev> pd(NP);
     auto stage = [&](int sa, int ba, int cols) -> cudaError_t {  // host lists + upload + descriptors
         int n_small = 0;
-        const int items = raster_lists(tuv.data(), T, W, H, rows.data(), small.data(), &n_small, sa, cols);
-        const int n_batch = small_batches(tuv.data(), small.data(), n_small, W, H, batch.data(), ba);
+        const int items = raster_lists(tuv.data(), T, W, H, rows.data(), small.data(), &n_small, sa, cols, box.data());
+        const int n_batch = small_batches(box.data(), n_small, batch.data(), ba);
         const size_t bytes = tri_stage_bytes(T, items, n_small, n_hull, n_batch);
         blob.assign(bytes, 0);
         char* q = blob.data();
@@ -1407,6 +1419,7 @@ int stereo_submit(stereo_ctx* c, int stream_id, const uint8_t* left, const uint8
     if (!valid_size(w, h) || dmax < 1 || dmax > 256 || iters < 1 || cell < 1) return STEREO_E_INVAL;
     Request* r = new Request();
     r->in_host.pool = r->st_tri.pool = r->st_kp.pool = r->st_cells.pool = &c->pinned;
+    r->pool = &c->pool;
     r->stream_id = stream_id;
     r->W = w;
     r->H = h;
@@ -1633,7 +1646,8 @@ int stereo_epipolar_match(const uint32_t* cL, const uint32_t* cR, int w, int h, 
     return to_rc(launch_match_list(cL, cR, w, h, q_uv, n, dmax, prm, out_d, (cudaStream_t)stream));
 }
 
-int stereo_delaunay(const int32_t* uv, int n, int32_t* tri, int cap) {
+namespace {
+int check_canonical(const int32_t* uv, int n, int32_t* tri, int cap) {
     if (n < 0 || (n > 0 && !uv) || cap < 0 || (cap > 0 && !tri)) return STEREO_E_INVAL;
     for (int i = 0; i < n; i++) {
         if (uv[2 * i] < 0 || uv[2 * i + 1] < 0 || uv[2 * i] > 16383 || uv[2 * i + 1] > 16383) return STEREO_E_INVAL;
@@ -1642,8 +1656,36 @@ int stereo_delaunay(const int32_t* uv, int n, int32_t* tri, int cap) {
             if (b < a || (b == a && uv[2 * i] <= uv[2 * i - 2])) return STEREO_E_INVAL;  // not canonical
         }
     }
-    return delaunay(uv, n, tri, cap);
+    return STEREO_OK;
 }
+}  // namespace
+
+int stereo_delaunay(const int32_t* uv, int n, int32_t* tri, int cap) {
+    const int rc = check_canonical(uv, n, tri, cap);
+    return rc != STEREO_OK ? rc : delaunay(uv, n, tri, cap);
+}
+
+int stereo_delaunay_parallel(const int32_t* uv, int n, int32_t* tri, int cap, int threads) {
+    const int rc = check_canonical(uv, n, tri, cap);
+    if (rc != STEREO_OK) return rc;
+    if (threads < 1) return STEREO_E_INVAL;
+    const int depth = threads >= 8 ? 3 : threads >= 4 ? 2 : threads >= 2 ? 1 : 0;
+    std::mutex mu;
+    std::vector<std::thread> helpers;  // joined before returning
+    const Spawn spawn = [&](std::function<void()> f) {
+        std::lock_guard<std::mutex> g(mu);
+        helpers.emplace_back(std::move(f));
+    };
+    int T;
+    try {
+        T = delaunay(uv, n, tri, cap, nullptr, nullptr, depth, depth ? &spawn : nullptr);
+    } catch (...) {  // a helper thread or an allocation refused
+        T = STEREO_E_NOMEM;
+    }
+    for (auto& t : helpers) t.join();
+    return T;
+}
+
 
 int stereo_planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float* abc) {
     if (T < 0 || (T > 0 && (!uv || !d || !tri || !abc))) return STEREO_E_INVAL;

@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 
 #include <cuda_runtime.h>
 
@@ -129,18 +130,25 @@ int delaunay(const int32_t* uv, int n, int32_t* tri, int cap);
 // Also returns the directed hull edges (org, dest vertex index pairs, the
 // triangles on the left as in a positively oriented triangle) in hull[2 * n]
 // and their count in *n_hull (0 when there is no triangle).
-int delaunay(const int32_t* uv, int n, int32_t* tri, int cap, int32_t* hull, int* n_hull);
+// depth > 0 with spawn: the top `depth` levels of the divide and conquer
+// (at most 3) fork, the lower half of each split offered to spawn, which runs
+// the function it is given on another thread or not at all (the caller then
+// runs it itself); the result is the same.
+using Spawn = std::function<void(std::function<void()>)>;
+int delaunay(const int32_t* uv, int n, int32_t* tri, int cap, int32_t* hull, int* n_hull, int depth = 0,
+             const Spawn* spawn = nullptr);
 void planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float* abc);
 // Raster work lists of a mesh: small[] the triangles whose clipped bounding
-// box has at most kSmallArea pixels (returns their count in *n_small); rows[T + 1]
-// the exclusive prefix of the 8x128 work items of the others (returns the total).
+// box has at most kSmallArea pixels (returns their count in *n_small), and,
+// when small_box is given, each one's box area (at least 1) in the same
+// order; rows[T + 1] the exclusive prefix of the 8x128 work items of the
+// others (returns the total).
 int raster_lists(const int32_t* tri_uv, int T, int W, int H, int32_t* rows, int32_t* small, int* n_small,
-                 int small_area = kSmallArea, int cols = kRasterCols);
-// Warp batches of the (sorted) small list: consecutive runs of at most 32
-// triangles and kBatchArea box pixels (a single larger box runs alone);
-// batch[0..n] are their starts plus n_small; returns n.
-int small_batches(const int32_t* tri_uv, const int32_t* small, int n_small, int W, int H, int32_t* batch,
-                  int batch_area = kBatchArea);
+                 int small_area = kSmallArea, int cols = kRasterCols, int32_t* small_box = nullptr);
+// Warp batches of the (sorted) small list, from its box areas: consecutive
+// runs of at most 32 triangles and kBatchArea box pixels (a single larger box
+// runs alone); batch[0..n] are their starts plus n_small; returns n.
+int small_batches(const int32_t* small_box, int n_small, int32_t* batch, int batch_area = kBatchArea);
 // Triangle of every large-triangle work item (items = rows[T] entries).
 void raster_item_tri(const int32_t* rows, int T, int32_t* item_tri);
 

@@ -18,9 +18,13 @@
 // Compiled with -ffp-contract=off: the plane coefficients are a fixed fp64
 // expression rounded to fp32, and contraction would change their bits.
 #include <algorithm>
+#include <atomic>
+#include <condition_variable>
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <memory>
+#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -41,11 +45,20 @@ struct alignas(32) Quad {
     int32_t outer;
 };
 
+// One builder of a triangulation.  The quad records are shared by every
+// builder of the same triangulation; each builder hands out fresh records
+// from its own range [lo, hi) (so that two halves can be built at the same
+// time) and reuses the records it removed first.  The mesh is a planar
+// subdivision at every step, so a builder over m points never holds more than
+// 3m - 3 live edges, and a range of 3m + 16 records cannot run out; a builder
+// that owns the whole array (grow = true) still grows it if it ever did.
 struct Mesh {
     const int32_t* P;  // (u, v) of canonical index i at P[2i], P[2i+1]
     const uint32_t* key[2];  // per-frame order keys of the points (see reroot)
-    std::unique_ptr<Quad[]> q;
-    int nq = 0, cap = 0;
+    Quad* q = nullptr;
+    std::unique_ptr<Quad[]>* store = nullptr;  // the owning array, when this builder may grow it
+    int lo = 0, nq = 0, hi = 0;                // fresh records [lo, nq) handed out, up to hi
+    bool overflow = false;
     std::vector<int> freed;  // quad edges removed by a merge, reused first
 
     static int rot(int e) { return (e & ~3) | ((e + 1) & 3); }
@@ -106,12 +119,18 @@ struct Mesh {
             k = freed.back();
             freed.pop_back();
         } else {
-            if (nq == cap) {
-                const int nc = std::max(2 * cap, 64);
-                std::unique_ptr<Quad[]> g(new Quad[nc]);
-                if (nq) std::memcpy(g.get(), q.get(), sizeof(Quad) * (size_t)nq);
-                q.swap(g);
-                cap = nc;
+            if (nq == hi) {
+                if (store && lo == 0) {
+                    const int nc = std::max(2 * hi, 64);
+                    std::unique_ptr<Quad[]> g(new Quad[nc]);
+                    if (nq) std::memcpy(g.get(), q, sizeof(Quad) * (size_t)nq);
+                    store->swap(g);
+                    q = store->get();
+                    hi = nc;
+                } else {  // unreachable (see above); keeps every access in bounds
+                    overflow = true;
+                    nq = hi - 1;
+                }
             }
             k = nq++;
         }
@@ -211,7 +230,18 @@ struct Mesh {
             }
             return {a, sym(b)};
         }
+        const int h = split(s0, s1, n, f, tmp, side);
+        const auto L = build(s0, s1, h, 1 - f, tmp, side);
+        const auto R = build(s0 + h, s1 + h, n - h, 1 - f, tmp, side);
+        return merge(L, R, f);
+    }
+
+    // Splits a subproblem of n > 3 ids at the median of frame f: the first h
+    // = n / 2 ids of both lists become the lower half, each part still sorted
+    // in both frames.  Returns h.
+    static int split(int* s0, int* s1, int n, int f, int* tmp, uint8_t* side) {
         const int h = n / 2;
+        int* sf = f == 0 ? s0 : s1;  // sorted in the cut frame
         int* so = f == 0 ? s1 : s0;  // sorted in the other frame: split stably
         for (int i = 0; i < h; i++) side[sf[i]] = 0;
         for (int i = h; i < n; i++) side[sf[i]] = 1;
@@ -222,9 +252,13 @@ struct Mesh {
             else tmp[nl++] = v;
         }
         std::memcpy(so, tmp, sizeof(int) * (size_t)n);
-        const int g = 1 - f;
-        auto L = build(s0, s1, h, g, tmp, side);
-        auto R = build(s0 + h, s1 + h, n - h, g, tmp, side);
+        return h;
+    }
+
+    // Merges the triangulations of the lower (L) and upper (R) halves of a
+    // frame-f split, given by their children's hull handles (in the
+    // children's frame), and returns the merged hull handles in frame f.
+    std::pair<int, int> merge(std::pair<int, int> L, std::pair<int, int> R, int f) {
         // hull handles of the children in this frame
         auto Lf = reroot(L.second, f);
         auto Rf = reroot(R.second, f);
@@ -273,26 +307,117 @@ struct Mesh {
     }
 };
 
+// Every builder of one triangulation: the shared quad records and a bump
+// allocator that gives each builder a range of its own.
+struct Builders {
+    const int32_t* P;
+    const uint32_t* key[2];
+    std::unique_ptr<Quad[]> store;
+    int total = 0;
+    std::atomic<int> next{0};
+    std::mutex mu;
+    std::vector<std::unique_ptr<Mesh>> all;
+
+    // A builder for a subproblem of m points (grow: it is the only one).
+    Mesh* make(int m, bool grow) {
+        std::unique_ptr<Mesh> b(new Mesh);
+        b->P = P;
+        b->key[0] = key[0];
+        b->key[1] = key[1];
+        b->q = store.get();
+        const int len = 3 * m + 16;
+        b->lo = b->nq = next.fetch_add(len);
+        b->hi = std::min(total, b->lo + len);
+        if (grow) b->store = &store;
+        Mesh* out = b.get();
+        std::lock_guard<std::mutex> g(mu);
+        all.push_back(std::move(b));
+        return out;
+    }
+};
+
+// Runs a() on this thread and b() on this thread or on a helper started by
+// spawn, and returns when both have finished.  Whichever thread claims b
+// first runs it, so nothing waits for a helper that never starts.
+void fork_join(const Spawn& spawn, const std::function<void()>& a, const std::function<void()>& b) {
+    struct Job {
+        std::atomic<bool> claimed{false};
+        std::mutex mu;
+        std::condition_variable cv;
+        bool done = false;
+        const std::function<void()>* run = nullptr;
+    };
+    auto job = std::make_shared<Job>();
+    job->run = &b;
+    spawn([job] {
+        if (job->claimed.exchange(true)) return;
+        (*job->run)();
+        {
+            std::lock_guard<std::mutex> g(job->mu);
+            job->done = true;
+        }
+        job->cv.notify_all();
+    });
+    a();
+    if (!job->claimed.exchange(true)) {
+        b();
+        return;
+    }
+    std::unique_lock<std::mutex> g(job->mu);
+    job->cv.wait(g, [&] { return job->done; });
+}
+
+constexpr int kParallelMin = 2048;  // smallest subproblem worth a second thread
+
+// The divide and conquer, its top `depth` levels forked (the lower half of
+// each split on a helper when spawn finds one); *out receives the builder of
+// the top merge.  The result is the same as a single-threaded build: the same
+// splits and merges, only the quad records differ.
+std::pair<int, int> build_parallel(Builders& B, Mesh** out, int* s0, int* s1, int n, int f, int* tmp, uint8_t* side,
+                                   int depth, const Spawn& spawn) {
+    if (depth <= 0 || n < kParallelMin) {
+        Mesh* m = B.make(n, false);
+        *out = m;
+        return m->build(s0, s1, n, f, tmp, side);
+    }
+    const int h = Mesh::split(s0, s1, n, f, tmp, side);
+    Mesh *ml = nullptr, *mr = nullptr;
+    std::pair<int, int> L, R;
+    fork_join(
+        spawn, [&] { R = build_parallel(B, &mr, s0 + h, s1 + h, n - h, 1 - f, tmp + h, side, depth - 1, spawn); },
+        [&] { L = build_parallel(B, &ml, s0, s1, h, 1 - f, tmp, side, depth - 1, spawn); });
+    Mesh* m = B.make(n, false);  // reuses the halves' removed records first
+    m->freed.swap(ml->freed);
+    m->freed.insert(m->freed.end(), mr->freed.begin(), mr->freed.end());
+    mr->freed.clear();
+    *out = m;
+    return m->merge(L, R, f);
+}
+
 }  // namespace
 
 int delaunay(const int32_t* uv, int n, int32_t* tri, int cap) { return delaunay(uv, n, tri, cap, nullptr, nullptr); }
 
-int delaunay(const int32_t* uv, int n, int32_t* tri, int cap, int32_t* hull, int* n_hull) {
+int delaunay(const int32_t* uv, int n, int32_t* tri, int cap, int32_t* hull, int* n_hull, int depth,
+             const Spawn* spawn) {
     if (n_hull) *n_hull = 0;
     if (n < 3) return 0;
+    if (!spawn) depth = 0;
+    depth = std::max(0, std::min(depth, 3));
     std::unique_ptr<uint32_t[]> keys(new uint32_t[(size_t)2 * n]);
     for (int i = 0; i < n; i++) {
         const uint32_t u = (uint32_t)uv[2 * i], v = (uint32_t)uv[2 * i + 1];
         keys[i] = (u << 16) | v;
         keys[n + i] = (v << 16) | (0xFFFFu - u);
     }
-    Mesh m;
-    m.P = uv;
-    m.key[0] = keys.get();
-    m.key[1] = keys.get() + n;
-    m.cap = 3 * n + 16;
-    m.q.reset(new Quad[m.cap]);
-    m.freed.reserve(n);
+    Builders B;
+    B.P = uv;
+    B.key[0] = keys.get();
+    B.key[1] = keys.get() + n;
+    // one range of 3m + 16 per builder: the leaves of the forked levels cover
+    // n points, and so do the merges of each forked level
+    B.total = (depth + 1) * (3 * n + 16) + 16 * (2 << depth);
+    B.store.reset(new Quad[B.total]);
     // the vertex ids in both frames' orders: the input is in (v, u) order, so
     // frame 1 (v ascending, u descending) reverses each row's run, and frame
     // 0 (u, then v) is a stable counting sort of the input by u
@@ -312,10 +437,22 @@ int delaunay(const int32_t* uv, int n, int32_t* tri, int cap, int32_t* hull, int
         for (int u = 0; u <= umax; u++) cnt[u + 1] += cnt[u];
         for (int i = 0; i < n; i++) s0[cnt[uv[2 * i]]++] = i;
     }
-    const int ldo = m.build(s0.get(), s1.get(), n, 0, tmp.get(), side.get()).first;
+    Mesh* top = nullptr;
+    int ldo;
+    if (depth == 0) {
+        top = B.make(n, true);
+        ldo = top->build(s0.get(), s1.get(), n, 0, tmp.get(), side.get()).first;
+    } else {
+        ldo = build_parallel(B, &top, s0.get(), s1.get(), n, 0, tmp.get(), side.get(), depth, *spawn).first;
+    }
+    for (const auto& b : B.all)
+        if (b->overflow) return -10;  // unreachable: a range outgrown
+    const Mesh& m = *top;
+    Quad* const q = top->q;  // the top builder sees the array after any growth
+    for (const auto& b : B.all)
+        for (int k = b->lo; k < b->nq; k++) q[k].outer = 0;
     // the outer face, walked from the reverse of a hull edge: its edges are
     // the hull edges (reported tail-first in the interior's orientation)
-    for (int k = 0; k < m.nq; k++) m.q[k].outer = 0;
     int nh = 0;
     {
         const int e0 = Mesh::sym(ldo);
@@ -326,7 +463,7 @@ int delaunay(const int32_t* uv, int n, int32_t* tri, int cap, int32_t* hull, int
                 hull[2 * nh + 1] = m.org(e);
             }
             nh++;
-            m.q[e >> 2].outer |= 1 << ((e >> 1) & 1);
+            q[e >> 2].outer |= 1 << ((e >> 1) & 1);
             e = m.lnext(e);
         } while (e != e0 && nh <= 4 * n);
     }
@@ -340,20 +477,21 @@ int delaunay(const int32_t* uv, int n, int32_t* tri, int cap, int32_t* hull, int
     std::vector<uint64_t> bc;
     own.reserve((size_t)2 * n + 8);
     bc.reserve((size_t)2 * n + 8);
-    for (int k = 0; k < m.nq; k++) {
-        const Quad& Q = m.q[k];
-        if (Q.dead) continue;
-        for (int r = 0; r < 2; r++) {
-            if ((Q.outer >> r) & 1) continue;
-            const int a = Q.org[r], b = Q.org[r ^ 1];
-            if (b < a) continue;
-            const int c = m.dest(m.lnext(4 * k + 2 * r));
-            if (c < a) continue;
-            own.push_back(a);
-            bc.push_back(((uint64_t)(uint32_t)std::min(b, c) << 32) | (uint32_t)std::max(b, c));
-            first[a + 1]++;
+    for (const auto& bl : B.all)
+        for (int k = bl->lo; k < bl->nq; k++) {
+            const Quad& Q = q[k];
+            if (Q.dead) continue;
+            for (int r = 0; r < 2; r++) {
+                if ((Q.outer >> r) & 1) continue;
+                const int a = Q.org[r], b = Q.org[r ^ 1];
+                if (b < a) continue;
+                const int c = m.dest(m.lnext(4 * k + 2 * r));
+                if (c < a) continue;
+                own.push_back(a);
+                bc.push_back(((uint64_t)(uint32_t)std::min(b, c) << 32) | (uint32_t)std::max(b, c));
+                first[a + 1]++;
+            }
         }
-    }
     const int T = (int)own.size();
     if (T > cap) return -9;  // STEREO_E_CAP
     for (int i = 0; i < n; i++) first[i + 1] += first[i];
@@ -405,13 +543,13 @@ void planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float*
 }
 
 int raster_lists(const int32_t* q, int T, int W, int H, int32_t* rows, int32_t* small, int* n_small, int small_area,
-                 int cols) {
+                 int cols, int32_t* small_box) {
     // small triangles are listed by box width class, then by box area (a
     // counting sort), so the 32 triangles of a warp have boxes of similar
     // width and size
-    std::vector<int> area_of(T, -1);
     constexpr int kClasses = 7;  // box width 1, 2, <=4, <=8, <=16, <=32, wider
     const int kKeys = kClasses * (small_area + 1);
+    std::unique_ptr<int32_t[]> key(new int32_t[(size_t)T + 1]);  // sort key | area << 16, or -1
     std::vector<int> cnt(kKeys + 1, 0);
     int s = 0;
     for (int t = 0; t < T; t++, q += 6) {
@@ -423,31 +561,32 @@ int raster_lists(const int32_t* q, int T, int W, int H, int32_t* rows, int32_t* 
         const int area = (x1 < x0 || y1 < y0) ? 0 : (x1 - x0 + 1) * (y1 - y0 + 1);
         if (area <= small_area) {
             const int bw = x1 - x0 + 1;
-            int cls = 0;
-            while (cls < kClasses - 1 && (1 << cls) < bw) cls++;
-            area_of[t] = cls * (small_area + 1) + area;
-            cnt[area_of[t] + 1]++;
+            const int cls = bw <= 1 ? 0 : std::min(kClasses - 1, 32 - __builtin_clz((unsigned)(bw - 1)));
+            const int k = cls * (small_area + 1) + area;
+            key[t] = k | (area << 16);
+            cnt[k + 1]++;
         } else {
+            key[t] = -1;
             s += ((y1 - y0) / kRasterRows + 1) * ((x1 - x0) / cols + 1);
         }
     }
     rows[T] = s;
     for (int a = 0; a < kKeys; a++) cnt[a + 1] += cnt[a];
-    for (int t = 0; t < T; t++)
-        if (area_of[t] >= 0) small[cnt[area_of[t]]++] = t;
+    for (int t = 0; t < T; t++) {
+        const int32_t k = key[t];
+        if (k < 0) continue;
+        const int pos = cnt[k & 0xFFFF]++;
+        small[pos] = t;
+        if (small_box) small_box[pos] = std::max(1, k >> 16);
+    }
     *n_small = cnt[kKeys - 1];
     return s;
 }
 
-int small_batches(const int32_t* q, const int32_t* small, int n_small, int W, int H, int32_t* batch, int batch_area) {
+int small_batches(const int32_t* small_box, int n_small, int32_t* batch, int batch_area) {
     int nb = 0, cnt = 0, area = 0;
     for (int i = 0; i < n_small; i++) {
-        const int32_t* t = q + 6 * (size_t)small[i];
-        const int x0 = std::max(0, std::min(t[0], std::min(t[2], t[4])));
-        const int x1 = std::min(W - 1, std::max(t[0], std::max(t[2], t[4])));
-        const int y0 = std::max(0, std::min(t[1], std::min(t[3], t[5])));
-        const int y1 = std::min(H - 1, std::max(t[1], std::max(t[3], t[5])));
-        const int a = (x1 < x0 || y1 < y0) ? 1 : (x1 - x0 + 1) * (y1 - y0 + 1);
+        const int a = small_box[i];
         if (cnt == 0 || cnt == 32 || area + a > batch_area) {  // open a new batch
             batch[nb++] = i;
             cnt = 0;

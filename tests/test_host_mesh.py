@@ -70,6 +70,27 @@ def test_delaunay_support_like_points(oracle_mod):
     assert np.array_equal(_lib_delaunay(P), oracle_mod.delaunay(P))
 
 
+def _lattice_points(seed, w, h, step):
+    rng = np.random.default_rng(seed)
+    pts = {(min(w - 1, u + int(rng.integers(0, step))), min(h - 1, v + int(rng.integers(0, step))))
+           for v in range(0, h, step) for u in range(0, w, step)}
+    return _canon(sorted(pts))
+
+
+@pytest.mark.parametrize("threads", [2, 4, 8])
+def test_delaunay_parallel_matches_serial(oracle_mod, threads):
+    """The forked top splits (halves of 2048 points or more) give the serial triangulation."""
+    P = _lattice_points(30 + threads, 1242, 375, 7)  # about 9500 points: three forked levels
+    n = len(P)
+    cap = 2 * n + 8
+    tri = np.zeros((cap, 3), np.int32)
+    T = S.delaunay_parallel(P, n, tri, cap, threads)
+    serial = _lib_delaunay(P)
+    assert T == len(serial) and np.array_equal(tri[:T], serial)
+    if threads == 8:  # and the oracle's gift wrapping, once
+        assert np.array_equal(serial, oracle_mod.delaunay(P))
+
+
 def test_planes_bit_exact(oracle_mod):
     rng = np.random.default_rng(10)
     P = _canon(np.unique(rng.integers(0, 300, (200, 2)), axis=0))
@@ -85,6 +106,10 @@ def test_host_argument_errors(L):
     P = np.array([[5, 5], [1, 5], [3, 9]], np.int32)  # not canonical: (1,5) must come first
     tri = np.zeros((8, 3), np.int32)
     assert L.stereo_delaunay(P.ctypes.data, 3, tri.ctypes.data, 8) == -1
+    assert L.stereo_delaunay_parallel(P.ctypes.data, 3, tri.ctypes.data, 8, 4) == -1
+    Q = np.ascontiguousarray(P[[1, 0, 2]])
+    assert L.stereo_delaunay_parallel(Q.ctypes.data, 3, tri.ctypes.data, 8, 0) == -1  # threads < 1
+    assert L.stereo_delaunay_parallel(Q.ctypes.data, 3, tri.ctypes.data, 8, 2) == 1
     assert L.stereo_census(None, None, 64, 64, 8, None, None, None, None) == -1
     assert L.stereo_census(1, 1, 3, 64, 8, None, None, None, None) == -1
     assert L.stereo_epipolar_match(1, 1, 64, 64, 1, 4, 300, 4, 2, 1, None) == -1
