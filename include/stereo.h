@@ -135,11 +135,11 @@ const char* stereo_last_error(void);
 #define STEREO_K_FAST_SCORE 1    /* FAST-9 scores */
 #define STEREO_K_FAST_BINS 2     /* non-maximum suppression + per-bin top-K */
 #define STEREO_K_MATCH_KP 3      /* epipolar match of the keypoints */
-#define STEREO_K_RASTER_CLEAR 4  /* plane-index map reset to -1 */
+#define STEREO_K_RASTER_CLEAR 4  /* plane-index map reset to -1 (inside the raster in the engine) */
 #define STEREO_K_RASTER 5        /* scan conversion of the triangles */
 #define STEREO_K_VALIDATE 6      /* fused interpolate + cost + refine */
 #define STEREO_K_RESAMPLE 7      /* per-cell resample + epipolar match */
-#define STEREO_K_FILL 8          /* cell-record resets */
+#define STEREO_K_FILL 8          /* cell-record resets (inside the raster in the engine) */
 #define STEREO_K_KINDS 9
 
 /* Counters of the context since creation.  kernel_launches counts every

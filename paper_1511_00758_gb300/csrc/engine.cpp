@@ -794,8 +794,8 @@ cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, 
         CK(cudaMemcpyAsync(c->err_host.p, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
         return cudaSuccess;
     }
-    CKQ(Lr.run(STEREO_K_FILL, ni, cells_bytes, [&] { return launch_fill_cells(batch_of(iter, WK_FILL), s); }));
-    CKQ(Lr.run(STEREO_K_RASTER, ni, raster_bytes, [&] { return launch_raster(batch_of(iter, WK_RASTER), s); }));
+    // the raster also resets this pass's cell records (no launch of their own)
+    CKQ(Lr.run(STEREO_K_RASTER, ni, raster_bytes + cells_bytes, [&] { return launch_raster(batch_of(iter, WK_RASTER), s); }));
     CKQ(Lr.run(STEREO_K_VALIDATE, ni, validate_bytes, [&] {
         if (c->bulk_validate) return launch_validate_bulk(batch_of(iter, WK_VALIDATE_BULK), prm, s);
         const int fixed = (std::max(1, c->cfg.max_slots) + kVBatch - 1) / kVBatch;

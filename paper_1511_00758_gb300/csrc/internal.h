@@ -14,6 +14,7 @@ constexpr int kFastBinsX = 12;
 constexpr int kFastBinsY = 10;
 constexpr int kMaxK = 32;               // keypoints per bin, upper bound
 constexpr int kRasterRows = 8;          // rows of a raster work item of a large triangle
+constexpr int kFillCells = 2048;        // cell records reset per block (raster launch or the fill kernel)
 constexpr int kRasterCols = 128;        // columns of a raster work item of a large triangle
 constexpr int kVBatch = 64;            // pair descriptors per fused-validate launch (about 7 KB of kernel parameters)
 constexpr int kBatchArea = 1024;        // box pixels of a warp's batch of small triangles (at most 32)

@@ -41,10 +41,10 @@ int work_items(WorkKind k, const PairDev& p) {
         case WK_FAST_BINS: return kFastBins;
         case WK_MATCH_KP: return cdiv((long long)kFastBins * p.K, 8);
         case WK_CLEAR: return cdiv((long long)p.W * p.H, 4096);
-        case WK_FILL: return p.cg_key ? cdiv((long long)p.Wc * p.Hc, 4096) : 0;
+        case WK_FILL: return p.cg_key ? cdiv((long long)p.Wc * p.Hc, kFillCells) : 0;
         case WK_RASTER:
             return (p.small_batch ? cdiv(p.n_batch, 8) : cdiv(p.n_small, 256)) + cdiv(p.raster_items, 8) +
-                   (p.n_hull >= 0 ? cdiv(p.H, 8) : 0);
+                   (p.n_hull >= 0 ? cdiv(p.H, 8) : 0) + (p.cg_key ? cdiv((long long)p.Wc * p.Hc, kFillCells) : 0);
         case WK_RESAMPLE: return cdiv((long long)p.Wc * p.Hc, 8);
         default: return 0;
     }
@@ -106,55 +106,99 @@ __device__ __forceinline__ void stage_tile(uint8_t (*s)[kTileW + 2 * HALO], cons
     }
 }
 
-__device__ __forceinline__ uint32_t census_at(const uint8_t (*s)[kTileW + 4], int r, int c) {
-    const int p = s[r][c];
-    uint32_t code = 0;
-    int bit = 0;
+// Census codes of four adjacent pixels at once.  Staged row r + 2 holds
+// their row and staged columns c + 2 .. c + 5 the pixels (c a multiple of 4,
+// so each staged row is read as two aligned words).  A neighbour's four
+// bytes come from a funnel shift of the two words, and the four comparisons
+// N < C are done at once on bytes: with H = 0x80 in every byte,
+// d = (N | H) - (C & ~H) never borrows across bytes and its top bit is set
+// when the low seven bits of N are >= those of C, so the top bit of
+// (~N & C) | (~(N ^ C) & ~d) is N < C.  Neighbour k (raster order of the 5x5
+// window without its centre) lands in bit k of each pixel's code.
+__device__ __forceinline__ void census4(const uint8_t (*s)[kTileW + 4], int r, int c, uint32_t out[4]) {
+    uint32_t w0[5], w1[5];
 #pragma unroll
-    for (int dy = -2; dy <= 2; dy++) {
+    for (int dy = 0; dy < 5; dy++) {
+        w0[dy] = *reinterpret_cast<const uint32_t*>(&s[r + dy][c]);
+        w1[dy] = *reinterpret_cast<const uint32_t*>(&s[r + dy][c + 4]);
+    }
+    const uint32_t C = __funnelshift_r(w0[2], w1[2], 16);
+    const uint32_t Cl = C & 0x7F7F7F7Fu;
+    uint32_t acc[3] = {0u, 0u, 0u};
+    int k = 0;
 #pragma unroll
-        for (int dx = -2; dx <= 2; dx++) {
-            if (dx == 0 && dy == 0) continue;
-            code |= (uint32_t)(s[r + dy][c + dx] < p) << bit;
-            bit++;
+    for (int dy = 0; dy < 5; dy++) {
+#pragma unroll
+        for (int dx = 0; dx < 5; dx++) {
+            if (dy == 2 && dx == 2) continue;
+            const uint32_t N = dx == 0 ? w0[dy] : dx == 4 ? w1[dy] : __funnelshift_r(w0[dy], w1[dy], 8 * dx);
+            const uint32_t d = (N | 0x80808080u) - Cl;
+            const uint32_t lt = (~N & C) | (~(N ^ C) & ~d);  // top bit of each byte: N < C
+            const int i = k & 7;
+            acc[k >> 3] |= (lt >> (7 - i)) & (0x01010101u << i);
+            k++;
         }
     }
-    return code;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const uint32_t lo = __byte_perm(acc[0], acc[1], (unsigned)(j | ((4 + j) << 4))) & 0xFFFFu;
+        out[j] = lo | (__byte_perm(acc[2], 0u, 0x4440u | j) << 16);
+    }
 }
 
+// One thread per four adjacent pixels of a tile row (8 threads a row, 32 rows).
 __device__ __forceinline__ void census_body(const PairDev& P, int local, const Params& prm) {
-    __shared__ uint8_t sL[kSeedRows + 4][kTileW + 4];
-    __shared__ uint8_t sR[kSeedRows + 4][kTileW + 4];
+    __shared__ __align__(16) uint8_t sL[kSeedRows + 4][kTileW + 4];
+    __shared__ __align__(16) uint8_t sR[kSeedRows + 4][kTileW + 4];
     const int W = P.W, H = P.H;
     const int tx_n = (W + kTileW - 1) / kTileW;
     const int u0 = (local % tx_n) * kTileW, v0 = (local / tx_n) * kSeedRows;
     stage_tile<2>(sL, P.L, W, H, u0, v0);
     if (P.cR) stage_tile<2>(sR, P.R, W, H, u0, v0);
     __syncthreads();
-    const int lx = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int u = u0 + lx;
-    const int words = (W + 31) >> 5;
+    const int ly = threadIdx.x >> 3, c = (threadIdx.x & 7) * 4;
+    const int v = v0 + ly, ub = u0 + c;
+    const bool row_in = v >= 2 && v < H - 2;
+    uint32_t cl[4], cr[4] = {0u, 0u, 0u, 0u};
+    census4(sL, ly, c, cl);
+    if (P.cR) census4(sR, ly, c, cr);
+    // Omega_I: |I(u+1) - I(u-1)| + |I(v+1) - I(v-1)| >= t_grad, from the staged bytes
+    unsigned om = 0;
 #pragma unroll
-    for (int k = 0; k < kSeedRows / 8; k++) {
-        const int ly = w + 8 * k, v = v0 + ly;
-        const bool interior = u >= 2 && u < W - 2 && v >= 2 && v < H - 2;
-        uint32_t cl = 0, cr = 0;
-        bool om = false;
-        if (interior) {
-            cl = census_at(sL, ly + 2, lx + 2);
-            if (P.cR) cr = census_at(sR, ly + 2, lx + 2);
-            const int gx = abs((int)sL[ly + 2][lx + 3] - (int)sL[ly + 2][lx + 1]);
-            const int gy = abs((int)sL[ly + 3][lx + 2] - (int)sL[ly + 1][lx + 2]);
-            om = gx + gy >= prm.t_grad;
+    for (int j = 0; j < 4; j++) {
+        const int u = ub + j;
+        const bool interior = row_in && u >= 2 && u < W - 2;
+        if (!interior) {
+            cl[j] = 0u;
+            cr[j] = 0u;
+        } else {
+            const int gx = abs((int)sL[ly + 2][c + j + 3] - (int)sL[ly + 2][c + j + 1]);
+            const int gy = abs((int)sL[ly + 3][c + j + 2] - (int)sL[ly + 1][c + j + 2]);
+            om |= (unsigned)(gx + gy >= prm.t_grad) << j;
         }
-        if (u < W && v < H) {
-            const size_t p = (size_t)v * W + u;
-            if (P.cL) P.cL[p] = cl;
-            if (P.cR) P.cR[p] = cr;
-        }
-        const unsigned bits = __ballot_sync(0xffffffffu, om);
-        if (lx == 0 && v < H && P.omega) P.omega[(size_t)v * words + (u0 >> 5)] = bits;
     }
+    if (v < H) {
+        const size_t p = (size_t)v * W + ub;
+        const uintptr_t al = (P.cL ? (uintptr_t)(P.cL + p) : 0) | (P.cR ? (uintptr_t)(P.cR + p) : 0);
+        if (ub + 3 < W && (al & 15) == 0) {
+            if (P.cL) *reinterpret_cast<uint4*>(P.cL + p) = make_uint4(cl[0], cl[1], cl[2], cl[3]);
+            if (P.cR) *reinterpret_cast<uint4*>(P.cR + p) = make_uint4(cr[0], cr[1], cr[2], cr[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if (ub + j < W) {
+                    if (P.cL) P.cL[p + j] = cl[j];
+                    if (P.cR) P.cR[p + j] = cr[j];
+                }
+        }
+    }
+    // the row's 32 bits from its 8 threads (adjacent lanes)
+    unsigned bits = om << c;
+    bits |= __shfl_xor_sync(0xffffffffu, bits, 1);
+    bits |= __shfl_xor_sync(0xffffffffu, bits, 2);
+    bits |= __shfl_xor_sync(0xffffffffu, bits, 4);
+    const int words = (W + 31) >> 5;
+    if ((threadIdx.x & 7) == 0 && v < H && P.omega) P.omega[(size_t)v * words + (u0 >> 5)] = bits;
     __syncthreads();
 }
 
@@ -201,15 +245,27 @@ __device__ __forceinline__ void fast_score_body(const PairDev& P, int local, con
             const int p = s[ly + 3][lx + 3];
             uint32_t mb = 0, md = 0;
             int sb = 0, sd = 0;
+            if (t >= 0) {  // brighter and darker exclude each other: no branches
 #pragma unroll
-            for (int i = 0; i < 16; i++) {
-                const int q = s[ly + 3 + fast_dy(i)][lx + 3 + fast_dx(i)];
-                if (q > p + t) {
-                    mb |= 1u << i;
-                    sb += q - p - t;
-                } else if (q < p - t) {
-                    md |= 1u << i;
-                    sd += p - q - t;
+                for (int i = 0; i < 16; i++) {
+                    const int q = s[ly + 3 + fast_dy(i)][lx + 3 + fast_dx(i)];
+                    const int db = q - p - t, dd = p - q - t;
+                    mb |= (uint32_t)(db > 0) << i;
+                    md |= (uint32_t)(dd > 0) << i;
+                    sb += max(db, 0);
+                    sd += max(dd, 0);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; i++) {
+                    const int q = s[ly + 3 + fast_dy(i)][lx + 3 + fast_dx(i)];
+                    if (q > p + t) {
+                        mb |= 1u << i;
+                        sb += q - p - t;
+                    } else if (q < p - t) {
+                        md |= 1u << i;
+                        sd += p - q - t;
+                    }
                 }
             }
             if (has_run9(mb) || has_run9(md)) score = sb > sd ? sb : sd;
@@ -636,8 +692,19 @@ __device__ __forceinline__ void hull_row_clear(const int32_t* __restrict__ hull,
 
 // Work of one pair: blocks of small triangles (8 warp batches each, or 256
 // triangles when no batches are given), ceil(items / 8) blocks of
-// large-triangle work items (one per warp),
-// then, when the hull is given, ceil(H / 8) blocks of hull row clears.
+// large-triangle work items (one per warp), then, when the hull is given,
+// ceil(H / 8) blocks of hull row clears, and, when the pair has cell records,
+// blocks that reset kFillCells of them each for the validate's atomic minima
+// (the raster runs just before it, so no launch of its own is needed).
+__device__ __forceinline__ void fill_cells_range(const PairDev& P, int chunk) {
+    const size_t n = (size_t)P.Wc * P.Hc;
+    const size_t end = min(n, (size_t)(chunk + 1) * kFillCells);
+    for (size_t i = (size_t)chunk * kFillCells + threadIdx.x; i < end; i += blockDim.x) {
+        P.cg_key[i] = kNoKey;
+        P.cb_key[i] = kNoKey;
+    }
+}
+
 __device__ __forceinline__ void raster_body(const PairDev& P, int local, SmallTri* s) {
     const int nsb = P.small_batch ? (P.n_batch + 7) / 8 : (P.n_small + 255) / 256;
     const int ncb = (P.raster_items + 7) / 8;
@@ -664,8 +731,13 @@ __device__ __forceinline__ void raster_body(const PairDev& P, int local, SmallTr
                         P.raster_cols > 0 ? P.raster_cols : kRasterCols);
         return;
     }
-    const int v = (local - nsb - ncb) * 8 + w;
-    if (v < P.H) hull_row_clear(P.hull, P.n_hull, v, P.W, P.planeidx, P.Dit);
+    const int nhb = P.n_hull >= 0 ? (P.H + 7) / 8 : 0;
+    if (local < nsb + ncb + nhb) {
+        const int v = (local - nsb - ncb) * 8 + w;
+        if (v < P.H) hull_row_clear(P.hull, P.n_hull, v, P.W, P.planeidx, P.Dit);
+        return;
+    }
+    fill_cells_range(P, local - nsb - ncb - nhb);
 }
 
 __global__ void __launch_bounds__(256) k_raster(PairBatch b) {
@@ -1494,13 +1566,7 @@ __global__ void __launch_bounds__(256) k_resample(PairBatch b, Params prm) {
 }
 
 // Cell records of a pass start empty (0xFFFFFFFF) for the atomic minimum.
-__device__ __forceinline__ void fill_cells_body(const PairDev& P, int local) {
-    const size_t n = (size_t)P.Wc * P.Hc;
-    for (size_t i = (size_t)local * 4096 + threadIdx.x; i < n && i < (size_t)(local + 1) * 4096; i += blockDim.x) {
-        P.cg_key[i] = kNoKey;
-        P.cb_key[i] = kNoKey;
-    }
-}
+__device__ __forceinline__ void fill_cells_body(const PairDev& P, int local) { fill_cells_range(P, local); }
 
 __global__ void __launch_bounds__(256) k_fill_cells(PairBatch b) {
 #define BODY(P, l) fill_cells_body(P, l)
