@@ -297,6 +297,27 @@ def test_end_to_end_autotuned(oracle_mod):
     _compare_run(oracle_mod, p, got)
 
 
+def test_end_to_end_idle_workers_and_round_shapes(oracle_mod):
+    """Four host workers on one driving pair: the idle ones take halves of the
+    large triangulations (same triangles, so the same results), and each round
+    launches only the stage it has work for (the raster also resets the cell
+    records, so neither the clear nor the reset has launches of its own)."""
+    p = scenes.config_pairs("driving_1242x375")[0]
+    H, W = p.left.shape
+    with S.Context(mem_budget_bytes=1 << 30, max_slots=1, host_threads=4, **PRM) as ctx:
+        t = ctx.submit(_t(p.left), _t(p.right), W, H, p.dmax, p.iters, p.cell)
+        got = ctx.result_tensors(ctx.poll(t))
+        ctx.release(t)
+        st = ctx.stats()
+    want = _compare_run(oracle_mod, p, got)
+    assert max(len(s) for s in want["support"]) >= 4096  # large enough to fork
+    k = list(st.kind_launches)
+    assert k[0:4] == [1, 1, 1, 1]  # one seed round
+    assert k[5] == k[6] == k[7] == p.iters  # one iteration round per pass
+    assert k[4] == 0 and k[8] == 0
+    assert st.gpu_rounds == 1 + p.iters
+
+
 def test_end_to_end_vga_one_iteration(oracle_mod):
     p = scenes.config_pairs("vga_polygons")[0]
     want = _compare_run(oracle_mod, p, _run_ctx([p])[0])
