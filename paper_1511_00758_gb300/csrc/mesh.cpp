@@ -119,7 +119,7 @@ struct Mesh {
             k = freed.back();
             freed.pop_back();
         } else {
-            if (nq == hi) {
+            if (nq >= hi) {
                 if (store && lo == 0) {
                     const int nc = std::max(2 * hi, 64);
                     std::unique_ptr<Quad[]> g(new Quad[nc]);
