@@ -211,34 +211,19 @@ def run_ours(args):
                     profile=1, batch_window_us=args.window_us, autotune=0 if args.no_autotune else 1,
                     tune_w=W, tune_h=H, **PRM)
     stream = ctx.stream
-    copy_stream = torch.cuda.Stream()
 
     def one_step(host=False):
         lat = []
         ins = host_in if host else dev_in
         tickets = [ctx.submit(l, r, W, H, p.dmax, p.iters, p.cell) for (l, r), p in zip(ins, pairs)]
-        pending = []  # (ticket, copy-done event): results go to pinned host buffers on a copy stream
         for i, t in enumerate(tickets):
-            r = ctx.poll(t)
+            # host leg: the library copies D_f and C_f into page-locked host buffers on the
+            # polling thread's own stream while later requests keep computing
+            r = ctx.poll_host(t, host_out[i][0], host_out[i][1]) if host else ctx.poll(t)
             if r.status != 0:
                 raise RuntimeError(f"request failed: {r.status}")
             lat.append(r.latency_ms)
-            if not host:
-                ctx.release(t)
-                continue
-            with torch.cuda.stream(copy_stream):
-                host_out[i][0].copy_(S.device_view(r.disparity, (H, W), "<f4"), non_blocking=True)
-                host_out[i][1].copy_(S.device_view(r.cost, (H, W), "|u1"), non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(copy_stream)
-            pending.append((t, ev))
-            while pending and pending[0][1].query():  # release what has landed
-                ctx.release(pending.pop(0)[0])
-        for t, ev in pending:
-            ev.synchronize()
             ctx.release(t)
-        if host:
-            stream.wait_stream(copy_stream)  # the step's span ends after the copies
         return lat
 
     def timed(nsteps, host=False):

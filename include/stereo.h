@@ -119,6 +119,16 @@ int stereo_submit(stereo_ctx* ctx, int stream_id, const uint8_t* left, const uin
  * returns its error code (out->status holds it too). */
 int stereo_poll(stereo_ctx* ctx, uint64_t ticket, stereo_result* out, int timeout_us);
 
+/* stereo_poll, then the result copied into the caller's host buffers: D_f
+ * (w*h fp32), C_f and the mask (w*h bytes each); a NULL buffer is skipped.
+ * The copies run on the calling thread's own stream (other requests keep
+ * computing meanwhile) and have landed when the call returns; page-locked
+ * buffers copy fastest, pageable ones work too.  No counterpart in the paper:
+ * it delivers Alg. 1's output D_f to host memory in one call.  Returns what
+ * stereo_poll returns, or STEREO_E_CUDA if a copy failed. */
+int stereo_poll_host(stereo_ctx* ctx, uint64_t ticket, stereo_result* out, int timeout_us,
+                     float* disparity, uint8_t* cost, uint8_t* mask);
+
 /* Return a finished request's buffers to the pool. */
 int stereo_release(stereo_ctx* ctx, uint64_t ticket);
 

@@ -73,6 +73,7 @@ _SIGS = {
     "stereo_create": (_I, [ctypes.POINTER(Config), ctypes.POINTER(_P)]),
     "stereo_submit": (_I, [_P, _I, _P, _P, _I, _I, _I, _I, _I, ctypes.POINTER(ctypes.c_uint64)]),
     "stereo_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(Result), _I]),
+    "stereo_poll_host": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(Result), _I, _P, _P, _P]),
     "stereo_release": (_I, [_P, ctypes.c_uint64]),
     "stereo_destroy": (None, [_P]),
     "stereo_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
@@ -252,6 +253,17 @@ class Context:
         if rc == E_PENDING:
             return None
         _check(rc, "poll")
+        return r
+
+    def poll_host(self, ticket, disparity, cost, mask=None, timeout_us=-1):
+        """poll, then D_f / C_f / mask copied by the library into the given host
+        buffers (numpy arrays or CPU tensors; page-locked copies fastest)."""
+        r = Result()
+        rc = lib().stereo_poll_host(self.h, ticket, ctypes.byref(r), timeout_us, _ptr(disparity), _ptr(cost),
+                                    _ptr(mask))
+        if rc == E_PENDING:
+            return None
+        _check(rc, "poll_host")
         return r
 
     def release(self, ticket):

@@ -1517,6 +1517,25 @@ int stereo_poll(stereo_ctx* c, uint64_t ticket, stereo_result* out, int timeout_
     return r->status;
 }
 
+int stereo_poll_host(stereo_ctx* c, uint64_t ticket, stereo_result* out, int timeout_us, float* disparity,
+                     uint8_t* cost, uint8_t* mask) {
+    const int rc = stereo_poll(c, ticket, out, timeout_us);
+    if (rc != STEREO_OK) return rc;
+    const size_t N = (size_t)out->w * out->h;
+    cudaSetDevice(c->cfg.device);
+    cudaStream_t s = cudaStreamPerThread;
+    cudaError_t e = cudaSuccess;
+    if (disparity && e == cudaSuccess) e = cudaMemcpyAsync(disparity, out->disparity, 4 * N, cudaMemcpyDeviceToHost, s);
+    if (cost && e == cudaSuccess) e = cudaMemcpyAsync(cost, out->cost, N, cudaMemcpyDeviceToHost, s);
+    if (mask && e == cudaSuccess) e = cudaMemcpyAsync(mask, out->mask, N, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return STEREO_E_CUDA;
+    }
+    return STEREO_OK;
+}
+
 int stereo_release(stereo_ctx* c, uint64_t ticket) {
     if (!c) return STEREO_E_INVAL;
     std::unique_lock<std::mutex> g(c->mu);

@@ -387,11 +387,24 @@ def test_batched_mixed_cell_classes(oracle_mod):
 
 
 def test_host_input_pointers(oracle_mod):
+    """Host inputs, and the result delivered to host buffers by poll_host (pageable
+    numpy arrays and page-locked tensors) equal to the device result."""
     p = scenes.config_pairs("vga_polygons")[0]
     with S.Context(mem_budget_bytes=1 << 28, **PRM) as ctx:
         t = ctx.submit(p.left, p.right, 640, 480, p.dmax, p.iters, p.cell)
         got = ctx.result_tensors(ctx.poll(t))
+        d = np.full((480, 640), -7.0, np.float32)
+        c = np.zeros((480, 640), np.uint8)
+        m = np.zeros((480, 640), np.uint8)
+        r = ctx.poll_host(t, d, c, m)
+        assert r.status == 0 and r.w == 640
+        dp = torch.empty((480, 640), dtype=torch.float32).pin_memory()
+        cp = torch.empty((480, 640), dtype=torch.uint8).pin_memory()
+        ctx.poll_host(t, dp, cp)  # the mask skipped
         ctx.release(t)
+    assert np.array_equal(d.view(np.uint32), got["D_f"].cpu().numpy().view(np.uint32))
+    assert np.array_equal(c, got["C_f"].cpu().numpy()) and np.array_equal(m, got["mask"].cpu().numpy())
+    assert np.array_equal(dp.numpy().view(np.uint32), d.view(np.uint32)) and np.array_equal(cp.numpy(), c)
     _compare_run(oracle_mod, p, got)
 
 
