@@ -59,21 +59,23 @@ def build(force=False, verbose=False):
     for obj, cmd in jobs.items():
         procs[obj] = subprocess.Popen(cmd + ["-o", os.path.join(tmp, obj)], stdout=subprocess.PIPE,
                                       stderr=subprocess.STDOUT, text=True)
-    failed = []
-    for obj, p in procs.items():
-        out, _ = p.communicate()
-        if verbose or p.returncode != 0:
-            sys.stderr.write(out)
-        if p.returncode != 0:
-            failed.append(obj)
-    if failed:
-        raise RuntimeError(f"libstereo build failed: {failed}")
-    lib_tmp = LIB + f".{os.getpid()}.tmp"
-    link = [nvcc, *ARCH, "-shared", "-o", lib_tmp, *[os.path.join(tmp, o) for o in jobs],
-            "-cudart", "shared", "-Xlinker", "-rpath," + os.path.join(cuda, "lib64"), "-lpthread"]
-    subprocess.check_call(link)
-    os.replace(lib_tmp, LIB)
-    shutil.rmtree(tmp, ignore_errors=True)
+    try:
+        failed = []
+        for obj, p in procs.items():
+            out, _ = p.communicate()
+            if verbose or p.returncode != 0:
+                sys.stderr.write(out)
+            if p.returncode != 0:
+                failed.append(obj)
+        if failed:
+            raise RuntimeError(f"libstereo build failed: {failed}")
+        lib_tmp = LIB + f".{os.getpid()}.tmp"
+        link = [nvcc, *ARCH, "-shared", "-o", lib_tmp, *[os.path.join(tmp, o) for o in jobs],
+                "-cudart", "shared", "-Xlinker", "-rpath," + os.path.join(cuda, "lib64"), "-lpthread"]
+        subprocess.check_call(link)
+        os.replace(lib_tmp, LIB)
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
     return LIB
 
 
