@@ -247,6 +247,14 @@ struct Request {
     Pinned st_kp;             // kp_uv + kp_d
     Pinned st_cells;          // cg_key, cg_d, cb_key, x_d
     bool resample_now = false;
+    // The seed stage's keypoints (a few KB) are written by the kernels
+    // straight into the page-locked staging buffer (device-mapped), so a seed
+    // round issues no copy back for them; false when the mapping is
+    // unavailable and the round copies them instead.  (Writing a pass's cell
+    // records to host memory the same way made the resample slower than the
+    // copy it saves: many scattered 4-byte writes over the host link.)
+    bool direct_kp = false;
+    int32_t* kp_dev = nullptr;  // the device block's keypoint region (the copy-back path)
     class Pool* pool = nullptr;  // the context's host workers (idle ones help triangulate)
 };
 
@@ -287,6 +295,7 @@ void carve(Request& r, int K) {
     d.mask = (uint8_t*)take(N);
     d.kp_uv = (int32_t*)take((size_t)kFastBins * K * 12);  // (u, v) slots, then the matches
     d.kp_d = d.kp_uv + (size_t)kFastBins * K * 2;
+    r.kp_dev = d.kp_uv;
     // cell records: four arrays laid out at the current pass's cell count, so
     // one copy moves them (set per pass by set_cells)
     r.cells_dev = (uint32_t*)take(16 * (size_t)r.ncell_max);
@@ -763,7 +772,8 @@ cudaError_t issue_inputs(Group& iter, cudaStream_t s) {
 
 cudaError_t issue_outputs(stereo_ctx* c, Group& seed, Group& iter, cudaStream_t s) {
     for (Request* r : seed.reqs)  // keypoint slots and their matches, one copy
-        CK(cudaMemcpyAsync(r->st_kp.p, r->dev.kp_uv, (size_t)kFastBins * c->K * 12, cudaMemcpyDeviceToHost, s));
+        if (!r->direct_kp)
+            CK(cudaMemcpyAsync(r->st_kp.p, r->dev.kp_uv, (size_t)kFastBins * c->K * 12, cudaMemcpyDeviceToHost, s));
     for (Request* r : iter.reqs) {  // the four cell arrays of this pass, one copy
         if (!r->resample_now) continue;
         const size_t nc = (size_t)r->dev.Wc * r->dev.Hc;
@@ -828,6 +838,11 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
     for (Request* r : seed.reqs) {
         seed_px += (double)r->W * r->H;
         if (!r->st_kp.ensure((size_t)kFastBins * c->K * 12)) return cudaErrorMemoryAllocation;
+        void* hp = nullptr;
+        r->direct_kp = cudaHostGetDevicePointer(&hp, r->st_kp.p, 0) == cudaSuccess && hp;
+        if (!r->direct_kp) cudaGetLastError();
+        r->dev.kp_uv = r->direct_kp ? (int32_t*)hp : r->kp_dev;
+        r->dev.kp_d = r->dev.kp_uv + (size_t)kFastBins * c->K * 2;
     }
     for (Request* r : iter.reqs) {
         const size_t tri_bytes = align_up(tri_stage_bytes(r->T, r->raster_items, r->n_small, r->n_hull, r->n_batch) + 64, 256);
