@@ -7,7 +7,10 @@
 // thread gathers every admitted request that is ready for a GPU stage and
 // launches each stage kind once for all of them (kernels take a PairBatch);
 // host mesh steps run on a worker pool meanwhile, so requests at different
-// iterations overlap.  max_slots = 1 gives the plain per-pair path.
+// iterations overlap.  A round's launches are captured into a CUDA graph, one
+// executable graph per round shape (seed stage, iteration stage or both)
+// updated in place; workers with nothing queued take halves of a large
+// triangulation.  max_slots = 1 gives the plain per-pair path.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
