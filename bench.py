@@ -439,8 +439,36 @@ def run_batch_workload(args, name):
            "validate_gbs": (kb / (kms * 1e-3) / 1e9) if kms > 0 else None,
            "validate_pairs_per_launch": (s1.batched_pairs - s0.batched_pairs) / max(1, s1.kernel_launches - s0.kernel_launches),
            "gpu_launches": s1.kernel_launches - s0.kernel_launches}
+    out["cpu_baseline"] = None if args.no_cpu else _oracle_all_cores(name, pairs)
     print(json.dumps(out))
     return 0
+
+
+def _oracle_all_cores(name, pairs):
+    """The oracle, one pair per thread on min(pairs, cores) host cores (the C oracle releases the
+    interpreter lock), over pairs spread evenly through the workload: a bounded sample of it."""
+    if name == "large":
+        return {"value": None, "unit": "Mpix/s", "cores": 0, "kind": "oracle",
+                "sample": "not run: the oracle's gift-wrapping triangulation is O(n^2) in the support points, "
+                          "and cells down to 1x1 make millions of them per pair (hours per pair)"}
+    import threading
+
+    import oracle
+    oracle.build()
+    ncore = max(1, min(len(pairs), os.cpu_count() or 1))
+    step = max(1, len(pairs) // ncore)
+    sample = pairs[::step][:ncore]
+    th = [threading.Thread(target=oracle.run, args=(p.left, p.right, p.dmax, p.iters, p.cell), kwargs=PRM)
+          for p in sample]
+    t0 = time.perf_counter()
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    dt = time.perf_counter() - t0
+    return {"value": sum(p.left.size for p in sample) / dt / 1e6, "unit": "Mpix/s", "cores": ncore,
+            "kind": "oracle", "sample": f"{len(sample)} pairs spread through the workload, one per thread on "
+                                        f"{ncore} host cores, whole method"}
 
 
 def run_kernel(args, which):
