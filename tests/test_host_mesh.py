@@ -91,6 +91,24 @@ def test_delaunay_parallel_matches_serial(oracle_mod, threads):
         assert np.array_equal(serial, oracle_mod.delaunay(P))
 
 
+def test_delaunay_parallel_degenerate_sets():
+    """Forked splits on degenerate sets give the serial triangulation: a full
+    lattice (every square cocircular), three long collinear rows, and all
+    points on one line (no triangle)."""
+    lattice = _canon([(u, v) for v in range(0, 300, 3) for u in range(0, 420, 3)])  # 14000 points
+    rows = _canon([(u, v) for v in (0, 1, 57) for u in range(0, 3000)])
+    line = _canon([(u, 5) for u in range(9000)])
+    for P in (lattice, rows, line):
+        n = len(P)
+        cap = 2 * n + 8
+        serial = _lib_delaunay(P)
+        for threads in (2, 8):
+            tri = np.zeros((cap, 3), np.int32)
+            T = S.delaunay_parallel(P, n, tri, cap, threads)
+            assert T == len(serial) and np.array_equal(tri[:T], serial)
+    assert len(_lib_delaunay(line)) == 0
+
+
 def test_planes_bit_exact(oracle_mod):
     rng = np.random.default_rng(10)
     P = _canon(np.unique(rng.integers(0, 300, (200, 2)), axis=0))
