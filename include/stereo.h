@@ -65,8 +65,10 @@ typedef struct {
     int uniq_margin;           /* epipolar uniqueness margin in census bits */
     int host_threads;          /* host triangulation workers (0 = 1) */
     void* stream;              /* cudaStream_t for all work (NULL = library creates one) */
-    int profile;               /* 1 = time every kernel launch with CUDA events on `stream`
-                                  and accumulate per-kind durations in stereo_stats */
+    int profile;               /* N > 0: time the kernel launches of every N-th GPU round with
+                                  CUDA events on `stream` and accumulate per-kind durations in
+                                  stereo_stats (1 = every round; event nodes lengthen a round,
+                                  so a larger N disturbs the timing less); 0 = off */
     int inject_mesh_failure;   /* testing: the n-th host mesh step of the context (1-based) fails
                                   as if the triangulation had failed (STEREO_E_INTERNAL); 0 = off */
     int batch_window_us;       /* continuous batching: when some requests are ready for a GPU
@@ -155,8 +157,10 @@ const char* stereo_last_error(void);
 /* Counters of the context since creation.  kernel_launches counts every
  * kernel the library launched; batched_pairs sums the pairs each launch
  * covered (batched_pairs / kernel_launches = mean pairs per launch).  With
- * profile = 1, kind_ms[k] holds the summed CUDA-event durations of kind k and
- * kind_bytes[k] the algorithmic bytes those launches had to move (census:
+ * profile = N > 0, kind_ms[k] holds the summed CUDA-event durations of the
+ * kind_timed[k] launches of kind k that were timed (those of every N-th
+ * round; kind_ms[k] / kind_timed[k] is the mean launch time), and
+ * kind_bytes[k] the algorithmic bytes all kind_launches[k] launches had to move (census:
  * 2 B/px read + 8.125 B/px written; raster clear and raster: 4 B/px written each; validate:
  * 13.125 B/px read (12.125 on a first pass) + 6 B/px written). */
 typedef struct {
@@ -172,6 +176,7 @@ typedef struct {
     double graph_ms;              /* of which capturing and updating / instantiating the round's graph */
     double exec_ms;               /* of which from the graph launch to the round's synchronisation */
     long long graph_instantiations; /* rounds whose graph could not be updated in place */
+    long long kind_timed[STEREO_K_KINDS]; /* launches of each kind timed with events (see profile) */
 } stereo_stats;
 int stereo_get_stats(stereo_ctx* ctx, stereo_stats* out);
 

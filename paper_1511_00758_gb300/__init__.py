@@ -53,7 +53,7 @@ class Stats(ctypes.Structure):
                 ("host_mesh_ms", ctypes.c_double), ("kind_launches", ctypes.c_longlong * 9),
                 ("kind_ms", ctypes.c_double * 9), ("kind_bytes", ctypes.c_double * 9),
                 ("round_ms", ctypes.c_double), ("graph_ms", ctypes.c_double), ("exec_ms", ctypes.c_double),
-                ("graph_instantiations", ctypes.c_longlong)]
+                ("graph_instantiations", ctypes.c_longlong), ("kind_timed", ctypes.c_longlong * 9)]
 
 
 class Tuning(ctypes.Structure):

@@ -389,8 +389,10 @@ struct stereo_ctx {
     cudaStream_t copy_stream = nullptr;      // submit-time device copies (never captured)
     cudaStream_t capture_stream = nullptr;   // private stream the rounds are captured on
     // executable graphs by round shape (bit 0: seed stage, bit 1: iteration
-    // stage), each updated in place by the next round of its shape
-    cudaGraphExec_t graph_exec[4] = {nullptr, nullptr, nullptr, nullptr};
+    // stage, bit 2: timed with events), each updated in place by the next
+    // round of its shape
+    cudaGraphExec_t graph_exec[8] = {};
+    long long rounds_seen = 0;  // for timing every profile-th round
     int* err_dev = nullptr;                  // set by a device-side wait that gave up
     Pinned err_host;
     bool bulk_validate = false;              // the bulk-copy validate kernel (else the plain one)
@@ -689,9 +691,11 @@ struct Launcher {
     struct Timed {
         int kind;
         cudaEvent_t a, b;
+        int launches;
     };
     std::vector<Timed> timed;
     int launched = 1;  // kernels issued by the current run() body (a body may set it)
+    bool prof = false;  // this round's launches are timed (every profile-th round)
 
     cudaEvent_t event() {  // the pool is filled before each capture (at most 24 per round)
         cudaEvent_t e = c->ev_pool.back();
@@ -702,7 +706,7 @@ struct Launcher {
     cudaError_t run(int kind, int npairs, double bytes, F&& f) {
         cudaEvent_t a = nullptr;
         cudaError_t e;
-        if (c->cfg.profile) {  // event nodes of the round's graph: timed on the GPU, after it
+        if (prof) {  // event nodes of the round's graph: timed on the GPU, after it
             a = event();
             if ((e = cudaEventRecordWithFlags(a, s, cudaEventRecordExternal)) != cudaSuccess) {
                 note_error(e, "event record before a launch", __LINE__);
@@ -713,13 +717,13 @@ struct Launcher {
             note_error(e, "kernel launch", __LINE__);
             return e;
         }
-        if (c->cfg.profile) {
+        if (prof) {
             cudaEvent_t b = event();
             if ((e = cudaEventRecordWithFlags(b, s, cudaEventRecordExternal)) != cudaSuccess) {
                 note_error(e, "event record after a launch", __LINE__);
                 return e;
             }
-            timed.push_back({kind, a, b});
+            timed.push_back({kind, a, b, launched});
         }
         if (c->launch_log)  // one line per launch; a run() body's bytes split evenly over its launches
             for (int i = 0; i < launched; i++)
@@ -738,7 +742,10 @@ struct Launcher {
         c->ev_retired.clear();
         for (auto& t : timed) {
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) delta.kind_ms[t.kind] += ms;
+            if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+                delta.kind_ms[t.kind] += ms;
+                delta.kind_timed[t.kind] += t.launches;
+            }
             c->ev_retired.push_back(t.a);
             c->ev_retired.push_back(t.b);
         }
@@ -758,6 +765,7 @@ void add_stats(stereo_stats& to, const stereo_stats& d) {
         to.kind_launches[k] += d.kind_launches[k];
         to.kind_ms[k] += d.kind_ms[k];
         to.kind_bytes[k] += d.kind_bytes[k];
+        to.kind_timed[k] += d.kind_timed[k];
     }
 }
 
@@ -908,7 +916,8 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
     // that graph has run, so they are recycled a round later; events are
     // never destroyed while the context lives, and an executable graph is
     // always updated with fresh events before it is launched again.
-    if (c->cfg.profile)
+    Lr.prof = c->cfg.profile > 0 && c->rounds_seen++ % c->cfg.profile == 0;
+    if (Lr.prof)
         while (c->ev_pool.size() < 32) {
             cudaEvent_t ev = nullptr;
             CK(cudaEventCreate(&ev));
@@ -935,7 +944,7 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         Lr.timed.clear();
         return err;
     }
-    cudaGraphExec_t& exec = c->graph_exec[(seed.reqs.empty() ? 0 : 1) | (iter.reqs.empty() ? 0 : 2)];
+    cudaGraphExec_t& exec = c->graph_exec[(seed.reqs.empty() ? 0 : 1) | (iter.reqs.empty() ? 0 : 2) | (Lr.prof ? 4 : 0)];
     bool updated = false;
     if (exec) {
         cudaGraphExecUpdateResultInfo info{};
