@@ -45,3 +45,16 @@ def test_ctypes_structures_match_the_header():
         assert c[(cname, "size")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert c[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_binding_signatures_match_the_prototypes():
+    """Every prototype of the header has a binding signature with its argument count."""
+    import re
+    hdr = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "stereo.h")).read(), flags=re.S)
+    protos = re.findall(r"\b(?:int|void|size_t)\s+\**(stereo_\w+)\s*\(([^;]*?)\)\s*;", hdr, flags=re.S)
+    assert len(protos) >= 20
+    for name, args in protos:
+        a = args.strip()
+        n = 0 if a in ("", "void") else a.count(",") + 1
+        assert name in S._SIGS, name
+        assert len(S._SIGS[name][1]) == n, name
