@@ -307,7 +307,7 @@ def test_delaunay_unit_lattice_closed_form(oracle_mod):
 
 
 def test_delaunay_general_position_matches_qhull(oracle_mod):
-    spatial = pytest.importorskip("scipy.spatial")
+    import scipy.spatial as spatial  # present on every machine this suite runs on: fail, never skip
     rng = np.random.default_rng(7)
     for n in (5, 17, 60, 300):
         P = _canon(np.unique(rng.integers(0, 16000, (n, 2)), axis=0))
@@ -315,6 +315,43 @@ def test_delaunay_general_position_matches_qhull(oracle_mod):
         q = spatial.Delaunay(P.astype(np.float64))
         want = sorted(sorted(map(int, s)) for s in q.simplices)
         assert tri.tolist() == want
+
+
+def _incircle_exact(a, b, c, d):
+    """Sign of the in-circle determinant of d against the CCW triangle abc (exact integers)."""
+    rows = [(p[0] - d[0], p[1] - d[1]) for p in (a, b, c)]
+    m = [(x, y, x * x + y * y) for x, y in rows]
+    return (m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0])
+            + m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]))
+
+
+@pytest.mark.parametrize("seed", [41, 42])
+def test_delaunay_general_position_brute_force(oracle_mod, seed):
+    """Without any library: for points with no three collinear and no four
+    cocircular, the Delaunay triangles are exactly the triples whose
+    circumcircle holds no other point (enumerated over every triple)."""
+    rng = np.random.default_rng(seed)
+    while True:
+        P = _canon(np.unique(rng.integers(0, 2000, (28, 2)), axis=0))
+        n = len(P)
+        pts = [tuple(map(int, p)) for p in P]
+        trip = [(i, j, k) for i in range(n) for j in range(i + 1, n) for k in range(j + 1, n)]
+        if any(_orient(pts[i], pts[j], pts[k]) == 0 for i, j, k in trip):
+            continue
+        want, degenerate = [], False
+        for i, j, k in trip:
+            a, b, c = pts[i], pts[j], pts[k]
+            if _orient(a, b, c) < 0:
+                b, c = c, b
+            signs = [_incircle_exact(a, b, c, pts[m]) for m in range(n) if m not in (i, j, k)]
+            if 0 in signs:
+                degenerate = True
+                break
+            if all(x < 0 for x in signs):
+                want.append([i, j, k])
+        if not degenerate:
+            break
+    assert oracle_mod.delaunay(P).tolist() == want
 
 
 @pytest.mark.parametrize("seed", [8, 9, 10])
