@@ -2,9 +2,9 @@
 // cannot allocate device memory.
 //
 // Some callers may not call cudaMalloc (or any allocating routine) on the
-// path that runs the raster: a real-time loop with a fixed memory plan, code
-// running while another component owns the allocator, or work recorded into
-// a capture where allocation is not allowed.  stereo_raster needs scratch for
+// path that runs the raster: a real-time loop with a fixed memory plan that
+// allocates everything up front, or code running while another component
+// owns the device allocator.  stereo_raster needs scratch for
 // its per-triangle work lists; this variant takes that scratch from one
 // fixed, file-scope device array instead, so the caller passes only its
 // inputs and outputs.
@@ -14,7 +14,10 @@
 // until the process exits.  All calls share it: two calls whose work
 // overlaps on the GPU (different streams, or different threads without
 // ordering) race on it and must be serialised by the caller.  Nothing in it
-// needs clearing: each call writes every entry it later reads.
+// needs clearing: each call writes every entry it later reads.  The address
+// of the array is looked up once per device and kept; a cudaDeviceReset (or
+// anything else that destroys the device's primary context) makes it stale,
+// so this entry point must not be used after one.
 #include <mutex>
 
 #include "internal.h"
@@ -27,8 +30,9 @@ constexpr int kMaxDevices = 64;
 
 // Work lists: work-item offsets of the large triangles (T + 1), the small-triangle list (T + 1),
 // then per-block offsets of the list builder.
-static __device__ __align__(256) int32_t
-    g_raster_lists[2 * (kNoAllocMaxTriangles + 1) + 2 * ((kNoAllocMaxTriangles + 1023) / 1024)];
+static __device__ __align__(256) int32_t g_raster_lists[stereo::raster_list_words(kNoAllocMaxTriangles)];
+static_assert(sizeof(g_raster_lists) == sizeof(int32_t) * stereo::raster_list_words(kNoAllocMaxTriangles),
+              "the array holds the work lists of kNoAllocMaxTriangles triangles");
 
 std::mutex g_mu;
 int32_t* g_addr[kMaxDevices] = {};
@@ -56,7 +60,7 @@ int lists_address(int32_t** out) {
 
 extern "C" int stereo_raster_noalloc(const int32_t* tri_uv, const float* abc, int T, int w, int h,
                                      int32_t* planeidx, float* D_it, void* stream) {
-    if (w < 5 || h < 5 || w > 8192 || h > 8192 || (long long)w * h >= (1ll << 27) || T < 0 ||
+    if (!stereo::valid_size(w, h) || T < 0 ||
         (T > 0 && !tri_uv) || (!planeidx && !D_it) || (D_it && T > 0 && !abc) ||
         ((uintptr_t)planeidx & 15) != 0 || ((uintptr_t)D_it & 15) != 0)
         return STEREO_E_INVAL;
