@@ -78,6 +78,12 @@ typedef struct {
                                   synthetic round of tune_w x tune_h pairs and keep the fastest
                                   (results do not depend on it; see stereo_get_tuning) */
     int tune_w, tune_h;        /* frame of the synthetic tuning round (0 = 1242 x 375) */
+    int inject_wait_timeout;   /* testing: n > 0 makes the context use the bulk-copy validate
+                                  (stereo_validate_bulk's kernel, the one kernel with device-side
+                                  waits) and, in its n-th GPU round with an iteration stage, has
+                                  that kernel's producer issue no copy, so every bounded wait gives
+                                  up after a second: the round's requests fail with
+                                  STEREO_E_TIMEOUT and the context stays usable; 0 = off */
 } stereo_config;
 
 /* Fill *cfg with the defaults: t_lo 4, t_hi 8, t_grad 8, t_fast 20,
@@ -272,16 +278,19 @@ int stereo_raster(const int32_t* tri_uv, const float* abc, int T, int w, int h, 
                   float* D_it, void* scratch, size_t scratch_bytes, void* stream);
 
 /* stereo_raster without a scratch argument, for callers that cannot allocate
- * device memory where they run the raster (a fixed real-time memory plan, an
- * allocator owned by another component, work recorded into a capture).  The
+ * device memory where they run the raster (a real-time loop whose memory is
+ * all allocated up front, or code running while another component owns the
+ * device allocator).  The
  * paper has no counterpart: it is a memory-management variant of
  * stereo_raster with the same arguments and results otherwise.  Its work
  * lists live in one file-scope device array sized for at most 262143
  * triangles (just over 2 MiB, held by every GPU that loads the library until exit);
  * larger T returns STEREO_E_CAP.  The first call on each device looks up the
  * array's device address (no allocation); make that first call before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
- * race and must be serialised by the caller. */
+ * stream capture.  The address is kept for the life of the process: after a
+ * cudaDeviceReset the entry point must not be called again.  All calls share
+ * the array: calls that overlap on the GPU race and must be serialised by the
+ * caller. */
 int stereo_raster_noalloc(const int32_t* tri_uv, const float* abc, int T, int w, int h,
                           int32_t* planeidx, float* D_it, void* stream);
 

@@ -36,7 +36,7 @@ class Config(ctypes.Structure):
                 ("kp_per_bin", ctypes.c_int), ("uniq_margin", ctypes.c_int), ("host_threads", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("profile", ctypes.c_int), ("inject_mesh_failure", ctypes.c_int),
                 ("batch_window_us", ctypes.c_int), ("autotune", ctypes.c_int), ("tune_w", ctypes.c_int),
-                ("tune_h", ctypes.c_int)]
+                ("tune_h", ctypes.c_int), ("inject_wait_timeout", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):

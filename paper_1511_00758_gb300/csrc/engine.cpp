@@ -393,6 +393,7 @@ struct stereo_ctx {
     // round of its shape
     cudaGraphExec_t graph_exec[8] = {};
     long long rounds_seen = 0;  // for timing every profile-th round
+    long long iter_rounds = 0;  // rounds with an iteration stage (for the wait-timeout test hook)
     int* err_dev = nullptr;                  // set by a device-side wait that gave up
     Pinned err_host;
     bool bulk_validate = false;              // the bulk-copy validate kernel (else the plain one)
@@ -405,15 +406,15 @@ struct stereo_ctx {
     stereo_stats stats{};
 };
 
+bool stereo::valid_size(int w, int h) {
+    return w >= 5 && h >= 5 && w <= 8192 && h <= 8192 && (long long)w * h < (1ll << 27);
+}
+
 namespace {
 
 bool valid_params(const stereo_config& c) {
     return c.t_lo >= 0 && c.t_lo <= c.t_hi && c.t_hi < 24 && c.t_grad >= 0 && c.t_fast >= 0 &&
            c.kp_per_bin >= 1 && c.kp_per_bin <= kMaxK && c.uniq_margin >= 0;
-}
-
-bool valid_size(int w, int h) {
-    return w >= 5 && h >= 5 && w <= 8192 && h <= 8192 && (long long)w * h < (1ll << 27);
 }
 
 // Staging layout of one mesh: the hull edges (4 int32 each, first so they
@@ -805,6 +806,9 @@ cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, 
     Params prm = c->prm;
     prm.err = c->err_dev;
     const int ns = (int)seed.reqs.size(), ni = (int)iter.reqs.size();
+    // test hook: this round's bulk validate withholds its copies (its waits run out)
+    prm.withhold = ni > 0 && c->bulk_validate && c->cfg.inject_wait_timeout > 0 &&
+                   ++c->iter_rounds == c->cfg.inject_wait_timeout;
     if (ns > 0) {
         CKQ(Lr.run(STEREO_K_CENSUS, ns, seed_px * 10.125, [&] { return launch_census(batch_of(seed, WK_CENSUS), prm, s); }));
         CKQ(Lr.run(STEREO_K_FAST_SCORE, ns, seed_px * 3.0, [&] { return launch_fast_score(batch_of(seed, WK_FAST_SCORE), prm, s); }));
@@ -1425,6 +1429,7 @@ int stereo_create(const stereo_config* cfg, stereo_ctx** out) {
         c->bulk_validate = std::strcmp(v, "bulk") == 0;
         c->tune.validate_mixed = std::strcmp(v, "classes") != 0;
     }
+    if (cfg->inject_wait_timeout > 0) c->bulk_validate = true;
     if (prepare_kernels() != cudaSuccess) c->bulk_validate = false;
     if (cfg->autotune) {  // before the scheduler starts: the tuning round owns the stream
         const Tuning keep = c->tune;

@@ -76,6 +76,7 @@ struct PairBatch {
 struct Params {
     int t_lo, t_hi, t_grad, t_fast, K, margin;
     int* err;  // device flag set when a bounded device-side wait gave up (may be null)
+    int withhold;  // testing: the bulk-copy validate's producer issues nothing, so every bounded wait runs out
 };
 
 // Work items per pair for each kernel kind.
@@ -97,7 +98,7 @@ cudaError_t launch_raster(const PairBatch& b, cudaStream_t s);
 // tri_rows needs T + 1 entries; small_tri T + 1 entries followed by
 // 2 * ceil(T / 1024) entries of block offsets
 cudaError_t launch_raster_device_lists(const PairDev& p, cudaStream_t s);
-inline size_t raster_list_words(int T) { return 2 * ((size_t)T + 1) + 2 * (((size_t)T + 1023) / 1024); }
+constexpr size_t raster_list_words(int T) { return 2 * ((size_t)T + 1) + 2 * (((size_t)T + 1023) / 1024); }
 // Fused validate: one kernel variant per cell-side class; a pair has work
 // only under its own class, validate_kind(p): WK_VALIDATE (no cells, or
 // 8 | sz), WK_VALIDATE_UNIT (sz 1), WK_VALIDATE_C4 (sz 4), WK_VALIDATE_C2
@@ -125,6 +126,9 @@ cudaError_t launch_match_list(const uint32_t* cL, const uint32_t* cR, int W, int
                               int32_t* out, cudaStream_t s);
 
 int sm_count();
+// Frame sizes every entry point accepts: 5 <= W, H <= 8192 and W * H < 2^27
+// (pixel indices fit the 27-bit index field of the cell keys).
+bool valid_size(int w, int h);
 
 // Host mesh step (mesh.cpp).
 int delaunay(const int32_t* uv, int n, int32_t* tri, int cap);

@@ -1201,7 +1201,7 @@ constexpr int kBRowF = 160;                  // bytes per staged C_f row
 constexpr int kBRowO = 8;                    // words per staged Omega_I row
 constexpr int kBRowR = 264;                  // words per staged right-census window row
 constexpr int kBWinMax = kBRowR - 8;         // widest column range staged
-constexpr unsigned kSpinLimit = 1u << 24;    // about a second with the back-off below
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // a bounded wait gives up after one second
 
 // Pair descriptor and local work index of a batch item.
 __device__ __forceinline__ const PairDev& item_pair(const PairBatch& b, int item, int& local) {
@@ -1250,22 +1250,34 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, u
 __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
     asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test_wait(unsigned long long* bar, unsigned parity) {
     unsigned ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the completion of the phase with the given parity.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the completion of the phase with the given parity: gives
+// up (false) after kWaitLimitNs of wall time on the GPU's global timer, so
+// the bound does not depend on how long one poll takes.
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-    for (unsigned i = 0; i < kSpinLimit; i++) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (i > 32) __nanosleep(64);
+    if (mbar_test_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned i = 0;; i++) {
+        if (mbar_test_wait(bar, parity)) return true;
+        if (i > 32) {
+            __nanosleep(64);
+            if (global_ns() - t0 > kWaitLimitNs) return false;
+        }
     }
-    return false;
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -1303,6 +1315,7 @@ __device__ __forceinline__ void plan_row(const void* base, size_t ntot, int es, 
 
 __device__ __forceinline__ void bulk_producer(const PairBatch& b, const Params& prm, BulkSmem& sm) {
     const int lane = threadIdx.x & 31;
+    if (prm.withhold) return;  // testing: no copy is issued, no stage released, so the consumers' waits run out
     int k = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < b.total; item += gridDim.x, k++) {

@@ -49,6 +49,30 @@ def test_injected_host_failure_is_reported_and_isolated():
                 assert torch.equal(o[k], want[k])
 
 
+def test_device_wait_timeout_is_reported_and_context_recovers():
+    """A bounded device-side wait that runs out: in the context's first GPU
+    round with an iteration stage, the bulk-copy validate's producer issues no
+    copy, so its consumers give up after a second and set the error flag.  The
+    request fails with STEREO_E_TIMEOUT (-5) in seconds, and the next request
+    on the same context equals its solo result."""
+    import time
+    pairs = _pairs(2)
+    with S.Context(mem_budget_bytes=1 << 28, max_slots=1, inject_wait_timeout=1, **PRM) as ctx:
+        t0 = time.time()
+        tk = ctx.submit(pairs[0].left, pairs[0].right, 320, 240, pairs[0].dmax, pairs[0].iters, pairs[0].cell)
+        with pytest.raises(S.StereoError) as e:
+            ctx.poll(tk)
+        assert e.value.code == -5
+        assert time.time() - t0 < 30
+        ctx.release(tk)
+        tk = ctx.submit(pairs[1].left, pairs[1].right, 320, 240, pairs[1].dmax, pairs[1].iters, pairs[1].cell)
+        got = ctx.result_tensors(ctx.poll(tk))
+        ctx.release(tk)
+    want = _solo(pairs[1])
+    for k in ("D_f", "C_f", "mask", "planeidx"):
+        assert torch.equal(got[k], want[k])
+
+
 def test_queue_full_returns_busy_then_drains():
     pairs = _pairs(8, 1242, 375)
     got_busy = 0
