@@ -255,6 +255,25 @@ int stereo_delaunay(const int32_t* uv, int n, int32_t* tri, int cap);
  * workers at the end of a burst. */
 int stereo_delaunay_parallel(const int32_t* uv, int n, int32_t* tri, int cap, int threads);
 
+/* The re-tessellation between passes on the device (Alg. 1: the
+ * DelaunayTriangulation of S_{it+1} = S_it + the new points of a resampling,
+ * Alg. 4): the points are inserted into the given triangulation of S_it and
+ * the mesh is flipped to the triangulation stereo_delaunay defines, on the
+ * GPU, as the engine does between passes.  uv: n >= 3 (u, v) pairs in
+ * canonical order and tri: T sorted index triples, the triangulation
+ * stereo_delaunay returns for them (host).  uv_new (host): m (u, v) pixels of
+ * a w x h frame, each covered by the old mesh's plane-index map (inside its
+ * hull, or on a top or left hull edge: the pixels a pass can evaluate); a
+ * pixel already in uv, or repeated, is skipped (an existing point keeps its
+ * pixel).  tri_out (host): up to cap sorted index triples in ascending
+ * order, indices into the union sorted by (v, u).  Synchronous; allocates
+ * and frees device memory of its own on the current device.  Returns the
+ * triangle count, or STEREO_E_INVAL (arguments, or a new point outside the
+ * old mesh), STEREO_E_CAP (cap too small; 2 (n + m) suffices),
+ * STEREO_E_NOMEM, STEREO_E_CUDA or STEREO_E_INTERNAL. */
+int stereo_delaunay_insert(const int32_t* uv, int n, const int32_t* tri, int T, const int32_t* uv_new, int m,
+                           int w, int h, int32_t* tri_out, int cap);
+
 /* Disparity plane d = a*u + b*v + c per triangle (Eq. 3, "solving a linear
  * system"; host, synchronous): Cramer's rule in fp64 over the vertices in
  * index order, rounded to fp32.  d: n fp32 support disparities; abc: 3*T. */

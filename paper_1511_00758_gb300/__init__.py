@@ -14,7 +14,7 @@ from . import _build
 
 __all__ = [
     "StereoError", "load", "lib", "Config", "Result", "Stats", "Tuning", "Context",
-    "census", "fast", "epipolar_match", "delaunay", "delaunay_parallel", "planes", "raster_scratch_bytes", "raster", "raster_noalloc", "validate_bulk",
+    "census", "fast", "epipolar_match", "delaunay", "delaunay_parallel", "delaunay_insert", "planes", "raster_scratch_bytes", "raster", "raster_noalloc", "validate_bulk",
     "validate", "resample_match", "ERRORS",
 ]
 
@@ -84,6 +84,7 @@ _SIGS = {
     "stereo_epipolar_match": (_I, [_P, _P, _I, _I, _P, _I, _I, _I, _I, _P, _P]),
     "stereo_delaunay": (_I, [_P, _I, _P, _I]),
     "stereo_delaunay_parallel": (_I, [_P, _I, _P, _I, _I]),
+    "stereo_delaunay_insert": (_I, [_P, _I, _P, _I, _P, _I, _I, _I, _P, _I]),
     "stereo_planes": (_I, [_P, _P, _P, _I, _P]),
     "stereo_raster_scratch_bytes": (ctypes.c_size_t, [_I]),
     "stereo_raster": (_I, [_P, _P, _I, _I, _I, _P, _P, _P, ctypes.c_size_t, _P]),
@@ -170,6 +171,12 @@ def delaunay(uv, n, tri, cap):
 def delaunay_parallel(uv, n, tri, cap, threads):
     """Host call, as delaunay, with the top splits on up to `threads` host threads."""
     return _check(lib().stereo_delaunay_parallel(_ptr(uv), n, _ptr(tri), cap, threads), "delaunay_parallel")
+
+
+def delaunay_insert(uv, n, tri, T, uv_new, m, w, h, tri_out, cap):
+    """Device re-tessellation: the triangulation of uv + uv_new by insertion into (uv, tri) (host arrays)."""
+    return _check(lib().stereo_delaunay_insert(_ptr(uv), n, _ptr(tri), T, _ptr(uv_new), m, w, h, _ptr(tri_out), cap),
+                  "delaunay_insert")
 
 
 def planes(uv, d, tri, T, abc):

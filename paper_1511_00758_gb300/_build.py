@@ -26,7 +26,8 @@ def _cuda_home():
 
 
 def _sources():
-    return [os.path.join(CSRC, f) for f in ("kernels.cu", "noalloc.cu", "mesh.cpp", "engine.cpp", "internal.h")] + \
+    return [os.path.join(CSRC, f) for f in ("kernels.cu", "retess.cu", "noalloc.cu", "mesh.cpp", "engine.cpp",
+                                              "internal.h")] + \
            [os.path.join(ROOT, "include", "stereo.h")]
 
 
@@ -48,6 +49,9 @@ def build(force=False, verbose=False):
     jobs = {
         "kernels.o": [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
                       "-Xptxas", "-warn-spills", *inc, "-c", os.path.join(CSRC, "kernels.cu")],
+        # the plane solve uses explicitly rounded fp64 operations (no contraction)
+        "retess.o": [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+                     "-Xptxas", "-warn-spills", *inc, "-c", os.path.join(CSRC, "retess.cu")],
         "noalloc.o": [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", *inc,
                       "-c", os.path.join(CSRC, "noalloc.cu")],
         # the plane solve is a fixed fp64 expression: no contraction into FMAs

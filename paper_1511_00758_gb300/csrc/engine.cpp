@@ -1738,6 +1738,153 @@ int stereo_delaunay_parallel(const int32_t* uv, int n, int32_t* tri, int cap, in
 }
 
 
+namespace {
+// k_mesh_pass's occupancy, looked up once per device (outside any capture).
+std::mutex g_mesh_mu;
+unsigned long long g_mesh_ready = 0;  // bit per device ordinal
+cudaError_t ensure_mesh_kernels() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(g_mesh_mu);
+    if (dev < 64 && (g_mesh_ready >> dev) & 1ull) return cudaSuccess;
+    e = prepare_mesh_kernels();
+    if (e == cudaSuccess && dev < 64) g_mesh_ready |= 1ull << dev;
+    return e;
+}
+}  // namespace
+
+int stereo_delaunay_insert(const int32_t* uv, int n, const int32_t* tri, int T, const int32_t* uv_new, int m, int w,
+                           int h, int32_t* tri_out, int cap) {
+    if (!tri || T < 1 || n < 3 || m < 0 || (m > 0 && !uv_new) || !valid_size(w, h) || cap < 0 || (cap > 0 && !tri_out))
+        return STEREO_E_INVAL;
+    if (check_canonical(uv, n, tri_out, cap) != STEREO_OK) return STEREO_E_INVAL;
+    for (int i = 0; i < n; i++)
+        if (uv[2 * i] >= w || uv[2 * i + 1] >= h) return STEREO_E_INVAL;
+    for (int i = 0; i < m; i++)
+        if (uv_new[2 * i] < 0 || uv_new[2 * i + 1] < 0 || uv_new[2 * i] >= w || uv_new[2 * i + 1] >= h)
+            return STEREO_E_INVAL;
+    for (int i = 0; i < 3 * T; i++)
+        if (tri[i] < 0 || tri[i] >= n) return STEREO_E_INVAL;
+    std::vector<int32_t> ccw((size_t)4 * T), opp((size_t)4 * T), tuv((size_t)6 * T);
+    mesh_adjacency(uv, tri, T, ccw.data(), opp.data());
+    for (int t = 0; t < T; t++)
+        for (int k = 0; k < 3; k++) {
+            tuv[6 * (size_t)t + 2 * k] = uv[2 * tri[3 * t + k]];
+            tuv[6 * (size_t)t + 2 * k + 1] = uv[2 * tri[3 * t + k] + 1];
+        }
+    const int n_cap = n + m, t_cap = 2 * n_cap + 8, p_cap = m > 0 ? m : 1;
+    const size_t N = (size_t)w * h;
+    const size_t b_mesh = align_up(mesh_bytes(w, h, n_cap, t_cap, p_cap), 256);
+    const size_t b_pos = align_up(8 * (size_t)n, 256), b_d = align_up(4 * (size_t)n, 256);
+    const size_t b_tri = align_up(16 * (size_t)T, 256), b_list = align_up(8 * (size_t)p_cap, 256);
+    const size_t b_tuv = align_up(24 * (size_t)T, 256), b_pidx = align_up(4 * N, 256);
+    const size_t b_scr = align_up(4 * raster_list_words(T), 256), b_md = align_up(sizeof(MeshDev), 256);
+    const size_t total = b_mesh + b_pos + b_d + 2 * b_tri + b_list + b_tuv + b_pidx + b_scr + b_md + 256;
+    if (ensure_mesh_kernels() != cudaSuccess) return STEREO_E_CUDA;
+    char* base = nullptr;
+    cudaStream_t s = nullptr;
+    int rc = STEREO_OK;
+    if (cudaMalloc((void**)&base, total) != cudaSuccess) {
+        cudaGetLastError();
+        return STEREO_E_NOMEM;
+    }
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaFree(base);
+        cudaGetLastError();
+        return STEREO_E_CUDA;
+    }
+    char* q = base;
+    auto take = [&](size_t b) { char* r = q; q += b; return r; };
+    char* mesh = take(b_mesh);
+    int32_t* d_pos = (int32_t*)take(b_pos);
+    float* d_d = (float*)take(b_d);
+    int4* d_tri = (int4*)take(b_tri);
+    int4* d_opp = (int4*)take(b_tri);
+    int32_t* d_list = (int32_t*)take(b_list);
+    int32_t* d_tuv = (int32_t*)take(b_tuv);
+    int32_t* d_pidx = (int32_t*)take(b_pidx);
+    int32_t* d_scr = (int32_t*)take(b_scr);
+    MeshDev* d_md = (MeshDev*)take(b_md);
+    MeshCtl* d_ctl = (MeshCtl*)take(256);
+    MeshDev md{};
+    mesh_carve(md, mesh, w, h, n_cap, t_cap, p_cap);
+    md.seed_pos = d_pos;
+    md.seed_d = d_d;
+    md.seed_tri = d_tri;
+    md.seed_opp = d_opp;
+    md.seed_n = n;
+    md.seed_T = T;
+    md.list_uv = d_list;
+    md.list_n = m;
+    md.planeidx = d_pidx;
+    md.pass = 2;
+    md.canonical = 1;
+    md.small_area = kSmallArea;
+    md.cols = kRasterCols;
+    PairDev p{};
+    p.W = w;
+    p.H = h;
+    p.T = T;
+    p.tri_uv = d_tuv;
+    p.tri_rows = d_scr;
+    p.small_tri = d_scr + T + 1;
+    p.n_hull = -1;
+    p.planeidx = d_pidx;
+    PairBatch clear{};
+    clear.one = p;
+    clear.npairs = 1;
+    clear.total = work_items(WK_CLEAR, p);
+    cudaError_t e = cudaMemcpyAsync(d_pos, uv, 8 * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_d, 0, 4 * (size_t)n, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tri, ccw.data(), 16 * (size_t)T, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_opp, opp.data(), 16 * (size_t)T, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(d_list, uv_new, 8 * (size_t)m, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tuv, tuv.data(), 24 * (size_t)T, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_md, &md, sizeof(MeshDev), cudaMemcpyHostToDevice, s);
+    // the old mesh's plane-index map locates the new points, as a pass's raster does in the engine
+    if (e == cudaSuccess) e = launch_raster_clear(clear, s);
+    if (e == cudaSuccess) e = launch_raster_device_lists(p, s);
+    if (e == cudaSuccess) e = launch_mesh_pass(d_md, 1, d_ctl, s);
+    MeshHdr hd{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hd, md.hdr, sizeof(MeshHdr), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        note_error(e, "stereo_delaunay_insert", __LINE__);
+        rc = STEREO_E_CUDA;
+    } else if (hd.err == 2) {
+        rc = STEREO_E_INVAL;  // a new point outside the raster's cover of the old mesh
+    } else if (hd.err != 0) {
+        rc = STEREO_E_INTERNAL;
+    } else if (hd.T > cap) {
+        rc = STEREO_E_CAP;
+    } else {
+        std::vector<int4> t4(hd.T);
+        std::vector<int32_t> perm(hd.T), rank(hd.n);
+        e = cudaMemcpyAsync(t4.data(), md.tri, 16 * (size_t)hd.T, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(perm.data(), md.tperm, 4 * (size_t)hd.T, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rank.data(), md.vrank, 4 * (size_t)hd.n, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            note_error(e, "stereo_delaunay_insert copy back", __LINE__);
+            rc = STEREO_E_CUDA;
+        } else {
+            for (int i = 0; i < hd.T; i++) {
+                const int4 tt = t4[perm[i]];
+                int r[3] = {rank[tt.x], rank[tt.y], rank[tt.z]};
+                std::sort(r, r + 3);
+                tri_out[3 * i] = r[0];
+                tri_out[3 * i + 1] = r[1];
+                tri_out[3 * i + 2] = r[2];
+            }
+            rc = hd.T;
+        }
+    }
+    cudaStreamDestroy(s);
+    cudaFree(base);
+    return rc;
+}
+
 int stereo_planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float* abc) {
     if (T < 0 || (T > 0 && (!uv || !d || !tri || !abc))) return STEREO_E_INVAL;
     planes(uv, d, tri, T, abc);

@@ -130,6 +130,101 @@ int sm_count();
 // (pixel indices fit the 27-bit index field of the cell keys).
 bool valid_size(int w, int h);
 
+// ---------------------------------------------------------------- device mesh (retess.cu)
+// The triangulation G(S_it) of a pair kept on the device between passes:
+// after a pass's resampling, the new support points are inserted into it and
+// the mesh is flipped back to the unique triangulation of reading 6, its
+// planes and raster lists are built for the next pass, all on the GPU.
+constexpr int kMeshBatch = 64;      // pairs per mesh launch
+constexpr int kMeshClasses = 7;     // small-triangle box width classes: 1, 2, <=4, <=8, <=16, <=32, wider
+
+// Counters of one pair's device mesh (device memory).
+struct MeshHdr {
+    int n, T;                        // vertices, triangles
+    int n_new;                       // points of this pass waiting for insertion (pending entries)
+    int n_small, n_large, n_items, n_hull;  // raster lists of the mesh
+    int cls[kMeshClasses];           // small triangles per box width class
+    int cls_fill[kMeshClasses];
+    int stamp;                       // last stamp of the split / flip records
+    int err;                         // nonzero: 1 capacity, 2 a point not found in its triangle, 3 round limit
+    int rounds, flips;               // insertion rounds and flips of the last pass
+    int pad[2];
+};
+
+struct MeshDev {
+    // vertices (slot order: as inserted)
+    int2* pos;                // (u, v)
+    float* vd;                // support disparity
+    uint8_t* vpass;           // iteration the point joined the support set (1-based)
+    int* vrank;               // canonical index (rank in (v, u) order), when ranked
+    int4* vcanon;             // (u, v, d bits, pass) in canonical order, when ranked
+    uint32_t* occ;            // W*H bits: pixel holds a vertex
+    uint32_t* wpre;           // exclusive prefix of popcount(occ) per word
+    // triangles (slot order)
+    int4* tri;                // vertex slots (a, b, c) with positive orientation
+    int4* opp;                // per edge k (opposite vertex k): (t << 2) | j of the neighbour's twin edge, -1 on the hull
+    unsigned long long* claim;  // insertion / flip claims (all ~0 between rounds)
+    int4* smap;               // split / flip record: (stamp, new ref of old edge 0, 1, 2)
+    unsigned long long* tkey; // canonical key (i << 42 | j << 21 | k), when ranked
+    int* gcnt;                // triangles per smallest canonical vertex, then their prefix [n_cap + 1]
+    int* tperm;               // canonical triangle order: position -> slot
+    int* pend;                // pending vertex slots of this pass
+    int* ploc;                // their current triangle (-1 once inserted, -2 - t while the round that inserted
+                              // it into t links its pieces)
+    int* pnb;                 // the edge a pending point lies on: -1 inside, else
+                              // ((neighbour + 1) << 4) | (twin edge << 2) | edge
+    int* scan;                // scan scratch: chunk totals [scan_cap]
+    int* large;               // large-triangle list (triangle ids of the raster) and item prefix [t_cap + 1]
+    int* lrows;
+    // raster inputs of the next pass (triangle id = slot, or canonical position)
+    int32_t* tri_uv;          // 6 int32 per triangle
+    float* abc;               // 3 fp32 per triangle
+    int32_t* small;           // small triangles by width class
+    int32_t* hull;            // directed hull edges (ax, ay, bx, by)
+    MeshHdr* hdr;
+    int n_cap, t_cap, p_cap, scan_cap;
+    int W, H;
+    // the pass's new points: from cell records (engine) or a point list (stage entry)
+    const uint32_t* cg_key;
+    const float* cg_d;
+    const uint32_t* cb_key;
+    const int32_t* x_d;
+    int ncells;
+    const int32_t* list_uv;
+    int list_n;
+    const int32_t* planeidx;  // the pass's plane-index map (triangle slot per pixel)
+    // seed mesh to take over (first device pass), in the host staging layout
+    const int32_t* seed_pos;  // n (u, v)
+    const float* seed_d;
+    const int4* seed_tri;     // T (a, b, c, -) positive orientation, canonical order
+    const int4* seed_opp;
+    int seed_n, seed_T;       // > 0: take the seed mesh over first
+    int pass;                 // iteration the new points join
+    int canonical;            // the next pass is the last: canonical triangle order and vertex ranks
+    int small_area, cols;     // raster work shapes
+};
+
+// Bytes of one pair's device mesh for the given capacities, and the carving
+// of a block of that size (256-byte aligned arrays).
+size_t mesh_bytes(int W, int H, int n_cap, int t_cap, int p_cap);
+void mesh_carve(MeshDev& m, void* block, int W, int H, int n_cap, int t_cap, int p_cap);
+// Vertex capacity of a request: the seed keypoints plus two points per cell
+// of every pass that resamples, at most one per pixel.
+int mesh_vertex_cap(int W, int H, int seed_points, int iters, int cell);
+// One pass of mesh work for up to kMeshBatch pairs (device descriptors md[np]):
+// take over seed meshes, collect and insert the new points, flip to the
+// triangulation, rank canonically where asked, build the next raster inputs.
+// One cooperative launch (grid-wide barriers between its phases).
+struct MeshCtl {                     // grid-wide counters of one mesh launch (device memory)
+    unsigned long long total_new, inserted, flips;
+    int err, rounds;
+};
+cudaError_t launch_mesh_pass(const MeshDev* md, int np, MeshCtl* ctl, cudaStream_t s);
+// Raster of device meshes: PairBatch b lists the pairs (their PairDev:
+// outputs, cells), md the same pairs' meshes (counts read on the device).
+cudaError_t launch_raster_mesh(const PairBatch& b, const MeshDev* md, cudaStream_t s);
+cudaError_t prepare_mesh_kernels();
+
 // Host mesh step (mesh.cpp).
 int delaunay(const int32_t* uv, int n, int32_t* tri, int cap);
 // Also returns the directed hull edges (org, dest vertex index pairs, the
@@ -143,6 +238,11 @@ using Spawn = std::function<void(std::function<void()>)>;
 int delaunay(const int32_t* uv, int n, int32_t* tri, int cap, int32_t* hull, int* n_hull, int depth = 0,
              const Spawn* spawn = nullptr);
 void planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float* abc);
+// Positively oriented vertex order (ccw: 4 int32 per triangle, the fourth 0)
+// and the neighbour across each edge (opp: 4 int32 per triangle; edge e joins
+// vertices e + 1 and e + 2, entry (s << 2) | e' names the twin edge e' of
+// triangle s, -1 on the hull) of a triangle list.
+void mesh_adjacency(const int32_t* uv, const int32_t* tri, int T, int32_t* ccw, int32_t* opp);
 // Raster work lists of a mesh: small[] the triangles whose clipped bounding
 // box has at most kSmallArea pixels (returns their count in *n_small), and,
 // when small_box is given, each one's box area (at least 1) in the same

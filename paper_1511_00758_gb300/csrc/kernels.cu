@@ -747,6 +747,92 @@ __global__ void __launch_bounds__(256) k_raster(PairBatch b) {
 #undef BODY
 }
 
+// Raster of meshes built on the device (the re-tessellation between passes):
+// the lists and their sizes come from each pair's mesh header.  Work of a
+// pair, in blocks: small triangles 256 to a block (32 per warp, in box width
+// class order), large-triangle work items 8 to a block (one per warp; the
+// item's triangle found by binary search of the item prefix), hull row
+// clears 8 rows to a block, then the resets of the pass's cell records.
+__device__ __forceinline__ int raster_mesh_blocks(const PairDev& P, const MeshDev& M) {
+    const MeshHdr& h = *M.hdr;
+    return (h.n_small + 255) / 256 + (h.n_items + 7) / 8 + (P.H + 7) / 8 +
+           (P.cg_key ? (P.Wc * P.Hc + kFillCells - 1) / kFillCells : 0);
+}
+
+__global__ void __launch_bounds__(256) k_raster_mesh(const PairDev* __restrict__ pd, const MeshDev* __restrict__ md,
+                                                     int np) {
+    __shared__ SmallTri s[256];
+    __shared__ int pre[kMeshBatch + 1];
+    if (threadIdx.x < 32) {  // prefix of the pairs' block counts (np <= 64)
+        const int l = threadIdx.x;
+        int s0 = l < np ? raster_mesh_blocks(pd[l], md[l]) : 0;
+        int s1 = l + 32 < np ? raster_mesh_blocks(pd[l + 32], md[l + 32]) : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x0 = __shfl_up_sync(0xffffffffu, s0, o), x1 = __shfl_up_sync(0xffffffffu, s1, o);
+            if (l >= o) {
+                s0 += x0;
+                s1 += x1;
+            }
+        }
+        const int tot0 = __shfl_sync(0xffffffffu, s0, 31);
+        if (l == 0) pre[0] = 0;
+        pre[l + 1] = s0;
+        pre[l + 33] = tot0 + s1;
+    }
+    __syncthreads();
+    const int total = pre[np];
+    const int w = threadIdx.x >> 5;
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        int p = 0, hi = np - 1;
+        while (p < hi) {
+            const int mid = (p + hi + 1) >> 1;
+            if (pre[mid] <= item) p = mid;
+            else hi = mid - 1;
+        }
+        int local = item - pre[p];
+        const PairDev& P = pd[p];
+        const MeshDev& M = md[p];
+        const int n_small = M.hdr->n_small, n_items = M.hdr->n_items;
+        const int nsb = (n_small + 255) / 256, ncb = (n_items + 7) / 8, nhb = (P.H + 7) / 8;
+        if (local < nsb) {
+            const int i0 = local * 256 + w * 32;
+            const int n = min(32, n_small - i0);
+            if (n > 0) raster_small_warp(M.tri_uv, M.abc, M.small + i0, n, P.W, P.H, P.planeidx, P.Dit, s + w * 32);
+            continue;
+        }
+        local -= nsb;
+        if (local < ncb) {
+            const int it = local * 8 + w;
+            if (it < n_items) {
+                int lo = 0, up = M.hdr->n_large - 1;  // the last large triangle whose first item is <= it
+                while (lo < up) {
+                    const int mid = (lo + up + 1) >> 1;
+                    if (__ldg(M.lrows + mid) <= it) lo = mid;
+                    else up = mid - 1;
+                }
+                raster_chunk_tc(M.tri_uv, M.abc, __ldg(M.large + lo), it - __ldg(M.lrows + lo), P.W, P.H, P.planeidx,
+                                P.Dit, M.cols);
+            }
+            continue;
+        }
+        local -= ncb;
+        if (local < nhb) {
+            const int v = local * 8 + w;
+            if (v < P.H) hull_row_clear(M.hull, M.hdr->n_hull, v, P.W, P.planeidx, P.Dit);
+            continue;
+        }
+        fill_cells_range(P, local - nhb);
+    }
+}
+
+cudaError_t launch_raster_mesh(const PairBatch& b, const MeshDev* md, cudaStream_t s) {
+    if (b.npairs <= 0) return cudaSuccess;
+    if (b.npairs > kMeshBatch || !b.pd) return cudaErrorInvalidValue;
+    k_raster_mesh<<<sm_count() * 8, 256, 0, s>>>(b.pd, md, b.npairs);
+    return cudaGetLastError();
+}
+
 // Device-built work lists for callers without a host copy of the triangles,
 // in three launches over blocks of 1024 triangles: per-block totals, a scan
 // of the block totals, then each block's exclusive scan written out.

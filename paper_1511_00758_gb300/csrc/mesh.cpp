@@ -542,6 +542,37 @@ void planes(const int32_t* uv, const float* d, const int32_t* tri, int T, float*
     }
 }
 
+void mesh_adjacency(const int32_t* uv, const int32_t* tri, int T, int32_t* ccw, int32_t* opp) {
+    // every edge once per side: (smaller vertex, larger vertex) -> (t << 2) | e
+    std::vector<std::pair<uint64_t, int32_t>> half((size_t)3 * T);
+    for (int t = 0; t < T; t++) {
+        int a = tri[3 * t], b = tri[3 * t + 1], c = tri[3 * t + 2];
+        const int64_t o = (int64_t)(uv[2 * b] - uv[2 * a]) * (uv[2 * c + 1] - uv[2 * a + 1]) -
+                          (int64_t)(uv[2 * b + 1] - uv[2 * a + 1]) * (uv[2 * c] - uv[2 * a]);
+        if (o < 0) std::swap(b, c);  // positive orientation
+        const int v[3] = {a, b, c};
+        ccw[4 * t] = a;
+        ccw[4 * t + 1] = b;
+        ccw[4 * t + 2] = c;
+        ccw[4 * t + 3] = 0;
+        opp[4 * t + 3] = 0;
+        for (int e = 0; e < 3; e++) {  // edge e joins v[e + 1] and v[e + 2]
+            const uint32_t x = (uint32_t)v[(e + 1) % 3], y = (uint32_t)v[(e + 2) % 3];
+            const uint64_t key = x < y ? ((uint64_t)x << 32) | y : ((uint64_t)y << 32) | x;
+            half[(size_t)3 * t + e] = {key, (t << 2) | e};
+            opp[4 * t + e] = -1;
+        }
+    }
+    std::sort(half.begin(), half.end());
+    for (size_t i = 0; i + 1 < half.size(); i++)
+        if (half[i].first == half[i + 1].first) {
+            const int32_t r0 = half[i].second, r1 = half[i + 1].second;
+            opp[4 * (r0 >> 2) + (r0 & 3)] = r1;
+            opp[4 * (r1 >> 2) + (r1 & 3)] = r0;
+            i++;
+        }
+}
+
 int raster_lists(const int32_t* q, int T, int W, int H, int32_t* rows, int32_t* small, int* n_small, int small_area,
                  int cols, int32_t* small_box) {
     // small triangles are listed by box width class, then by box area (a

@@ -1,0 +1,914 @@
+// On-device re-tessellation between passes (Alg. 1: DelaunayTriangulation of
+// S_{it+1} after SupportResampling), planes (Eq. 3) and the raster inputs of
+// the next pass.
+//
+// S_{it+1} = S_it + the pass's new points, and every new point is a pixel
+// that the pass evaluated, so it lies in the closed hull of G(S_it) and the
+// pass's own plane-index map names a triangle that contains it.  The mesh of
+// the previous pass therefore stays on the device and the new points are
+// inserted into it, in rounds: every pending point claims the triangle it
+// lies in (and the neighbour, when it lies on an edge); a point that holds
+// all its claims splits them (1 -> 3 inside a triangle, 2 -> 4 on an inner
+// edge, 1 -> 2 on a hull edge), and the points left in a split triangle move
+// to the piece that contains them.  Then Lawson flips restore the Delaunay
+// property: an edge whose opposite vertex lies inside the circle of the
+// triangle is flipped, each triangle in at most one flip per round, until no
+// edge is illegal.  The orientation test is exact in int64 and the in-circle
+// test is the same symbolically perturbed one as the host triangulation
+// (Edelsbrunner & Muecke's Simulation of Simplicity on the lifted coordinate,
+// a point earlier in (v, u) order carrying the larger perturbation); with it
+// every flip is valid and the flips end at the unique triangulation of the
+// perturbed point set, the one the host routine returns.
+//
+// Before the last pass the triangles are put in canonical order (rank of
+// the sorted canonical vertex triple), the ranks of the vertices coming from
+// a W x H bit map of the vertex pixels: the canonical index of (u, v) is the
+// number of vertex pixels before it in raster order, which is (v, u) order.
+//
+// Everything runs in one cooperative launch per pass over up to kMeshBatch
+// pairs; grid-wide barriers separate the phases and every loop decision is
+// read after a barrier, so all blocks take it alike.  Loops are bounded: a
+// pair that does not finish sets its error code.
+#include <cooperative_groups.h>
+
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace stereo {
+
+namespace {
+
+constexpr int kMeshThreads = 256;
+constexpr int kMaxInsertRounds = 4096;
+constexpr int kMaxFlipRounds = 1 << 15;
+constexpr int kScanChunk = 1024;  // elements per warp in the two-level scans
+constexpr unsigned long long kNoClaim = ~0ull;
+
+size_t al(size_t x) { return (x + 255) / 256 * 256; }
+
+__device__ __forceinline__ uint32_t vkey(int2 p) { return ((uint32_t)p.y << 14) | (uint32_t)p.x; }
+
+__device__ __forceinline__ long long orient(int2 a, int2 b, int2 c) {
+    return (long long)(b.x - a.x) * (c.y - a.y) - (long long)(b.y - a.y) * (c.x - a.x);
+}
+
+// d strictly inside the circle of the positively oriented (a, b, c), in the
+// perturbed configuration: at an exact tie the sign is that of the cofactor
+// of the lifted entry of the point earliest in (v, u) order, then the next.
+__device__ __forceinline__ bool incircle_sos(int2 a, int2 b, int2 c, int2 d) {
+    const long long ax = a.x - d.x, ay = a.y - d.y;
+    const long long bx = b.x - d.x, by = b.y - d.y;
+    const long long cx = c.x - d.x, cy = c.y - d.y;
+    const long long la = ax * ax + ay * ay, lb = bx * bx + by * by, lc = cx * cx + cy * cy;
+    const long long det = la * (bx * cy - by * cx) - lb * (ax * cy - ay * cx) + lc * (ax * by - ay * bx);
+    if (det != 0) return det > 0;
+    uint32_t k[4] = {vkey(a), vkey(b), vkey(c), vkey(d)};
+    for (int r = 0; r < 4; r++) {
+        int m = 0;
+        for (int j = 1; j < 4; j++)
+            if (k[j] < k[m]) m = j;
+        long long cof;
+        switch (m) {
+            case 0: cof = orient(b, c, d); break;
+            case 1: cof = -orient(a, c, d); break;
+            case 2: cof = orient(a, b, d); break;
+            default: cof = -orient(a, b, c); break;
+        }
+        if (cof != 0) return cof > 0;
+        k[m] = 0xFFFFFFFFu;
+    }
+    return false;
+}
+
+__device__ __forceinline__ int vtx(const int4& t, int k) { return k == 0 ? t.x : k == 1 ? t.y : t.z; }
+__device__ __forceinline__ int& vtx(int4& t, int k) { return k == 0 ? t.x : k == 1 ? t.y : t.z; }
+__device__ __forceinline__ int ref_of(const int4& r, int k) { return k == 0 ? r.x : k == 1 ? r.y : r.z; }
+__device__ __forceinline__ int& ref_of(int4& r, int k) { return k == 0 ? r.x : k == 1 ? r.y : r.z; }
+__device__ __forceinline__ int smap_ref(const int4& s, int k) { return k == 0 ? s.y : k == 1 ? s.z : s.w; }
+__device__ __forceinline__ int mk_ref(int t, int e) { return (t << 2) | e; }
+
+// q in the closed triangle t (all three edge functions >= 0)
+__device__ __forceinline__ bool contains(const int2* __restrict__ pos, const int4& t, int2 q) {
+    const int2 a = pos[t.x], b = pos[t.y], c = pos[t.z];
+    return orient(b, c, q) >= 0 && orient(c, a, q) >= 0 && orient(a, b, q) >= 0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- sizes
+int mesh_vertex_cap(int W, int H, int seed_points, int iters, int cell) {
+    long long n = seed_points;
+    int sz = cell;
+    for (int it = 1; it < iters; it++) {
+        n += 2ll * ((W + sz - 1) / sz) * ((H + sz - 1) / sz);
+        sz = sz / 2 > 1 ? sz / 2 : 1;
+    }
+    const long long px = (long long)W * H;
+    return (int)(n < px ? n : px);
+}
+
+namespace {
+__host__ __device__ __forceinline__ int scan_chunks(int n) { return (n + kScanChunk - 1) / kScanChunk; }
+int scan_cap_of(int W, int H, int n_cap, int t_cap) {
+    const int words = (int)(((long long)W * H + 31) / 32);
+    int m = words > n_cap + 1 ? words : n_cap + 1;
+    if (t_cap + 1 > m) m = t_cap + 1;
+    return scan_chunks(m) + 2;
+}
+}  // namespace
+
+// The arrays in carving order; size_t x[] of element counts and sizes.
+#define MESH_ARRAYS(X)                                      \
+    X(hdr, MeshHdr, 1)                                      \
+    X(pos, int2, n_cap)                                     \
+    X(vd, float, n_cap)                                     \
+    X(vpass, uint8_t, n_cap)                                \
+    X(vrank, int, n_cap)                                    \
+    X(vcanon, int4, n_cap)                                  \
+    X(occ, uint32_t, words)                                 \
+    X(wpre, uint32_t, words + 1)                            \
+    X(tri, int4, t_cap)                                     \
+    X(opp, int4, t_cap)                                     \
+    X(claim, unsigned long long, t_cap)                     \
+    X(smap, int4, t_cap)                                    \
+    X(tkey, unsigned long long, t_cap)                      \
+    X(gcnt, int, (size_t)n_cap + 1)                         \
+    X(tperm, int, t_cap)                                    \
+    X(pend, int, p_cap)                                     \
+    X(ploc, int, p_cap)                                     \
+    X(pnb, int, p_cap)                                      \
+    X(scan, int, scap)                                      \
+    X(large, int, (size_t)t_cap + 1)                        \
+    X(lrows, int, (size_t)t_cap + 1)                        \
+    X(tri_uv, int32_t, (size_t)6 * t_cap)                   \
+    X(abc, float, (size_t)3 * t_cap)                        \
+    X(small, int32_t, (size_t)t_cap + 1)                    \
+    X(hull, int4, n_cap)
+
+size_t mesh_bytes(int W, int H, int n_cap, int t_cap, int p_cap) {
+    const size_t words = ((size_t)W * H + 31) / 32;
+    const int scap = scan_cap_of(W, H, n_cap, t_cap);
+    size_t b = 0;
+#define SZ(name, type, count) b += al(sizeof(type) * (size_t)(count));
+    MESH_ARRAYS(SZ)
+#undef SZ
+    return b;
+}
+
+void mesh_carve(MeshDev& m, void* block, int W, int H, int n_cap, int t_cap, int p_cap) {
+    const size_t words = ((size_t)W * H + 31) / 32;
+    const int scap = scan_cap_of(W, H, n_cap, t_cap);
+    char* p = (char*)block;
+    MeshDev z{};
+    m = z;
+#define CV(name, type, count)                     \
+    m.name = (decltype(m.name))(p);               \
+    p += al(sizeof(type) * (size_t)(count));
+    MESH_ARRAYS(CV)
+#undef CV
+    m.n_cap = n_cap;
+    m.t_cap = t_cap;
+    m.p_cap = p_cap;
+    m.scan_cap = scap;
+    m.W = W;
+    m.H = H;
+}
+
+// ---------------------------------------------------------------- phase plumbing
+namespace {
+
+__device__ __forceinline__ int words_of(const MeshDev& m) { return (int)(((long long)m.W * m.H + 31) / 32); }
+
+// Block-local exclusive prefix of the pairs' item counts (np <= 64) in
+// pre[0..np]; returns the total.  Every thread of the block calls it.
+template <class C>
+__device__ __forceinline__ int pair_prefix(int np, int* pre, C count) {
+    __syncthreads();  // pre may still be read by the previous phase
+    if (threadIdx.x < 32) {
+        const int l = threadIdx.x;
+        int s0 = l < np ? count(l) : 0;
+        int s1 = l + 32 < np ? count(l + 32) : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x0 = __shfl_up_sync(0xffffffffu, s0, o), x1 = __shfl_up_sync(0xffffffffu, s1, o);
+            if (l >= o) {
+                s0 += x0;
+                s1 += x1;
+            }
+        }
+        const int tot0 = __shfl_sync(0xffffffffu, s0, 31);
+        if (l == 0) pre[0] = 0;
+        pre[l + 1] = s0;
+        pre[l + 33] = tot0 + s1;
+    }
+    __syncthreads();
+    return pre[np];
+}
+
+__device__ __forceinline__ int pair_of(const int* pre, int np, int g) {
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// body(pair, local item) for every item, one thread each.
+template <class C, class B>
+__device__ __forceinline__ void each_item(int np, int* pre, C count, B body) {
+    const int total = pair_prefix(np, pre, count);
+    const int stride = gridDim.x * blockDim.x;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        const int p = pair_of(pre, np, g);
+        body(p, g - pre[p]);
+    }
+}
+
+// body(pair, local item) for every item, one warp each (warp-uniform).
+template <class C, class B>
+__device__ __forceinline__ void each_warp_item(int np, int* pre, C count, B body) {
+    const int total = pair_prefix(np, pre, count);
+    const int wpb = blockDim.x >> 5;
+    const int stride = gridDim.x * wpb;
+    for (int g = blockIdx.x * wpb + (threadIdx.x >> 5); g < total; g += stride) {
+        const int p = pair_of(pre, np, g);
+        body(p, g - pre[p]);
+    }
+}
+
+__device__ __forceinline__ int warp_excl_scan(int x, int& total) {
+    const int l = threadIdx.x & 31;
+    int s = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, s, o);
+        if (l >= o) s += y;
+    }
+    total = __shfl_sync(0xffffffffu, s, 31);
+    return s - x;
+}
+
+// Two-level exclusive scan of f(in[0..n)) into out[0..n) (out may be in),
+// over three phases separated by grid barriers: (A) a warp sums each chunk
+// of kScanChunk elements into chunk[c]; (B) one warp per array scans the
+// chunk sums and stores the total; (C) a warp writes each chunk's prefixes
+// (lane l owns 32 consecutive elements).
+template <class F>
+__device__ __forceinline__ void scan_a(const uint32_t* in, int n, int* chunk, int c, F f) {
+    const int l = threadIdx.x & 31;
+    const int base = c * kScanChunk;
+    int s = 0;
+    for (int i = base + l; i < base + kScanChunk && i < n; i += 32) s += f(in[i]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (l == 0) chunk[c] = s;
+}
+__device__ __forceinline__ void scan_b(int* chunk, int nch, int* total) {
+    const int l = threadIdx.x & 31;
+    int carry = 0;
+    for (int b = 0; b < nch; b += 32) {
+        const int x = b + l < nch ? chunk[b + l] : 0;
+        int tot;
+        const int e = warp_excl_scan(x, tot);
+        if (b + l < nch) chunk[b + l] = carry + e;
+        carry += tot;
+    }
+    if (l == 0 && total) *total = carry;
+}
+template <class F>
+__device__ __forceinline__ void scan_c(const uint32_t* in, uint32_t* out, int n, const int* chunk, int c, F f) {
+    const int l = threadIdx.x & 31;
+    const int i0 = c * kScanChunk + 32 * l;
+    int s = 0;
+    for (int i = i0; i < i0 + 32 && i < n; i++) s += f(in[i]);
+    int tot;
+    int run = chunk[c] + warp_excl_scan(s, tot);
+    for (int i = i0; i < i0 + 32 && i < n; i++) {
+        const int x = f(in[i]);
+        out[i] = (uint32_t)run;
+        run += x;
+    }
+}
+struct Ident {
+    __device__ int operator()(uint32_t x) const { return (int)x; }
+};
+struct Popc {
+    __device__ int operator()(uint32_t x) const { return __popc(x); }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------- mesh edits
+// Triangle t = (v0, v1, v2) has edge k from v(k+1) to v(k+2), opposite v(k),
+// the interior on its positive side.  opp[t][k] = (s << 2) | e names the
+// twin edge e of the neighbour s.  An edit writes the new pieces with their
+// outer edges still naming the old neighbours, and records in smap[old
+// slot] (stamped with the round) where each old edge went; relink() then
+// moves those names through the neighbours' records.
+namespace {
+
+__device__ __forceinline__ void set_ref(int4* opp, int t, int e, int r) { reinterpret_cast<int*>(opp + t)[e] = r; }
+
+__device__ __forceinline__ int4 smap_rec(int stamp, int k, int r_k, int k1, int r_k1, int k2, int r_k2) {
+    int r[3];
+    r[k] = r_k;
+    r[k1] = r_k1;
+    r[k2] = r_k2;
+    return make_int4(stamp, r[0], r[1], r[2]);
+}
+
+// p strictly inside t: pieces replace vertex k by p (piece k keeps old edge
+// k); piece j's edge k is the twin of piece k's edge j.
+__device__ __forceinline__ bool split3(const MeshDev& m, int t, int p, int stamp) {
+    const int base = atomicAdd(&m.hdr->T, 2);
+    if (base + 2 > m.t_cap) {
+        m.hdr->err = 1;
+        return false;
+    }
+    const int4 o = m.tri[t], r = m.opp[t];
+    const int s0 = t, s1 = base, s2 = base + 1;
+    m.tri[s0] = make_int4(p, o.y, o.z, 0);
+    m.tri[s1] = make_int4(o.x, p, o.z, 0);
+    m.tri[s2] = make_int4(o.x, o.y, p, 0);
+    m.opp[s0] = make_int4(r.x, mk_ref(s1, 0), mk_ref(s2, 0), 0);
+    m.opp[s1] = make_int4(mk_ref(s0, 1), r.y, mk_ref(s2, 1), 0);
+    m.opp[s2] = make_int4(mk_ref(s0, 2), mk_ref(s1, 2), r.z, 0);
+    m.smap[t] = make_int4(stamp, mk_ref(s0, 0), mk_ref(s1, 1), mk_ref(s2, 2));
+    m.claim[s1] = m.claim[s2] = kNoClaim;
+    m.smap[s1] = m.smap[s2] = make_int4(0, -1, -1, -1);
+    return true;
+}
+
+// p on edge k of t (from b = v(k+1) to c = v(k+2)), strictly between b and c.
+// t splits into A (c replaced by p, slot t) and B (b replaced by p); when the
+// edge is inner, its twin edge j of n splits n into A' (b replaced, slot n)
+// and B' (c replaced).  A's edge k (b -> p) is the twin of edge j of B',
+// B's edge k (p -> c) the twin of edge j of A'.
+__device__ __forceinline__ bool split_edge(const MeshDev& m, int t, int k, int n, int j, int p, int stamp) {
+    const int need = n >= 0 ? 2 : 1;
+    const int base = atomicAdd(&m.hdr->T, need);
+    if (base + need > m.t_cap) {
+        m.hdr->err = 1;
+        return false;
+    }
+    const int k1 = k == 2 ? 0 : k + 1, k2 = k == 0 ? 2 : k - 1;
+    const int4 ot = m.tri[t], rt = m.opp[t];
+    const int sB = base, sB2 = n >= 0 ? base + 1 : -1;
+    int4 A = ot, B = ot;
+    vtx(A, k2) = p;
+    vtx(B, k1) = p;
+    int4 rA = rt, rB = rt;
+    ref_of(rA, k) = n >= 0 ? mk_ref(sB2, j) : -1;
+    ref_of(rA, k1) = mk_ref(sB, k2);
+    ref_of(rB, k2) = mk_ref(t, k1);
+    ref_of(rB, k) = n >= 0 ? mk_ref(n, j) : -1;
+    m.tri[t] = A;
+    m.tri[sB] = B;
+    m.opp[t] = rA;
+    m.opp[sB] = rB;
+    m.smap[t] = smap_rec(stamp, k, -1, k1, mk_ref(sB, k1), k2, mk_ref(t, k2));
+    m.claim[sB] = kNoClaim;
+    m.smap[sB] = make_int4(0, -1, -1, -1);
+    if (n >= 0) {
+        const int j1 = j == 2 ? 0 : j + 1, j2 = j == 0 ? 2 : j - 1;
+        const int4 on = m.tri[n], rn = m.opp[n];
+        int4 A2 = on, B2 = on;
+        vtx(A2, j2) = p;  // w(j+2) = b
+        vtx(B2, j1) = p;  // w(j+1) = c
+        int4 rA2 = rn, rB2 = rn;
+        ref_of(rA2, j) = mk_ref(sB, k);
+        ref_of(rA2, j1) = mk_ref(sB2, j2);
+        ref_of(rB2, j2) = mk_ref(n, j1);
+        ref_of(rB2, j) = mk_ref(t, k);
+        m.tri[n] = A2;
+        m.tri[sB2] = B2;
+        m.opp[n] = rA2;
+        m.opp[sB2] = rB2;
+        m.smap[n] = smap_rec(stamp, j, -1, j1, mk_ref(sB2, j1), j2, mk_ref(n, j2));
+        m.claim[sB2] = kNoClaim;
+        m.smap[sB2] = make_int4(0, -1, -1, -1);
+    }
+    return true;
+}
+
+// Flip edge k of t (twin edge j of n): with x = v(k), b = v(k+1), c = v(k+2)
+// of t and y = w(j) of n, the pieces are t' = (x, b, y) and n' = (y, c, x);
+// edge 1 of each is the new diagonal, edges 0 and 2 are old outer edges.
+__device__ __forceinline__ void flip(const MeshDev& m, int t, int k, int n, int j, int stamp) {
+    const int k1 = k == 2 ? 0 : k + 1, k2 = k == 0 ? 2 : k - 1;
+    const int j1 = j == 2 ? 0 : j + 1, j2 = j == 0 ? 2 : j - 1;
+    const int4 tt = m.tri[t], tn = m.tri[n], rt = m.opp[t], rn = m.opp[n];
+    const int x = vtx(tt, k), b = vtx(tt, k1), c = vtx(tt, k2), y = vtx(tn, j);
+    m.tri[t] = make_int4(x, b, y, 0);
+    m.tri[n] = make_int4(y, c, x, 0);
+    m.opp[t] = make_int4(ref_of(rn, j1), mk_ref(n, 1), ref_of(rt, k2), 0);
+    m.opp[n] = make_int4(ref_of(rt, k1), mk_ref(t, 1), ref_of(rn, j2), 0);
+    m.smap[t] = smap_rec(stamp, k, -1, k1, mk_ref(n, 0), k2, mk_ref(t, 2));
+    m.smap[n] = smap_rec(stamp, j, -1, j1, mk_ref(t, 0), j2, mk_ref(n, 2));
+}
+
+// Outer edge e of a piece s made this round: its name of the old neighbour
+// (m', i) goes through m''s record when m' was edited this round too (that
+// edit links its own side); otherwise the neighbour is told about s.
+__device__ __forceinline__ void relink(const MeshDev& m, int s, int e, int stamp) {
+    const int r = reinterpret_cast<const int*>(m.opp + s)[e];
+    if (r < 0) return;
+    const int mm = r >> 2, i = r & 3;
+    const int4 sm = m.smap[mm];
+    if (sm.x == stamp) set_ref(m.opp, s, e, smap_ref(sm, i));
+    else set_ref(m.opp, mm, i, mk_ref(s, e));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- the pass kernel
+namespace {
+
+// Claim priority of a pending point: squared distance of 3q from the sum of
+// its triangle's vertices (points near the middle first, so the pieces split
+// the remaining points evenly), then the vertex slot (unique).
+__device__ __forceinline__ unsigned long long claim_key(const MeshDev& m, int4 t, int2 q, int vid) {
+    const int2 a = m.pos[t.x], b = m.pos[t.y], c = m.pos[t.z];
+    const long long dx = 3ll * q.x - a.x - b.x - c.x, dy = 3ll * q.y - a.y - b.y - c.y;
+    return ((unsigned long long)(dx * dx + dy * dy) << 27) | (unsigned)vid;
+}
+
+__device__ __forceinline__ void add_point(const MeshDev& m, MeshCtl* ctl, uint32_t px, float d, int T0) {
+    const uint32_t bit = 1u << (px & 31);
+    if (atomicOr(m.occ + (px >> 5), bit) & bit) return;  // a point already at this pixel keeps it
+    const int vid = atomicAdd(&m.hdr->n, 1);
+    const int slot = atomicAdd(&m.hdr->n_new, 1);
+    if (vid >= m.n_cap || slot >= m.p_cap) {
+        m.hdr->err = 1;
+        if (slot < m.p_cap) m.ploc[slot] = -1;
+        return;
+    }
+    const int t = m.planeidx[px];
+    m.pos[vid] = make_int2((int)(px % (uint32_t)m.W), (int)(px / (uint32_t)m.W));
+    m.vd[vid] = d;
+    m.vpass[vid] = (uint8_t)m.pass;
+    m.pend[slot] = vid;
+    m.pnb[slot] = -1;
+    if (t < 0 || t >= T0) {  // an evaluated pixel always has a triangle
+        m.hdr->err = 2;
+        m.ploc[slot] = -1;
+        return;
+    }
+    m.ploc[slot] = t;
+    atomicAdd(&ctl->total_new, 1ull);
+}
+
+// Where pending entry e lies: -1 inside its triangle, else the edge code of
+// the pnb array; -2 when it is not in its triangle (an error).
+__device__ __forceinline__ int classify(const MeshDev& m, int t, int2 q) {
+    const int4 tt = m.tri[t];
+    const int2 a = m.pos[tt.x], b = m.pos[tt.y], c = m.pos[tt.z];
+    const long long o[3] = {orient(b, c, q), orient(c, a, q), orient(a, b, q)};
+    int k = -1;
+    for (int i = 0; i < 3; i++) {
+        if (o[i] < 0) return -2;
+        if (o[i] == 0) {
+            if (k >= 0) return -2;  // on two edges: a vertex (never: pixels of vertices are skipped)
+            k = i;
+        }
+    }
+    if (k < 0) return -1;
+    const int r = ref_of(m.opp[t], k);
+    const int n = r >= 0 ? r >> 2 : -1, j = r >= 0 ? r & 3 : 0;
+    return ((n + 1) << 4) | (j << 2) | k;
+}
+
+__device__ __forceinline__ int ld_int(const int* p) { return *(const volatile int*)p; }
+__device__ __forceinline__ unsigned long long ld_u64(const unsigned long long* p) {
+    return *(const volatile unsigned long long*)p;
+}
+
+__global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __restrict__ md, int np, MeshCtl* ctl) {
+    __shared__ int pre[kMeshBatch + 1];
+    cg::grid_group grid = cg::this_grid();
+
+    // ---- 0: take over seed meshes; reset the pass's counters
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->total_new = ctl->inserted = ctl->flips = 0;
+        ctl->err = 0;
+        ctl->rounds = 0;
+    }
+    each_item(np, pre, [&](int p) { const MeshDev& m = md[p]; return 1 + (m.seed_T > 0 ? words_of(m) + m.seed_n + m.seed_T : 0); },
+              [&](int p, int i) {
+                  const MeshDev& m = md[p];
+                  if (i == 0) {
+                      MeshHdr& h = *m.hdr;
+                      if (m.seed_T > 0) {
+                          h.n = m.seed_n;
+                          h.T = m.seed_T;
+                          h.stamp = 0;
+                          h.err = 0;
+                      }
+                      h.n_new = h.n_small = h.n_large = h.n_items = h.n_hull = 0;
+                      for (int c = 0; c < kMeshClasses; c++) h.cls[c] = h.cls_fill[c] = 0;
+                      h.rounds = h.flips = 0;
+                      return;
+                  }
+                  i -= 1;
+                  const int words = words_of(m);
+                  if (i < words) {
+                      m.occ[i] = 0u;
+                      return;
+                  }
+                  i -= words;
+                  if (i < m.seed_n) {
+                      m.pos[i] = make_int2(m.seed_pos[2 * i], m.seed_pos[2 * i + 1]);
+                      m.vd[i] = m.seed_d[i];
+                      m.vpass[i] = 1;
+                      return;
+                  }
+                  i -= m.seed_n;
+                  m.tri[i] = m.seed_tri[i];
+                  m.opp[i] = m.seed_opp[i];
+                  m.claim[i] = kNoClaim;
+                  m.smap[i] = make_int4(0, -1, -1, -1);
+              });
+    grid.sync();
+    each_item(np, pre, [&](int p) { return md[p].seed_T > 0 ? md[p].seed_n : 0; }, [&](int p, int i) {
+        const MeshDev& m = md[p];
+        const int2 q = m.pos[i];
+        const uint32_t px = (uint32_t)q.y * (uint32_t)m.W + (uint32_t)q.x;
+        atomicOr(m.occ + (px >> 5), 1u << (px & 31));
+    });
+    grid.sync();
+
+    // ---- 1: collect the new points (cell records in raster order of cells, or a list)
+    each_item(np, pre, [&](int p) { const MeshDev& m = md[p]; return m.cg_key ? m.ncells : m.list_n; },
+              [&](int p, int c) {
+                  const MeshDev& m = md[p];
+                  const int T0 = m.hdr->T;
+                  if (m.cg_key) {
+                      const uint32_t gk = m.cg_key[c], bk = m.cb_key[c];
+                      if (gk != kNoKey) add_point(m, ctl, gk & kIdxMask, m.cg_d[c], T0);
+                      if (bk != kNoKey && m.x_d[c] >= 0) add_point(m, ctl, bk & kIdxMask, (float)m.x_d[c], T0);
+                  } else {
+                      const int u = m.list_uv[2 * c], v = m.list_uv[2 * c + 1];
+                      add_point(m, ctl, (uint32_t)v * (uint32_t)m.W + (uint32_t)u, 0.0f, T0);
+                  }
+              });
+    grid.sync();
+
+    // ---- 2: insertion rounds
+    int round = 0;
+    for (; round < kMaxInsertRounds; round++) {
+        if (ld_u64(&ctl->inserted) >= ld_u64(&ctl->total_new)) break;
+        // claim the triangle (and the neighbour across the edge the point lies on)
+        each_item(np, pre, [&](int p) { return ld_int(&md[p].hdr->n_new); }, [&](int p, int e) {
+            const MeshDev& m = md[p];
+            const int t = m.ploc[e];
+            if (t < 0) return;
+            const int vid = m.pend[e];
+            const int2 q = m.pos[vid];
+            const int code = classify(m, t, q);
+            if (code == -2) {
+                m.hdr->err = 2;
+                m.ploc[e] = -1;
+                atomicAdd(&ctl->inserted, 1ull);
+                return;
+            }
+            const unsigned long long key = claim_key(m, m.tri[t], q, vid);
+            m.tkey[e] = key;
+            m.pnb[e] = code;
+            atomicMin(m.claim + t, key);
+            if (code >= 0 && (code >> 4) > 0) atomicMin(m.claim + ((code >> 4) - 1), key);
+        });
+        grid.sync();
+        // a point holding all its claims splits them
+        each_item(np, pre, [&](int p) { return ld_int(&md[p].hdr->n_new); }, [&](int p, int e) {
+            const MeshDev& m = md[p];
+            const int t = m.ploc[e];
+            if (t < 0) return;
+            const unsigned long long key = m.tkey[e];
+            const int code = m.pnb[e];
+            const int n = code >= 0 ? (code >> 4) - 1 : -1;
+            if (m.claim[t] != key || (n >= 0 && m.claim[n] != key)) return;
+            const int stamp = m.hdr->stamp + round + 1;
+            const int vid = m.pend[e];
+            const bool ok = code < 0 ? split3(m, t, vid, stamp) : split_edge(m, t, code & 3, n, (code >> 2) & 3, vid, stamp);
+            m.ploc[e] = ok ? -2 - t : -1;
+            atomicAdd(&ctl->inserted, 1ull);
+        });
+        grid.sync();
+        // link the pieces to their neighbours; the others move to the piece they lie in
+        each_item(np, pre, [&](int p) { return ld_int(&md[p].hdr->n_new); }, [&](int p, int e) {
+            const MeshDev& m = md[p];
+            const int lt = m.ploc[e];
+            if (lt == -1) return;
+            const int stamp = m.hdr->stamp + round + 1;
+            const int code = m.pnb[e];
+            const int n = code >= 0 ? (code >> 4) - 1 : -1;
+            if (lt <= -2) {
+                const int t = -2 - lt;
+                const int4 st = m.smap[t];
+                for (int k = 0; k < 3; k++) {
+                    const int r = smap_ref(st, k);
+                    if (r >= 0) relink(m, r >> 2, r & 3, stamp);
+                }
+                if (n >= 0) {
+                    const int4 sn = m.smap[n];
+                    for (int k = 0; k < 3; k++) {
+                        const int r = smap_ref(sn, k);
+                        if (r >= 0) relink(m, r >> 2, r & 3, stamp);
+                    }
+                    m.claim[n] = kNoClaim;
+                }
+                m.claim[t] = kNoClaim;
+                m.ploc[e] = -1;
+                return;
+            }
+            const int t = lt;
+            m.claim[t] = kNoClaim;
+            if (n >= 0) m.claim[n] = kNoClaim;
+            const int4 st = m.smap[t];
+            if (st.x != stamp) return;  // its triangle was not split
+            const int2 q = m.pos[m.pend[e]];
+            int found = -1;
+            for (int k = 0; k < 3 && found < 0; k++) {
+                const int r = smap_ref(st, k);
+                if (r >= 0 && contains(m.pos, m.tri[r >> 2], q)) found = r >> 2;
+            }
+            if (found < 0) {
+                m.hdr->err = 2;
+                atomicAdd(&ctl->inserted, 1ull);
+            }
+            m.ploc[e] = found;
+        });
+        grid.sync();
+    }
+    if (round == kMaxInsertRounds && ld_u64(&ctl->inserted) < ld_u64(&ctl->total_new)) {
+        if (blockIdx.x == 0 && threadIdx.x < np) md[threadIdx.x].hdr->err = 3;
+    }
+    const int ins_rounds = round;
+
+    // ---- 3: flip rounds until no edge is illegal
+    unsigned long long flips_seen = 0;
+    int fround = 0;
+    for (; fround < kMaxFlipRounds; fround++) {
+        const int stamp_off = ins_rounds + fround + 1;
+        // propose: an illegal edge claims both its triangles (lower slot proposes)
+        each_item(np, pre, [&](int p) { return ld_int(&md[p].hdr->T); }, [&](int p, int t) {
+            const MeshDev& m = md[p];
+            const int4 tt = m.tri[t], rt = m.opp[t];
+            const int2 a = m.pos[tt.x], b = m.pos[tt.y], c = m.pos[tt.z];
+            for (int k = 0; k < 3; k++) {
+                const int r = ref_of(rt, k);
+                if (r < 0 || (r >> 2) < t) continue;
+                const int n = r >> 2;
+                const int y = vtx(m.tri[n], r & 3);
+                if (incircle_sos(a, b, c, m.pos[y])) {
+                    const unsigned long long key = (unsigned long long)mk_ref(t, k);
+                    atomicMin(m.claim + t, key);
+                    atomicMin(m.claim + n, key);
+                }
+            }
+        });
+        grid.sync();
+        // flip where an edge holds both claims
+        each_item(np, pre, [&](int p) { return ld_int(&md[p].hdr->T); }, [&](int p, int t) {
+            const MeshDev& m = md[p];
+            const unsigned long long key = m.claim[t];
+            if (key == kNoClaim || (int)(key >> 2) != t) return;
+            const int k = (int)(key & 3);
+            const int r = ref_of(m.opp[t], k);
+            const int n = r >> 2;
+            if (m.claim[n] != key) return;
+            flip(m, t, k, n, r & 3, m.hdr->stamp + stamp_off);
+            atomicAdd(&ctl->flips, 1ull);
+            atomicAdd(&m.hdr->flips, 1);
+        });
+        grid.sync();
+        // claims back to empty; flipped triangles link their outer edges (0 and 2)
+        each_item(np, pre, [&](int p) { return ld_int(&md[p].hdr->T); }, [&](int p, int t) {
+            const MeshDev& m = md[p];
+            if (m.claim[t] != kNoClaim) m.claim[t] = kNoClaim;
+            const int stamp = m.hdr->stamp + stamp_off;
+            if (m.smap[t].x != stamp) return;
+            relink(m, t, 0, stamp);
+            relink(m, t, 2, stamp);
+        });
+        grid.sync();
+        const unsigned long long f = ld_u64(&ctl->flips);
+        if (f == flips_seen) break;
+        flips_seen = f;
+    }
+    if (fround == kMaxFlipRounds && blockIdx.x == 0 && threadIdx.x < np) md[threadIdx.x].hdr->err = 3;
+
+    // ---- 4: canonical ranks (pairs whose next pass is the last)
+    // vertex rank = vertex pixels before it in raster order (the bit map's prefix)
+    each_warp_item(np, pre, [&](int p) { return md[p].canonical ? scan_chunks(words_of(md[p])) : 0; }, [&](int p, int c) {
+        const MeshDev& m = md[p];
+        scan_a(m.occ, words_of(m), m.scan, c, Popc());
+    });
+    each_item(np, pre, [&](int p) { return md[p].canonical ? ld_int(&md[p].hdr->n) + 1 : 0; },
+              [&](int p, int i) { md[p].gcnt[i] = 0; });
+    grid.sync();
+    each_warp_item(np, pre, [&](int p) { return md[p].canonical ? 1 : 0; }, [&](int p, int) {
+        const MeshDev& m = md[p];
+        scan_b(m.scan, scan_chunks(words_of(m)), nullptr);
+    });
+    grid.sync();
+    each_warp_item(np, pre, [&](int p) { return md[p].canonical ? scan_chunks(words_of(md[p])) : 0; }, [&](int p, int c) {
+        const MeshDev& m = md[p];
+        scan_c(m.occ, m.wpre, words_of(m), m.scan, c, Popc());
+    });
+    grid.sync();
+    each_item(np, pre, [&](int p) { return md[p].canonical ? ld_int(&md[p].hdr->n) : 0; }, [&](int p, int v) {
+        const MeshDev& m = md[p];
+        const int2 q = m.pos[v];
+        const uint32_t px = (uint32_t)q.y * (uint32_t)m.W + (uint32_t)q.x;
+        const int r = (int)m.wpre[px >> 5] + __popc(m.occ[px >> 5] & ((1u << (px & 31)) - 1u));
+        m.vrank[v] = r;
+        m.vcanon[r] = make_int4(q.x, q.y, __float_as_int(m.vd[v]), m.vpass[v]);
+    });
+    grid.sync();
+    // triangle key (i < j < k canonical); count the triangles of each smallest vertex
+    each_item(np, pre, [&](int p) { return md[p].canonical ? ld_int(&md[p].hdr->T) : 0; }, [&](int p, int t) {
+        const MeshDev& m = md[p];
+        const int4 tt = m.tri[t];
+        int a = m.vrank[tt.x], b = m.vrank[tt.y], c = m.vrank[tt.z];
+        if (a > b) { const int x = a; a = b; b = x; }
+        if (b > c) { const int x = b; b = c; c = x; }
+        if (a > b) { const int x = a; a = b; b = x; }
+        m.tkey[t] = ((unsigned long long)(unsigned)b << 32) | (unsigned)c;
+        atomicAdd(m.gcnt + a, 1);
+    });
+    grid.sync();
+    each_warp_item(np, pre, [&](int p) { return md[p].canonical ? scan_chunks(ld_int(&md[p].hdr->n)) : 0; }, [&](int p, int c) {
+        const MeshDev& m = md[p];
+        scan_a((const uint32_t*)m.gcnt, ld_int(&m.hdr->n), m.scan, c, Ident());
+    });
+    grid.sync();
+    each_warp_item(np, pre, [&](int p) { return md[p].canonical ? 1 : 0; }, [&](int p, int) {
+        const MeshDev& m = md[p];
+        scan_b(m.scan, scan_chunks(ld_int(&m.hdr->n)), nullptr);
+    });
+    grid.sync();
+    each_warp_item(np, pre, [&](int p) { return md[p].canonical ? scan_chunks(ld_int(&md[p].hdr->n)) : 0; }, [&](int p, int c) {
+        const MeshDev& m = md[p];
+        scan_c((const uint32_t*)m.gcnt, (uint32_t*)m.gcnt, ld_int(&m.hdr->n), m.scan, c, Ident());
+    });
+    grid.sync();
+    // scatter by smallest vertex (gcnt[i] ends at the start of group i + 1)
+    each_item(np, pre, [&](int p) { return md[p].canonical ? ld_int(&md[p].hdr->T) : 0; }, [&](int p, int t) {
+        const MeshDev& m = md[p];
+        const int4 tt = m.tri[t];
+        const int a = min(m.vrank[tt.x], min(m.vrank[tt.y], m.vrank[tt.z]));
+        m.tperm[atomicAdd(m.gcnt + a, 1)] = t;
+    });
+    grid.sync();
+    // order each group by (j, k): groups are a vertex's few triangles
+    each_item(np, pre, [&](int p) { return md[p].canonical ? ld_int(&md[p].hdr->n) : 0; }, [&](int p, int i) {
+        const MeshDev& m = md[p];
+        const int lo = i ? m.gcnt[i - 1] : 0, hi = m.gcnt[i];
+        for (int x = lo + 1; x < hi; x++) {
+            const int t = m.tperm[x];
+            const unsigned long long kt = m.tkey[t];
+            int y = x - 1;
+            while (y >= lo && m.tkey[m.tperm[y]] > kt) {
+                m.tperm[y + 1] = m.tperm[y];
+                y--;
+            }
+            m.tperm[y + 1] = t;
+        }
+    });
+    grid.sync();
+
+    // ---- 5: the next pass's raster inputs: triangle id = slot, or canonical position
+    each_item(np, pre, [&](int p) { return ld_int(&md[p].hdr->T); }, [&](int p, int s) {
+        const MeshDev& m = md[p];
+        const int t = m.canonical ? m.tperm[s] : s;
+        const int4 tt = m.tri[t];
+        int id[3] = {tt.x, tt.y, tt.z};
+        int2 P[3] = {m.pos[id[0]], m.pos[id[1]], m.pos[id[2]]};
+        // the vertices in canonical (v, u) order, as the plane solve takes them
+        for (int a = 0; a < 2; a++)
+            for (int b = 0; b < 2 - a; b++)
+                if (vkey(P[b]) > vkey(P[b + 1])) {
+                    const int2 x = P[b]; P[b] = P[b + 1]; P[b + 1] = x;
+                    const int y = id[b]; id[b] = id[b + 1]; id[b + 1] = y;
+                }
+        int32_t* q = m.tri_uv + 6 * (size_t)s;
+        q[0] = P[0].x; q[1] = P[0].y; q[2] = P[1].x; q[3] = P[1].y; q[4] = P[2].x; q[5] = P[2].y;
+        // Eq. 3 by Cramer's rule in fp64, the host's expression operation by
+        // operation (each rounded on its own: no contraction into FMAs)
+        const long long u0 = P[0].x, v0 = P[0].y, u1 = P[1].x, v1 = P[1].y, u2 = P[2].x, v2 = P[2].y;
+        const long long det = (u1 - u0) * (v2 - v0) - (u2 - u0) * (v1 - v0);
+        const double d0 = (double)m.vd[id[0]];
+        const double e1 = __dsub_rn((double)m.vd[id[1]], d0);
+        const double e2 = __dsub_rn((double)m.vd[id[2]], d0);
+        const double na = __dsub_rn(__dmul_rn(e1, (double)(v2 - v0)), __dmul_rn(e2, (double)(v1 - v0)));
+        const double nb = __dsub_rn(__dmul_rn((double)(u1 - u0), e2), __dmul_rn((double)(u2 - u0), e1));
+        const double A = __ddiv_rn(na, (double)det);
+        const double B = __ddiv_rn(nb, (double)det);
+        const double C = __dsub_rn(__dsub_rn(d0, __dmul_rn(A, (double)u0)), __dmul_rn(B, (double)v0));
+        m.abc[3 * (size_t)s] = __double2float_rn(A);
+        m.abc[3 * (size_t)s + 1] = __double2float_rn(B);
+        m.abc[3 * (size_t)s + 2] = __double2float_rn(C);
+        // raster lists: small boxes by width class, large ones by work items
+        const int x0 = max(0, min(q[0], min(q[2], q[4]))), x1 = min(m.W - 1, max(q[0], max(q[2], q[4])));
+        const int y0 = max(0, min(q[1], min(q[3], q[5]))), y1 = min(m.H - 1, max(q[1], max(q[3], q[5])));
+        const int area = (x1 < x0 || y1 < y0) ? 0 : (x1 - x0 + 1) * (y1 - y0 + 1);
+        if (area <= m.small_area) {
+            const int bw = x1 - x0 + 1;
+            const int cls = bw <= 1 ? 0 : min(kMeshClasses - 1, 32 - __clz(bw - 1));
+            atomicAdd(&m.hdr->cls[cls], 1);
+        } else {
+            const int li = atomicAdd(&m.hdr->n_large, 1);
+            m.large[li] = s;
+            m.lrows[li] = ((y1 - y0) / kRasterRows + 1) * ((x1 - x0) / m.cols + 1);
+        }
+        // hull edges, directed with the interior on the positive side
+        const int4 rt = m.opp[t];
+        for (int k = 0; k < 3; k++) {
+            if (ref_of(rt, k) >= 0) continue;
+            const int h = atomicAdd(&m.hdr->n_hull, 1);
+            const int2 a = m.pos[vtx(tt, k == 2 ? 0 : k + 1)], b = m.pos[vtx(tt, k == 0 ? 2 : k - 1)];
+            if (h < m.n_cap) reinterpret_cast<int4*>(m.hull)[h] = make_int4(a.x, a.y, b.x, b.y);
+            else m.hdr->err = 1;
+        }
+    });
+    grid.sync();
+    // small list in class order; work-item counts of the large ones summed per chunk
+    each_item(np, pre, [&](int p) { return ld_int(&md[p].hdr->T); }, [&](int p, int s) {
+        const MeshDev& m = md[p];
+        const int32_t* q = m.tri_uv + 6 * (size_t)s;
+        const int x0 = max(0, min(q[0], min(q[2], q[4]))), x1 = min(m.W - 1, max(q[0], max(q[2], q[4])));
+        const int y0 = max(0, min(q[1], min(q[3], q[5]))), y1 = min(m.H - 1, max(q[1], max(q[3], q[5])));
+        const int area = (x1 < x0 || y1 < y0) ? 0 : (x1 - x0 + 1) * (y1 - y0 + 1);
+        if (area > m.small_area) return;
+        const int bw = x1 - x0 + 1;
+        const int cls = bw <= 1 ? 0 : min(kMeshClasses - 1, 32 - __clz(bw - 1));
+        int off = 0;
+        for (int c = 0; c < cls; c++) off += m.hdr->cls[c];
+        m.small[off + atomicAdd(&m.hdr->cls_fill[cls], 1)] = s;
+    });
+    each_warp_item(np, pre, [&](int p) { return scan_chunks(ld_int(&md[p].hdr->n_large)); }, [&](int p, int c) {
+        const MeshDev& m = md[p];
+        scan_a((const uint32_t*)m.lrows, ld_int(&m.hdr->n_large), m.scan, c, Ident());
+    });
+    grid.sync();
+    each_warp_item(np, pre, [&](int p) { return 1; }, [&](int p, int) {
+        const MeshDev& m = md[p];
+        scan_b(m.scan, scan_chunks(ld_int(&m.hdr->n_large)), &m.hdr->n_items);
+        if ((threadIdx.x & 31) == 0) {
+            int ns = 0;
+            for (int c = 0; c < kMeshClasses; c++) ns += m.hdr->cls[c];
+            m.hdr->n_small = ns;
+        }
+    });
+    grid.sync();
+    each_warp_item(np, pre, [&](int p) { return scan_chunks(ld_int(&md[p].hdr->n_large)); }, [&](int p, int c) {
+        const MeshDev& m = md[p];
+        scan_c((const uint32_t*)m.lrows, (uint32_t*)m.lrows, ld_int(&m.hdr->n_large), m.scan, c, Ident());
+    });
+    if (blockIdx.x == 0 && threadIdx.x < np) {
+        MeshHdr& h = *md[threadIdx.x].hdr;
+        h.rounds = ins_rounds;
+        h.stamp += ins_rounds + fround + 2;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->rounds = ins_rounds + fround;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launch
+namespace {
+int g_mesh_per_sm = 0;  // co-resident blocks of k_mesh_pass per SM (set outside any capture)
+}
+
+cudaError_t prepare_mesh_kernels() {
+    int per_sm = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mesh_pass, kMeshThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+    g_mesh_per_sm = per_sm;
+    return cudaSuccess;
+}
+
+cudaError_t launch_mesh_pass(const MeshDev* md, int np, MeshCtl* ctl, cudaStream_t s) {
+    if (np <= 0) return cudaSuccess;
+    if (np > kMeshBatch || g_mesh_per_sm < 1) return cudaErrorInvalidValue;
+    // every block must be resident at once for the grid-wide barriers: a
+    // cooperative launch of at most the occupancy limit
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(g_mesh_per_sm * sm_count()));
+    cfg.blockDim = dim3(kMeshThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_mesh_pass, md, np, ctl);
+}
+
+}  // namespace stereo
