@@ -214,7 +214,7 @@ def run_ours(args):
     budget = int(0.5 * 2**30) + B * (40 * W * H + (64 << 20))
     ctx = S.Context(device=local, mem_budget_bytes=budget, max_slots=B, max_queue=4 * B, host_threads=threads,
                     profile=PROFILE_EVERY, batch_window_us=args.window_us, autotune=0 if args.no_autotune else 1,
-                    tune_w=W, tune_h=H, **PRM)
+                    tune_w=W, tune_h=H, host_mesh=1 if args.host_mesh else 0, **PRM)
     stream = ctx.stream
 
     def one_step(host=False):
@@ -319,6 +319,13 @@ def run_ours(args):
     launches = s1.kernel_launches - s0.kernel_launches
     if launches:
         roofline["pairs_per_launch_mean"] = (s1.batched_pairs - s0.batched_pairs) / launches
+    mp = s1.mesh_passes - s0.mesh_passes
+    mesh_stats = {"path": "host" if args.host_mesh else "device",
+                  "device_passes_per_step": mp / args.steps,
+                  "insert_rounds_per_pass": (s1.mesh_insert_rounds - s0.mesh_insert_rounds) / max(1, mp),
+                  "flip_rounds_per_pass": (s1.mesh_flip_rounds - s0.mesh_flip_rounds) / max(1, mp),
+                  "flips_per_pass": (s1.mesh_flips - s0.mesh_flips) / max(1, mp),
+                  "points_per_pass": (s1.mesh_points - s0.mesh_points) / max(1, mp)}
 
     # end to end through the public API with host buffers, copies inside the span
     e2e_spans, _ = timed(max(1, min(args.steps, 3)), host=True)
@@ -331,7 +338,8 @@ def run_ours(args):
     plain = None
     if not args.no_plain:
         pctx = S.Context(device=local, mem_budget_bytes=budget, max_slots=1, max_queue=4 * B, host_threads=1,
-                         autotune=0 if args.no_autotune else 1, tune_w=W, tune_h=H, **PRM)
+                         autotune=0 if args.no_autotune else 1, tune_w=W, tune_h=H,
+                         host_mesh=1 if args.host_mesh else 0, **PRM)
         ctx_plain = pctx
         nplain = min(B, 4)
 
@@ -377,7 +385,7 @@ def run_ours(args):
                "pairs_per_s": world * B * args.steps / (max_ms / 1e3),
                "latency_ms": {"p50": lats[len(lats) // 2], "p99": lats[min(len(lats) - 1, int(0.99 * len(lats)))]},
                "host_mesh_ms_per_pair": mesh_ms, "host_threads": threads,
-               "plain": plain, "roofline": roofline, "kernels": kinds, "rounds": round_stats, "tuning": tuning,
+               "plain": plain, "roofline": roofline, "kernels": kinds, "rounds": round_stats, "mesh": mesh_stats, "tuning": tuning,
                "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": clk}
         print(json.dumps(out))
@@ -745,6 +753,8 @@ def main():
     ap.add_argument("--dense", action="store_true", help="the dense variant: t_grad 0, every pixel evaluated")
     ap.add_argument("--host-threads", type=int, default=0, help="host triangulation workers (0: the core count)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel work shapes")
+    ap.add_argument("--host-mesh", action="store_true",
+                    help="triangulate every pass on the host (the default re-tessellates on the device)")
     ap.add_argument("--config", choices=("driving_1242x375", "vga_polygons"), default="driving_1242x375",
                     help="scene configuration of the main workload (and of --impl reference)")
     ap.add_argument("--kernel-size", type=int, default=4096)

@@ -73,11 +73,17 @@ typedef struct {
                                   as if the triangulation had failed (STEREO_E_INTERNAL); 0 = off */
     int batch_window_us;       /* continuous batching: when some requests are ready for a GPU
                                   stage while others are still in their host step, wait up to
-                                  this long for more of them before launching (0 = launch at once) */
+                                  this long for more of them before launching; 0 = the default
+                                  (with device meshes, wait up to 4 ms for seed host steps in
+                                  flight; with host meshes, launch at once); < 0 = never wait */
     int autotune;              /* 1 = at create, time the kernels' work-shape candidates on a
                                   synthetic round of tune_w x tune_h pairs and keep the fastest
                                   (results do not depend on it; see stereo_get_tuning) */
     int tune_w, tune_h;        /* frame of the synthetic tuning round (0 = 1242 x 375) */
+    int host_mesh;             /* 1 = triangulate S_it on the host between passes (the earlier
+                                  design, kept for comparison); 0 = only S_1's mesh on the host,
+                                  every later mesh re-tessellated on the GPU (stereo_delaunay_insert's
+                                  kernels), with no host step between passes.  Same results. */
     int inject_wait_timeout;   /* testing: n > 0 makes the context use the bulk-copy validate
                                   (stereo_validate_bulk's kernel, the one kernel with device-side
                                   waits) and, in its n-th GPU round with an iteration stage, has
@@ -158,7 +164,8 @@ const char* stereo_last_error(void);
 #define STEREO_K_VALIDATE 6      /* fused interpolate + cost + refine */
 #define STEREO_K_RESAMPLE 7      /* per-cell resample + epipolar match */
 #define STEREO_K_FILL 8          /* cell-record resets (inside the raster in the engine) */
-#define STEREO_K_KINDS 9
+#define STEREO_K_MESH 9          /* re-tessellation, planes and raster lists on the device */
+#define STEREO_K_KINDS 10
 
 /* Counters of the context since creation.  kernel_launches counts every
  * kernel the library launched; batched_pairs sums the pairs each launch
@@ -183,6 +190,10 @@ typedef struct {
     double exec_ms;               /* of which from the graph launch to the round's synchronisation */
     long long graph_instantiations; /* rounds whose graph could not be updated in place */
     long long kind_timed[STEREO_K_KINDS]; /* launches of each kind timed with events (see profile) */
+    /* device re-tessellation, summed over the passes of every request: passes, insertion
+     * rounds and flip rounds of the launch that served each (a launch serves several
+     * pairs), edge flips, and points inserted */
+    long long mesh_passes, mesh_insert_rounds, mesh_flip_rounds, mesh_flips, mesh_points;
 } stereo_stats;
 int stereo_get_stats(stereo_ctx* ctx, stereo_stats* out);
 

@@ -36,7 +36,7 @@ class Config(ctypes.Structure):
                 ("kp_per_bin", ctypes.c_int), ("uniq_margin", ctypes.c_int), ("host_threads", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("profile", ctypes.c_int), ("inject_mesh_failure", ctypes.c_int),
                 ("batch_window_us", ctypes.c_int), ("autotune", ctypes.c_int), ("tune_w", ctypes.c_int),
-                ("tune_h", ctypes.c_int), ("inject_wait_timeout", ctypes.c_int)]
+                ("tune_h", ctypes.c_int), ("host_mesh", ctypes.c_int), ("inject_wait_timeout", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -50,10 +50,13 @@ class Result(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_longlong), ("requests_done", ctypes.c_longlong),
                 ("batched_pairs", ctypes.c_longlong), ("gpu_rounds", ctypes.c_longlong),
-                ("host_mesh_ms", ctypes.c_double), ("kind_launches", ctypes.c_longlong * 9),
-                ("kind_ms", ctypes.c_double * 9), ("kind_bytes", ctypes.c_double * 9),
+                ("host_mesh_ms", ctypes.c_double), ("kind_launches", ctypes.c_longlong * 10),
+                ("kind_ms", ctypes.c_double * 10), ("kind_bytes", ctypes.c_double * 10),
                 ("round_ms", ctypes.c_double), ("graph_ms", ctypes.c_double), ("exec_ms", ctypes.c_double),
-                ("graph_instantiations", ctypes.c_longlong), ("kind_timed", ctypes.c_longlong * 9)]
+                ("graph_instantiations", ctypes.c_longlong), ("kind_timed", ctypes.c_longlong * 10),
+                ("mesh_passes", ctypes.c_longlong), ("mesh_insert_rounds", ctypes.c_longlong),
+                ("mesh_flip_rounds", ctypes.c_longlong), ("mesh_flips", ctypes.c_longlong),
+                ("mesh_points", ctypes.c_longlong)]
 
 
 class Tuning(ctypes.Structure):
@@ -62,7 +65,8 @@ class Tuning(ctypes.Structure):
                 ("raster_us", ctypes.c_double), ("validate_us", ctypes.c_double)]
 
 
-KINDS = ("census", "fast_score", "fast_bins", "match_kp", "raster_clear", "raster", "validate", "resample", "fill")
+KINDS = ("census", "fast_score", "fast_bins", "match_kp", "raster_clear", "raster", "validate", "resample", "fill",
+         "mesh")
 
 
 _lib = None

@@ -34,6 +34,12 @@ using namespace stereo;
 
 namespace {
 
+// Default batching window with device meshes: how long a round waits for
+// seed host steps still running (a few hundred microseconds each).
+constexpr int kSeedWindowUs = 4000;
+// ... and how long after the last submission it still expects more.
+constexpr int kQuietUs = 200;
+
 double now_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -259,6 +265,16 @@ struct Request {
     bool direct_kp = false;
     int32_t* kp_dev = nullptr;  // the device block's keypoint region (the copy-back path)
     class Pool* pool = nullptr;  // the context's host workers (idle ones help triangulate)
+    // device mesh (re-tessellation on the GPU after the first pass)
+    bool dev_mesh = false;      // later passes' meshes are built on the device
+    void* mesh_block = nullptr; // arena block of the device mesh
+    MeshDev mesh{};             // its arrays (host copy of the descriptor)
+    size_t seed_off = 0;        // offset of the seed mesh arrays in the staging blob (pass 1)
+    Pinned st_hdr;              // the mesh header after each device pass
+    Pinned st_vcanon;           // the final support set in canonical order (u, v, d bits, pass)
+    int dev_n = 0;              // vertices after the last device pass
+    bool mesh_now = false;      // this round runs the device mesh pass for this request
+    bool raster_dev = false;    // this round rasters the device mesh
 };
 
 size_t block_bytes(const Request& r, int K) {
@@ -380,6 +396,8 @@ struct stereo_ctx {
     std::thread sched;
     bool stop = false;
     int host_busy = 0;
+    int seed_busy = 0;  // of which seed host steps
+    std::chrono::steady_clock::time_point last_submit{};  // time of the latest submission
     std::atomic<int> mesh_steps{0};  // host mesh steps run (for the failure-injection hook)
     Pool pool;
     Pinned desc_host;
@@ -391,12 +409,13 @@ struct stereo_ctx {
     // executable graphs by round shape (bit 0: seed stage, bit 1: iteration
     // stage, bit 2: timed with events), each updated in place by the next
     // round of its shape
-    cudaGraphExec_t graph_exec[8] = {};
+    std::map<int, cudaGraphExec_t> graph_exec;  // by round shape
     long long rounds_seen = 0;  // for timing every profile-th round
     long long iter_rounds = 0;  // rounds with an iteration stage (for the wait-timeout test hook)
     int* err_dev = nullptr;                  // set by a device-side wait that gave up
     Pinned err_host;
     bool bulk_validate = false;              // the bulk-copy validate kernel (else the plain one)
+    bool dev_mesh = true;                    // re-tessellate on the device (cfg.host_mesh == 0)
     Tuning tune;                             // kernel work shapes (defaults, or chosen by the autotuner)
     bool tuned = false;                      // tune chosen by the autotuner
     double tune_raster_us = 0, tune_validate_us = 0;
@@ -424,6 +443,16 @@ bool valid_params(const stereo_config& c) {
 size_t tri_stage_bytes(int T, int items, int n_small, int n_hull, int n_batch) {
     return (size_t)n_hull * 16 + (size_t)T * 40 + 4 + (size_t)items * 4 + (size_t)n_small * 4 +
            ((size_t)n_batch + 1) * 4;
+}
+
+// Bytes of the request's staging blob: the mesh of tri_stage_bytes(), then,
+// for a device mesh, S_1's positions (8 B) and disparities (4 B) per point and
+// its triangles' vertices and neighbours (16 B each per triangle).
+size_t stage_bytes(const Request& r) {
+    const size_t base = tri_stage_bytes(r.T, r.raster_items, r.n_small, r.n_hull, r.n_batch);
+    if (!r.dev_mesh || r.seed_off == 0) return base;
+    const size_t n = r.n_support.empty() ? 0 : (size_t)r.n_support.back();
+    return align_up(r.seed_off + 12 * n, 16) + 32 * (size_t)r.T;
 }
 
 // Support set -> triangles, planes and raster inputs in the request's pinned
@@ -462,7 +491,20 @@ int mesh_step(Request& r) {
                                    r.tune.small_area, r.tune.raster_cols, box_v.get());
     std::unique_ptr<int32_t[]> batch_v(new int32_t[(size_t)n_small + 1]);
     const int n_batch = small_batches(box_v.get(), n_small, batch_v.get(), r.tune.batch_area);
-    if (!r.st_tri.ensure(tri_stage_bytes(T, items, n_small, n_hull, n_batch))) return STEREO_E_NOMEM;
+    // device mesh: S_1's mesh goes up with the first pass (positions, disparities, the triangles
+    // in positive orientation and their neighbours), for the device to insert into
+    if (T == 0) r.dev_mesh = false;
+    const size_t base_bytes = tri_stage_bytes(T, items, n_small, n_hull, n_batch);
+    r.seed_off = r.dev_mesh ? align_up(base_bytes, 16) : 0;
+    const size_t ccw_off = align_up(r.seed_off + 12 * (size_t)n, 16);
+    const size_t all_bytes = r.dev_mesh ? ccw_off + 32 * (size_t)T : base_bytes;
+    if (!r.st_tri.ensure(all_bytes)) return STEREO_E_NOMEM;
+    if (r.dev_mesh) {
+        char* b = r.st_tri.as<char>();
+        std::memcpy(b + r.seed_off, P.data(), 8 * (size_t)n);
+        std::memcpy(b + r.seed_off + 8 * (size_t)n, D.data(), 4 * (size_t)n);
+        mesh_adjacency(P.data(), tri.get(), T, (int32_t*)(b + ccw_off), (int32_t*)(b + ccw_off + 16 * (size_t)T));
+    }
     int32_t* hull = r.st_tri.as<int32_t>();
     for (int j = 0; j < n_hull; j++) {
         const int a = hull_v[2 * j], b = hull_v[2 * j + 1];
@@ -587,6 +629,34 @@ int host_after_iter(Request& r) {
     return mesh_step(r);
 }
 
+// The support sets S_1 .. S_iters of a device-mesh request from the final
+// vertex list (canonical order, each with the pass it joined): S_it is the
+// points that joined at pass it or before, in the same order.
+void build_trace(Request& r) {
+    const int4* v = r.st_vcanon.as<int4>();
+    const int n = r.dev_n;
+    std::vector<int32_t> joined(r.iters + 1, 0);
+    for (int i = 0; i < n; i++) joined[std::min(std::max(v[i].w, 1), r.iters)]++;
+    r.n_support.assign(r.iters, 0);
+    size_t total = 0;
+    for (int it = 1, acc = 0; it <= r.iters; it++) {
+        acc += joined[it];
+        r.n_support[it - 1] = acc;
+        total += (size_t)acc;
+    }
+    r.trace.clear();
+    r.trace.reserve(3 * total);
+    for (int it = 1; it <= r.iters; it++)
+        for (int i = 0; i < n; i++)
+            if (v[i].w <= it) {
+                r.trace.push_back((float)v[i].x);
+                r.trace.push_back((float)v[i].y);
+                float d;
+                std::memcpy(&d, &v[i].z, 4);
+                r.trace.push_back(d);
+            }
+}
+
 void finish(stereo_ctx* c, Request& r, int status) {
     r.status = status;
     r.state = status == STEREO_OK ? Q_DONE : Q_FAILED;
@@ -609,6 +679,25 @@ void admit(stereo_ctx* c) {
                 continue;
             }
             break;
+        }
+        if (c->dev_mesh && r->iters >= 2) {  // the device mesh of the passes after the first
+            const int n_cap = mesh_vertex_cap(r->W, r->H, kFastBins * c->K, r->iters, r->cell);
+            const int p_cap = (int)std::min<long long>(2ll * r->ncell_max, (long long)r->W * r->H);
+            const size_t mb = mesh_bytes(r->W, r->H, n_cap, 2 * n_cap + 8, p_cap);
+            void* mblk = c->arena.alloc(mb);
+            if (!mblk) {
+                c->arena.release(blk);
+                if (c->active.empty()) {
+                    c->queue.pop_front();
+                    finish(c, *r, STEREO_E_NOMEM);
+                    c->cv_done.notify_all();
+                    continue;
+                }
+                break;
+            }
+            r->mesh_block = mblk;
+            mesh_carve(r->mesh, mblk, r->W, r->H, n_cap, 2 * n_cap + 8, p_cap);
+            r->dev_mesh = true;
         }
         c->queue.pop_front();
         r->block = blk;
@@ -633,16 +722,36 @@ void admit(stereo_ctx* c) {
 
 // Descriptor upload for one group of pairs: PairDev[n] then per work kind
 // an offset array of n + 1 ints.  Returns device pointers via out params.
+// Then, for the pairs whose mesh is on the device: their PairDev and
+// MeshDev for the device-mesh raster (pass >= 2), the MeshDev of those that
+// re-tessellate this round, and one MeshCtl per launch of kMeshBatch pairs.
 struct Group {
     std::vector<Request*> reqs;
     const PairDev* pd = nullptr;
     const PairDev* hpd = nullptr;  // host copies of the descriptors (as uploaded)
     const int* off[WK_COUNT] = {};
     int total[WK_COUNT] = {};
+    int n_mr = 0, n_mp = 0;        // pairs of the device-mesh raster and of the mesh pass
+    const PairDev* mr_pd = nullptr;
+    const MeshDev* mr_md = nullptr;
+    const MeshDev* mp_md = nullptr;
+    MeshCtl* ctl = nullptr;
 };
 
+void count_mesh(Group& g) {
+    g.n_mr = g.n_mp = 0;
+    for (Request* r : g.reqs) {
+        g.n_mr += r->raster_dev ? 1 : 0;
+        g.n_mp += r->mesh_now ? 1 : 0;
+    }
+}
+
 size_t group_bytes(const Group& g) {
-    return align_up(sizeof(PairDev) * g.reqs.size(), 256) + WK_COUNT * align_up(sizeof(int) * (g.reqs.size() + 1), 256);
+    const size_t n = g.reqs.size();
+    const int chunks = (g.n_mp + kMeshBatch - 1) / kMeshBatch;
+    return align_up(sizeof(PairDev) * n, 256) + WK_COUNT * align_up(sizeof(int) * (n + 1), 256) +
+           align_up(sizeof(PairDev) * g.n_mr, 256) + align_up(sizeof(MeshDev) * g.n_mr, 256) +
+           align_up(sizeof(MeshDev) * g.n_mp, 256) + align_up(sizeof(MeshCtl) * chunks, 256);
 }
 
 void fill_group(Group& g, char* host, char* dev) {
@@ -670,6 +779,25 @@ void fill_group(Group& g, char* host, char* dev) {
         g.off[k] = (const int*)(dev + off);
         g.total[k] = s;
         off += align_up(sizeof(int) * (n + 1), 256);
+    }
+    PairDev* mr_pd = (PairDev*)(host + off);
+    g.mr_pd = (const PairDev*)(dev + off);
+    off += align_up(sizeof(PairDev) * g.n_mr, 256);
+    MeshDev* mr_md = (MeshDev*)(host + off);
+    g.mr_md = (const MeshDev*)(dev + off);
+    off += align_up(sizeof(MeshDev) * g.n_mr, 256);
+    MeshDev* mp_md = (MeshDev*)(host + off);
+    g.mp_md = (const MeshDev*)(dev + off);
+    off += align_up(sizeof(MeshDev) * g.n_mp, 256);
+    g.ctl = (MeshCtl*)(dev + off);
+    int a = 0, b = 0;
+    for (size_t i = 0; i < n; i++) {
+        const Request* r = g.reqs[i];
+        if (r->raster_dev) {
+            mr_pd[a] = hp[i];
+            mr_md[a++] = r->mesh;
+        }
+        if (r->mesh_now) mp_md[b++] = r->mesh;
     }
 }
 
@@ -775,10 +903,8 @@ void add_stats(stereo_stats& to, const stereo_stats& d) {
 // depend on how many requests the round holds.
 cudaError_t issue_inputs(Group& iter, cudaStream_t s) {
     for (Request* r : iter.reqs)
-        if (r->T > 0)
-            CK(cudaMemcpyAsync((void*)r->dev.hull, r->st_tri.p,
-                               tri_stage_bytes(r->T, r->raster_items, r->n_small, r->n_hull, r->n_batch),
-                               cudaMemcpyHostToDevice, s));
+        if (r->T > 0 && !r->raster_dev)
+            CK(cudaMemcpyAsync((void*)r->dev.hull, r->st_tri.p, stage_bytes(*r), cudaMemcpyHostToDevice, s));
     return cudaSuccess;
 }
 
@@ -786,8 +912,17 @@ cudaError_t issue_outputs(stereo_ctx* c, Group& seed, Group& iter, cudaStream_t 
     for (Request* r : seed.reqs)  // keypoint slots and their matches, one copy
         if (!r->direct_kp)
             CK(cudaMemcpyAsync(r->st_kp.p, r->dev.kp_uv, (size_t)kFastBins * c->K * 12, cudaMemcpyDeviceToHost, s));
-    for (Request* r : iter.reqs) {  // the four cell arrays of this pass, one copy
+    for (Request* r : iter.reqs) {
+        if (r->mesh_now) {  // the device mesh's counters after its re-tessellation
+            CK(cudaMemcpyAsync(r->st_hdr.p, r->mesh.hdr, sizeof(MeshHdr), cudaMemcpyDeviceToHost, s));
+            continue;
+        }
+        if (r->dev_mesh && !r->resample_now && r->dev_n > 0) {  // last pass: the support set, canonical order
+            CK(cudaMemcpyAsync(r->st_vcanon.p, r->mesh.vcanon, 16 * (size_t)r->dev_n, cudaMemcpyDeviceToHost, s));
+            continue;
+        }
         if (!r->resample_now) continue;
+        // the four cell arrays of this pass, one copy, for the host mesh step
         const size_t nc = (size_t)r->dev.Wc * r->dev.Hc;
         CK(cudaMemcpyAsync(r->st_cells.p, r->cells_dev, 16 * nc, cudaMemcpyDeviceToHost, s));
     }
@@ -819,8 +954,20 @@ cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, 
         CK(cudaMemcpyAsync(c->err_host.p, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
         return cudaSuccess;
     }
-    // the raster also resets this pass's cell records (no launch of their own)
-    CKQ(Lr.run(STEREO_K_RASTER, ni, raster_bytes + cells_bytes, [&] { return launch_raster(batch_of(iter, WK_RASTER), s); }));
+    // the raster also resets this pass's cell records (no launch of their own): meshes
+    // listed on the host (every first pass, and every pass of the host-mesh path), then
+    // meshes built on the device, kMeshBatch pairs per launch
+    const int n_host_raster = ni - iter.n_mr;
+    if (n_host_raster > 0)
+        CKQ(Lr.run(STEREO_K_RASTER, n_host_raster, raster_bytes + cells_bytes,
+                   [&] { return launch_raster(batch_of(iter, WK_RASTER), s); }));
+    for (int a = 0; a < iter.n_mr; a += kMeshBatch) {
+        PairBatch mb{};
+        mb.pd = iter.mr_pd + a;
+        mb.npairs = std::min(kMeshBatch, iter.n_mr - a);
+        CKQ(Lr.run(STEREO_K_RASTER, mb.npairs, n_host_raster > 0 ? 0.0 : raster_bytes + cells_bytes,
+                   [&] { return launch_raster_mesh(mb, iter.mr_md + a, s); }));
+    }
     CKQ(Lr.run(STEREO_K_VALIDATE, ni, validate_bytes, [&] {
         if (c->bulk_validate) return launch_validate_bulk(batch_of(iter, WK_VALIDATE_BULK), prm, s);
         const int fixed = (std::max(1, c->cfg.max_slots) + kVBatch - 1) / kVBatch;
@@ -839,6 +986,10 @@ cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, 
         return cudaSuccess;
     }));
     CKQ(Lr.run(STEREO_K_RESAMPLE, ni, 0.0, [&] { return launch_resample(batch_of(iter, WK_RESAMPLE), prm, s); }));
+    for (int a = 0, k = 0; a < iter.n_mp; a += kMeshBatch, k++) {
+        const int np = std::min(kMeshBatch, iter.n_mp - a);
+        CKQ(Lr.run(STEREO_K_MESH, np, 0.0, [&] { return launch_mesh_pass(iter.mp_md + a, np, iter.ctl + k, s); }));
+    }
     CK(cudaMemcpyAsync(c->err_host.p, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
     return cudaSuccess;
 }
@@ -860,15 +1011,25 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         r->dev.kp_d = r->dev.kp_uv + (size_t)kFastBins * c->K * 2;
     }
     for (Request* r : iter.reqs) {
-        const size_t tri_bytes = align_up(tri_stage_bytes(r->T, r->raster_items, r->n_small, r->n_hull, r->n_batch) + 64, 256);
-        if (tri_bytes > r->tri_block_bytes) {
+        r->raster_dev = r->dev_mesh && r->it >= 2;  // the device built this pass's mesh
+        r->resample_now = r->it < r->iters;
+        r->mesh_now = r->dev_mesh && r->resample_now;
+        r->dev.mesh_raster = r->raster_dev ? 1 : 0;
+        if (r->raster_dev) {  // raster inputs live in the device mesh
+            r->dev.small_batch = nullptr;
+            r->dev.n_small = r->dev.raster_items = r->dev.n_batch = 0;
+            r->dev.n_hull = -1;
+        }
+        const size_t tri_bytes = r->raster_dev ? 0 : align_up(stage_bytes(*r) + 64, 256);
+        if (!r->raster_dev && tri_bytes > r->tri_block_bytes) {
             std::lock_guard<std::mutex> g(c->mu);
             c->arena.release(r->tri_block);
             r->tri_block = c->arena.alloc(tri_bytes * 5 / 4);
             r->tri_block_bytes = r->tri_block ? tri_bytes * 5 / 4 : 0;
         }
-        if (!r->tri_block) return cudaErrorMemoryAllocation;
+        if (!r->raster_dev && !r->tri_block) return cudaErrorMemoryAllocation;
         char* tb = (char*)r->tri_block;
+        if (!r->raster_dev) {
         r->dev.hull = (const int32_t*)tb;
         r->dev.n_hull = r->n_hull;
         tb += (size_t)r->n_hull * 16;
@@ -882,11 +1043,12 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         r->dev.raster_cols = r->tune.raster_cols;
         r->dev.raster_items = r->raster_items;
         r->dev.n_small = r->n_small;
-        r->dev.planeidx = r->it == r->iters ? r->pidx_buf : nullptr;  // the LUT is an output of the last pass
         r->dev.T = r->T;
+        }
+        // the LUT is an output of the last pass, and with a device mesh it locates the new points of every pass
+        r->dev.planeidx = r->it == r->iters || r->dev_mesh ? r->pidx_buf : nullptr;
         set_cell_size(r->dev, r->sz);
         r->dev.first_pass = r->it == 1;
-        r->resample_now = r->it < r->iters;
         r->dev.Wc = r->resample_now ? (r->W + r->sz - 1) / r->sz : 0;
         r->dev.Hc = r->resample_now ? (r->H + r->sz - 1) / r->sz : 0;
         {
@@ -901,9 +1063,42 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         validate_bytes += px * (r->dev.first_pass ? 18.125 : 19.125);
         if (r->resample_now) {
             cells_bytes += 8.0 * r->dev.Wc * r->dev.Hc;
-            if (!r->st_cells.ensure(16 * (size_t)r->ncell_max)) return cudaErrorMemoryAllocation;
+            if (!r->mesh_now && !r->st_cells.ensure(16 * (size_t)r->ncell_max)) return cudaErrorMemoryAllocation;
         }
+        if (r->raster_dev || r->mesh_now) {  // the device mesh's fields for this pass
+            MeshDev& m = r->mesh;
+            m.small_area = r->tune.small_area;
+            m.cols = r->tune.raster_cols;
+            m.planeidx = r->pidx_buf;
+            m.seed_n = m.seed_T = 0;
+            m.cg_key = nullptr;
+            m.ncells = 0;
+            if (r->mesh_now) {
+                m.cg_key = r->dev.cg_key;
+                m.cg_d = r->dev.cg_d;
+                m.cb_key = r->dev.cb_key;
+                m.x_d = r->dev.x_d;
+                m.ncells = r->dev.Wc * r->dev.Hc;
+                m.pass = r->it + 1;
+                m.canonical = r->it + 1 == r->iters;
+                if (r->it == 1) {  // take S_1's mesh over from the staging blob uploaded this round
+                    const char* base = (const char*)r->tri_block + r->seed_off;
+                    const int n = r->n_support.back();
+                    m.seed_pos = (const int32_t*)base;
+                    m.seed_d = (const float*)(base + 8 * (size_t)n);
+                    m.seed_tri = (const int4*)((const char*)r->tri_block + align_up(r->seed_off + 12 * (size_t)n, 16));
+                    m.seed_opp = m.seed_tri + r->T;
+                    m.seed_n = n;
+                    m.seed_T = r->T;
+                }
+                if (!r->st_hdr.ensure(sizeof(MeshHdr))) return cudaErrorMemoryAllocation;
+            }
+        }
+        if (r->dev_mesh && !r->resample_now && r->dev_n > 0 && !r->st_vcanon.ensure(16 * (size_t)r->dev_n))
+            return cudaErrorMemoryAllocation;
     }
+    count_mesh(seed);
+    count_mesh(iter);
     const size_t bs = group_bytes(seed), bi = group_bytes(iter);
     if (bs + bi > c->desc_cap) {
         if (c->desc_dev) cudaFree(c->desc_dev);
@@ -948,7 +1143,11 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         Lr.timed.clear();
         return err;
     }
-    cudaGraphExec_t& exec = c->graph_exec[(seed.reqs.empty() ? 0 : 1) | (iter.reqs.empty() ? 0 : 2) | (Lr.prof ? 4 : 0)];
+    // shape: stages present, timing, and the launch counts of the raster kinds and the mesh pass
+    const int n_mr_launch = (iter.n_mr + kMeshBatch - 1) / kMeshBatch, n_mp_launch = (iter.n_mp + kMeshBatch - 1) / kMeshBatch;
+    const int shape = (seed.reqs.empty() ? 0 : 1) | (iter.reqs.empty() ? 0 : 2) | (Lr.prof ? 4 : 0) |
+                      ((int)iter.reqs.size() > iter.n_mr ? 8 : 0) | (n_mr_launch << 4) | (n_mp_launch << 12);
+    cudaGraphExec_t& exec = c->graph_exec[shape];
     bool updated = false;
     if (exec) {
         cudaGraphExecUpdateResultInfo info{};
@@ -1006,14 +1205,25 @@ void scheduler(stereo_ctx* c) {
                 const size_t ready = seed.reqs.size() + iter.reqs.size();
                 if (ready > 0) {
                     // batching window: others are still in their host step
-                    if (c->cfg.batch_window_us > 0 && c->host_busy > 0 && !c->stop) {
+                    // (with device meshes the only host steps are the short seed meshes, so by
+                    // default the round waits for them: every pair then takes its passes in the
+                    // same rounds, and each mesh launch serves them all)
+                    const int window = c->cfg.batch_window_us > 0 ? c->cfg.batch_window_us
+                                       : c->cfg.batch_window_us == 0 && c->dev_mesh ? kSeedWindowUs : 0;
+                    // requests still arriving (a submission less than kQuietUs ago, a slot free)
+                    // are waited for the same way: a burst of submissions starts as one round
+                    const int busy = c->cfg.batch_window_us > 0 ? c->host_busy : c->seed_busy;
+                    const auto now = std::chrono::steady_clock::now();
+                    const auto quiet_end = c->last_submit + std::chrono::microseconds(kQuietUs);
+                    const bool arriving = c->dev_mesh && c->cfg.batch_window_us == 0 && now < quiet_end &&
+                                          (int)c->active.size() < c->cfg.max_slots;
+                    if (window > 0 && (busy > 0 || arriving) && !c->stop) {
                         if (!waiting) {
                             waiting = true;
-                            deadline = std::chrono::steady_clock::now() +
-                                       std::chrono::microseconds(c->cfg.batch_window_us);
+                            deadline = now + std::chrono::microseconds(window);
                         }
-                        if (std::chrono::steady_clock::now() < deadline) {
-                            c->cv_sched.wait_until(g, deadline);
+                        if (now < deadline) {
+                            c->cv_sched.wait_until(g, busy > 0 ? deadline : std::min(deadline, quiet_end));
                             continue;
                         }
                     }
@@ -1045,17 +1255,53 @@ void scheduler(stereo_ctx* c) {
             c->cv_done.notify_all();
             continue;
         }
-        for (Request* r : iter.reqs) {
-            if (!r->resample_now) finish(c, *r, STEREO_OK);
-        }
-        std::vector<Request*> host;
+        std::vector<Request*> host, traces;
         for (Request* r : seed.reqs) host.push_back(r);
-        for (Request* r : iter.reqs)
-            if (r->resample_now) host.push_back(r);
+        for (Request* r : iter.reqs) {
+            if (r->mesh_now) {  // the device built the next pass's mesh: no host step
+                const MeshHdr& h = *r->st_hdr.as<MeshHdr>();
+                if (h.err != 0) {
+                    note_error(cudaErrorUnknown, "device mesh pass failed (capacity, location or round limit)", __LINE__);
+                    finish(c, *r, STEREO_E_INTERNAL);
+                    continue;
+                }
+                c->stats.mesh_passes++;
+                c->stats.mesh_insert_rounds += h.rounds;
+                c->stats.mesh_flip_rounds += h.frounds;
+                c->stats.mesh_flips += h.flips;
+                c->stats.mesh_points += h.n - (r->dev_n > 0 ? r->dev_n : r->n_support.back());
+                r->dev_n = h.n;
+                r->T = h.T;
+                r->n_tri.push_back(h.T);
+                r->it += 1;
+                r->sz = std::max(1, r->sz / 2);
+                r->state = Q_ITER_READY;
+                continue;
+            }
+            if (!r->resample_now) {
+                if (r->dev_mesh && r->dev_n > 0) traces.push_back(r);  // support sets from the device's list
+                else finish(c, *r, STEREO_OK);
+                continue;
+            }
+            host.push_back(r);
+        }
+        for (Request* r : traces) {
+            r->state = Q_HOST;
+            c->host_busy++;
+            c->pool.push([c, r] {
+                build_trace(*r);
+                std::lock_guard<std::mutex> g2(c->mu);
+                c->host_busy--;
+                finish(c, *r, STEREO_OK);
+                c->cv_sched.notify_all();
+                c->cv_done.notify_all();
+            });
+        }
         for (Request* r : host) {
             r->state = Q_HOST;
             c->host_busy++;
             const bool is_seed = r->it == 0;
+            if (is_seed) c->seed_busy++;
             c->pool.push([c, r, is_seed] {
                 const double t0 = now_ms();
                 int rc = is_seed ? host_after_seed(c, *r) : host_after_iter(*r);
@@ -1064,6 +1310,7 @@ void scheduler(stereo_ctx* c) {
                     rc = STEREO_E_INTERNAL;  // test hook: this host step reports a failure
                 std::lock_guard<std::mutex> g2(c->mu);
                 c->host_busy--;
+                if (is_seed) c->seed_busy--;
                 if (rc != STEREO_OK) finish(c, *r, rc);
                 else r->state = Q_ITER_READY;
                 c->cv_sched.notify_all();
@@ -1383,6 +1630,10 @@ void stereo_default_config(stereo_config* cfg) {
     cfg->host_threads = 1;
 }
 
+namespace {
+cudaError_t ensure_mesh_kernels();
+}
+
 int stereo_create(const stereo_config* cfg, stereo_ctx** out) {
     if (!cfg || !out) return STEREO_E_INVAL;
     if (!valid_params(*cfg) || cfg->max_slots < 1 || cfg->max_queue < 0) return STEREO_E_INVAL;
@@ -1431,6 +1682,11 @@ int stereo_create(const stereo_config* cfg, stereo_ctx** out) {
     }
     if (cfg->inject_wait_timeout > 0) c->bulk_validate = true;
     if (prepare_kernels() != cudaSuccess) c->bulk_validate = false;
+    c->dev_mesh = cfg->host_mesh == 0;
+    if (c->dev_mesh && ensure_mesh_kernels() != cudaSuccess) {
+        note_error(cudaGetLastError(), "device mesh kernels unavailable (host meshes kept)", __LINE__);
+        c->dev_mesh = false;
+    }
     if (cfg->autotune) {  // before the scheduler starts: the tuning round owns the stream
         const Tuning keep = c->tune;
         if (autotune(c) != cudaSuccess) {
@@ -1450,7 +1706,8 @@ int stereo_submit(stereo_ctx* c, int stream_id, const uint8_t* left, const uint8
     if (!c || !left || !right || !ticket_out) return STEREO_E_INVAL;
     if (!valid_size(w, h) || dmax < 1 || dmax > 256 || iters < 1 || cell < 1) return STEREO_E_INVAL;
     Request* r = new Request();
-    r->in_host.pool = r->st_tri.pool = r->st_kp.pool = r->st_cells.pool = &c->pinned;
+    r->in_host.pool = r->st_tri.pool = r->st_kp.pool = r->st_cells.pool = r->st_hdr.pool = r->st_vcanon.pool =
+        &c->pinned;
     r->pool = &c->pool;
     r->stream_id = stream_id;
     r->W = w;
@@ -1510,6 +1767,7 @@ int stereo_submit(stereo_ctx* c, int stream_id, const uint8_t* left, const uint8
     }
     r->ticket = c->next_ticket++;
     r->t_submit = now_ms();
+    c->last_submit = std::chrono::steady_clock::now();
     c->reqs[r->ticket] = r;
     c->queue.push_back(r);
     *ticket_out = r->ticket;
@@ -1580,11 +1838,14 @@ int stereo_release(stereo_ctx* c, uint64_t ticket) {
     c->arena.release(r->block);
     c->arena.release(r->tri_block);
     c->arena.release(r->in_dev);
+    c->arena.release(r->mesh_block);
     g.unlock();
     r->in_host.free();
     r->st_tri.free();
     r->st_kp.free();
     r->st_cells.free();
+    r->st_hdr.free();
+    r->st_vcanon.free();
     delete r;
     c->cv_sched.notify_all();
     return STEREO_OK;
@@ -1624,6 +1885,8 @@ void stereo_destroy(stereo_ctx* c) {
         r->st_tri.free();
         r->st_kp.free();
         r->st_cells.free();
+        r->st_hdr.free();
+        r->st_vcanon.free();
         delete r;
     }
     c->reqs.clear();
@@ -1631,8 +1894,8 @@ void stereo_destroy(stereo_ctx* c) {
     c->desc_host.free();
     if (c->desc_dev) cudaFree(c->desc_dev);
     if (c->own_arena) cudaFree(c->arena_base);
-    for (cudaGraphExec_t g : c->graph_exec)
-        if (g) cudaGraphExecDestroy(g);
+    for (auto& kv : c->graph_exec)
+        if (kv.second) cudaGraphExecDestroy(kv.second);
     if (c->err_dev) cudaFree(c->err_dev);
     c->err_host.free();
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);

@@ -61,6 +61,7 @@ struct PairDev {
     int raster_items;         // tri_rows[T] when known on the host
     int first_pass;
     int K;                    // keypoints per bin
+    int mesh_raster;          // the pass's mesh is on the device: k_raster_mesh rasters it (no k_raster work)
 };
 
 // One launch's pairs: either a single descriptor by value (pd == nullptr)
@@ -148,7 +149,10 @@ struct MeshHdr {
     int stamp;                       // last stamp of the split / flip records
     int err;                         // nonzero: 1 capacity, 2 a point not found in its triangle, 3 round limit
     int rounds, flips;               // insertion rounds and flips of the last pass
-    int pad[2];
+    int frounds;                     // flip rounds of the last pass
+    int n_pl[2];                     // entries of the two pending worklists (this round's, the next's)
+    int n_al[2];                     // entries of the two active-triangle worklists of the flip rounds
+    int pad;
 };
 
 struct MeshDev {
@@ -163,7 +167,9 @@ struct MeshDev {
     // triangles (slot order)
     int4* tri;                // vertex slots (a, b, c) with positive orientation
     int4* opp;                // per edge k (opposite vertex k): (t << 2) | j of the neighbour's twin edge, -1 on the hull
-    unsigned long long* claim;  // insertion / flip claims (all ~0 between rounds)
+    unsigned long long* claim;  // insertion claims (all ~0 between rounds)
+    unsigned long long* fclaim; // flip claims, the round in the high bits (newer rounds win)
+    int* alist;               // two worklists of triangles to check in the flip rounds (2 * t_cap)
     int4* smap;               // split / flip record: (stamp, new ref of old edge 0, 1, 2)
     unsigned long long* tkey; // canonical key (i << 42 | j << 21 | k), when ranked
     int* gcnt;                // triangles per smallest canonical vertex, then their prefix [n_cap + 1]
@@ -171,6 +177,7 @@ struct MeshDev {
     int* pend;                // pending vertex slots of this pass
     int* ploc;                // their current triangle (-1 once inserted, -2 - t while the round that inserted
                               // it into t links its pieces)
+    int* plist;               // two worklists of pending entries (2 * p_cap): the points still to insert
     int* pnb;                 // the edge a pending point lies on: -1 inside, else
                               // ((neighbour + 1) << 4) | (twin edge << 2) | edge
     int* scan;                // scan scratch: chunk totals [scan_cap]

@@ -43,6 +43,7 @@ int work_items(WorkKind k, const PairDev& p) {
         case WK_CLEAR: return cdiv((long long)p.W * p.H, 4096);
         case WK_FILL: return p.cg_key ? cdiv((long long)p.Wc * p.Hc, kFillCells) : 0;
         case WK_RASTER:
+            if (p.mesh_raster) return 0;
             return (p.small_batch ? cdiv(p.n_batch, 8) : cdiv(p.n_small, 256)) + cdiv(p.raster_items, 8) +
                    (p.n_hull >= 0 ? cdiv(p.H, 8) : 0) + (p.cg_key ? cdiv((long long)p.Wc * p.Hc, kFillCells) : 0);
         case WK_RESAMPLE: return cdiv((long long)p.Wc * p.Hc, 8);

@@ -39,9 +39,10 @@ namespace stereo {
 
 namespace {
 
-constexpr int kMeshThreads = 256;
+constexpr int kMeshThreads = 1024;  // one block per SM: the grid barrier has few arrivals
 constexpr int kMaxInsertRounds = 4096;
 constexpr int kMaxFlipRounds = 1 << 15;
+constexpr int kFlipEvery = 0;  // flip sequence after every kFlipEvery-th insertion round (0: at the end)
 constexpr int kScanChunk = 1024;  // elements per warp in the two-level scans
 constexpr unsigned long long kNoClaim = ~0ull;
 
@@ -131,6 +132,8 @@ int scan_cap_of(int W, int H, int n_cap, int t_cap) {
     X(tri, int4, t_cap)                                     \
     X(opp, int4, t_cap)                                     \
     X(claim, unsigned long long, t_cap)                     \
+    X(fclaim, unsigned long long, t_cap)                    \
+    X(alist, int, (size_t)2 * t_cap)                        \
     X(smap, int4, t_cap)                                    \
     X(tkey, unsigned long long, t_cap)                      \
     X(gcnt, int, (size_t)n_cap + 1)                         \
@@ -138,6 +141,7 @@ int scan_cap_of(int W, int H, int n_cap, int t_cap) {
     X(pend, int, p_cap)                                     \
     X(ploc, int, p_cap)                                     \
     X(pnb, int, p_cap)                                      \
+    X(plist, int, (size_t)2 * p_cap)                        \
     X(scan, int, scap)                                      \
     X(large, int, (size_t)t_cap + 1)                        \
     X(lrows, int, (size_t)t_cap + 1)                        \
@@ -234,6 +238,17 @@ __device__ __forceinline__ void each_warp_item(int np, int* pre, C count, B body
     const int wpb = blockDim.x >> 5;
     const int stride = gridDim.x * wpb;
     for (int g = blockIdx.x * wpb + (threadIdx.x >> 5); g < total; g += stride) {
+        const int p = pair_of(pre, np, g);
+        body(p, g - pre[p]);
+    }
+}
+
+// body(pair, local item) over a prefix already in shared memory (no barrier).
+template <class B>
+__device__ __forceinline__ void each_pre(int np, const int* pre, B body) {
+    const int total = pre[np];
+    const int stride = gridDim.x * blockDim.x;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
         const int p = pair_of(pre, np, g);
         body(p, g - pre[p]);
     }
@@ -338,7 +353,8 @@ __device__ __forceinline__ bool split3(const MeshDev& m, int t, int p, int stamp
     m.opp[s2] = make_int4(mk_ref(s0, 2), mk_ref(s1, 2), r.z, 0);
     m.smap[t] = make_int4(stamp, mk_ref(s0, 0), mk_ref(s1, 1), mk_ref(s2, 2));
     m.claim[s1] = m.claim[s2] = kNoClaim;
-    m.smap[s1] = m.smap[s2] = make_int4(0, -1, -1, -1);
+    m.fclaim[s1] = m.fclaim[s2] = kNoClaim;
+    m.smap[s1] = m.smap[s2] = make_int4(stamp, -1, -1, -1);  // new this round: no old edges to map
     return true;
 }
 
@@ -371,7 +387,8 @@ __device__ __forceinline__ bool split_edge(const MeshDev& m, int t, int k, int n
     m.opp[sB] = rB;
     m.smap[t] = smap_rec(stamp, k, -1, k1, mk_ref(sB, k1), k2, mk_ref(t, k2));
     m.claim[sB] = kNoClaim;
-    m.smap[sB] = make_int4(0, -1, -1, -1);
+    m.fclaim[sB] = kNoClaim;
+    m.smap[sB] = make_int4(stamp, -1, -1, -1);
     if (n >= 0) {
         const int j1 = j == 2 ? 0 : j + 1, j2 = j == 0 ? 2 : j - 1;
         const int4 on = m.tri[n], rn = m.opp[n];
@@ -389,7 +406,8 @@ __device__ __forceinline__ bool split_edge(const MeshDev& m, int t, int k, int n
         m.opp[sB2] = rB2;
         m.smap[n] = smap_rec(stamp, j, -1, j1, mk_ref(sB2, j1), j2, mk_ref(n, j2));
         m.claim[sB2] = kNoClaim;
-        m.smap[sB2] = make_int4(0, -1, -1, -1);
+        m.fclaim[sB2] = kNoClaim;
+        m.smap[sB2] = make_int4(stamp, -1, -1, -1);
     }
     return true;
 }
@@ -458,6 +476,7 @@ __device__ __forceinline__ void add_point(const MeshDev& m, MeshCtl* ctl, uint32
         return;
     }
     m.ploc[slot] = t;
+    m.plist[atomicAdd(&m.hdr->n_pl[0], 1)] = slot;
     atomicAdd(&ctl->total_new, 1ull);
 }
 
@@ -486,9 +505,35 @@ __device__ __forceinline__ unsigned long long ld_u64(const unsigned long long* p
     return *(const volatile unsigned long long*)p;
 }
 
-__global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __restrict__ md, int np, MeshCtl* ctl) {
+// A pending point whose triangle t was split or flipped in the round with
+// this stamp moves to the piece that contains it (the pieces are named by
+// t's record).
+__device__ __forceinline__ void relocate(const MeshDev& m, int e, int t, int stamp, MeshCtl* ctl) {
+    const int4 st = m.smap[t];
+    if (st.x != stamp) return;
+    const int2 q = m.pos[m.pend[e]];
+    int found = -1;
+    for (int k = 0; k < 3 && found < 0; k++) {
+        const int r = smap_ref(st, k);
+        if (r >= 0 && contains(m.pos, m.tri[r >> 2], q)) found = r >> 2;
+    }
+    if (found < 0) {
+        m.hdr->err = 2;
+        atomicAdd(&ctl->inserted, 1ull);
+    }
+    m.ploc[e] = found;
+}
+
+__global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __restrict__ mdg, int np, MeshCtl* ctl) {
     __shared__ int pre[kMeshBatch + 1];
+    __shared__ int pre_new[kMeshBatch + 1];  // prefix of the pairs' pending points (fixed after the collection)
+    __shared__ int pre_T[kMeshBatch + 1];    // prefix of their triangle counts (refreshed before each flip sequence)
+    __shared__ MeshDev smd[kMeshBatch];      // the pairs' descriptors, read without a trip to global memory
     cg::grid_group grid = cg::this_grid();
+    for (int i = threadIdx.x; i < np * (int)(sizeof(MeshDev) / 4); i += blockDim.x)
+        reinterpret_cast<int*>(smd)[i] = reinterpret_cast<const int*>(mdg)[i];
+    __syncthreads();
+    const MeshDev* md = smd;
 
     // ---- 0: take over seed meshes; reset the pass's counters
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -496,7 +541,10 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
         ctl->err = 0;
         ctl->rounds = 0;
     }
-    each_item(np, pre, [&](int p) { const MeshDev& m = md[p]; return 1 + (m.seed_T > 0 ? words_of(m) + m.seed_n + m.seed_T : 0); },
+    each_item(np, pre, [&](int p) {
+                  const MeshDev& m = md[p];
+                  return 1 + (m.seed_T > 0 ? words_of(m) + m.seed_n + m.seed_T : ld_int(&m.hdr->T));
+              },
               [&](int p, int i) {
                   const MeshDev& m = md[p];
                   if (i == 0) {
@@ -510,9 +558,15 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
                       h.n_new = h.n_small = h.n_large = h.n_items = h.n_hull = 0;
                       for (int c = 0; c < kMeshClasses; c++) h.cls[c] = h.cls_fill[c] = 0;
                       h.rounds = h.flips = 0;
+                      h.n_pl[0] = h.n_pl[1] = 0;
+                      h.n_al[0] = h.n_al[1] = 0;
                       return;
                   }
                   i -= 1;
+                  if (m.seed_T == 0) {  // a mesh kept from the last pass: its flip claims start empty
+                      m.fclaim[i] = kNoClaim;
+                      return;
+                  }
                   const int words = words_of(m);
                   if (i < words) {
                       m.occ[i] = 0u;
@@ -529,6 +583,7 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
                   m.tri[i] = m.seed_tri[i];
                   m.opp[i] = m.seed_opp[i];
                   m.claim[i] = kNoClaim;
+                  m.fclaim[i] = kNoClaim;
                   m.smap[i] = make_int4(0, -1, -1, -1);
               });
     grid.sync();
@@ -556,13 +611,124 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
               });
     grid.sync();
 
-    // ---- 2: insertion rounds
-    int round = 0;
-    for (; round < kMaxInsertRounds; round++) {
+    // ---- 2: insertion rounds, with flip rounds until no edge is illegal after every
+    // kFlipEvery-th of them (0: once all points are in).  Every round (insertion or
+    // flip) has its own stamp, hdr->stamp + step; the triangles touched since the
+    // last flip sequence (stamp >= that of the first insertion round after it) are
+    // the only ones whose edges can be illegal, the rest being left legal by it.
+    pair_prefix(np, pre_new, [&](int p) { return ld_int(&md[p].hdr->n_new); });
+    __shared__ int pre_pl[kMeshBatch + 1];   // prefix of this round's pending worklists
+    int step = 0, ins_rounds = 0, flip_rounds = 0;
+    unsigned long long flips_seen = 0;
+    // Flip rounds.  Round 0 checks every triangle touched since act_step; later
+    // rounds check a worklist: the triangles flipped in the round before and the
+    // proposers whose flip lost.  A proposal claims both triangles of its edge with
+    // (round tag << 32) | edge, the tag falling with each round so that a newer
+    // claim beats any older one (no reset); tkey[t] holds t's own best proposal.
+    // The flip of a winning edge is made by its lower slot when that one proposed
+    // it, else by the other.
+    __shared__ int pre_al[kMeshBatch + 1];
+    auto run_flips = [&](int act_step) {
+        pair_prefix(np, pre_T, [&](int p) { return ld_int(&md[p].hdr->T); });
+        if (blockIdx.x == 0 && threadIdx.x < np) md[threadIdx.x].hdr->n_al[0] = md[threadIdx.x].hdr->n_al[1] = 0;
+        grid.sync();
+        for (int f = 0; f < kMaxFlipRounds; f++) {
+            const int fstep = ++step;
+            flip_rounds++;
+            const int ab = f & 1;  // this round's worklist (round 0: every triangle, filtered)
+            if (f > 0) pair_prefix(np, pre_al, [&](int p) { return ld_int(&md[p].hdr->n_al[ab]); });
+            if (blockIdx.x == 0 && threadIdx.x < np) md[threadIdx.x].hdr->n_al[ab ^ 1] = 0;
+            const unsigned long long tag = (unsigned long long)(0xFFFFFFFFu - (unsigned)fstep) << 32;
+            const int* pre_f = f == 0 ? pre_T : pre_al;
+            auto item_tri = [&](const MeshDev& m, int i) { return f == 0 ? i : m.alist[ab * m.t_cap + i]; };
+            // propose
+            each_pre(np, pre_f, [&](int p, int i) {
+                const MeshDev& m = md[p];
+                const int t = item_tri(m, i);
+                if (f == 0 && m.smap[t].x < m.hdr->stamp + act_step) return;
+                const int4 tt = m.tri[t], rt = m.opp[t];
+                const int2 a = m.pos[tt.x], b = m.pos[tt.y], c = m.pos[tt.z];
+                unsigned long long best = kNoClaim;
+                for (int k = 0; k < 3; k++) {
+                    const int r = ref_of(rt, k);
+                    if (r < 0) continue;
+                    const int n = r >> 2;
+                    const int y = vtx(m.tri[n], r & 3);
+                    if (incircle_sos(a, b, c, m.pos[y])) {
+                        const unsigned long long key = tag | (unsigned)(n < t ? r : mk_ref(t, k));
+                        atomicMin(m.fclaim + t, key);
+                        atomicMin(m.fclaim + n, key);
+                        best = min(best, key);
+                    }
+                }
+                m.tkey[t] = best;
+            });
+            grid.sync();
+            // flip each winning edge once
+            each_pre(np, pre_f, [&](int p, int i) {
+                const MeshDev& m = md[p];
+                const int t = item_tri(m, i);
+                if (f == 0 && m.smap[t].x < m.hdr->stamp + act_step) return;
+                const unsigned long long key = m.fclaim[t];
+                if (m.tkey[t] != key || (key >> 32) != (tag >> 32)) return;  // t did not propose the winner
+                const int tm = (int)((key & 0xFFFFFFFFull) >> 2), km = (int)(key & 3);
+                int n;
+                if (t == tm) n = ref_of(m.opp[t], km) >> 2;
+                else n = tm;
+                if (m.fclaim[n] != key) return;
+                if (t != tm && m.tkey[tm] == key && m.fclaim[tm] == key) return;  // the lower slot proposed it too: it flips
+                const int r = ref_of(m.opp[tm], km);
+                flip(m, tm, km, r >> 2, r & 3, m.hdr->stamp + fstep);
+                const int at = atomicAdd(&m.hdr->n_al[ab ^ 1], 2);
+                m.alist[(ab ^ 1) * m.t_cap + at] = tm;
+                m.alist[(ab ^ 1) * m.t_cap + at + 1] = r >> 2;
+                atomicAdd(&ctl->flips, 1ull);
+                atomicAdd(&m.hdr->flips, 1);
+            });
+            grid.sync();
+            // the flipped triangles link their outer edges (0 and 2); proposers that
+            // lost join the next worklist; waiting points move with their triangle
+            __shared__ int pre_fl[kMeshBatch + 1];
+            pair_prefix(np, pre_fl, [&](int p) { return ld_int(&md[p].hdr->n_al[ab ^ 1]); });
+            each_pre(np, pre_fl, [&](int p, int i) {
+                const MeshDev& m = md[p];
+                const int t = m.alist[(ab ^ 1) * m.t_cap + i];
+                const int stamp = m.hdr->stamp + fstep;
+                relink(m, t, 0, stamp);
+                relink(m, t, 2, stamp);
+            });
+            each_pre(np, pre_f, [&](int p, int i) {
+                const MeshDev& m = md[p];
+                const int t = item_tri(m, i);
+                if (f == 0 && m.smap[t].x < m.hdr->stamp + act_step) return;
+                const unsigned long long key = m.tkey[t];
+                if (key == kNoClaim || m.smap[t].x == m.hdr->stamp + fstep) return;  // no proposal, or flipped
+                m.alist[(ab ^ 1) * m.t_cap + atomicAdd(&m.hdr->n_al[ab ^ 1], 1)] = t;
+            });
+            if (kFlipEvery > 0)
+                each_pre(np, pre_new, [&](int p, int e) {
+                    const MeshDev& m = md[p];
+                    const int lt = m.ploc[e];
+                    if (lt >= 0) relocate(m, e, lt, m.hdr->stamp + fstep, ctl);
+                });
+            grid.sync();
+            const unsigned long long fl = ld_u64(&ctl->flips);
+            if (fl == flips_seen) break;
+            flips_seen = fl;
+            if (f == kMaxFlipRounds - 1 && blockIdx.x == 0 && threadIdx.x < np) md[threadIdx.x].hdr->err = 3;
+        }
+    };
+    int act_step = 1;  // first step not yet covered by a flip sequence
+    for (; ins_rounds < kMaxInsertRounds; ins_rounds++) {
         if (ld_u64(&ctl->inserted) >= ld_u64(&ctl->total_new)) break;
+        const int ins_step = ++step;
+        const int wb = ins_rounds & 1;  // this round's worklist; survivors go to the other
+        pair_prefix(np, pre_pl, [&](int p) { return ld_int(&md[p].hdr->n_pl[wb]); });
+        if (blockIdx.x == 0 && threadIdx.x < np) md[threadIdx.x].hdr->n_pl[wb ^ 1] = 0;
         // claim the triangle (and the neighbour across the edge the point lies on)
-        each_item(np, pre, [&](int p) { return ld_int(&md[p].hdr->n_new); }, [&](int p, int e) {
+        each_pre(np, pre_pl, [&](int p, int i) {
             const MeshDev& m = md[p];
+            const int e = m.plist[wb * m.p_cap + i];
             const int t = m.ploc[e];
             if (t < 0) return;
             const int vid = m.pend[e];
@@ -582,15 +748,16 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
         });
         grid.sync();
         // a point holding all its claims splits them
-        each_item(np, pre, [&](int p) { return ld_int(&md[p].hdr->n_new); }, [&](int p, int e) {
+        each_pre(np, pre_pl, [&](int p, int i) {
             const MeshDev& m = md[p];
+            const int e = m.plist[wb * m.p_cap + i];
             const int t = m.ploc[e];
             if (t < 0) return;
             const unsigned long long key = m.tkey[e];
             const int code = m.pnb[e];
             const int n = code >= 0 ? (code >> 4) - 1 : -1;
             if (m.claim[t] != key || (n >= 0 && m.claim[n] != key)) return;
-            const int stamp = m.hdr->stamp + round + 1;
+            const int stamp = m.hdr->stamp + ins_step;
             const int vid = m.pend[e];
             const bool ok = code < 0 ? split3(m, t, vid, stamp) : split_edge(m, t, code & 3, n, (code >> 2) & 3, vid, stamp);
             m.ploc[e] = ok ? -2 - t : -1;
@@ -598,11 +765,13 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
         });
         grid.sync();
         // link the pieces to their neighbours; the others move to the piece they lie in
-        each_item(np, pre, [&](int p) { return ld_int(&md[p].hdr->n_new); }, [&](int p, int e) {
+        // and stay on the worklist
+        each_pre(np, pre_pl, [&](int p, int i) {
             const MeshDev& m = md[p];
+            const int e = m.plist[wb * m.p_cap + i];
             const int lt = m.ploc[e];
             if (lt == -1) return;
-            const int stamp = m.hdr->stamp + round + 1;
+            const int stamp = m.hdr->stamp + ins_step;
             const int code = m.pnb[e];
             const int n = code >= 0 ? (code >> 4) - 1 : -1;
             if (lt <= -2) {
@@ -624,82 +793,21 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
                 m.ploc[e] = -1;
                 return;
             }
-            const int t = lt;
-            m.claim[t] = kNoClaim;
+            m.claim[lt] = kNoClaim;
             if (n >= 0) m.claim[n] = kNoClaim;
-            const int4 st = m.smap[t];
-            if (st.x != stamp) return;  // its triangle was not split
-            const int2 q = m.pos[m.pend[e]];
-            int found = -1;
-            for (int k = 0; k < 3 && found < 0; k++) {
-                const int r = smap_ref(st, k);
-                if (r >= 0 && contains(m.pos, m.tri[r >> 2], q)) found = r >> 2;
-            }
-            if (found < 0) {
-                m.hdr->err = 2;
-                atomicAdd(&ctl->inserted, 1ull);
-            }
-            m.ploc[e] = found;
+            relocate(m, e, lt, stamp, ctl);
+            if (m.ploc[e] >= 0) m.plist[(wb ^ 1) * m.p_cap + atomicAdd(&m.hdr->n_pl[wb ^ 1], 1)] = e;
         });
         grid.sync();
+        if (kFlipEvery > 0 && (ins_rounds + 1) % kFlipEvery == 0) {
+            run_flips(act_step);
+            act_step = step + 1;
+        }
     }
-    if (round == kMaxInsertRounds && ld_u64(&ctl->inserted) < ld_u64(&ctl->total_new)) {
+    if (act_step <= step) run_flips(act_step);  // the insertions since the last flip sequence
+    if (ins_rounds == kMaxInsertRounds && ld_u64(&ctl->inserted) < ld_u64(&ctl->total_new)) {
         if (blockIdx.x == 0 && threadIdx.x < np) md[threadIdx.x].hdr->err = 3;
     }
-    const int ins_rounds = round;
-
-    // ---- 3: flip rounds until no edge is illegal
-    unsigned long long flips_seen = 0;
-    int fround = 0;
-    for (; fround < kMaxFlipRounds; fround++) {
-        const int stamp_off = ins_rounds + fround + 1;
-        // propose: an illegal edge claims both its triangles (lower slot proposes)
-        each_item(np, pre, [&](int p) { return ld_int(&md[p].hdr->T); }, [&](int p, int t) {
-            const MeshDev& m = md[p];
-            const int4 tt = m.tri[t], rt = m.opp[t];
-            const int2 a = m.pos[tt.x], b = m.pos[tt.y], c = m.pos[tt.z];
-            for (int k = 0; k < 3; k++) {
-                const int r = ref_of(rt, k);
-                if (r < 0 || (r >> 2) < t) continue;
-                const int n = r >> 2;
-                const int y = vtx(m.tri[n], r & 3);
-                if (incircle_sos(a, b, c, m.pos[y])) {
-                    const unsigned long long key = (unsigned long long)mk_ref(t, k);
-                    atomicMin(m.claim + t, key);
-                    atomicMin(m.claim + n, key);
-                }
-            }
-        });
-        grid.sync();
-        // flip where an edge holds both claims
-        each_item(np, pre, [&](int p) { return ld_int(&md[p].hdr->T); }, [&](int p, int t) {
-            const MeshDev& m = md[p];
-            const unsigned long long key = m.claim[t];
-            if (key == kNoClaim || (int)(key >> 2) != t) return;
-            const int k = (int)(key & 3);
-            const int r = ref_of(m.opp[t], k);
-            const int n = r >> 2;
-            if (m.claim[n] != key) return;
-            flip(m, t, k, n, r & 3, m.hdr->stamp + stamp_off);
-            atomicAdd(&ctl->flips, 1ull);
-            atomicAdd(&m.hdr->flips, 1);
-        });
-        grid.sync();
-        // claims back to empty; flipped triangles link their outer edges (0 and 2)
-        each_item(np, pre, [&](int p) { return ld_int(&md[p].hdr->T); }, [&](int p, int t) {
-            const MeshDev& m = md[p];
-            if (m.claim[t] != kNoClaim) m.claim[t] = kNoClaim;
-            const int stamp = m.hdr->stamp + stamp_off;
-            if (m.smap[t].x != stamp) return;
-            relink(m, t, 0, stamp);
-            relink(m, t, 2, stamp);
-        });
-        grid.sync();
-        const unsigned long long f = ld_u64(&ctl->flips);
-        if (f == flips_seen) break;
-        flips_seen = f;
-    }
-    if (fround == kMaxFlipRounds && blockIdx.x == 0 && threadIdx.x < np) md[threadIdx.x].hdr->err = 3;
 
     // ---- 4: canonical ranks (pairs whose next pass is the last)
     // vertex rank = vertex pixels before it in raster order (the bit map's prefix)
@@ -872,9 +980,10 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
     if (blockIdx.x == 0 && threadIdx.x < np) {
         MeshHdr& h = *md[threadIdx.x].hdr;
         h.rounds = ins_rounds;
-        h.stamp += ins_rounds + fround + 2;
+        h.frounds = flip_rounds;
+        h.stamp += step + 1;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->rounds = ins_rounds + fround;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->rounds = ins_rounds + flip_rounds;
 }
 
 }  // namespace

@@ -241,9 +241,9 @@ def test_validate(oracle_mod, name, sz, first, bulk):
     assert np.array_equal(xd.cpu().numpy(), want)
 
 
-def _run_ctx(pairs, max_slots=1, host_threads=1, budget=1 << 30, window_us=0, prm=PRM):
+def _run_ctx(pairs, max_slots=1, host_threads=1, budget=1 << 30, window_us=0, prm=PRM, host_mesh=0):
     with S.Context(mem_budget_bytes=budget, max_slots=max_slots, host_threads=host_threads,
-                   batch_window_us=window_us, **prm) as ctx:
+                   batch_window_us=window_us, host_mesh=host_mesh, **prm) as ctx:
         tickets = [ctx.submit(_t(p.left), _t(p.right), p.left.shape[1], p.left.shape[0], p.dmax, p.iters, p.cell)
                    for p in pairs]
         outs = []
@@ -304,7 +304,7 @@ def test_end_to_end_idle_workers_and_round_shapes(oracle_mod):
     records, so neither the clear nor the reset has launches of its own)."""
     p = scenes.config_pairs("driving_1242x375")[0]
     H, W = p.left.shape
-    with S.Context(mem_budget_bytes=1 << 30, max_slots=1, host_threads=4, **PRM) as ctx:
+    with S.Context(mem_budget_bytes=1 << 30, max_slots=1, host_threads=4, host_mesh=1, **PRM) as ctx:
         t = ctx.submit(_t(p.left), _t(p.right), W, H, p.dmax, p.iters, p.cell)
         got = ctx.result_tensors(ctx.poll(t))
         ctx.release(t)
@@ -314,7 +314,27 @@ def test_end_to_end_idle_workers_and_round_shapes(oracle_mod):
     k = list(st.kind_launches)
     assert k[0:4] == [1, 1, 1, 1]  # one seed round
     assert k[5] == k[6] == k[7] == p.iters  # one iteration round per pass
-    assert k[4] == 0 and k[8] == 0
+    assert k[4] == 0 and k[8] == 0 and k[9] == 0
+    assert st.gpu_rounds == 1 + p.iters
+
+
+@pytest.mark.parametrize("host_mesh", [0, 1])
+def test_end_to_end_mesh_paths(oracle_mod, host_mesh):
+    """Both mesh paths on one driving pair: the host triangulating every pass,
+    or only the first pass's mesh on the host and each later one re-tessellated
+    on the device (one mesh launch per resampling pass, no host step between
+    passes).  Both equal the oracle."""
+    p = scenes.config_pairs("driving_1242x375")[0]
+    H, W = p.left.shape
+    with S.Context(mem_budget_bytes=1 << 30, max_slots=1, host_threads=2, host_mesh=host_mesh, **PRM) as ctx:
+        t = ctx.submit(_t(p.left), _t(p.right), W, H, p.dmax, p.iters, p.cell)
+        got = ctx.result_tensors(ctx.poll(t))
+        ctx.release(t)
+        st = ctx.stats()
+    _compare_run(oracle_mod, p, got)
+    k = list(st.kind_launches)
+    assert k[5] == k[6] == k[7] == p.iters
+    assert k[9] == (0 if host_mesh else p.iters - 1)
     assert st.gpu_rounds == 1 + p.iters
 
 
@@ -362,9 +382,9 @@ def test_batched_serving_matches_solo(oracle_mod):
     """Continuous batching: results in a mixed batch equal solo results bit for bit."""
     pairs = [scenes.make_pair("polygon", 320, 240, 500 + i, 64, 3, 16, n_poly=10) for i in range(3)]
     pairs += [scenes.make_pair("driving", 400, 150, 600 + i, 96, 2, 8, n_box=10) for i in range(3)]
-    solo = [_run_ctx([p])[0] for p in pairs]
+    solo = [_run_ctx([p], host_mesh=1)[0] for p in pairs]  # host meshes, one pair at a time
     for slots, threads, window in ((4, 3, 0), (6, 2, 2000)):
-        mixed = _run_ctx(pairs, max_slots=slots, host_threads=threads, window_us=window)
+        mixed = _run_ctx(pairs, max_slots=slots, host_threads=threads, window_us=window)  # device meshes, batched
         for a, b in zip(solo, mixed):
             for k in ("D_f", "C_f", "mask", "planeidx"):
                 assert torch.equal(a[k], b[k]), k
