@@ -325,7 +325,8 @@ def run_ours(args):
                   "insert_rounds_per_pass": (s1.mesh_insert_rounds - s0.mesh_insert_rounds) / max(1, mp),
                   "flip_rounds_per_pass": (s1.mesh_flip_rounds - s0.mesh_flip_rounds) / max(1, mp),
                   "flips_per_pass": (s1.mesh_flips - s0.mesh_flips) / max(1, mp),
-                  "points_per_pass": (s1.mesh_points - s0.mesh_points) / max(1, mp)}
+                  "points_per_pass": (s1.mesh_points - s0.mesh_points) / max(1, mp),
+                  "edge_points_per_pass": (s1.mesh_edge_points - s0.mesh_edge_points) / max(1, mp)}
 
     # end to end through the public API with host buffers, copies inside the span
     e2e_spans, _ = timed(max(1, min(args.steps, 3)), host=True)

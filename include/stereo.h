@@ -65,7 +65,8 @@ typedef struct {
     int uniq_margin;           /* epipolar uniqueness margin in census bits */
     int host_threads;          /* host triangulation workers (0 = 1) */
     void* stream;              /* cudaStream_t for all work (NULL = library creates one) */
-    int profile;               /* N > 0: time the kernel launches of every N-th GPU round with
+    int profile;               /* N > 0: time the kernel launches of one GPU round in N (the
+                                  sampled position within each N rounds rotates) with
                                   CUDA events on `stream` and accumulate per-kind durations in
                                   stereo_stats (1 = every round; event nodes lengthen a round,
                                   so a larger N disturbs the timing less); 0 = off */
@@ -194,6 +195,7 @@ typedef struct {
      * rounds and flip rounds of the launch that served each (a launch serves several
      * pairs), edge flips, and points inserted */
     long long mesh_passes, mesh_insert_rounds, mesh_flip_rounds, mesh_flips, mesh_points;
+    long long mesh_edge_points;  /* of the points, those that lay on an edge when inserted */
 } stereo_stats;
 int stereo_get_stats(stereo_ctx* ctx, stereo_stats* out);
 

@@ -56,7 +56,7 @@ class Stats(ctypes.Structure):
                 ("graph_instantiations", ctypes.c_longlong), ("kind_timed", ctypes.c_longlong * 10),
                 ("mesh_passes", ctypes.c_longlong), ("mesh_insert_rounds", ctypes.c_longlong),
                 ("mesh_flip_rounds", ctypes.c_longlong), ("mesh_flips", ctypes.c_longlong),
-                ("mesh_points", ctypes.c_longlong)]
+                ("mesh_points", ctypes.c_longlong), ("mesh_edge_points", ctypes.c_longlong)]
 
 
 class Tuning(ctypes.Structure):

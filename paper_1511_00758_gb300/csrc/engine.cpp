@@ -1115,7 +1115,12 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
     // that graph has run, so they are recycled a round later; events are
     // never destroyed while the context lives, and an executable graph is
     // always updated with fresh events before it is launched again.
-    Lr.prof = c->cfg.profile > 0 && c->rounds_seen++ % c->cfg.profile == 0;
+    // one round in every `profile`, the sampled position rotating (round r is timed when
+    // r mod P == (r / P) mod P), so rounds that recur with period P are all sampled
+    {
+        const long long P = c->cfg.profile, r = c->rounds_seen++;
+        Lr.prof = P > 0 && r % P == (r / P) % P;
+    }
     if (Lr.prof)
         while (c->ev_pool.size() < 32) {
             cudaEvent_t ev = nullptr;
@@ -1269,6 +1274,7 @@ void scheduler(stereo_ctx* c) {
                 c->stats.mesh_insert_rounds += h.rounds;
                 c->stats.mesh_flip_rounds += h.frounds;
                 c->stats.mesh_flips += h.flips;
+                c->stats.mesh_edge_points += h.edge_ins;
                 c->stats.mesh_points += h.n - (r->dev_n > 0 ? r->dev_n : r->n_support.back());
                 r->dev_n = h.n;
                 r->T = h.T;

@@ -152,7 +152,7 @@ struct MeshHdr {
     int frounds;                     // flip rounds of the last pass
     int n_pl[2];                     // entries of the two pending worklists (this round's, the next's)
     int n_al[2];                     // entries of the two active-triangle worklists of the flip rounds
-    int pad;
+    int edge_ins;                    // insertions on an edge (2 -> 4 or hull 1 -> 2) in the last pass
 };
 
 struct MeshDev {

@@ -560,6 +560,7 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
                       h.rounds = h.flips = 0;
                       h.n_pl[0] = h.n_pl[1] = 0;
                       h.n_al[0] = h.n_al[1] = 0;
+                      h.edge_ins = 0;
                       return;
                   }
                   i -= 1;
@@ -760,6 +761,7 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
             const int stamp = m.hdr->stamp + ins_step;
             const int vid = m.pend[e];
             const bool ok = code < 0 ? split3(m, t, vid, stamp) : split_edge(m, t, code & 3, n, (code >> 2) & 3, vid, stamp);
+            if (code >= 0) atomicAdd(&m.hdr->edge_ins, 1);
             m.ploc[e] = ok ? -2 - t : -1;
             atomicAdd(&ctl->inserted, 1ull);
         });
