@@ -128,6 +128,25 @@ int stereo_create(const stereo_config* cfg, stereo_ctx** out);
 int stereo_submit(stereo_ctx* ctx, int stream_id, const uint8_t* left, const uint8_t* right,
                   int w, int h, int dmax, int iters, int cell, uint64_t* ticket_out);
 
+/* One pair of a batch submission: the arguments of stereo_submit. */
+typedef struct {
+    int stream_id;
+    const uint8_t* left;
+    const uint8_t* right;
+    int w, h, dmax, iters, cell;
+} stereo_pair;
+
+/* stereo_submit for n pairs at once, for callers serving many cameras: the
+ * inputs are copied with one synchronisation and the pairs queued together,
+ * so they start in the same GPU round (no counterpart in the paper, which
+ * takes one pair).  Every pair is checked first: an invalid one rejects the
+ * batch (STEREO_E_INVAL, nothing queued), as does one that needs more than
+ * the whole budget (STEREO_E_NOMEM).  Pairs are then taken in order while the
+ * queue has room; tickets_out[i] receives the ticket of pair i.  Returns the
+ * number of pairs taken (1..n), or STEREO_E_BUSY when none could be, or
+ * STEREO_E_CUDA / STEREO_E_NOMEM when copying failed (nothing queued). */
+int stereo_submit_batch(stereo_ctx* ctx, const stereo_pair* pairs, int n, uint64_t* tickets_out);
+
 /* Wait up to timeout_us (<0 = forever, 0 = test only) for a ticket.  On
  * STEREO_OK, *out describes the result; its buffers stay valid until
  * stereo_release.  STEREO_E_PENDING = not ready yet.  A request that failed
@@ -176,7 +195,8 @@ const char* stereo_last_error(void);
  * round; kind_ms[k] / kind_timed[k] is the mean launch time), and
  * kind_bytes[k] the algorithmic bytes all kind_launches[k] launches had to move (census:
  * 2 B/px read + 8.125 B/px written; raster clear and raster: 4 B/px written each; validate:
- * 13.125 B/px read (12.125 on a first pass) + 6 B/px written). */
+ * 13.125 B/px read (12.125 on a first pass) + 6 B/px written; mesh: 16 B per cell record read,
+ * 16 B per new support point and 72 B per triangle of the new mesh written). */
 typedef struct {
     long long kernel_launches;
     long long requests_done;

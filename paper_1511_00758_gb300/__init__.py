@@ -13,7 +13,7 @@ import os
 from . import _build
 
 __all__ = [
-    "StereoError", "load", "lib", "Config", "Result", "Stats", "Tuning", "Context",
+    "StereoError", "load", "lib", "Config", "Result", "Pair", "Stats", "Tuning", "Context",
     "census", "fast", "epipolar_match", "delaunay", "delaunay_parallel", "delaunay_insert", "planes", "raster_scratch_bytes", "raster", "raster_noalloc", "validate_bulk",
     "validate", "resample_match", "ERRORS",
 ]
@@ -47,6 +47,12 @@ class Result(ctypes.Structure):
                 ("host_mesh_ms", ctypes.c_double), ("status", ctypes.c_int)]
 
 
+class Pair(ctypes.Structure):
+    _fields_ = [("stream_id", ctypes.c_int), ("left", ctypes.c_void_p), ("right", ctypes.c_void_p),
+                ("w", ctypes.c_int), ("h", ctypes.c_int), ("dmax", ctypes.c_int), ("iters", ctypes.c_int),
+                ("cell", ctypes.c_int)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_longlong), ("requests_done", ctypes.c_longlong),
                 ("batched_pairs", ctypes.c_longlong), ("gpu_rounds", ctypes.c_longlong),
@@ -76,6 +82,7 @@ _SIGS = {
     "stereo_default_config": (None, [ctypes.POINTER(Config)]),
     "stereo_create": (_I, [ctypes.POINTER(Config), ctypes.POINTER(_P)]),
     "stereo_submit": (_I, [_P, _I, _P, _P, _I, _I, _I, _I, _I, ctypes.POINTER(ctypes.c_uint64)]),
+    "stereo_submit_batch": (_I, [_P, ctypes.POINTER(Pair), _I, ctypes.POINTER(ctypes.c_uint64)]),
     "stereo_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(Result), _I]),
     "stereo_poll_host": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(Result), _I, _P, _P, _P]),
     "stereo_release": (_I, [_P, ctypes.c_uint64]),
@@ -257,6 +264,17 @@ class Context:
         _check(lib().stereo_submit(self.h, stream_id, _ptr(left), _ptr(right), w, h, dmax, iters, cell,
                                    ctypes.byref(t)), "submit")
         return t.value
+
+    def submit_batch(self, pairs):
+        """pairs: (left, right, w, h, dmax, iters, cell[, stream_id]) tuples.  Returns the
+        tickets of the pairs taken (a prefix of the list; raises when none is)."""
+        arr = (Pair * len(pairs))()
+        for i, q in enumerate(pairs):
+            left, right, w, h, dmax, iters, cell = q[:7]
+            arr[i] = Pair(q[7] if len(q) > 7 else 0, _ptr(left), _ptr(right), w, h, dmax, iters, cell)
+        tk = (ctypes.c_uint64 * len(pairs))()
+        n = _check(lib().stereo_submit_batch(self.h, arr, len(pairs), tk), "submit_batch")
+        return list(tk[:n])
 
     def poll(self, ticket, timeout_us=-1):
         r = Result()

@@ -398,6 +398,7 @@ struct stereo_ctx {
     int host_busy = 0;
     int seed_busy = 0;  // of which seed host steps
     std::chrono::steady_clock::time_point last_submit{};  // time of the latest submission
+    bool last_batch = false;  // it was a batch of several pairs (no more are expected right after it)
     std::atomic<int> mesh_steps{0};  // host mesh steps run (for the failure-injection hook)
     Pool pool;
     Pinned desc_host;
@@ -724,7 +725,7 @@ void admit(stereo_ctx* c) {
 // an offset array of n + 1 ints.  Returns device pointers via out params.
 // Then, for the pairs whose mesh is on the device: their PairDev and
 // MeshDev for the device-mesh raster (pass >= 2), the MeshDev of those that
-// re-tessellate this round, and one MeshCtl per launch of kMeshBatch pairs.
+// re-tessellate this round.
 struct Group {
     std::vector<Request*> reqs;
     const PairDev* pd = nullptr;
@@ -735,7 +736,6 @@ struct Group {
     const PairDev* mr_pd = nullptr;
     const MeshDev* mr_md = nullptr;
     const MeshDev* mp_md = nullptr;
-    MeshCtl* ctl = nullptr;
 };
 
 void count_mesh(Group& g) {
@@ -748,10 +748,9 @@ void count_mesh(Group& g) {
 
 size_t group_bytes(const Group& g) {
     const size_t n = g.reqs.size();
-    const int chunks = (g.n_mp + kMeshBatch - 1) / kMeshBatch;
     return align_up(sizeof(PairDev) * n, 256) + WK_COUNT * align_up(sizeof(int) * (n + 1), 256) +
            align_up(sizeof(PairDev) * g.n_mr, 256) + align_up(sizeof(MeshDev) * g.n_mr, 256) +
-           align_up(sizeof(MeshDev) * g.n_mp, 256) + align_up(sizeof(MeshCtl) * chunks, 256);
+           align_up(sizeof(MeshDev) * g.n_mp, 256);
 }
 
 void fill_group(Group& g, char* host, char* dev) {
@@ -789,7 +788,6 @@ void fill_group(Group& g, char* host, char* dev) {
     MeshDev* mp_md = (MeshDev*)(host + off);
     g.mp_md = (const MeshDev*)(dev + off);
     off += align_up(sizeof(MeshDev) * g.n_mp, 256);
-    g.ctl = (MeshCtl*)(dev + off);
     int a = 0, b = 0;
     for (size_t i = 0; i < n; i++) {
         const Request* r = g.reqs[i];
@@ -986,9 +984,9 @@ cudaError_t record_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr, 
         return cudaSuccess;
     }));
     CKQ(Lr.run(STEREO_K_RESAMPLE, ni, 0.0, [&] { return launch_resample(batch_of(iter, WK_RESAMPLE), prm, s); }));
-    for (int a = 0, k = 0; a < iter.n_mp; a += kMeshBatch, k++) {
+    for (int a = 0; a < iter.n_mp; a += kMeshBatch) {
         const int np = std::min(kMeshBatch, iter.n_mp - a);
-        CKQ(Lr.run(STEREO_K_MESH, np, 0.0, [&] { return launch_mesh_pass(iter.mp_md + a, np, iter.ctl + k, s); }));
+        CKQ(Lr.run(STEREO_K_MESH, np, 0.0, [&] { return launch_mesh_pass(iter.mp_md + a, np, s); }));
     }
     CK(cudaMemcpyAsync(c->err_host.p, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
     return cudaSuccess;
@@ -1220,8 +1218,8 @@ void scheduler(stereo_ctx* c) {
                     const int busy = c->cfg.batch_window_us > 0 ? c->host_busy : c->seed_busy;
                     const auto now = std::chrono::steady_clock::now();
                     const auto quiet_end = c->last_submit + std::chrono::microseconds(kQuietUs);
-                    const bool arriving = c->dev_mesh && c->cfg.batch_window_us == 0 && now < quiet_end &&
-                                          (int)c->active.size() < c->cfg.max_slots;
+                    const bool arriving = c->dev_mesh && c->cfg.batch_window_us == 0 && !c->last_batch &&
+                                          now < quiet_end && (int)c->active.size() < c->cfg.max_slots;
                     if (window > 0 && (busy > 0 || arriving) && !c->stop) {
                         if (!waiting) {
                             waiting = true;
@@ -1270,6 +1268,10 @@ void scheduler(stereo_ctx* c) {
                     finish(c, *r, STEREO_E_INTERNAL);
                     continue;
                 }
+                // algorithmic bytes of the pass: the cell records read (16 B each), the new
+                // points written (16 B), the finished mesh written (72 B per triangle: vertices
+                // and neighbours 32 B, raster inputs 40 B)
+                c->stats.kind_bytes[STEREO_K_MESH] += 16.0 * r->dev.Wc * r->dev.Hc + 16.0 * h.n_new + 72.0 * h.T;
                 c->stats.mesh_passes++;
                 c->stats.mesh_insert_rounds += h.rounds;
                 c->stats.mesh_flip_rounds += h.frounds;
@@ -1707,79 +1709,121 @@ int stereo_create(const stereo_config* cfg, stereo_ctx** out) {
     return STEREO_OK;
 }
 
+namespace {
+bool valid_pair(const stereo_pair& p) {
+    return p.left && p.right && valid_size(p.w, p.h) && p.dmax >= 1 && p.dmax <= 256 && p.iters >= 1 && p.cell >= 1;
+}
+}  // namespace
+
+// Submission of n pairs: every argument is checked first (one bad pair
+// rejects the batch); the pairs are then taken in order while the queue has
+// room, their inputs copied with one synchronisation for the batch, and
+// queued under one lock, so the scheduler sees them together.
+int stereo_submit_batch(stereo_ctx* c, const stereo_pair* pairs, int n, uint64_t* tickets_out) {
+    if (!c || !pairs || n < 1 || !tickets_out) return STEREO_E_INVAL;
+    for (int i = 0; i < n; i++)
+        if (!valid_pair(pairs[i])) return STEREO_E_INVAL;
+    std::vector<Request*> rs;
+    rs.reserve(n);
+    auto drop_all = [&](int rc) {
+        {
+            std::lock_guard<std::mutex> g2(c->mu);
+            for (Request* r : rs) c->arena.release(r->in_dev);
+        }
+        for (Request* r : rs) {
+            r->in_host.free();
+            delete r;
+        }
+        return rc;
+    };
+    for (int i = 0; i < n; i++) {
+        const stereo_pair& q = pairs[i];
+        Request* r = new Request();
+        r->in_host.pool = r->st_tri.pool = r->st_kp.pool = r->st_cells.pool = r->st_hdr.pool = r->st_vcanon.pool =
+            &c->pinned;
+        r->pool = &c->pool;
+        r->stream_id = q.stream_id;
+        r->W = q.w;
+        r->H = q.h;
+        r->dmax = q.dmax;
+        r->iters = q.iters;
+        r->cell = q.cell;
+        const int sz_min = q.iters >= 2 ? std::max(1, q.cell >> (q.iters - 2)) : 0;
+        r->ncell_max = q.iters >= 2 ? cells_of(q.w, q.h, sz_min) : 1;
+        rs.push_back(r);
+        if (block_bytes(*r, c->K) > c->cfg.mem_budget_bytes) return drop_all(STEREO_E_NOMEM);
+    }
+    // where the inputs live: device (or managed) memory and page-locked host memory are
+    // copied straight to the arena (one DMA each), pageable memory through pinned staging
+    std::vector<char> kind(n);  // 'd' device, 'p' page-locked, 'h' pageable
+    for (int i = 0; i < n; i++) {
+        cudaPointerAttributes at{}, at_r{};
+        const bool known = cudaPointerGetAttributes(&at, pairs[i].left) == cudaSuccess &&
+                           cudaPointerGetAttributes(&at_r, pairs[i].right) == cudaSuccess;
+        cudaGetLastError();
+        const bool dev_in = known && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+        const bool pinned_in = known && !dev_in && at.type == cudaMemoryTypeHost && at_r.type == cudaMemoryTypeHost;
+        kind[i] = dev_in ? 'd' : pinned_in ? 'p' : 'h';
+    }
+    int take = 0;
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        int queued = (int)c->queue.size();
+        for (; take < n; take++) {
+            if (queued >= c->cfg.max_queue && (int)c->active.size() >= c->cfg.max_slots) break;
+            Request* r = rs[take];
+            if (kind[take] != 'h') {
+                r->in_dev = (uint8_t*)c->arena.alloc(2 * (size_t)r->W * r->H);
+                if (!r->in_dev) break;
+            }
+            queued++;
+        }
+    }
+    if (take == 0) return drop_all(STEREO_E_BUSY);
+    for (int i = take; i < n; i++) delete rs[i];
+    rs.resize(take);
+    bool copied = false;
+    for (int i = 0; i < take; i++) {
+        Request* r = rs[i];
+        const size_t N = (size_t)r->W * r->H;
+        if (kind[i] != 'h') {
+            const cudaMemcpyKind k = kind[i] == 'd' ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+            cudaMemcpyAsync(r->in_dev, pairs[i].left, N, k, c->copy_stream);
+            cudaMemcpyAsync(r->in_dev + N, pairs[i].right, N, k, c->copy_stream);
+            copied = true;
+        } else {
+            if (!r->in_host.ensure(2 * N)) return drop_all(STEREO_E_NOMEM);
+            std::memcpy(r->in_host.p, pairs[i].left, N);
+            std::memcpy((char*)r->in_host.p + N, pairs[i].right, N);
+        }
+    }
+    if (copied && cudaStreamSynchronize(c->copy_stream) != cudaSuccess) {
+        cudaGetLastError();
+        return drop_all(STEREO_E_CUDA);
+    }
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        const double t = now_ms();
+        for (int i = 0; i < take; i++) {
+            Request* r = rs[i];
+            r->ticket = c->next_ticket++;
+            r->t_submit = t;
+            c->reqs[r->ticket] = r;
+            c->queue.push_back(r);
+            tickets_out[i] = r->ticket;
+        }
+        c->last_submit = std::chrono::steady_clock::now();
+        c->last_batch = n > 1;
+    }
+    c->cv_sched.notify_all();
+    return take;
+}
+
 int stereo_submit(stereo_ctx* c, int stream_id, const uint8_t* left, const uint8_t* right, int w, int h,
                   int dmax, int iters, int cell, uint64_t* ticket_out) {
-    if (!c || !left || !right || !ticket_out) return STEREO_E_INVAL;
-    if (!valid_size(w, h) || dmax < 1 || dmax > 256 || iters < 1 || cell < 1) return STEREO_E_INVAL;
-    Request* r = new Request();
-    r->in_host.pool = r->st_tri.pool = r->st_kp.pool = r->st_cells.pool = r->st_hdr.pool = r->st_vcanon.pool =
-        &c->pinned;
-    r->pool = &c->pool;
-    r->stream_id = stream_id;
-    r->W = w;
-    r->H = h;
-    r->dmax = dmax;
-    r->iters = iters;
-    r->cell = cell;
-    int sz_min = iters >= 2 ? std::max(1, cell >> (iters - 2)) : 0;
-    r->ncell_max = iters >= 2 ? cells_of(w, h, sz_min) : 1;
-    const size_t need = block_bytes(*r, c->K);
-    if (need > c->cfg.mem_budget_bytes) {
-        delete r;
-        return STEREO_E_NOMEM;
-    }
-    const size_t N = (size_t)w * h;
-    cudaPointerAttributes at{}, at_r{};
-    const bool known = cudaPointerGetAttributes(&at, left) == cudaSuccess &&
-                       cudaPointerGetAttributes(&at_r, right) == cudaSuccess;
-    cudaGetLastError();
-    const bool dev_in = known && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
-    // page-locked host inputs are copied straight to the device (one DMA each),
-    // pageable ones through a pinned staging buffer
-    const bool pinned_in = known && !dev_in && at.type == cudaMemoryTypeHost && at_r.type == cudaMemoryTypeHost;
-    std::unique_lock<std::mutex> g(c->mu);
-    if ((int)c->queue.size() >= c->cfg.max_queue && (int)c->active.size() >= c->cfg.max_slots) {
-        g.unlock();
-        delete r;
-        return STEREO_E_BUSY;
-    }
-    if (dev_in || pinned_in) {
-        r->in_dev = (uint8_t*)c->arena.alloc(2 * N);
-        if (!r->in_dev) {
-            g.unlock();
-            delete r;
-            return STEREO_E_BUSY;
-        }
-        g.unlock();
-        const cudaMemcpyKind kind = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-        cudaMemcpyAsync(r->in_dev, left, N, kind, c->copy_stream);
-        cudaMemcpyAsync(r->in_dev + N, right, N, kind, c->copy_stream);
-        if (cudaStreamSynchronize(c->copy_stream) != cudaSuccess) {
-            std::lock_guard<std::mutex> g2(c->mu);
-            c->arena.release(r->in_dev);
-            delete r;
-            return STEREO_E_CUDA;
-        }
-        g.lock();
-    } else {
-        g.unlock();
-        if (!r->in_host.ensure(2 * N)) {
-            delete r;
-            return STEREO_E_NOMEM;
-        }
-        std::memcpy(r->in_host.p, left, N);
-        std::memcpy((char*)r->in_host.p + N, right, N);
-        g.lock();
-    }
-    r->ticket = c->next_ticket++;
-    r->t_submit = now_ms();
-    c->last_submit = std::chrono::steady_clock::now();
-    c->reqs[r->ticket] = r;
-    c->queue.push_back(r);
-    *ticket_out = r->ticket;
-    g.unlock();
-    c->cv_sched.notify_all();
-    return STEREO_OK;
+    const stereo_pair p{stream_id, left, right, w, h, dmax, iters, cell};
+    const int rc = stereo_submit_batch(c, &p, 1, ticket_out);
+    return rc == 1 ? STEREO_OK : rc;
 }
 
 int stereo_poll(stereo_ctx* c, uint64_t ticket, stereo_result* out, int timeout_us) {
@@ -2075,7 +2119,6 @@ int stereo_delaunay_insert(const int32_t* uv, int n, const int32_t* tri, int T, 
     int32_t* d_pidx = (int32_t*)take(b_pidx);
     int32_t* d_scr = (int32_t*)take(b_scr);
     MeshDev* d_md = (MeshDev*)take(b_md);
-    MeshCtl* d_ctl = (MeshCtl*)take(256);
     MeshDev md{};
     mesh_carve(md, mesh, w, h, n_cap, t_cap, p_cap);
     md.seed_pos = d_pos;
@@ -2114,7 +2157,7 @@ int stereo_delaunay_insert(const int32_t* uv, int n, const int32_t* tri, int T, 
     // the old mesh's plane-index map locates the new points, as a pass's raster does in the engine
     if (e == cudaSuccess) e = launch_raster_clear(clear, s);
     if (e == cudaSuccess) e = launch_raster_device_lists(p, s);
-    if (e == cudaSuccess) e = launch_mesh_pass(d_md, 1, d_ctl, s);
+    if (e == cudaSuccess) e = launch_mesh_pass(d_md, 1, s);
     MeshHdr hd{};
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hd, md.hdr, sizeof(MeshHdr), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

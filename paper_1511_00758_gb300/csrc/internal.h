@@ -153,6 +153,7 @@ struct MeshHdr {
     int n_pl[2];                     // entries of the two pending worklists (this round's, the next's)
     int n_al[2];                     // entries of the two active-triangle worklists of the flip rounds
     int edge_ins;                    // insertions on an edge (2 -> 4 or hull 1 -> 2) in the last pass
+    int total_new, inserted;         // points of the pass to insert, and those inserted (or given up)
 };
 
 struct MeshDev {
@@ -221,12 +222,9 @@ int mesh_vertex_cap(int W, int H, int seed_points, int iters, int cell);
 // One pass of mesh work for up to kMeshBatch pairs (device descriptors md[np]):
 // take over seed meshes, collect and insert the new points, flip to the
 // triangulation, rank canonically where asked, build the next raster inputs.
-// One cooperative launch (grid-wide barriers between its phases).
-struct MeshCtl {                     // grid-wide counters of one mesh launch (device memory)
-    unsigned long long total_new, inserted, flips;
-    int err, rounds;
-};
-cudaError_t launch_mesh_pass(const MeshDev* md, int np, MeshCtl* ctl, cudaStream_t s);
+// One thread-block cluster per pair (mesh_cluster_blocks(np) blocks each).
+cudaError_t launch_mesh_pass(const MeshDev* md, int np, cudaStream_t s);
+int mesh_cluster_blocks(int np);
 // Raster of device meshes: PairBatch b lists the pairs (their PairDev:
 // outputs, cells), md the same pairs' meshes (counts read on the device).
 cudaError_t launch_raster_mesh(const PairBatch& b, const MeshDev* md, cudaStream_t s);

@@ -25,10 +25,14 @@
 // a W x H bit map of the vertex pixels: the canonical index of (u, v) is the
 // number of vertex pixels before it in raster order, which is (v, u) order.
 //
-// Everything runs in one cooperative launch per pass over up to kMeshBatch
-// pairs; grid-wide barriers separate the phases and every loop decision is
-// read after a barrier, so all blocks take it alike.  Loops are bounded: a
-// pair that does not finish sets its error code.
+// Everything runs in one launch per pass over up to kMeshBatch pairs, one
+// thread-block cluster per pair: the cluster's blocks share the pair's items
+// and meet at the hardware cluster barrier between phases (pairs are
+// independent meshes, so nothing waits across clusters), and every loop
+// decision is read after a barrier, so all blocks of a cluster take it alike.
+// The phases are latency-bound (short chains of dependent loads with a
+// barrier after each), so the rounds, not the bytes, set the time.  Loops are
+// bounded: a pair that does not finish sets its error code.
 #include <cooperative_groups.h>
 
 #include "internal.h"
@@ -39,10 +43,9 @@ namespace stereo {
 
 namespace {
 
-constexpr int kMeshThreads = 1024;  // one block per SM: the grid barrier has few arrivals
+constexpr int kMeshThreads = 1024;  // one block per SM (61 registers a thread)
 constexpr int kMaxInsertRounds = 4096;
 constexpr int kMaxFlipRounds = 1 << 15;
-constexpr int kFlipEvery = 0;  // flip sequence after every kFlipEvery-th insertion round (0: at the end)
 constexpr int kScanChunk = 1024;  // elements per warp in the two-level scans
 constexpr unsigned long long kNoClaim = ~0ull;
 
@@ -184,76 +187,6 @@ namespace {
 
 __device__ __forceinline__ int words_of(const MeshDev& m) { return (int)(((long long)m.W * m.H + 31) / 32); }
 
-// Block-local exclusive prefix of the pairs' item counts (np <= 64) in
-// pre[0..np]; returns the total.  Every thread of the block calls it.
-template <class C>
-__device__ __forceinline__ int pair_prefix(int np, int* pre, C count) {
-    __syncthreads();  // pre may still be read by the previous phase
-    if (threadIdx.x < 32) {
-        const int l = threadIdx.x;
-        int s0 = l < np ? count(l) : 0;
-        int s1 = l + 32 < np ? count(l + 32) : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int x0 = __shfl_up_sync(0xffffffffu, s0, o), x1 = __shfl_up_sync(0xffffffffu, s1, o);
-            if (l >= o) {
-                s0 += x0;
-                s1 += x1;
-            }
-        }
-        const int tot0 = __shfl_sync(0xffffffffu, s0, 31);
-        if (l == 0) pre[0] = 0;
-        pre[l + 1] = s0;
-        pre[l + 33] = tot0 + s1;
-    }
-    __syncthreads();
-    return pre[np];
-}
-
-__device__ __forceinline__ int pair_of(const int* pre, int np, int g) {
-    int lo = 0, hi = np - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (pre[mid] <= g) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-// body(pair, local item) for every item, one thread each.
-template <class C, class B>
-__device__ __forceinline__ void each_item(int np, int* pre, C count, B body) {
-    const int total = pair_prefix(np, pre, count);
-    const int stride = gridDim.x * blockDim.x;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
-        const int p = pair_of(pre, np, g);
-        body(p, g - pre[p]);
-    }
-}
-
-// body(pair, local item) for every item, one warp each (warp-uniform).
-template <class C, class B>
-__device__ __forceinline__ void each_warp_item(int np, int* pre, C count, B body) {
-    const int total = pair_prefix(np, pre, count);
-    const int wpb = blockDim.x >> 5;
-    const int stride = gridDim.x * wpb;
-    for (int g = blockIdx.x * wpb + (threadIdx.x >> 5); g < total; g += stride) {
-        const int p = pair_of(pre, np, g);
-        body(p, g - pre[p]);
-    }
-}
-
-// body(pair, local item) over a prefix already in shared memory (no barrier).
-template <class B>
-__device__ __forceinline__ void each_pre(int np, const int* pre, B body) {
-    const int total = pre[np];
-    const int stride = gridDim.x * blockDim.x;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
-        const int p = pair_of(pre, np, g);
-        body(p, g - pre[p]);
-    }
-}
-
 __device__ __forceinline__ int warp_excl_scan(int x, int& total) {
     const int l = threadIdx.x & 31;
     int s = x;
@@ -267,7 +200,7 @@ __device__ __forceinline__ int warp_excl_scan(int x, int& total) {
 }
 
 // Two-level exclusive scan of f(in[0..n)) into out[0..n) (out may be in),
-// over three phases separated by grid barriers: (A) a warp sums each chunk
+// over three phases separated by cluster barriers: (A) a warp sums each chunk
 // of kScanChunk elements into chunk[c]; (B) one warp per array scans the
 // chunk sums and stores the total; (C) a warp writes each chunk's prefixes
 // (lane l owns 32 consecutive elements).
@@ -445,6 +378,18 @@ __device__ __forceinline__ void relink(const MeshDev& m, int s, int e, int stamp
 // ---------------------------------------------------------------- the pass kernel
 namespace {
 
+// A 32-bit mix of an edge id and a round (the murmur3 finaliser applied to
+// their combination): an arbitrary but fixed priority per edge and round.
+__device__ __forceinline__ unsigned mix32(unsigned x, unsigned r) {
+    unsigned h = x * 0x9E3779B1u ^ (r + 0x7F4A7C15u);
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
 // Claim priority of a pending point: squared distance of 3q from the sum of
 // its triangle's vertices (points near the middle first, so the pieces split
 // the remaining points evenly), then the vertex slot (unique).
@@ -454,7 +399,9 @@ __device__ __forceinline__ unsigned long long claim_key(const MeshDev& m, int4 t
     return ((unsigned long long)(dx * dx + dy * dy) << 27) | (unsigned)vid;
 }
 
-__device__ __forceinline__ void add_point(const MeshDev& m, MeshCtl* ctl, uint32_t px, float d, int T0) {
+__device__ __forceinline__ int ld_int(const int* p) { return *(const volatile int*)p; }
+
+__device__ __forceinline__ void add_point(const MeshDev& m, uint32_t px, float d, int T0) {
     const uint32_t bit = 1u << (px & 31);
     if (atomicOr(m.occ + (px >> 5), bit) & bit) return;  // a point already at this pixel keeps it
     const int vid = atomicAdd(&m.hdr->n, 1);
@@ -477,11 +424,11 @@ __device__ __forceinline__ void add_point(const MeshDev& m, MeshCtl* ctl, uint32
     }
     m.ploc[slot] = t;
     m.plist[atomicAdd(&m.hdr->n_pl[0], 1)] = slot;
-    atomicAdd(&ctl->total_new, 1ull);
+    atomicAdd(&m.hdr->total_new, 1);
 }
 
-// Where pending entry e lies: -1 inside its triangle, else the edge code of
-// the pnb array; -2 when it is not in its triangle (an error).
+// Where a pending point lies in triangle t: -1 inside, else the edge code of
+// the pnb array; -2 when it is not in t (an error).
 __device__ __forceinline__ int classify(const MeshDev& m, int t, int2 q) {
     const int4 tt = m.tri[t];
     const int2 a = m.pos[tt.x], b = m.pos[tt.y], c = m.pos[tt.z];
@@ -500,15 +447,9 @@ __device__ __forceinline__ int classify(const MeshDev& m, int t, int2 q) {
     return ((n + 1) << 4) | (j << 2) | k;
 }
 
-__device__ __forceinline__ int ld_int(const int* p) { return *(const volatile int*)p; }
-__device__ __forceinline__ unsigned long long ld_u64(const unsigned long long* p) {
-    return *(const volatile unsigned long long*)p;
-}
-
-// A pending point whose triangle t was split or flipped in the round with
-// this stamp moves to the piece that contains it (the pieces are named by
-// t's record).
-__device__ __forceinline__ void relocate(const MeshDev& m, int e, int t, int stamp, MeshCtl* ctl) {
+// A pending point whose triangle t was split in the round with this stamp
+// moves to the piece that contains it (the pieces are named by t's record).
+__device__ __forceinline__ void relocate(const MeshDev& m, int e, int t, int stamp) {
     const int4 st = m.smap[t];
     if (st.x != stamp) return;
     const int2 q = m.pos[m.pend[e]];
@@ -519,226 +460,113 @@ __device__ __forceinline__ void relocate(const MeshDev& m, int e, int t, int sta
     }
     if (found < 0) {
         m.hdr->err = 2;
-        atomicAdd(&ctl->inserted, 1ull);
+        atomicAdd(&m.hdr->inserted, 1);
     }
     m.ploc[e] = found;
 }
 
-__global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __restrict__ mdg, int np, MeshCtl* ctl) {
-    __shared__ int pre[kMeshBatch + 1];
-    __shared__ int pre_new[kMeshBatch + 1];  // prefix of the pairs' pending points (fixed after the collection)
-    __shared__ int pre_T[kMeshBatch + 1];    // prefix of their triangle counts (refreshed before each flip sequence)
-    __shared__ MeshDev smd[kMeshBatch];      // the pairs' descriptors, read without a trip to global memory
-    cg::grid_group grid = cg::this_grid();
-    for (int i = threadIdx.x; i < np * (int)(sizeof(MeshDev) / 4); i += blockDim.x)
-        reinterpret_cast<int*>(smd)[i] = reinterpret_cast<const int*>(mdg)[i];
+// One pair per thread-block cluster: the cluster's blocks share the pair's
+// items and meet at the cluster barrier between phases, so each pair runs at
+// its own pace and no barrier spans the grid.
+__global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __restrict__ mdg) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int nblk = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    __shared__ MeshDev sm;  // the pair's descriptor
+    for (int i = threadIdx.x; i < (int)(sizeof(MeshDev) / 4); i += blockDim.x)
+        reinterpret_cast<int*>(&sm)[i] = reinterpret_cast<const int*>(mdg + blockIdx.x / nblk)[i];
     __syncthreads();
-    const MeshDev* md = smd;
+    const MeshDev& m = sm;
+    MeshHdr* hd = m.hdr;
+    const bool lead = rank == 0 && threadIdx.x == 0;
+    const int t0 = rank * blockDim.x + threadIdx.x, tstride = nblk * blockDim.x;
+    const int w0 = rank * (blockDim.x >> 5) + (threadIdx.x >> 5), wstride = nblk * (blockDim.x >> 5);
+    auto items = [&](int n, auto body) {
+        for (int i = t0; i < n; i += tstride) body(i);
+    };
+    auto warp_items = [&](int n, auto body) {
+        for (int i = w0; i < n; i += wstride) body(i);
+    };
+    const int words = words_of(m);
 
-    // ---- 0: take over seed meshes; reset the pass's counters
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ctl->total_new = ctl->inserted = ctl->flips = 0;
-        ctl->err = 0;
-        ctl->rounds = 0;
+    // ---- 0: take over the seed mesh; reset the pass's counters
+    if (lead) {
+        if (m.seed_T > 0) {
+            hd->n = m.seed_n;
+            hd->T = m.seed_T;
+            hd->stamp = 0;
+            hd->err = 0;
+        }
+        hd->n_new = hd->n_small = hd->n_large = hd->n_items = hd->n_hull = 0;
+        for (int c = 0; c < kMeshClasses; c++) hd->cls[c] = hd->cls_fill[c] = 0;
+        hd->rounds = hd->flips = hd->frounds = hd->edge_ins = 0;
+        hd->n_pl[0] = hd->n_pl[1] = hd->n_al[0] = hd->n_al[1] = 0;
+        hd->total_new = hd->inserted = 0;
     }
-    each_item(np, pre, [&](int p) {
-                  const MeshDev& m = md[p];
-                  return 1 + (m.seed_T > 0 ? words_of(m) + m.seed_n + m.seed_T : ld_int(&m.hdr->T));
-              },
-              [&](int p, int i) {
-                  const MeshDev& m = md[p];
-                  if (i == 0) {
-                      MeshHdr& h = *m.hdr;
-                      if (m.seed_T > 0) {
-                          h.n = m.seed_n;
-                          h.T = m.seed_T;
-                          h.stamp = 0;
-                          h.err = 0;
-                      }
-                      h.n_new = h.n_small = h.n_large = h.n_items = h.n_hull = 0;
-                      for (int c = 0; c < kMeshClasses; c++) h.cls[c] = h.cls_fill[c] = 0;
-                      h.rounds = h.flips = 0;
-                      h.n_pl[0] = h.n_pl[1] = 0;
-                      h.n_al[0] = h.n_al[1] = 0;
-                      h.edge_ins = 0;
-                      return;
-                  }
-                  i -= 1;
-                  if (m.seed_T == 0) {  // a mesh kept from the last pass: its flip claims start empty
-                      m.fclaim[i] = kNoClaim;
-                      return;
-                  }
-                  const int words = words_of(m);
-                  if (i < words) {
-                      m.occ[i] = 0u;
-                      return;
-                  }
-                  i -= words;
-                  if (i < m.seed_n) {
-                      m.pos[i] = make_int2(m.seed_pos[2 * i], m.seed_pos[2 * i + 1]);
-                      m.vd[i] = m.seed_d[i];
-                      m.vpass[i] = 1;
-                      return;
-                  }
-                  i -= m.seed_n;
-                  m.tri[i] = m.seed_tri[i];
-                  m.opp[i] = m.seed_opp[i];
-                  m.claim[i] = kNoClaim;
-                  m.fclaim[i] = kNoClaim;
-                  m.smap[i] = make_int4(0, -1, -1, -1);
-              });
-    grid.sync();
-    each_item(np, pre, [&](int p) { return md[p].seed_T > 0 ? md[p].seed_n : 0; }, [&](int p, int i) {
-        const MeshDev& m = md[p];
-        const int2 q = m.pos[i];
-        const uint32_t px = (uint32_t)q.y * (uint32_t)m.W + (uint32_t)q.x;
-        atomicOr(m.occ + (px >> 5), 1u << (px & 31));
-    });
-    grid.sync();
+    if (m.seed_T > 0) {
+        items(words, [&](int i) { m.occ[i] = 0u; });
+        items(m.seed_n, [&](int i) {
+            m.pos[i] = make_int2(m.seed_pos[2 * i], m.seed_pos[2 * i + 1]);
+            m.vd[i] = m.seed_d[i];
+            m.vpass[i] = 1;
+        });
+        items(m.seed_T, [&](int i) {
+            m.tri[i] = m.seed_tri[i];
+            m.opp[i] = m.seed_opp[i];
+            m.claim[i] = kNoClaim;
+            m.fclaim[i] = kNoClaim;
+            m.smap[i] = make_int4(0, -1, -1, -1);
+        });
+    } else {  // a mesh kept from the last pass: its flip claims start empty
+        items(ld_int(&hd->T), [&](int i) { m.fclaim[i] = kNoClaim; });
+    }
+    cl.sync();
+    if (m.seed_T > 0)
+        items(m.seed_n, [&](int i) {
+            const int2 q = m.pos[i];
+            const uint32_t px = (uint32_t)q.y * (uint32_t)m.W + (uint32_t)q.x;
+            atomicOr(m.occ + (px >> 5), 1u << (px & 31));
+        });
+    cl.sync();
 
     // ---- 1: collect the new points (cell records in raster order of cells, or a list)
-    each_item(np, pre, [&](int p) { const MeshDev& m = md[p]; return m.cg_key ? m.ncells : m.list_n; },
-              [&](int p, int c) {
-                  const MeshDev& m = md[p];
-                  const int T0 = m.hdr->T;
-                  if (m.cg_key) {
-                      const uint32_t gk = m.cg_key[c], bk = m.cb_key[c];
-                      if (gk != kNoKey) add_point(m, ctl, gk & kIdxMask, m.cg_d[c], T0);
-                      if (bk != kNoKey && m.x_d[c] >= 0) add_point(m, ctl, bk & kIdxMask, (float)m.x_d[c], T0);
-                  } else {
-                      const int u = m.list_uv[2 * c], v = m.list_uv[2 * c + 1];
-                      add_point(m, ctl, (uint32_t)v * (uint32_t)m.W + (uint32_t)u, 0.0f, T0);
-                  }
-              });
-    grid.sync();
+    {
+        const int T0 = ld_int(&hd->T);
+        items(m.cg_key ? m.ncells : m.list_n, [&](int c) {
+            if (m.cg_key) {
+                const uint32_t gk = m.cg_key[c], bk = m.cb_key[c];
+                if (gk != kNoKey) add_point(m, gk & kIdxMask, m.cg_d[c], T0);
+                if (bk != kNoKey && m.x_d[c] >= 0) add_point(m, bk & kIdxMask, (float)m.x_d[c], T0);
+            } else {
+                const int u = m.list_uv[2 * c], v = m.list_uv[2 * c + 1];
+                add_point(m, (uint32_t)v * (uint32_t)m.W + (uint32_t)u, 0.0f, T0);
+            }
+        });
+    }
+    cl.sync();
 
-    // ---- 2: insertion rounds, with flip rounds until no edge is illegal after every
-    // kFlipEvery-th of them (0: once all points are in).  Every round (insertion or
-    // flip) has its own stamp, hdr->stamp + step; the triangles touched since the
-    // last flip sequence (stamp >= that of the first insertion round after it) are
-    // the only ones whose edges can be illegal, the rest being left legal by it.
-    pair_prefix(np, pre_new, [&](int p) { return ld_int(&md[p].hdr->n_new); });
-    __shared__ int pre_pl[kMeshBatch + 1];   // prefix of this round's pending worklists
+    // ---- 2: insertion rounds over a worklist of the points still pending
+    const int stamp0 = ld_int(&hd->stamp);
     int step = 0, ins_rounds = 0, flip_rounds = 0;
-    unsigned long long flips_seen = 0;
-    // Flip rounds.  Round 0 checks every triangle touched since act_step; later
-    // rounds check a worklist: the triangles flipped in the round before and the
-    // proposers whose flip lost.  A proposal claims both triangles of its edge with
-    // (round tag << 32) | edge, the tag falling with each round so that a newer
-    // claim beats any older one (no reset); tkey[t] holds t's own best proposal.
-    // The flip of a winning edge is made by its lower slot when that one proposed
-    // it, else by the other.
-    __shared__ int pre_al[kMeshBatch + 1];
-    auto run_flips = [&](int act_step) {
-        pair_prefix(np, pre_T, [&](int p) { return ld_int(&md[p].hdr->T); });
-        if (blockIdx.x == 0 && threadIdx.x < np) md[threadIdx.x].hdr->n_al[0] = md[threadIdx.x].hdr->n_al[1] = 0;
-        grid.sync();
-        for (int f = 0; f < kMaxFlipRounds; f++) {
-            const int fstep = ++step;
-            flip_rounds++;
-            const int ab = f & 1;  // this round's worklist (round 0: every triangle, filtered)
-            if (f > 0) pair_prefix(np, pre_al, [&](int p) { return ld_int(&md[p].hdr->n_al[ab]); });
-            if (blockIdx.x == 0 && threadIdx.x < np) md[threadIdx.x].hdr->n_al[ab ^ 1] = 0;
-            const unsigned long long tag = (unsigned long long)(0xFFFFFFFFu - (unsigned)fstep) << 32;
-            const int* pre_f = f == 0 ? pre_T : pre_al;
-            auto item_tri = [&](const MeshDev& m, int i) { return f == 0 ? i : m.alist[ab * m.t_cap + i]; };
-            // propose
-            each_pre(np, pre_f, [&](int p, int i) {
-                const MeshDev& m = md[p];
-                const int t = item_tri(m, i);
-                if (f == 0 && m.smap[t].x < m.hdr->stamp + act_step) return;
-                const int4 tt = m.tri[t], rt = m.opp[t];
-                const int2 a = m.pos[tt.x], b = m.pos[tt.y], c = m.pos[tt.z];
-                unsigned long long best = kNoClaim;
-                for (int k = 0; k < 3; k++) {
-                    const int r = ref_of(rt, k);
-                    if (r < 0) continue;
-                    const int n = r >> 2;
-                    const int y = vtx(m.tri[n], r & 3);
-                    if (incircle_sos(a, b, c, m.pos[y])) {
-                        const unsigned long long key = tag | (unsigned)(n < t ? r : mk_ref(t, k));
-                        atomicMin(m.fclaim + t, key);
-                        atomicMin(m.fclaim + n, key);
-                        best = min(best, key);
-                    }
-                }
-                m.tkey[t] = best;
-            });
-            grid.sync();
-            // flip each winning edge once
-            each_pre(np, pre_f, [&](int p, int i) {
-                const MeshDev& m = md[p];
-                const int t = item_tri(m, i);
-                if (f == 0 && m.smap[t].x < m.hdr->stamp + act_step) return;
-                const unsigned long long key = m.fclaim[t];
-                if (m.tkey[t] != key || (key >> 32) != (tag >> 32)) return;  // t did not propose the winner
-                const int tm = (int)((key & 0xFFFFFFFFull) >> 2), km = (int)(key & 3);
-                int n;
-                if (t == tm) n = ref_of(m.opp[t], km) >> 2;
-                else n = tm;
-                if (m.fclaim[n] != key) return;
-                if (t != tm && m.tkey[tm] == key && m.fclaim[tm] == key) return;  // the lower slot proposed it too: it flips
-                const int r = ref_of(m.opp[tm], km);
-                flip(m, tm, km, r >> 2, r & 3, m.hdr->stamp + fstep);
-                const int at = atomicAdd(&m.hdr->n_al[ab ^ 1], 2);
-                m.alist[(ab ^ 1) * m.t_cap + at] = tm;
-                m.alist[(ab ^ 1) * m.t_cap + at + 1] = r >> 2;
-                atomicAdd(&ctl->flips, 1ull);
-                atomicAdd(&m.hdr->flips, 1);
-            });
-            grid.sync();
-            // the flipped triangles link their outer edges (0 and 2); proposers that
-            // lost join the next worklist; waiting points move with their triangle
-            __shared__ int pre_fl[kMeshBatch + 1];
-            pair_prefix(np, pre_fl, [&](int p) { return ld_int(&md[p].hdr->n_al[ab ^ 1]); });
-            each_pre(np, pre_fl, [&](int p, int i) {
-                const MeshDev& m = md[p];
-                const int t = m.alist[(ab ^ 1) * m.t_cap + i];
-                const int stamp = m.hdr->stamp + fstep;
-                relink(m, t, 0, stamp);
-                relink(m, t, 2, stamp);
-            });
-            each_pre(np, pre_f, [&](int p, int i) {
-                const MeshDev& m = md[p];
-                const int t = item_tri(m, i);
-                if (f == 0 && m.smap[t].x < m.hdr->stamp + act_step) return;
-                const unsigned long long key = m.tkey[t];
-                if (key == kNoClaim || m.smap[t].x == m.hdr->stamp + fstep) return;  // no proposal, or flipped
-                m.alist[(ab ^ 1) * m.t_cap + atomicAdd(&m.hdr->n_al[ab ^ 1], 1)] = t;
-            });
-            if (kFlipEvery > 0)
-                each_pre(np, pre_new, [&](int p, int e) {
-                    const MeshDev& m = md[p];
-                    const int lt = m.ploc[e];
-                    if (lt >= 0) relocate(m, e, lt, m.hdr->stamp + fstep, ctl);
-                });
-            grid.sync();
-            const unsigned long long fl = ld_u64(&ctl->flips);
-            if (fl == flips_seen) break;
-            flips_seen = fl;
-            if (f == kMaxFlipRounds - 1 && blockIdx.x == 0 && threadIdx.x < np) md[threadIdx.x].hdr->err = 3;
-        }
-    };
-    int act_step = 1;  // first step not yet covered by a flip sequence
     for (; ins_rounds < kMaxInsertRounds; ins_rounds++) {
-        if (ld_u64(&ctl->inserted) >= ld_u64(&ctl->total_new)) break;
-        const int ins_step = ++step;
+        if (ld_int(&hd->inserted) >= ld_int(&hd->total_new)) break;
+        const int stamp = stamp0 + (++step);
         const int wb = ins_rounds & 1;  // this round's worklist; survivors go to the other
-        pair_prefix(np, pre_pl, [&](int p) { return ld_int(&md[p].hdr->n_pl[wb]); });
-        if (blockIdx.x == 0 && threadIdx.x < np) md[threadIdx.x].hdr->n_pl[wb ^ 1] = 0;
+        const int npl = ld_int(&hd->n_pl[wb]);
+        const int* wl = m.plist + wb * m.p_cap;
+        int* wn = m.plist + (wb ^ 1) * m.p_cap;
+        if (lead) hd->n_pl[wb ^ 1] = 0;
         // claim the triangle (and the neighbour across the edge the point lies on)
-        each_pre(np, pre_pl, [&](int p, int i) {
-            const MeshDev& m = md[p];
-            const int e = m.plist[wb * m.p_cap + i];
+        items(npl, [&](int i) {
+            const int e = wl[i];
             const int t = m.ploc[e];
             if (t < 0) return;
             const int vid = m.pend[e];
             const int2 q = m.pos[vid];
             const int code = classify(m, t, q);
             if (code == -2) {
-                m.hdr->err = 2;
+                hd->err = 2;
                 m.ploc[e] = -1;
-                atomicAdd(&ctl->inserted, 1ull);
+                atomicAdd(&hd->inserted, 1);
                 return;
             }
             const unsigned long long key = claim_key(m, m.tri[t], q, vid);
@@ -747,33 +575,29 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
             atomicMin(m.claim + t, key);
             if (code >= 0 && (code >> 4) > 0) atomicMin(m.claim + ((code >> 4) - 1), key);
         });
-        grid.sync();
+        cl.sync();
         // a point holding all its claims splits them
-        each_pre(np, pre_pl, [&](int p, int i) {
-            const MeshDev& m = md[p];
-            const int e = m.plist[wb * m.p_cap + i];
+        items(npl, [&](int i) {
+            const int e = wl[i];
             const int t = m.ploc[e];
             if (t < 0) return;
             const unsigned long long key = m.tkey[e];
             const int code = m.pnb[e];
             const int n = code >= 0 ? (code >> 4) - 1 : -1;
             if (m.claim[t] != key || (n >= 0 && m.claim[n] != key)) return;
-            const int stamp = m.hdr->stamp + ins_step;
             const int vid = m.pend[e];
             const bool ok = code < 0 ? split3(m, t, vid, stamp) : split_edge(m, t, code & 3, n, (code >> 2) & 3, vid, stamp);
-            if (code >= 0) atomicAdd(&m.hdr->edge_ins, 1);
+            if (code >= 0) atomicAdd(&hd->edge_ins, 1);
             m.ploc[e] = ok ? -2 - t : -1;
-            atomicAdd(&ctl->inserted, 1ull);
+            atomicAdd(&hd->inserted, 1);
         });
-        grid.sync();
+        cl.sync();
         // link the pieces to their neighbours; the others move to the piece they lie in
         // and stay on the worklist
-        each_pre(np, pre_pl, [&](int p, int i) {
-            const MeshDev& m = md[p];
-            const int e = m.plist[wb * m.p_cap + i];
+        items(npl, [&](int i) {
+            const int e = wl[i];
             const int lt = m.ploc[e];
             if (lt == -1) return;
-            const int stamp = m.hdr->stamp + ins_step;
             const int code = m.pnb[e];
             const int n = code >= 0 ? (code >> 4) - 1 : -1;
             if (lt <= -2) {
@@ -797,103 +621,160 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
             }
             m.claim[lt] = kNoClaim;
             if (n >= 0) m.claim[n] = kNoClaim;
-            relocate(m, e, lt, stamp, ctl);
-            if (m.ploc[e] >= 0) m.plist[(wb ^ 1) * m.p_cap + atomicAdd(&m.hdr->n_pl[wb ^ 1], 1)] = e;
+            relocate(m, e, lt, stamp);
+            if (m.ploc[e] >= 0) wn[atomicAdd(&hd->n_pl[wb ^ 1], 1)] = e;
         });
-        grid.sync();
-        if (kFlipEvery > 0 && (ins_rounds + 1) % kFlipEvery == 0) {
-            run_flips(act_step);
-            act_step = step + 1;
+        cl.sync();
+    }
+    if (ins_rounds == kMaxInsertRounds && lead) hd->err = 3;
+
+    // ---- 3: flip rounds, once every point is in.  Round 0 checks every triangle
+    // touched by the insertions; later rounds a worklist: the triangles flipped in
+    // the round before and the proposers whose flip lost.  A proposal claims both
+    // triangles of its edge with (round tag << 44) | (priority << 25) | edge: the
+    // tag falls with each round so that a newer claim beats any older one (no
+    // reset), the priority is a hash of the edge and the round; tkey[t] holds t's
+    // own best proposal.  The flip of a winning edge is made by its lower slot
+    // when that one proposed it, else by the other.
+    if (step > 0) {
+        const int T = ld_int(&hd->T);
+        int flips_seen = 0;
+        for (int f = 0; f < kMaxFlipRounds; f++) {
+            const int fstep = ++step;
+            const int stamp = stamp0 + fstep;
+            flip_rounds++;
+            const int ab = f & 1;
+            const int nitems = f == 0 ? T : ld_int(&hd->n_al[ab]);
+            const int* al = m.alist + ab * m.t_cap;
+            int* an = m.alist + (ab ^ 1) * m.t_cap;
+            if (lead) hd->n_al[ab ^ 1] = 0;
+            const unsigned long long tag = (unsigned long long)(0xFFFFFu - (unsigned)fstep) << 44;
+            auto tri_of = [&](int i) { return f == 0 ? i : al[i]; };
+            // propose
+            items(nitems, [&](int i) {
+                const int t = tri_of(i);
+                if (f == 0 && m.smap[t].x <= stamp0) return;  // untouched this pass: its edges are legal
+                const int4 tt = m.tri[t], rt = m.opp[t];
+                const int2 a = m.pos[tt.x], b = m.pos[tt.y], c = m.pos[tt.z];
+                unsigned long long best = kNoClaim;
+                for (int k = 0; k < 3; k++) {
+                    const int r = ref_of(rt, k);
+                    if (r < 0) continue;
+                    const int n = r >> 2;
+                    const int y = vtx(m.tri[n], r & 3);
+                    if (incircle_sos(a, b, c, m.pos[y])) {
+                        const unsigned eid = (unsigned)(n < t ? r : mk_ref(t, k));
+                        const unsigned long long key = tag | ((unsigned long long)(mix32(eid, fstep) & 0x7FFFFu) << 25) | eid;
+                        atomicMin(m.fclaim + t, key);
+                        atomicMin(m.fclaim + n, key);
+                        best = min(best, key);
+                    }
+                }
+                m.tkey[t] = best;
+            });
+            cl.sync();
+            // flip each winning edge once
+            items(nitems, [&](int i) {
+                const int t = tri_of(i);
+                if (f == 0 && m.smap[t].x <= stamp0) return;
+                const unsigned long long key = m.fclaim[t];
+                if (m.tkey[t] != key || (key >> 44) != (tag >> 44)) return;  // t did not propose the winner
+                const int tm = (int)((key & 0x1FFFFFFull) >> 2), km = (int)(key & 3);
+                const int n = t == tm ? ref_of(m.opp[t], km) >> 2 : tm;
+                if (m.fclaim[n] != key) return;
+                if (t != tm && m.tkey[tm] == key && m.fclaim[tm] == key) return;  // the lower slot flips it
+                const int r = ref_of(m.opp[tm], km);
+                flip(m, tm, km, r >> 2, r & 3, stamp);
+                const int at = atomicAdd(&hd->n_al[ab ^ 1], 2);
+                an[at] = tm;
+                an[at + 1] = r >> 2;
+                atomicAdd(&hd->flips, 1);
+            });
+            cl.sync();
+            // the flipped triangles link their outer edges (0 and 2); proposers that lost
+            // join the next worklist
+            const int nfl = ld_int(&hd->n_al[ab ^ 1]);
+            items(nfl, [&](int i) {
+                const int t = an[i];
+                relink(m, t, 0, stamp);
+                relink(m, t, 2, stamp);
+            });
+            items(nitems, [&](int i) {
+                const int t = tri_of(i);
+                if (f == 0 && m.smap[t].x <= stamp0) return;
+                if (m.tkey[t] == kNoClaim || m.smap[t].x == stamp) return;  // no proposal, or flipped
+                an[atomicAdd(&hd->n_al[ab ^ 1], 1)] = t;
+            });
+            cl.sync();
+            const int fl = ld_int(&hd->flips);
+            if (fl == flips_seen) break;
+            flips_seen = fl;
+            if (f == kMaxFlipRounds - 1 && lead) hd->err = 3;
         }
     }
-    if (act_step <= step) run_flips(act_step);  // the insertions since the last flip sequence
-    if (ins_rounds == kMaxInsertRounds && ld_u64(&ctl->inserted) < ld_u64(&ctl->total_new)) {
-        if (blockIdx.x == 0 && threadIdx.x < np) md[threadIdx.x].hdr->err = 3;
-    }
 
-    // ---- 4: canonical ranks (pairs whose next pass is the last)
-    // vertex rank = vertex pixels before it in raster order (the bit map's prefix)
-    each_warp_item(np, pre, [&](int p) { return md[p].canonical ? scan_chunks(words_of(md[p])) : 0; }, [&](int p, int c) {
-        const MeshDev& m = md[p];
-        scan_a(m.occ, words_of(m), m.scan, c, Popc());
-    });
-    each_item(np, pre, [&](int p) { return md[p].canonical ? ld_int(&md[p].hdr->n) + 1 : 0; },
-              [&](int p, int i) { md[p].gcnt[i] = 0; });
-    grid.sync();
-    each_warp_item(np, pre, [&](int p) { return md[p].canonical ? 1 : 0; }, [&](int p, int) {
-        const MeshDev& m = md[p];
-        scan_b(m.scan, scan_chunks(words_of(m)), nullptr);
-    });
-    grid.sync();
-    each_warp_item(np, pre, [&](int p) { return md[p].canonical ? scan_chunks(words_of(md[p])) : 0; }, [&](int p, int c) {
-        const MeshDev& m = md[p];
-        scan_c(m.occ, m.wpre, words_of(m), m.scan, c, Popc());
-    });
-    grid.sync();
-    each_item(np, pre, [&](int p) { return md[p].canonical ? ld_int(&md[p].hdr->n) : 0; }, [&](int p, int v) {
-        const MeshDev& m = md[p];
-        const int2 q = m.pos[v];
-        const uint32_t px = (uint32_t)q.y * (uint32_t)m.W + (uint32_t)q.x;
-        const int r = (int)m.wpre[px >> 5] + __popc(m.occ[px >> 5] & ((1u << (px & 31)) - 1u));
-        m.vrank[v] = r;
-        m.vcanon[r] = make_int4(q.x, q.y, __float_as_int(m.vd[v]), m.vpass[v]);
-    });
-    grid.sync();
-    // triangle key (i < j < k canonical); count the triangles of each smallest vertex
-    each_item(np, pre, [&](int p) { return md[p].canonical ? ld_int(&md[p].hdr->T) : 0; }, [&](int p, int t) {
-        const MeshDev& m = md[p];
-        const int4 tt = m.tri[t];
-        int a = m.vrank[tt.x], b = m.vrank[tt.y], c = m.vrank[tt.z];
-        if (a > b) { const int x = a; a = b; b = x; }
-        if (b > c) { const int x = b; b = c; c = x; }
-        if (a > b) { const int x = a; a = b; b = x; }
-        m.tkey[t] = ((unsigned long long)(unsigned)b << 32) | (unsigned)c;
-        atomicAdd(m.gcnt + a, 1);
-    });
-    grid.sync();
-    each_warp_item(np, pre, [&](int p) { return md[p].canonical ? scan_chunks(ld_int(&md[p].hdr->n)) : 0; }, [&](int p, int c) {
-        const MeshDev& m = md[p];
-        scan_a((const uint32_t*)m.gcnt, ld_int(&m.hdr->n), m.scan, c, Ident());
-    });
-    grid.sync();
-    each_warp_item(np, pre, [&](int p) { return md[p].canonical ? 1 : 0; }, [&](int p, int) {
-        const MeshDev& m = md[p];
-        scan_b(m.scan, scan_chunks(ld_int(&m.hdr->n)), nullptr);
-    });
-    grid.sync();
-    each_warp_item(np, pre, [&](int p) { return md[p].canonical ? scan_chunks(ld_int(&md[p].hdr->n)) : 0; }, [&](int p, int c) {
-        const MeshDev& m = md[p];
-        scan_c((const uint32_t*)m.gcnt, (uint32_t*)m.gcnt, ld_int(&m.hdr->n), m.scan, c, Ident());
-    });
-    grid.sync();
-    // scatter by smallest vertex (gcnt[i] ends at the start of group i + 1)
-    each_item(np, pre, [&](int p) { return md[p].canonical ? ld_int(&md[p].hdr->T) : 0; }, [&](int p, int t) {
-        const MeshDev& m = md[p];
-        const int4 tt = m.tri[t];
-        const int a = min(m.vrank[tt.x], min(m.vrank[tt.y], m.vrank[tt.z]));
-        m.tperm[atomicAdd(m.gcnt + a, 1)] = t;
-    });
-    grid.sync();
-    // order each group by (j, k): groups are a vertex's few triangles
-    each_item(np, pre, [&](int p) { return md[p].canonical ? ld_int(&md[p].hdr->n) : 0; }, [&](int p, int i) {
-        const MeshDev& m = md[p];
-        const int lo = i ? m.gcnt[i - 1] : 0, hi = m.gcnt[i];
-        for (int x = lo + 1; x < hi; x++) {
-            const int t = m.tperm[x];
-            const unsigned long long kt = m.tkey[t];
-            int y = x - 1;
-            while (y >= lo && m.tkey[m.tperm[y]] > kt) {
-                m.tperm[y + 1] = m.tperm[y];
-                y--;
+    const int n = ld_int(&hd->n), T = ld_int(&hd->T);
+    // ---- 4: canonical ranks (the next pass is the last).  Vertex rank = vertex
+    // pixels before it in raster order (the bit map's prefix); triangles grouped by
+    // their smallest canonical vertex, each group ordered by the other two.
+    if (m.canonical) {
+        const int nch = scan_chunks(words);
+        warp_items(nch, [&](int c) { scan_a(m.occ, words, m.scan, c, Popc()); });
+        items(n + 1, [&](int i) { m.gcnt[i] = 0; });
+        cl.sync();
+        warp_items(1, [&](int) { scan_b(m.scan, nch, nullptr); });
+        cl.sync();
+        warp_items(nch, [&](int c) { scan_c(m.occ, m.wpre, words, m.scan, c, Popc()); });
+        cl.sync();
+        items(n, [&](int v) {
+            const int2 q = m.pos[v];
+            const uint32_t px = (uint32_t)q.y * (uint32_t)m.W + (uint32_t)q.x;
+            const int r = (int)m.wpre[px >> 5] + __popc(m.occ[px >> 5] & ((1u << (px & 31)) - 1u));
+            m.vrank[v] = r;
+            m.vcanon[r] = make_int4(q.x, q.y, __float_as_int(m.vd[v]), m.vpass[v]);
+        });
+        cl.sync();
+        items(T, [&](int t) {
+            const int4 tt = m.tri[t];
+            int a = m.vrank[tt.x], b = m.vrank[tt.y], c = m.vrank[tt.z];
+            if (a > b) { const int x = a; a = b; b = x; }
+            if (b > c) { const int x = b; b = c; c = x; }
+            if (a > b) { const int x = a; a = b; b = x; }
+            m.tkey[t] = ((unsigned long long)(unsigned)b << 32) | (unsigned)c;
+            atomicAdd(m.gcnt + a, 1);
+        });
+        cl.sync();
+        const int nchn = scan_chunks(n);
+        warp_items(nchn, [&](int c) { scan_a((const uint32_t*)m.gcnt, n, m.scan, c, Ident()); });
+        cl.sync();
+        warp_items(1, [&](int) { scan_b(m.scan, nchn, nullptr); });
+        cl.sync();
+        warp_items(nchn, [&](int c) { scan_c((const uint32_t*)m.gcnt, (uint32_t*)m.gcnt, n, m.scan, c, Ident()); });
+        cl.sync();
+        items(T, [&](int t) {  // gcnt[i] ends at the start of group i + 1
+            const int4 tt = m.tri[t];
+            const int a = min(m.vrank[tt.x], min(m.vrank[tt.y], m.vrank[tt.z]));
+            m.tperm[atomicAdd(m.gcnt + a, 1)] = t;
+        });
+        cl.sync();
+        items(n, [&](int i) {
+            const int lo = i ? m.gcnt[i - 1] : 0, hi = m.gcnt[i];
+            for (int x = lo + 1; x < hi; x++) {
+                const int t = m.tperm[x];
+                const unsigned long long kt = m.tkey[t];
+                int y = x - 1;
+                while (y >= lo && m.tkey[m.tperm[y]] > kt) {
+                    m.tperm[y + 1] = m.tperm[y];
+                    y--;
+                }
+                m.tperm[y + 1] = t;
             }
-            m.tperm[y + 1] = t;
-        }
-    });
-    grid.sync();
+        });
+        cl.sync();
+    }
 
-    // ---- 5: the next pass's raster inputs: triangle id = slot, or canonical position
-    each_item(np, pre, [&](int p) { return ld_int(&md[p].hdr->T); }, [&](int p, int s) {
-        const MeshDev& m = md[p];
+    // ---- 5: the next pass's raster inputs (triangle id = slot, or canonical position)
+    items(T, [&](int s) {
         const int t = m.canonical ? m.tperm[s] : s;
         const int4 tt = m.tri[t];
         int id[3] = {tt.x, tt.y, tt.z};
@@ -929,9 +810,9 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
         if (area <= m.small_area) {
             const int bw = x1 - x0 + 1;
             const int cls = bw <= 1 ? 0 : min(kMeshClasses - 1, 32 - __clz(bw - 1));
-            atomicAdd(&m.hdr->cls[cls], 1);
+            atomicAdd(&hd->cls[cls], 1);
         } else {
-            const int li = atomicAdd(&m.hdr->n_large, 1);
+            const int li = atomicAdd(&hd->n_large, 1);
             m.large[li] = s;
             m.lrows[li] = ((y1 - y0) / kRasterRows + 1) * ((x1 - x0) / m.cols + 1);
         }
@@ -939,16 +820,15 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
         const int4 rt = m.opp[t];
         for (int k = 0; k < 3; k++) {
             if (ref_of(rt, k) >= 0) continue;
-            const int h = atomicAdd(&m.hdr->n_hull, 1);
+            const int h = atomicAdd(&hd->n_hull, 1);
             const int2 a = m.pos[vtx(tt, k == 2 ? 0 : k + 1)], b = m.pos[vtx(tt, k == 0 ? 2 : k - 1)];
             if (h < m.n_cap) reinterpret_cast<int4*>(m.hull)[h] = make_int4(a.x, a.y, b.x, b.y);
-            else m.hdr->err = 1;
+            else hd->err = 1;
         }
     });
-    grid.sync();
+    cl.sync();
     // small list in class order; work-item counts of the large ones summed per chunk
-    each_item(np, pre, [&](int p) { return ld_int(&md[p].hdr->T); }, [&](int p, int s) {
-        const MeshDev& m = md[p];
+    items(T, [&](int s) {
         const int32_t* q = m.tri_uv + 6 * (size_t)s;
         const int x0 = max(0, min(q[0], min(q[2], q[4]))), x1 = min(m.W - 1, max(q[0], max(q[2], q[4])));
         const int y0 = max(0, min(q[1], min(q[3], q[5]))), y1 = min(m.H - 1, max(q[1], max(q[3], q[5])));
@@ -957,69 +837,61 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
         const int bw = x1 - x0 + 1;
         const int cls = bw <= 1 ? 0 : min(kMeshClasses - 1, 32 - __clz(bw - 1));
         int off = 0;
-        for (int c = 0; c < cls; c++) off += m.hdr->cls[c];
-        m.small[off + atomicAdd(&m.hdr->cls_fill[cls], 1)] = s;
+        for (int c = 0; c < cls; c++) off += hd->cls[c];
+        m.small[off + atomicAdd(&hd->cls_fill[cls], 1)] = s;
     });
-    each_warp_item(np, pre, [&](int p) { return scan_chunks(ld_int(&md[p].hdr->n_large)); }, [&](int p, int c) {
-        const MeshDev& m = md[p];
-        scan_a((const uint32_t*)m.lrows, ld_int(&m.hdr->n_large), m.scan, c, Ident());
-    });
-    grid.sync();
-    each_warp_item(np, pre, [&](int p) { return 1; }, [&](int p, int) {
-        const MeshDev& m = md[p];
-        scan_b(m.scan, scan_chunks(ld_int(&m.hdr->n_large)), &m.hdr->n_items);
+    const int nl = ld_int(&hd->n_large);
+    const int nchl = scan_chunks(nl);
+    warp_items(nchl, [&](int c) { scan_a((const uint32_t*)m.lrows, nl, m.scan, c, Ident()); });
+    cl.sync();
+    warp_items(1, [&](int) {
+        scan_b(m.scan, nchl, &hd->n_items);
         if ((threadIdx.x & 31) == 0) {
             int ns = 0;
-            for (int c = 0; c < kMeshClasses; c++) ns += m.hdr->cls[c];
-            m.hdr->n_small = ns;
+            for (int c = 0; c < kMeshClasses; c++) ns += hd->cls[c];
+            hd->n_small = ns;
         }
     });
-    grid.sync();
-    each_warp_item(np, pre, [&](int p) { return scan_chunks(ld_int(&md[p].hdr->n_large)); }, [&](int p, int c) {
-        const MeshDev& m = md[p];
-        scan_c((const uint32_t*)m.lrows, (uint32_t*)m.lrows, ld_int(&m.hdr->n_large), m.scan, c, Ident());
-    });
-    if (blockIdx.x == 0 && threadIdx.x < np) {
-        MeshHdr& h = *md[threadIdx.x].hdr;
-        h.rounds = ins_rounds;
-        h.frounds = flip_rounds;
-        h.stamp += step + 1;
+    cl.sync();
+    warp_items(nchl, [&](int c) { scan_c((const uint32_t*)m.lrows, (uint32_t*)m.lrows, nl, m.scan, c, Ident()); });
+    if (lead) {
+        hd->rounds = ins_rounds;
+        hd->frounds = flip_rounds;
+        hd->stamp = stamp0 + step + 1;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->rounds = ins_rounds + flip_rounds;
 }
-
 }  // namespace
 
 // ---------------------------------------------------------------- launch
-namespace {
-int g_mesh_per_sm = 0;  // co-resident blocks of k_mesh_pass per SM (set outside any capture)
-}
-
 cudaError_t prepare_mesh_kernels() {
-    int per_sm = 0;
-    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mesh_pass, kMeshThreads, 0);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-    g_mesh_per_sm = per_sm;
-    return cudaSuccess;
+    // every cluster of the launch is resident at once when np * cluster blocks fit
+    // the SMs; larger launches queue clusters, which is fine (they are independent)
+    return cudaFuncSetAttribute(k_mesh_pass, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
-cudaError_t launch_mesh_pass(const MeshDev* md, int np, MeshCtl* ctl, cudaStream_t s) {
+int mesh_cluster_blocks(int np) {
+    int c = 1;
+    while (c < 8 && np * c * 2 <= sm_count()) c *= 2;
+    return c;
+}
+
+cudaError_t launch_mesh_pass(const MeshDev* md, int np, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
-    if (np > kMeshBatch || g_mesh_per_sm < 1) return cudaErrorInvalidValue;
-    // every block must be resident at once for the grid-wide barriers: a
-    // cooperative launch of at most the occupancy limit
+    if (np > kMeshBatch) return cudaErrorInvalidValue;
+    const int c = mesh_cluster_blocks(np);
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)(g_mesh_per_sm * sm_count()));
+    cfg.gridDim = dim3((unsigned)(np * c));
     cfg.blockDim = dim3(kMeshThreads);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeCooperative;
-    at[0].val.cooperative = 1;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)c;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_mesh_pass, md, np, ctl);
+    return cudaLaunchKernelEx(&cfg, k_mesh_pass, md);
 }
 
 }  // namespace stereo

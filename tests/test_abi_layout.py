@@ -13,7 +13,7 @@ import paper_1511_00758_gb300 as S
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 STRUCTS = {"stereo_config": S.Config, "stereo_result": S.Result, "stereo_stats": S.Stats,
-           "stereo_tuning": S.Tuning}
+           "stereo_tuning": S.Tuning, "stereo_pair": S.Pair}
 
 
 def _c_layout():

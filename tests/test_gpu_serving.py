@@ -73,6 +73,28 @@ def test_device_wait_timeout_is_reported_and_context_recovers():
         assert torch.equal(got[k], want[k])
 
 
+def test_batch_submit_matches_single_and_takes_a_prefix():
+    """stereo_submit_batch: the pairs of a batch give the results they give when
+    submitted alone, and one invalid pair rejects the whole batch."""
+    pairs = _pairs(4)
+    with S.Context(mem_budget_bytes=1 << 29, max_slots=4, host_threads=2, **PRM) as ctx:
+        tks = ctx.submit_batch([(p.left, p.right, 320, 240, p.dmax, p.iters, p.cell) for p in pairs])
+        assert len(tks) == 4
+        outs = [ctx.result_tensors(ctx.poll(t)) for t in tks]
+        for t in tks:
+            ctx.release(t)
+    for p, o in zip(pairs, outs):
+        want = _solo(p)
+        for k in ("D_f", "C_f", "mask", "planeidx"):
+            assert torch.equal(o[k], want[k])
+    with S.Context(mem_budget_bytes=1 << 29, max_slots=1, **PRM) as ctx:
+        good = (pairs[0].left, pairs[0].right, 320, 240, 48, 2, 16)
+        with pytest.raises(S.StereoError) as e:
+            ctx.submit_batch([good, (pairs[1].left, pairs[1].right, 320, 240, 300, 2, 16)])
+        assert e.value.code == -1
+        assert ctx.stats().requests_done == 0
+
+
 def test_queue_full_returns_busy_then_drains():
     pairs = _pairs(8, 1242, 375)
     got_busy = 0
