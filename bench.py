@@ -213,7 +213,7 @@ def run_ours(args):
     ncpu = os.cpu_count() or 1
     # one core stays free for the scheduler thread and this client thread (measured faster)
     threads = args.host_threads or max(1, min(B, ncpu // max(1, world) - 1))
-    budget = int(0.5 * 2**30) + B * (40 * W * H + (64 << 20))
+    budget = int(0.5 * 2**30) + B * S.request_bytes(W, H, p0.dmax, p0.iters, p0.cell)
     ctx = S.Context(device=local, mem_budget_bytes=budget, max_slots=B, max_queue=4 * B, host_threads=threads,
                     profile=PROFILE_EVERY, batch_window_us=args.window_us, autotune=0 if args.no_autotune else 1,
                     tune_w=W, tune_h=H, host_mesh=1 if args.host_mesh else 0, **PRM)
@@ -414,7 +414,7 @@ def run_ours(args):
 
 # ------------------------------------------------------------------ other workloads
 def _make_ctx(S, local, pairs, slots, threads, window_us=0, profile=PROFILE_EVERY):
-    need = sum(80 * p.left.size + (96 << 20) for p in pairs[:slots])
+    need = sum(S.request_bytes(p.left.shape[1], p.left.shape[0], p.dmax, p.iters, p.cell) for p in pairs[:slots])
     big = max(pairs, key=lambda p: p.left.size)  # the tuning round uses the largest frame
     return S.Context(device=local, mem_budget_bytes=int(0.5 * 2**30) + need, max_slots=slots, max_queue=4096,
                      host_threads=threads, profile=profile, batch_window_us=window_us, autotune=1,

@@ -75,8 +75,11 @@ typedef struct {
     int batch_window_us;       /* continuous batching: when some requests are ready for a GPU
                                   stage while others are still in their host step, wait up to
                                   this long for more of them before launching; 0 = the default
-                                  (with device meshes, wait up to 4 ms for seed host steps in
-                                  flight; with host meshes, launch at once); < 0 = never wait */
+                                  (with device meshes, a request about to take its first pass
+                                  waits up to 4 ms for the requests of its seed round still in
+                                  their seed host step, so a burst submitted together runs its
+                                  passes together; with host meshes, launch at once);
+                                  < 0 = never wait */
     int autotune;              /* 1 = at create, time the kernels' work-shape candidates on a
                                   synthetic round of tune_w x tune_h pairs and keep the fastest
                                   (results do not depend on it; see stereo_get_tuning) */
@@ -118,6 +121,13 @@ typedef struct stereo_ctx stereo_ctx;
 
 /* Alg. 1 as a service.  stereo_create makes a context on cfg->device. */
 int stereo_create(const stereo_config* cfg, stereo_ctx** out);
+
+/* Device memory one request of this shape takes from the context's budget
+ * (mem_budget_bytes) while in flight under cfg: its frame buffers, cell
+ * records, device mesh (unless cfg->host_mesh) and staging; a budget of k times
+ * this admits k such requests at once.  No counterpart in the paper.  Returns
+ * 0 for invalid arguments. */
+size_t stereo_request_bytes(const stereo_config* cfg, int w, int h, int dmax, int iters, int cell);
 
 /* Submit one pair (I_l, I_r) with N_D = dmax, n_iters = iters and the initial
  * occupancy-grid size sz_occ = cell (Alg. 1, Table 1).  left/right may be host

@@ -13,7 +13,7 @@ import os
 from . import _build
 
 __all__ = [
-    "StereoError", "load", "lib", "Config", "Result", "Pair", "Stats", "Tuning", "Context",
+    "StereoError", "load", "lib", "Config", "Result", "Pair", "Stats", "Tuning", "Context", "request_bytes",
     "census", "fast", "epipolar_match", "delaunay", "delaunay_parallel", "delaunay_insert", "planes", "raster_scratch_bytes", "raster", "raster_noalloc", "validate_bulk",
     "validate", "resample_match", "ERRORS",
 ]
@@ -83,6 +83,7 @@ _SIGS = {
     "stereo_create": (_I, [ctypes.POINTER(Config), ctypes.POINTER(_P)]),
     "stereo_submit": (_I, [_P, _I, _P, _P, _I, _I, _I, _I, _I, ctypes.POINTER(ctypes.c_uint64)]),
     "stereo_submit_batch": (_I, [_P, ctypes.POINTER(Pair), _I, ctypes.POINTER(ctypes.c_uint64)]),
+    "stereo_request_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config), _I, _I, _I, _I, _I]),
     "stereo_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(Result), _I]),
     "stereo_poll_host": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(Result), _I, _P, _P, _P]),
     "stereo_release": (_I, [_P, ctypes.c_uint64]),
@@ -156,6 +157,15 @@ def _check(rc, what):
             what = f"{what} [{_lib.stereo_last_error().decode()}]"
         raise StereoError(rc, what)
     return rc
+
+
+def request_bytes(w, h, dmax, iters, cell, host_mesh=0, kp_per_bin=4):
+    """Device memory one request of this shape takes from a context's budget."""
+    cfg = Config()
+    lib().stereo_default_config(ctypes.byref(cfg))
+    cfg.host_mesh = host_mesh
+    cfg.kp_per_bin = kp_per_bin
+    return int(lib().stereo_request_bytes(ctypes.byref(cfg), w, h, dmax, iters, cell))
 
 
 # ---------------------------------------------------------------- stage calls

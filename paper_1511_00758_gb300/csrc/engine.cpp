@@ -37,8 +37,6 @@ namespace {
 // Default batching window with device meshes: how long a round waits for
 // seed host steps still running (a few hundred microseconds each).
 constexpr int kSeedWindowUs = 4000;
-// ... and how long after the last submission it still expects more.
-constexpr int kQuietUs = 200;
 
 double now_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -275,6 +273,7 @@ struct Request {
     int dev_n = 0;              // vertices after the last device pass
     bool mesh_now = false;      // this round runs the device mesh pass for this request
     bool raster_dev = false;    // this round rasters the device mesh
+    long long cohort = -1;      // the seed round it took part in
 };
 
 size_t block_bytes(const Request& r, int K) {
@@ -396,9 +395,8 @@ struct stereo_ctx {
     std::thread sched;
     bool stop = false;
     int host_busy = 0;
-    int seed_busy = 0;  // of which seed host steps
-    std::chrono::steady_clock::time_point last_submit{};  // time of the latest submission
-    bool last_batch = false;  // it was a batch of several pairs (no more are expected right after it)
+    long long seed_rounds = 0;                        // seed rounds run (cohort ids)
+    std::unordered_map<long long, int> cohort_busy;   // cohort -> members still in their seed host step
     std::atomic<int> mesh_steps{0};  // host mesh steps run (for the failure-injection hook)
     Pool pool;
     Pinned desc_host;
@@ -1207,26 +1205,31 @@ void scheduler(stereo_ctx* c) {
                 }
                 const size_t ready = seed.reqs.size() + iter.reqs.size();
                 if (ready > 0) {
-                    // batching window: others are still in their host step
-                    // (with device meshes the only host steps are the short seed meshes, so by
-                    // default the round waits for them: every pair then takes its passes in the
-                    // same rounds, and each mesh launch serves them all)
-                    const int window = c->cfg.batch_window_us > 0 ? c->cfg.batch_window_us
-                                       : c->cfg.batch_window_us == 0 && c->dev_mesh ? kSeedWindowUs : 0;
-                    // requests still arriving (a submission less than kQuietUs ago, a slot free)
-                    // are waited for the same way: a burst of submissions starts as one round
-                    const int busy = c->cfg.batch_window_us > 0 ? c->host_busy : c->seed_busy;
+                    // batching window: others are still in their host step.  By default, with
+                    // device meshes (whose only host steps are the short seed meshes), a request
+                    // about to take its first pass waits for the rest of its seed cohort (the
+                    // requests of the same seed round): a burst then takes every pass in the same
+                    // rounds and each mesh launch serves all of it, while a request that arrived
+                    // alone waits for nobody.
+                    int window = 0, busy = 0;
+                    if (c->cfg.batch_window_us > 0) {
+                        window = c->cfg.batch_window_us;
+                        busy = c->host_busy;
+                    } else if (c->cfg.batch_window_us == 0 && c->dev_mesh) {
+                        window = kSeedWindowUs;
+                        for (Request* r : iter.reqs) {
+                            auto it = c->cohort_busy.find(r->cohort);
+                            if (r->it == 1 && it != c->cohort_busy.end()) busy += it->second;
+                        }
+                    }
                     const auto now = std::chrono::steady_clock::now();
-                    const auto quiet_end = c->last_submit + std::chrono::microseconds(kQuietUs);
-                    const bool arriving = c->dev_mesh && c->cfg.batch_window_us == 0 && !c->last_batch &&
-                                          now < quiet_end && (int)c->active.size() < c->cfg.max_slots;
-                    if (window > 0 && (busy > 0 || arriving) && !c->stop) {
+                    if (window > 0 && busy > 0 && !c->stop) {
                         if (!waiting) {
                             waiting = true;
                             deadline = now + std::chrono::microseconds(window);
                         }
                         if (now < deadline) {
-                            c->cv_sched.wait_until(g, busy > 0 ? deadline : std::min(deadline, quiet_end));
+                            c->cv_sched.wait_until(g, deadline);
                             continue;
                         }
                     }
@@ -1259,7 +1262,11 @@ void scheduler(stereo_ctx* c) {
             continue;
         }
         std::vector<Request*> host, traces;
-        for (Request* r : seed.reqs) host.push_back(r);
+        const long long cohort = c->seed_rounds++;
+        for (Request* r : seed.reqs) {
+            r->cohort = cohort;
+            host.push_back(r);
+        }
         for (Request* r : iter.reqs) {
             if (r->mesh_now) {  // the device built the next pass's mesh: no host step
                 const MeshHdr& h = *r->st_hdr.as<MeshHdr>();
@@ -1309,7 +1316,7 @@ void scheduler(stereo_ctx* c) {
             r->state = Q_HOST;
             c->host_busy++;
             const bool is_seed = r->it == 0;
-            if (is_seed) c->seed_busy++;
+            if (is_seed) c->cohort_busy[r->cohort]++;
             c->pool.push([c, r, is_seed] {
                 const double t0 = now_ms();
                 int rc = is_seed ? host_after_seed(c, *r) : host_after_iter(*r);
@@ -1318,7 +1325,10 @@ void scheduler(stereo_ctx* c) {
                     rc = STEREO_E_INTERNAL;  // test hook: this host step reports a failure
                 std::lock_guard<std::mutex> g2(c->mu);
                 c->host_busy--;
-                if (is_seed) c->seed_busy--;
+                if (is_seed) {
+                    auto cb = c->cohort_busy.find(r->cohort);
+                    if (cb != c->cohort_busy.end() && --cb->second <= 0) c->cohort_busy.erase(cb);
+                }
                 if (rc != STEREO_OK) finish(c, *r, rc);
                 else r->state = Q_ITER_READY;
                 c->cv_sched.notify_all();
@@ -1638,6 +1648,32 @@ void stereo_default_config(stereo_config* cfg) {
     cfg->host_threads = 1;
 }
 
+size_t stereo_request_bytes(const stereo_config* cfg, int w, int h, int dmax, int iters, int cell) {
+    if (!cfg || !valid_size(w, h) || dmax < 1 || dmax > 256 || iters < 1 || cell < 1 || cfg->kp_per_bin < 1 ||
+        cfg->kp_per_bin > kMaxK)
+        return 0;
+    Request r;
+    r.W = w;
+    r.H = h;
+    r.iters = iters;
+    const int sz_min = iters >= 2 ? std::max(1, cell >> (iters - 2)) : 0;
+    r.ncell_max = iters >= 2 ? cells_of(w, h, sz_min) : 1;
+    size_t b = align_up(block_bytes(r, cfg->kp_per_bin), 256);
+    const size_t N = (size_t)w * h;
+    const int n_cap = mesh_vertex_cap(w, h, kFastBins * cfg->kp_per_bin, iters, cell);
+    if (cfg->host_mesh == 0 && iters >= 2) {
+        const int p_cap = (int)std::min<long long>(2ll * r.ncell_max, (long long)N);
+        b += align_up(mesh_bytes(w, h, n_cap, 2 * n_cap + 8, p_cap), 256);
+        b += align_up((size_t)kFastBins * cfg->kp_per_bin * 140 + (1 << 16), 256);  // S_1's staged mesh
+    } else {
+        // a staged host mesh: up to 2 triangles per support point, 40 B each plus its
+        // raster lists and hull, with the 5/4 headroom the engine keeps
+        b += align_up((size_t)n_cap * 2 * 56 * 5 / 4 + (1 << 16), 256);
+    }
+    b += align_up(2 * N, 256);  // the submitted inputs awaiting admission
+    return b;
+}
+
 namespace {
 cudaError_t ensure_mesh_kernels();
 }
@@ -1783,13 +1819,24 @@ int stereo_submit_batch(stereo_ctx* c, const stereo_pair* pairs, int n, uint64_t
     for (int i = take; i < n; i++) delete rs[i];
     rs.resize(take);
     bool copied = false;
+    CopyList cl{};  // device inputs: one gather-copy launch per kCopyBatch buffers
     for (int i = 0; i < take; i++) {
         Request* r = rs[i];
         const size_t N = (size_t)r->W * r->H;
-        if (kind[i] != 'h') {
-            const cudaMemcpyKind k = kind[i] == 'd' ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-            cudaMemcpyAsync(r->in_dev, pairs[i].left, N, k, c->copy_stream);
-            cudaMemcpyAsync(r->in_dev + N, pairs[i].right, N, k, c->copy_stream);
+        if (kind[i] == 'd') {
+            for (int k = 0; k < 2; k++) {
+                cl.src[cl.count] = k ? pairs[i].right : pairs[i].left;
+                cl.dst[cl.count] = r->in_dev + k * N;
+                cl.n[cl.count++] = (long long)N;
+            }
+            if (cl.count + 2 > kCopyBatch) {
+                if (launch_copy_list(cl, c->copy_stream) != cudaSuccess) return drop_all(STEREO_E_CUDA);
+                cl.count = 0;
+            }
+            copied = true;
+        } else if (kind[i] == 'p') {
+            cudaMemcpyAsync(r->in_dev, pairs[i].left, N, cudaMemcpyHostToDevice, c->copy_stream);
+            cudaMemcpyAsync(r->in_dev + N, pairs[i].right, N, cudaMemcpyHostToDevice, c->copy_stream);
             copied = true;
         } else {
             if (!r->in_host.ensure(2 * N)) return drop_all(STEREO_E_NOMEM);
@@ -1797,6 +1844,7 @@ int stereo_submit_batch(stereo_ctx* c, const stereo_pair* pairs, int n, uint64_t
             std::memcpy((char*)r->in_host.p + N, pairs[i].right, N);
         }
     }
+    if (cl.count > 0 && launch_copy_list(cl, c->copy_stream) != cudaSuccess) return drop_all(STEREO_E_CUDA);
     if (copied && cudaStreamSynchronize(c->copy_stream) != cudaSuccess) {
         cudaGetLastError();
         return drop_all(STEREO_E_CUDA);
@@ -1812,8 +1860,6 @@ int stereo_submit_batch(stereo_ctx* c, const stereo_pair* pairs, int n, uint64_t
             c->queue.push_back(r);
             tickets_out[i] = r->ticket;
         }
-        c->last_submit = std::chrono::steady_clock::now();
-        c->last_batch = n > 1;
     }
     c->cv_sched.notify_all();
     return take;

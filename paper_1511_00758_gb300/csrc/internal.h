@@ -126,6 +126,17 @@ cudaError_t launch_match_list(const uint32_t* cL, const uint32_t* cR, int W, int
                               const int32_t* q, int n, int dmax, const Params& prm,
                               int32_t* out, cudaStream_t s);
 
+// Copies of up to kCopyBatch device buffers in one launch (the inputs of a
+// batch submission): entry i copies n[i] bytes from src[i] to dst[i].
+constexpr int kCopyBatch = 128;
+struct CopyList {
+    const uint8_t* src[kCopyBatch];
+    uint8_t* dst[kCopyBatch];
+    long long n[kCopyBatch];
+    int count;
+};
+cudaError_t launch_copy_list(const CopyList& L, cudaStream_t s);
+
 int sm_count();
 // Frame sizes every entry point accepts: 5 <= W, H <= 8192 and W * H < 2^27
 // (pixel indices fit the 27-bit index field of the cell keys).

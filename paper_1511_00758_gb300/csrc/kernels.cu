@@ -1789,6 +1789,33 @@ cudaError_t launch_validate_bulk(const PairBatch& b, const Params& prm, cudaStre
     k_validate_bulk<<<grid_for(b.total, 2), 288, sizeof(BulkSmem), s>>>(b, prm);
     return cudaGetLastError();
 }
+// Gather copy: kCopyParts blocks per entry, each a contiguous part of it, in
+// 16-byte words when both ends are 16-byte aligned (bytes otherwise).
+constexpr int kCopyParts = 8;
+__global__ void __launch_bounds__(256) k_copy_list(const __grid_constant__ CopyList L) {
+    const int e = blockIdx.x / kCopyParts, part = blockIdx.x % kCopyParts;
+    if (e >= L.count) return;
+    const long long n = L.n[e];
+    const uint8_t* src = L.src[e];
+    uint8_t* dst = L.dst[e];
+    const long long per = (n / kCopyParts + 15) / 16 * 16;
+    const long long lo = min(n, per * part), hi = min(n, lo + per);
+    if ((((uintptr_t)src | (uintptr_t)dst) & 15) == 0) {
+        const long long w0 = lo / 16, w1 = hi / 16;
+        for (long long w = w0 + threadIdx.x; w < w1; w += blockDim.x)
+            reinterpret_cast<uint4*>(dst)[w] = __ldg(reinterpret_cast<const uint4*>(src) + w);
+        for (long long i = max(lo, w1 * 16) + threadIdx.x; i < hi; i += blockDim.x) dst[i] = src[i];
+    } else {
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) dst[i] = src[i];
+    }
+}
+
+cudaError_t launch_copy_list(const CopyList& L, cudaStream_t s) {
+    if (L.count <= 0) return cudaSuccess;
+    k_copy_list<<<L.count * kCopyParts, 256, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_resample(const PairBatch& b, const Params& prm, cudaStream_t s) {
     k_resample<<<grid_for(b.total, 8), 256, 0, s>>>(b, prm);
     return cudaGetLastError();
