@@ -178,6 +178,7 @@ struct MeshDev {
     uint32_t* wpre;           // exclusive prefix of popcount(occ) per word
     // triangles (slot order)
     int4* tri;                // vertex slots (a, b, c) with positive orientation
+    int4* tpk;                // their positions packed as (v << 14) | u, beside them
     int4* opp;                // per edge k (opposite vertex k): (t << 2) | j of the neighbour's twin edge, -1 on the hull
     unsigned long long* claim;  // insertion claims (all ~0 between rounds)
     unsigned long long* fclaim; // flip claims, the round in the high bits (newer rounds win)
@@ -186,12 +187,12 @@ struct MeshDev {
     unsigned long long* tkey; // canonical key (i << 42 | j << 21 | k), when ranked
     int* gcnt;                // triangles per smallest canonical vertex, then their prefix [n_cap + 1]
     int* tperm;               // canonical triangle order: position -> slot
-    int* pend;                // pending vertex slots of this pass
-    int* ploc;                // their current triangle (-1 once inserted, -2 - t while the round that inserted
-                              // it into t links its pieces)
-    int* plist;               // two worklists of pending entries (2 * p_cap): the points still to insert
-    int* pnb;                 // the edge a pending point lies on: -1 inside, else
+    int4* plist;              // two worklists (2 * p_cap) of the points still to insert, one record each:
+                              // (vertex slot, current triangle, edge code, packed position); the
+                              // triangle is -2 - t while the round that inserted it into t links its
+                              // pieces; the edge code is -1 inside, else
                               // ((neighbour + 1) << 4) | (twin edge << 2) | edge
+    unsigned long long* pkey; // this round's claim key of each worklist entry
     int* scan;                // scan scratch: chunk totals [scan_cap]
     int* large;               // large-triangle list (triangle ids of the raster) and item prefix [t_cap + 1]
     int* lrows;

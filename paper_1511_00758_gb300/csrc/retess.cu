@@ -92,9 +92,13 @@ __device__ __forceinline__ int& ref_of(int4& r, int k) { return k == 0 ? r.x : k
 __device__ __forceinline__ int smap_ref(const int4& s, int k) { return k == 0 ? s.y : k == 1 ? s.z : s.w; }
 __device__ __forceinline__ int mk_ref(int t, int e) { return (t << 2) | e; }
 
-// q in the closed triangle t (all three edge functions >= 0)
-__device__ __forceinline__ bool contains(const int2* __restrict__ pos, const int4& t, int2 q) {
-    const int2 a = pos[t.x], b = pos[t.y], c = pos[t.z];
+// A position packed as (v << 14) | u (u, v < 16384), and back.
+__device__ __forceinline__ int pk(int2 p) { return (p.y << 14) | p.x; }
+__device__ __forceinline__ int2 unpk(int k) { return make_int2(k & 0x3FFF, k >> 14); }
+
+// q in the closed triangle with packed vertex positions tp (all three edge functions >= 0)
+__device__ __forceinline__ bool contains(const int4& tp, int2 q) {
+    const int2 a = unpk(tp.x), b = unpk(tp.y), c = unpk(tp.z);
     return orient(b, c, q) >= 0 && orient(c, a, q) >= 0 && orient(a, b, q) >= 0;
 }
 
@@ -133,6 +137,7 @@ int scan_cap_of(int W, int H, int n_cap, int t_cap) {
     X(occ, uint32_t, words)                                 \
     X(wpre, uint32_t, words + 1)                            \
     X(tri, int4, t_cap)                                     \
+    X(tpk, int4, t_cap)                                     \
     X(opp, int4, t_cap)                                     \
     X(claim, unsigned long long, t_cap)                     \
     X(fclaim, unsigned long long, t_cap)                    \
@@ -141,10 +146,8 @@ int scan_cap_of(int W, int H, int n_cap, int t_cap) {
     X(tkey, unsigned long long, t_cap)                      \
     X(gcnt, int, (size_t)n_cap + 1)                         \
     X(tperm, int, t_cap)                                    \
-    X(pend, int, p_cap)                                     \
-    X(ploc, int, p_cap)                                     \
-    X(pnb, int, p_cap)                                      \
-    X(plist, int, (size_t)2 * p_cap)                        \
+    X(plist, int4, (size_t)2 * p_cap)                       \
+    X(pkey, unsigned long long, p_cap)                      \
     X(scan, int, scap)                                      \
     X(large, int, (size_t)t_cap + 1)                        \
     X(lrows, int, (size_t)t_cap + 1)                        \
@@ -270,17 +273,20 @@ __device__ __forceinline__ int4 smap_rec(int stamp, int k, int r_k, int k1, int 
 
 // p strictly inside t: pieces replace vertex k by p (piece k keeps old edge
 // k); piece j's edge k is the twin of piece k's edge j.
-__device__ __forceinline__ bool split3(const MeshDev& m, int t, int p, int stamp) {
+__device__ __forceinline__ bool split3(const MeshDev& m, int t, int p, int pkp, int stamp) {
     const int base = atomicAdd(&m.hdr->T, 2);
     if (base + 2 > m.t_cap) {
         m.hdr->err = 1;
         return false;
     }
-    const int4 o = m.tri[t], r = m.opp[t];
+    const int4 o = m.tri[t], r = m.opp[t], op = m.tpk[t];
     const int s0 = t, s1 = base, s2 = base + 1;
     m.tri[s0] = make_int4(p, o.y, o.z, 0);
     m.tri[s1] = make_int4(o.x, p, o.z, 0);
     m.tri[s2] = make_int4(o.x, o.y, p, 0);
+    m.tpk[s0] = make_int4(pkp, op.y, op.z, 0);
+    m.tpk[s1] = make_int4(op.x, pkp, op.z, 0);
+    m.tpk[s2] = make_int4(op.x, op.y, pkp, 0);
     m.opp[s0] = make_int4(r.x, mk_ref(s1, 0), mk_ref(s2, 0), 0);
     m.opp[s1] = make_int4(mk_ref(s0, 1), r.y, mk_ref(s2, 1), 0);
     m.opp[s2] = make_int4(mk_ref(s0, 2), mk_ref(s1, 2), r.z, 0);
@@ -296,7 +302,7 @@ __device__ __forceinline__ bool split3(const MeshDev& m, int t, int p, int stamp
 // edge is inner, its twin edge j of n splits n into A' (b replaced, slot n)
 // and B' (c replaced).  A's edge k (b -> p) is the twin of edge j of B',
 // B's edge k (p -> c) the twin of edge j of A'.
-__device__ __forceinline__ bool split_edge(const MeshDev& m, int t, int k, int n, int j, int p, int stamp) {
+__device__ __forceinline__ bool split_edge(const MeshDev& m, int t, int k, int n, int j, int p, int pkp, int stamp) {
     const int need = n >= 0 ? 2 : 1;
     const int base = atomicAdd(&m.hdr->T, need);
     if (base + need > m.t_cap) {
@@ -304,11 +310,13 @@ __device__ __forceinline__ bool split_edge(const MeshDev& m, int t, int k, int n
         return false;
     }
     const int k1 = k == 2 ? 0 : k + 1, k2 = k == 0 ? 2 : k - 1;
-    const int4 ot = m.tri[t], rt = m.opp[t];
+    const int4 ot = m.tri[t], rt = m.opp[t], pt = m.tpk[t];
     const int sB = base, sB2 = n >= 0 ? base + 1 : -1;
-    int4 A = ot, B = ot;
+    int4 A = ot, B = ot, pA = pt, pB = pt;
     vtx(A, k2) = p;
     vtx(B, k1) = p;
+    vtx(pA, k2) = pkp;
+    vtx(pB, k1) = pkp;
     int4 rA = rt, rB = rt;
     ref_of(rA, k) = n >= 0 ? mk_ref(sB2, j) : -1;
     ref_of(rA, k1) = mk_ref(sB, k2);
@@ -316,6 +324,8 @@ __device__ __forceinline__ bool split_edge(const MeshDev& m, int t, int k, int n
     ref_of(rB, k) = n >= 0 ? mk_ref(n, j) : -1;
     m.tri[t] = A;
     m.tri[sB] = B;
+    m.tpk[t] = pA;
+    m.tpk[sB] = pB;
     m.opp[t] = rA;
     m.opp[sB] = rB;
     m.smap[t] = smap_rec(stamp, k, -1, k1, mk_ref(sB, k1), k2, mk_ref(t, k2));
@@ -324,10 +334,12 @@ __device__ __forceinline__ bool split_edge(const MeshDev& m, int t, int k, int n
     m.smap[sB] = make_int4(stamp, -1, -1, -1);
     if (n >= 0) {
         const int j1 = j == 2 ? 0 : j + 1, j2 = j == 0 ? 2 : j - 1;
-        const int4 on = m.tri[n], rn = m.opp[n];
-        int4 A2 = on, B2 = on;
+        const int4 on = m.tri[n], rn = m.opp[n], pn = m.tpk[n];
+        int4 A2 = on, B2 = on, pA2 = pn, pB2 = pn;
         vtx(A2, j2) = p;  // w(j+2) = b
         vtx(B2, j1) = p;  // w(j+1) = c
+        vtx(pA2, j2) = pkp;
+        vtx(pB2, j1) = pkp;
         int4 rA2 = rn, rB2 = rn;
         ref_of(rA2, j) = mk_ref(sB, k);
         ref_of(rA2, j1) = mk_ref(sB2, j2);
@@ -335,6 +347,8 @@ __device__ __forceinline__ bool split_edge(const MeshDev& m, int t, int k, int n
         ref_of(rB2, j) = mk_ref(t, k);
         m.tri[n] = A2;
         m.tri[sB2] = B2;
+        m.tpk[n] = pA2;
+        m.tpk[sB2] = pB2;
         m.opp[n] = rA2;
         m.opp[sB2] = rB2;
         m.smap[n] = smap_rec(stamp, j, -1, j1, mk_ref(sB2, j1), j2, mk_ref(n, j2));
@@ -351,10 +365,13 @@ __device__ __forceinline__ bool split_edge(const MeshDev& m, int t, int k, int n
 __device__ __forceinline__ void flip(const MeshDev& m, int t, int k, int n, int j, int stamp) {
     const int k1 = k == 2 ? 0 : k + 1, k2 = k == 0 ? 2 : k - 1;
     const int j1 = j == 2 ? 0 : j + 1, j2 = j == 0 ? 2 : j - 1;
-    const int4 tt = m.tri[t], tn = m.tri[n], rt = m.opp[t], rn = m.opp[n];
+    const int4 tt = m.tri[t], tn = m.tri[n], rt = m.opp[t], rn = m.opp[n], pt = m.tpk[t], pn = m.tpk[n];
     const int x = vtx(tt, k), b = vtx(tt, k1), c = vtx(tt, k2), y = vtx(tn, j);
+    const int px = vtx(pt, k), pb = vtx(pt, k1), pc = vtx(pt, k2), py = vtx(pn, j);
     m.tri[t] = make_int4(x, b, y, 0);
     m.tri[n] = make_int4(y, c, x, 0);
+    m.tpk[t] = make_int4(px, pb, py, 0);
+    m.tpk[n] = make_int4(py, pc, px, 0);
     m.opp[t] = make_int4(ref_of(rn, j1), mk_ref(n, 1), ref_of(rt, k2), 0);
     m.opp[n] = make_int4(ref_of(rt, k1), mk_ref(t, 1), ref_of(rn, j2), 0);
     m.smap[t] = smap_rec(stamp, k, -1, k1, mk_ref(n, 0), k2, mk_ref(t, 2));
@@ -393,8 +410,8 @@ __device__ __forceinline__ unsigned mix32(unsigned x, unsigned r) {
 // Claim priority of a pending point: squared distance of 3q from the sum of
 // its triangle's vertices (points near the middle first, so the pieces split
 // the remaining points evenly), then the vertex slot (unique).
-__device__ __forceinline__ unsigned long long claim_key(const MeshDev& m, int4 t, int2 q, int vid) {
-    const int2 a = m.pos[t.x], b = m.pos[t.y], c = m.pos[t.z];
+__device__ __forceinline__ unsigned long long claim_key(int4 tp, int2 q, int vid) {
+    const int2 a = unpk(tp.x), b = unpk(tp.y), c = unpk(tp.z);
     const long long dx = 3ll * q.x - a.x - b.x - c.x, dy = 3ll * q.y - a.y - b.y - c.y;
     return ((unsigned long long)(dx * dx + dy * dy) << 27) | (unsigned)vid;
 }
@@ -408,30 +425,25 @@ __device__ __forceinline__ void add_point(const MeshDev& m, uint32_t px, float d
     const int slot = atomicAdd(&m.hdr->n_new, 1);
     if (vid >= m.n_cap || slot >= m.p_cap) {
         m.hdr->err = 1;
-        if (slot < m.p_cap) m.ploc[slot] = -1;
         return;
     }
     const int t = m.planeidx[px];
-    m.pos[vid] = make_int2((int)(px % (uint32_t)m.W), (int)(px / (uint32_t)m.W));
+    const int2 q = make_int2((int)(px % (uint32_t)m.W), (int)(px / (uint32_t)m.W));
+    m.pos[vid] = q;
     m.vd[vid] = d;
     m.vpass[vid] = (uint8_t)m.pass;
-    m.pend[slot] = vid;
-    m.pnb[slot] = -1;
     if (t < 0 || t >= T0) {  // an evaluated pixel always has a triangle
         m.hdr->err = 2;
-        m.ploc[slot] = -1;
         return;
     }
-    m.ploc[slot] = t;
-    m.plist[atomicAdd(&m.hdr->n_pl[0], 1)] = slot;
+    m.plist[atomicAdd(&m.hdr->n_pl[0], 1)] = make_int4(vid, t, -1, pk(q));
     atomicAdd(&m.hdr->total_new, 1);
 }
 
-// Where a pending point lies in triangle t: -1 inside, else the edge code of
-// the pnb array; -2 when it is not in t (an error).
-__device__ __forceinline__ int classify(const MeshDev& m, int t, int2 q) {
-    const int4 tt = m.tri[t];
-    const int2 a = m.pos[tt.x], b = m.pos[tt.y], c = m.pos[tt.z];
+// Where q lies in triangle t (packed positions tp, neighbours rt): -1 inside,
+// else the edge code of the worklist record; -2 when it is not in t (an error).
+__device__ __forceinline__ int classify(int4 tp, int4 rt, int2 q) {
+    const int2 a = unpk(tp.x), b = unpk(tp.y), c = unpk(tp.z);
     const long long o[3] = {orient(b, c, q), orient(c, a, q), orient(a, b, q)};
     int k = -1;
     for (int i = 0; i < 3; i++) {
@@ -442,27 +454,23 @@ __device__ __forceinline__ int classify(const MeshDev& m, int t, int2 q) {
         }
     }
     if (k < 0) return -1;
-    const int r = ref_of(m.opp[t], k);
+    const int r = ref_of(rt, k);
     const int n = r >= 0 ? r >> 2 : -1, j = r >= 0 ? r & 3 : 0;
     return ((n + 1) << 4) | (j << 2) | k;
 }
 
-// A pending point whose triangle t was split in the round with this stamp
-// moves to the piece that contains it (the pieces are named by t's record).
-__device__ __forceinline__ void relocate(const MeshDev& m, int e, int t, int stamp) {
+// The triangle a pending point at q moves to when its triangle t was split in
+// the round with this stamp: the piece that contains it (the pieces are named
+// by t's record); t itself when t was not split; -1 when no piece holds it (an
+// error).
+__device__ __forceinline__ int relocate(const MeshDev& m, int t, int2 q, int stamp) {
     const int4 st = m.smap[t];
-    if (st.x != stamp) return;
-    const int2 q = m.pos[m.pend[e]];
-    int found = -1;
-    for (int k = 0; k < 3 && found < 0; k++) {
+    if (st.x != stamp) return t;
+    for (int k = 0; k < 3; k++) {
         const int r = smap_ref(st, k);
-        if (r >= 0 && contains(m.pos, m.tri[r >> 2], q)) found = r >> 2;
+        if (r >= 0 && contains(m.tpk[r >> 2], q)) return r >> 2;
     }
-    if (found < 0) {
-        m.hdr->err = 2;
-        atomicAdd(&m.hdr->inserted, 1);
-    }
-    m.ploc[e] = found;
+    return -1;
 }
 
 // One pair per thread-block cluster: the cluster's blocks share the pair's
@@ -510,7 +518,11 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
             m.vpass[i] = 1;
         });
         items(m.seed_T, [&](int i) {
-            m.tri[i] = m.seed_tri[i];
+            const int4 st = m.seed_tri[i];
+            m.tri[i] = st;
+            m.tpk[i] = make_int4(pk(make_int2(m.seed_pos[2 * st.x], m.seed_pos[2 * st.x + 1])),
+                                 pk(make_int2(m.seed_pos[2 * st.y], m.seed_pos[2 * st.y + 1])),
+                                 pk(make_int2(m.seed_pos[2 * st.z], m.seed_pos[2 * st.z + 1])), 0);
             m.opp[i] = m.seed_opp[i];
             m.claim[i] = kNoClaim;
             m.fclaim[i] = kNoClaim;
@@ -544,7 +556,9 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
     }
     cl.sync();
 
-    // ---- 2: insertion rounds over a worklist of the points still pending
+    // ---- 2: insertion rounds over a worklist of the points still pending; each
+    // record carries the point's position, so a phase reads the record and the
+    // triangle's vertices, positions and neighbours side by side
     const int stamp0 = ld_int(&hd->stamp);
     int step = 0, ins_rounds = 0, flip_rounds = 0;
     for (; ins_rounds < kMaxInsertRounds; ins_rounds++) {
@@ -552,53 +566,53 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
         const int stamp = stamp0 + (++step);
         const int wb = ins_rounds & 1;  // this round's worklist; survivors go to the other
         const int npl = ld_int(&hd->n_pl[wb]);
-        const int* wl = m.plist + wb * m.p_cap;
-        int* wn = m.plist + (wb ^ 1) * m.p_cap;
+        int4* wl = m.plist + wb * m.p_cap;
+        int4* wn = m.plist + (wb ^ 1) * m.p_cap;
         if (lead) hd->n_pl[wb ^ 1] = 0;
         // claim the triangle (and the neighbour across the edge the point lies on)
         items(npl, [&](int i) {
-            const int e = wl[i];
-            const int t = m.ploc[e];
+            const int4 rec = wl[i];
+            const int t = rec.y;
             if (t < 0) return;
-            const int vid = m.pend[e];
-            const int2 q = m.pos[vid];
-            const int code = classify(m, t, q);
+            const int2 q = unpk(rec.w);
+            const int4 tp = m.tpk[t], rt = m.opp[t];
+            const int code = classify(tp, rt, q);
             if (code == -2) {
                 hd->err = 2;
-                m.ploc[e] = -1;
+                wl[i].y = -1;
                 atomicAdd(&hd->inserted, 1);
                 return;
             }
-            const unsigned long long key = claim_key(m, m.tri[t], q, vid);
-            m.tkey[e] = key;
-            m.pnb[e] = code;
+            const unsigned long long key = claim_key(tp, q, rec.x);
+            m.pkey[i] = key;
+            wl[i].z = code;
             atomicMin(m.claim + t, key);
             if (code >= 0 && (code >> 4) > 0) atomicMin(m.claim + ((code >> 4) - 1), key);
         });
         cl.sync();
         // a point holding all its claims splits them
         items(npl, [&](int i) {
-            const int e = wl[i];
-            const int t = m.ploc[e];
+            const int4 rec = wl[i];
+            const int t = rec.y;
             if (t < 0) return;
-            const unsigned long long key = m.tkey[e];
-            const int code = m.pnb[e];
+            const unsigned long long key = m.pkey[i];
+            const int code = rec.z;
             const int n = code >= 0 ? (code >> 4) - 1 : -1;
             if (m.claim[t] != key || (n >= 0 && m.claim[n] != key)) return;
-            const int vid = m.pend[e];
-            const bool ok = code < 0 ? split3(m, t, vid, stamp) : split_edge(m, t, code & 3, n, (code >> 2) & 3, vid, stamp);
+            const bool ok = code < 0 ? split3(m, t, rec.x, rec.w, stamp)
+                                     : split_edge(m, t, code & 3, n, (code >> 2) & 3, rec.x, rec.w, stamp);
             if (code >= 0) atomicAdd(&hd->edge_ins, 1);
-            m.ploc[e] = ok ? -2 - t : -1;
+            wl[i].y = ok ? -2 - t : -1;
             atomicAdd(&hd->inserted, 1);
         });
         cl.sync();
         // link the pieces to their neighbours; the others move to the piece they lie in
         // and stay on the worklist
         items(npl, [&](int i) {
-            const int e = wl[i];
-            const int lt = m.ploc[e];
+            const int4 rec = wl[i];
+            const int lt = rec.y;
             if (lt == -1) return;
-            const int code = m.pnb[e];
+            const int code = rec.z;
             const int n = code >= 0 ? (code >> 4) - 1 : -1;
             if (lt <= -2) {
                 const int t = -2 - lt;
@@ -616,13 +630,17 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
                     m.claim[n] = kNoClaim;
                 }
                 m.claim[t] = kNoClaim;
-                m.ploc[e] = -1;
                 return;
             }
             m.claim[lt] = kNoClaim;
             if (n >= 0) m.claim[n] = kNoClaim;
-            relocate(m, e, lt, stamp);
-            if (m.ploc[e] >= 0) wn[atomicAdd(&hd->n_pl[wb ^ 1], 1)] = e;
+            const int nt = relocate(m, lt, unpk(rec.w), stamp);
+            if (nt < 0) {
+                hd->err = 2;
+                atomicAdd(&hd->inserted, 1);
+                return;
+            }
+            wn[atomicAdd(&hd->n_pl[wb ^ 1], 1)] = make_int4(rec.x, nt, -1, rec.w);
         });
         cl.sync();
     }
@@ -654,15 +672,14 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
             items(nitems, [&](int i) {
                 const int t = tri_of(i);
                 if (f == 0 && m.smap[t].x <= stamp0) return;  // untouched this pass: its edges are legal
-                const int4 tt = m.tri[t], rt = m.opp[t];
-                const int2 a = m.pos[tt.x], b = m.pos[tt.y], c = m.pos[tt.z];
+                const int4 tp = m.tpk[t], rt = m.opp[t];
+                const int2 a = unpk(tp.x), b = unpk(tp.y), c = unpk(tp.z);
                 unsigned long long best = kNoClaim;
                 for (int k = 0; k < 3; k++) {
                     const int r = ref_of(rt, k);
                     if (r < 0) continue;
                     const int n = r >> 2;
-                    const int y = vtx(m.tri[n], r & 3);
-                    if (incircle_sos(a, b, c, m.pos[y])) {
+                    if (incircle_sos(a, b, c, unpk(vtx(m.tpk[n], r & 3)))) {
                         const unsigned eid = (unsigned)(n < t ? r : mk_ref(t, k));
                         const unsigned long long key = tag | ((unsigned long long)(mix32(eid, fstep) & 0x7FFFFu) << 25) | eid;
                         atomicMin(m.fclaim + t, key);
@@ -776,9 +793,9 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
     // ---- 5: the next pass's raster inputs (triangle id = slot, or canonical position)
     items(T, [&](int s) {
         const int t = m.canonical ? m.tperm[s] : s;
-        const int4 tt = m.tri[t];
+        const int4 tt = m.tri[t], tp = m.tpk[t];
         int id[3] = {tt.x, tt.y, tt.z};
-        int2 P[3] = {m.pos[id[0]], m.pos[id[1]], m.pos[id[2]]};
+        int2 P[3] = {unpk(tp.x), unpk(tp.y), unpk(tp.z)};
         // the vertices in canonical (v, u) order, as the plane solve takes them
         for (int a = 0; a < 2; a++)
             for (int b = 0; b < 2 - a; b++)
@@ -821,7 +838,7 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
         for (int k = 0; k < 3; k++) {
             if (ref_of(rt, k) >= 0) continue;
             const int h = atomicAdd(&hd->n_hull, 1);
-            const int2 a = m.pos[vtx(tt, k == 2 ? 0 : k + 1)], b = m.pos[vtx(tt, k == 0 ? 2 : k - 1)];
+            const int2 a = unpk(vtx(tp, k == 2 ? 0 : k + 1)), b = unpk(vtx(tp, k == 0 ? 2 : k - 1));
             if (h < m.n_cap) reinterpret_cast<int4*>(m.hull)[h] = make_int4(a.x, a.y, b.x, b.y);
             else hd->err = 1;
         }
