@@ -153,7 +153,7 @@ def _stream(s):
 
 def _check(rc, what):
     if rc < 0:
-        if rc == -7 and _lib is not None:
+        if rc in (-6, -7) and _lib is not None:
             what = f"{what} [{_lib.stereo_last_error().decode()}]"
         raise StereoError(rc, what)
     return rc

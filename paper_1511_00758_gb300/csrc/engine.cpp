@@ -1271,7 +1271,12 @@ void scheduler(stereo_ctx* c) {
             if (r->mesh_now) {  // the device built the next pass's mesh: no host step
                 const MeshHdr& h = *r->st_hdr.as<MeshHdr>();
                 if (h.err != 0) {
-                    note_error(cudaErrorUnknown, "device mesh pass failed (capacity, location or round limit)", __LINE__);
+                    char what[160];
+                    std::snprintf(what, sizeof(what),
+                                  "device mesh pass %d failed: code %d (1 capacity, 2 location, 3 round limit), "
+                                  "n %d T %d new %d inserted %d/%d rounds %d", r->it, h.err, h.n, h.T, h.n_new,
+                                  h.inserted, h.total_new, h.rounds);
+                    note_error(cudaErrorUnknown, what, __LINE__);
                     finish(c, *r, STEREO_E_INTERNAL);
                     continue;
                 }
