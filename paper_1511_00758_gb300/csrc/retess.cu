@@ -709,8 +709,12 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
             });
             cl.sync();
             // the flipped triangles link their outer edges (0 and 2); proposers that lost
-            // join the next worklist
-            const int nfl = ld_int(&hd->n_al[ab ^ 1]);
+            // join the next worklist.  The flipped pairs fill the worklist's first
+            // 2 x (this round's flips) entries; the count comes from the flip counter,
+            // which no block changes in this phase (the worklist's own counter grows
+            // here as the losers are appended, so a block reading it late would take
+            // losers, or entries not yet written, for flipped triangles)
+            const int nfl = 2 * (ld_int(&hd->flips) - flips_seen);
             items(nfl, [&](int i) {
                 const int t = an[i];
                 relink(m, t, 0, stamp);

@@ -4,7 +4,8 @@ the oracle; and the full large workload (2048x1536, dmax 256, 5 iterations,
 4x4 cells down to 1x1, millions of support points, beyond the oracle's
 quadratic triangulation) checked on sampled pixels against values the oracle
 computes one by one, and for equality between the device-mesh and host-mesh
-paths."""
+paths; and the driving workload's whole 64-pair batch in one submission, device
+meshes against host meshes."""
 from fractions import Fraction
 
 import numpy as np
@@ -132,3 +133,40 @@ def test_full_large_workload_sampled(oracle_mod):
     for v, u in pick:
         k = int(np.rint(Df[v, u]))
         assert bin(int(cL[v, u]) ^ int(cR[v, u - k])).count("1") == Cf[v, u]
+
+
+def _run_batch(pairs, host_mesh):
+    H, W = pairs[0].left.shape
+    p0 = pairs[0]
+    need = len(pairs) * S.request_bytes(W, H, p0.dmax, p0.iters, p0.cell)
+    with S.Context(mem_budget_bytes=(1 << 29) + need, max_slots=len(pairs), max_queue=2 * len(pairs),
+                   host_threads=8, host_mesh=host_mesh, **PRM) as ctx:
+        ins = [(torch.from_numpy(p.left).cuda(), torch.from_numpy(p.right).cuda()) for p in pairs]
+        outs = []
+        for rep in range(1 if host_mesh else 3):
+            tickets = ctx.submit_batch([(l, r, W, H, p.dmax, p.iters, p.cell) for (l, r), p in zip(ins, pairs)])
+            assert len(tickets) == len(pairs)
+            run = []
+            for t in tickets:
+                res = ctx.poll(t)
+                assert res.status == 0
+                run.append(ctx.result_tensors(res))
+                ctx.release(t)
+            outs.append(run)
+        return outs
+
+
+def test_full_batch_device_mesh_equals_host_mesh():
+    """64 pairs of 1242x375 (the driving workload's whole batch) in one submission:
+    each device mesh pass runs 64 thread-block clusters of several blocks, whose
+    insertion and flip rounds share worklists and counters across the blocks of a
+    cluster.  Three repetitions of the batch equal the host-mesh path bit for bit."""
+    pairs = scenes.config_pairs("driving_1242x375", n=64)
+    ref = _run_batch(pairs, host_mesh=1)[0]
+    for run in _run_batch(pairs, host_mesh=0):
+        for a, b in zip(ref, run):
+            for k in ("D_f", "C_f", "mask", "planeidx"):
+                assert torch.equal(a[k], b[k]), k
+            assert list(a["n_tri"]) == list(b["n_tri"])
+            for x, y in zip(a["support"], b["support"]):
+                assert np.array_equal(x, y)
