@@ -165,6 +165,8 @@ struct MeshHdr {
     int n_al[2];                     // entries of the two active-triangle worklists of the flip rounds
     int edge_ins;                    // insertions on an edge (2 -> 4 or hull 1 -> 2) in the last pass
     int total_new, inserted;         // points of the pass to insert, and those inserted (or given up)
+    int step;                        // rounds (insertion and flip) taken so far in this pass
+    int fdone;                       // the flip rounds ended (a round without flips)
 };
 
 struct MeshDev {
@@ -193,6 +195,8 @@ struct MeshDev {
                               // pieces; the edge code is -1 inside, else
                               // ((neighbour + 1) << 4) | (twin edge << 2) | edge
     unsigned long long* pkey; // this round's claim key of each worklist entry
+    unsigned long long* acc;  // per triangle: sums of the u and v of its pending points (u << 32 | v)
+    int* accn;                // per triangle: how many points are pending in it
     int* scan;                // scan scratch: chunk totals [scan_cap]
     int* large;               // large-triangle list (triangle ids of the raster) and item prefix [t_cap + 1]
     int* lrows;

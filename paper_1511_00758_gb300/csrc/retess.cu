@@ -46,8 +46,10 @@ namespace {
 constexpr int kMeshThreads = 1024;  // one block per SM (61 registers a thread)
 constexpr int kMaxInsertRounds = 4096;
 constexpr int kMaxFlipRounds = 1 << 15;
+constexpr int kSoloItems = kMeshThreads;  // rounds this small run in one block
 constexpr int kScanChunk = 1024;  // elements per warp in the two-level scans
 constexpr unsigned long long kNoClaim = ~0ull;
+constexpr int kDropped = -3;  // edge code of a pending point not found in its triangle
 
 size_t al(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -148,6 +150,8 @@ int scan_cap_of(int W, int H, int n_cap, int t_cap) {
     X(tperm, int, t_cap)                                    \
     X(plist, int4, (size_t)2 * p_cap)                       \
     X(pkey, unsigned long long, p_cap)                      \
+    X(acc, unsigned long long, t_cap)                       \
+    X(accn, int, t_cap)                                     \
     X(scan, int, scap)                                      \
     X(large, int, (size_t)t_cap + 1)                        \
     X(lrows, int, (size_t)t_cap + 1)                        \
@@ -294,6 +298,8 @@ __device__ __forceinline__ bool split3(const MeshDev& m, int t, int p, int pkp, 
     m.claim[s1] = m.claim[s2] = kNoClaim;
     m.fclaim[s1] = m.fclaim[s2] = kNoClaim;
     m.smap[s1] = m.smap[s2] = make_int4(stamp, -1, -1, -1);  // new this round: no old edges to map
+    m.acc[s0] = m.acc[s1] = m.acc[s2] = 0ull;  // the points left in t are counted where they move
+    m.accn[s0] = m.accn[s1] = m.accn[s2] = 0;
     return true;
 }
 
@@ -332,6 +338,8 @@ __device__ __forceinline__ bool split_edge(const MeshDev& m, int t, int k, int n
     m.claim[sB] = kNoClaim;
     m.fclaim[sB] = kNoClaim;
     m.smap[sB] = make_int4(stamp, -1, -1, -1);
+    m.acc[t] = m.acc[sB] = 0ull;
+    m.accn[t] = m.accn[sB] = 0;
     if (n >= 0) {
         const int j1 = j == 2 ? 0 : j + 1, j2 = j == 0 ? 2 : j - 1;
         const int4 on = m.tri[n], rn = m.opp[n], pn = m.tpk[n];
@@ -355,6 +363,8 @@ __device__ __forceinline__ bool split_edge(const MeshDev& m, int t, int k, int n
         m.claim[sB2] = kNoClaim;
         m.fclaim[sB2] = kNoClaim;
         m.smap[sB2] = make_int4(stamp, -1, -1, -1);
+        m.acc[n] = m.acc[sB2] = 0ull;
+        m.accn[n] = m.accn[sB2] = 0;
     }
     return true;
 }
@@ -407,13 +417,22 @@ __device__ __forceinline__ unsigned mix32(unsigned x, unsigned r) {
     return h;
 }
 
-// Claim priority of a pending point: squared distance of 3q from the sum of
-// its triangle's vertices (points near the middle first, so the pieces split
-// the remaining points evenly), then the vertex slot (unique).
-__device__ __forceinline__ unsigned long long claim_key(int4 tp, int2 q, int vid) {
-    const int2 a = unpk(tp.x), b = unpk(tp.y), c = unpk(tp.z);
-    const long long dx = 3ll * q.x - a.x - b.x - c.x, dy = 3ll * q.y - a.y - b.y - c.y;
-    return ((unsigned long long)(dx * dx + dy * dy) << 27) | (unsigned)vid;
+// Claim priority of a pending point: squared distance from the mean of the
+// points pending in its triangle (sum s of their (u, v), count c), then the
+// vertex slot (unique).  The point nearest the middle of the points, not of
+// the triangle, splits them most evenly between the pieces, which keeps the
+// rounds few where the points crowd one corner of a large triangle.  The key
+// only orders the claims (the triangulation reached does not depend on it);
+// the fp32 square of a non-negative distance orders as its bit pattern.
+__device__ __forceinline__ unsigned long long claim_key(unsigned long long s, int c, int2 q, int vid) {
+    const float mu = (float)(unsigned)(s >> 32) / (float)c, mv = (float)(unsigned)(s & 0xFFFFFFFFu) / (float)c;
+    const float dx = (float)q.x - mu, dy = (float)q.y - mv;
+    return ((unsigned long long)__float_as_uint(dx * dx + dy * dy) << 27) | (unsigned)vid;
+}
+
+__device__ __forceinline__ void count_pending(const MeshDev& m, int t, int2 q) {
+    atomicAdd(m.acc + t, ((unsigned long long)q.x << 32) | (unsigned)q.y);
+    atomicAdd(m.accn + t, 1);
 }
 
 __device__ __forceinline__ int ld_int(const int* p) { return *(const volatile int*)p; }
@@ -437,6 +456,7 @@ __device__ __forceinline__ void add_point(const MeshDev& m, uint32_t px, float d
         return;
     }
     m.plist[atomicAdd(&m.hdr->n_pl[0], 1)] = make_int4(vid, t, -1, pk(q));
+    count_pending(m, t, q);
     atomicAdd(&m.hdr->total_new, 1);
 }
 
@@ -462,10 +482,11 @@ __device__ __forceinline__ int classify(int4 tp, int4 rt, int2 q) {
 // The triangle a pending point at q moves to when its triangle t was split in
 // the round with this stamp: the piece that contains it (the pieces are named
 // by t's record); t itself when t was not split; -1 when no piece holds it (an
-// error).
-__device__ __forceinline__ int relocate(const MeshDev& m, int t, int2 q, int stamp) {
+// error).  split tells which.
+__device__ __forceinline__ int relocate(const MeshDev& m, int t, int2 q, int stamp, bool& split) {
     const int4 st = m.smap[t];
-    if (st.x != stamp) return t;
+    split = st.x == stamp;
+    if (!split) return t;
     for (int k = 0; k < 3; k++) {
         const int r = smap_ref(st, k);
         if (r >= 0 && contains(m.tpk[r >> 2], q)) return r >> 2;
@@ -509,6 +530,7 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
         hd->rounds = hd->flips = hd->frounds = hd->edge_ins = 0;
         hd->n_pl[0] = hd->n_pl[1] = hd->n_al[0] = hd->n_al[1] = 0;
         hd->total_new = hd->inserted = 0;
+        hd->step = hd->fdone = 0;
     }
     if (m.seed_T > 0) {
         items(words, [&](int i) { m.occ[i] = 0u; });
@@ -527,9 +549,15 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
             m.claim[i] = kNoClaim;
             m.fclaim[i] = kNoClaim;
             m.smap[i] = make_int4(0, -1, -1, -1);
+            m.acc[i] = 0ull;
+            m.accn[i] = 0;
         });
-    } else {  // a mesh kept from the last pass: its flip claims start empty
-        items(ld_int(&hd->T), [&](int i) { m.fclaim[i] = kNoClaim; });
+    } else {  // a mesh kept from the last pass: its flip claims start empty, no point pending
+        items(ld_int(&hd->T), [&](int i) {
+            m.fclaim[i] = kNoClaim;
+            m.acc[i] = 0ull;
+            m.accn[i] = 0;
+        });
     }
     cl.sync();
     if (m.seed_T > 0)
@@ -558,11 +586,26 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
 
     // ---- 2: insertion rounds over a worklist of the points still pending; each
     // record carries the point's position, so a phase reads the record and the
-    // triangle's vertices, positions and neighbours side by side
+    // triangle's vertices, positions and neighbours side by side.
+    // A round runs over the cluster's threads with the cluster barrier between its
+    // phases.  A round with no more items than a block has threads runs in block 0
+    // alone, with the block barrier between its phases (far cheaper, and the
+    // round's data stays in one SM), and block 0 goes on while the rounds stay that
+    // small; the others wait at the cluster barrier, then read the round and step
+    // counts from the header.  Most rounds are small: the worklists shrink fast and
+    // the flips end in chains of a few flips a round.
     const int stamp0 = ld_int(&hd->stamp);
     int step = 0, ins_rounds = 0, flip_rounds = 0;
-    for (; ins_rounds < kMaxInsertRounds; ins_rounds++) {
-        if (ld_int(&hd->inserted) >= ld_int(&hd->total_new)) break;
+    const int b0 = threadIdx.x, bstride = blockDim.x;
+    auto sync = [&](bool solo) {
+        if (solo) __syncthreads();
+        else cl.sync();
+    };
+    auto ins_round = [&](bool solo) {
+        const int i0 = solo ? b0 : t0, is = solo ? bstride : tstride;
+        auto its = [&](int n, auto body) {
+            for (int i = i0; i < n; i += is) body(i);
+        };
         const int stamp = stamp0 + (++step);
         const int wb = ins_rounds & 1;  // this round's worklist; survivors go to the other
         const int npl = ld_int(&hd->n_pl[wb]);
@@ -570,33 +613,37 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
         int4* wn = m.plist + (wb ^ 1) * m.p_cap;
         if (lead) hd->n_pl[wb ^ 1] = 0;
         // claim the triangle (and the neighbour across the edge the point lies on)
-        items(npl, [&](int i) {
+        its(npl, [&](int i) {
             const int4 rec = wl[i];
             const int t = rec.y;
             if (t < 0) return;
             const int2 q = unpk(rec.w);
             const int4 tp = m.tpk[t], rt = m.opp[t];
             const int code = classify(tp, rt, q);
-            if (code == -2) {
+            if (code == -2) {  // dropped in the next phase: the loop's counts change only after a barrier
                 hd->err = 2;
-                wl[i].y = -1;
-                atomicAdd(&hd->inserted, 1);
+                wl[i].z = kDropped;
                 return;
             }
-            const unsigned long long key = claim_key(tp, q, rec.x);
+            const unsigned long long key = claim_key(m.acc[t], m.accn[t], q, rec.x);
             m.pkey[i] = key;
             wl[i].z = code;
             atomicMin(m.claim + t, key);
             if (code >= 0 && (code >> 4) > 0) atomicMin(m.claim + ((code >> 4) - 1), key);
         });
-        cl.sync();
+        sync(solo);
         // a point holding all its claims splits them
-        items(npl, [&](int i) {
+        its(npl, [&](int i) {
             const int4 rec = wl[i];
             const int t = rec.y;
             if (t < 0) return;
-            const unsigned long long key = m.pkey[i];
             const int code = rec.z;
+            if (code == kDropped) {
+                wl[i].y = -1;
+                atomicAdd(&hd->inserted, 1);
+                return;
+            }
+            const unsigned long long key = m.pkey[i];
             const int n = code >= 0 ? (code >> 4) - 1 : -1;
             if (m.claim[t] != key || (n >= 0 && m.claim[n] != key)) return;
             const bool ok = code < 0 ? split3(m, t, rec.x, rec.w, stamp)
@@ -605,10 +652,10 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
             wl[i].y = ok ? -2 - t : -1;
             atomicAdd(&hd->inserted, 1);
         });
-        cl.sync();
+        sync(solo);
         // link the pieces to their neighbours; the others move to the piece they lie in
         // and stay on the worklist
-        items(npl, [&](int i) {
+        its(npl, [&](int i) {
             const int4 rec = wl[i];
             const int lt = rec.y;
             if (lt == -1) return;
@@ -634,15 +681,39 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
             }
             m.claim[lt] = kNoClaim;
             if (n >= 0) m.claim[n] = kNoClaim;
-            const int nt = relocate(m, lt, unpk(rec.w), stamp);
+            const int2 q = unpk(rec.w);
+            bool split;
+            const int nt = relocate(m, lt, q, stamp, split);
             if (nt < 0) {
                 hd->err = 2;
                 atomicAdd(&hd->inserted, 1);
                 return;
             }
+            if (split) count_pending(m, nt, q);  // t's count still holds the point when t was not split
             wn[atomicAdd(&hd->n_pl[wb ^ 1], 1)] = make_int4(rec.x, nt, -1, rec.w);
         });
+        sync(solo);
+        ins_rounds++;
+    };
+    auto ins_pending = [&] {
+        return ins_rounds < kMaxInsertRounds && ld_int(&hd->inserted) < ld_int(&hd->total_new);
+    };
+    while (ins_pending()) {
+        if (ld_int(&hd->n_pl[ins_rounds & 1]) > kSoloItems) {
+            ins_round(false);
+            continue;
+        }
+        if (rank == 0) {
+            do ins_round(true);
+            while (ins_pending() && ld_int(&hd->n_pl[ins_rounds & 1]) <= kSoloItems);
+            if (lead) {
+                hd->rounds = ins_rounds;
+                hd->step = step;
+            }
+        }
         cl.sync();
+        ins_rounds = ld_int(&hd->rounds);
+        step = ld_int(&hd->step);
     }
     if (ins_rounds == kMaxInsertRounds && lead) hd->err = 3;
 
@@ -656,8 +727,14 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
     // when that one proposed it, else by the other.
     if (step > 0) {
         const int T = ld_int(&hd->T);
-        int flips_seen = 0;
-        for (int f = 0; f < kMaxFlipRounds; f++) {
+        int flips_seen = 0;  // the flip count when the round began
+        // one flip round; true when it flipped nothing (the mesh is Delaunay)
+        auto flip_round = [&](bool solo) {
+            const int i0 = solo ? b0 : t0, is = solo ? bstride : tstride;
+            auto its = [&](int n, auto body) {
+                for (int i = i0; i < n; i += is) body(i);
+            };
+            const int f = flip_rounds;
             const int fstep = ++step;
             const int stamp = stamp0 + fstep;
             flip_rounds++;
@@ -669,7 +746,7 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
             const unsigned long long tag = (unsigned long long)(0xFFFFFu - (unsigned)fstep) << 44;
             auto tri_of = [&](int i) { return f == 0 ? i : al[i]; };
             // propose
-            items(nitems, [&](int i) {
+            its(nitems, [&](int i) {
                 const int t = tri_of(i);
                 if (f == 0 && m.smap[t].x <= stamp0) return;  // untouched this pass: its edges are legal
                 const int4 tp = m.tpk[t], rt = m.opp[t];
@@ -689,9 +766,9 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
                 }
                 m.tkey[t] = best;
             });
-            cl.sync();
+            sync(solo);
             // flip each winning edge once
-            items(nitems, [&](int i) {
+            its(nitems, [&](int i) {
                 const int t = tri_of(i);
                 if (f == 0 && m.smap[t].x <= stamp0) return;
                 const unsigned long long key = m.fclaim[t];
@@ -707,7 +784,7 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
                 an[at + 1] = r >> 2;
                 atomicAdd(&hd->flips, 1);
             });
-            cl.sync();
+            sync(solo);
             // the flipped triangles link their outer edges (0 and 2); proposers that lost
             // join the next worklist.  The flipped pairs fill the worklist's first
             // 2 x (this round's flips) entries; the count comes from the flip counter,
@@ -715,23 +792,46 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
             // here as the losers are appended, so a block reading it late would take
             // losers, or entries not yet written, for flipped triangles)
             const int nfl = 2 * (ld_int(&hd->flips) - flips_seen);
-            items(nfl, [&](int i) {
+            its(nfl, [&](int i) {
                 const int t = an[i];
                 relink(m, t, 0, stamp);
                 relink(m, t, 2, stamp);
             });
-            items(nitems, [&](int i) {
+            its(nitems, [&](int i) {
                 const int t = tri_of(i);
                 if (f == 0 && m.smap[t].x <= stamp0) return;
                 if (m.tkey[t] == kNoClaim || m.smap[t].x == stamp) return;  // no proposal, or flipped
                 an[atomicAdd(&hd->n_al[ab ^ 1], 1)] = t;
             });
-            cl.sync();
+            sync(solo);
             const int fl = ld_int(&hd->flips);
-            if (fl == flips_seen) break;
+            const bool none = fl == flips_seen;
             flips_seen = fl;
-            if (f == kMaxFlipRounds - 1 && lead) hd->err = 3;
+            return none;
+        };
+        bool done = false;
+        while (!done && flip_rounds < kMaxFlipRounds) {
+            if (flip_rounds == 0 || ld_int(&hd->n_al[flip_rounds & 1]) > kSoloItems) {
+                done = flip_round(false);
+                continue;
+            }
+            if (rank == 0) {
+                bool none;
+                do none = flip_round(true);
+                while (!none && flip_rounds < kMaxFlipRounds && ld_int(&hd->n_al[flip_rounds & 1]) <= kSoloItems);
+                if (lead) {
+                    hd->frounds = flip_rounds;
+                    hd->step = step;
+                    hd->fdone = none ? 1 : 0;
+                }
+            }
+            cl.sync();
+            flip_rounds = ld_int(&hd->frounds);
+            step = ld_int(&hd->step);
+            flips_seen = ld_int(&hd->flips);
+            done = ld_int(&hd->fdone) != 0;
         }
+        if (!done && lead) hd->err = 3;
     }
 
     const int n = ld_int(&hd->n), T = ld_int(&hd->T);
