@@ -2222,24 +2222,27 @@ int stereo_delaunay_insert(const int32_t* uv, int n, const int32_t* tri, int T, 
     } else if (hd.T > cap) {
         rc = STEREO_E_CAP;
     } else {
-        std::vector<int4> t4(hd.T);
-        std::vector<int32_t> perm(hd.T), rank(hd.n);
-        e = cudaMemcpyAsync(t4.data(), md.tri, 16 * (size_t)hd.T, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(perm.data(), md.tperm, 4 * (size_t)hd.T, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(rank.data(), md.vrank, 4 * (size_t)hd.n, cudaMemcpyDeviceToHost, s);
+        // the canonical triangles as vertex positions (each triple in (v, u) order); a
+        // vertex's index is its rank among S = uv + the new points, in (v, u) order
+        std::vector<int32_t> tq((size_t)6 * hd.T);
+        e = cudaMemcpyAsync(tq.data(), md.tri_uv, 24 * (size_t)hd.T, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
             note_error(e, "stereo_delaunay_insert copy back", __LINE__);
             rc = STEREO_E_CUDA;
         } else {
-            for (int i = 0; i < hd.T; i++) {
-                const int4 tt = t4[perm[i]];
-                int r[3] = {rank[tt.x], rank[tt.y], rank[tt.z]};
-                std::sort(r, r + 3);
-                tri_out[3 * i] = r[0];
-                tri_out[3 * i + 1] = r[1];
-                tri_out[3 * i + 2] = r[2];
-            }
+            std::vector<int64_t> keys;
+            keys.reserve((size_t)n + m);
+            for (int i = 0; i < n; i++) keys.push_back(((int64_t)uv[2 * i + 1] << 32) | uv[2 * i]);
+            for (int i = 0; i < m; i++) keys.push_back(((int64_t)uv_new[2 * i + 1] << 32) | uv_new[2 * i]);
+            std::sort(keys.begin(), keys.end());
+            keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+            auto rank = [&](int32_t u, int32_t v) {
+                const int64_t k = ((int64_t)v << 32) | u;
+                return (int32_t)(std::lower_bound(keys.begin(), keys.end(), k) - keys.begin());
+            };
+            for (int i = 0; i < hd.T; i++)
+                for (int k = 0; k < 3; k++) tri_out[3 * i + k] = rank(tq[6 * (size_t)i + 2 * k], tq[6 * (size_t)i + 2 * k + 1]);
             rc = hd.T;
         }
     }

@@ -169,24 +169,39 @@ struct MeshHdr {
     int fdone;                       // the flip rounds ended (a round without flips)
 };
 
+// A triangle of the device mesh, one 32-byte sector: a = the packed positions
+// (v << 14 | u) of its vertices a, b, c (positive orientation) and the
+// neighbour ref of edge 0; b = the neighbour refs of edges 1 and 2, the number
+// of points pending in it (insertion), and a scratch word (its smallest
+// canonical vertex, when ranked).  Edge k runs opposite vertex k; a ref is
+// (t << 2) | j, the neighbour's twin edge, or -1 on the hull.  A vertex is
+// named by its pixel: the rounds never need a vertex slot.
+struct TriRec {
+    int4 a, b;
+};
+
+// Per triangle: its claim (an insertion claim, then in the flip rounds a flip
+// claim whose high bits hold the round, so newer rounds win; all ~0 between
+// insertion rounds) and a second word: the sums of the u and v of the points
+// pending in it (u << 32 | v) while points are inserted, its own best flip
+// proposal in the flip rounds, its canonical key when ranked.
+struct ClaimRec {
+    unsigned long long key, acc;
+};
+
 struct MeshDev {
     // vertices (slot order: as inserted)
     int2* pos;                // (u, v)
-    float* vd;                // support disparity
     uint8_t* vpass;           // iteration the point joined the support set (1-based)
-    int* vrank;               // canonical index (rank in (v, u) order), when ranked
     int4* vcanon;             // (u, v, d bits, pass) in canonical order, when ranked
+    float* dmap;              // W*H: the support disparity at each vertex pixel
     uint32_t* occ;            // W*H bits: pixel holds a vertex
     uint32_t* wpre;           // exclusive prefix of popcount(occ) per word
     // triangles (slot order)
-    int4* tri;                // vertex slots (a, b, c) with positive orientation
-    int4* tpk;                // their positions packed as (v << 14) | u, beside them
-    int4* opp;                // per edge k (opposite vertex k): (t << 2) | j of the neighbour's twin edge, -1 on the hull
-    unsigned long long* claim;  // insertion claims (all ~0 between rounds)
-    unsigned long long* fclaim; // flip claims, the round in the high bits (newer rounds win)
+    TriRec* tr;
+    ClaimRec* cl;
     int* alist;               // two worklists of triangles to check in the flip rounds (2 * t_cap)
     int4* smap;               // split / flip record: (stamp, new ref of old edge 0, 1, 2)
-    unsigned long long* tkey; // canonical key (i << 42 | j << 21 | k), when ranked
     int* gcnt;                // triangles per smallest canonical vertex, then their prefix [n_cap + 1]
     int* tperm;               // canonical triangle order: position -> slot
     int4* plist;              // two worklists (2 * p_cap) of the points still to insert, one record each:
@@ -195,8 +210,6 @@ struct MeshDev {
                               // pieces; the edge code is -1 inside, else
                               // ((neighbour + 1) << 4) | (twin edge << 2) | edge
     unsigned long long* pkey; // this round's claim key of each worklist entry
-    unsigned long long* acc;  // per triangle: sums of the u and v of its pending points (u << 32 | v)
-    int* accn;                // per triangle: how many points are pending in it
     int* scan;                // scan scratch: chunk totals [scan_cap]
     int* large;               // large-triangle list (triangle ids of the raster) and item prefix [t_cap + 1]
     int* lrows;

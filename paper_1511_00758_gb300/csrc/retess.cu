@@ -132,26 +132,19 @@ int scan_cap_of(int W, int H, int n_cap, int t_cap) {
 #define MESH_ARRAYS(X)                                      \
     X(hdr, MeshHdr, 1)                                      \
     X(pos, int2, n_cap)                                     \
-    X(vd, float, n_cap)                                     \
     X(vpass, uint8_t, n_cap)                                \
-    X(vrank, int, n_cap)                                    \
     X(vcanon, int4, n_cap)                                  \
+    X(dmap, float, (size_t)W * H)                           \
     X(occ, uint32_t, words)                                 \
     X(wpre, uint32_t, words + 1)                            \
-    X(tri, int4, t_cap)                                     \
-    X(tpk, int4, t_cap)                                     \
-    X(opp, int4, t_cap)                                     \
-    X(claim, unsigned long long, t_cap)                     \
-    X(fclaim, unsigned long long, t_cap)                    \
+    X(tr, TriRec, t_cap)                                    \
+    X(cl, ClaimRec, t_cap)                                  \
     X(alist, int, (size_t)2 * t_cap)                        \
     X(smap, int4, t_cap)                                    \
-    X(tkey, unsigned long long, t_cap)                      \
     X(gcnt, int, (size_t)n_cap + 1)                         \
     X(tperm, int, t_cap)                                    \
     X(plist, int4, (size_t)2 * p_cap)                       \
     X(pkey, unsigned long long, p_cap)                      \
-    X(acc, unsigned long long, t_cap)                       \
-    X(accn, int, t_cap)                                     \
     X(scan, int, scap)                                      \
     X(large, int, (size_t)t_cap + 1)                        \
     X(lrows, int, (size_t)t_cap + 1)                        \
@@ -258,14 +251,27 @@ struct Popc {
 
 // ---------------------------------------------------------------- mesh edits
 // Triangle t = (v0, v1, v2) has edge k from v(k+1) to v(k+2), opposite v(k),
-// the interior on its positive side.  opp[t][k] = (s << 2) | e names the
-// twin edge e of the neighbour s.  An edit writes the new pieces with their
-// outer edges still naming the old neighbours, and records in smap[old
-// slot] (stamped with the round) where each old edge went; relink() then
-// moves those names through the neighbours' records.
+// the interior on its positive side; its record holds the vertices' packed
+// positions and, per edge k, (s << 2) | e naming the twin edge e of the
+// neighbour s.  An edit writes the new pieces whole, their outer edges still
+// naming the old neighbours, and records in smap[old slot] (stamped with the
+// round) where each old edge went; relink() then moves those names through
+// the neighbours' records.
 namespace {
 
-__device__ __forceinline__ void set_ref(int4* opp, int t, int e, int r) { reinterpret_cast<int*>(opp + t)[e] = r; }
+__device__ __forceinline__ int4 pks_of(const TriRec& r) { return make_int4(r.a.x, r.a.y, r.a.z, 0); }
+__device__ __forceinline__ int4 refs_of(const TriRec& r) { return make_int4(r.a.w, r.b.x, r.b.y, 0); }
+
+// the whole record of t: positions p, neighbour refs r, no point pending
+__device__ __forceinline__ void put_tri(const MeshDev& m, int t, int4 p, int4 r) {
+    m.tr[t].a = make_int4(p.x, p.y, p.z, r.x);
+    m.tr[t].b = make_int4(r.y, r.z, 0, 0);
+}
+__device__ __forceinline__ int* ref_ptr(const MeshDev& m, int t, int e) {
+    return e == 0 ? &m.tr[t].a.w : &m.tr[t].b.x + (e - 1);
+}
+__device__ __forceinline__ int get_ref(const MeshDev& m, int t, int e) { return *ref_ptr(m, t, e); }
+__device__ __forceinline__ void set_ref(const MeshDev& m, int t, int e, int r) { *ref_ptr(m, t, e) = r; }
 
 __device__ __forceinline__ int4 smap_rec(int stamp, int k, int r_k, int k1, int r_k1, int k2, int r_k2) {
     int r[3];
@@ -275,31 +281,26 @@ __device__ __forceinline__ int4 smap_rec(int stamp, int k, int r_k, int k1, int 
     return make_int4(stamp, r[0], r[1], r[2]);
 }
 
-// p strictly inside t: pieces replace vertex k by p (piece k keeps old edge
-// k); piece j's edge k is the twin of piece k's edge j.
-__device__ __forceinline__ bool split3(const MeshDev& m, int t, int p, int pkp, int stamp) {
+// p (packed position pkp) strictly inside t: pieces replace vertex k by p
+// (piece k keeps old edge k); piece j's edge k is the twin of piece k's edge j.
+// t keeps the claim that won it (the round resets it); the points left in t
+// are counted in the pieces they move to.
+__device__ __forceinline__ bool split3(const MeshDev& m, int t, int pkp, int stamp) {
     const int base = atomicAdd(&m.hdr->T, 2);
     if (base + 2 > m.t_cap) {
         m.hdr->err = 1;
         return false;
     }
-    const int4 o = m.tri[t], r = m.opp[t], op = m.tpk[t];
+    const TriRec o = m.tr[t];
+    const int4 op = pks_of(o), r = refs_of(o);
     const int s0 = t, s1 = base, s2 = base + 1;
-    m.tri[s0] = make_int4(p, o.y, o.z, 0);
-    m.tri[s1] = make_int4(o.x, p, o.z, 0);
-    m.tri[s2] = make_int4(o.x, o.y, p, 0);
-    m.tpk[s0] = make_int4(pkp, op.y, op.z, 0);
-    m.tpk[s1] = make_int4(op.x, pkp, op.z, 0);
-    m.tpk[s2] = make_int4(op.x, op.y, pkp, 0);
-    m.opp[s0] = make_int4(r.x, mk_ref(s1, 0), mk_ref(s2, 0), 0);
-    m.opp[s1] = make_int4(mk_ref(s0, 1), r.y, mk_ref(s2, 1), 0);
-    m.opp[s2] = make_int4(mk_ref(s0, 2), mk_ref(s1, 2), r.z, 0);
+    put_tri(m, s0, make_int4(pkp, op.y, op.z, 0), make_int4(r.x, mk_ref(s1, 0), mk_ref(s2, 0), 0));
+    put_tri(m, s1, make_int4(op.x, pkp, op.z, 0), make_int4(mk_ref(s0, 1), r.y, mk_ref(s2, 1), 0));
+    put_tri(m, s2, make_int4(op.x, op.y, pkp, 0), make_int4(mk_ref(s0, 2), mk_ref(s1, 2), r.z, 0));
     m.smap[t] = make_int4(stamp, mk_ref(s0, 0), mk_ref(s1, 1), mk_ref(s2, 2));
-    m.claim[s1] = m.claim[s2] = kNoClaim;
-    m.fclaim[s1] = m.fclaim[s2] = kNoClaim;
     m.smap[s1] = m.smap[s2] = make_int4(stamp, -1, -1, -1);  // new this round: no old edges to map
-    m.acc[s0] = m.acc[s1] = m.acc[s2] = 0ull;  // the points left in t are counted where they move
-    m.accn[s0] = m.accn[s1] = m.accn[s2] = 0;
+    m.cl[s0].acc = 0ull;
+    m.cl[s1] = m.cl[s2] = ClaimRec{kNoClaim, 0ull};
     return true;
 }
 
@@ -308,7 +309,7 @@ __device__ __forceinline__ bool split3(const MeshDev& m, int t, int p, int pkp, 
 // edge is inner, its twin edge j of n splits n into A' (b replaced, slot n)
 // and B' (c replaced).  A's edge k (b -> p) is the twin of edge j of B',
 // B's edge k (p -> c) the twin of edge j of A'.
-__device__ __forceinline__ bool split_edge(const MeshDev& m, int t, int k, int n, int j, int p, int pkp, int stamp) {
+__device__ __forceinline__ bool split_edge(const MeshDev& m, int t, int k, int n, int j, int pkp, int stamp) {
     const int need = n >= 0 ? 2 : 1;
     const int base = atomicAdd(&m.hdr->T, need);
     if (base + need > m.t_cap) {
@@ -316,11 +317,10 @@ __device__ __forceinline__ bool split_edge(const MeshDev& m, int t, int k, int n
         return false;
     }
     const int k1 = k == 2 ? 0 : k + 1, k2 = k == 0 ? 2 : k - 1;
-    const int4 ot = m.tri[t], rt = m.opp[t], pt = m.tpk[t];
+    const TriRec ot = m.tr[t];
+    const int4 pt = pks_of(ot), rt = refs_of(ot);
     const int sB = base, sB2 = n >= 0 ? base + 1 : -1;
-    int4 A = ot, B = ot, pA = pt, pB = pt;
-    vtx(A, k2) = p;
-    vtx(B, k1) = p;
+    int4 pA = pt, pB = pt;
     vtx(pA, k2) = pkp;
     vtx(pB, k1) = pkp;
     int4 rA = rt, rB = rt;
@@ -328,43 +328,30 @@ __device__ __forceinline__ bool split_edge(const MeshDev& m, int t, int k, int n
     ref_of(rA, k1) = mk_ref(sB, k2);
     ref_of(rB, k2) = mk_ref(t, k1);
     ref_of(rB, k) = n >= 0 ? mk_ref(n, j) : -1;
-    m.tri[t] = A;
-    m.tri[sB] = B;
-    m.tpk[t] = pA;
-    m.tpk[sB] = pB;
-    m.opp[t] = rA;
-    m.opp[sB] = rB;
+    put_tri(m, t, pA, rA);
+    put_tri(m, sB, pB, rB);
     m.smap[t] = smap_rec(stamp, k, -1, k1, mk_ref(sB, k1), k2, mk_ref(t, k2));
-    m.claim[sB] = kNoClaim;
-    m.fclaim[sB] = kNoClaim;
     m.smap[sB] = make_int4(stamp, -1, -1, -1);
-    m.acc[t] = m.acc[sB] = 0ull;
-    m.accn[t] = m.accn[sB] = 0;
+    m.cl[t].acc = 0ull;
+    m.cl[sB] = ClaimRec{kNoClaim, 0ull};
     if (n >= 0) {
         const int j1 = j == 2 ? 0 : j + 1, j2 = j == 0 ? 2 : j - 1;
-        const int4 on = m.tri[n], rn = m.opp[n], pn = m.tpk[n];
-        int4 A2 = on, B2 = on, pA2 = pn, pB2 = pn;
-        vtx(A2, j2) = p;  // w(j+2) = b
-        vtx(B2, j1) = p;  // w(j+1) = c
-        vtx(pA2, j2) = pkp;
-        vtx(pB2, j1) = pkp;
+        const TriRec on = m.tr[n];
+        const int4 pn = pks_of(on), rn = refs_of(on);
+        int4 pA2 = pn, pB2 = pn;
+        vtx(pA2, j2) = pkp;  // w(j+2) = b
+        vtx(pB2, j1) = pkp;  // w(j+1) = c
         int4 rA2 = rn, rB2 = rn;
         ref_of(rA2, j) = mk_ref(sB, k);
         ref_of(rA2, j1) = mk_ref(sB2, j2);
         ref_of(rB2, j2) = mk_ref(n, j1);
         ref_of(rB2, j) = mk_ref(t, k);
-        m.tri[n] = A2;
-        m.tri[sB2] = B2;
-        m.tpk[n] = pA2;
-        m.tpk[sB2] = pB2;
-        m.opp[n] = rA2;
-        m.opp[sB2] = rB2;
+        put_tri(m, n, pA2, rA2);
+        put_tri(m, sB2, pB2, rB2);
         m.smap[n] = smap_rec(stamp, j, -1, j1, mk_ref(sB2, j1), j2, mk_ref(n, j2));
-        m.claim[sB2] = kNoClaim;
-        m.fclaim[sB2] = kNoClaim;
         m.smap[sB2] = make_int4(stamp, -1, -1, -1);
-        m.acc[n] = m.acc[sB2] = 0ull;
-        m.accn[n] = m.accn[sB2] = 0;
+        m.cl[n].acc = 0ull;
+        m.cl[sB2] = ClaimRec{kNoClaim, 0ull};
     }
     return true;
 }
@@ -375,15 +362,11 @@ __device__ __forceinline__ bool split_edge(const MeshDev& m, int t, int k, int n
 __device__ __forceinline__ void flip(const MeshDev& m, int t, int k, int n, int j, int stamp) {
     const int k1 = k == 2 ? 0 : k + 1, k2 = k == 0 ? 2 : k - 1;
     const int j1 = j == 2 ? 0 : j + 1, j2 = j == 0 ? 2 : j - 1;
-    const int4 tt = m.tri[t], tn = m.tri[n], rt = m.opp[t], rn = m.opp[n], pt = m.tpk[t], pn = m.tpk[n];
-    const int x = vtx(tt, k), b = vtx(tt, k1), c = vtx(tt, k2), y = vtx(tn, j);
+    const TriRec Rt = m.tr[t], Rn = m.tr[n];
+    const int4 pt = pks_of(Rt), pn = pks_of(Rn), rt = refs_of(Rt), rn = refs_of(Rn);
     const int px = vtx(pt, k), pb = vtx(pt, k1), pc = vtx(pt, k2), py = vtx(pn, j);
-    m.tri[t] = make_int4(x, b, y, 0);
-    m.tri[n] = make_int4(y, c, x, 0);
-    m.tpk[t] = make_int4(px, pb, py, 0);
-    m.tpk[n] = make_int4(py, pc, px, 0);
-    m.opp[t] = make_int4(ref_of(rn, j1), mk_ref(n, 1), ref_of(rt, k2), 0);
-    m.opp[n] = make_int4(ref_of(rt, k1), mk_ref(t, 1), ref_of(rn, j2), 0);
+    put_tri(m, t, make_int4(px, pb, py, 0), make_int4(ref_of(rn, j1), mk_ref(n, 1), ref_of(rt, k2), 0));
+    put_tri(m, n, make_int4(py, pc, px, 0), make_int4(ref_of(rt, k1), mk_ref(t, 1), ref_of(rn, j2), 0));
     m.smap[t] = smap_rec(stamp, k, -1, k1, mk_ref(n, 0), k2, mk_ref(t, 2));
     m.smap[n] = smap_rec(stamp, j, -1, j1, mk_ref(t, 0), j2, mk_ref(n, 2));
 }
@@ -392,12 +375,12 @@ __device__ __forceinline__ void flip(const MeshDev& m, int t, int k, int n, int 
 // (m', i) goes through m''s record when m' was edited this round too (that
 // edit links its own side); otherwise the neighbour is told about s.
 __device__ __forceinline__ void relink(const MeshDev& m, int s, int e, int stamp) {
-    const int r = reinterpret_cast<const int*>(m.opp + s)[e];
+    const int r = get_ref(m, s, e);
     if (r < 0) return;
     const int mm = r >> 2, i = r & 3;
     const int4 sm = m.smap[mm];
-    if (sm.x == stamp) set_ref(m.opp, s, e, smap_ref(sm, i));
-    else set_ref(m.opp, mm, i, mk_ref(s, e));
+    if (sm.x == stamp) set_ref(m, s, e, smap_ref(sm, i));
+    else set_ref(m, mm, i, mk_ref(s, e));
 }
 
 }  // namespace
@@ -431,8 +414,8 @@ __device__ __forceinline__ unsigned long long claim_key(unsigned long long s, in
 }
 
 __device__ __forceinline__ void count_pending(const MeshDev& m, int t, int2 q) {
-    atomicAdd(m.acc + t, ((unsigned long long)q.x << 32) | (unsigned)q.y);
-    atomicAdd(m.accn + t, 1);
+    atomicAdd(&m.cl[t].acc, ((unsigned long long)q.x << 32) | (unsigned)q.y);
+    atomicAdd(&m.tr[t].b.z, 1);
 }
 
 __device__ __forceinline__ int ld_int(const int* p) { return *(const volatile int*)p; }
@@ -449,8 +432,8 @@ __device__ __forceinline__ void add_point(const MeshDev& m, uint32_t px, float d
     const int t = m.planeidx[px];
     const int2 q = make_int2((int)(px % (uint32_t)m.W), (int)(px / (uint32_t)m.W));
     m.pos[vid] = q;
-    m.vd[vid] = d;
     m.vpass[vid] = (uint8_t)m.pass;
+    m.dmap[px] = d;
     if (t < 0 || t >= T0) {  // an evaluated pixel always has a triangle
         m.hdr->err = 2;
         return;
@@ -489,7 +472,7 @@ __device__ __forceinline__ int relocate(const MeshDev& m, int t, int2 q, int sta
     if (!split) return t;
     for (int k = 0; k < 3; k++) {
         const int r = smap_ref(st, k);
-        if (r >= 0 && contains(m.tpk[r >> 2], q)) return r >> 2;
+        if (r >= 0 && contains(m.tr[r >> 2].a, q)) return r >> 2;
     }
     return -1;
 }
@@ -535,28 +518,25 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
     if (m.seed_T > 0) {
         items(words, [&](int i) { m.occ[i] = 0u; });
         items(m.seed_n, [&](int i) {
-            m.pos[i] = make_int2(m.seed_pos[2 * i], m.seed_pos[2 * i + 1]);
-            m.vd[i] = m.seed_d[i];
+            const int2 q = make_int2(m.seed_pos[2 * i], m.seed_pos[2 * i + 1]);
+            m.pos[i] = q;
             m.vpass[i] = 1;
+            m.dmap[(size_t)q.y * m.W + q.x] = m.seed_d[i];
         });
         items(m.seed_T, [&](int i) {
             const int4 st = m.seed_tri[i];
-            m.tri[i] = st;
-            m.tpk[i] = make_int4(pk(make_int2(m.seed_pos[2 * st.x], m.seed_pos[2 * st.x + 1])),
-                                 pk(make_int2(m.seed_pos[2 * st.y], m.seed_pos[2 * st.y + 1])),
-                                 pk(make_int2(m.seed_pos[2 * st.z], m.seed_pos[2 * st.z + 1])), 0);
-            m.opp[i] = m.seed_opp[i];
-            m.claim[i] = kNoClaim;
-            m.fclaim[i] = kNoClaim;
+            put_tri(m, i,
+                    make_int4(pk(make_int2(m.seed_pos[2 * st.x], m.seed_pos[2 * st.x + 1])),
+                              pk(make_int2(m.seed_pos[2 * st.y], m.seed_pos[2 * st.y + 1])),
+                              pk(make_int2(m.seed_pos[2 * st.z], m.seed_pos[2 * st.z + 1])), 0),
+                    m.seed_opp[i]);
+            m.cl[i] = ClaimRec{kNoClaim, 0ull};
             m.smap[i] = make_int4(0, -1, -1, -1);
-            m.acc[i] = 0ull;
-            m.accn[i] = 0;
         });
-    } else {  // a mesh kept from the last pass: its flip claims start empty, no point pending
+    } else {  // a mesh kept from the last pass: its claims start empty, no point pending
         items(ld_int(&hd->T), [&](int i) {
-            m.fclaim[i] = kNoClaim;
-            m.acc[i] = 0ull;
-            m.accn[i] = 0;
+            m.cl[i] = ClaimRec{kNoClaim, 0ull};
+            m.tr[i].b.z = 0;
         });
     }
     cl.sync();
@@ -618,18 +598,18 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
             const int t = rec.y;
             if (t < 0) return;
             const int2 q = unpk(rec.w);
-            const int4 tp = m.tpk[t], rt = m.opp[t];
-            const int code = classify(tp, rt, q);
+            const TriRec R = m.tr[t];
+            const int code = classify(pks_of(R), refs_of(R), q);
             if (code == -2) {  // dropped in the next phase: the loop's counts change only after a barrier
                 hd->err = 2;
                 wl[i].z = kDropped;
                 return;
             }
-            const unsigned long long key = claim_key(m.acc[t], m.accn[t], q, rec.x);
+            const unsigned long long key = claim_key(m.cl[t].acc, R.b.z, q, rec.x);
             m.pkey[i] = key;
             wl[i].z = code;
-            atomicMin(m.claim + t, key);
-            if (code >= 0 && (code >> 4) > 0) atomicMin(m.claim + ((code >> 4) - 1), key);
+            atomicMin(&m.cl[t].key, key);
+            if (code >= 0 && (code >> 4) > 0) atomicMin(&m.cl[(code >> 4) - 1].key, key);
         });
         sync(solo);
         // a point holding all its claims splits them
@@ -645,9 +625,9 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
             }
             const unsigned long long key = m.pkey[i];
             const int n = code >= 0 ? (code >> 4) - 1 : -1;
-            if (m.claim[t] != key || (n >= 0 && m.claim[n] != key)) return;
-            const bool ok = code < 0 ? split3(m, t, rec.x, rec.w, stamp)
-                                     : split_edge(m, t, code & 3, n, (code >> 2) & 3, rec.x, rec.w, stamp);
+            if (m.cl[t].key != key || (n >= 0 && m.cl[n].key != key)) return;
+            const bool ok = code < 0 ? split3(m, t, rec.w, stamp)
+                                     : split_edge(m, t, code & 3, n, (code >> 2) & 3, rec.w, stamp);
             if (code >= 0) atomicAdd(&hd->edge_ins, 1);
             wl[i].y = ok ? -2 - t : -1;
             atomicAdd(&hd->inserted, 1);
@@ -674,13 +654,13 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
                         const int r = smap_ref(sn, k);
                         if (r >= 0) relink(m, r >> 2, r & 3, stamp);
                     }
-                    m.claim[n] = kNoClaim;
+                    m.cl[n].key = kNoClaim;
                 }
-                m.claim[t] = kNoClaim;
+                m.cl[t].key = kNoClaim;
                 return;
             }
-            m.claim[lt] = kNoClaim;
-            if (n >= 0) m.claim[n] = kNoClaim;
+            m.cl[lt].key = kNoClaim;
+            if (n >= 0) m.cl[n].key = kNoClaim;
             const int2 q = unpk(rec.w);
             bool split;
             const int nt = relocate(m, lt, q, stamp, split);
@@ -749,35 +729,40 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
             its(nitems, [&](int i) {
                 const int t = tri_of(i);
                 if (f == 0 && m.smap[t].x <= stamp0) return;  // untouched this pass: its edges are legal
-                const int4 tp = m.tpk[t], rt = m.opp[t];
-                const int2 a = unpk(tp.x), b = unpk(tp.y), c = unpk(tp.z);
+                const TriRec R = m.tr[t];
+                const int4 rt = refs_of(R);
+                const int2 a = unpk(R.a.x), b = unpk(R.a.y), c = unpk(R.a.z);
                 unsigned long long best = kNoClaim;
                 for (int k = 0; k < 3; k++) {
                     const int r = ref_of(rt, k);
                     if (r < 0) continue;
                     const int n = r >> 2;
-                    if (incircle_sos(a, b, c, unpk(vtx(m.tpk[n], r & 3)))) {
+                    if (incircle_sos(a, b, c, unpk(vtx(m.tr[n].a, r & 3)))) {
                         const unsigned eid = (unsigned)(n < t ? r : mk_ref(t, k));
                         const unsigned long long key = tag | ((unsigned long long)(mix32(eid, fstep) & 0x7FFFFu) << 25) | eid;
-                        atomicMin(m.fclaim + t, key);
-                        atomicMin(m.fclaim + n, key);
+                        atomicMin(&m.cl[t].key, key);
+                        atomicMin(&m.cl[n].key, key);
                         best = min(best, key);
                     }
                 }
-                m.tkey[t] = best;
+                m.cl[t].acc = best;
             });
             sync(solo);
             // flip each winning edge once
             its(nitems, [&](int i) {
                 const int t = tri_of(i);
                 if (f == 0 && m.smap[t].x <= stamp0) return;
-                const unsigned long long key = m.fclaim[t];
-                if (m.tkey[t] != key || (key >> 44) != (tag >> 44)) return;  // t did not propose the winner
+                const ClaimRec ct = m.cl[t];
+                const unsigned long long key = ct.key;
+                if (ct.acc != key || (key >> 44) != (tag >> 44)) return;  // t did not propose the winner
                 const int tm = (int)((key & 0x1FFFFFFull) >> 2), km = (int)(key & 3);
-                const int n = t == tm ? ref_of(m.opp[t], km) >> 2 : tm;
-                if (m.fclaim[n] != key) return;
-                if (t != tm && m.tkey[tm] == key && m.fclaim[tm] == key) return;  // the lower slot flips it
-                const int r = ref_of(m.opp[tm], km);
+                const int n = t == tm ? get_ref(m, t, km) >> 2 : tm;
+                if (m.cl[n].key != key) return;
+                if (t != tm) {
+                    const ClaimRec cm = m.cl[tm];
+                    if (cm.acc == key && cm.key == key) return;  // the lower slot flips it
+                }
+                const int r = get_ref(m, tm, km);
                 flip(m, tm, km, r >> 2, r & 3, stamp);
                 const int at = atomicAdd(&hd->n_al[ab ^ 1], 2);
                 an[at] = tm;
@@ -800,7 +785,7 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
             its(nitems, [&](int i) {
                 const int t = tri_of(i);
                 if (f == 0 && m.smap[t].x <= stamp0) return;
-                if (m.tkey[t] == kNoClaim || m.smap[t].x == stamp) return;  // no proposal, or flipped
+                if (m.cl[t].acc == kNoClaim || m.smap[t].x == stamp) return;  // no proposal, or flipped
                 an[atomicAdd(&hd->n_al[ab ^ 1], 1)] = t;
             });
             sync(solo);
@@ -847,21 +832,25 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
         cl.sync();
         warp_items(nch, [&](int c) { scan_c(m.occ, m.wpre, words, m.scan, c, Popc()); });
         cl.sync();
+        // the rank of the vertex at packed position k: vertex pixels before it
+        auto rank_of = [&](int k) {
+            const int2 q = unpk(k);
+            const uint32_t px = (uint32_t)q.y * (uint32_t)m.W + (uint32_t)q.x;
+            return (int)m.wpre[px >> 5] + __popc(m.occ[px >> 5] & ((1u << (px & 31)) - 1u));
+        };
         items(n, [&](int v) {
             const int2 q = m.pos[v];
-            const uint32_t px = (uint32_t)q.y * (uint32_t)m.W + (uint32_t)q.x;
-            const int r = (int)m.wpre[px >> 5] + __popc(m.occ[px >> 5] & ((1u << (px & 31)) - 1u));
-            m.vrank[v] = r;
-            m.vcanon[r] = make_int4(q.x, q.y, __float_as_int(m.vd[v]), m.vpass[v]);
+            const int r = rank_of(pk(q));
+            m.vcanon[r] = make_int4(q.x, q.y, __float_as_int(m.dmap[(size_t)q.y * m.W + q.x]), m.vpass[v]);
         });
-        cl.sync();
         items(T, [&](int t) {
-            const int4 tt = m.tri[t];
-            int a = m.vrank[tt.x], b = m.vrank[tt.y], c = m.vrank[tt.z];
+            const int4 tp = m.tr[t].a;
+            int a = rank_of(tp.x), b = rank_of(tp.y), c = rank_of(tp.z);
             if (a > b) { const int x = a; a = b; b = x; }
             if (b > c) { const int x = b; b = c; c = x; }
             if (a > b) { const int x = a; a = b; b = x; }
-            m.tkey[t] = ((unsigned long long)(unsigned)b << 32) | (unsigned)c;
+            m.cl[t].acc = ((unsigned long long)(unsigned)b << 32) | (unsigned)c;
+            m.tr[t].b.w = a;
             atomicAdd(m.gcnt + a, 1);
         });
         cl.sync();
@@ -873,18 +862,16 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
         warp_items(nchn, [&](int c) { scan_c((const uint32_t*)m.gcnt, (uint32_t*)m.gcnt, n, m.scan, c, Ident()); });
         cl.sync();
         items(T, [&](int t) {  // gcnt[i] ends at the start of group i + 1
-            const int4 tt = m.tri[t];
-            const int a = min(m.vrank[tt.x], min(m.vrank[tt.y], m.vrank[tt.z]));
-            m.tperm[atomicAdd(m.gcnt + a, 1)] = t;
+            m.tperm[atomicAdd(m.gcnt + m.tr[t].b.w, 1)] = t;
         });
         cl.sync();
         items(n, [&](int i) {
             const int lo = i ? m.gcnt[i - 1] : 0, hi = m.gcnt[i];
             for (int x = lo + 1; x < hi; x++) {
                 const int t = m.tperm[x];
-                const unsigned long long kt = m.tkey[t];
+                const unsigned long long kt = m.cl[t].acc;
                 int y = x - 1;
-                while (y >= lo && m.tkey[m.tperm[y]] > kt) {
+                while (y >= lo && m.cl[m.tperm[y]].acc > kt) {
                     m.tperm[y + 1] = m.tperm[y];
                     y--;
                 }
@@ -897,15 +884,14 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
     // ---- 5: the next pass's raster inputs (triangle id = slot, or canonical position)
     items(T, [&](int s) {
         const int t = m.canonical ? m.tperm[s] : s;
-        const int4 tt = m.tri[t], tp = m.tpk[t];
-        int id[3] = {tt.x, tt.y, tt.z};
+        const TriRec R = m.tr[t];
+        const int4 tp = pks_of(R);
         int2 P[3] = {unpk(tp.x), unpk(tp.y), unpk(tp.z)};
         // the vertices in canonical (v, u) order, as the plane solve takes them
         for (int a = 0; a < 2; a++)
             for (int b = 0; b < 2 - a; b++)
                 if (vkey(P[b]) > vkey(P[b + 1])) {
                     const int2 x = P[b]; P[b] = P[b + 1]; P[b + 1] = x;
-                    const int y = id[b]; id[b] = id[b + 1]; id[b + 1] = y;
                 }
         int32_t* q = m.tri_uv + 6 * (size_t)s;
         q[0] = P[0].x; q[1] = P[0].y; q[2] = P[1].x; q[3] = P[1].y; q[4] = P[2].x; q[5] = P[2].y;
@@ -913,9 +899,9 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
         // operation (each rounded on its own: no contraction into FMAs)
         const long long u0 = P[0].x, v0 = P[0].y, u1 = P[1].x, v1 = P[1].y, u2 = P[2].x, v2 = P[2].y;
         const long long det = (u1 - u0) * (v2 - v0) - (u2 - u0) * (v1 - v0);
-        const double d0 = (double)m.vd[id[0]];
-        const double e1 = __dsub_rn((double)m.vd[id[1]], d0);
-        const double e2 = __dsub_rn((double)m.vd[id[2]], d0);
+        const double d0 = (double)m.dmap[v0 * m.W + u0];
+        const double e1 = __dsub_rn((double)m.dmap[v1 * m.W + u1], d0);
+        const double e2 = __dsub_rn((double)m.dmap[v2 * m.W + u2], d0);
         const double na = __dsub_rn(__dmul_rn(e1, (double)(v2 - v0)), __dmul_rn(e2, (double)(v1 - v0)));
         const double nb = __dsub_rn(__dmul_rn((double)(u1 - u0), e2), __dmul_rn((double)(u2 - u0), e1));
         const double A = __ddiv_rn(na, (double)det);
@@ -938,7 +924,7 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
             m.lrows[li] = ((y1 - y0) / kRasterRows + 1) * ((x1 - x0) / m.cols + 1);
         }
         // hull edges, directed with the interior on the positive side
-        const int4 rt = m.opp[t];
+        const int4 rt = refs_of(R);
         for (int k = 0; k < 3; k++) {
             if (ref_of(rt, k) >= 0) continue;
             const int h = atomicAdd(&hd->n_hull, 1);
