@@ -138,12 +138,23 @@ size_t stereo_request_bytes(const stereo_config* cfg, int w, int h, int dmax, in
 int stereo_submit(stereo_ctx* ctx, int stream_id, const uint8_t* left, const uint8_t* right,
                   int w, int h, int dmax, int iters, int cell, uint64_t* ticket_out);
 
-/* One pair of a batch submission: the arguments of stereo_submit. */
+/* One pair of a batch submission: the arguments of stereo_submit, and
+ * optional destinations of the results.  out_disparity (w*h fp32 D_f),
+ * out_cost (w*h bytes C_f) and out_mask (w*h bytes of mask bits, as
+ * stereo_result.mask), each NULL or a caller buffer that receives the result
+ * before the request is reported done: the library copies it in the GPU round
+ * that finishes the request, so a poll finds it in place.  Page-locked host
+ * memory and device memory are written by the copy kernel of that round;
+ * pageable host memory is copied with cudaMemcpyAsync (slower).  The buffers
+ * stay the caller's and must stay valid until the request is done. */
 typedef struct {
     int stream_id;
     const uint8_t* left;
     const uint8_t* right;
     int w, h, dmax, iters, cell;
+    float* out_disparity;
+    uint8_t* out_cost;
+    uint8_t* out_mask;
 } stereo_pair;
 
 /* stereo_submit for n pairs at once, for callers serving many cameras: the

@@ -50,7 +50,8 @@ class Result(ctypes.Structure):
 class Pair(ctypes.Structure):
     _fields_ = [("stream_id", ctypes.c_int), ("left", ctypes.c_void_p), ("right", ctypes.c_void_p),
                 ("w", ctypes.c_int), ("h", ctypes.c_int), ("dmax", ctypes.c_int), ("iters", ctypes.c_int),
-                ("cell", ctypes.c_int)]
+                ("cell", ctypes.c_int), ("out_disparity", ctypes.c_void_p), ("out_cost", ctypes.c_void_p),
+                ("out_mask", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -276,12 +277,16 @@ class Context:
         return t.value
 
     def submit_batch(self, pairs):
-        """pairs: (left, right, w, h, dmax, iters, cell[, stream_id]) tuples.  Returns the
-        tickets of the pairs taken (a prefix of the list; raises when none is)."""
+        """pairs: (left, right, w, h, dmax, iters, cell[, stream_id[, outputs]]) tuples, where
+        outputs is (disparity, cost, mask) (each a buffer or None) that receives D_f, C_f and
+        the mask before the request is done.  Returns the tickets of the pairs taken (a
+        prefix of the list; raises when none is)."""
         arr = (Pair * len(pairs))()
         for i, q in enumerate(pairs):
             left, right, w, h, dmax, iters, cell = q[:7]
-            arr[i] = Pair(q[7] if len(q) > 7 else 0, _ptr(left), _ptr(right), w, h, dmax, iters, cell)
+            out = q[8] if len(q) > 8 and q[8] is not None else (None, None, None)
+            arr[i] = Pair(q[7] if len(q) > 7 else 0, _ptr(left), _ptr(right), w, h, dmax, iters, cell,
+                          _ptr(out[0]), _ptr(out[1]), _ptr(out[2]))
         tk = (ctypes.c_uint64 * len(pairs))()
         n = _check(lib().stereo_submit_batch(self.h, arr, len(pairs), tk), "submit_batch")
         return list(tk[:n])

@@ -234,6 +234,10 @@ struct Request {
     double t_submit = 0, t_done = 0, mesh_ms = 0;
     // inputs before admission
     Pinned in_host;           // 2*W*H bytes when the caller gave host pointers
+    // the caller's destinations of D_f, C_f and the mask (optional); direct ones are
+    // written by the copy kernel (device pointers of page-locked or device memory)
+    void* out[3] = {nullptr, nullptr, nullptr};
+    bool out_direct[3] = {false, false, false};
     uint8_t* in_dev = nullptr;  // arena copy when the caller gave device pointers
     // device block
     void* block = nullptr;
@@ -703,16 +707,12 @@ void admit(stereo_ctx* c) {
         r->tune = c->tune;
         carve(*r, c->K);
         const size_t N = (size_t)r->W * r->H;
-        if (r->in_dev) {
-            cudaMemcpyAsync((void*)r->dev.L, r->in_dev, N, cudaMemcpyDeviceToDevice, c->stream);
-            cudaMemcpyAsync((void*)r->dev.R, r->in_dev + N, N, cudaMemcpyDeviceToDevice, c->stream);
+        if (r->in_dev) {  // the submit's copy is read in place (it stays until release)
+            r->dev.L = r->in_dev;
+            r->dev.R = r->in_dev + N;
         } else {
             cudaMemcpyAsync((void*)r->dev.L, r->in_host.p, N, cudaMemcpyHostToDevice, c->stream);
             cudaMemcpyAsync((void*)r->dev.R, (char*)r->in_host.p + N, N, cudaMemcpyHostToDevice, c->stream);
-        }
-        if (r->in_dev) {  // the copy above is ordered before any later use of this memory
-            c->arena.release(r->in_dev);
-            r->in_dev = nullptr;
         }
         r->state = Q_SEED_READY;
         c->active.push_back(r);
@@ -908,6 +908,30 @@ cudaError_t issue_outputs(stereo_ctx* c, Group& seed, Group& iter, cudaStream_t 
     for (Request* r : seed.reqs)  // keypoint slots and their matches, one copy
         if (!r->direct_kp)
             CK(cudaMemcpyAsync(r->st_kp.p, r->dev.kp_uv, (size_t)kFastBins * c->K * 12, cudaMemcpyDeviceToHost, s));
+    // the results of the requests this round finishes, into the caller's buffers: one
+    // gather-copy launch for those the device can write, a copy each for the others
+    CopyList outs{};
+    for (Request* r : iter.reqs) {
+        if (r->resample_now) continue;
+        const size_t N = (size_t)r->W * r->H;
+        const void* src[3] = {r->dev.Df, r->dev.Cf, r->dev.mask};
+        const size_t bytes[3] = {4 * N, N, N};
+        for (int k = 0; k < 3; k++) {
+            if (!r->out[k]) continue;
+            if (!r->out_direct[k]) {
+                CK(cudaMemcpyAsync(r->out[k], src[k], bytes[k], cudaMemcpyDeviceToHost, s));
+                continue;
+            }
+            outs.src[outs.count] = (const uint8_t*)src[k];
+            outs.dst[outs.count] = (uint8_t*)r->out[k];
+            outs.n[outs.count++] = (long long)bytes[k];
+            if (outs.count == kCopyBatch) {
+                CK(launch_copy_list(outs, s));
+                outs.count = 0;
+            }
+        }
+    }
+    if (outs.count > 0) CK(launch_copy_list(outs, s));
     for (Request* r : iter.reqs) {
         if (r->mesh_now) {  // the device mesh's counters after its re-tessellation
             CK(cudaMemcpyAsync(r->st_hdr.p, r->mesh.hdr, sizeof(MeshHdr), cudaMemcpyDeviceToHost, s));
@@ -1796,15 +1820,39 @@ int stereo_submit_batch(stereo_ctx* c, const stereo_pair* pairs, int n, uint64_t
     }
     // where the inputs live: device (or managed) memory and page-locked host memory are
     // copied straight to the arena (one DMA each), pageable memory through pinned staging
-    std::vector<char> kind(n);  // 'd' device, 'p' page-locked, 'h' pageable
-    for (int i = 0; i < n; i++) {
-        cudaPointerAttributes at{}, at_r{};
-        const bool known = cudaPointerGetAttributes(&at, pairs[i].left) == cudaSuccess &&
-                           cudaPointerGetAttributes(&at_r, pairs[i].right) == cudaSuccess;
+    // page-locked memory is read by the same gather-copy kernel through its device
+    // pointers (over the CPU-GPU link), like device memory
+    std::vector<char> kind(n);  // 'd' device or page-locked (device-readable), 'h' pageable
+    std::vector<const uint8_t*> src_l(n), src_r(n);
+    auto dev_view = [](const void* p, const void** dp) {  // a pointer the device can use, or none
+        cudaPointerAttributes at{};
+        const bool known = cudaPointerGetAttributes(&at, p) == cudaSuccess;
         cudaGetLastError();
-        const bool dev_in = known && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
-        const bool pinned_in = known && !dev_in && at.type == cudaMemoryTypeHost && at_r.type == cudaMemoryTypeHost;
-        kind[i] = dev_in ? 'd' : pinned_in ? 'p' : 'h';
+        if (!known) return false;
+        if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+            *dp = p;
+            return true;
+        }
+        if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+            *dp = at.devicePointer;
+            return true;
+        }
+        return false;
+    };
+    for (int i = 0; i < n; i++) {
+        const void *dl = nullptr, *dr = nullptr;
+        const bool direct = dev_view(pairs[i].left, &dl) && dev_view(pairs[i].right, &dr);
+        kind[i] = direct ? 'd' : 'h';
+        src_l[i] = (const uint8_t*)dl;
+        src_r[i] = (const uint8_t*)dr;
+        void* outs[3] = {pairs[i].out_disparity, pairs[i].out_cost, pairs[i].out_mask};
+        for (int k = 0; k < 3; k++) {
+            Request* r = rs[i];
+            if (!outs[k]) continue;
+            const void* dp = nullptr;
+            r->out_direct[k] = dev_view(outs[k], &dp);
+            r->out[k] = r->out_direct[k] ? const_cast<void*>(dp) : outs[k];
+        }
     }
     int take = 0;
     {
@@ -1813,7 +1861,7 @@ int stereo_submit_batch(stereo_ctx* c, const stereo_pair* pairs, int n, uint64_t
         for (; take < n; take++) {
             if (queued >= c->cfg.max_queue && (int)c->active.size() >= c->cfg.max_slots) break;
             Request* r = rs[take];
-            if (kind[take] != 'h') {
+            if (kind[take] == 'd') {
                 r->in_dev = (uint8_t*)c->arena.alloc(2 * (size_t)r->W * r->H);
                 if (!r->in_dev) break;
             }
@@ -1830,7 +1878,7 @@ int stereo_submit_batch(stereo_ctx* c, const stereo_pair* pairs, int n, uint64_t
         const size_t N = (size_t)r->W * r->H;
         if (kind[i] == 'd') {
             for (int k = 0; k < 2; k++) {
-                cl.src[cl.count] = k ? pairs[i].right : pairs[i].left;
+                cl.src[cl.count] = k ? src_r[i] : src_l[i];
                 cl.dst[cl.count] = r->in_dev + k * N;
                 cl.n[cl.count++] = (long long)N;
             }
@@ -1838,10 +1886,6 @@ int stereo_submit_batch(stereo_ctx* c, const stereo_pair* pairs, int n, uint64_t
                 if (launch_copy_list(cl, c->copy_stream) != cudaSuccess) return drop_all(STEREO_E_CUDA);
                 cl.count = 0;
             }
-            copied = true;
-        } else if (kind[i] == 'p') {
-            cudaMemcpyAsync(r->in_dev, pairs[i].left, N, cudaMemcpyHostToDevice, c->copy_stream);
-            cudaMemcpyAsync(r->in_dev + N, pairs[i].right, N, cudaMemcpyHostToDevice, c->copy_stream);
             copied = true;
         } else {
             if (!r->in_host.ensure(2 * N)) return drop_all(STEREO_E_NOMEM);

@@ -443,6 +443,49 @@ def test_pinned_host_input_pointers(oracle_mod):
     _compare_run(oracle_mod, p, got)
 
 
+def test_result_destinations_at_submit(oracle_mod):
+    """Results written to the caller's buffers named at submit, in the round that
+    finishes each request: page-locked host tensors, pageable numpy arrays, device
+    tensors and a partial set (D_f only), in one batch with device-mesh and
+    mixed sizes; each equals the request's own device result.  Page-locked inputs
+    are read by the copy kernel and may be reused at once."""
+    pairs = scenes.config_pairs("vga_polygons", n=2) + [scenes.make_pair("driving", 400, 150, 611, 96, 3, 8, n_box=10)]
+    outs = []
+    for i, p in enumerate(pairs):
+        H, W = p.left.shape
+        if i == 0:
+            o = (torch.full((H, W), -7.0).pin_memory(), torch.zeros((H, W), dtype=torch.uint8).pin_memory(),
+                 torch.zeros((H, W), dtype=torch.uint8).pin_memory())
+        elif i == 1:
+            o = (np.full((H, W), -7.0, np.float32), np.zeros((H, W), np.uint8), np.zeros((H, W), np.uint8))
+        else:
+            o = (torch.full((H, W), -7.0, device=DEV), None, None)
+        outs.append(o)
+    ins = [(torch.from_numpy(p.left.copy()).pin_memory(), torch.from_numpy(p.right.copy()).pin_memory()) for p in pairs]
+    with S.Context(mem_budget_bytes=1 << 30, max_slots=3, host_threads=2, **PRM) as ctx:
+        tk = ctx.submit_batch([(l, r, p.left.shape[1], p.left.shape[0], p.dmax, p.iters, p.cell, 0, o)
+                               for (l, r), p, o in zip(ins, pairs, outs)])
+        assert len(tk) == 3
+        for l, r in ins:
+            l.zero_()
+            r.zero_()
+        got = []
+        for t in tk:
+            got.append(ctx.result_tensors(ctx.poll(t)))
+            ctx.release(t)
+    torch.cuda.synchronize()
+
+    def host(x):
+        return x.cpu().numpy() if torch.is_tensor(x) else x
+
+    for o, g in zip(outs, got):
+        assert np.array_equal(host(o[0]).view(np.uint32), g["D_f"].cpu().numpy().view(np.uint32))
+        if o[1] is not None:
+            assert np.array_equal(host(o[1]), g["C_f"].cpu().numpy())
+            assert np.array_equal(host(o[2]), g["mask"].cpu().numpy())
+    _compare_run(oracle_mod, pairs[0], got[0])
+
+
 def test_budget_errors():
     with S.Context(mem_budget_bytes=1 << 22, **PRM) as ctx:
         img = np.zeros((480, 640), np.uint8)
