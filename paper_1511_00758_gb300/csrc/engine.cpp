@@ -175,6 +175,30 @@ private:
     size_t idle_ = 0;
 };
 
+// Support-set buffers (the trace of a result) of released requests, kept for
+// the next ones: a request's trace is a few hundred KB, written once.
+class TracePool {
+public:
+    static constexpr size_t kKeep = 256;
+    std::vector<float> get() {
+        std::lock_guard<std::mutex> g(mu_);
+        if (free_.empty()) return {};
+        std::vector<float> v = std::move(free_.back());
+        free_.pop_back();
+        v.clear();
+        return v;
+    }
+    void put(std::vector<float>&& v) {
+        if (v.capacity() == 0) return;
+        std::lock_guard<std::mutex> g(mu_);
+        if (free_.size() < kKeep) free_.push_back(std::move(v));
+    }
+
+private:
+    std::mutex mu_;
+    std::vector<std::vector<float>> free_;
+};
+
 struct Pinned {
     void* p = nullptr;
     size_t cap = 0;
@@ -252,6 +276,7 @@ struct Request {
     std::vector<SupportPoint> S;
     std::vector<int32_t> n_support, n_tri;
     std::vector<float> trace;
+    TracePool* tpool = nullptr;  // where the trace buffer comes from and goes back to
     int T = 0;
     int raster_items = 0, n_small = 0, n_hull = 0, n_batch = 0;
     Pinned st_tri;            // one mesh, laid out as tri_stage_bytes() describes
@@ -382,6 +407,7 @@ private:
 
 struct stereo_ctx {
     PinnedPool pinned;  // first member, destroyed last (after every request's buffers came back)
+    TracePool traces;
     stereo_config cfg{};
     Params prm{};
     int K = 4;
@@ -533,6 +559,7 @@ int mesh_step(Request& r) {
     r.n_hull = n_hull;
     r.n_support.push_back(n);
     r.n_tri.push_back(T);
+    if (r.trace.capacity() == 0 && r.tpool) r.trace = r.tpool->get();
     r.trace.reserve(r.trace.size() + 3 * r.S.size());
     for (const auto& s : r.S) {
         r.trace.push_back((float)s.u);
@@ -637,27 +664,34 @@ int host_after_iter(Request& r) {
 // points that joined at pass it or before, in the same order.
 void build_trace(Request& r) {
     const int4* v = r.st_vcanon.as<int4>();
-    const int n = r.dev_n;
-    std::vector<int32_t> joined(r.iters + 1, 0);
-    for (int i = 0; i < n; i++) joined[std::min(std::max(v[i].w, 1), r.iters)]++;
-    r.n_support.assign(r.iters, 0);
+    const int n = r.dev_n, iters = r.iters;
+    auto pass_of = [&](int i) { return std::min(std::max(v[i].w, 1), iters); };
+    std::vector<int32_t> joined(iters + 1, 0);
+    for (int i = 0; i < n; i++) joined[pass_of(i)]++;
+    r.n_support.assign(iters, 0);
+    std::vector<size_t> at(iters + 1, 0);  // where S_it's next point goes
     size_t total = 0;
-    for (int it = 1, acc = 0; it <= r.iters; it++) {
+    for (int it = 1, acc = 0; it <= iters; it++) {
         acc += joined[it];
         r.n_support[it - 1] = acc;
+        at[it] = 3 * total;
         total += (size_t)acc;
     }
-    r.trace.clear();
-    r.trace.reserve(3 * total);
-    for (int it = 1; it <= r.iters; it++)
-        for (int i = 0; i < n; i++)
-            if (v[i].w <= it) {
-                r.trace.push_back((float)v[i].x);
-                r.trace.push_back((float)v[i].y);
-                float d;
-                std::memcpy(&d, &v[i].z, 4);
-                r.trace.push_back(d);
-            }
+    if (r.trace.capacity() == 0 && r.tpool) r.trace = r.tpool->get();
+    r.trace.resize(3 * total);
+    float* out = r.trace.data();
+    for (int i = 0; i < n; i++) {  // one pass: the point goes to every S_it it belongs to
+        float d;
+        std::memcpy(&d, &v[i].z, 4);
+        const float x = (float)v[i].x, y = (float)v[i].y;
+        for (int it = pass_of(i); it <= iters; it++) {
+            float* o = out + at[it];
+            o[0] = x;
+            o[1] = y;
+            o[2] = d;
+            at[it] += 3;
+        }
+    }
 }
 
 void finish(stereo_ctx* c, Request& r, int status) {
@@ -1806,6 +1840,7 @@ int stereo_submit_batch(stereo_ctx* c, const stereo_pair* pairs, int n, uint64_t
         Request* r = new Request();
         r->in_host.pool = r->st_tri.pool = r->st_kp.pool = r->st_cells.pool = r->st_hdr.pool = r->st_vcanon.pool =
             &c->pinned;
+        r->tpool = &c->traces;
         r->pool = &c->pool;
         r->stream_id = q.stream_id;
         r->W = q.w;
@@ -1991,6 +2026,7 @@ int stereo_release(stereo_ctx* c, uint64_t ticket) {
     r->st_cells.free();
     r->st_hdr.free();
     r->st_vcanon.free();
+    c->traces.put(std::move(r->trace));
     delete r;
     c->cv_sched.notify_all();
     return STEREO_OK;

@@ -1790,7 +1790,9 @@ cudaError_t launch_validate_bulk(const PairBatch& b, const Params& prm, cudaStre
     return cudaGetLastError();
 }
 // Gather copy: kCopyParts blocks per entry, each a contiguous part of it, in
-// 16-byte words when both ends are 16-byte aligned (bytes otherwise).
+// 16-byte words when both ends are 16-byte aligned (bytes otherwise).  A source
+// may be page-locked host memory that the caller rewrites between calls, so the
+// loads fetch again rather than trust a cached line (ld.global.cv).
 constexpr int kCopyParts = 8;
 __global__ void __launch_bounds__(256) k_copy_list(const __grid_constant__ CopyList L) {
     const int e = blockIdx.x / kCopyParts, part = blockIdx.x % kCopyParts;
@@ -1803,10 +1805,10 @@ __global__ void __launch_bounds__(256) k_copy_list(const __grid_constant__ CopyL
     if ((((uintptr_t)src | (uintptr_t)dst) & 15) == 0) {
         const long long w0 = lo / 16, w1 = hi / 16;
         for (long long w = w0 + threadIdx.x; w < w1; w += blockDim.x)
-            reinterpret_cast<uint4*>(dst)[w] = __ldg(reinterpret_cast<const uint4*>(src) + w);
-        for (long long i = max(lo, w1 * 16) + threadIdx.x; i < hi; i += blockDim.x) dst[i] = src[i];
+            reinterpret_cast<uint4*>(dst)[w] = __ldcv(reinterpret_cast<const uint4*>(src) + w);
+        for (long long i = max(lo, w1 * 16) + threadIdx.x; i < hi; i += blockDim.x) dst[i] = __ldcv(src + i);
     } else {
-        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) dst[i] = src[i];
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) dst[i] = __ldcv(src + i);
     }
 }
 
