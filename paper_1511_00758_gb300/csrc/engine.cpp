@@ -298,7 +298,8 @@ struct Request {
     MeshDev mesh{};             // its arrays (host copy of the descriptor)
     size_t seed_off = 0;        // offset of the seed mesh arrays in the staging blob (pass 1)
     Pinned st_hdr;              // the mesh header after each device pass
-    Pinned st_vcanon;           // the final support set in canonical order (u, v, d bits, pass)
+    Pinned st_trace;            // device mesh: S_1 .. S_iters as (u, v, d) floats, written by the last pass
+    bool dev_trace = false;     // st_trace holds the trace (the device wrote it)
     int dev_n = 0;              // vertices after the last device pass
     bool mesh_now = false;      // this round runs the device mesh pass for this request
     bool raster_dev = false;    // this round rasters the device mesh
@@ -659,41 +660,6 @@ int host_after_iter(Request& r) {
     return mesh_step(r);
 }
 
-// The support sets S_1 .. S_iters of a device-mesh request from the final
-// vertex list (canonical order, each with the pass it joined): S_it is the
-// points that joined at pass it or before, in the same order.
-void build_trace(Request& r) {
-    const int4* v = r.st_vcanon.as<int4>();
-    const int n = r.dev_n, iters = r.iters;
-    auto pass_of = [&](int i) { return std::min(std::max(v[i].w, 1), iters); };
-    std::vector<int32_t> joined(iters + 1, 0);
-    for (int i = 0; i < n; i++) joined[pass_of(i)]++;
-    r.n_support.assign(iters, 0);
-    std::vector<size_t> at(iters + 1, 0);  // where S_it's next point goes
-    size_t total = 0;
-    for (int it = 1, acc = 0; it <= iters; it++) {
-        acc += joined[it];
-        r.n_support[it - 1] = acc;
-        at[it] = 3 * total;
-        total += (size_t)acc;
-    }
-    if (r.trace.capacity() == 0 && r.tpool) r.trace = r.tpool->get();
-    r.trace.resize(3 * total);
-    float* out = r.trace.data();
-    for (int i = 0; i < n; i++) {  // one pass: the point goes to every S_it it belongs to
-        float d;
-        std::memcpy(&d, &v[i].z, 4);
-        const float x = (float)v[i].x, y = (float)v[i].y;
-        for (int it = pass_of(i); it <= iters; it++) {
-            float* o = out + at[it];
-            o[0] = x;
-            o[1] = y;
-            o[2] = d;
-            at[it] += 3;
-        }
-    }
-}
-
 void finish(stereo_ctx* c, Request& r, int status) {
     r.status = status;
     r.state = status == STEREO_OK ? Q_DONE : Q_FAILED;
@@ -971,10 +937,6 @@ cudaError_t issue_outputs(stereo_ctx* c, Group& seed, Group& iter, cudaStream_t 
             CK(cudaMemcpyAsync(r->st_hdr.p, r->mesh.hdr, sizeof(MeshHdr), cudaMemcpyDeviceToHost, s));
             continue;
         }
-        if (r->dev_mesh && !r->resample_now && r->dev_n > 0) {  // last pass: the support set, canonical order
-            CK(cudaMemcpyAsync(r->st_vcanon.p, r->mesh.vcanon, 16 * (size_t)r->dev_n, cudaMemcpyDeviceToHost, s));
-            continue;
-        }
         if (!r->resample_now) continue;
         // the four cell arrays of this pass, one copy, for the host mesh step
         const size_t nc = (size_t)r->dev.Wc * r->dev.Hc;
@@ -1146,10 +1108,26 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
                     m.seed_T = r->T;
                 }
                 if (!r->st_hdr.ensure(sizeof(MeshHdr))) return cudaErrorMemoryAllocation;
+                m.trace = nullptr;
+                m.trace_cap = 0;
+                m.iters = r->iters;
+                if (m.canonical) {  // the pass writes the trace into page-locked memory: room for
+                    // the known S_1 .. S_it and the largest S_iters this pass can make
+                    size_t known = 0;
+                    for (int k : r->n_support) known += (size_t)k;
+                    const size_t grow = std::min((size_t)r->W * r->H, (size_t)r->n_support.back() + 2 * (size_t)m.ncells);
+                    const size_t floats = 3 * (known + grow);
+                    void* hp = nullptr;
+                    if (!r->st_trace.ensure(4 * floats)) return cudaErrorMemoryAllocation;
+                    if (cudaHostGetDevicePointer(&hp, r->st_trace.p, 0) != cudaSuccess || !hp) {
+                        cudaGetLastError();
+                        return cudaErrorMemoryAllocation;
+                    }
+                    m.trace = (float*)hp;
+                    m.trace_cap = (int)std::min(floats, (size_t)INT32_MAX);
+                }
             }
         }
-        if (r->dev_mesh && !r->resample_now && r->dev_n > 0 && !r->st_vcanon.ensure(16 * (size_t)r->dev_n))
-            return cudaErrorMemoryAllocation;
     }
     count_mesh(seed);
     count_mesh(iter);
@@ -1319,7 +1297,7 @@ void scheduler(stereo_ctx* c) {
             c->cv_done.notify_all();
             continue;
         }
-        std::vector<Request*> host, traces;
+        std::vector<Request*> host;
         const long long cohort = c->seed_rounds++;
         for (Request* r : seed.reqs) {
             r->cohort = cohort;
@@ -1349,6 +1327,8 @@ void scheduler(stereo_ctx* c) {
                 c->stats.mesh_edge_points += h.edge_ins;
                 c->stats.mesh_points += h.n - (r->dev_n > 0 ? r->dev_n : r->n_support.back());
                 r->dev_n = h.n;
+                r->n_support.push_back(h.n);  // S_{it+1}
+                r->dev_trace = r->it + 1 == r->iters;  // the last pass wrote S_1 .. S_iters
                 r->T = h.T;
                 r->n_tri.push_back(h.T);
                 r->it += 1;
@@ -1357,23 +1337,10 @@ void scheduler(stereo_ctx* c) {
                 continue;
             }
             if (!r->resample_now) {
-                if (r->dev_mesh && r->dev_n > 0) traces.push_back(r);  // support sets from the device's list
-                else finish(c, *r, STEREO_OK);
+                finish(c, *r, STEREO_OK);
                 continue;
             }
             host.push_back(r);
-        }
-        for (Request* r : traces) {
-            r->state = Q_HOST;
-            c->host_busy++;
-            c->pool.push([c, r] {
-                build_trace(*r);
-                std::lock_guard<std::mutex> g2(c->mu);
-                c->host_busy--;
-                finish(c, *r, STEREO_OK);
-                c->cv_sched.notify_all();
-                c->cv_done.notify_all();
-            });
         }
         for (Request* r : host) {
             r->state = Q_HOST;
@@ -1838,7 +1805,7 @@ int stereo_submit_batch(stereo_ctx* c, const stereo_pair* pairs, int n, uint64_t
     for (int i = 0; i < n; i++) {
         const stereo_pair& q = pairs[i];
         Request* r = new Request();
-        r->in_host.pool = r->st_tri.pool = r->st_kp.pool = r->st_cells.pool = r->st_hdr.pool = r->st_vcanon.pool =
+        r->in_host.pool = r->st_tri.pool = r->st_kp.pool = r->st_cells.pool = r->st_hdr.pool = r->st_trace.pool =
             &c->pinned;
         r->tpool = &c->traces;
         r->pool = &c->pool;
@@ -1982,7 +1949,7 @@ int stereo_poll(stereo_ctx* c, uint64_t ticket, stereo_result* out, int timeout_
         out->planeidx = r->pidx_buf;
         out->n_support = r->n_support.data();
         out->n_tri = r->n_tri.data();
-        out->support = r->trace.data();
+        out->support = r->dev_trace ? r->st_trace.as<float>() : r->trace.data();
     }
     return r->status;
 }
@@ -2025,7 +1992,7 @@ int stereo_release(stereo_ctx* c, uint64_t ticket) {
     r->st_kp.free();
     r->st_cells.free();
     r->st_hdr.free();
-    r->st_vcanon.free();
+    r->st_trace.free();
     c->traces.put(std::move(r->trace));
     delete r;
     c->cv_sched.notify_all();
@@ -2067,7 +2034,7 @@ void stereo_destroy(stereo_ctx* c) {
         r->st_kp.free();
         r->st_cells.free();
         r->st_hdr.free();
-        r->st_vcanon.free();
+        r->st_trace.free();
         delete r;
     }
     c->reqs.clear();

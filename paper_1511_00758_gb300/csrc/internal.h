@@ -149,6 +149,7 @@ bool valid_size(int w, int h);
 // planes and raster lists are built for the next pass, all on the GPU.
 constexpr int kMeshBatch = 64;      // pairs per mesh launch
 constexpr int kMeshClasses = 7;     // small-triangle box width classes: 1, 2, <=4, <=8, <=16, <=32, wider
+constexpr int kMeshMaxIters = 16;   // iterations a request may take (the trace's support sets)
 
 // Counters of one pair's device mesh (device memory).
 struct MeshHdr {
@@ -167,6 +168,8 @@ struct MeshHdr {
     int total_new, inserted;         // points of the pass to insert, and those inserted (or given up)
     int step;                        // rounds (insertion and flip) taken so far in this pass
     int fdone;                       // the flip rounds ended (a round without flips)
+    int s_count[kMeshMaxIters + 1];  // |S_it| of the trace (canonical pass)
+    int trace_floats;                // floats written to the trace
 };
 
 // A triangle of the device mesh, one 32-byte sector: a = the packed positions
@@ -204,6 +207,8 @@ struct MeshDev {
     int4* smap;               // split / flip record: (stamp, new ref of old edge 0, 1, 2)
     int* gcnt;                // triangles per smallest canonical vertex, then their prefix [n_cap + 1]
     int* tperm;               // canonical triangle order: position -> slot
+    uint32_t* tpass;          // canonical pass: the pass each vertex joined, by rank
+    uint32_t* tpos;           // and its position within S_it (scan scratch)
     int4* plist;              // two worklists (2 * p_cap) of the points still to insert, one record each:
                               // (vertex slot, current triangle, edge code, packed position); the
                               // triangle is -2 - t while the round that inserted it into t links its
@@ -238,6 +243,11 @@ struct MeshDev {
     int seed_n, seed_T;       // > 0: take the seed mesh over first
     int pass;                 // iteration the new points join
     int canonical;            // the next pass is the last: canonical triangle order and vertex ranks
+    // canonical pass: the support sets S_1 .. S_iters, each in canonical order as (u, v, d) floats,
+    // one after the other, written to trace (the request's page-locked buffer, trace_cap floats)
+    float* trace;
+    int trace_cap;
+    int iters;
     int small_area, cols;     // raster work shapes
 };
 

@@ -26,10 +26,12 @@ static int validate_items(WorkKind k, const PairDev& p);
 
 constexpr int kTileW = 32;     // census / FAST score tile: 32 columns (a warp's lanes)
 constexpr int kSeedRows = 32;  // by 32 rows
+constexpr int kScanCols = 128;  // census: a warp's strip of columns
+constexpr int kScanRows = 14;   // and rows per strip item (a multiple of the 7-row ring)
 
 int work_items(WorkKind k, const PairDev& p) {
     switch (k) {
-        case WK_CENSUS:
+        case WK_CENSUS: return cdiv(p.W, kScanCols) * cdiv(p.H, kScanRows);
         case WK_FAST_SCORE: return cdiv(p.W, kTileW) * cdiv(p.H, kSeedRows);
         case WK_VALIDATE:
         case WK_VALIDATE_UNIT:
@@ -90,49 +92,96 @@ static int grid_for(int total, int per_sm) {
 }
 
 // ---------------------------------------------------------------- census + Omega_I
-// Census 5x5 (Sec. III-C) of L and R and the Omega_I bit map of L.  One
-// 32x32 tile per block of 256 threads; lane l of warp w computes column l of
-// rows w, w + 8, w + 16, w + 24.  Rows are staged with a 2-pixel halo in
-// shared memory (borders clamped), loaded by row and column loops without
-// divisions.
+// Census 5x5 (Sec. III-C) of L and R and the Omega_I bit map of L.  One warp per
+// strip of 128 columns x kScanRows rows: lane l owns the four columns
+// u0 + 4l .. u0 + 4l + 3 and slides down the strip keeping the rows it needs in
+// registers, each row as three words (the lane's own four bytes and the four on
+// either side, taken from the neighbouring lanes by shuffles, the strip's edge
+// lanes loading theirs).  A row is read once per strip, as aligned words with a
+// funnel shift for the row's misalignment; only the first and last rows of an
+// image (where the aligned span would leave the buffer) are read byte by byte.
+// Bytes outside the image read as 0: they are seen only by border pixels, whose
+// outputs are fixed (code 0, not in Omega_I).
 
-template <int HALO>
-__device__ __forceinline__ void stage_tile(uint8_t (*s)[kTileW + 2 * HALO], const uint8_t* __restrict__ img, int W,
-                                           int H, int u0, int v0) {
-    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
-    for (int r = ly; r < kSeedRows + 2 * HALO; r += 8) {
-        const size_t row = (size_t)min(max(v0 + r - HALO, 0), H - 1) * W;
-        s[r][lx] = __ldg(img + row + min(max(u0 + lx - HALO, 0), W - 1));
-        if (lx < 2 * HALO) s[r][kTileW + lx] = __ldg(img + row + min(max(u0 + kTileW + lx - HALO, 0), W - 1));
-    }
+
+struct Row3 {
+    uint32_t l, c, r;  // bytes u-4 .. u-1, u .. u+3, u+4 .. u+7 of the lane's columns u .. u+3
+};
+
+__device__ __forceinline__ uint32_t byte_at(const uint8_t* img, size_t n, long long i) {
+    return i >= 0 && (size_t)i < n ? (uint32_t)__ldg(img + i) : 0u;
 }
 
-// Census codes of four adjacent pixels at once.  Staged row r + 2 holds
-// their row and staged columns c + 2 .. c + 5 the pixels (c a multiple of 4,
-// so each staged row is read as two aligned words).  A neighbour's four
-// bytes come from a funnel shift of the two words, and the four comparisons
-// N < C are done at once on bytes: with H = 0x80 in every byte,
-// d = (N | H) - (C & ~H) never borrows across bytes and its top bit is set
-// when the low seven bits of N are >= those of C, so the top bit of
-// (~N & C) | (~(N ^ C) & ~d) is N < C.  Neighbour k (raster order of the 5x5
-// window without its centre) lands in bit k of each pixel's code.
-__device__ __forceinline__ void census4(const uint8_t (*s)[kTileW + 4], int r, int c, uint32_t out[4]) {
-    uint32_t w0[5], w1[5];
+// A row's loads in flight: the three aligned words of the lane (fast) or the
+// finished bytes (edge rows, read byte by byte).  issue_row() starts them,
+// finish_row() (a row later, so the loads overlap a row of work) makes the Row3.
+struct RowLoad {
+    uint32_t a, b, c;
+    int sh;     // the row's misalignment in bits; -1: a, b, c are already l, c, r
+};
+
+// Row v of img (W x H) around the lane's columns u0 + 4 lane ..; v and u0 warp-uniform.
+__device__ __forceinline__ RowLoad issue_row(const uint8_t* img, int W, int H, int v, int u0, int lane) {
+    RowLoad x{0u, 0u, 0u, -1};
+    if (v < 0 || v >= H) return x;
+    const size_t n = (size_t)W * H;
+    const long long base = (long long)v * W + u0;  // byte offset of the strip's first column
+    const uintptr_t a = (uintptr_t)(img + base), a0 = a & ~(uintptr_t)3;
+    if (a0 >= (uintptr_t)img + 4 && a0 + 4 * 34 <= (uintptr_t)img + n) {  // words -1 .. 33 all inside
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(a0);
+        x.a = __ldg(w + lane);
+        x.b = __ldg(w + lane + 1);
+        x.c = __ldg(w + (lane == 0 ? -1 : lane + 2));
+        x.sh = (int)(a & 3) * 8;
+    } else {
+        const long long o = base + 4 * lane;
 #pragma unroll
-    for (int dy = 0; dy < 5; dy++) {
-        w0[dy] = *reinterpret_cast<const uint32_t*>(&s[r + dy][c]);
-        w1[dy] = *reinterpret_cast<const uint32_t*>(&s[r + dy][c + 4]);
+        for (int j = 0; j < 4; j++) {
+            x.a |= byte_at(img, n, o - 4 + j) << (8 * j);
+            x.b |= byte_at(img, n, o + j) << (8 * j);
+            x.c |= byte_at(img, n, o + 4 + j) << (8 * j);
+        }
     }
-    const uint32_t C = __funnelshift_r(w0[2], w1[2], 16);
+    return x;
+}
+
+__device__ __forceinline__ Row3 finish_row(const RowLoad& x, int lane) {
+    if (x.sh < 0) return Row3{x.a, x.b, x.c};  // warp-uniform
+    Row3 y;
+    y.c = __funnelshift_r(x.a, x.b, x.sh);
+    const uint32_t edge = lane == 0 ? __funnelshift_r(x.c, x.a, x.sh) : __funnelshift_r(x.b, x.c, x.sh);
+    const uint32_t up = __shfl_up_sync(0xffffffffu, y.c, 1), dn = __shfl_down_sync(0xffffffffu, y.c, 1);
+    y.l = lane == 0 ? edge : up;
+    y.r = lane == 31 ? edge : dn;
+    return y;
+}
+
+// The four bytes at column offset dx (-3 .. 3) from the lane's columns.
+__device__ __forceinline__ uint32_t shifted(const Row3& x, int dx) {
+    return dx == -3 ? __funnelshift_r(x.l, x.c, 8) : dx == -2 ? __funnelshift_r(x.l, x.c, 16)
+         : dx == -1 ? __funnelshift_r(x.l, x.c, 24) : dx == 0 ? x.c
+         : dx == 1  ? __funnelshift_r(x.c, x.r, 8) : dx == 2 ? __funnelshift_r(x.c, x.r, 16)
+                    : __funnelshift_r(x.c, x.r, 24);
+}
+
+// Census codes of the lane's four pixels from rows v-2 .. v+2 (ring slots s0 ..
+// s0+4 mod 7).  A neighbour's four comparisons N < C are done at once on bytes:
+// with H = 0x80 in every byte, d = (N | H) - (C & ~H) never borrows across bytes
+// and its top bit is set when the low seven bits of N are >= those of C, so the
+// top bit of (~N & C) | (~(N ^ C) & ~d) is N < C.  Neighbour k (raster order of
+// the 5x5 window without its centre) lands in bit k of each pixel's code.
+template <int S0>
+__device__ __forceinline__ void census4(const Row3 (&ring)[7], uint32_t out[4]) {
+    const uint32_t C = ring[(S0 + 2) % 7].c;
     const uint32_t Cl = C & 0x7F7F7F7Fu;
     uint32_t acc[3] = {0u, 0u, 0u};
     int k = 0;
 #pragma unroll
     for (int dy = 0; dy < 5; dy++) {
 #pragma unroll
-        for (int dx = 0; dx < 5; dx++) {
-            if (dy == 2 && dx == 2) continue;
-            const uint32_t N = dx == 0 ? w0[dy] : dx == 4 ? w1[dy] : __funnelshift_r(w0[dy], w1[dy], 8 * dx);
+        for (int dx = -2; dx <= 2; dx++) {
+            if (dy == 2 && dx == 0) continue;
+            const uint32_t N = shifted(ring[(S0 + dy) % 7], dx);
             const uint32_t d = (N | 0x80808080u) - Cl;
             const uint32_t lt = (~N & C) | (~(N ^ C) & ~d);  // top bit of each byte: N < C
             const int i = k & 7;
@@ -147,39 +196,34 @@ __device__ __forceinline__ void census4(const uint8_t (*s)[kTileW + 4], int r, i
     }
 }
 
-// One thread per four adjacent pixels of a tile row (8 threads a row, 32 rows).
-__device__ __forceinline__ void census_body(const PairDev& P, int local, const Params& prm) {
-    __shared__ __align__(16) uint8_t sL[kSeedRows + 4][kTileW + 4];
-    __shared__ __align__(16) uint8_t sR[kSeedRows + 4][kTileW + 4];
+// One output row v of the strip: ring slot K + 3 holds row v (slots mod 7).
+template <int K>
+__device__ __forceinline__ void census_row(const PairDev& P, const Params& prm, const Row3 (&rl)[7],
+                                           const Row3 (&rr)[7], int v, int u0, int lane) {
     const int W = P.W, H = P.H;
-    const int tx_n = (W + kTileW - 1) / kTileW;
-    const int u0 = (local % tx_n) * kTileW, v0 = (local / tx_n) * kSeedRows;
-    stage_tile<2>(sL, P.L, W, H, u0, v0);
-    if (P.cR) stage_tile<2>(sR, P.R, W, H, u0, v0);
-    __syncthreads();
-    const int ly = threadIdx.x >> 3, c = (threadIdx.x & 7) * 4;
-    const int v = v0 + ly, ub = u0 + c;
-    const bool row_in = v >= 2 && v < H - 2;
+    const int ub = u0 + 4 * lane;
     uint32_t cl[4], cr[4] = {0u, 0u, 0u, 0u};
-    census4(sL, ly, c, cl);
-    if (P.cR) census4(sR, ly, c, cr);
-    // Omega_I: |I(u+1) - I(u-1)| + |I(v+1) - I(v-1)| >= t_grad, from the staged bytes
+    census4<(K + 1) % 7>(rl, cl);
+    if (P.cR) census4<(K + 1) % 7>(rr, cr);
+    // Omega_I: |I(u+1) - I(u-1)| + |I(v+1) - I(v-1)| >= t_grad
+    const uint32_t E = shifted(rl[(K + 3) % 7], 1), Wd = shifted(rl[(K + 3) % 7], -1);
+    const uint32_t Sd = rl[(K + 4) % 7].c, Nd = rl[(K + 2) % 7].c;
+    const bool row_in = v >= 2 && v < H - 2;
     unsigned om = 0;
 #pragma unroll
     for (int j = 0; j < 4; j++) {
         const int u = ub + j;
-        const bool interior = row_in && u >= 2 && u < W - 2;
-        if (!interior) {
+        if (!row_in || u < 2 || u >= W - 2) {
             cl[j] = 0u;
             cr[j] = 0u;
         } else {
-            const int gx = abs((int)sL[ly + 2][c + j + 3] - (int)sL[ly + 2][c + j + 1]);
-            const int gy = abs((int)sL[ly + 3][c + j + 2] - (int)sL[ly + 1][c + j + 2]);
+            const int gx = abs((int)((E >> (8 * j)) & 0xFFu) - (int)((Wd >> (8 * j)) & 0xFFu));
+            const int gy = abs((int)((Sd >> (8 * j)) & 0xFFu) - (int)((Nd >> (8 * j)) & 0xFFu));
             om |= (unsigned)(gx + gy >= prm.t_grad) << j;
         }
     }
-    if (v < H) {
-        const size_t p = (size_t)v * W + ub;
+    const size_t p = (size_t)v * W + ub;
+    if (ub < W) {
         const uintptr_t al = (P.cL ? (uintptr_t)(P.cL + p) : 0) | (P.cR ? (uintptr_t)(P.cR + p) : 0);
         if (ub + 3 < W && (al & 15) == 0) {
             if (P.cL) *reinterpret_cast<uint4*>(P.cL + p) = make_uint4(cl[0], cl[1], cl[2], cl[3]);
@@ -193,21 +237,67 @@ __device__ __forceinline__ void census_body(const PairDev& P, int local, const P
                 }
         }
     }
-    // the row's 32 bits from its 8 threads (adjacent lanes)
-    unsigned bits = om << c;
+    // each omega word: 32 columns from eight adjacent lanes
+    unsigned bits = om << (4 * (lane & 7));
     bits |= __shfl_xor_sync(0xffffffffu, bits, 1);
     bits |= __shfl_xor_sync(0xffffffffu, bits, 2);
     bits |= __shfl_xor_sync(0xffffffffu, bits, 4);
-    const int words = (W + 31) >> 5;
-    if ((threadIdx.x & 7) == 0 && v < H && P.omega) P.omega[(size_t)v * words + (u0 >> 5)] = bits;
-    __syncthreads();
+    const int words = (W + 31) >> 5, wi = (u0 >> 5) + (lane >> 3);
+    if ((lane & 7) == 0 && wi < words && P.omega) P.omega[(size_t)v * words + wi] = bits;
 }
 
 __global__ void __launch_bounds__(256) k_census(PairBatch b, Params prm) {
-#define BODY(P, l) census_body(P, l, prm)
-    FOR_EACH_ITEM(b, BODY)
-#undef BODY
+    const int lane = threadIdx.x & 31;
+    for (int item = blockIdx.x * 8 + (threadIdx.x >> 5); item < b.total; item += gridDim.x * 8) {
+        const PairDev* Pp = &b.one;
+        int local = item;
+        if (b.pd) {
+            const int pi = find_pair(b.work_off, b.npairs, item);
+            Pp = b.pd + pi;
+            local = item - __ldg(b.work_off + pi);
+        }
+        const PairDev& P = *Pp;
+        const int nsx = (P.W + kScanCols - 1) / kScanCols;
+        const int u0 = (local % nsx) * kScanCols, v0 = (local / nsx) * kScanRows;
+        Row3 rl[7], rr[7];
+        // slot (i + 3 + d) mod 7 holds row v0 + i + d: rows v0 - 3 .. v0 + 1 first, v0 + 2 in flight
+#pragma unroll
+        for (int k = 0; k < 5; k++) {
+            rl[k] = finish_row(issue_row(P.L, P.W, P.H, v0 - 3 + k, u0, lane), lane);
+            rr[k] = P.cR ? finish_row(issue_row(P.R, P.W, P.H, v0 - 3 + k, u0, lane), lane) : Row3{0u, 0u, 0u};
+        }
+        RowLoad nl = issue_row(P.L, P.W, P.H, v0 + 2, u0, lane);
+        RowLoad nr = P.cR ? issue_row(P.R, P.W, P.H, v0 + 2, u0, lane) : RowLoad{0u, 0u, 0u, -1};
+        for (int g = 0; g < kScanRows / 7; g++) {
+            const int vg = v0 + 7 * g;
+            if (vg >= P.H) break;
+            // row v: finish row v + 2 (issued a row ago), issue row v + 3, then row v's outputs
+#define ROW(K)                                                                            \
+    {                                                                                     \
+        const int v = vg + K;                                                             \
+        rl[(K + 5) % 7] = finish_row(nl, lane);                                           \
+        if (P.cR) rr[(K + 5) % 7] = finish_row(nr, lane);                                 \
+        nl = issue_row(P.L, P.W, P.H, v + 3, u0, lane);                                   \
+        if (P.cR) nr = issue_row(P.R, P.W, P.H, v + 3, u0, lane);                         \
+        if (v < P.H) census_row<K>(P, prm, rl, rr, v, u0, lane);                          \
+    }
+            ROW(0) ROW(1) ROW(2) ROW(3) ROW(4) ROW(5) ROW(6)
+#undef ROW
+        }
+    }
 }
+
+template <int HALO>
+__device__ __forceinline__ void stage_tile(uint8_t (*s)[kTileW + 2 * HALO], const uint8_t* __restrict__ img, int W,
+                                           int H, int u0, int v0) {
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    for (int r = ly; r < kSeedRows + 2 * HALO; r += 8) {
+        const size_t row = (size_t)min(max(v0 + r - HALO, 0), H - 1) * W;
+        s[r][lx] = __ldg(img + row + min(max(u0 + lx - HALO, 0), W - 1));
+        if (lx < 2 * HALO) s[r][kTileW + lx] = __ldg(img + row + min(max(u0 + kTileW + lx - HALO, 0), W - 1));
+    }
+}
+
 
 // ---------------------------------------------------------------- FAST score
 // FAST-9 on the radius-3 Bresenham circle (Sec. III-A, [rosten2006machine]),
@@ -1680,7 +1770,7 @@ __global__ void k_fill_u32(uint32_t* p, uint32_t value, size_t n) {
 
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_census(const PairBatch& b, const Params& prm, cudaStream_t s) {
-    k_census<<<grid_for(b.total, 8), 256, 0, s>>>(b, prm);
+    k_census<<<grid_for(cdiv(b.total, 8), 8), 256, 0, s>>>(b, prm);  // a warp per strip item
     return cudaGetLastError();
 }
 cudaError_t launch_fast_score(const PairBatch& b, const Params& prm, cudaStream_t s) {

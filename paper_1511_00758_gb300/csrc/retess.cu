@@ -143,6 +143,8 @@ int scan_cap_of(int W, int H, int n_cap, int t_cap) {
     X(smap, int4, t_cap)                                    \
     X(gcnt, int, (size_t)n_cap + 1)                         \
     X(tperm, int, t_cap)                                    \
+    X(tpass, uint32_t, n_cap)                               \
+    X(tpos, uint32_t, n_cap)                                \
     X(plist, int4, (size_t)2 * p_cap)                       \
     X(pkey, unsigned long long, p_cap)                      \
     X(scan, int, scap)                                      \
@@ -842,6 +844,7 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
             const int2 q = m.pos[v];
             const int r = rank_of(pk(q));
             m.vcanon[r] = make_int4(q.x, q.y, __float_as_int(m.dmap[(size_t)q.y * m.W + q.x]), m.vpass[v]);
+            m.tpass[r] = m.vpass[v];
         });
         items(T, [&](int t) {
             const int4 tp = m.tr[t].a;
@@ -879,6 +882,45 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
             }
         });
         cl.sync();
+        // the support sets S_1 .. S_iters into the trace, each in canonical order: S_it is the
+        // vertices that joined at pass it or before, at their rank among those (a prefix count
+        // over the ranks per iteration); S_iters is every vertex, at its rank
+        if (m.trace && m.iters >= 1 && m.iters <= kMeshMaxIters) {
+            const int nchv = scan_chunks(n);
+            int off = 0;  // floats before S_it
+            for (int it = 1; it <= m.iters; it++) {
+                const bool last = it == m.iters;
+                if (!last) {
+                    const uint32_t lim = (uint32_t)it;
+                    auto le = [lim](uint32_t x) { return (int)(x <= lim); };
+                    warp_items(nchv, [&](int c) { scan_a(m.tpass, n, m.scan, c, le); });
+                    cl.sync();
+                    warp_items(1, [&](int) { scan_b(m.scan, nchv, &hd->s_count[it]); });
+                    cl.sync();
+                    warp_items(nchv, [&](int c) { scan_c(m.tpass, m.tpos, n, m.scan, c, le); });
+                    cl.sync();
+                } else if (lead) {
+                    hd->s_count[it] = n;
+                }
+                const int cnt = last ? n : ld_int(&hd->s_count[it]);
+                if (off + 3 * cnt > m.trace_cap) {
+                    if (lead) hd->err = 1;
+                    break;
+                }
+                items(n, [&](int r) {
+                    if (!last && m.tpass[r] > (uint32_t)it) return;
+                    const int4 q = m.vcanon[r];
+                    float* o = m.trace + off + 3 * (last ? r : (int)m.tpos[r]);
+                    o[0] = (float)q.x;
+                    o[1] = (float)q.y;
+                    o[2] = __int_as_float(q.z);
+                });
+                off += 3 * cnt;
+                // the next iteration's scan rewrites tpos: every write of this one first
+                if (!last) cl.sync();
+            }
+            if (lead) hd->trace_floats = off;
+        }
     }
 
     // ---- 5: the next pass's raster inputs (triangle id = slot, or canonical position)
