@@ -319,7 +319,7 @@ def run_ours(args):
         l_, m_, b_ = per[n]
         if l_ and m_ > 0:
             other[n] = {"gbs": (b_ / l_) / (m_ / l_ * 1e-3) / 1e9, "frac": (b_ / l_) / (m_ / l_ * 1e-3) / 1e9 / peak,
-                        "avg_launch_us": 1e3 * m_ / l_}
+                        "avg_launch_us": 1e3 * m_ / l_, "traffic": _traffic(n, b_ / l_)}
     roofline["other_kernels"] = other
     roofline["timed_launches"] = timed_launches.get(rk, 0) + (timed_launches.get("raster_clear", 0) if rk == "raster" else 0)
     roofline["timing"] = (f"CUDA events around the launches of every {PROFILE_EVERY}th round (event nodes lengthen "
