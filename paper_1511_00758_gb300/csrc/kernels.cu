@@ -48,7 +48,7 @@ int work_items(WorkKind k, const PairDev& p) {
             if (p.mesh_raster) return 0;
             return (p.small_batch ? cdiv(p.n_batch, 8) : cdiv(p.n_small, 256)) + cdiv(p.raster_items, 8) +
                    (p.n_hull >= 0 ? cdiv(p.H, 8) : 0) + (p.cg_key ? cdiv((long long)p.Wc * p.Hc, kFillCells) : 0);
-        case WK_RESAMPLE: return cdiv((long long)p.Wc * p.Hc, 8);
+        case WK_RESAMPLE: return cdiv((long long)p.Wc * p.Hc, 256);
         default: return 0;
     }
 }
@@ -1728,25 +1728,26 @@ __global__ void __launch_bounds__(288, 2) k_validate_bulk(PairBatch b, Params pr
 // ---------------------------------------------------------------- resample + match (Alg. 4)
 // One warp per cell: a C_g key becomes the interpolated disparity at its
 // pixel; a C_b key is matched along its row by the same warp search.
+// A thread per cell decodes its records (C_g's disparity D_it, 32 cells a warp, the
+// key loads coalesced); the warp then takes its cells with a C_b pick through the
+// epipolar match one after another, all 32 lanes on each (SparseEpipolarStereo).
 __device__ __forceinline__ void resample_body(const PairDev& P, int local, const Params& prm) {
-    const int cell = local * 8 + (threadIdx.x >> 5);
-    if (cell >= P.Wc * P.Hc) return;
     const int lane = threadIdx.x & 31;
-    const uint32_t gk = P.cg_key[cell], bk = P.cb_key[cell];
-    if (lane == 0) {
-        float d = __int_as_float(0x7fc00000);
-        if (gk != kNoKey) {
-            d = P.Dit[gk & kIdxMask];
-        }
-        P.cg_d[cell] = d;
-    }
+    const int cell = local * 256 + threadIdx.x;
+    const bool in = cell < P.Wc * P.Hc;
+    const uint32_t gk = in ? P.cg_key[cell] : kNoKey, bk = in ? P.cb_key[cell] : kNoKey;
+    if (in) P.cg_d[cell] = gk != kNoKey ? P.Dit[gk & kIdxMask] : __int_as_float(0x7fc00000);
     int xd = -1;
-    if (bk != kNoKey) {
-        const uint32_t p = bk & kIdxMask;
+    unsigned todo = __ballot_sync(0xffffffffu, bk != kNoKey);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint32_t p = __shfl_sync(0xffffffffu, bk, src) & kIdxMask;
         const int u = (int)(p % (uint32_t)P.W), v = (int)(p / (uint32_t)P.W);
-        xd = warp_match(P.cL, P.cR, P.W, P.H, u, v, P.dmax, prm.t_lo, prm.margin);
+        const int r = warp_match(P.cL, P.cR, P.W, P.H, u, v, P.dmax, prm.t_lo, prm.margin);
+        if (lane == src) xd = r;
     }
-    if (lane == 0) P.x_d[cell] = xd;
+    if (in) P.x_d[cell] = xd;
 }
 
 __global__ void __launch_bounds__(256) k_resample(PairBatch b, Params prm) {
