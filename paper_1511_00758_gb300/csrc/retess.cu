@@ -47,7 +47,7 @@ constexpr int kMeshThreads = 1024;  // one block per SM (61 registers a thread)
 constexpr int kMaxInsertRounds = 4096;
 constexpr int kMaxFlipRounds = 1 << 15;
 constexpr int kSoloItems = kMeshThreads;  // rounds this small run in one block
-constexpr int kScanChunk = 1024;  // elements per warp in the two-level scans
+constexpr int kScanChunk = 256;   // elements per warp in the two-level scans (8 a lane)
 constexpr unsigned long long kNoClaim = ~0ull;
 constexpr int kDropped = -3;  // edge code of a pending point not found in its triangle
 
@@ -205,7 +205,7 @@ __device__ __forceinline__ int warp_excl_scan(int x, int& total) {
 // over three phases separated by cluster barriers: (A) a warp sums each chunk
 // of kScanChunk elements into chunk[c]; (B) one warp per array scans the
 // chunk sums and stores the total; (C) a warp writes each chunk's prefixes
-// (lane l owns 32 consecutive elements).
+// (lane l owns kScanChunk / 32 consecutive elements).
 template <class F>
 __device__ __forceinline__ void scan_a(const uint32_t* in, int n, int* chunk, int c, F f) {
     const int l = threadIdx.x & 31;
@@ -231,12 +231,15 @@ __device__ __forceinline__ void scan_b(int* chunk, int nch, int* total) {
 template <class F>
 __device__ __forceinline__ void scan_c(const uint32_t* in, uint32_t* out, int n, const int* chunk, int c, F f) {
     const int l = threadIdx.x & 31;
-    const int i0 = c * kScanChunk + 32 * l;
+    constexpr int per = kScanChunk / 32;
+    const int i0 = c * kScanChunk + per * l;
     int s = 0;
-    for (int i = i0; i < i0 + 32 && i < n; i++) s += f(in[i]);
+#pragma unroll
+    for (int i = i0; i < i0 + per; i++)
+        if (i < n) s += f(in[i]);
     int tot;
     int run = chunk[c] + warp_excl_scan(s, tot);
-    for (int i = i0; i < i0 + 32 && i < n; i++) {
+    for (int i = i0; i < i0 + per && i < n; i++) {
         const int x = f(in[i]);
         out[i] = (uint32_t)run;
         run += x;
@@ -422,27 +425,72 @@ __device__ __forceinline__ void count_pending(const MeshDev& m, int t, int2 q) {
 
 __device__ __forceinline__ int ld_int(const int* p) { return *(const volatile int*)p; }
 
-__device__ __forceinline__ void add_point(const MeshDev& m, uint32_t px, float d, int T0) {
-    const uint32_t bit = 1u << (px & 31);
-    if (atomicOr(m.occ + (px >> 5), bit) & bit) return;  // a point already at this pixel keeps it
-    const int vid = atomicAdd(&m.hdr->n, 1);
-    const int slot = atomicAdd(&m.hdr->n_new, 1);
-    if (vid >= m.n_cap || slot >= m.p_cap) {
-        m.hdr->err = 1;
-        return;
+// The pass's candidate points of each lane of a warp, two a lane (want[k]: the
+// lane has candidate k, at pixel px[k] with disparity d[k]; the first wins when
+// both name one pixel), join S_{it+1} unless a point already holds the pixel.
+// The counters take one atomic per warp, and the two candidates' atomics and
+// loads are in flight together (every lane of the warp calls this).
+__device__ __forceinline__ void add_points(const MeshDev& m, const bool (&want)[2], const uint32_t (&px)[2],
+                                           const float (&d)[2], int T0) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    bool isnew[2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const uint32_t bit = 1u << (px[k] & 31);
+        isnew[k] = want[k] && !(atomicOr(m.occ + (px[k] >> 5), bit) & bit);  // a point already there keeps it
     }
-    const int t = m.planeidx[px];
-    const int2 q = make_int2((int)(px % (uint32_t)m.W), (int)(px / (uint32_t)m.W));
-    m.pos[vid] = q;
-    m.vpass[vid] = (uint8_t)m.pass;
-    m.dmap[px] = d;
-    if (t < 0 || t >= T0) {  // an evaluated pixel always has a triangle
-        m.hdr->err = 2;
-        return;
+    const unsigned nm0 = __ballot_sync(0xffffffffu, isnew[0]), nm1 = __ballot_sync(0xffffffffu, isnew[1]);
+    if ((nm0 | nm1) == 0u) return;
+    const int nn = __popc(nm0) + __popc(nm1);
+    int bv = 0, bs = 0;
+    if (lane == 0) {
+        bv = atomicAdd(&m.hdr->n, nn);
+        bs = atomicAdd(&m.hdr->n_new, nn);
     }
-    m.plist[atomicAdd(&m.hdr->n_pl[0], 1)] = make_int4(vid, t, -1, pk(q));
-    count_pending(m, t, q);
-    atomicAdd(&m.hdr->total_new, 1);
+    bv = __shfl_sync(0xffffffffu, bv, 0);
+    bs = __shfl_sync(0xffffffffu, bs, 0);
+    int t[2] = {-1, -1};
+    int2 q[2];
+    bool ok[2] = {false, false};
+    int vid[2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int o = k == 0 ? __popc(nm0 & below) : __popc(nm0) + __popc(nm1 & below);
+        vid[k] = bv + o;
+        q[k] = make_int2((int)(px[k] % (uint32_t)m.W), (int)(px[k] / (uint32_t)m.W));
+        if (!isnew[k]) continue;
+        if (vid[k] >= m.n_cap || bs + o >= m.p_cap) {
+            m.hdr->err = 1;
+            isnew[k] = false;
+            continue;
+        }
+        t[k] = m.planeidx[px[k]];
+    }
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        if (!isnew[k]) continue;
+        m.pos[vid[k]] = q[k];
+        m.vpass[vid[k]] = (uint8_t)m.pass;
+        m.dmap[px[k]] = d[k];
+        if (t[k] < 0 || t[k] >= T0) m.hdr->err = 2;  // an evaluated pixel always has a triangle
+        else ok[k] = true;
+    }
+    const unsigned om0 = __ballot_sync(0xffffffffu, ok[0]), om1 = __ballot_sync(0xffffffffu, ok[1]);
+    if ((om0 | om1) == 0u) return;
+    int bp = 0;
+    if (lane == 0) {
+        bp = atomicAdd(&m.hdr->n_pl[0], __popc(om0) + __popc(om1));
+        atomicAdd(&m.hdr->total_new, __popc(om0) + __popc(om1));
+    }
+    bp = __shfl_sync(0xffffffffu, bp, 0);
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        if (!ok[k]) continue;
+        const int o = k == 0 ? __popc(om0 & below) : __popc(om0) + __popc(om1 & below);
+        m.plist[bp + o] = make_int4(vid[k], t[k], -1, pk(q[k]));
+        count_pending(m, t[k], q[k]);
+    }
 }
 
 // Where q lies in triangle t (packed positions tp, neighbours rt): -1 inside,
@@ -553,16 +601,28 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
     // ---- 1: collect the new points (cell records in raster order of cells, or a list)
     {
         const int T0 = ld_int(&hd->T);
-        items(m.cg_key ? m.ncells : m.list_n, [&](int c) {
-            if (m.cg_key) {
-                const uint32_t gk = m.cg_key[c], bk = m.cb_key[c];
-                if (gk != kNoKey) add_point(m, gk & kIdxMask, m.cg_d[c], T0);
-                if (bk != kNoKey && m.x_d[c] >= 0) add_point(m, bk & kIdxMask, (float)m.x_d[c], T0);
-            } else {
-                const int u = m.list_uv[2 * c], v = m.list_uv[2 * c + 1];
-                add_point(m, (uint32_t)v * (uint32_t)m.W + (uint32_t)u, 0.0f, T0);
+        const int nc = m.cg_key ? m.ncells : m.list_n;
+        // whole warps iterate together (the counters are taken a warp at a time)
+        for (int c = t0; c < (nc + 31) / 32 * 32; c += tstride) {
+            const bool in = c < nc;
+            bool want[2] = {false, false};
+            uint32_t px[2] = {0u, 0u};
+            float d[2] = {0.0f, 0.0f};
+            if (m.cg_key) {  // the cell's C_g pick, then its accepted C_b match
+                const uint32_t gk = in ? m.cg_key[c] : kNoKey, bk = in ? m.cb_key[c] : kNoKey;
+                const int xd = bk != kNoKey ? m.x_d[c] : -1;
+                want[0] = gk != kNoKey;
+                px[0] = gk & kIdxMask;
+                d[0] = want[0] ? m.cg_d[c] : 0.0f;
+                want[1] = xd >= 0;
+                px[1] = bk & kIdxMask;
+                d[1] = (float)xd;
+            } else if (in) {
+                want[0] = true;
+                px[0] = (uint32_t)m.list_uv[2 * c + 1] * (uint32_t)m.W + (uint32_t)m.list_uv[2 * c];
             }
-        });
+            add_points(m, want, px, d, T0);
+        }
     }
     cl.sync();
 
