@@ -1018,6 +1018,8 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
     cudaStream_t s = c->stream;
     double seed_px = 0, validate_bytes = 0, cells_bytes = 0, raster_bytes = 0;
     for (Request* r : seed.reqs) {
+        // census and FAST strips: shorter items when few pairs share the launch (more warps)
+        r->dev.scan_rows = seed.reqs.size() >= 8 ? 14 : 7;
         seed_px += (double)r->W * r->H;
         if (!r->st_kp.ensure((size_t)kFastBins * c->K * 12)) return cudaErrorMemoryAllocation;
         void* hp = nullptr;
@@ -1548,8 +1550,13 @@ cudaError_t autotune(stereo_ctx* c) {
         b.total = o;
         return b;
     };
+    // A shape replaces the defaults only when it is measurably faster (by kTuneMargin):
+    // the candidates often time within noise of each other on the tuning round, and the
+    // small-triangle threshold also shapes the lists of the later passes' meshes, which
+    // this round does not time.
+    constexpr double kTuneMargin = 0.97;
     Tuning best = c->tune;
-    double best_r = 1e30;
+    double best_r = 1e30, default_r = -1.0;
     for (int sa : kSmall)
         for (int ba : kBatch)
             for (int cols : kCols) {
@@ -1558,6 +1565,7 @@ cudaError_t autotune(stereo_ctx* c) {
                 const PairBatch b = raster_batch();
                 const double us = time_runs(s, ea, eb, 3, [&] { return launch_raster(b, s); });
                 if (us < 0) return cudaErrorUnknown;
+                if (sa == kSmallArea && ba == kBatchArea && cols == kRasterCols) default_r = us;
                 if (us < best_r) {
                     best_r = us;
                     best.small_area = sa;
@@ -1565,6 +1573,12 @@ cudaError_t autotune(stereo_ctx* c) {
                     best.raster_cols = cols;
                 }
             }
+    if (default_r > 0 && best_r > kTuneMargin * default_r) {
+        best.small_area = kSmallArea;
+        best.batch_area = kBatchArea;
+        best.raster_cols = kRasterCols;
+        best_r = default_r;
+    }
     cudaError_t e = stage(best.small_area, best.batch_area, best.raster_cols);  // D_it for the validate
     if (e != cudaSuccess) return e;
     {
@@ -1623,7 +1637,8 @@ cudaError_t autotune(stereo_ctx* c) {
     }
     Params prm = c->prm;
     prm.err = c->err_dev;
-    double best_v = 1e30;
+    double best_v = 1e30, default_v = -1.0;
+    const Tuning defaults{};
     for (int mixed = 1; mixed >= 0; mixed--)
         for (int bps : {4, 8, 16}) {
             const double us = time_runs(s, ea, eb, 3, [&]() -> cudaError_t {
@@ -1635,12 +1650,18 @@ cudaError_t autotune(stereo_ctx* c) {
                 return cudaSuccess;
             });
             if (us < 0) return cudaErrorUnknown;
+            if (mixed == defaults.validate_mixed && bps == defaults.validate_bps) default_v = us;
             if (us < best_v) {
                 best_v = us;
                 best.validate_mixed = mixed;
                 best.validate_bps = bps;
             }
         }
+    if (default_v > 0 && best_v > kTuneMargin * default_v) {
+        best.validate_mixed = defaults.validate_mixed;
+        best.validate_bps = defaults.validate_bps;
+        best_v = default_v;
+    }
     c->tune = best;
     c->tuned = true;
     c->tune_raster_us = best_r;
@@ -2078,6 +2099,7 @@ int stereo_census(const uint8_t* left, const uint8_t* right, int w, int h, int t
     p.omega = omega;
     p.W = w;
     p.H = h;
+    p.scan_rows = 7;  // one frame: the shorter strip items (more warps)
     Params prm{0, 0, t_grad, 0, 1, 0};
     return to_rc(launch_census(single(p, WK_CENSUS), prm, (cudaStream_t)stream));
 }
@@ -2092,6 +2114,7 @@ int stereo_fast(const uint8_t* left, int w, int h, int t_fast, int K, int16_t* s
     p.W = w;
     p.H = h;
     p.K = K;
+    p.scan_rows = 7;
     Params prm{0, 0, 0, t_fast, K, 0};
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = launch_fast_score(single(p, WK_FAST_SCORE), prm, s);

@@ -31,6 +31,7 @@ struct PairDev {
     uint32_t* cR;
     uint32_t* omega;          // H * ceil(W/32) bit words
     int16_t* fast_score;      // W*H
+    int scan_rows;            // census / FAST strip rows per warp item: 7 or 14 (0: 14)
     int32_t* kp_uv;           // 120*K (u, v) slots
     int32_t* kp_d;            // 120*K matches
     const int32_t* tri_uv;    // T * 6

@@ -24,15 +24,14 @@ static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b)
 
 static int validate_items(WorkKind k, const PairDev& p);
 
-constexpr int kTileW = 32;     // census / FAST score tile: 32 columns (a warp's lanes)
-constexpr int kSeedRows = 32;  // by 32 rows
-constexpr int kScanCols = 128;  // census: a warp's strip of columns
-constexpr int kScanRows = 14;   // and rows per strip item (a multiple of the 7-row ring)
+constexpr int kScanCols = 128;  // census and FAST score: a warp's strip of columns
+constexpr int kScanRows = 14;   // and rows per strip item (a multiple of the 7-row ring; 7 on small launches)
+__host__ __device__ __forceinline__ int scan_rows(const PairDev& p) { return p.scan_rows == 7 ? 7 : kScanRows; }
 
 int work_items(WorkKind k, const PairDev& p) {
     switch (k) {
-        case WK_CENSUS: return cdiv(p.W, kScanCols) * cdiv(p.H, kScanRows);
-        case WK_FAST_SCORE: return cdiv(p.W, kTileW) * cdiv(p.H, kSeedRows);
+        case WK_CENSUS:
+        case WK_FAST_SCORE: return cdiv(p.W, kScanCols) * cdiv(p.H, scan_rows(p));
         case WK_VALIDATE:
         case WK_VALIDATE_UNIT:
         case WK_VALIDATE_C4:
@@ -258,7 +257,8 @@ __global__ void __launch_bounds__(256) k_census(PairBatch b, Params prm) {
         }
         const PairDev& P = *Pp;
         const int nsx = (P.W + kScanCols - 1) / kScanCols;
-        const int u0 = (local % nsx) * kScanCols, v0 = (local / nsx) * kScanRows;
+        const int rows = scan_rows(P);
+        const int u0 = (local % nsx) * kScanCols, v0 = (local / nsx) * rows;
         Row3 rl[7], rr[7];
         // slot (i + 3 + d) mod 7 holds row v0 + i + d: rows v0 - 3 .. v0 + 1 first, v0 + 2 in flight
 #pragma unroll
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(256) k_census(PairBatch b, Params prm) {
         }
         RowLoad nl = issue_row(P.L, P.W, P.H, v0 + 2, u0, lane);
         RowLoad nr = P.cR ? issue_row(P.R, P.W, P.H, v0 + 2, u0, lane) : RowLoad{0u, 0u, 0u, -1};
-        for (int g = 0; g < kScanRows / 7; g++) {
+        for (int g = 0; g < rows / 7; g++) {
             const int vg = v0 + 7 * g;
             if (vg >= P.H) break;
             // row v: finish row v + 2 (issued a row ago), issue row v + 3, then row v's outputs
@@ -286,18 +286,6 @@ __global__ void __launch_bounds__(256) k_census(PairBatch b, Params prm) {
         }
     }
 }
-
-template <int HALO>
-__device__ __forceinline__ void stage_tile(uint8_t (*s)[kTileW + 2 * HALO], const uint8_t* __restrict__ img, int W,
-                                           int H, int u0, int v0) {
-    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
-    for (int r = ly; r < kSeedRows + 2 * HALO; r += 8) {
-        const size_t row = (size_t)min(max(v0 + r - HALO, 0), H - 1) * W;
-        s[r][lx] = __ldg(img + row + min(max(u0 + lx - HALO, 0), W - 1));
-        if (lx < 2 * HALO) s[r][kTileW + lx] = __ldg(img + row + min(max(u0 + kTileW + lx - HALO, 0), W - 1));
-    }
-}
-
 
 // ---------------------------------------------------------------- FAST score
 // FAST-9 on the radius-3 Bresenham circle (Sec. III-A, [rosten2006machine]),
@@ -317,59 +305,137 @@ __device__ __forceinline__ bool has_run9(uint32_t m16) {
     return (r & 0xFFFFu) != 0;
 }
 
-__device__ __forceinline__ void fast_score_body(const PairDev& P, int local, const Params& prm) {
-    __shared__ uint8_t s[kSeedRows + 6][kTileW + 6];
+// One output row w of a FAST strip (ring slot K + 3 holds row w, slots mod 7 hold
+// rows w - 3 .. w + 3).  With t >= 0 a circle pixel q is brighter when
+// q > min(p + t, 255) and darker when q < max(p - t, 0) (the clamps only remove
+// comparisons that can never hold); both are tested on the lane's four pixels at
+// once with the borrow-free byte compare of the census, and the results gathered
+// into each pixel's two 16-bit masks.  The sums of the score are taken only for
+// the pixels whose masks hold a run of nine.  A negative t keeps the per-pixel
+// rule with brighter tested first.
+template <int K>
+__device__ __forceinline__ void fast_row(const PairDev& P, int t, const Row3 (&rl)[7], int w, int u0, int lane) {
     const int W = P.W, H = P.H;
-    const int tx_n = (W + kTileW - 1) / kTileW;
-    const int u0 = (local % tx_n) * kTileW, v0 = (local / tx_n) * kSeedRows;
-    stage_tile<3>(s, P.L, W, H, u0, v0);
-    __syncthreads();
-    const int lx = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int u = u0 + lx;
-    const int t = prm.t_fast;
+    const int ub = u0 + 4 * lane;
+    const uint32_t P4 = rl[(K + 3) % 7].c;
+    bool corner[4];
+    int score[4] = {0, 0, 0, 0};
+    const bool row_in = w >= 3 && w < H - 3;
+    if (t >= 0) {
+        uint32_t HI = 0u, LO = 0u;
 #pragma unroll
-    for (int k = 0; k < kSeedRows / 8; k++) {
-        const int ly = w + 8 * k, v = v0 + ly;
-        if (u >= W || v >= H) continue;
-        int score = 0;
-        if (u >= 3 && u < W - 3 && v >= 3 && v < H - 3) {
-            const int p = s[ly + 3][lx + 3];
-            uint32_t mb = 0, md = 0;
-            int sb = 0, sd = 0;
-            if (t >= 0) {  // brighter and darker exclude each other: no branches
+        for (int j = 0; j < 4; j++) {
+            const int p = (int)((P4 >> (8 * j)) & 0xFFu);
+            HI |= (uint32_t)min(p + t, 255) << (8 * j);
+            LO |= (uint32_t)max(p - t, 0) << (8 * j);
+        }
+        const uint32_t HIh = HI | 0x80808080u, LOl = LO & 0x7F7F7F7Fu;
+        uint32_t bl = 0u, bh = 0u, dl = 0u, dh = 0u;  // bit i of pixel j's masks: byte j, bit i (i < 8) of *l
 #pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    const int q = s[ly + 3 + fast_dy(i)][lx + 3 + fast_dx(i)];
-                    const int db = q - p - t, dd = p - q - t;
-                    mb |= (uint32_t)(db > 0) << i;
-                    md |= (uint32_t)(dd > 0) << i;
-                    sb += max(db, 0);
-                    sd += max(dd, 0);
-                }
+        for (int i = 0; i < 16; i++) {
+            const uint32_t Q = shifted(rl[(K + 3 + fast_dy(i) + 7) % 7], fast_dx(i));
+            const uint32_t db = HIh - (Q & 0x7F7F7F7Fu);
+            const uint32_t br = (~HI & Q) | (~(HI ^ Q) & ~db);  // top bit of each byte: HI < Q
+            const uint32_t dd = (Q | 0x80808080u) - LOl;
+            const uint32_t dk = (~Q & LO) | (~(Q ^ LO) & ~dd);  // top bit of each byte: Q < LO
+            const int b = i & 7;
+            if (i < 8) {
+                bl |= (br >> (7 - b)) & (0x01010101u << b);
+                dl |= (dk >> (7 - b)) & (0x01010101u << b);
             } else {
+                bh |= (br >> (7 - b)) & (0x01010101u << b);
+                dh |= (dk >> (7 - b)) & (0x01010101u << b);
+            }
+        }
 #pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    const int q = s[ly + 3 + fast_dy(i)][lx + 3 + fast_dx(i)];
-                    if (q > p + t) {
-                        mb |= 1u << i;
-                        sb += q - p - t;
-                    } else if (q < p - t) {
-                        md |= 1u << i;
-                        sd += p - q - t;
-                    }
+        for (int j = 0; j < 4; j++) {
+            const int u = ub + j;
+            const uint32_t mb = ((bl >> (8 * j)) & 0xFFu) | (((bh >> (8 * j)) & 0xFFu) << 8);
+            const uint32_t md = ((dl >> (8 * j)) & 0xFFu) | (((dh >> (8 * j)) & 0xFFu) << 8);
+            corner[j] = row_in && u >= 3 && u < W - 3 && (has_run9(mb) || has_run9(md));
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (!corner[j]) continue;
+            const int p = (int)((P4 >> (8 * j)) & 0xFFu);
+            int sb = 0, sd = 0;
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                const int q = (int)((shifted(rl[(K + 3 + fast_dy(i) + 7) % 7], fast_dx(i)) >> (8 * j)) & 0xFFu);
+                sb += max(q - p - t, 0);
+                sd += max(p - q - t, 0);
+            }
+            score[j] = sb > sd ? sb : sd;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int u = ub + j;
+            if (!row_in || u < 3 || u >= W - 3) continue;
+            const int p = (int)((P4 >> (8 * j)) & 0xFFu);
+            uint32_t mb = 0u, md = 0u;
+            int sb = 0, sd = 0;
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                const int q = (int)((shifted(rl[(K + 3 + fast_dy(i) + 7) % 7], fast_dx(i)) >> (8 * j)) & 0xFFu);
+                if (q > p + t) {
+                    mb |= 1u << i;
+                    sb += q - p - t;
+                } else if (q < p - t) {
+                    md |= 1u << i;
+                    sd += p - q - t;
                 }
             }
-            if (has_run9(mb) || has_run9(md)) score = sb > sd ? sb : sd;
+            if (has_run9(mb) || has_run9(md)) score[j] = sb > sd ? sb : sd;
         }
-        P.fast_score[(size_t)v * W + u] = (int16_t)score;
     }
-    __syncthreads();
+    if (ub >= W) return;
+    int16_t* out = P.fast_score + (size_t)w * W + ub;
+    if (ub + 3 < W && ((uintptr_t)out & 7) == 0) {
+        *reinterpret_cast<uint2*>(out) = make_uint2(((uint32_t)score[0] & 0xFFFFu) | ((uint32_t)score[1] << 16),
+                                                    ((uint32_t)score[2] & 0xFFFFu) | ((uint32_t)score[3] << 16));
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (ub + j < W) out[j] = (int16_t)score[j];
+    }
 }
 
+// FAST-9 scores of L in warp strips like the census: lane l owns four columns and
+// slides down the strip with rows w - 3 .. w + 3 in its ring (row w + 4 in flight).
 __global__ void __launch_bounds__(256) k_fast_score(PairBatch b, Params prm) {
-#define BODY(P, l) fast_score_body(P, l, prm)
-    FOR_EACH_ITEM(b, BODY)
-#undef BODY
+    const int lane = threadIdx.x & 31;
+    for (int item = blockIdx.x * 8 + (threadIdx.x >> 5); item < b.total; item += gridDim.x * 8) {
+        const PairDev* Pp = &b.one;
+        int local = item;
+        if (b.pd) {
+            const int pi = find_pair(b.work_off, b.npairs, item);
+            Pp = b.pd + pi;
+            local = item - __ldg(b.work_off + pi);
+        }
+        const PairDev& P = *Pp;
+        const int nsx = (P.W + kScanCols - 1) / kScanCols;
+        const int rows = scan_rows(P);
+        const int u0 = (local % nsx) * kScanCols, v0 = (local / nsx) * rows;
+        Row3 rl[7];
+        // slot (i + 3 + d) mod 7 holds row v0 + i + d: rows v0 - 3 .. v0 + 2 first, v0 + 3 in flight
+#pragma unroll
+        for (int k = 0; k < 6; k++) rl[k] = finish_row(issue_row(P.L, P.W, P.H, v0 - 3 + k, u0, lane), lane);
+        RowLoad nl = issue_row(P.L, P.W, P.H, v0 + 3, u0, lane);
+        for (int g = 0; g < rows / 7; g++) {
+            const int vg = v0 + 7 * g;
+            if (vg >= P.H) break;
+#define ROW(K)                                                                            \
+    {                                                                                     \
+        const int w = vg + K;                                                             \
+        rl[(K + 6) % 7] = finish_row(nl, lane);                                           \
+        nl = issue_row(P.L, P.W, P.H, w + 4, u0, lane);                                   \
+        if (w < P.H) fast_row<K>(P, prm.t_fast, rl, w, u0, lane);                         \
+    }
+            ROW(0) ROW(1) ROW(2) ROW(3) ROW(4) ROW(5) ROW(6)
+#undef ROW
+        }
+    }
 }
 
 // ---------------------------------------------------------------- FAST bins: NMS + top-K
@@ -1775,7 +1841,7 @@ cudaError_t launch_census(const PairBatch& b, const Params& prm, cudaStream_t s)
     return cudaGetLastError();
 }
 cudaError_t launch_fast_score(const PairBatch& b, const Params& prm, cudaStream_t s) {
-    k_fast_score<<<grid_for(b.total, 8), 256, 0, s>>>(b, prm);
+    k_fast_score<<<grid_for(cdiv(b.total, 8), 8), 256, 0, s>>>(b, prm);  // a warp per strip item
     return cudaGetLastError();
 }
 cudaError_t launch_fast_bins(const PairBatch& b, const Params& prm, cudaStream_t s) {

@@ -98,6 +98,37 @@ __device__ __forceinline__ int mk_ref(int t, int e) { return (t << 2) | e; }
 __device__ __forceinline__ int pk(int2 p) { return (p.y << 14) | p.x; }
 __device__ __forceinline__ int2 unpk(int k) { return make_int2(k & 0x3FFF, k >> 14); }
 
+// Conversions to and from fp64 built from the IEEE-754 bit layouts with integer
+// instructions: this GPU has few fp64 units, and the plane solve would otherwise
+// spend a quarter of its fp64 issue on conversions.  Each is exact (to fp64) or
+// round-to-nearest-even (to fp32); zeros, subnormals, infinities and results out
+// of fp32's normal range take the hardware conversion.
+__device__ __forceinline__ double i2d(int x) {  // exact for every int
+    if (x == 0) return 0.0;
+    const unsigned long long a = x < 0 ? (unsigned long long)(-(long long)x) : (unsigned long long)x;
+    const int e = 63 - __clzll((long long)a);
+    const unsigned long long mant = (a << (52 - e)) & ((1ull << 52) - 1ull);
+    const unsigned long long sign = x < 0 ? 1ull << 63 : 0ull;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 1023) << 52) | mant));
+}
+__device__ __forceinline__ double f2d(float f) {  // exact
+    const unsigned u = __float_as_uint(f), e8 = (u >> 23) & 0xFFu;
+    if (e8 == 0u || e8 == 255u) return (double)f;
+    return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
+                                            ((unsigned long long)(e8 - 127u + 1023u) << 52) |
+                                            ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+__device__ __forceinline__ float d2f_rn(double x) {  // round to nearest, ties to even
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e8 = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+    if (e8 <= 0 || e8 >= 254) return __double2float_rn(x);
+    const unsigned long long m = b & ((1ull << 52) - 1ull), rem = m & ((1ull << 29) - 1ull), half = 1ull << 28;
+    unsigned m23 = (unsigned)(m >> 29);
+    unsigned bits = ((unsigned)(b >> 63) << 31) | ((unsigned)e8 << 23);
+    if (rem > half || (rem == half && (m23 & 1u))) m23++;  // a carry out of the fraction raises the exponent
+    return __uint_as_float(bits + m23);
+}
+
 // q in the closed triangle with packed vertex positions tp (all three edge functions >= 0)
 __device__ __forceinline__ bool contains(const int4& tp, int2 q) {
     const int2 a = unpk(tp.x), b = unpk(tp.y), c = unpk(tp.z);
@@ -1001,17 +1032,17 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __res
         // operation (each rounded on its own: no contraction into FMAs)
         const long long u0 = P[0].x, v0 = P[0].y, u1 = P[1].x, v1 = P[1].y, u2 = P[2].x, v2 = P[2].y;
         const long long det = (u1 - u0) * (v2 - v0) - (u2 - u0) * (v1 - v0);
-        const double d0 = (double)m.dmap[v0 * m.W + u0];
-        const double e1 = __dsub_rn((double)m.dmap[v1 * m.W + u1], d0);
-        const double e2 = __dsub_rn((double)m.dmap[v2 * m.W + u2], d0);
-        const double na = __dsub_rn(__dmul_rn(e1, (double)(v2 - v0)), __dmul_rn(e2, (double)(v1 - v0)));
-        const double nb = __dsub_rn(__dmul_rn((double)(u1 - u0), e2), __dmul_rn((double)(u2 - u0), e1));
-        const double A = __ddiv_rn(na, (double)det);
-        const double B = __ddiv_rn(nb, (double)det);
-        const double C = __dsub_rn(__dsub_rn(d0, __dmul_rn(A, (double)u0)), __dmul_rn(B, (double)v0));
-        m.abc[3 * (size_t)s] = __double2float_rn(A);
-        m.abc[3 * (size_t)s + 1] = __double2float_rn(B);
-        m.abc[3 * (size_t)s + 2] = __double2float_rn(C);
+        const double d0 = f2d(m.dmap[v0 * m.W + u0]);
+        const double e1 = __dsub_rn(f2d(m.dmap[v1 * m.W + u1]), d0);
+        const double e2 = __dsub_rn(f2d(m.dmap[v2 * m.W + u2]), d0);
+        const double na = __dsub_rn(__dmul_rn(e1, i2d((int)(v2 - v0))), __dmul_rn(e2, i2d((int)(v1 - v0))));
+        const double nb = __dsub_rn(__dmul_rn(i2d((int)(u1 - u0)), e2), __dmul_rn(i2d((int)(u2 - u0)), e1));
+        const double A = __ddiv_rn(na, i2d((int)det));
+        const double B = __ddiv_rn(nb, i2d((int)det));
+        const double C = __dsub_rn(__dsub_rn(d0, __dmul_rn(A, i2d((int)u0))), __dmul_rn(B, i2d((int)v0)));
+        m.abc[3 * (size_t)s] = d2f_rn(A);
+        m.abc[3 * (size_t)s + 1] = d2f_rn(B);
+        m.abc[3 * (size_t)s + 2] = d2f_rn(C);
         // raster lists: small boxes by width class, large ones by work items
         const int x0 = max(0, min(q[0], min(q[2], q[4]))), x1 = min(m.W - 1, max(q[0], max(q[2], q[4])));
         const int y0 = max(0, min(q[1], min(q[3], q[5]))), y1 = min(m.H - 1, max(q[1], max(q[3], q[5])));
