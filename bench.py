@@ -239,12 +239,11 @@ def run_ours(args):
         t1 = time.perf_counter()
         if len(tickets) != len(pairs):
             raise RuntimeError(f"only {len(tickets)} of {len(pairs)} pairs taken")
-        for i, t in enumerate(tickets):
-            r = ctx.poll(t)
+        for r in ctx.poll_batch(tickets):
             if r.status != 0:
                 raise RuntimeError(f"request failed: {r.status}")
             lat.append(r.latency_ms)
-            ctx.release(t)
+        ctx.release_batch(tickets)
         if not host:
             host_ms["submit"] += 1e3 * (t1 - t0)
             host_ms["poll"] += 1e3 * (time.perf_counter() - t1)

@@ -187,6 +187,20 @@ int stereo_poll_host(stereo_ctx* ctx, uint64_t ticket, stereo_result* out, int t
 /* Return a finished request's buffers to the pool. */
 int stereo_release(stereo_ctx* ctx, uint64_t ticket);
 
+/* stereo_poll and stereo_release for n tickets at once, for callers serving
+ * many cameras (one call and one lock instead of n; no counterpart in the
+ * paper).  stereo_poll_batch waits up to timeout_us (<0 = forever, 0 = test
+ * only) until every ticket is done, then fills out[i] as stereo_poll would for
+ * tickets[i] (out[i].status is that request's own status).  Returns STEREO_OK
+ * when all are done (whatever their status), STEREO_E_PENDING when the time
+ * ran out first (out is then unspecified), STEREO_E_NOTFOUND when a ticket is
+ * unknown (nothing waited for), STEREO_E_INVAL for null pointers or n < 1.
+ * stereo_release_batch releases every done request among tickets[0..n) and
+ * returns STEREO_OK, or the first error stereo_release would have returned for
+ * one of them (the others are still released). */
+int stereo_poll_batch(stereo_ctx* ctx, const uint64_t* tickets, int n, stereo_result* out, int timeout_us);
+int stereo_release_batch(stereo_ctx* ctx, const uint64_t* tickets, int n);
+
 /* Cancel queued work, wait for in-flight work, free everything. */
 void stereo_destroy(stereo_ctx* ctx);
 

@@ -88,6 +88,8 @@ _SIGS = {
     "stereo_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(Result), _I]),
     "stereo_poll_host": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(Result), _I, _P, _P, _P]),
     "stereo_release": (_I, [_P, ctypes.c_uint64]),
+    "stereo_poll_batch": (_I, [_P, ctypes.POINTER(ctypes.c_uint64), _I, ctypes.POINTER(Result), _I]),
+    "stereo_release_batch": (_I, [_P, ctypes.POINTER(ctypes.c_uint64), _I]),
     "stereo_destroy": (None, [_P]),
     "stereo_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
     "stereo_get_tuning": (_I, [_P, ctypes.POINTER(Tuning)]),
@@ -312,6 +314,21 @@ class Context:
 
     def release(self, ticket):
         return _check(lib().stereo_release(self.h, ticket), "release")
+
+    def poll_batch(self, tickets, timeout_us=-1):
+        """poll for every ticket at once: the list of results (each with its own status) once
+        all are done, or None when the time ran out first."""
+        tk = (ctypes.c_uint64 * len(tickets))(*tickets)
+        out = (Result * len(tickets))()
+        rc = lib().stereo_poll_batch(self.h, tk, len(tickets), out, timeout_us)
+        if rc == E_PENDING:
+            return None
+        _check(rc, "poll_batch")
+        return list(out)
+
+    def release_batch(self, tickets):
+        tk = (ctypes.c_uint64 * len(tickets))(*tickets)
+        return _check(lib().stereo_release_batch(self.h, tk, len(tickets)), "release_batch")
 
     def stats(self):
         s = Stats()

@@ -1944,18 +1944,9 @@ int stereo_submit(stereo_ctx* c, int stream_id, const uint8_t* left, const uint8
     return rc == 1 ? STEREO_OK : rc;
 }
 
-int stereo_poll(stereo_ctx* c, uint64_t ticket, stereo_result* out, int timeout_us) {
-    if (!c || !out) return STEREO_E_INVAL;
-    std::unique_lock<std::mutex> g(c->mu);
-    auto it = c->reqs.find(ticket);
-    if (it == c->reqs.end()) return STEREO_E_NOTFOUND;
-    Request* r = it->second;
-    auto ready = [r] { return r->state == Q_DONE || r->state == Q_FAILED; };
-    if (!ready()) {
-        if (timeout_us == 0) return STEREO_E_PENDING;
-        if (timeout_us < 0) c->cv_done.wait(g, ready);
-        else if (!c->cv_done.wait_for(g, std::chrono::microseconds(timeout_us), ready)) return STEREO_E_PENDING;
-    }
+namespace {
+// A finished request's result, as stereo_poll reports it.  Called with c->mu held.
+void fill_result(const Request* r, stereo_result* out) {
     std::memset(out, 0, sizeof(*out));
     out->status = r->status;
     out->w = r->W;
@@ -1970,9 +1961,48 @@ int stereo_poll(stereo_ctx* c, uint64_t ticket, stereo_result* out, int timeout_
         out->planeidx = r->pidx_buf;
         out->n_support = r->n_support.data();
         out->n_tri = r->n_tri.data();
-        out->support = r->dev_trace ? r->st_trace.as<float>() : r->trace.data();
+        out->support = r->dev_trace ? const_cast<Pinned&>(r->st_trace).as<float>() : r->trace.data();
     }
+}
+}  // namespace
+
+int stereo_poll(stereo_ctx* c, uint64_t ticket, stereo_result* out, int timeout_us) {
+    if (!c || !out) return STEREO_E_INVAL;
+    std::unique_lock<std::mutex> g(c->mu);
+    auto it = c->reqs.find(ticket);
+    if (it == c->reqs.end()) return STEREO_E_NOTFOUND;
+    Request* r = it->second;
+    auto ready = [r] { return r->state == Q_DONE || r->state == Q_FAILED; };
+    if (!ready()) {
+        if (timeout_us == 0) return STEREO_E_PENDING;
+        if (timeout_us < 0) c->cv_done.wait(g, ready);
+        else if (!c->cv_done.wait_for(g, std::chrono::microseconds(timeout_us), ready)) return STEREO_E_PENDING;
+    }
+    fill_result(r, out);
     return r->status;
+}
+
+int stereo_poll_batch(stereo_ctx* c, const uint64_t* tickets, int n, stereo_result* out, int timeout_us) {
+    if (!c || !tickets || !out || n < 1) return STEREO_E_INVAL;
+    std::unique_lock<std::mutex> g(c->mu);
+    std::vector<Request*> rs((size_t)n);
+    for (int i = 0; i < n; i++) {
+        auto it = c->reqs.find(tickets[i]);
+        if (it == c->reqs.end()) return STEREO_E_NOTFOUND;
+        rs[i] = it->second;
+    }
+    auto all_ready = [&rs] {
+        for (const Request* r : rs)
+            if (r->state != Q_DONE && r->state != Q_FAILED) return false;
+        return true;
+    };
+    if (!all_ready()) {
+        if (timeout_us == 0) return STEREO_E_PENDING;
+        if (timeout_us < 0) c->cv_done.wait(g, all_ready);
+        else if (!c->cv_done.wait_for(g, std::chrono::microseconds(timeout_us), all_ready)) return STEREO_E_PENDING;
+    }
+    for (int i = 0; i < n; i++) fill_result(rs[i], out + i);
+    return STEREO_OK;
 }
 
 int stereo_poll_host(stereo_ctx* c, uint64_t ticket, stereo_result* out, int timeout_us, float* disparity,
@@ -1994,9 +2024,9 @@ int stereo_poll_host(stereo_ctx* c, uint64_t ticket, stereo_result* out, int tim
     return STEREO_OK;
 }
 
-int stereo_release(stereo_ctx* c, uint64_t ticket) {
-    if (!c) return STEREO_E_INVAL;
-    std::unique_lock<std::mutex> g(c->mu);
+namespace {
+// Take a done request out of the context (c->mu held): its ticket, slot and arena blocks.
+int detach(stereo_ctx* c, uint64_t ticket, Request** out) {
     auto it = c->reqs.find(ticket);
     if (it == c->reqs.end()) return STEREO_E_NOTFOUND;
     Request* r = it->second;
@@ -2007,7 +2037,11 @@ int stereo_release(stereo_ctx* c, uint64_t ticket) {
     c->arena.release(r->tri_block);
     c->arena.release(r->in_dev);
     c->arena.release(r->mesh_block);
-    g.unlock();
+    *out = r;
+    return STEREO_OK;
+}
+// Its host buffers back to the pools (c->mu not held).
+void free_request(stereo_ctx* c, Request* r) {
     r->in_host.free();
     r->st_tri.free();
     r->st_kp.free();
@@ -2016,8 +2050,39 @@ int stereo_release(stereo_ctx* c, uint64_t ticket) {
     r->st_trace.free();
     c->traces.put(std::move(r->trace));
     delete r;
+}
+}  // namespace
+
+int stereo_release(stereo_ctx* c, uint64_t ticket) {
+    if (!c) return STEREO_E_INVAL;
+    Request* r = nullptr;
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        const int rc = detach(c, ticket, &r);
+        if (rc != STEREO_OK) return rc;
+    }
+    free_request(c, r);
     c->cv_sched.notify_all();
     return STEREO_OK;
+}
+
+int stereo_release_batch(stereo_ctx* c, const uint64_t* tickets, int n) {
+    if (!c || !tickets || n < 1) return STEREO_E_INVAL;
+    std::vector<Request*> rs;
+    rs.reserve((size_t)n);
+    int first = STEREO_OK;
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        for (int i = 0; i < n; i++) {
+            Request* r = nullptr;
+            const int rc = detach(c, tickets[i], &r);
+            if (rc == STEREO_OK) rs.push_back(r);
+            else if (first == STEREO_OK) first = rc;
+        }
+    }
+    for (Request* r : rs) free_request(c, r);
+    c->cv_sched.notify_all();
+    return first;
 }
 
 const char* stereo_last_error(void) {

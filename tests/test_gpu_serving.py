@@ -95,6 +95,27 @@ def test_batch_submit_matches_single_and_takes_a_prefix():
         assert ctx.stats().requests_done == 0
 
 
+def test_poll_and_release_batch():
+    """poll_batch waits for every ticket and reports each request's own result (the same as
+    its single poll); release_batch frees them all; unknown tickets are reported."""
+    pairs = [scenes.make_pair("polygon", 160, 120, 900 + i, 32, 2, 8, n_poly=6) for i in range(5)]
+    with S.Context(mem_budget_bytes=1 << 29, max_slots=5, host_threads=2, **PRM) as ctx:
+        tk = ctx.submit_batch([(torch.from_numpy(p.left).cuda(), torch.from_numpy(p.right).cuda(), 160, 120,
+                                p.dmax, p.iters, p.cell) for p in pairs])
+        res = ctx.poll_batch(tk)
+        assert res is not None and len(res) == 5 and all(r.status == 0 and r.w == 160 for r in res)
+        single = [ctx.poll(t) for t in tk]
+        for a, b in zip(res, single):
+            assert a.disparity == b.disparity and a.latency_ms == b.latency_ms
+        with pytest.raises(S.StereoError):
+            ctx.poll_batch(tk + [123456789])
+        ctx.release_batch(tk)
+        with pytest.raises(S.StereoError):
+            ctx.poll(tk[0])  # released
+        with pytest.raises(S.StereoError):
+            ctx.release_batch(tk[:1])
+
+
 def test_queue_full_returns_busy_then_drains():
     pairs = _pairs(8, 1242, 375)
     got_busy = 0
