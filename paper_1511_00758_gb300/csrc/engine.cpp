@@ -803,6 +803,7 @@ PairBatch batch_of(const Group& g, WorkKind k) {
     b.work_off = g.off[k];
     b.npairs = (int)g.reqs.size();
     b.total = g.total[k];
+    b.scan_rows = g.reqs.empty() ? 0 : g.reqs[0]->dev.scan_rows;  // set alike for the whole group
     return b;
 }
 
@@ -2150,6 +2151,7 @@ static PairBatch single(const PairDev& p, WorkKind k) {
     b.one = p;
     b.npairs = 1;
     b.total = work_items(k, p);
+    b.scan_rows = p.scan_rows;
     return b;
 }
 

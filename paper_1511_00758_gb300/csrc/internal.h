@@ -73,6 +73,7 @@ struct PairBatch {
     int npairs;
     int total;                // work items in this launch
     PairDev one;
+    int scan_rows;            // census / FAST strip rows of every pair of the launch (PairDev::scan_rows)
 };
 
 struct Params {

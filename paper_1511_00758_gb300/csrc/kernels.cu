@@ -245,6 +245,40 @@ __device__ __forceinline__ void census_row(const PairDev& P, const Params& prm, 
     if ((lane & 7) == 0 && wi < words && P.omega) P.omega[(size_t)v * words + wi] = bits;
 }
 
+// One strip item of ROWS rows (a compile-time count, so the ring's turns unroll).
+template <int ROWS>
+__device__ __forceinline__ void census_item(const PairDev& P, const Params& prm, int local, int lane) {
+    const int nsx = (P.W + kScanCols - 1) / kScanCols;
+    const int u0 = (local % nsx) * kScanCols, v0 = (local / nsx) * ROWS;
+    Row3 rl[7], rr[7];
+    // slot (i + 3 + d) mod 7 holds row v0 + i + d: rows v0 - 3 .. v0 + 1 first, v0 + 2 in flight
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        rl[k] = finish_row(issue_row(P.L, P.W, P.H, v0 - 3 + k, u0, lane), lane);
+        rr[k] = P.cR ? finish_row(issue_row(P.R, P.W, P.H, v0 - 3 + k, u0, lane), lane) : Row3{0u, 0u, 0u};
+    }
+    RowLoad nl = issue_row(P.L, P.W, P.H, v0 + 2, u0, lane);
+    RowLoad nr = P.cR ? issue_row(P.R, P.W, P.H, v0 + 2, u0, lane) : RowLoad{0u, 0u, 0u, -1};
+    for (int g = 0; g < ROWS / 7; g++) {
+        const int vg = v0 + 7 * g;
+        if (vg >= P.H) break;
+        // row v: finish row v + 2 (issued a row ago), issue row v + 3, then row v's outputs
+#define ROW(K)                                                                            \
+    {                                                                                     \
+        const int v = vg + K;                                                             \
+        rl[(K + 5) % 7] = finish_row(nl, lane);                                           \
+        if (P.cR) rr[(K + 5) % 7] = finish_row(nr, lane);                                 \
+        nl = issue_row(P.L, P.W, P.H, v + 3, u0, lane);                                   \
+        if (P.cR) nr = issue_row(P.R, P.W, P.H, v + 3, u0, lane);                         \
+        if (v < P.H) census_row<K>(P, prm, rl, rr, v, u0, lane);                          \
+    }
+        ROW(0) ROW(1) ROW(2) ROW(3) ROW(4) ROW(5) ROW(6)
+#undef ROW
+    }
+}
+
+// Every pair of a launch takes the same strip rows (ROWS: 7 or kScanRows).
+template <int ROWS>
 __global__ void __launch_bounds__(256) k_census(PairBatch b, Params prm) {
     const int lane = threadIdx.x & 31;
     for (int item = blockIdx.x * 8 + (threadIdx.x >> 5); item < b.total; item += gridDim.x * 8) {
@@ -255,35 +289,7 @@ __global__ void __launch_bounds__(256) k_census(PairBatch b, Params prm) {
             Pp = b.pd + pi;
             local = item - __ldg(b.work_off + pi);
         }
-        const PairDev& P = *Pp;
-        const int nsx = (P.W + kScanCols - 1) / kScanCols;
-        const int rows = scan_rows(P);
-        const int u0 = (local % nsx) * kScanCols, v0 = (local / nsx) * rows;
-        Row3 rl[7], rr[7];
-        // slot (i + 3 + d) mod 7 holds row v0 + i + d: rows v0 - 3 .. v0 + 1 first, v0 + 2 in flight
-#pragma unroll
-        for (int k = 0; k < 5; k++) {
-            rl[k] = finish_row(issue_row(P.L, P.W, P.H, v0 - 3 + k, u0, lane), lane);
-            rr[k] = P.cR ? finish_row(issue_row(P.R, P.W, P.H, v0 - 3 + k, u0, lane), lane) : Row3{0u, 0u, 0u};
-        }
-        RowLoad nl = issue_row(P.L, P.W, P.H, v0 + 2, u0, lane);
-        RowLoad nr = P.cR ? issue_row(P.R, P.W, P.H, v0 + 2, u0, lane) : RowLoad{0u, 0u, 0u, -1};
-        for (int g = 0; g < rows / 7; g++) {
-            const int vg = v0 + 7 * g;
-            if (vg >= P.H) break;
-            // row v: finish row v + 2 (issued a row ago), issue row v + 3, then row v's outputs
-#define ROW(K)                                                                            \
-    {                                                                                     \
-        const int v = vg + K;                                                             \
-        rl[(K + 5) % 7] = finish_row(nl, lane);                                           \
-        if (P.cR) rr[(K + 5) % 7] = finish_row(nr, lane);                                 \
-        nl = issue_row(P.L, P.W, P.H, v + 3, u0, lane);                                   \
-        if (P.cR) nr = issue_row(P.R, P.W, P.H, v + 3, u0, lane);                         \
-        if (v < P.H) census_row<K>(P, prm, rl, rr, v, u0, lane);                          \
-    }
-            ROW(0) ROW(1) ROW(2) ROW(3) ROW(4) ROW(5) ROW(6)
-#undef ROW
-        }
+        census_item<ROWS>(*Pp, prm, local, lane);
     }
 }
 
@@ -401,8 +407,33 @@ __device__ __forceinline__ void fast_row(const PairDev& P, int t, const Row3 (&r
     }
 }
 
+template <int ROWS>
+__device__ __forceinline__ void fast_item(const PairDev& P, int t, int local, int lane) {
+    const int nsx = (P.W + kScanCols - 1) / kScanCols;
+    const int u0 = (local % nsx) * kScanCols, v0 = (local / nsx) * ROWS;
+    Row3 rl[7];
+    // slot (i + 3 + d) mod 7 holds row v0 + i + d: rows v0 - 3 .. v0 + 2 first, v0 + 3 in flight
+#pragma unroll
+    for (int k = 0; k < 6; k++) rl[k] = finish_row(issue_row(P.L, P.W, P.H, v0 - 3 + k, u0, lane), lane);
+    RowLoad nl = issue_row(P.L, P.W, P.H, v0 + 3, u0, lane);
+    for (int g = 0; g < ROWS / 7; g++) {
+        const int vg = v0 + 7 * g;
+        if (vg >= P.H) break;
+#define ROW(K)                                                                            \
+    {                                                                                     \
+        const int w = vg + K;                                                             \
+        rl[(K + 6) % 7] = finish_row(nl, lane);                                           \
+        nl = issue_row(P.L, P.W, P.H, w + 4, u0, lane);                                   \
+        if (w < P.H) fast_row<K>(P, t, rl, w, u0, lane);                                  \
+    }
+        ROW(0) ROW(1) ROW(2) ROW(3) ROW(4) ROW(5) ROW(6)
+#undef ROW
+    }
+}
+
 // FAST-9 scores of L in warp strips like the census: lane l owns four columns and
 // slides down the strip with rows w - 3 .. w + 3 in its ring (row w + 4 in flight).
+template <int ROWS>
 __global__ void __launch_bounds__(256) k_fast_score(PairBatch b, Params prm) {
     const int lane = threadIdx.x & 31;
     for (int item = blockIdx.x * 8 + (threadIdx.x >> 5); item < b.total; item += gridDim.x * 8) {
@@ -413,28 +444,7 @@ __global__ void __launch_bounds__(256) k_fast_score(PairBatch b, Params prm) {
             Pp = b.pd + pi;
             local = item - __ldg(b.work_off + pi);
         }
-        const PairDev& P = *Pp;
-        const int nsx = (P.W + kScanCols - 1) / kScanCols;
-        const int rows = scan_rows(P);
-        const int u0 = (local % nsx) * kScanCols, v0 = (local / nsx) * rows;
-        Row3 rl[7];
-        // slot (i + 3 + d) mod 7 holds row v0 + i + d: rows v0 - 3 .. v0 + 2 first, v0 + 3 in flight
-#pragma unroll
-        for (int k = 0; k < 6; k++) rl[k] = finish_row(issue_row(P.L, P.W, P.H, v0 - 3 + k, u0, lane), lane);
-        RowLoad nl = issue_row(P.L, P.W, P.H, v0 + 3, u0, lane);
-        for (int g = 0; g < rows / 7; g++) {
-            const int vg = v0 + 7 * g;
-            if (vg >= P.H) break;
-#define ROW(K)                                                                            \
-    {                                                                                     \
-        const int w = vg + K;                                                             \
-        rl[(K + 6) % 7] = finish_row(nl, lane);                                           \
-        nl = issue_row(P.L, P.W, P.H, w + 4, u0, lane);                                   \
-        if (w < P.H) fast_row<K>(P, prm.t_fast, rl, w, u0, lane);                         \
-    }
-            ROW(0) ROW(1) ROW(2) ROW(3) ROW(4) ROW(5) ROW(6)
-#undef ROW
-        }
+        fast_item<ROWS>(*Pp, prm.t_fast, local, lane);
     }
 }
 
@@ -1837,11 +1847,15 @@ __global__ void k_fill_u32(uint32_t* p, uint32_t value, size_t n) {
 
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_census(const PairBatch& b, const Params& prm, cudaStream_t s) {
-    k_census<<<grid_for(cdiv(b.total, 8), 8), 256, 0, s>>>(b, prm);  // a warp per strip item
+    const int grid = grid_for(cdiv(b.total, 8), 8);  // a warp per strip item
+    if (b.scan_rows == 7) k_census<7><<<grid, 256, 0, s>>>(b, prm);
+    else k_census<kScanRows><<<grid, 256, 0, s>>>(b, prm);
     return cudaGetLastError();
 }
 cudaError_t launch_fast_score(const PairBatch& b, const Params& prm, cudaStream_t s) {
-    k_fast_score<<<grid_for(cdiv(b.total, 8), 8), 256, 0, s>>>(b, prm);  // a warp per strip item
+    const int grid = grid_for(cdiv(b.total, 8), 8);  // a warp per strip item
+    if (b.scan_rows == 7) k_fast_score<7><<<grid, 256, 0, s>>>(b, prm);
+    else k_fast_score<kScanRows><<<grid, 256, 0, s>>>(b, prm);
     return cudaGetLastError();
 }
 cudaError_t launch_fast_bins(const PairBatch& b, const Params& prm, cudaStream_t s) {
