@@ -1183,10 +1183,19 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
         Lr.timed.clear();
         return err;
     }
-    // shape: stages present, timing, and the launch counts of the raster kinds and the mesh pass
+    // shape: stages present, timing, the launch counts of the raster kinds and the mesh pass, the
+    // cluster size of the last mesh launch and the census / FAST strip rows.  An executable graph is
+    // only updated in place from a graph of the same shape: the update carries new kernel arguments
+    // and grids, but a mesh launch's cluster size (set from its pair count) is a launch attribute,
+    // so graphs whose clusters differ are kept apart.
     const int n_mr_launch = (iter.n_mr + kMeshBatch - 1) / kMeshBatch, n_mp_launch = (iter.n_mp + kMeshBatch - 1) / kMeshBatch;
+    const int last_np = iter.n_mp - (n_mp_launch - 1) * kMeshBatch;
+    const int cluster = n_mp_launch > 0 ? mesh_cluster_blocks(last_np) : 0;
+    const int cluster_bits = cluster >= 8 ? 3 : cluster >= 4 ? 2 : cluster >= 2 ? 1 : 0;
+    const int short_strips = !seed.reqs.empty() && seed.reqs[0]->dev.scan_rows == 7 ? 1 : 0;
     const int shape = (seed.reqs.empty() ? 0 : 1) | (iter.reqs.empty() ? 0 : 2) | (Lr.prof ? 4 : 0) |
-                      ((int)iter.reqs.size() > iter.n_mr ? 8 : 0) | (n_mr_launch << 4) | (n_mp_launch << 12);
+                      ((int)iter.reqs.size() > iter.n_mr ? 8 : 0) | (n_mr_launch << 4) | (n_mp_launch << 12) |
+                      (cluster_bits << 24) | (short_strips << 26);
     cudaGraphExec_t& exec = c->graph_exec[shape];
     bool updated = false;
     if (exec) {
@@ -1312,7 +1321,7 @@ void scheduler(stereo_ctx* c) {
                 if (h.err != 0) {
                     char what[160];
                     std::snprintf(what, sizeof(what),
-                                  "device mesh pass %d failed: code %d (1 capacity, 2 location, 3 round limit), "
+                                  "device mesh pass %d failed: code %d (1 capacity, 2 location, 3 round limit, 4 launch shape), "
                                   "n %d T %d new %d inserted %d/%d rounds %d", r->it, h.err, h.n, h.T, h.n_new,
                                   h.inserted, h.total_new, h.rounds);
                     note_error(cudaErrorUnknown, what, __LINE__);

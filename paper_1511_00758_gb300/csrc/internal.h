@@ -161,7 +161,8 @@ struct MeshHdr {
     int cls[kMeshClasses];           // small triangles per box width class
     int cls_fill[kMeshClasses];
     int stamp;                       // last stamp of the split / flip records
-    int err;                         // nonzero: 1 capacity, 2 a point not found in its triangle, 3 round limit
+    int err;                         // nonzero: 1 capacity, 2 a point not found in its triangle, 3 round limit,
+                                     // 4 a launch whose clusters did not match its pair count
     int rounds, flips;               // insertion rounds and flips of the last pass
     int frounds;                     // flip rounds of the last pass
     int n_pl[2];                     // entries of the two pending worklists (this round's, the next's)

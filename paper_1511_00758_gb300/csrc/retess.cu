@@ -561,9 +561,13 @@ __device__ __forceinline__ int relocate(const MeshDev& m, int t, int2 q, int sta
 // One pair per thread-block cluster: the cluster's blocks share the pair's
 // items and meet at the cluster barrier between phases, so each pair runs at
 // its own pace and no barrier spans the grid.
-__global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __restrict__ mdg) {
+__global__ void __launch_bounds__(kMeshThreads) k_mesh_pass(const MeshDev* __restrict__ mdg, int np) {
     cg::cluster_group cl = cg::this_cluster();
     const int nblk = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    if ((int)gridDim.x != np * nblk) {  // clusters that do not tile the pairs: no descriptor is read past np
+        if (blockIdx.x == 0 && (int)threadIdx.x < np) atomicExch(&mdg[threadIdx.x].hdr->err, 4);
+        return;  // every block leaves (the test is uniform over the grid)
+    }
     __shared__ MeshDev sm;  // the pair's descriptor
     for (int i = threadIdx.x; i < (int)(sizeof(MeshDev) / 4); i += blockDim.x)
         reinterpret_cast<int*>(&sm)[i] = reinterpret_cast<const int*>(mdg + blockIdx.x / nblk)[i];
@@ -1131,7 +1135,7 @@ cudaError_t launch_mesh_pass(const MeshDev* md, int np, cudaStream_t s) {
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_mesh_pass, md);
+    return cudaLaunchKernelEx(&cfg, k_mesh_pass, md, np);
 }
 
 }  // namespace stereo

@@ -116,6 +116,34 @@ def test_poll_and_release_batch():
             ctx.release_batch(tk[:1])
 
 
+def test_rounds_of_changing_pair_counts():
+    """Rounds of 40, 5 and 24 pairs on one context: the device mesh launches of these rounds take
+    clusters of 2, 8 and 4 blocks, so each round's graph differs from the last in its launch
+    shape.  Every pair gives what it gives in a batch of its own kind on a fresh context."""
+    sizes = (40, 5, 24)
+    pairs = [scenes.make_pair("polygon", 160, 120, 950 + i, 32, 3, 8, n_poly=6) for i in range(sum(sizes))]
+    batch = lambda ps: [(p.left, p.right, 160, 120, p.dmax, p.iters, p.cell) for p in ps]
+    got = []
+    with S.Context(mem_budget_bytes=1 << 31, max_slots=64, host_threads=2, **PRM) as ctx:
+        o = 0
+        for n in sizes:
+            tk = ctx.submit_batch(batch(pairs[o:o + n]))
+            assert len(tk) == n
+            got += [ctx.result_tensors(r) for r in ctx.poll_batch(tk)]
+            ctx.release_batch(tk)
+            o += n
+    with S.Context(mem_budget_bytes=1 << 31, max_slots=64, host_threads=2, **PRM) as ctx:
+        tk = ctx.submit_batch(batch(pairs[:64]))
+        want = [ctx.result_tensors(r) for r in ctx.poll_batch(tk)]
+        ctx.release_batch(tk)
+        tk = ctx.submit_batch(batch(pairs[64:]))
+        want += [ctx.result_tensors(r) for r in ctx.poll_batch(tk)]
+        ctx.release_batch(tk)
+    for g, w in zip(got, want):
+        for k in ("D_f", "C_f", "mask", "planeidx"):
+            assert torch.equal(g[k], w[k])
+
+
 def test_queue_full_returns_busy_then_drains():
     pairs = _pairs(8, 1242, 375)
     got_busy = 0
