@@ -328,7 +328,9 @@ def run_ours(args):
         nl = s1.kind_launches[i] - s0.kind_launches[i]
         nt = s1.kind_timed[i] - s0.kind_timed[i]
         mt = s1.kind_ms[i] - s0.kind_ms[i]
-        kinds[name] = {"launches": nl, "timed": nt, "ms": round(mt / nt * nl, 4) if nt else 0.0}
+        kb = s1.kind_bytes[i] - s0.kind_bytes[i]
+        kinds[name] = {"launches": nl, "timed": nt, "ms": round(mt / nt * nl, 4) if nt else 0.0,
+                       "algorithmic_bytes_per_launch": kb / nl if nl else None}
     tuning = ctx.tuning()
     rounds = s1.gpu_rounds - s0.gpu_rounds
     round_stats = {"rounds_per_step": rounds / args.steps,
@@ -724,19 +726,21 @@ def run_sweep(args):
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
         for iters in (1, 2, 4):
             def step(keep=False):
-                ts = [ctx.submit(l, r, W, H, dmax, iters, p.cell) for (l, r), p in zip(dev, pairs)]
+                ts = ctx.submit_batch([(l, r, W, H, dmax, iters, p.cell) for (l, r), p in zip(dev, pairs)])
+                if len(ts) != len(pairs):
+                    raise RuntimeError("the batch was not taken whole")
                 res = []
-                for t in ts:
-                    r = ctx.poll(t)
+                for r in ctx.poll_batch(ts):
                     if r.status != 0:
                         raise RuntimeError(f"request failed: {r.status}")
                     if keep:
                         o = ctx.result_tensors(r)
                         res.append({k: o[k].cpu().numpy() for k in ("D_f", "C_f", "mask")})
-                    ctx.release(t)
+                ctx.release_batch(ts)
                 return res
             step()
             spans = []
+            s0 = ctx.stats()
             for _ in range(max(1, args.steps)):
                 flush.fill_(1)
                 torch.cuda.synchronize()
@@ -746,11 +750,19 @@ def run_sweep(args):
                 e1.record(ctx.stream)
                 e1.synchronize()
                 spans.append(e0.elapsed_time(e1))
+            s1 = ctx.stats()
+            nsteps = max(1, args.steps)
+            kern = {}
+            for i, name in enumerate(S.KINDS):
+                nl, nt = s1.kind_launches[i] - s0.kind_launches[i], s1.kind_timed[i] - s0.kind_timed[i]
+                if nl and nt:
+                    kern[name] = round((s1.kind_ms[i] - s0.kind_ms[i]) / nt * nl / nsteps, 4)
             res = step(keep=True)  # results for the accuracy protocol, outside the timed steps
             acc = [accuracy(o["D_f"], o["C_f"], o["mask"], p.gt_disp, p.gt_occ, PRM["t_hi"]) for o, p in zip(res, pairs)]
             ms = sum(spans) / len(spans) / len(pairs)
             rows.append({"W": W, "H": H, "dmax": dmax, "iters": iters, "pairs": len(pairs), "ms_per_pair": ms,
                          "mpix_s": W * H / (ms * 1e-3) / 1e6,
+                         "rounds_per_step": (s1.gpu_rounds - s0.gpu_rounds) / nsteps, "kernel_ms_per_step": kern,
                          **{k: float(np.mean([a[k] for a in acc])) for k in acc[0]}})
         ctx.close()
     out = {"metric": "ms per pair and error rates (sweep of the paper's runtime table)", "workload": "sweep",
