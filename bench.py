@@ -547,10 +547,10 @@ def run_kernel(args, which):
     Df = torch.zeros((H, W), dtype=torch.float32, device="cuda")
     Cf = torch.full((H, W), PRM["t_hi"], dtype=torch.uint8, device="cuda")
     mask = torch.empty((H, W), dtype=torch.uint8, device="cuda")
-    sz = 8
+    sz = max(1, args.cell)  # cell side of the resample records (--cell 0: the last pass, no records)
     nc = -(-W // sz) * -(-H // sz)
-    cg = torch.empty(nc, dtype=torch.int32, device="cuda")
-    cb = torch.empty(nc, dtype=torch.int32, device="cuda")
+    cg = torch.empty(nc, dtype=torch.int32, device="cuda") if args.cell > 0 else None
+    cb = torch.empty(nc, dtype=torch.int32, device="cuda") if args.cell > 0 else None
     # a mesh for the raster: a jittered lattice of support points, triangulated on the host
     import numpy as np
     rng = np.random.default_rng(6)
@@ -573,8 +573,9 @@ def run_kernel(args, which):
 
     def once():
         if which == "validate":
-            cg.fill_(-1)
-            cb.fill_(-1)
+            if cg is not None:
+                cg.fill_(-1)
+                cb.fill_(-1)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             if args.plain_kernel:
@@ -603,6 +604,7 @@ def run_kernel(args, which):
     out = {"kernel": ("k_validate" if args.plain_kernel else "k_validate_bulk") if which == "validate"
            else "k_raster_clear + k_raster (D_it only)",
            "frame": f"{W}x{H}", "pixels": px, "triangles": T if which == "raster" else None,
+           "cell": args.cell if which == "validate" else None,
            "algorithmic_bytes": algo, "avg_us": 1e3 * avg, "gbs": algo / (avg * 1e-3) / 1e9,
            "frac": algo / (avg * 1e-3) / 1e9 / peak, "peak": peak, "steps": args.steps, "warmup": args.warmup}
     print(json.dumps(out))
@@ -795,6 +797,7 @@ def main():
     ap.add_argument("--config", choices=("driving_1242x375", "vga_polygons"), default="driving_1242x375",
                     help="scene configuration of the main workload (and of --impl reference)")
     ap.add_argument("--kernel-size", type=int, default=4096)
+    ap.add_argument("--cell", type=int, default=8, help="kernel-validate: cell side of the resample records (0: none)")
     ap.add_argument("--plain-kernel", action="store_true", help="kernel-validate: the single-pass kernel")
     ap.add_argument("--mesh-step", type=int, default=6, help="kernel-raster: support-point spacing in pixels")
     ap.add_argument("--rate-hz", type=float, default=120.0)

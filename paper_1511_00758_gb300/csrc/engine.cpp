@@ -298,6 +298,8 @@ struct Request {
     MeshDev mesh{};             // its arrays (host copy of the descriptor)
     size_t seed_off = 0;        // offset of the seed mesh arrays in the staging blob (pass 1)
     Pinned st_hdr;              // the mesh header after each device pass
+    void* hdr_view = nullptr;   // st_hdr's address on the device (null: copied by the copy engine)
+    const void* hdr_view_of = nullptr;  // the st_hdr buffer hdr_view belongs to
     Pinned st_trace;            // device mesh: S_1 .. S_iters as (u, v, d) floats, written by the last pass
     bool dev_trace = false;     // st_trace holds the trace (the device wrote it)
     int dev_n = 0;              // vertices after the last device pass
@@ -909,10 +911,21 @@ cudaError_t issue_outputs(stereo_ctx* c, Group& seed, Group& iter, cudaStream_t 
     for (Request* r : seed.reqs)  // keypoint slots and their matches, one copy
         if (!r->direct_kp)
             CK(cudaMemcpyAsync(r->st_kp.p, r->dev.kp_uv, (size_t)kFastBins * c->K * 12, cudaMemcpyDeviceToHost, s));
-    // the results of the requests this round finishes, into the caller's buffers: one
-    // gather-copy launch for those the device can write, a copy each for the others
+    // the results of the requests this round finishes, into the caller's buffers, and the
+    // device meshes' headers, into page-locked memory: one gather-copy launch (per
+    // kCopyBatch buffers) for those the device can write, a copy each for the others
     CopyList outs{};
+    auto gather = [&](const void* src, void* dst, size_t bytes) -> cudaError_t {
+        outs.src[outs.count] = (const uint8_t*)src;
+        outs.dst[outs.count] = (uint8_t*)dst;
+        outs.n[outs.count++] = (long long)bytes;
+        if (outs.count < kCopyBatch) return cudaSuccess;
+        const cudaError_t e = launch_copy_list(outs, s);
+        outs.count = 0;
+        return e;
+    };
     for (Request* r : iter.reqs) {
+        if (r->mesh_now && r->hdr_view) CK(gather(r->mesh.hdr, r->hdr_view, sizeof(MeshHdr)));
         if (r->resample_now) continue;
         const size_t N = (size_t)r->W * r->H;
         const void* src[3] = {r->dev.Df, r->dev.Cf, r->dev.mask};
@@ -923,19 +936,13 @@ cudaError_t issue_outputs(stereo_ctx* c, Group& seed, Group& iter, cudaStream_t 
                 CK(cudaMemcpyAsync(r->out[k], src[k], bytes[k], cudaMemcpyDeviceToHost, s));
                 continue;
             }
-            outs.src[outs.count] = (const uint8_t*)src[k];
-            outs.dst[outs.count] = (uint8_t*)r->out[k];
-            outs.n[outs.count++] = (long long)bytes[k];
-            if (outs.count == kCopyBatch) {
-                CK(launch_copy_list(outs, s));
-                outs.count = 0;
-            }
+            CK(gather(src[k], r->out[k], bytes[k]));
         }
     }
     if (outs.count > 0) CK(launch_copy_list(outs, s));
     for (Request* r : iter.reqs) {
-        if (r->mesh_now) {  // the device mesh's counters after its re-tessellation
-            CK(cudaMemcpyAsync(r->st_hdr.p, r->mesh.hdr, sizeof(MeshHdr), cudaMemcpyDeviceToHost, s));
+        if (r->mesh_now) {  // the device mesh's counters after its re-tessellation (gathered above)
+            if (!r->hdr_view) CK(cudaMemcpyAsync(r->st_hdr.p, r->mesh.hdr, sizeof(MeshHdr), cudaMemcpyDeviceToHost, s));
             continue;
         }
         if (!r->resample_now) continue;
@@ -1111,6 +1118,15 @@ cudaError_t gpu_round(stereo_ctx* c, Group& seed, Group& iter, Launcher& Lr) {
                     m.seed_T = r->T;
                 }
                 if (!r->st_hdr.ensure(sizeof(MeshHdr))) return cudaErrorMemoryAllocation;
+                if (r->hdr_view_of != r->st_hdr.p) {  // the device's view of the page-locked header
+                    void* hp = nullptr;
+                    if (cudaHostGetDevicePointer(&hp, r->st_hdr.p, 0) != cudaSuccess) {
+                        cudaGetLastError();
+                        hp = nullptr;
+                    }
+                    r->hdr_view = hp;
+                    r->hdr_view_of = r->st_hdr.p;
+                }
                 m.trace = nullptr;
                 m.trace_cap = 0;
                 m.iters = r->iters;
