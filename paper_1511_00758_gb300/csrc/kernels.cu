@@ -1419,8 +1419,10 @@ __device__ __forceinline__ void validate_dispatch(const VDesc& a, int s, const P
 
 // Warps stride over the batch's strips; each strip finds its pair in the
 // batch's prefix table (kernel parameters).
+// The 4- and 2-row strips of 4- and 2-pixel cells fit 32 registers: eight blocks an SM.
 template <int KIND>
-__global__ void __launch_bounds__(256, 4) k_validate(const __grid_constant__ VBatch b, Params prm) {
+__global__ void __launch_bounds__(256, (KIND == WK_VALIDATE_C4 || KIND == WK_VALIDATE_C2) ? 8 : 4)
+    k_validate(const __grid_constant__ VBatch b, Params prm) {
     const int nw = gridDim.x * (blockDim.x >> 5);
     if (b.npairs == 1) {  // one pair: its fields are fixed constant-bank operands
         for (int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < b.total; s += nw)
@@ -1931,23 +1933,30 @@ cudaError_t launch_validate(const PairDev* pairs, int n, WorkKind k, const Param
     while (i < n || nl < min_launches) {  // up to kVBatch pairs with work per launch
         vb.npairs = 0;
         vb.total = 0;
+        int cls = -1;         // the launch's one cell-side class, or -2 when it has several
         for (; i < n && vb.npairs < kVBatch; i++) {
             const int items = work_items(k, pairs[i]);
             if (items <= 0) continue;
+            const int pk = (int)validate_kind(pairs[i]);
+            cls = cls == -1 || cls == pk ? pk : -2;
             vb.d[vb.npairs] = vdesc_of(pairs[i]);
             vb.off[vb.npairs++] = vb.total;
             vb.total += items;
         }
         if (vb.npairs == 0 && nl >= min_launches) break;
         vb.off[vb.npairs] = vb.total;
+        // a mixed launch whose pairs share one class takes that class's kernel (no
+        // dispatch, fewer registers); the 4- and 2-row strips fill eight blocks an SM
+        const WorkKind kk = k == WK_VALIDATE_MIXED && cls >= 0 ? (WorkKind)cls : k;
+        const int bk = kk == WK_VALIDATE_C4 || kk == WK_VALIDATE_C2 ? std::max(bps, 8) : bps;
         cudaError_t e;
-        switch (k) {
-            case WK_VALIDATE: e = launch_vbatch<WK_VALIDATE>(vb, prm, s, bps); break;
-            case WK_VALIDATE_UNIT: e = launch_vbatch<WK_VALIDATE_UNIT>(vb, prm, s, bps); break;
-            case WK_VALIDATE_C4: e = launch_vbatch<WK_VALIDATE_C4>(vb, prm, s, bps); break;
-            case WK_VALIDATE_C2: e = launch_vbatch<WK_VALIDATE_C2>(vb, prm, s, bps); break;
-            case WK_VALIDATE_ANY: e = launch_vbatch<WK_VALIDATE_ANY>(vb, prm, s, bps); break;
-            case WK_VALIDATE_MIXED: e = launch_vbatch<WK_VALIDATE_MIXED>(vb, prm, s, bps); break;
+        switch (kk) {
+            case WK_VALIDATE: e = launch_vbatch<WK_VALIDATE>(vb, prm, s, bk); break;
+            case WK_VALIDATE_UNIT: e = launch_vbatch<WK_VALIDATE_UNIT>(vb, prm, s, bk); break;
+            case WK_VALIDATE_C4: e = launch_vbatch<WK_VALIDATE_C4>(vb, prm, s, bk); break;
+            case WK_VALIDATE_C2: e = launch_vbatch<WK_VALIDATE_C2>(vb, prm, s, bk); break;
+            case WK_VALIDATE_ANY: e = launch_vbatch<WK_VALIDATE_ANY>(vb, prm, s, bk); break;
+            case WK_VALIDATE_MIXED: e = launch_vbatch<WK_VALIDATE_MIXED>(vb, prm, s, bk); break;
             default: e = cudaErrorInvalidValue;
         }
         if (e != cudaSuccess) return e;
