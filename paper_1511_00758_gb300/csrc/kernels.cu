@@ -543,13 +543,13 @@ __global__ void __launch_bounds__(256) k_fast_bins(PairBatch b, Params prm) {
 // One warp per query (Sec. III-A; Alg. 4 SparseEpipolarStereo).  Lanes stride
 // the disparity range; the argmin packs (cost << 8) | d, so ties go to the
 // smallest d.  The uniqueness test is a second minimum over |d - d*| >= 2.
-__device__ __forceinline__ int warp_match(const uint32_t* __restrict__ cL, const uint32_t* __restrict__ cR,
-                                          int W, int H, int u, int v, int dmax, int t_lo, int margin) {
+// The query's left census code cl is passed in.
+__device__ __forceinline__ int warp_match_code(const uint32_t* __restrict__ cR, int W, int H, int u, int v,
+                                               uint32_t cl, int dmax, int t_lo, int margin) {
     const int lane = threadIdx.x & 31;
     if (u < 2 || u >= W - 2 || v < 2 || v >= H - 2) return -1;
     const int dlim = min(dmax - 1, u - 2);
     const size_t p = (size_t)v * W + u;
-    const uint32_t cl = __ldg(cL + p);
     const uint32_t* row = cR + p;
     uint32_t cost[8];
     uint32_t best = 0xFFFFFFFFu;
@@ -574,6 +574,13 @@ __device__ __forceinline__ int warp_match(const uint32_t* __restrict__ cL, const
     second = __reduce_min_sync(0xffffffffu, second);
     if (second != 0xFFu && (int)second < cstar + margin) return -1;
     return dstar;
+}
+
+// The same for a query whose left code is read here.
+__device__ __forceinline__ int warp_match(const uint32_t* __restrict__ cL, const uint32_t* __restrict__ cR,
+                                          int W, int H, int u, int v, int dmax, int t_lo, int margin) {
+    if (u < 2 || u >= W - 2 || v < 2 || v >= H - 2) return -1;
+    return warp_match_code(cR, W, H, u, v, __ldg(cL + (size_t)v * W + u), dmax, t_lo, margin);
 }
 
 __device__ __forceinline__ void match_kp_body(const PairDev& P, int local, const Params& prm) {
@@ -1820,14 +1827,18 @@ __device__ __forceinline__ void resample_body(const PairDev& P, int local, const
     const bool in = cell < P.Wc * P.Hc;
     const uint32_t gk = in ? P.cg_key[cell] : kNoKey, bk = in ? P.cb_key[cell] : kNoKey;
     if (in) P.cg_d[cell] = gk != kNoKey ? P.Dit[gk & kIdxMask] : __int_as_float(0x7fc00000);
+    // each lane reads its own C_b pick's left code up front (all lanes at once), so a
+    // match in the warp's chain waits on the right-row loads only
+    const uint32_t mycl = bk != kNoKey ? __ldg(P.cL + (bk & kIdxMask)) : 0u;
     int xd = -1;
     unsigned todo = __ballot_sync(0xffffffffu, bk != kNoKey);
     while (todo) {
         const int src = __ffs(todo) - 1;
         todo &= todo - 1;
         const uint32_t p = __shfl_sync(0xffffffffu, bk, src) & kIdxMask;
+        const uint32_t cl = __shfl_sync(0xffffffffu, mycl, src);
         const int u = (int)(p % (uint32_t)P.W), v = (int)(p / (uint32_t)P.W);
-        const int r = warp_match(P.cL, P.cR, P.W, P.H, u, v, P.dmax, prm.t_lo, prm.margin);
+        const int r = warp_match_code(P.cR, P.W, P.H, u, v, cl, P.dmax, prm.t_lo, prm.margin);
         if (lane == src) xd = r;
     }
     if (in) P.x_d[cell] = xd;
