@@ -370,6 +370,17 @@ public:
         }
         cv_.notify_one();
     }
+    // Many tasks under one lock, every idle worker woken at once (one wake-up per
+    // task in turn spread the starts of a round's host steps over 0.2 ms).
+    void push_all(std::vector<std::function<void()>>& fs) {
+        if (fs.empty()) return;
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            for (auto& f : fs) q_.push_back(std::move(f));
+        }
+        fs.clear();
+        cv_.notify_all();
+    }
     // Workers waiting for a task (a hint: it may change at once).
     int idle() const { return idle_.load(std::memory_order_relaxed); }
     void stop() {
@@ -1370,12 +1381,14 @@ void scheduler(stereo_ctx* c) {
             }
             host.push_back(r);
         }
+        std::vector<std::function<void()>> tasks;
+        tasks.reserve(host.size());
         for (Request* r : host) {
             r->state = Q_HOST;
             c->host_busy++;
             const bool is_seed = r->it == 0;
             if (is_seed) c->cohort_busy[r->cohort]++;
-            c->pool.push([c, r, is_seed] {
+            tasks.emplace_back([c, r, is_seed] {
                 const double t0 = now_ms();
                 int rc = is_seed ? host_after_seed(c, *r) : host_after_iter(*r);
                 r->mesh_ms += now_ms() - t0;  // the whole host step
@@ -1393,6 +1406,7 @@ void scheduler(stereo_ctx* c) {
                 c->cv_done.notify_all();
             });
         }
+        c->pool.push_all(tasks);
         c->cv_done.notify_all();
     }
 }
