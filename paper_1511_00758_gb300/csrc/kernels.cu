@@ -1999,9 +1999,19 @@ __global__ void __launch_bounds__(256) k_copy_list(const __grid_constant__ CopyL
     const long long per = (n / kCopyParts + 15) / 16 * 16;
     const long long lo = min(n, per * part), hi = min(n, lo + per);
     if ((((uintptr_t)src | (uintptr_t)dst) & 15) == 0) {
-        const long long w0 = lo / 16, w1 = hi / 16;
-        for (long long w = w0 + threadIdx.x; w < w1; w += blockDim.x)
-            reinterpret_cast<uint4*>(dst)[w] = __ldcv(reinterpret_cast<const uint4*>(src) + w);
+        const long long w0 = lo / 16, w1 = hi / 16, bs = blockDim.x;
+        const uint4* s4 = reinterpret_cast<const uint4*>(src);
+        uint4* d4 = reinterpret_cast<uint4*>(dst);
+        long long w = w0 + threadIdx.x;
+        for (; w + 3 * bs < w1; w += 4 * bs) {  // four loads in flight a thread
+            const uint4 a = __ldcv(s4 + w), b = __ldcv(s4 + w + bs), c = __ldcv(s4 + w + 2 * bs),
+                        d = __ldcv(s4 + w + 3 * bs);
+            d4[w] = a;
+            d4[w + bs] = b;
+            d4[w + 2 * bs] = c;
+            d4[w + 3 * bs] = d;
+        }
+        for (; w < w1; w += bs) d4[w] = __ldcv(s4 + w);
         for (long long i = max(lo, w1 * 16) + threadIdx.x; i < hi; i += blockDim.x) dst[i] = __ldcv(src + i);
     } else {
         for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) dst[i] = __ldcv(src + i);
