@@ -1989,7 +1989,7 @@ cudaError_t launch_validate_bulk(const PairBatch& b, const Params& prm, cudaStre
 // 16-byte words when both ends are 16-byte aligned (bytes otherwise).  A source
 // may be page-locked host memory that the caller rewrites between calls, so the
 // loads fetch again rather than trust a cached line (ld.global.cv).
-constexpr int kCopyParts = 8;
+constexpr int kCopyParts = 16;  // blocks per entry: 8 moved device-to-host results 1.4 % slower end to end
 __global__ void __launch_bounds__(256) k_copy_list(const __grid_constant__ CopyList L) {
     const int e = blockIdx.x / kCopyParts, part = blockIdx.x % kCopyParts;
     if (e >= L.count) return;
